@@ -1,0 +1,85 @@
+"""UNO training loss and gradients (oracle; test infrastructure only).
+
+* Loss (Eq. (fnocg-loss)): ``L = (1/N_s) sum_j || P_theta f_j - u_j ||^2`` with
+  ``P_theta = T^H Q(theta) T``; ``loss_by_definition`` evaluates it by applying the
+  preconditioner in real space.
+* Closed forms of Sec. 5.4: after transforming the data once, ``L`` is a quadratic in the
+  block entries v; for c = 1 (Eq. (features-c-1)) ``L = a . (v*v) - b . v + delta`` and
+  ``dL/dv = 2 a * v - b`` with ``a = mean |T f|^2`` and ``b = 2 mean Re(conj(T f) T u)``.
+  Here the sums over the full grid are taken on the half grid with the multiplicity of each
+  mode (1 on the self-conjugate planes, 2 elsewhere).
+* ``grad_entries_general``: the gradient for any c from
+  ``dL/dQ_ij(k) = (2/N_s) sum_j w_k Re(conj(Q R - U)_i R_j)`` with the symmetric entries
+  collected in the paper's order (App. B.2), then chained through psi.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import dft, uno
+
+
+def spectra(fields: np.ndarray) -> np.ndarray:
+    """Unitary half-grid spectra of a batch ``[B, c, N1, N2, N3] -> [B, c, N1, N2, N3h]``."""
+    return dft.rfftn_u(fields)
+
+
+def loss_by_definition(Q, f_batch, u_batch) -> float:
+    total = 0.0
+    for f, u in zip(f_batch, u_batch):
+        s = uno.uno_apply(Q, f)
+        total += float(np.sum((s - u) ** 2))
+    return total / len(f_batch)
+
+
+def loss_from_spectra(Q, R, U, shape) -> float:
+    w = dft.half_multiplicity(shape)
+    S = np.einsum("xyzij,bjxyz->bixyz", Q, R)
+    return float(np.sum(w * np.abs(S - U) ** 2)) / R.shape[0]
+
+
+def features_c1(R, U, shape):
+    """Features a, b of Eq. (features-c-1) on the half grid (multiplicity included)."""
+    w = dft.half_multiplicity(shape)
+    a = w * np.mean(np.abs(R[:, 0]) ** 2, axis=0)
+    b = w * 2.0 * np.mean(np.real(np.conj(R[:, 0]) * U[:, 0]), axis=0)
+    return a, b
+
+
+def grad_v_c1(v, R, U, shape):
+    """``dL/dv = 2 a * v - b`` (Sec. 5.4, c = 1)."""
+    a, b = features_c1(R, U, shape)
+    return 2.0 * a * v - b
+
+
+def grad_entries_general(Q, R, U, shape):
+    """Gradient of the loss w.r.t. the unique entries ``[N1,N2,N3h,C]`` (paper order)."""
+    c = Q.shape[-1]
+    w = dft.half_multiplicity(shape)
+    S = np.einsum("xyzij,bjxyz->bixyz", Q, R)
+    E = S - U
+    G = 2.0 * np.real(np.einsum("bixyz,bjxyz->xyzij", np.conj(E), R)) * w[..., None, None]
+    G /= R.shape[0]
+    if c == 1:
+        return G[..., 0, :]
+    out = np.zeros(G.shape[:3] + (6,))
+    for m, (i, j) in enumerate(uno.PAPER_ORDER):
+        out[..., m] = G[..., i, j] if i == j else G[..., i, j] + G[..., j, i]
+    return out
+
+
+def grad_theta(theta, grad_entries, c: int):
+    """Chain rule through psi: ``dL/dtheta`` from ``dL/dv``."""
+    theta = np.asarray(theta, dtype=np.float64)
+    if c == 1:
+        return 2.0 * theta * grad_entries
+    eps = 1e-7
+    out = np.zeros_like(theta)
+    for m in range(theta.shape[-1]):
+        tp = theta.copy()
+        tm = theta.copy()
+        tp[..., m] += eps
+        tm[..., m] -= eps
+        dv = (uno.entries_from_blocks(uno.psi(tp, 3)) - uno.entries_from_blocks(uno.psi(tm, 3))) / (2 * eps)
+        out[..., m] = np.sum(dv * grad_entries, axis=-1)
+    return out

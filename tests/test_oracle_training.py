@@ -1,0 +1,71 @@
+"""Pins of the oracle's training loss and gradients (Eq. fnocg-loss, Sec. 5.4)."""
+import numpy as np
+import pytest
+
+from oracle import dft, training, uno
+from synth import random_field
+
+
+def _data(c, shape, B, seed):
+    f = np.stack([random_field((c,) + shape, seed=seed + b) for b in range(B)])
+    u = np.stack([random_field((c,) + shape, seed=seed + 100 + b) for b in range(B)])
+    return f, u
+
+
+@pytest.mark.parametrize("c", [1, 3])
+def test_loss_spectral_equals_definition(c):
+    shape = (4, 3, 6)
+    f, u = _data(c, shape, 3, 1)
+    rng = np.random.default_rng(2)
+    th = rng.standard_normal((4, 3, 4, c * (c + 1) // 2))
+    Q = uno.symmetrize_half(uno.psi(th, c), 6)
+    R, U = training.spectra(f), training.spectra(u)
+    assert training.loss_from_spectra(Q, R, U, shape) == pytest.approx(
+        training.loss_by_definition(Q, f, u), rel=1e-12)
+
+
+def test_c1_closed_form_gradient_matches_fd():
+    shape = (4, 4, 6)
+    f, u = _data(1, shape, 2, 3)
+    rng = np.random.default_rng(4)
+    v = np.abs(rng.standard_normal((4, 4, 4))) + 0.1
+    v = uno.symmetrize_half(v[..., None, None], 6)[..., 0, 0]
+    R, U = training.spectra(f), training.spectra(u)
+    g = training.grad_v_c1(v, R, U, shape)
+    # independent check: central differences of the loss by definition, perturbing one
+    # half-grid entry (and its mirror on the self-conjugate planes)
+    for idx in [(1, 2, 1), (0, 1, 0), (2, 3, 3), (3, 0, 2)]:
+        eps = 1e-6
+        vp, vm = v.copy(), v.copy()
+        mirror = ((-idx[0]) % 4, (-idx[1]) % 4, idx[2])
+        for vv, s in ((vp, eps), (vm, -eps)):
+            vv[idx] += s
+            if idx[2] in (0, 3) and mirror != idx:
+                vv[mirror] += s
+        lp = training.loss_by_definition(vp[..., None, None], f, u)
+        lm = training.loss_by_definition(vm[..., None, None], f, u)
+        fd = (lp - lm) / (2 * eps)
+        an = g[idx] + (g[mirror] if idx[2] in (0, 3) and mirror != idx else 0.0)
+        assert an == pytest.approx(fd, rel=1e-6, abs=1e-8)
+
+
+def test_c3_gradient_and_theta_chain_match_fd():
+    shape = (3, 2, 4)
+    f, u = _data(3, shape, 2, 5)
+    rng = np.random.default_rng(6)
+    th = rng.standard_normal((3, 2, 3, 6))
+    R, U = training.spectra(f), training.spectra(u)
+    Q = uno.psi(th, 3)
+    ge = training.grad_entries_general(Q, R, U, shape)
+    gt = training.grad_theta(th, ge, 3)
+
+    def L(theta):
+        return training.loss_from_spectra(uno.psi(theta, 3), R, U, shape)
+
+    for idx in [(0, 1, 1, 0), (2, 0, 2, 4), (1, 1, 1, 5), (0, 0, 1, 2)]:
+        eps = 1e-6
+        tp, tm = th.copy(), th.copy()
+        tp[idx] += eps
+        tm[idx] -= eps
+        fd = (L(tp) - L(tm)) / (2 * eps)
+        assert gt[idx] == pytest.approx(fd, rel=1e-6, abs=1e-8)
