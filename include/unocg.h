@@ -1,0 +1,183 @@
+/*
+ * unocg.h -- C ABI of the GB300 (sm_103a) UNO-CG solver for periodic voxel homogenization.
+ *
+ * The solver is the preconditioned conjugate gradient method of Algorithm 1 with the unitary
+ * neural operator (UNO) preconditioner of Sec. 5.2, i.e. Algorithm 2 ("UNO-CG"), applied to the
+ * periodic FE homogenization problems of Sec. 6: thermal conduction (c = 1 DOF per node, Sec.
+ * 6.1) and linear elasticity (c = 3, Sec. 6.2) on a regular grid of trilinear hexahedral voxels
+ * (Sec. 4.1).  Every step of the solve runs in this library's CUDA kernels on one GPU.
+ *
+ * Conventions
+ *   - Grid N1 x N2 x N3, node/voxel (i1, i2, i3) with i3 fastest; voxel edge h = L0 / N1.
+ *   - Host field I/O uses the paper's interleaved DOF order (Sec. 2.1): value of component j
+ *     at node i at index c*i + j (double precision).
+ *   - Loads: thermal macroscopic gradients g_bar (3 values each); elastic macroscopic strains
+ *     eps_bar in Mandel notation [11, 22, 33, sqrt2*12, sqrt2*13, sqrt2*23] (App. A).
+ *   - A context holds B >= 1 instances of one grid size (a batch), each with the same number
+ *     of phases; all instances share the load cases.
+ *
+ * Ownership and errors
+ *   - Host pointers are read or written synchronously during the call and never retained.
+ *   - The library owns every device buffer it allocates; `_dev` entry points take caller-owned
+ *     device pointers plus a cudaStream_t (passed as void*), never free them, and enqueue work
+ *     on that stream without synchronizing.
+ *   - Every int-returning call returns UNOCG_OK (0) or a negative UNOCG_ERR_* code; the message
+ *     of the last failure of a context is returned by unocg_last_error().
+ */
+#ifndef UNOCG_H
+#define UNOCG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define UNOCG_OK 0
+#define UNOCG_ERR_INVALID_ARG -1    /* bad size, pointer, enum or unsupported grid */
+#define UNOCG_ERR_OOM -2            /* device allocation failed */
+#define UNOCG_ERR_NOT_SPD -3        /* weights fail the safety check lambda_min(Q(k)) > eps */
+#define UNOCG_ERR_NOT_CONVERGED -4  /* max_iter reached before the tolerance */
+#define UNOCG_ERR_BREAKDOWN -5      /* r.s <= 0, d.p <= 0 or a NaN/Inf in a reduction */
+#define UNOCG_ERR_DEVICE_TIMEOUT -6 /* a bounded device-side wait gave up */
+#define UNOCG_ERR_CUDA -7           /* a CUDA runtime call failed (message has the detail) */
+#define UNOCG_ERR_STATE -8          /* call out of order (e.g. solve before microstructure) */
+
+/* physics */
+#define UNOCG_THERMAL 1 /* c = 1: conductivity kappa per phase, loads are gradients (3)   */
+#define UNOCG_ELASTIC 3 /* c = 3: (E, nu) per phase, loads are Mandel strains (6)          */
+
+/* preconditioners */
+#define UNOCG_PRECOND_NONE 0
+#define UNOCG_PRECOND_JACOBI 1 /* P = diag(K)^-1, Sec. 4.2                          */
+#define UNOCG_PRECOND_UNO 2    /* P = T^H Q T, Eq. (FNOCG-prec-fields-disc)         */
+
+/* precision */
+#define UNOCG_FP64 0  /* every field and reduction in double precision                   */
+#define UNOCG_MIXED 1 /* FP32 fields, K.u, transforms and block multiply; BF16 weights;
+                         FP64 dot products, scalars, periodic true-residual replacement    */
+
+/* weight kinds for unocg_set_uno_weights */
+#define UNOCG_W_REFERENCE_MEDIUM 0 /* Q(k) = S_ref(k)^-1 (k != 0), Q(0) = 0: the FANS
+                                      fundamental solution of Sec. 4.3.4 for a homogeneous
+                                      medium with the arithmetic mean of the phase
+                                      conductivities / Lame constants; `w` unused          */
+#define UNOCG_W_BLOCKS 1           /* unique block entries on the half grid,
+                                      [N1][N2][N3/2+1][C] in the paper's order (App. B.2)
+                                      v1=Q11 v2=Q22 v3=Q12 v4=Q33 v5=Q23 v6=Q13 (C = 1 or 6) */
+#define UNOCG_W_THETA 2            /* parameters theta [N1][N2][N3/2+1][C] mapped through the
+                                      local parametrization psi (Sec. 5.2.2, App. B.1)        */
+
+/* dtypes of weight arrays */
+#define UNOCG_DTYPE_F64 0
+#define UNOCG_DTYPE_F32 1
+
+typedef struct unocg_ctx unocg_ctx;
+
+typedef struct {
+  double tol;        /* relative residual: stop when ||r||_inf <= tol * ||r_0||_inf        */
+  int max_iter;      /* iterations per (instance, load) before UNOCG_ERR_NOT_CONVERGED      */
+  int precond;       /* UNOCG_PRECOND_*                                                     */
+  int precision;     /* UNOCG_FP64 or UNOCG_MIXED                                           */
+  int replace_every; /* MIXED: true-residual replacement period (iterations), e.g. 50      */
+  int flexible;      /* 1: Polak-Ribiere coefficient (flexible CG), 0: Algorithm 1's        */
+  int use_graph;     /* 1: whole loop in one CUDA graph with device-side control (default);
+                        0: host-driven loop, one residual check per iteration (debugging)  */
+} unocg_solve_opts;
+
+typedef struct {
+  int status;          /* UNOCG_OK or the first failing per-(instance, load) status          */
+  int max_iters;       /* largest iteration count over all (instance, load)                 */
+  int* iters;          /* optional [B*L]: iterations                                        */
+  double* rel_res;     /* optional [B*L]: final ||r||_inf / ||r_0||_inf (recursive residual) */
+  double* true_rel_res;/* optional [B*L]: final ||f - K u||_inf / ||f||_inf in FP64         */
+  int* load_status;    /* optional [B*L]: per (instance, load) status                       */
+} unocg_solve_info;
+
+/* Create a context for `batch` instances on an n1 x n2 x n3 grid (each n_i of the form
+   2^a 3^b 5^c, n3 even, every n_i >= 2) with RVE edge L0 along axis 1.  Sec. 4.1.          */
+int unocg_create(unocg_ctx** out, int physics, int batch, int n1, int n2, int n3, double L0);
+void unocg_destroy(unocg_ctx* ctx);
+const char* unocg_last_error(const unocg_ctx* ctx);
+
+/* Use `stream` (a cudaStream_t) for all work of this context; NULL = the context's own.    */
+int unocg_set_stream(unocg_ctx* ctx, void* stream);
+
+/* Voxel phase labels, uint8 [B][N1][N2][N3] (host), labels < n_phases (Sec. 6).           */
+int unocg_set_microstructure(unocg_ctx* ctx, const uint8_t* phase, int n_phases);
+/* Same from caller-owned device memory (enqueued on `stream`).                             */
+int unocg_set_microstructure_dev(unocg_ctx* ctx, const uint8_t* phase_dev, int n_phases, void* stream);
+
+/* Phase properties [B][n_phases] kappa (thermal) or [B][n_phases][2] (E, nu) (elastic).    */
+int unocg_set_phase_properties(unocg_ctx* ctx, const double* props);
+
+/* Macroscopic load cases: [n_loads][3] gradients or [n_loads][6] Mandel strains.            */
+int unocg_set_macro_load(unocg_ctx* ctx, int n_loads, const double* loads);
+
+/* UNO weights (Eq. (fnocg-parametrization), Eq. (prec-sparse-def)); performs the safety check
+   of the Remark after Algorithm 2 (lambda_min(Q(k)) > spd_eps for all k != 0) and returns
+   UNOCG_ERR_NOT_SPD if it fails, also after rounding to BF16 for the mixed path.  `w` is host
+   memory of `dtype`; shared by all instances (REFERENCE_MEDIUM is per instance).            */
+int unocg_set_uno_weights(unocg_ctx* ctx, int kind, const void* w, int dtype, double spd_eps);
+
+/* Solve all (instance, load) systems K u = f to tolerance (Algorithm 1 / 2), then compute the
+   zero-mean fluctuations and the averaged flux / stress.  Blocks until done.               */
+int unocg_solve(unocg_ctx* ctx, const unocg_solve_opts* opts, unocg_solve_info* info);
+/* Enqueue the same work on the context stream without waiting; read results with
+   unocg_solve_wait.                                                                         */
+int unocg_solve_async(unocg_ctx* ctx, const unocg_solve_opts* opts);
+int unocg_solve_wait(unocg_ctx* ctx, unocg_solve_info* info);
+
+/* Zero-mean fluctuation of one (instance, load): host double [N1*N2*N3*c], interleaved.    */
+int unocg_get_fluctuation(unocg_ctx* ctx, int instance, int load, double* out);
+/* Same into caller-owned device memory, layout [c][N1][N2][N3] (double).                   */
+int unocg_get_fluctuation_dev(unocg_ctx* ctx, int instance, int load, double* out_dev, void* stream);
+
+/* Averaged flux / stress per load (Sec. 6): out[B][dim][n_loads], out[b][i][l] = <C (eps_bar_l
+   + eps(u_l))>_i (thermal dim 3: kappa_eff g_bar = -<q>; elastic dim 6, Mandel).  With the
+   unit loads in order this is the effective tensor, row-major.                             */
+int unocg_get_effective_tensor(unocg_ctx* ctx, double* out);
+
+/* Derivative of the energy averages W_lm = <(eps_bar_l + eps(u_l)) . C (eps_bar_m + eps(u_m))>
+   with respect to the phase properties (kappa_p; or E_p, nu_p): out[B][n_props][L][L].  K is
+   self-adjoint, so the adjoint states are the forward solutions; needs a converged solve.  */
+int unocg_get_sensitivity(unocg_ctx* ctx, double* out);
+
+/* Solve several contexts (different grid sizes) in one device-resident loop with
+   per-(instance, load) convergence masks.  infos may be NULL or hold n_ctx entries.        */
+int unocg_batch_solve(int n_ctx, unocg_ctx* const* ctxs, const unocg_solve_opts* opts,
+                      unocg_solve_info* infos);
+
+/* ---------------------------------------------------------------- standalone UNO operator
+   P = T^H Q T on a batch of fields, for training (Sec. 5.3, Algorithm 3).                  */
+typedef struct unocg_uno unocg_uno;
+int unocg_uno_create(unocg_uno** out, int c, int n1, int n2, int n3);
+void unocg_uno_destroy(unocg_uno* op);
+const char* unocg_uno_last_error(const unocg_uno* op);
+/* theta_dev: device float [N1][N2][N3/2+1][C], mapped through psi on every call.            */
+int unocg_uno_set_theta_dev(unocg_uno* op, const float* theta_dev, void* stream);
+/* s = P r for a batch: r_dev, s_dev device float [batch][c][N1][N2][N3].                    */
+int unocg_uno_apply_dev(unocg_uno* op, int batch, const float* r_dev, float* s_dev, void* stream);
+/* Backward of s = P r: gr = P gs (P is self-adjoint) and gtheta = dL/dtheta (device float,
+   [N1][N2][N3/2+1][C]; overwritten) from dL/dQ(k) = sum_b w_k Re(conj(T gs_b) (T r_b)^T).   */
+int unocg_uno_backward_dev(unocg_uno* op, int batch, const float* r_dev, const float* gs_dev,
+                           float* gr_dev, float* gtheta_dev, void* stream);
+
+/* ---------------------------------------------------------------- operator-level entry points
+   Device-pointer access to single steps of the hot path, on a context's microstructure and
+   properties (instance 0 .. B-1 via `instance`).  Fields are double [c][N1][N2][N3].        */
+/* p = K d (Sec. 4.1, matrix-free), in FP64.                                                 */
+int unocg_apply_K_dev(unocg_ctx* ctx, int instance, const double* d_dev, double* p_dev, void* stream);
+/* s = P r with the context's current UNO weights (Algorithm 2, transform / block multiply /
+   inverse transform), in FP64.                                                             */
+int unocg_apply_uno_dev(unocg_ctx* ctx, int instance, const double* r_dev, double* s_dev, void* stream);
+/* Right-hand side f of load `load` (Sec. 6): double [c][N1][N2][N3].                        */
+int unocg_rhs_dev(unocg_ctx* ctx, int instance, int load, double* f_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* UNOCG_H */

@@ -1,0 +1,203 @@
+"""Python entry points with the names of the C ABI (``include/unocg.h``).
+
+Host arrays are NumPy arrays; device arrays are torch CUDA tensors (PyTorch supplies device
+memory and streams only).  Every function marshals its arguments and calls the library.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import SolveInfo, SolveOpts, UnocgError
+
+
+def _check(ctx, rc):
+    if rc != _lib.OK:
+        lib = _lib.load()
+        msg = lib.unocg_last_error(ctx).decode() if ctx else ""
+        raise UnocgError(rc, msg)
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def unocg_create(physics: int, batch: int, n1: int, n2: int, n3: int, L0: float = 1.0):
+    lib = _lib.load()
+    h = C.c_void_p()
+    rc = lib.unocg_create(C.byref(h), physics, batch, n1, n2, n3, L0)
+    if rc != _lib.OK:
+        msg = lib.unocg_last_error(h).decode() if h.value else "invalid arguments or unsupported grid"
+        if h.value:
+            lib.unocg_destroy(h)
+        raise UnocgError(rc, msg)
+    return h
+
+
+def unocg_destroy(ctx):
+    _lib.load().unocg_destroy(ctx)
+
+
+def unocg_set_stream(ctx, stream=None):
+    _check(ctx, _lib.load().unocg_set_stream(ctx, _stream(stream) if stream is not None else None))
+
+
+def unocg_set_microstructure(ctx, phase: np.ndarray, n_phases: int):
+    ph = np.ascontiguousarray(phase, dtype=np.uint8)
+    _check(ctx, _lib.load().unocg_set_microstructure(ctx, _ptr(ph), n_phases))
+
+
+def unocg_set_microstructure_dev(ctx, phase_dev, n_phases: int, stream=None):
+    _check(ctx, _lib.load().unocg_set_microstructure_dev(ctx, C.c_void_p(phase_dev.data_ptr()), n_phases, _stream(stream)))
+
+
+def unocg_set_phase_properties(ctx, props: np.ndarray):
+    p = np.ascontiguousarray(props, dtype=np.float64)
+    _check(ctx, _lib.load().unocg_set_phase_properties(ctx, _ptr(p)))
+
+
+def unocg_set_macro_load(ctx, loads: np.ndarray):
+    l2 = np.ascontiguousarray(np.atleast_2d(loads), dtype=np.float64)
+    _check(ctx, _lib.load().unocg_set_macro_load(ctx, l2.shape[0], _ptr(l2)))
+
+
+def unocg_set_uno_weights(ctx, kind: int, w: np.ndarray | None = None, spd_eps: float = 0.0):
+    if w is None:
+        _check(ctx, _lib.load().unocg_set_uno_weights(ctx, kind, None, _lib.DTYPE_F64, spd_eps))
+        return
+    a = np.ascontiguousarray(w)
+    dt = _lib.DTYPE_F64 if a.dtype == np.float64 else _lib.DTYPE_F32
+    if dt == _lib.DTYPE_F32:
+        a = a.astype(np.float32)
+    _check(ctx, _lib.load().unocg_set_uno_weights(ctx, kind, _ptr(a), dt, spd_eps))
+
+
+def make_opts(tol=1e-6, max_iter=10000, precond=_lib.PRECOND_UNO, precision=_lib.FP64,
+              replace_every=50, flexible=None, use_graph=1) -> SolveOpts:
+    if flexible is None:
+        flexible = 1 if precision == _lib.MIXED else 0
+    return SolveOpts(tol, max_iter, precond, precision, replace_every, flexible, use_graph)
+
+
+class Info:
+    """Per-(instance, load) results of a solve."""
+
+    def __init__(self, n: int):
+        self.iters = np.zeros(n, dtype=np.int32)
+        self.rel_res = np.zeros(n)
+        self.true_rel_res = np.zeros(n)
+        self.load_status = np.zeros(n, dtype=np.int32)
+        self.c = SolveInfo(0, 0, self.iters.ctypes.data_as(C.POINTER(C.c_int)),
+                           self.rel_res.ctypes.data_as(C.POINTER(C.c_double)),
+                           self.true_rel_res.ctypes.data_as(C.POINTER(C.c_double)),
+                           self.load_status.ctypes.data_as(C.POINTER(C.c_int)))
+
+    @property
+    def status(self):
+        return self.c.status
+
+
+def unocg_solve(ctx, opts: SolveOpts, n_results: int, raise_on_error: bool = True) -> Info:
+    info = Info(n_results)
+    rc = _lib.load().unocg_solve(ctx, C.byref(opts), C.byref(info.c))
+    if raise_on_error:
+        _check(ctx, rc)
+    return info
+
+
+def unocg_solve_async(ctx, opts: SolveOpts):
+    _check(ctx, _lib.load().unocg_solve_async(ctx, C.byref(opts)))
+
+
+def unocg_solve_wait(ctx, n_results: int, raise_on_error: bool = True) -> Info:
+    info = Info(n_results)
+    rc = _lib.load().unocg_solve_wait(ctx, C.byref(info.c))
+    if raise_on_error:
+        _check(ctx, rc)
+    return info
+
+
+def unocg_get_fluctuation(ctx, instance: int, load: int, n_values: int) -> np.ndarray:
+    out = np.empty(n_values, dtype=np.float64)
+    _check(ctx, _lib.load().unocg_get_fluctuation(ctx, instance, load, _ptr(out)))
+    return out
+
+
+def unocg_get_fluctuation_dev(ctx, instance: int, load: int, out_dev, stream=None):
+    _check(ctx, _lib.load().unocg_get_fluctuation_dev(ctx, instance, load, C.c_void_p(out_dev.data_ptr()), _stream(stream)))
+
+
+def unocg_get_effective_tensor(ctx, batch: int, dim: int, n_loads: int) -> np.ndarray:
+    out = np.empty((batch, dim, n_loads), dtype=np.float64)
+    _check(ctx, _lib.load().unocg_get_effective_tensor(ctx, _ptr(out)))
+    return out
+
+
+def unocg_get_sensitivity(ctx, batch: int, n_props: int, n_loads: int) -> np.ndarray:
+    out = np.empty((batch, n_props, n_loads, n_loads), dtype=np.float64)
+    _check(ctx, _lib.load().unocg_get_sensitivity(ctx, _ptr(out)))
+    return out
+
+
+def unocg_batch_solve(ctxs, opts: SolveOpts):
+    arr = (C.c_void_p * len(ctxs))(*[c.value for c in ctxs])
+    rc = _lib.load().unocg_batch_solve(len(ctxs), arr, C.byref(opts), None)
+    if rc != _lib.OK:
+        raise UnocgError(rc, "batch solve failed")
+
+
+def unocg_apply_K_dev(ctx, instance: int, d_dev, p_dev, stream=None):
+    _check(ctx, _lib.load().unocg_apply_K_dev(ctx, instance, C.c_void_p(d_dev.data_ptr()),
+                                              C.c_void_p(p_dev.data_ptr()), _stream(stream)))
+
+
+def unocg_apply_uno_dev(ctx, instance: int, r_dev, s_dev, stream=None):
+    _check(ctx, _lib.load().unocg_apply_uno_dev(ctx, instance, C.c_void_p(r_dev.data_ptr()),
+                                                C.c_void_p(s_dev.data_ptr()), _stream(stream)))
+
+
+def unocg_rhs_dev(ctx, instance: int, load: int, f_dev, stream=None):
+    _check(ctx, _lib.load().unocg_rhs_dev(ctx, instance, load, C.c_void_p(f_dev.data_ptr()), _stream(stream)))
+
+
+# ---------------------------------------------------------------- standalone UNO operator
+def _ucheck(op, rc):
+    if rc != _lib.OK:
+        raise UnocgError(rc, _lib.load().unocg_uno_last_error(op).decode() if op else "")
+
+
+def unocg_uno_create(c: int, n1: int, n2: int, n3: int):
+    h = C.c_void_p()
+    _ucheck(None, _lib.load().unocg_uno_create(C.byref(h), c, n1, n2, n3))
+    return h
+
+
+def unocg_uno_destroy(op):
+    _lib.load().unocg_uno_destroy(op)
+
+
+def unocg_uno_set_theta_dev(op, theta_dev, stream=None):
+    _ucheck(op, _lib.load().unocg_uno_set_theta_dev(op, C.c_void_p(theta_dev.data_ptr()), _stream(stream)))
+
+
+def unocg_uno_apply_dev(op, batch: int, r_dev, s_dev, stream=None):
+    _ucheck(op, _lib.load().unocg_uno_apply_dev(op, batch, C.c_void_p(r_dev.data_ptr()),
+                                                C.c_void_p(s_dev.data_ptr()), _stream(stream)))
+
+
+def unocg_uno_backward_dev(op, batch: int, r_dev, gs_dev, gr_dev, gtheta_dev, stream=None):
+    _ucheck(op, _lib.load().unocg_uno_backward_dev(
+        op, batch, C.c_void_p(r_dev.data_ptr()), C.c_void_p(gs_dev.data_ptr()),
+        C.c_void_p(gr_dev.data_ptr()) if gr_dev is not None else None,
+        C.c_void_p(gtheta_dev.data_ptr()) if gtheta_dev is not None else None, _stream(stream)))

@@ -1,0 +1,1155 @@
+// C ABI of the UNO-CG solver (include/unocg.h): contexts, set-up, the device-resident CG loop
+// of Algorithm 1 / Algorithm 2 in a CUDA graph with conditional nodes, post-processing.
+//
+// One CG iteration of UNO-CG is four kernels (see k_fft.cu / k_stencil.cu):
+//   k_line      FFT axis 1, s_hat = Q r_hat / n, gamma = r.s (Parseval), inverse axis 1, beta
+//   k_plane_inv inverse FFT axes 2/3, u += alpha d_old, d = s + beta d_old
+//   k_ku        p = K d, d.p, alpha
+//   k_plane_fwd r -= alpha p, ||r||_inf, stopping test, forward FFT axes 3/2
+// Jacobi / unpreconditioned CG uses k_jac_b, k_ku, k_jac_a.  In mixed precision a conditional
+// IF node runs the FP64 residual replacement (fold u, r = f - K u) when the last residual check
+// requests it.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "kargs.h"
+#include "setup.h"
+#include "unocg.h"
+
+using namespace unocg;
+
+namespace {
+
+constexpr int kMaxTickets = 8;
+enum Ticket { T_PLANE = 0, T_LINE = 1, T_KU = 2, T_JAC = 3, T_PLANE2 = 4, T_JAC2 = 5 };
+
+bool factor_plan(int N, FftPlan* p) {
+  p->N = N;
+  p->nst = 0;
+  int m = N;
+  while (m % 4 == 0) { p->radix[p->nst++] = 4; m /= 4; }
+  while (m % 2 == 0) { p->radix[p->nst++] = 2; m /= 2; }
+  while (m % 3 == 0) { p->radix[p->nst++] = 3; m /= 3; }
+  while (m % 5 == 0) { p->radix[p->nst++] = 5; m /= 5; }
+  return m == 1 && p->nst <= 12;
+}
+
+template <typename T>
+std::vector<cplx<T>> twiddles(int N) {
+  std::vector<cplx<T>> w(N);
+  for (int m = 0; m < N; ++m) {
+    long double ang = -2.0L * 3.14159265358979323846264338327950288L * (long double)m / (long double)N;
+    w[m] = mk<T>((T)std::cos(ang), (T)std::sin(ang));
+  }
+  return w;
+}
+
+struct Fields64 {
+  double *r = nullptr, *d = nullptr, *p = nullptr, *u = nullptr;
+  double2 *rhat = nullptr, *shat = nullptr;
+};
+struct Fields32 {
+  float *r = nullptr, *d = nullptr, *p = nullptr, *u = nullptr;
+  float2 *rhat = nullptr, *shat = nullptr;
+  double* u64 = nullptr;
+};
+
+struct GraphKey {
+  int precond = -1, precision = -1, flexible = -1, replace_every = -1, max_iter = -1, L = -1;
+  double tol = -1.0;
+  bool operator==(const GraphKey& o) const {
+    return precond == o.precond && precision == o.precision && flexible == o.flexible &&
+           replace_every == o.replace_every && max_iter == o.max_iter && L == o.L && tol == o.tol;
+  }
+};
+
+}  // namespace
+
+struct unocg_ctx {
+  int physics = 1, c = 1, B = 1, dim = 3;
+  Grid g{};
+  double L0 = 1.0;
+  int n_phases = 0, L = 0;
+  bool have_phase = false, have_props = false, have_loads = false;
+  int wkind = -1;
+  bool q_dirty = true, bf16_spd_ok = true;
+  double spd_eps = 0.0;
+  std::vector<double> w_host;  // user weights (BLOCKS / THETA), FP64
+  cudaStream_t stream = nullptr, own_stream = nullptr;
+  std::string err;
+  // device data
+  uint8_t* phase = nullptr;
+  double* props_d = nullptr;  // raw properties
+  double* mat64 = nullptr;
+  float* mat32 = nullptr;
+  double* ref = nullptr;      // [B][2]
+  double* loads_d = nullptr;
+  double* Q64 = nullptr;
+  float* Q32 = nullptr;
+  __nv_bfloat16* Q16 = nullptr;
+  int Bq = 1;
+  void* tw64[4] = {nullptr, nullptr, nullptr, nullptr};
+  void* tw32[4] = {nullptr, nullptr, nullptr, nullptr};
+  FftPlan p1{}, p2{}, p3h{};
+  CgScal* sc = nullptr;
+  double* part = nullptr;
+  size_t part_n = 0;
+  unsigned int* tickets = nullptr;
+  int* flags = nullptr;  // [0] active, [1] replace
+  unsigned long long* fails = nullptr;
+  Fields64 f64;
+  Fields32 f32;
+  double* invdiag64 = nullptr;
+  float* invdiag32 = nullptr;
+  double* ceff = nullptr;   // [B][dim][L]
+  double* sens = nullptr;
+  double* stage = nullptr;  // [c*n] interleave staging
+  bool solved = false;
+  int last_precision = 0;
+  // graph cache
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  GraphKey key;
+  unocg_solve_opts last_opts{};
+};
+
+struct unocg_uno {
+  int c = 1;
+  Grid g{};
+  FftPlan p1{}, p2{}, p3h{};
+  void* tw32[4] = {nullptr, nullptr, nullptr, nullptr};
+  float* Q32 = nullptr;
+  float* Qtmp = nullptr;
+  const float* theta = nullptr;
+  float2 *hat = nullptr, *shat = nullptr, *ghat = nullptr;
+  size_t cap = 0;  // fields of capacity
+  float* gq = nullptr;
+  float* gq2 = nullptr;
+  std::string err;
+};
+
+// ------------------------------------------------------------------ helpers
+static int fail(unocg_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+#define CK(...)                                                                           \
+  do {                                                                                    \
+    cudaError_t e_ = (__VA_ARGS__);                                                       \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? UNOCG_ERR_OOM : UNOCG_ERR_CUDA,  \
+                  std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_));             \
+  } while (0)
+
+template <typename P>
+static cudaError_t dalloc(P** p, size_t count) {
+  if (*p) return cudaSuccess;
+  return cudaMalloc((void**)p, count * sizeof(P));
+}
+
+static FftTables tables(unocg_ctx* ctx, bool fp64) {
+  FftTables t;
+  t.p1 = ctx->p1;
+  t.p2 = ctx->p2;
+  t.p3h = ctx->p3h;
+  void* const* tw = fp64 ? ctx->tw64 : ctx->tw32;
+  t.tw1 = tw[0];
+  t.tw2 = tw[1];
+  t.tw3h = tw[2];
+  t.tw3 = tw[3];
+  return t;
+}
+
+static Material material(unocg_ctx* ctx) {
+  Material m;
+  m.n_phases = ctx->n_phases;
+  m.m64 = ctx->mat64;
+  m.m32 = ctx->mat32;
+  return m;
+}
+
+static bool grid_ok(int n1, int n2, int n3) {
+  FftPlan p;
+  if (n1 < 2 || n2 < 2 || n3 < 4 || (n3 % 2)) return false;
+  return factor_plan(n1, &p) && factor_plan(n2, &p) && factor_plan(n3 / 2, &p);
+}
+
+template <typename T>
+static cudaError_t upload_twiddles(void** dst, int n1, int n2, int n3) {
+  int Ns[4] = {n1, n2, n3 / 2, n3};
+  for (int i = 0; i < 4; ++i) {
+    auto w = twiddles<T>(Ns[i]);
+    cudaError_t e = cudaMalloc(&dst[i], w.size() * sizeof(cplx<T>));
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpy(dst[i], w.data(), w.size() * sizeof(cplx<T>), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// ------------------------------------------------------------------ create / destroy
+extern "C" int unocg_create(unocg_ctx** out, int physics, int batch, int n1, int n2, int n3, double L0) {
+  unocg_ctx* ctx = nullptr;
+  if (!out) return UNOCG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if ((physics != UNOCG_THERMAL && physics != UNOCG_ELASTIC) || batch < 1 || !(L0 > 0.0))
+    return UNOCG_ERR_INVALID_ARG;
+  if (!grid_ok(n1, n2, n3)) return UNOCG_ERR_INVALID_ARG;
+  if (!plane_fits(Grid{n1, n2, n3, n3 / 2 + 1, 0, 0, 0.0}, 8)) return UNOCG_ERR_INVALID_ARG;
+  ctx = new unocg_ctx();
+  ctx->physics = physics;
+  ctx->c = physics == UNOCG_THERMAL ? 1 : 3;
+  ctx->dim = physics == UNOCG_THERMAL ? 3 : 6;
+  ctx->B = batch;
+  ctx->L0 = L0;
+  ctx->g.n1 = n1;
+  ctx->g.n2 = n2;
+  ctx->g.n3 = n3;
+  ctx->g.n3h = n3 / 2 + 1;
+  ctx->g.n = (long long)n1 * n2 * n3;
+  ctx->g.nh = (long long)n1 * n2 * (n3 / 2 + 1);
+  ctx->g.h = L0 / n1;
+  factor_plan(n1, &ctx->p1);
+  factor_plan(n2, &ctx->p2);
+  factor_plan(n3 / 2, &ctx->p3h);
+  *out = ctx;
+  CK(cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking));
+  ctx->stream = ctx->own_stream;
+  CK(upload_twiddles<double>(ctx->tw64, n1, n2, n3));
+  CK(upload_twiddles<float>(ctx->tw32, n1, n2, n3));
+  CK(cudaMalloc(&ctx->phase, (size_t)batch * ctx->g.n));
+  CK(cudaMalloc(&ctx->tickets, kMaxTickets * sizeof(unsigned int)));
+  CK(cudaMemset(ctx->tickets, 0, kMaxTickets * sizeof(unsigned int)));
+  CK(cudaMalloc(&ctx->flags, 4 * sizeof(int)));
+  CK(cudaMalloc(&ctx->fails, sizeof(unsigned long long)));
+  CK(cudaMalloc(&ctx->ref, 2 * batch * sizeof(double)));
+  return UNOCG_OK;
+}
+
+static void free_graph(unocg_ctx* ctx) {
+  if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
+  if (ctx->graph) cudaGraphDestroy(ctx->graph);
+  ctx->exec = nullptr;
+  ctx->graph = nullptr;
+  ctx->key = GraphKey();
+}
+
+extern "C" void unocg_destroy(unocg_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  free_graph(ctx);
+  void* ptrs[] = {ctx->phase, ctx->props_d, ctx->mat64, ctx->mat32, ctx->ref, ctx->loads_d, ctx->Q64,
+                  ctx->Q32, ctx->Q16, ctx->sc, ctx->part, ctx->tickets, ctx->flags, ctx->fails,
+                  ctx->f64.r, ctx->f64.d, ctx->f64.p, ctx->f64.u, ctx->f64.rhat, ctx->f64.shat,
+                  ctx->f32.r, ctx->f32.d, ctx->f32.p, ctx->f32.u, ctx->f32.rhat, ctx->f32.shat,
+                  ctx->f32.u64, ctx->invdiag64, ctx->invdiag32, ctx->ceff, ctx->sens, ctx->stage,
+                  ctx->tw64[0], ctx->tw64[1], ctx->tw64[2], ctx->tw64[3],
+                  ctx->tw32[0], ctx->tw32[1], ctx->tw32[2], ctx->tw32[3]};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+  delete ctx;
+}
+
+extern "C" const char* unocg_last_error(const unocg_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+extern "C" int unocg_set_stream(unocg_ctx* ctx, void* stream) {
+  if (!ctx) return UNOCG_ERR_INVALID_ARG;
+  ctx->stream = stream ? (cudaStream_t)stream : ctx->own_stream;
+  return UNOCG_OK;
+}
+
+// ------------------------------------------------------------------ inputs
+static int check_phase_range(unocg_ctx* ctx, int n_phases) {
+  if (n_phases < 1 || n_phases > 255) return fail(ctx, UNOCG_ERR_INVALID_ARG, "n_phases must be in [1, 255]");
+  if (ctx->have_props && n_phases != ctx->n_phases) {
+    ctx->have_props = false;  // properties must be set again for the new phase count
+  }
+  ctx->n_phases = n_phases;
+  return UNOCG_OK;
+}
+
+extern "C" int unocg_set_microstructure(unocg_ctx* ctx, const uint8_t* phase, int n_phases) {
+  if (!ctx || !phase) return fail(ctx, UNOCG_ERR_INVALID_ARG, "null argument");
+  int rc = check_phase_range(ctx, n_phases);
+  if (rc) return rc;
+  size_t m = (size_t)ctx->B * ctx->g.n;
+  for (size_t i = 0; i < m; ++i)
+    if (phase[i] >= n_phases) return fail(ctx, UNOCG_ERR_INVALID_ARG, "phase label >= n_phases");
+  CK(cudaMemcpyAsync(ctx->phase, phase, m, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->have_phase = true;
+  return UNOCG_OK;
+}
+
+extern "C" int unocg_set_microstructure_dev(unocg_ctx* ctx, const uint8_t* phase_dev, int n_phases, void* stream) {
+  if (!ctx || !phase_dev) return fail(ctx, UNOCG_ERR_INVALID_ARG, "null argument");
+  int rc = check_phase_range(ctx, n_phases);
+  if (rc) return rc;
+  cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
+  CK(cudaMemcpyAsync(ctx->phase, phase_dev, (size_t)ctx->B * ctx->g.n, cudaMemcpyDeviceToDevice, s));
+  if (s != ctx->stream) {
+    cudaEvent_t ev;
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    CK(cudaEventRecord(ev, s));
+    CK(cudaStreamWaitEvent(ctx->stream, ev, 0));
+    cudaEventDestroy(ev);
+  }
+  ctx->have_phase = true;
+  return UNOCG_OK;
+}
+
+extern "C" int unocg_set_phase_properties(unocg_ctx* ctx, const double* props) {
+  if (!ctx || !props) return fail(ctx, UNOCG_ERR_INVALID_ARG, "null argument");
+  if (ctx->n_phases < 1) return fail(ctx, UNOCG_ERR_STATE, "set the microstructure (phase count) first");
+  const int np = ctx->physics == UNOCG_THERMAL ? 1 : 2;
+  const int count = ctx->B * ctx->n_phases;
+  for (int i = 0; i < count; ++i) {
+    if (ctx->physics == UNOCG_THERMAL) {
+      if (!(props[i] > 0.0) || !std::isfinite(props[i]))
+        return fail(ctx, UNOCG_ERR_INVALID_ARG, "conductivities must be positive");
+    } else {
+      double E = props[2 * i], nu = props[2 * i + 1];
+      if (!(E > 0.0) || !(nu > -1.0 && nu < 0.5))
+        return fail(ctx, UNOCG_ERR_INVALID_ARG, "need E > 0 and -1 < nu < 0.5");
+    }
+  }
+  CK(dalloc(&ctx->props_d, (size_t)count * np));
+  CK(dalloc(&ctx->mat64, (size_t)count * 2));
+  CK(dalloc(&ctx->mat32, (size_t)count * 2));
+  CK(cudaMemcpyAsync(ctx->props_d, props, (size_t)count * np * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  CK(launch_material(ctx->props_d, ctx->mat64, ctx->mat32, count, ctx->physics, ctx->stream));
+  CK(launch_ref_props(ctx->mat64, ctx->ref, ctx->B, ctx->n_phases, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->have_props = true;
+  if (ctx->wkind == UNOCG_W_REFERENCE_MEDIUM) ctx->q_dirty = true;
+  return UNOCG_OK;
+}
+
+extern "C" int unocg_set_macro_load(unocg_ctx* ctx, int n_loads, const double* loads) {
+  if (!ctx || !loads || n_loads < 1 || n_loads > 8)
+    return fail(ctx, UNOCG_ERR_INVALID_ARG, "need 1 <= n_loads <= 8 and a load array");
+  if (ctx->loads_d && n_loads != ctx->L) {
+    cudaFree(ctx->loads_d);
+    ctx->loads_d = nullptr;
+  }
+  if (n_loads != ctx->L) {
+    // per-(instance, load) buffers depend on L
+    free_graph(ctx);
+    Fields64& a = ctx->f64;
+    Fields32& b = ctx->f32;
+    void* ptrs[] = {a.r, a.d, a.p, a.u, a.rhat, a.shat, b.r, b.d, b.p, b.u, b.rhat, b.shat, b.u64,
+                    ctx->sc, ctx->ceff, ctx->sens, ctx->part};
+    cudaStreamSynchronize(ctx->stream);
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
+    ctx->f64 = Fields64();
+    ctx->f32 = Fields32();
+    ctx->sc = nullptr;
+    ctx->ceff = nullptr;
+    ctx->sens = nullptr;
+    ctx->part = nullptr;
+    ctx->solved = false;
+  }
+  ctx->L = n_loads;
+  CK(dalloc(&ctx->loads_d, (size_t)n_loads * ctx->dim));
+  CK(cudaMemcpy(ctx->loads_d, loads, (size_t)n_loads * ctx->dim * sizeof(double), cudaMemcpyHostToDevice));
+  ctx->have_loads = true;
+  return UNOCG_OK;
+}
+
+// ------------------------------------------------------------------ weights
+static int finish_weights(unocg_ctx* ctx) {
+  // FP64 entries are in Q64 ([Bq][nh][C]); check, then make the FP32 / BF16 copies.
+  const int NQ = ctx->c == 1 ? 1 : 6;
+  const long long m = (long long)ctx->Bq * ctx->g.nh * NQ;
+  CK(cudaMemsetAsync(ctx->fails, 0, sizeof(unsigned long long), ctx->stream));
+  CK(launch_spd_check64(ctx->Q64, ctx->g.nh, ctx->Bq, ctx->c, ctx->spd_eps, ctx->fails, ctx->stream));
+  unsigned long long nf = 0;
+  CK(cudaMemcpyAsync(&nf, ctx->fails, sizeof(nf), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (nf) return fail(ctx, UNOCG_ERR_NOT_SPD, "UNO weights fail the safety check on " + std::to_string(nf) + " modes");
+  CK(dalloc(&ctx->Q32, (size_t)m));
+  CK(dalloc(&ctx->Q16, (size_t)m));
+  CK(launch_convert32(ctx->Q64, ctx->Q32, m, ctx->stream));
+  CK(launch_convert16(ctx->Q64, ctx->Q16, m, ctx->stream));
+  CK(cudaMemsetAsync(ctx->fails, 0, sizeof(unsigned long long), ctx->stream));
+  CK(launch_spd_check16(ctx->Q16, ctx->g.nh, ctx->Bq, ctx->c, ctx->spd_eps, ctx->fails, ctx->stream));
+  CK(cudaMemcpyAsync(&nf, ctx->fails, sizeof(nf), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->bf16_spd_ok = (nf == 0);
+  ctx->q_dirty = false;
+  return UNOCG_OK;
+}
+
+static int build_weights(unocg_ctx* ctx) {
+  const int NQ = ctx->c == 1 ? 1 : 6;
+  if (ctx->wkind == UNOCG_W_REFERENCE_MEDIUM) {
+    if (!ctx->have_props) return fail(ctx, UNOCG_ERR_STATE, "reference-medium weights need phase properties");
+    if (ctx->Bq != ctx->B && ctx->Q64) {
+      cudaFree(ctx->Q64); cudaFree(ctx->Q32); cudaFree(ctx->Q16);
+      ctx->Q64 = nullptr; ctx->Q32 = nullptr; ctx->Q16 = nullptr;
+    }
+    ctx->Bq = ctx->B;
+    CK(dalloc(&ctx->Q64, (size_t)ctx->B * ctx->g.nh * NQ));
+    RefQArgs a{ctx->g, ctx->c, ctx->ref, ctx->Q64};
+    CK(launch_ref_q(a, ctx->B, ctx->stream));
+    return finish_weights(ctx);
+  }
+  // user weights: host FP64 copy -> device, psi (THETA), symmetrize the self-conjugate planes
+  if (ctx->Bq != 1 && ctx->Q64) {
+    cudaFree(ctx->Q64); cudaFree(ctx->Q32); cudaFree(ctx->Q16);
+    ctx->Q64 = nullptr; ctx->Q32 = nullptr; ctx->Q16 = nullptr;
+  }
+  ctx->Bq = 1;
+  const size_t m = (size_t)ctx->g.nh * NQ;
+  CK(dalloc(&ctx->Q64, m));
+  double* tmp = nullptr;
+  double* tmp2 = nullptr;
+  CK(cudaMalloc(&tmp, m * sizeof(double)));
+  cudaError_t e = cudaMalloc(&tmp2, m * sizeof(double));
+  if (e != cudaSuccess) { cudaFree(tmp); return fail(ctx, UNOCG_ERR_OOM, "weights buffer"); }
+  e = cudaMemcpyAsync(tmp, ctx->w_host.data(), m * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess && ctx->wkind == UNOCG_W_THETA) {
+    e = launch_psi64(tmp, tmp2, ctx->g.nh, ctx->c, ctx->stream);
+    std::swap(tmp, tmp2);
+  }
+  if (e == cudaSuccess) e = launch_symmetrize64(tmp, ctx->Q64, ctx->g, NQ, 1, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cudaFree(tmp);
+  cudaFree(tmp2);
+  if (e != cudaSuccess) return fail(ctx, UNOCG_ERR_CUDA, std::string("weights: ") + cudaGetErrorString(e));
+  return finish_weights(ctx);
+}
+
+extern "C" int unocg_set_uno_weights(unocg_ctx* ctx, int kind, const void* w, int dtype, double spd_eps) {
+  if (!ctx) return UNOCG_ERR_INVALID_ARG;
+  if (kind != UNOCG_W_REFERENCE_MEDIUM && kind != UNOCG_W_BLOCKS && kind != UNOCG_W_THETA)
+    return fail(ctx, UNOCG_ERR_INVALID_ARG, "unknown weight kind");
+  if (!(spd_eps >= 0.0)) return fail(ctx, UNOCG_ERR_INVALID_ARG, "spd_eps must be >= 0");
+  ctx->spd_eps = spd_eps;
+  ctx->wkind = kind;
+  ctx->q_dirty = true;
+  if (kind != UNOCG_W_REFERENCE_MEDIUM) {
+    if (!w || (dtype != UNOCG_DTYPE_F64 && dtype != UNOCG_DTYPE_F32))
+      return fail(ctx, UNOCG_ERR_INVALID_ARG, "weights need a host array of dtype F64 or F32");
+    const size_t m = (size_t)ctx->g.nh * (ctx->c == 1 ? 1 : 6);
+    ctx->w_host.resize(m);
+    for (size_t i = 0; i < m; ++i)
+      ctx->w_host[i] = dtype == UNOCG_DTYPE_F64 ? ((const double*)w)[i] : (double)((const float*)w)[i];
+    return build_weights(ctx);
+  }
+  if (ctx->have_props) return build_weights(ctx);
+  return UNOCG_OK;
+}
+
+// ------------------------------------------------------------------ workspaces
+static int ensure_workspace(unocg_ctx* ctx, int precision, int precond) {
+  const long long n = ctx->g.n;
+  const size_t BLc = (size_t)ctx->B * ctx->L * ctx->c;
+  const size_t fld = BLc * n;
+  const size_t hat = BLc * ctx->g.nh;
+  const int BL = ctx->B * ctx->L;
+  CK(dalloc(&ctx->sc, (size_t)BL));
+  // partial sums: the largest per-kernel demand
+  size_t need = 0;
+  need = std::max(need, (size_t)BL * line_blocks_x(ctx->g, ctx->c, 8) * 2);
+  need = std::max(need, (size_t)BL * line_blocks_x(ctx->g, ctx->c, 16) * 2);
+  need = std::max(need, (size_t)BL * node_blocks_x(ctx->g));
+  need = std::max(need, (size_t)BL * jac_blocks_x((long long)ctx->c * n, BL));
+  need = std::max(need, (size_t)BL * ctx->c * 1184);
+  need = std::max(need, (size_t)ctx->B * node_blocks_x(ctx->g) * 48);
+  if (need > ctx->part_n) {
+    if (ctx->part) cudaFree(ctx->part);
+    ctx->part = nullptr;
+    CK(cudaMalloc(&ctx->part, need * sizeof(double)));
+    ctx->part_n = need;
+  }
+  CK(dalloc(&ctx->ceff, (size_t)ctx->B * ctx->dim * ctx->L));
+  if (precision == UNOCG_FP64) {
+    Fields64& f = ctx->f64;
+    CK(dalloc(&f.r, fld)); CK(dalloc(&f.d, fld)); CK(dalloc(&f.p, fld)); CK(dalloc(&f.u, fld));
+    if (precond == UNOCG_PRECOND_UNO) { CK(dalloc(&f.rhat, hat)); CK(dalloc(&f.shat, hat)); }
+    if (precond == UNOCG_PRECOND_JACOBI) CK(dalloc(&ctx->invdiag64, (size_t)ctx->B * ctx->c * n));
+  } else {
+    Fields32& f = ctx->f32;
+    CK(dalloc(&f.r, fld)); CK(dalloc(&f.d, fld)); CK(dalloc(&f.p, fld)); CK(dalloc(&f.u, fld));
+    CK(dalloc(&f.u64, fld));
+    if (precond == UNOCG_PRECOND_UNO) { CK(dalloc(&f.rhat, hat)); CK(dalloc(&f.shat, hat)); }
+    if (precond == UNOCG_PRECOND_JACOBI) CK(dalloc(&ctx->invdiag32, (size_t)ctx->B * ctx->c * n));
+  }
+  return UNOCG_OK;
+}
+
+// ------------------------------------------------------------------ the iteration, as launches
+template <typename T> struct Sel;
+template <> struct Sel<double> {
+  using QT = double;
+  static Fields64& f(unocg_ctx* c) { return c->f64; }
+  static const double* Q(unocg_ctx* c) { return c->Q64; }
+  static double* invdiag(unocg_ctx* c) { return c->invdiag64; }
+  static double* u64(unocg_ctx* c) { return c->f64.u; }
+  static double* u32(unocg_ctx*) { return nullptr; }
+};
+template <> struct Sel<float> {
+  using QT = __nv_bfloat16;
+  static Fields32& f(unocg_ctx* c) { return c->f32; }
+  static const __nv_bfloat16* Q(unocg_ctx* c) { return c->Q16; }
+  static float* invdiag(unocg_ctx* c) { return c->invdiag32; }
+  static double* u64(unocg_ctx* c) { return c->f32.u64; }
+  static float* u32(unocg_ctx* c) { return c->f32.u; }
+};
+
+struct Plan {
+  unocg_solve_opts o;
+  int mixed;
+};
+
+template <typename T>
+static cudaError_t enq_plane_fwd(unocg_ctx* ctx, cudaStream_t s, const LoopCtl& ctl, int after_replace, int ticket) {
+  auto& f = Sel<T>::f(ctx);
+  PlaneFwdArgs<T> a{};
+  a.g = ctx->g; a.c = ctx->c; a.BL = ctx->B * ctx->L;
+  a.r = f.r; a.p = f.p; a.src = nullptr; a.hat = f.rhat; a.sc = ctx->sc;
+  a.ft = tables(ctx, sizeof(T) == 8);
+  a.ticket = ctx->tickets + ticket;
+  a.ctl = ctl; a.after_replace = after_replace; a.standalone = 0;
+  return launch_plane_fwd<T>(a, s);
+}
+
+template <typename T>
+static cudaError_t enq_jac_a(unocg_ctx* ctx, cudaStream_t s, const LoopCtl& ctl, int after_replace, int ticket, int precond) {
+  auto& f = Sel<T>::f(ctx);
+  JacArgs<T> a{};
+  a.c = ctx->c; a.BL = ctx->B * ctx->L; a.L = ctx->L; a.n = ctx->g.n;
+  a.r = f.r; a.p = f.p; a.d = f.d; a.u = f.u;
+  a.invdiag = precond == UNOCG_PRECOND_JACOBI ? Sel<T>::invdiag(ctx) : nullptr;
+  a.sc = ctx->sc; a.red = Reduce{ctx->part, ctx->tickets + ticket};
+  a.ctl = ctl; a.after_replace = after_replace;
+  return launch_jac<T>(a, 0, s);
+}
+
+template <typename T>
+static cudaError_t enq_residual_check(unocg_ctx* ctx, cudaStream_t s, const LoopCtl& ctl, int after_replace, int precond) {
+  if (precond == UNOCG_PRECOND_UNO)
+    return enq_plane_fwd<T>(ctx, s, ctl, after_replace, after_replace ? T_PLANE2 : T_PLANE);
+  return enq_jac_a<T>(ctx, s, ctl, after_replace, after_replace ? T_JAC2 : T_JAC, precond);
+}
+
+template <typename T>
+static cudaError_t enq_pre(unocg_ctx* ctx, cudaStream_t s, const Plan& pl, const LoopCtl& ctl) {
+  auto& f = Sel<T>::f(ctx);
+  const int BL = ctx->B * ctx->L;
+  cudaError_t e = cudaMemsetAsync(ctx->sc, 0, BL * sizeof(CgScal), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->tickets, 0, kMaxTickets * sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  InitArgs<T> ia{};
+  ia.g = ctx->g; ia.c = ctx->c; ia.L = ctx->L; ia.phase = ctx->phase; ia.mat = material(ctx);
+  ia.loads = ctx->loads_d; ia.r = f.r; ia.u = f.u; ia.d = f.d; ia.p = f.p;
+  ia.u64 = pl.mixed ? ctx->f32.u64 : nullptr;
+  e = launch_init<T>(ia, BL, s);
+  if (e != cudaSuccess) return e;
+  if (pl.o.precond == UNOCG_PRECOND_JACOBI) {
+    DiagArgs<T> da{ctx->g, ctx->c, ctx->phase, material(ctx), Sel<T>::invdiag(ctx)};
+    e = launch_invdiag<T>(da, ctx->B, s);
+    if (e != cudaSuccess) return e;
+  }
+  return enq_residual_check<T>(ctx, s, ctl, 0, pl.o.precond);
+}
+
+template <typename T>
+static cudaError_t enq_body(unocg_ctx* ctx, cudaStream_t s, const Plan& pl, const LoopCtl& ctl) {
+  auto& f = Sel<T>::f(ctx);
+  const int BL = ctx->B * ctx->L;
+  cudaError_t e;
+  if (pl.o.precond == UNOCG_PRECOND_UNO) {
+    using QT = typename Sel<T>::QT;
+    LineArgs<T, QT> la{};
+    la.g = ctx->g; la.c = ctx->c; la.BL = BL; la.L = ctx->L;
+    la.hat = f.rhat; la.shat = f.shat; la.ghat = nullptr;
+    la.Q = Sel<T>::Q(ctx);
+    la.q_inst_stride = ctx->Bq > 1 ? ctx->g.nh * (ctx->c == 1 ? 1 : 6) : 0;
+    la.scale = 1.0 / (double)ctx->g.n;
+    la.sc = ctx->sc; la.red = Reduce{ctx->part, ctx->tickets + T_LINE};
+    la.ft = tables(ctx, sizeof(T) == 8);
+    la.flexible = pl.o.flexible; la.standalone = 0; la.gq = nullptr;
+    e = launch_line<T, QT>(la, 0, s);
+    if (e != cudaSuccess) return e;
+    PlaneInvArgs<T> pa{};
+    pa.g = ctx->g; pa.c = ctx->c; pa.BL = BL; pa.shat = f.shat; pa.d = f.d; pa.u = f.u; pa.dst = nullptr;
+    pa.sc = ctx->sc; pa.ft = tables(ctx, sizeof(T) == 8); pa.standalone = 0;
+    e = launch_plane_inv<T>(pa, s);
+  } else {
+    JacArgs<T> a{};
+    a.c = ctx->c; a.BL = BL; a.L = ctx->L; a.n = ctx->g.n;
+    a.r = f.r; a.p = f.p; a.d = f.d; a.u = f.u;
+    a.invdiag = pl.o.precond == UNOCG_PRECOND_JACOBI ? Sel<T>::invdiag(ctx) : nullptr;
+    a.sc = ctx->sc; a.red = Reduce{ctx->part, ctx->tickets + T_JAC};
+    a.ctl = ctl;
+    e = launch_jac<T>(a, 1, s);
+  }
+  if (e != cudaSuccess) return e;
+  StencilArgs<T> ka{};
+  ka.g = ctx->g; ka.c = ctx->c; ka.BL = BL; ka.L = ctx->L; ka.phase = ctx->phase; ka.mat = material(ctx);
+  ka.d = f.d; ka.p = f.p; ka.sc = ctx->sc; ka.red = Reduce{ctx->part, ctx->tickets + T_KU}; ka.standalone = 0;
+  e = launch_ku<T>(ka, s);
+  if (e != cudaSuccess) return e;
+  return enq_residual_check<T>(ctx, s, ctl, 0, pl.o.precond);
+}
+
+// FP64 residual replacement for the pending (instance, load) pairs, then a fresh residual check
+template <typename T>
+static cudaError_t enq_replace(unocg_ctx* ctx, cudaStream_t s, const Plan& pl, const LoopCtl& ctl) {
+  auto& f = Sel<T>::f(ctx);
+  const int BL = ctx->B * ctx->L;
+  FoldArgs<T> fa{};
+  fa.c = ctx->c; fa.n = ctx->g.n; fa.u64 = Sel<T>::u64(ctx); fa.u32 = Sel<T>::u32(ctx); fa.d = f.d;
+  fa.sc = ctx->sc; fa.only_pending = 1; fa.part = nullptr;
+  cudaError_t e = launch_fold<T>(fa, BL, s);
+  if (e != cudaSuccess) return e;
+  TrueResArgs<T> ta{};
+  ta.g = ctx->g; ta.c = ctx->c; ta.L = ctx->L; ta.phase = ctx->phase; ta.mat = material(ctx);
+  ta.loads = ctx->loads_d; ta.u64 = Sel<T>::u64(ctx); ta.r = f.r; ta.sc = ctx->sc;
+  ta.only_pending = 1; ta.require_started = 0; ta.into_rmax = 1;
+  e = launch_true_res<T>(ta, BL, s);
+  if (e != cudaSuccess) return e;
+  return enq_residual_check<T>(ctx, s, ctl, 1, pl.o.precond);
+}
+
+template <typename T>
+static cudaError_t enq_post(unocg_ctx* ctx, cudaStream_t s, const Plan& pl) {
+  auto& f = Sel<T>::f(ctx);
+  const int BL = ctx->B * ctx->L;
+  const int nparts = 64;
+  FoldArgs<T> fa{};
+  fa.c = ctx->c; fa.n = ctx->g.n; fa.u64 = Sel<T>::u64(ctx); fa.u32 = Sel<T>::u32(ctx); fa.d = f.d;
+  fa.sc = ctx->sc; fa.only_pending = 0; fa.part = ctx->part;
+  cudaError_t e = launch_final<T>(fa, BL, nparts, s);
+  if (e != cudaSuccess) return e;
+  // true FP64 residual of the final iterate (reported), then zero mean, then averages
+  TrueResArgs<T> ta{};
+  ta.g = ctx->g; ta.c = ctx->c; ta.L = ctx->L; ta.phase = ctx->phase; ta.mat = material(ctx);
+  ta.loads = ctx->loads_d; ta.u64 = Sel<T>::u64(ctx); ta.r = nullptr; ta.sc = ctx->sc;
+  ta.only_pending = 0; ta.require_started = 0; ta.into_rmax = 0;
+  e = launch_true_res<T>(ta, BL, s);
+  if (e != cudaSuccess) return e;
+  e = launch_zero_mean(Sel<T>::u64(ctx), ctx->part, nparts, ctx->c, ctx->g.n, BL, s);
+  if (e != cudaSuccess) return e;
+  AvgArgs aa{};
+  aa.g = ctx->g; aa.c = ctx->c; aa.L = ctx->L; aa.phase = ctx->phase; aa.mat = material(ctx);
+  aa.loads = ctx->loads_d; aa.u64 = Sel<T>::u64(ctx); aa.part = ctx->part;
+  return launch_average(aa, ctx->B, ctx->ceff, s);
+}
+
+template <typename T>
+static int build_graph(unocg_ctx* ctx, const Plan& pl) {
+  cudaStream_t cs = nullptr, bs = nullptr, rs = nullptr;
+  CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithFlags(&rs, cudaStreamNonBlocking));
+  auto cleanup = [&]() {
+    cudaStreamDestroy(cs);
+    cudaStreamDestroy(bs);
+    cudaStreamDestroy(rs);
+  };
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+  cudaGraph_t cg = nullptr;
+  cudaStreamCaptureStatus st;
+  if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(cs, &st, nullptr, &cg, nullptr, nullptr, nullptr);
+  cudaGraphConditionalHandle hw = 0, hi = 0;
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hw, cg, 0, cudaGraphCondAssignDefault);
+  LoopCtl ctl{};
+  ctl.tol = pl.o.tol; ctl.max_iter = pl.o.max_iter; ctl.mixed = pl.mixed;
+  ctl.replace_every = pl.o.replace_every; ctl.flexible = pl.o.flexible;
+  ctl.h_while = hw; ctl.set_while = 1; ctl.set_if = 0;
+  if (e == cudaSuccess) e = enq_pre<T>(ctx, cs, pl, ctl);
+  cudaGraphNode_t wnode;
+  cudaGraphNodeParams wp{};
+  if (e == cudaSuccess) {
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    e = cudaStreamGetCaptureInfo(cs, &st, nullptr, &cg, &deps, nullptr, &nd);
+    if (e == cudaSuccess) {
+      wp.type = cudaGraphNodeTypeConditional;
+      wp.conditional.handle = hw;
+      wp.conditional.type = cudaGraphCondTypeWhile;
+      wp.conditional.size = 1;
+      e = cudaGraphAddNode(&wnode, cg, deps, nullptr, nd, &wp);
+    }
+    if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(cs, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+  }
+  if (e == cudaSuccess) {
+    cudaGraph_t body = wp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    LoopCtl bctl = ctl;
+    if (e == cudaSuccess && pl.mixed) {
+      e = cudaGraphConditionalHandleCreate(&hi, body, 0, cudaGraphCondAssignDefault);
+      bctl.h_if = hi;
+      bctl.set_if = 1;
+    }
+    if (e == cudaSuccess) e = enq_body<T>(ctx, bs, pl, bctl);
+    if (e == cudaSuccess && pl.mixed) {
+      const cudaGraphNode_t* deps = nullptr;
+      size_t nd = 0;
+      cudaGraph_t bg = nullptr;
+      e = cudaStreamGetCaptureInfo(bs, &st, nullptr, &bg, &deps, nullptr, &nd);
+      cudaGraphNode_t inode;
+      cudaGraphNodeParams ip{};
+      if (e == cudaSuccess) {
+        ip.type = cudaGraphNodeTypeConditional;
+        ip.conditional.handle = hi;
+        ip.conditional.type = cudaGraphCondTypeIf;
+        ip.conditional.size = 1;
+        e = cudaGraphAddNode(&inode, bg, deps, nullptr, nd, &ip);
+      }
+      if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(bs, &inode, nullptr, 1, cudaStreamSetCaptureDependencies);
+      if (e == cudaSuccess) {
+        e = cudaStreamBeginCaptureToGraph(rs, ip.conditional.phGraph_out[0], nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+        LoopCtl rctl = ctl;
+        rctl.set_while = 0;
+        rctl.set_if = 0;
+        if (e == cudaSuccess) e = enq_replace<T>(ctx, rs, pl, rctl);
+        cudaGraph_t tmp;
+        cudaError_t e2 = cudaStreamEndCapture(rs, &tmp);
+        if (e == cudaSuccess) e = e2;
+      }
+    }
+    cudaGraph_t tmp;
+    cudaError_t e2 = cudaStreamEndCapture(bs, &tmp);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = enq_post<T>(ctx, cs, pl);
+  cudaError_t e3 = cudaStreamEndCapture(cs, &g);
+  if (e == cudaSuccess) e = e3;
+  cleanup();
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return fail(ctx, UNOCG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  }
+  cudaGraphExec_t ex = nullptr;
+  e = cudaGraphInstantiate(&ex, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return fail(ctx, UNOCG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  }
+  free_graph(ctx);
+  ctx->graph = g;
+  ctx->exec = ex;
+  return UNOCG_OK;
+}
+
+// Host-driven loop (debugging): one residual check per iteration read back by the host.
+template <typename T>
+static int run_host_loop(unocg_ctx* ctx, const Plan& pl) {
+  cudaStream_t s = ctx->stream;
+  LoopCtl ctl{};
+  ctl.tol = pl.o.tol; ctl.max_iter = pl.o.max_iter; ctl.mixed = pl.mixed;
+  ctl.replace_every = pl.o.replace_every; ctl.flexible = pl.o.flexible;
+  ctl.active_flag = ctx->flags; ctl.replace_flag = ctx->flags + 1;
+  CK(enq_pre<T>(ctx, s, pl, ctl));
+  int hf[2] = {0, 0};
+  const long long cap = 4LL * pl.o.max_iter + 16;
+  for (long long it = 0; it < cap; ++it) {
+    CK(cudaMemcpyAsync(hf, ctx->flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (!hf[0]) break;
+    CK(enq_body<T>(ctx, s, pl, ctl));
+    if (pl.mixed) {
+      CK(cudaMemcpyAsync(hf, ctx->flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (hf[1]) {
+        LoopCtl rctl = ctl;
+        rctl.active_flag = nullptr;  // keep the loop running; the next check decides
+        CK(enq_replace<T>(ctx, s, pl, rctl));
+      }
+    }
+  }
+  CK(enq_post<T>(ctx, s, pl));
+  return UNOCG_OK;
+}
+
+static int prepare_solve(unocg_ctx* ctx, const unocg_solve_opts* o, Plan* pl) {
+  if (!ctx || !o) return fail(ctx, UNOCG_ERR_INVALID_ARG, "null argument");
+  if (!ctx->have_phase || !ctx->have_props || !ctx->have_loads)
+    return fail(ctx, UNOCG_ERR_STATE, "set microstructure, phase properties and loads first");
+  if (o->precond < 0 || o->precond > 2 || (o->precision != UNOCG_FP64 && o->precision != UNOCG_MIXED) ||
+      !(o->tol > 0.0) || o->max_iter < 1 || o->replace_every < 0)
+    return fail(ctx, UNOCG_ERR_INVALID_ARG, "invalid solve options");
+  if (o->precond == UNOCG_PRECOND_UNO) {
+    if (ctx->wkind < 0) return fail(ctx, UNOCG_ERR_STATE, "set UNO weights first");
+    if (ctx->q_dirty) {
+      int rc = build_weights(ctx);
+      if (rc) return rc;
+    }
+    if (o->precision == UNOCG_MIXED && !ctx->bf16_spd_ok)
+      return fail(ctx, UNOCG_ERR_NOT_SPD, "UNO weights fail the safety check after rounding to BF16");
+  }
+  pl->o = *o;
+  pl->mixed = o->precision == UNOCG_MIXED;
+  if (!pl->mixed) pl->o.replace_every = 0;
+  return ensure_workspace(ctx, o->precision, o->precond);
+}
+
+extern "C" int unocg_solve_async(unocg_ctx* ctx, const unocg_solve_opts* o) {
+  Plan pl;
+  int rc = prepare_solve(ctx, o, &pl);
+  if (rc) return rc;
+  ctx->last_opts = *o;
+  ctx->last_precision = o->precision;
+  ctx->solved = false;
+  if (!o->use_graph) {
+    rc = pl.mixed ? run_host_loop<float>(ctx, pl) : run_host_loop<double>(ctx, pl);
+    if (rc) return rc;
+  } else {
+    GraphKey k;
+    k.precond = o->precond; k.precision = o->precision; k.flexible = o->flexible;
+    k.replace_every = pl.o.replace_every; k.max_iter = o->max_iter; k.L = ctx->L; k.tol = o->tol;
+    if (!ctx->exec || !(k == ctx->key)) {
+      rc = pl.mixed ? build_graph<float>(ctx, pl) : build_graph<double>(ctx, pl);
+      if (rc) return rc;
+      ctx->key = k;
+    }
+    CK(cudaGraphLaunch(ctx->exec, ctx->stream));
+  }
+  ctx->solved = true;
+  return UNOCG_OK;
+}
+
+extern "C" int unocg_solve_wait(unocg_ctx* ctx, unocg_solve_info* info) {
+  if (!ctx) return UNOCG_ERR_INVALID_ARG;
+  if (!ctx->solved) return fail(ctx, UNOCG_ERR_STATE, "no solve in flight");
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaGetLastError());
+  const int BL = ctx->B * ctx->L;
+  std::vector<CgScal> hs(BL);
+  CK(cudaMemcpy(hs.data(), ctx->sc, BL * sizeof(CgScal), cudaMemcpyDeviceToHost));
+  int status = UNOCG_OK, mx = 0;
+  for (int i = 0; i < BL; ++i) {
+    const CgScal& s = hs[i];
+    int st = s.done ? s.status : UNOCG_ERR_NOT_CONVERGED;
+    if (status == UNOCG_OK && st != UNOCG_OK) status = st;
+    mx = std::max(mx, s.iters);
+    if (info) {
+      double f0 = s.r0max;
+      if (info->iters) info->iters[i] = s.iters;
+      if (info->rel_res) info->rel_res[i] = f0 > 0 ? s.rmax / f0 : 0.0;
+      if (info->true_rel_res) {
+        double tm;
+        std::memcpy(&tm, &s.tmax_bits, sizeof(tm));
+        info->true_rel_res[i] = f0 > 0 ? tm / f0 : 0.0;
+      }
+      if (info->load_status) info->load_status[i] = st;
+    }
+  }
+  if (info) {
+    info->status = status;
+    info->max_iters = mx;
+  }
+  if (status != UNOCG_OK) {
+    ctx->err = status == UNOCG_ERR_NOT_CONVERGED ? "not converged within max_iter" : "CG breakdown";
+  }
+  return status;
+}
+
+extern "C" int unocg_solve(unocg_ctx* ctx, const unocg_solve_opts* o, unocg_solve_info* info) {
+  int rc = unocg_solve_async(ctx, o);
+  if (rc) return rc;
+  return unocg_solve_wait(ctx, info);
+}
+
+// ------------------------------------------------------------------ outputs
+static const double* final_u(unocg_ctx* ctx) {
+  return ctx->last_precision == UNOCG_FP64 ? ctx->f64.u : ctx->f32.u64;
+}
+
+extern "C" int unocg_get_fluctuation(unocg_ctx* ctx, int instance, int load, double* out) {
+  if (!ctx || !out) return fail(ctx, UNOCG_ERR_INVALID_ARG, "null argument");
+  if (!ctx->solved) return fail(ctx, UNOCG_ERR_STATE, "no solution");
+  if (instance < 0 || instance >= ctx->B || load < 0 || load >= ctx->L)
+    return fail(ctx, UNOCG_ERR_INVALID_ARG, "instance/load out of range");
+  const long long n = ctx->g.n;
+  CK(dalloc(&ctx->stage, (size_t)ctx->c * n));
+  const double* src = final_u(ctx) + ((long long)instance * ctx->L + load) * ctx->c * n;
+  CK(launch_interleave(src, ctx->stage, ctx->c, n, ctx->stream));
+  CK(cudaMemcpyAsync(out, ctx->stage, (size_t)ctx->c * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return UNOCG_OK;
+}
+
+extern "C" int unocg_get_fluctuation_dev(unocg_ctx* ctx, int instance, int load, double* out_dev, void* stream) {
+  if (!ctx || !out_dev) return fail(ctx, UNOCG_ERR_INVALID_ARG, "null argument");
+  if (!ctx->solved) return fail(ctx, UNOCG_ERR_STATE, "no solution");
+  if (instance < 0 || instance >= ctx->B || load < 0 || load >= ctx->L)
+    return fail(ctx, UNOCG_ERR_INVALID_ARG, "instance/load out of range");
+  const long long n = ctx->g.n;
+  const double* src = final_u(ctx) + ((long long)instance * ctx->L + load) * ctx->c * n;
+  CK(cudaMemcpyAsync(out_dev, src, (size_t)ctx->c * n * sizeof(double), cudaMemcpyDeviceToDevice,
+                     stream ? (cudaStream_t)stream : ctx->stream));
+  return UNOCG_OK;
+}
+
+extern "C" int unocg_get_effective_tensor(unocg_ctx* ctx, double* out) {
+  if (!ctx || !out) return fail(ctx, UNOCG_ERR_INVALID_ARG, "null argument");
+  if (!ctx->solved) return fail(ctx, UNOCG_ERR_STATE, "no solution");
+  CK(cudaMemcpyAsync(out, ctx->ceff, (size_t)ctx->B * ctx->dim * ctx->L * sizeof(double),
+                     cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return UNOCG_OK;
+}
+
+extern "C" int unocg_get_sensitivity(unocg_ctx* ctx, double* out) {
+  if (!ctx || !out) return fail(ctx, UNOCG_ERR_INVALID_ARG, "null argument");
+  if (!ctx->solved) return fail(ctx, UNOCG_ERR_STATE, "no solution");
+  const int L = ctx->L, np = ctx->n_phases, nq = ctx->c == 1 ? 1 : 2;
+  const int tot = np * nq * L * L;
+  if (tot > 6000) return fail(ctx, UNOCG_ERR_INVALID_ARG, "too many phases x loads for the sensitivity kernel");
+  CK(dalloc(&ctx->sens, (size_t)ctx->B * tot));
+  double* spart = nullptr;
+  CK(cudaMallocAsync(&spart, (size_t)ctx->B * sens_blocks_x(ctx->g) * tot * sizeof(double), ctx->stream));
+  AvgArgs aa{};
+  aa.g = ctx->g; aa.c = ctx->c; aa.L = L; aa.phase = ctx->phase; aa.mat = material(ctx);
+  aa.loads = ctx->loads_d; aa.u64 = final_u(ctx); aa.part = spart;
+  cudaError_t se = launch_sens(aa, ctx->B, ctx->sens, ctx->stream);
+  cudaFreeAsync(spart, ctx->stream);
+  CK(se);
+  std::vector<double> raw((size_t)ctx->B * tot);
+  CK(cudaMemcpyAsync(raw.data(), ctx->sens, raw.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (ctx->c == 1) {
+    std::memcpy(out, raw.data(), raw.size() * sizeof(double));
+    return UNOCG_OK;
+  }
+  // elastic: chain (dW/dlambda, dW/dmu) to (dW/dE, dW/dnu) per phase
+  std::vector<double> props((size_t)ctx->B * np * 2);
+  CK(cudaMemcpy(props.data(), ctx->props_d, props.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  for (int b = 0; b < ctx->B; ++b)
+    for (int p = 0; p < np; ++p) {
+      double E = props[(b * np + p) * 2], nu = props[(b * np + p) * 2 + 1];
+      double dlE = nu / ((1.0 + nu) * (1.0 - 2.0 * nu)), dmE = 1.0 / (2.0 * (1.0 + nu));
+      double dln = E * (1.0 + 2.0 * nu * nu) / ((1.0 + nu) * (1.0 + nu) * (1.0 - 2.0 * nu) * (1.0 - 2.0 * nu));
+      double dmn = -E / (2.0 * (1.0 + nu) * (1.0 + nu));
+      const double* wl = raw.data() + (size_t)b * tot + (size_t)p * 2 * L * L;
+      const double* wm = wl + L * L;
+      double* oE = out + ((size_t)b * 2 * np + 2 * p) * L * L;
+      double* on = oE + L * L;
+      for (int q = 0; q < L * L; ++q) {
+        oE[q] = wl[q] * dlE + wm[q] * dmE;
+        on[q] = wl[q] * dln + wm[q] * dmn;
+      }
+    }
+  return UNOCG_OK;
+}
+
+extern "C" int unocg_batch_solve(int n_ctx, unocg_ctx* const* ctxs, const unocg_solve_opts* opts,
+                                 unocg_solve_info* infos) {
+  if (n_ctx < 1 || !ctxs || !opts) return UNOCG_ERR_INVALID_ARG;
+  // each context's loop is one graph launch on its own stream; they run concurrently
+  for (int i = 0; i < n_ctx; ++i) {
+    int rc = unocg_solve_async(ctxs[i], opts);
+    if (rc) return rc;
+  }
+  int status = UNOCG_OK;
+  for (int i = 0; i < n_ctx; ++i) {
+    int rc = unocg_solve_wait(ctxs[i], infos ? infos + i : nullptr);
+    if (status == UNOCG_OK && rc != UNOCG_OK) status = rc;
+  }
+  return status;
+}
+
+// ------------------------------------------------------------------ operator-level entry points
+extern "C" int unocg_apply_K_dev(unocg_ctx* ctx, int instance, const double* d_dev, double* p_dev, void* stream) {
+  if (!ctx || !d_dev || !p_dev) return fail(ctx, UNOCG_ERR_INVALID_ARG, "null argument");
+  if (!ctx->have_phase || !ctx->have_props) return fail(ctx, UNOCG_ERR_STATE, "microstructure/properties missing");
+  if (instance < 0 || instance >= ctx->B) return fail(ctx, UNOCG_ERR_INVALID_ARG, "instance out of range");
+  StencilArgs<double> a{};
+  a.g = ctx->g; a.c = ctx->c; a.BL = 1; a.L = 1;
+  a.phase = ctx->phase + (long long)instance * ctx->g.n;
+  a.mat = material(ctx);
+  a.mat.m64 += (long long)instance * ctx->n_phases * 2;
+  a.mat.m32 += (long long)instance * ctx->n_phases * 2;
+  a.d = d_dev; a.p = p_dev; a.sc = nullptr; a.standalone = 1;
+  CK(launch_ku<double>(a, stream ? (cudaStream_t)stream : ctx->stream));
+  return UNOCG_OK;
+}
+
+extern "C" int unocg_apply_uno_dev(unocg_ctx* ctx, int instance, const double* r_dev, double* s_dev, void* stream) {
+  if (!ctx || !r_dev || !s_dev) return fail(ctx, UNOCG_ERR_INVALID_ARG, "null argument");
+  if (instance < 0 || instance >= ctx->B) return fail(ctx, UNOCG_ERR_INVALID_ARG, "instance out of range");
+  if (ctx->wkind < 0) return fail(ctx, UNOCG_ERR_STATE, "set UNO weights first");
+  if (ctx->q_dirty) {
+    int rc = build_weights(ctx);
+    if (rc) return rc;
+  }
+  cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
+  double2* hat = nullptr;
+  double2* shat = nullptr;
+  const size_t m = (size_t)ctx->c * ctx->g.nh;
+  CK(cudaMallocAsync(&hat, m * sizeof(double2), s));
+  CK(cudaMallocAsync(&shat, m * sizeof(double2), s));
+  PlaneFwdArgs<double> pf{};
+  pf.g = ctx->g; pf.c = ctx->c; pf.BL = 1; pf.src = r_dev; pf.hat = hat; pf.ft = tables(ctx, true); pf.standalone = 1;
+  cudaError_t e = launch_plane_fwd<double>(pf, s);
+  if (e == cudaSuccess) {
+    LineArgs<double, double> la{};
+    la.g = ctx->g; la.c = ctx->c; la.BL = 1; la.L = 1; la.hat = hat; la.shat = shat;
+    la.Q = ctx->Q64 + (ctx->Bq > 1 ? (long long)instance * ctx->g.nh * (ctx->c == 1 ? 1 : 6) : 0);
+    la.q_inst_stride = 0; la.scale = 1.0 / (double)ctx->g.n; la.ft = tables(ctx, true); la.standalone = 1;
+    e = launch_line<double, double>(la, 0, s);
+  }
+  if (e == cudaSuccess) {
+    PlaneInvArgs<double> pi{};
+    pi.g = ctx->g; pi.c = ctx->c; pi.BL = 1; pi.shat = shat; pi.dst = s_dev; pi.ft = tables(ctx, true); pi.standalone = 1;
+    e = launch_plane_inv<double>(pi, s);
+  }
+  cudaFreeAsync(hat, s);
+  cudaFreeAsync(shat, s);
+  if (e != cudaSuccess) return fail(ctx, UNOCG_ERR_CUDA, cudaGetErrorString(e));
+  return UNOCG_OK;
+}
+
+extern "C" int unocg_rhs_dev(unocg_ctx* ctx, int instance, int load, double* f_dev, void* stream) {
+  if (!ctx || !f_dev) return fail(ctx, UNOCG_ERR_INVALID_ARG, "null argument");
+  if (!ctx->have_phase || !ctx->have_props || !ctx->have_loads) return fail(ctx, UNOCG_ERR_STATE, "inputs missing");
+  if (instance < 0 || instance >= ctx->B || load < 0 || load >= ctx->L)
+    return fail(ctx, UNOCG_ERR_INVALID_ARG, "instance/load out of range");
+  InitArgs<double> ia{};
+  ia.g = ctx->g; ia.c = ctx->c; ia.L = 1;
+  ia.phase = ctx->phase + (long long)instance * ctx->g.n;
+  ia.mat = material(ctx);
+  ia.mat.m64 += (long long)instance * ctx->n_phases * 2;
+  ia.mat.m32 += (long long)instance * ctx->n_phases * 2;
+  ia.loads = ctx->loads_d + (long long)load * ctx->dim;
+  ia.f64 = f_dev;
+  CK(launch_init<double>(ia, 1, stream ? (cudaStream_t)stream : ctx->stream));
+  return UNOCG_OK;
+}
+
+// ------------------------------------------------------------------ standalone UNO operator
+static int ufail(unocg_uno* op, int code, const std::string& m) {
+  if (op) op->err = m;
+  return code;
+}
+#define UCK(...)                                                                                  \
+  do {                                                                                            \
+    cudaError_t e_ = (__VA_ARGS__);                                                               \
+    if (e_ != cudaSuccess) return ufail(op, e_ == cudaErrorMemoryAllocation ? UNOCG_ERR_OOM : UNOCG_ERR_CUDA, \
+                                        std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+extern "C" int unocg_uno_create(unocg_uno** out, int c, int n1, int n2, int n3) {
+  if (!out || (c != 1 && c != 3) || !grid_ok(n1, n2, n3)) return UNOCG_ERR_INVALID_ARG;
+  Grid g{n1, n2, n3, n3 / 2 + 1, (long long)n1 * n2 * n3, (long long)n1 * n2 * (n3 / 2 + 1), 1.0 / n1};
+  if (!plane_fits(g, 8)) return UNOCG_ERR_INVALID_ARG;
+  unocg_uno* op = new unocg_uno();
+  *out = op;
+  op->c = c;
+  op->g = g;
+  factor_plan(n1, &op->p1);
+  factor_plan(n2, &op->p2);
+  factor_plan(n3 / 2, &op->p3h);
+  UCK(upload_twiddles<float>(op->tw32, n1, n2, n3));
+  const size_t m = (size_t)g.nh * (c == 1 ? 1 : 6);
+  UCK(cudaMalloc(&op->Q32, m * sizeof(float)));
+  UCK(cudaMalloc(&op->Qtmp, m * sizeof(float)));
+  UCK(cudaMalloc(&op->gq, m * sizeof(float)));
+  UCK(cudaMalloc(&op->gq2, m * sizeof(float)));
+  return UNOCG_OK;
+}
+
+extern "C" void unocg_uno_destroy(unocg_uno* op) {
+  if (!op) return;
+  cudaDeviceSynchronize();
+  void* ptrs[] = {op->Q32, op->Qtmp, op->hat, op->shat, op->ghat, op->gq, op->gq2,
+                  op->tw32[0], op->tw32[1], op->tw32[2], op->tw32[3]};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete op;
+}
+
+extern "C" const char* unocg_uno_last_error(const unocg_uno* op) { return op ? op->err.c_str() : "null operator"; }
+
+static FftTables uno_tables(unocg_uno* op) {
+  FftTables t;
+  t.p1 = op->p1; t.p2 = op->p2; t.p3h = op->p3h;
+  t.tw1 = op->tw32[0]; t.tw2 = op->tw32[1]; t.tw3h = op->tw32[2]; t.tw3 = op->tw32[3];
+  return t;
+}
+
+extern "C" int unocg_uno_set_theta_dev(unocg_uno* op, const float* theta_dev, void* stream) {
+  if (!op || !theta_dev) return UNOCG_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  op->theta = theta_dev;
+  UCK(launch_psi32(theta_dev, op->Qtmp, op->g.nh, op->c, s));
+  UCK(launch_symmetrize32(op->Qtmp, op->Q32, op->g, op->c == 1 ? 1 : 6, 1, s));
+  return UNOCG_OK;
+}
+
+static int uno_ensure(unocg_uno* op, int batch) {
+  size_t need = (size_t)batch * op->c * op->g.nh;
+  if (need <= op->cap) return UNOCG_OK;
+  if (op->hat) { cudaFree(op->hat); cudaFree(op->shat); cudaFree(op->ghat); }
+  op->hat = op->shat = op->ghat = nullptr;
+  UCK(cudaMalloc(&op->hat, need * sizeof(float2)));
+  UCK(cudaMalloc(&op->shat, need * sizeof(float2)));
+  UCK(cudaMalloc(&op->ghat, need * sizeof(float2)));
+  op->cap = need;
+  return UNOCG_OK;
+}
+
+extern "C" int unocg_uno_apply_dev(unocg_uno* op, int batch, const float* r_dev, float* s_dev, void* stream) {
+  if (!op || batch < 1 || !r_dev || !s_dev) return UNOCG_ERR_INVALID_ARG;
+  if (!op->theta) return ufail(op, UNOCG_ERR_STATE, "set theta first");
+  int rc = uno_ensure(op, batch);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  PlaneFwdArgs<float> pf{};
+  pf.g = op->g; pf.c = op->c; pf.BL = batch; pf.src = r_dev; pf.hat = op->hat; pf.ft = uno_tables(op); pf.standalone = 1;
+  UCK(launch_plane_fwd<float>(pf, s));
+  LineArgs<float, float> la{};
+  la.g = op->g; la.c = op->c; la.BL = batch; la.L = 1; la.hat = op->hat; la.shat = op->shat;
+  la.Q = op->Q32; la.q_inst_stride = 0; la.scale = 1.0 / (double)op->g.n; la.ft = uno_tables(op); la.standalone = 1;
+  UCK(launch_line<float, float>(la, 0, s));
+  PlaneInvArgs<float> pi{};
+  pi.g = op->g; pi.c = op->c; pi.BL = batch; pi.shat = op->shat; pi.dst = s_dev; pi.ft = uno_tables(op); pi.standalone = 1;
+  UCK(launch_plane_inv<float>(pi, s));
+  return UNOCG_OK;
+}
+
+extern "C" int unocg_uno_backward_dev(unocg_uno* op, int batch, const float* r_dev, const float* gs_dev,
+                                      float* gr_dev, float* gtheta_dev, void* stream) {
+  if (!op || batch < 1 || !r_dev || !gs_dev) return UNOCG_ERR_INVALID_ARG;
+  if (!op->theta) return ufail(op, UNOCG_ERR_STATE, "set theta first");
+  int rc = uno_ensure(op, batch);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int NQ = op->c == 1 ? 1 : 6;
+  PlaneFwdArgs<float> pf{};
+  pf.g = op->g; pf.c = op->c; pf.BL = batch; pf.src = r_dev; pf.hat = op->hat; pf.ft = uno_tables(op); pf.standalone = 1;
+  UCK(launch_plane_fwd<float>(pf, s));
+  pf.src = gs_dev;
+  pf.hat = op->ghat;
+  UCK(launch_plane_fwd<float>(pf, s));
+  UCK(cudaMemsetAsync(op->gq, 0, (size_t)op->g.nh * NQ * sizeof(float), s));
+  LineArgs<float, float> la{};
+  la.g = op->g; la.c = op->c; la.BL = batch; la.L = 1; la.hat = op->hat; la.shat = op->shat; la.ghat = op->ghat;
+  la.Q = op->Q32; la.q_inst_stride = 0; la.scale = 1.0 / (double)op->g.n; la.ft = uno_tables(op);
+  la.standalone = 1; la.gq = op->gq;
+  UCK(launch_line<float, float>(la, 1, s));
+  if (gr_dev) {
+    PlaneInvArgs<float> pi{};
+    pi.g = op->g; pi.c = op->c; pi.BL = batch; pi.shat = op->shat; pi.dst = gr_dev; pi.ft = uno_tables(op); pi.standalone = 1;
+    UCK(launch_plane_inv<float>(pi, s));
+  }
+  if (gtheta_dev) {
+    // Q_sym = S psi(theta) with S the (self-adjoint) plane averaging: dL/dpsi = S dL/dQ_sym
+    UCK(launch_symmetrize32(op->gq, op->gq2, op->g, NQ, 1, s));
+    UCK(launch_psi_grad(op->theta, op->gq2, gtheta_dev, op->g.nh, op->c, s));
+  }
+  return UNOCG_OK;
+}

@@ -1,0 +1,153 @@
+// Shared device-side definitions of the UNO-CG kernels: complex helpers, per-solve CG
+// scalars, problem descriptors and the last-block reduction pattern.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace unocg {
+
+// ---------------------------------------------------------------- complex numbers
+template <typename T> struct CplxOf;
+template <> struct CplxOf<float> { using type = float2; };
+template <> struct CplxOf<double> { using type = double2; };
+template <typename T> using cplx = typename CplxOf<T>::type;
+
+template <typename T> __host__ __device__ __forceinline__ cplx<T> mk(T x, T y) {
+  cplx<T> r; r.x = x; r.y = y; return r;
+}
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { a.x -= b.x; a.y -= b.y; return a; }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  C r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+template <typename C> __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
+// multiply by -i (forward) / +i (inverse)
+template <int DIR, typename C> __device__ __forceinline__ C cmul_mi(C a) {
+  C r;
+  if (DIR < 0) { r.x = a.y; r.y = -a.x; } else { r.x = -a.y; r.y = a.x; }
+  return r;
+}
+
+// ---------------------------------------------------------------- CG state per (instance, load)
+struct CgScal {
+  double gamma;       // r . s of the current iteration
+  double gamma_prev;  // r . s of the previous iteration
+  double alpha;       // step width pending for the next residual / solution update
+  double beta;        // search-direction coefficient
+  double rs_old;      // r_{m+1} . s_m (flexible variant)
+  double r0max;       // ||r_0||_inf
+  double rmax;        // ||r||_inf of the latest residual
+  double true_res;    // ||f - K u||_inf / ||f||_inf (FP64) at the latest check
+  unsigned long long rmax_bits;  // running max of |r| as ordered bits (non-negative doubles)
+  unsigned long long tmax_bits;  // running max of |f - K u| (true residual kernel)
+  int iters;
+  int done;
+  int status;         // 0 ok, UNOCG_ERR_* when done
+  int need_replace;   // residual replacement requested (mixed precision)
+  int started;        // r0max recorded
+  int pad[3];
+};
+
+// ---------------------------------------------------------------- problem descriptor
+struct Grid {
+  int n1, n2, n3, n3h;      // n3h = n3/2 + 1
+  long long n;              // nodes per field
+  long long nh;             // half-grid modes per field
+  double h;                 // voxel edge
+};
+
+// Radix plan of one transform length.
+struct FftPlan {
+  int N;
+  int nst;
+  int radix[12];
+};
+
+struct FftTables {
+  FftPlan p1, p2, p3h;          // axis 1 (N1), axis 2 (N2), half axis 3 (N3/2)
+  const void* tw1;              // W_{N1}^m, m < N1    (cplx<T>)
+  const void* tw2;              // W_{N2}^m
+  const void* tw3h;             // W_{N3/2}^m
+  const void* tw3;              // W_{N3}^m, m < N3 (real-to-complex post-processing)
+};
+
+// Per-instance phase table: m64/m32[(b * n_phases + p) * 2 + {0,1}] = (kappa, 0) or (lambda, mu).
+struct Material {
+  int n_phases;
+  const double* m64;
+  const float* m32;
+};
+
+template <typename T> __device__ __forceinline__ const T* mat_ptr(const Material& m);
+template <> __device__ __forceinline__ const double* mat_ptr<double>(const Material& m) { return m.m64; }
+template <> __device__ __forceinline__ const float* mat_ptr<float>(const Material& m) { return m.m32; }
+
+// Copy the table of instance b to shared memory (n_phases <= 256).
+template <typename T> __device__ __forceinline__ void load_material(T* mt, const Material& m, int b) {
+  const T* src = mat_ptr<T>(m) + (long long)b * m.n_phases * 2;
+  for (int i = threadIdx.x; i < 2 * m.n_phases; i += blockDim.x) mt[i] = src[i];
+}
+
+// Counters and partial sums of one kernel "site" (reductions finished by the last block).
+struct Reduce {
+  double* part;                 // [BL][gridDim.x][nv]
+  unsigned int* ticket;         // one counter, reset by the last block
+};
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, double v) {
+  atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+__device__ __forceinline__ double bits_to_double(unsigned long long b) {
+  return __longlong_as_double((long long)b);
+}
+
+// Block-wide sum of one double; result valid in thread 0.  Uses `sh` (>= 32 doubles).
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  }
+  return s;
+}
+__device__ __forceinline__ double block_max(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+  }
+  return s;
+}
+
+// Returns true in every thread of the block that arrives last at `ticket` (over all blocks
+// of the grid).  Callers write their partials before and read all partials after.
+__device__ __forceinline__ bool last_block(unsigned int* ticket) {
+  __shared__ bool am_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned total = gridDim.x * gridDim.y * gridDim.z;
+    unsigned t = atomicAdd(ticket, 1u);
+    am_last = (t == total - 1);
+  }
+  __syncthreads();
+  if (am_last) __threadfence();
+  return am_last;
+}
+
+__device__ __forceinline__ double ld_cg(const double* p) { return __ldcg(p); }
+
+}  // namespace unocg

@@ -1,0 +1,462 @@
+// Matrix-free operator and pointwise kernels of the UNO-CG hot path.
+//
+//  * K d on the periodic voxel grid (Sec. 4.1, "matrix-free implementations" of Sec. 5.5),
+//    gathered per node from the 8 elements around it (27-point node stencil).  Thermal:
+//      p_a = (h/12) [ 4 (sum_e kappa_e) d_a - sum_{12 edge-diagonal b} (kappa_e1 + kappa_e2) d_b
+//                     - sum_{8 corner b} kappa_e d_b ]
+//    (face neighbours do not couple for trilinear bricks).  Elastic: the 3x3 blocks of
+//    h (lambda_e Klam + mu_e Kmu) from element.cuh.
+//  * right-hand side f = -sum_e A_e^T int_e B^T C_e eps_bar (Sec. 6), r_0 = f for u_0 = 0
+//  * Jacobi preconditioner (Sec. 4.2) and the pointwise CG updates of Algorithm 1
+//  * true residual f - K u in FP64, post-processing (averaged flux/stress, sensitivities)
+#include "kargs.h"
+#include "element.cuh"
+#include "stencil.cuh"
+
+namespace unocg {
+
+// ============================================================================ K d
+template <typename T, int CC>
+__global__ void __launch_bounds__(256) k_ku(StencilArgs<T> a) {
+  __shared__ T mt[2 * 256];
+  __shared__ double red_sh[32];
+  const Grid& g = a.g;
+  const int bl = blockIdx.y;
+  const int b = bl / a.L;
+  load_material<T>(mt, a.mat, b);
+  __syncthreads();
+  bool active = a.standalone || !a.sc[bl].done;
+  double dp = 0.0;
+  int i1, i2, i3;
+  if (active && tile_node(g, i1, i2, i3)) {
+    const long long n = g.n;
+    const uint8_t* ph = a.phase + (long long)b * n;
+    const T* d = a.d + (long long)bl * CC * n;
+    T* p = a.p + (long long)bl * CC * n;
+    const long long node = ((long long)i1 * g.n2 + i2) * g.n3 + i3;
+    T out[CC];
+    node_Ku<T, CC>(d, ph, mt, g, i1, i2, i3, out);
+#pragma unroll
+    for (int i = 0; i < CC; ++i) {
+      p[i * n + node] = out[i];
+      dp += (double)out[i] * (double)d[i * n + node];
+    }
+  }
+  if (a.standalone) return;
+  double bs = block_sum(dp, red_sh);
+  if (threadIdx.x == 0) a.red.part[(long long)bl * gridDim.x + blockIdx.x] = bs;
+  if (last_block(a.red.ticket)) {
+    for (int q = threadIdx.x; q < a.BL; q += blockDim.x) {
+      CgScal& s = a.sc[q];
+      if (s.done) continue;
+      double sum = 0.0;
+      const double* pp = a.red.part + (long long)q * gridDim.x;
+      for (int x = 0; x < (int)gridDim.x; ++x) sum += ld_cg(pp + x);
+      step_update(s, sum);
+    }
+    if (threadIdx.x == 0) *a.red.ticket = 0u;
+  }
+}
+
+// ============================================================================ init: r = f, u = d = 0
+template <typename T, int CC>
+__global__ void __launch_bounds__(256) k_init(InitArgs<T> a) {
+  __shared__ double mt[2 * 256];
+  const Grid& g = a.g;
+  const int bl = blockIdx.y;
+  const int b = bl / a.L, l = bl % a.L;
+  load_material<double>(mt, a.mat, b);
+  __syncthreads();
+  int i1, i2, i3;
+  if (!tile_node(g, i1, i2, i3)) return;
+  const long long n = g.n;
+  const uint8_t* ph = a.phase + (long long)b * n;
+  const long long node = ((long long)i1 * g.n2 + i2) * g.n3 + i3;
+  double f[CC];
+  node_rhs<CC>(ph, mt, g, i1, i2, i3, a.loads + l * (CC == 1 ? 3 : 6), f);
+  const long long o = (long long)bl * CC * n + node;
+#pragma unroll
+  for (int i = 0; i < CC; ++i) {
+    if (a.r) a.r[o + i * n] = (T)f[i];
+    if (a.u) a.u[o + i * n] = (T)0;
+    if (a.d) a.d[o + i * n] = (T)0;
+    if (a.p) a.p[o + i * n] = (T)0;
+    if (a.u64) a.u64[o + i * n] = 0.0;
+    if (a.f64) a.f64[o + i * n] = f[i];
+  }
+}
+
+// ============================================================================ true residual
+// r_true = f - K u (FP64).  u = u64 (+ u32 + alpha d when folding a mixed-precision increment,
+// which is done by k_fold beforehand).  Optionally stores r_true into r (type T).
+template <typename T, int CC>
+__global__ void __launch_bounds__(256) k_true_res(TrueResArgs<T> a) {
+  __shared__ double mt[2 * 256];
+  const Grid& g = a.g;
+  const int bl = blockIdx.y;
+  const int b = bl / a.L, l = bl % a.L;
+  load_material<double>(mt, a.mat, b);
+  __syncthreads();
+  if (a.only_pending && !a.sc[bl].need_replace) return;
+  if (!a.only_pending && a.sc[bl].started == 0 && a.require_started) return;
+  int i1, i2, i3;
+  double lmax = 0.0;
+  if (tile_node(g, i1, i2, i3)) {
+    const long long n = g.n;
+    const uint8_t* ph = a.phase + (long long)b * n;
+    const double* u = a.u64 + (long long)bl * CC * n;
+    const long long node = ((long long)i1 * g.n2 + i2) * g.n3 + i3;
+    double f[CC], ku[CC];
+    node_rhs<CC>(ph, mt, g, i1, i2, i3, a.loads + l * (CC == 1 ? 3 : 6), f);
+    node_Ku<double, CC>(u, ph, mt, g, i1, i2, i3, ku);
+#pragma unroll
+    for (int i = 0; i < CC; ++i) {
+      double rr = f[i] - ku[i];
+      lmax = fmax(lmax, fabs(rr));
+      if (a.r) a.r[(long long)bl * CC * n + i * n + node] = (T)rr;
+    }
+  }
+  __shared__ double red_sh[32];
+  double bm = block_max(lmax, red_sh);
+  if (threadIdx.x == 0) atomic_max_nonneg(a.into_rmax ? &a.sc[bl].rmax_bits : &a.sc[bl].tmax_bits, bm);
+}
+
+// ============================================================================ pointwise kernels
+// Mixed-precision fold before a residual replacement: u64 += u32 + alpha d; u32 = 0; alpha = 0.
+template <typename T>
+__global__ void k_fold(FoldArgs<T> a) {
+  const int bl = blockIdx.y;
+  CgScal& s = a.sc[bl];
+  if (a.only_pending && !s.need_replace) return;
+  const double al = s.alpha;
+  const long long m = (long long)a.c * a.n;
+  const long long base = (long long)bl * m;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x) {
+    double v = a.u64[base + i];
+    if (a.u32) {
+      v += (double)a.u32[base + i];
+      a.u32[base + i] = (T)0;
+    }
+    v += al * (double)a.d[base + i];
+    a.u64[base + i] = v;
+  }
+}
+// alpha = 0 after a fold (run after k_fold has finished everywhere)
+__global__ void k_clear_alpha(CgScal* sc, int BL, int only_pending) {
+  int bl = blockIdx.x * blockDim.x + threadIdx.x;
+  if (bl >= BL) return;
+  if (only_pending && !sc[bl].need_replace) return;
+  sc[bl].alpha = 0.0;
+}
+
+// Jacobi / no preconditioner, first half: r <- r - alpha p, ||r||_inf, s = r / diag(K),
+// gamma = r . s; last block: stopping test and search-direction coefficient.
+template <typename T>
+__global__ void __launch_bounds__(256) k_jac_a(JacArgs<T> a) {
+  __shared__ double red_sh[32];
+  const int bl = blockIdx.y;
+  CgScal& s = a.sc[bl];
+  const bool active = !s.done;
+  const double al = a.after_replace ? 0.0 : s.alpha;
+  double lmax = 0.0, gam = 0.0;
+  if (active) {
+    const long long m = (long long)a.c * a.n;
+    const long long base = (long long)bl * m;
+    const long long ib = (long long)(bl / a.L) * m;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x) {
+      T r = a.r[base + i];
+      if (al != 0.0) {
+        r -= (T)al * a.p[base + i];
+        a.r[base + i] = r;
+      }
+      T sv = a.invdiag ? r * a.invdiag[ib + i] : r;
+      lmax = fmax(lmax, fabs((double)r));
+      gam += (double)r * (double)sv;
+    }
+  }
+  double bm = block_max(lmax, red_sh);
+  double bg = block_sum(gam, red_sh);
+  if (threadIdx.x == 0) {
+    if (active) atomic_max_nonneg(&s.rmax_bits, bm);
+    a.red.part[(long long)bl * gridDim.x + blockIdx.x] = bg;
+  }
+  if (last_block(a.red.ticket)) {
+    residual_decision(a.sc, a.BL, a.ctl, a.after_replace);
+    __syncthreads();
+    for (int q = threadIdx.x; q < a.BL; q += blockDim.x) {
+      CgScal& t = a.sc[q];
+      if (t.done || t.need_replace) continue;
+      double sum = 0.0;
+      const double* pp = a.red.part + (long long)q * gridDim.x;
+      for (int x = 0; x < (int)gridDim.x; ++x) sum += ld_cg(pp + x);
+      direction_update(t, sum, 0.0, 0);
+    }
+    if (threadIdx.x == 0) *a.red.ticket = 0u;
+  }
+}
+
+// second half: u <- u + alpha d_old; d <- s + beta d_old
+template <typename T>
+__global__ void __launch_bounds__(256) k_jac_b(JacArgs<T> a) {
+  const int bl = blockIdx.y;
+  const CgScal& s = a.sc[bl];
+  if (s.done) return;
+  const T al = (T)s.alpha, be = (T)s.beta;
+  const long long m = (long long)a.c * a.n;
+  const long long base = (long long)bl * m;
+  const long long ib = (long long)(bl / a.L) * m;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x) {
+    T r = a.r[base + i];
+    T sv = a.invdiag ? r * a.invdiag[ib + i] : r;
+    T dold = a.d[base + i];
+    a.u[base + i] += al * dold;
+    a.d[base + i] = sv + be * dold;
+  }
+}
+
+// inverse of the diagonal of K per instance: [B][c][n]
+template <typename T, int CC>
+__global__ void __launch_bounds__(256) k_invdiag(DiagArgs<T> a) {
+  __shared__ double mt[2 * 256];
+  const Grid& g = a.g;
+  const int b = blockIdx.y;
+  load_material<double>(mt, a.mat, b);
+  __syncthreads();
+  int i1, i2, i3;
+  if (!tile_node(g, i1, i2, i3)) return;
+  const long long n = g.n;
+  const uint8_t* ph = a.phase + (long long)b * n;
+  const long long node = ((long long)i1 * g.n2 + i2) * g.n3 + i3;
+  double dg[CC];
+  node_diag<CC>(ph, mt, g, i1, i2, i3, dg);
+#pragma unroll
+  for (int i = 0; i < CC; ++i) a.invdiag[(long long)b * CC * n + i * n + node] = (T)(1.0 / dg[i]);
+}
+
+// ============================================================================ post-processing
+// Final pending update (u += alpha d, or the mixed fold) and per-(field) sums for the mean.
+template <typename T>
+__global__ void __launch_bounds__(256) k_final(FoldArgs<T> a) {
+  __shared__ double red_sh[32];
+  const int bl = blockIdx.y;
+  const int comp = blockIdx.z;
+  const double al = a.sc[bl].alpha;
+  const long long base = ((long long)bl * a.c + comp) * a.n;
+  double sum = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.n; i += (long long)gridDim.x * blockDim.x) {
+    double v = a.u64[base + i];
+    if (a.u32) {
+      v += (double)a.u32[base + i];
+      a.u32[base + i] = (T)0;
+    }
+    v += al * (double)a.d[base + i];
+    a.u64[base + i] = v;
+    sum += v;
+  }
+  double bs = block_sum(sum, red_sh);
+  if (threadIdx.x == 0)
+    a.part[(((long long)bl * a.c + comp) * gridDim.x) + blockIdx.x] = bs;
+}
+
+__global__ void k_zero_mean(double* u, const double* part, int nparts, int c, long long n) {
+  const int bl = blockIdx.y, comp = blockIdx.z;
+  const long long f = (long long)bl * c + comp;
+  __shared__ double mean;
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int x = 0; x < nparts; ++x) s += part[f * nparts + x];
+    mean = s / (double)n;
+  }
+  __syncthreads();
+  double* uf = u + f * n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    uf[i] -= mean;
+}
+
+// Averaged flux / stress per (instance, load) with the element-mean gradient, and optionally
+// the energy-form sensitivity sums.  One thread per element, all loads of an instance.
+template <int CC>
+__global__ void __launch_bounds__(256) k_average(AvgArgs a) {
+  __shared__ double mt[2 * 256];
+  __shared__ double acc_sh[6 * 8];  // [L<=8][dim<=6]
+  const Grid& g = a.g;
+  const int b = blockIdx.y;
+  const int DIM = CC == 1 ? 3 : 6;
+  load_material<double>(mt, a.mat, b);
+  for (int i = threadIdx.x; i < 6 * 8; i += blockDim.x) acc_sh[i] = 0.0;
+  __syncthreads();
+  int i1, i2, i3;
+  if (tile_node(g, i1, i2, i3)) {
+    const long long n = g.n;
+    const uint8_t* ph = a.phase + (long long)b * n;
+    const long long e = ((long long)i1 * g.n2 + i2) * g.n3 + i3;
+    const int p = ph[e];
+    for (int l = 0; l < a.L; ++l) {
+      const double* u = a.u64 + ((long long)b * a.L + l) * CC * n;
+      double sig[6];
+      element_mean_flux<CC>(u, mt, p, g, i1, i2, i3, a.loads + l * DIM, sig);
+      for (int i = 0; i < DIM; ++i) atomicAdd(&acc_sh[l * DIM + i], sig[i]);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < a.L * DIM; i += blockDim.x)
+    a.part[((long long)b * gridDim.x + blockIdx.x) * (8 * 6) + i] = acc_sh[i];
+}
+
+__global__ void k_average_finish(double* out, const double* part, int nparts, int B, int L, int dim, double inv_n) {
+  int b = blockIdx.x;
+  for (int q = threadIdx.x; q < L * dim; q += blockDim.x) {
+    int l = q / dim, i = q % dim;
+    double s = 0.0;
+    for (int x = 0; x < nparts; ++x) s += part[((long long)b * nparts + x) * (8 * 6) + q];
+    out[((long long)b * dim + i) * L + l] = s * inv_n;
+  }
+}
+
+// Sensitivities: for every element, Gauss-point strains of all loads, products per phase.
+template <int CC>
+__global__ void __launch_bounds__(128) k_sens(AvgArgs a) {
+  __shared__ double mt[2 * 256];
+  extern __shared__ double sacc[];  // [n_phases][nq][L][L]
+  const Grid& g = a.g;
+  const int b = blockIdx.y;
+  const int L = a.L;
+  const int nq = CC == 1 ? 1 : 2;
+  const int tot = a.mat.n_phases * nq * L * L;
+  load_material<double>(mt, a.mat, b);
+  for (int i = threadIdx.x; i < tot; i += blockDim.x) sacc[i] = 0.0;
+  __syncthreads();
+  int i1, i2, i3;
+  if (tile_node(g, i1, i2, i3)) {
+    const long long n = g.n;
+    const long long e = ((long long)i1 * g.n2 + i2) * g.n3 + i3;
+    const int p = a.phase[(long long)b * n + e];
+    element_sensitivity<CC>(a.u64 + (long long)b * L * CC * n, L, g, i1, i2, i3, a.loads,
+                            sacc + (long long)p * nq * L * L);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < tot; i += blockDim.x)
+    a.part[((long long)b * gridDim.x + blockIdx.x) * tot + i] = sacc[i];
+}
+
+__global__ void k_sens_finish(double* out, const double* part, int nparts, int tot, double inv_n) {
+  int b = blockIdx.x;
+  for (int q = threadIdx.x; q < tot; q += blockDim.x) {
+    double s = 0.0;
+    for (int x = 0; x < nparts; ++x) s += part[((long long)b * nparts + x) * tot + q];
+    out[(long long)b * tot + q] = s * inv_n;
+  }
+}
+
+// [c][n] (double) -> interleaved [n][c]
+__global__ void k_interleave(const double* src, double* dst, int c, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    for (int j = 0; j < c; ++j) dst[i * c + j] = src[j * n + i];
+}
+
+__global__ void k_copy_d2f(const double* src, float* dst, long long m) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
+}
+
+// ============================================================================ launchers
+static dim3 node_grid(const Grid& g, int y) {
+  int tx = (g.n3 + 31) / 32, ty = (g.n2 + 3) / 4, tz = (g.n1 + 1) / 2;
+  return dim3(tx * ty * tz, y);
+}
+int node_blocks_x(const Grid& g) { return node_grid(g, 1).x; }
+
+template <typename T> cudaError_t launch_ku(const StencilArgs<T>& a, cudaStream_t s) {
+  dim3 grid = node_grid(a.g, a.BL);
+  if (a.c == 1) k_ku<T, 1><<<grid, 256, 0, s>>>(a);
+  else k_ku<T, 3><<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+template <typename T> cudaError_t launch_init(const InitArgs<T>& a, int BL, cudaStream_t s) {
+  dim3 grid = node_grid(a.g, BL);
+  if (a.c == 1) k_init<T, 1><<<grid, 256, 0, s>>>(a);
+  else k_init<T, 3><<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+template <typename T> cudaError_t launch_true_res(const TrueResArgs<T>& a, int BL, cudaStream_t s) {
+  dim3 grid = node_grid(a.g, BL);
+  if (a.c == 1) k_true_res<T, 1><<<grid, 256, 0, s>>>(a);
+  else k_true_res<T, 3><<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+static int pw_blocks(long long m) {
+  long long b = (m + 255) / 256;
+  if (b > 1184) b = 1184;  // 8 blocks per SM on 148+ SMs, grid-stride beyond
+  return (int)(b < 1 ? 1 : b);
+}
+template <typename T> cudaError_t launch_fold(const FoldArgs<T>& a, int BL, cudaStream_t s) {
+  k_fold<T><<<dim3(pw_blocks((long long)a.c * a.n), BL), 256, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_clear_alpha<<<(BL + 127) / 128, 128, 0, s>>>(a.sc, BL, a.only_pending);
+  return cudaGetLastError();
+}
+template <typename T> cudaError_t launch_final(const FoldArgs<T>& a, int BL, int nparts, cudaStream_t s) {
+  k_final<T><<<dim3(nparts, BL, a.c), 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t launch_zero_mean(double* u, const double* part, int nparts, int c, long long n, int BL, cudaStream_t s) {
+  k_zero_mean<<<dim3(nparts, BL, c), 256, 0, s>>>(u, part, nparts, c, n);
+  return cudaGetLastError();
+}
+template <typename T> cudaError_t launch_jac(const JacArgs<T>& a, int which, cudaStream_t s) {
+  dim3 grid(pw_blocks((long long)a.c * a.n) / (a.BL > 8 ? 4 : 1) + 1, a.BL);
+  if (which == 0) k_jac_a<T><<<grid, 256, 0, s>>>(a);
+  else k_jac_b<T><<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+int jac_blocks_x(long long m, int BL) { return pw_blocks(m) / (BL > 8 ? 4 : 1) + 1; }
+template <typename T> cudaError_t launch_invdiag(const DiagArgs<T>& a, int B, cudaStream_t s) {
+  dim3 grid = node_grid(a.g, B);
+  if (a.c == 1) k_invdiag<T, 1><<<grid, 256, 0, s>>>(a);
+  else k_invdiag<T, 3><<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t launch_average(const AvgArgs& a, int B, double* out, cudaStream_t s) {
+  dim3 grid = node_grid(a.g, B);
+  if (a.c == 1) k_average<1><<<grid, 256, 0, s>>>(a);
+  else k_average<3><<<grid, 256, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_average_finish<<<B, 64, 0, s>>>(out, a.part, grid.x, B, a.L, a.c == 1 ? 3 : 6, 1.0 / (double)a.g.n);
+  return cudaGetLastError();
+}
+cudaError_t launch_sens(const AvgArgs& a, int B, double* out, cudaStream_t s) {
+  dim3 grid = node_grid(a.g, B);
+  int nq = a.c == 1 ? 1 : 2;
+  int tot = a.mat.n_phases * nq * a.L * a.L;
+  size_t smem = (size_t)tot * sizeof(double);
+  if (a.c == 1) k_sens<1><<<dim3(grid.x * 2, B), 128, smem, s>>>(a);
+  else k_sens<3><<<dim3(grid.x * 2, B), 128, smem, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_sens_finish<<<B, 128, 0, s>>>(out, a.part, grid.x * 2, tot, 1.0 / (double)a.g.n);
+  return cudaGetLastError();
+}
+int sens_blocks_x(const Grid& g) { return node_grid(g, 1).x * 2; }
+cudaError_t launch_interleave(const double* src, double* dst, int c, long long n, cudaStream_t s) {
+  k_interleave<<<pw_blocks(n), 256, 0, s>>>(src, dst, c, n);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_ku<double>(const StencilArgs<double>&, cudaStream_t);
+template cudaError_t launch_ku<float>(const StencilArgs<float>&, cudaStream_t);
+template cudaError_t launch_init<double>(const InitArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_init<float>(const InitArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_true_res<double>(const TrueResArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_true_res<float>(const TrueResArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_fold<double>(const FoldArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_fold<float>(const FoldArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_final<double>(const FoldArgs<double>&, int, int, cudaStream_t);
+template cudaError_t launch_final<float>(const FoldArgs<float>&, int, int, cudaStream_t);
+template cudaError_t launch_jac<double>(const JacArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_jac<float>(const JacArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_invdiag<double>(const DiagArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_invdiag<float>(const DiagArgs<float>&, int, cudaStream_t);
+
+}  // namespace unocg

@@ -1,0 +1,157 @@
+// Kernel argument blocks and host launchers shared by the kernel translation units and the
+// C ABI driver.
+#pragma once
+#include "common.cuh"
+#include "cg.cuh"
+
+namespace unocg {
+
+// ---------------------------------------------------------------- FFT passes
+template <typename T> struct PlaneFwdArgs {
+  Grid g;
+  int c, BL;
+  T* r;                 // CG mode: residual, updated in place r <- r - alpha p
+  const T* p;           // CG mode: K d of the previous iteration
+  const T* src;         // standalone mode: input fields [BL][c][n]
+  cplx<T>* hat;         // output: axes-2/3 spectra [BL][c][n1][n2][n3h]
+  CgScal* sc;           // CG mode
+  FftTables ft;
+  unsigned int* ticket;
+  LoopCtl ctl;
+  int after_replace;    // CG mode: residual was just replaced (no update, alpha = 0)
+  int standalone;       // transform src only (no CG bookkeeping)
+};
+
+template <typename T, typename QT> struct LineArgs {
+  Grid g;
+  int c, BL, L;         // L = loads per instance (weights may be per instance)
+  const cplx<T>* hat;   // axes-2/3 spectra of r  [BL][c][n1][M], M = n2*n3h
+  cplx<T>* shat;        // output: P applied, axis 1 inverted again  [BL][c][n1][M]
+  const cplx<T>* ghat;  // backward mode: spectra of the upstream gradient
+  const QT* Q;          // unique block entries [Bq][n1][M][C]
+  long long q_inst_stride;  // entries per instance (0 = shared)
+  double scale;         // 1 / n (unnormalized transform pair)
+  CgScal* sc;
+  Reduce red;
+  FftTables ft;
+  int tb;               // positions per block
+  int flexible;
+  int standalone;       // 1: apply only (no CG bookkeeping)
+  float* gq;            // backward: dL/dv accumulated over the batch [n1][M][C] (float)
+};
+
+template <typename T> struct PlaneInvArgs {
+  Grid g;
+  int c, BL;
+  const cplx<T>* shat;  // [BL][c][n1][n2][n3h]
+  T* d;                 // CG mode: search direction, d <- s + beta d
+  T* u;                 // CG mode: solution, u <- u + alpha d_old
+  T* dst;               // standalone: output s
+  CgScal* sc;
+  FftTables ft;
+  int standalone;
+};
+
+// ---------------------------------------------------------------- material / stencil
+
+template <typename T> struct StencilArgs {
+  Grid g;
+  int c, BL, L;
+  const uint8_t* phase; // [B][n]
+  Material mat;
+  const T* d;           // [BL][c][n]
+  T* p;                 // [BL][c][n]
+  CgScal* sc;
+  Reduce red;
+  int standalone;       // no CG bookkeeping (operator apply)
+};
+
+template <typename T> struct InitArgs {
+  Grid g;
+  int c, L;
+  const uint8_t* phase;
+  Material mat;
+  const double* loads;  // [L][3 or 6]
+  T* r; T* u; T* d; T* p;   // any may be null
+  double* u64;          // optional FP64 solution (zeroed)
+  double* f64;          // optional FP64 right-hand side output
+};
+
+template <typename T> struct TrueResArgs {
+  Grid g;
+  int c, L;
+  const uint8_t* phase;
+  Material mat;
+  const double* loads;
+  const double* u64;    // [BL][c][n]
+  T* r;                 // optional: store f - K u
+  CgScal* sc;
+  int only_pending;     // only (instance, load) with need_replace set
+  int require_started;
+  int into_rmax;        // accumulate into rmax_bits (replacement) instead of tmax_bits (report)
+};
+
+template <typename T> struct FoldArgs {
+  int c;
+  long long n;
+  double* u64;
+  T* u32;               // optional increment (mixed precision)
+  const T* d;
+  CgScal* sc;
+  int only_pending;
+  double* part;         // k_final: per-block sums for the mean
+};
+
+template <typename T> struct JacArgs {
+  int c, BL, L;
+  long long n;
+  T* r; const T* p; T* d; T* u;
+  const T* invdiag;     // [B][c][n] or null (no preconditioner)
+  CgScal* sc;
+  Reduce red;
+  LoopCtl ctl;
+  int after_replace;
+};
+
+template <typename T> struct DiagArgs {
+  Grid g;
+  int c;
+  const uint8_t* phase;
+  Material mat;
+  T* invdiag;
+};
+
+struct AvgArgs {
+  Grid g;
+  int c, L;
+  const uint8_t* phase;
+  Material mat;
+  const double* loads;
+  const double* u64;    // [B][L][c][n]
+  double* part;
+};
+
+// launchers (k_stencil.cu)
+template <typename T> cudaError_t launch_ku(const StencilArgs<T>& a, cudaStream_t s);
+template <typename T> cudaError_t launch_init(const InitArgs<T>& a, int BL, cudaStream_t s);
+template <typename T> cudaError_t launch_true_res(const TrueResArgs<T>& a, int BL, cudaStream_t s);
+template <typename T> cudaError_t launch_fold(const FoldArgs<T>& a, int BL, cudaStream_t s);
+template <typename T> cudaError_t launch_final(const FoldArgs<T>& a, int BL, int nparts, cudaStream_t s);
+template <typename T> cudaError_t launch_jac(const JacArgs<T>& a, int which, cudaStream_t s);
+template <typename T> cudaError_t launch_invdiag(const DiagArgs<T>& a, int B, cudaStream_t s);
+cudaError_t launch_zero_mean(double* u, const double* part, int nparts, int c, long long n, int BL, cudaStream_t s);
+cudaError_t launch_average(const AvgArgs& a, int B, double* out, cudaStream_t s);
+cudaError_t launch_sens(const AvgArgs& a, int B, double* out, cudaStream_t s);
+cudaError_t launch_interleave(const double* src, double* dst, int c, long long n, cudaStream_t s);
+int node_blocks_x(const Grid& g);
+int jac_blocks_x(long long m, int BL);
+int sens_blocks_x(const Grid& g);
+
+// launchers (k_fft.cu)
+template <typename T> cudaError_t launch_plane_fwd(const PlaneFwdArgs<T>& a, cudaStream_t s);
+template <typename T, typename QT> cudaError_t launch_line(const LineArgs<T, QT>& a, int backward, cudaStream_t s);
+template <typename T> cudaError_t launch_plane_inv(const PlaneInvArgs<T>& a, cudaStream_t s);
+int line_blocks_x(const Grid& g, int c, int elem_bytes);
+bool plane_fits(const Grid& g, int elem_bytes);
+
+}  // namespace unocg

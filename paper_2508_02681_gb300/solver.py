@@ -1,0 +1,93 @@
+"""Convenience wrappers over the C ABI: a homogenization solver object and the UNO operator as a
+``torch.autograd.Function`` (forward and backward both run in the library's kernels)."""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _lib, api
+
+
+class Homogenization:
+    """One context: ``batch`` instances of an ``n1 x n2 x n3`` periodic voxel problem.
+
+    ``physics``: ``_lib.THERMAL`` (kappa per phase) or ``_lib.ELASTIC`` ((E, nu) per phase).
+    """
+
+    def __init__(self, physics: int, shape, batch: int = 1, L0: float = 1.0):
+        self.physics = physics
+        self.c = 1 if physics == _lib.THERMAL else 3
+        self.dim = 3 if physics == _lib.THERMAL else 6
+        self.shape = tuple(int(s) for s in shape)
+        self.batch = batch
+        self.n = int(np.prod(self.shape))
+        self.ctx = api.unocg_create(physics, batch, *self.shape, L0)
+        self.n_loads = 0
+        self.n_phases = 0
+
+    def close(self):
+        if self.ctx is not None:
+            api.unocg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_microstructure(self, phase, n_phases: int):
+        api.unocg_set_microstructure(self.ctx, phase, n_phases)
+        self.n_phases = n_phases
+
+    def set_phase_properties(self, props):
+        api.unocg_set_phase_properties(self.ctx, props)
+
+    def set_macro_load(self, loads):
+        loads = np.atleast_2d(np.asarray(loads, dtype=np.float64))
+        api.unocg_set_macro_load(self.ctx, loads)
+        self.n_loads = loads.shape[0]
+
+    def set_uno_weights(self, kind=_lib.W_REFERENCE_MEDIUM, w=None, spd_eps: float = 0.0):
+        api.unocg_set_uno_weights(self.ctx, kind, w, spd_eps)
+
+    def solve(self, raise_on_error: bool = True, **opts) -> api.Info:
+        return api.unocg_solve(self.ctx, api.make_opts(**opts), self.batch * self.n_loads, raise_on_error)
+
+    def fluctuation(self, instance: int = 0, load: int = 0) -> np.ndarray:
+        """Zero-mean fluctuation, interleaved ``[n * c]`` (the paper's DOF order)."""
+        return api.unocg_get_fluctuation(self.ctx, instance, load, self.n * self.c)
+
+    def effective_tensor(self) -> np.ndarray:
+        return api.unocg_get_effective_tensor(self.ctx, self.batch, self.dim, self.n_loads)
+
+    def sensitivity(self) -> np.ndarray:
+        n_props = self.n_phases * (1 if self.physics == _lib.THERMAL else 2)
+        return api.unocg_get_sensitivity(self.ctx, self.batch, n_props, self.n_loads)
+
+
+def uno_function():
+    """``torch.autograd.Function`` for ``s = P_theta r`` on a batch ``[B, c, N1, N2, N3]``."""
+    import torch
+
+    class UnoApply(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, r, theta, op):
+            r = r.contiguous()
+            api.unocg_uno_set_theta_dev(op, theta)
+            s = torch.empty_like(r)
+            api.unocg_uno_apply_dev(op, r.shape[0], r, s)
+            ctx.save_for_backward(r, theta)
+            ctx.op = op
+            return s
+
+        @staticmethod
+        def backward(ctx, gs):
+            r, theta = ctx.saved_tensors
+            gs = gs.contiguous()
+            gr = torch.empty_like(r) if ctx.needs_input_grad[0] else None
+            gt = torch.empty_like(theta) if ctx.needs_input_grad[1] else None
+            api.unocg_uno_set_theta_dev(ctx.op, theta)
+            api.unocg_uno_backward_dev(ctx.op, r.shape[0], r, gs, gr, gt)
+            return gr, gt, None
+
+    return UnoApply
