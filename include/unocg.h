@@ -94,6 +94,8 @@ typedef struct {
   double* rel_res;     /* optional [B*L]: final ||r||_inf / ||r_0||_inf (recursive residual) */
   double* true_rel_res;/* optional [B*L]: final ||f - K u||_inf / ||f||_inf in FP64         */
   int* load_status;    /* optional [B*L]: per (instance, load) status                       */
+  int checks;          /* residual checks after CG steps (= loop bodies executed + 1)        */
+  int replacements;    /* residual replacements executed (mixed precision)                  */
 } unocg_solve_info;
 
 /* Create a context for `batch` instances on an n1 x n2 x n3 grid (each n_i of the form
@@ -149,6 +151,13 @@ int unocg_get_sensitivity(unocg_ctx* ctx, double* out);
    per-(instance, load) convergence masks.  infos may be NULL or hold n_ctx entries.        */
 int unocg_batch_solve(int n_ctx, unocg_ctx* const* ctxs, const unocg_solve_opts* opts,
                       unocg_solve_info* infos);
+
+/* Timing of the hot-path kernels: runs the first `reps` CG iterations of a fresh solve with the
+   options `opts`, each kernel launched on its own between two CUDA events on the context stream,
+   and writes the mean milliseconds per launch to ms_out[0..3]: UNO: [axis-1 pass with block
+   multiply, inverse plane pass, K d, residual update + forward plane pass]; Jacobi / none:
+   [direction update, (unused, 0), K d, residual update].  Invalidates the last solution.     */
+int unocg_profile_iteration(unocg_ctx* ctx, const unocg_solve_opts* opts, int reps, double* ms_out, int n_out);
 
 /* ---------------------------------------------------------------- standalone UNO operator
    P = T^H Q T on a batch of fields, for training (Sec. 5.3, Algorithm 3).                  */

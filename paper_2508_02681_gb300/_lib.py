@@ -47,7 +47,7 @@ class SolveOpts(C.Structure):
 class SolveInfo(C.Structure):
     _fields_ = [("status", C.c_int), ("max_iters", C.c_int), ("iters", C.POINTER(C.c_int)),
                 ("rel_res", C.POINTER(C.c_double)), ("true_rel_res", C.POINTER(C.c_double)),
-                ("load_status", C.POINTER(C.c_int))]
+                ("load_status", C.POINTER(C.c_int)), ("checks", C.c_int), ("replacements", C.c_int)]
 
 
 _vp = C.c_void_p
@@ -73,6 +73,7 @@ SIGNATURES = {
     "unocg_get_effective_tensor": (_i, [_vp, _vp]),
     "unocg_get_sensitivity": (_i, [_vp, _vp]),
     "unocg_batch_solve": (_i, [_i, C.POINTER(_vp), C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
+    "unocg_profile_iteration": (_i, [_vp, C.POINTER(SolveOpts), _i, _vp, _i]),
     "unocg_uno_create": (_i, [C.POINTER(_vp), _i, _i, _i, _i]),
     "unocg_uno_destroy": (None, [_vp]),
     "unocg_uno_last_error": (C.c_char_p, [_vp]),

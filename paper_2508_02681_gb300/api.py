@@ -101,11 +101,19 @@ class Info:
         self.c = SolveInfo(0, 0, self.iters.ctypes.data_as(C.POINTER(C.c_int)),
                            self.rel_res.ctypes.data_as(C.POINTER(C.c_double)),
                            self.true_rel_res.ctypes.data_as(C.POINTER(C.c_double)),
-                           self.load_status.ctypes.data_as(C.POINTER(C.c_int)))
+                           self.load_status.ctypes.data_as(C.POINTER(C.c_int)), 0, 0)
 
     @property
     def status(self):
         return self.c.status
+
+    @property
+    def checks(self):
+        return self.c.checks
+
+    @property
+    def replacements(self):
+        return self.c.replacements
 
 
 def unocg_solve(ctx, opts: SolveOpts, n_results: int, raise_on_error: bool = True) -> Info:
@@ -169,6 +177,12 @@ def unocg_apply_uno_dev(ctx, instance: int, r_dev, s_dev, stream=None):
 
 def unocg_rhs_dev(ctx, instance: int, load: int, f_dev, stream=None):
     _check(ctx, _lib.load().unocg_rhs_dev(ctx, instance, load, C.c_void_p(f_dev.data_ptr()), _stream(stream)))
+
+
+def unocg_profile_iteration(ctx, opts: SolveOpts, reps: int = 10) -> np.ndarray:
+    out = np.zeros(4)
+    _check(ctx, _lib.load().unocg_profile_iteration(ctx, C.byref(opts), reps, _ptr(out), 4))
+    return out
 
 
 # ---------------------------------------------------------------- standalone UNO operator

@@ -547,6 +547,7 @@ static cudaError_t enq_pre(unocg_ctx* ctx, cudaStream_t s, const Plan& pl, const
   const int BL = ctx->B * ctx->L;
   cudaError_t e = cudaMemsetAsync(ctx->sc, 0, BL * sizeof(CgScal), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->tickets, 0, kMaxTickets * sizeof(unsigned int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->flags + 2, 0, 2 * sizeof(int), s);
   if (e != cudaSuccess) return e;
   InitArgs<T> ia{};
   ia.g = ctx->g; ia.c = ctx->c; ia.L = ctx->L; ia.phase = ctx->phase; ia.mat = material(ctx);
@@ -563,43 +564,57 @@ static cudaError_t enq_pre(unocg_ctx* ctx, cudaStream_t s, const Plan& pl, const
 }
 
 template <typename T>
-static cudaError_t enq_body(unocg_ctx* ctx, cudaStream_t s, const Plan& pl, const LoopCtl& ctl) {
+static cudaError_t enq_precond(unocg_ctx* ctx, cudaStream_t s, const Plan& pl, const LoopCtl& ctl, int part) {
+  // part 0: transform axis 1 + block multiply (UNO) / direction update (Jacobi, none)
+  // part 1: inverse plane transform with the direction update (UNO only)
   auto& f = Sel<T>::f(ctx);
   const int BL = ctx->B * ctx->L;
-  cudaError_t e;
   if (pl.o.precond == UNOCG_PRECOND_UNO) {
-    using QT = typename Sel<T>::QT;
-    LineArgs<T, QT> la{};
-    la.g = ctx->g; la.c = ctx->c; la.BL = BL; la.L = ctx->L;
-    la.hat = f.rhat; la.shat = f.shat; la.ghat = nullptr;
-    la.Q = Sel<T>::Q(ctx);
-    la.q_inst_stride = ctx->Bq > 1 ? ctx->g.nh * (ctx->c == 1 ? 1 : 6) : 0;
-    la.scale = 1.0 / (double)ctx->g.n;
-    la.sc = ctx->sc; la.red = Reduce{ctx->part, ctx->tickets + T_LINE};
-    la.ft = tables(ctx, sizeof(T) == 8);
-    la.flexible = pl.o.flexible; la.standalone = 0; la.gq = nullptr;
-    e = launch_line<T, QT>(la, 0, s);
-    if (e != cudaSuccess) return e;
+    if (part == 0) {
+      using QT = typename Sel<T>::QT;
+      LineArgs<T, QT> la{};
+      la.g = ctx->g; la.c = ctx->c; la.BL = BL; la.L = ctx->L;
+      la.hat = f.rhat; la.shat = f.shat; la.ghat = nullptr;
+      la.Q = Sel<T>::Q(ctx);
+      la.q_inst_stride = ctx->Bq > 1 ? ctx->g.nh * (ctx->c == 1 ? 1 : 6) : 0;
+      la.scale = 1.0 / (double)ctx->g.n;
+      la.sc = ctx->sc; la.red = Reduce{ctx->part, ctx->tickets + T_LINE};
+      la.ft = tables(ctx, sizeof(T) == 8);
+      la.flexible = pl.o.flexible; la.standalone = 0; la.gq = nullptr;
+      return launch_line<T, QT>(la, 0, s);
+    }
     PlaneInvArgs<T> pa{};
     pa.g = ctx->g; pa.c = ctx->c; pa.BL = BL; pa.shat = f.shat; pa.d = f.d; pa.u = f.u; pa.dst = nullptr;
     pa.sc = ctx->sc; pa.ft = tables(ctx, sizeof(T) == 8); pa.standalone = 0;
-    e = launch_plane_inv<T>(pa, s);
-  } else {
-    JacArgs<T> a{};
-    a.c = ctx->c; a.BL = BL; a.L = ctx->L; a.n = ctx->g.n;
-    a.r = f.r; a.p = f.p; a.d = f.d; a.u = f.u;
-    a.invdiag = pl.o.precond == UNOCG_PRECOND_JACOBI ? Sel<T>::invdiag(ctx) : nullptr;
-    a.sc = ctx->sc; a.red = Reduce{ctx->part, ctx->tickets + T_JAC};
-    a.ctl = ctl;
-    e = launch_jac<T>(a, 1, s);
+    return launch_plane_inv<T>(pa, s);
   }
-  if (e != cudaSuccess) return e;
+  if (part == 1) return cudaSuccess;
+  JacArgs<T> a{};
+  a.c = ctx->c; a.BL = BL; a.L = ctx->L; a.n = ctx->g.n;
+  a.r = f.r; a.p = f.p; a.d = f.d; a.u = f.u;
+  a.invdiag = pl.o.precond == UNOCG_PRECOND_JACOBI ? Sel<T>::invdiag(ctx) : nullptr;
+  a.sc = ctx->sc; a.red = Reduce{ctx->part, ctx->tickets + T_JAC};
+  a.ctl = ctl;
+  return launch_jac<T>(a, 1, s);
+}
+
+template <typename T>
+static cudaError_t enq_ku(unocg_ctx* ctx, cudaStream_t s) {
+  auto& f = Sel<T>::f(ctx);
   StencilArgs<T> ka{};
-  ka.g = ctx->g; ka.c = ctx->c; ka.BL = BL; ka.L = ctx->L; ka.phase = ctx->phase; ka.mat = material(ctx);
+  ka.g = ctx->g; ka.c = ctx->c; ka.BL = ctx->B * ctx->L; ka.L = ctx->L; ka.phase = ctx->phase;
+  ka.mat = material(ctx);
   ka.d = f.d; ka.p = f.p; ka.sc = ctx->sc; ka.red = Reduce{ctx->part, ctx->tickets + T_KU}; ka.standalone = 0;
-  e = launch_ku<T>(ka, s);
-  if (e != cudaSuccess) return e;
-  return enq_residual_check<T>(ctx, s, ctl, 0, pl.o.precond);
+  return launch_ku<T>(ka, s);
+}
+
+template <typename T>
+static cudaError_t enq_body(unocg_ctx* ctx, cudaStream_t s, const Plan& pl, const LoopCtl& ctl) {
+  cudaError_t e = enq_precond<T>(ctx, s, pl, ctl, 0);
+  if (e == cudaSuccess) e = enq_precond<T>(ctx, s, pl, ctl, 1);
+  if (e == cudaSuccess) e = enq_ku<T>(ctx, s);
+  if (e == cudaSuccess) e = enq_residual_check<T>(ctx, s, ctl, 0, pl.o.precond);
+  return e;
 }
 
 // FP64 residual replacement for the pending (instance, load) pairs, then a fresh residual check
@@ -668,6 +683,7 @@ static int build_graph(unocg_ctx* ctx, const Plan& pl) {
   ctl.tol = pl.o.tol; ctl.max_iter = pl.o.max_iter; ctl.mixed = pl.mixed;
   ctl.replace_every = pl.o.replace_every; ctl.flexible = pl.o.flexible;
   ctl.h_while = hw; ctl.set_while = 1; ctl.set_if = 0;
+  ctl.counters = ctx->flags + 2;
   if (e == cudaSuccess) e = enq_pre<T>(ctx, cs, pl, ctl);
   cudaGraphNode_t wnode;
   cudaGraphNodeParams wp{};
@@ -752,6 +768,7 @@ static int run_host_loop(unocg_ctx* ctx, const Plan& pl) {
   ctl.tol = pl.o.tol; ctl.max_iter = pl.o.max_iter; ctl.mixed = pl.mixed;
   ctl.replace_every = pl.o.replace_every; ctl.flexible = pl.o.flexible;
   ctl.active_flag = ctx->flags; ctl.replace_flag = ctx->flags + 1;
+  ctl.counters = ctx->flags + 2;
   CK(enq_pre<T>(ctx, s, pl, ctl));
   int hf[2] = {0, 0};
   const long long cap = 4LL * pl.o.max_iter + 16;
@@ -848,8 +865,12 @@ extern "C" int unocg_solve_wait(unocg_ctx* ctx, unocg_solve_info* info) {
     }
   }
   if (info) {
+    int cnt[2] = {0, 0};
+    CK(cudaMemcpy(cnt, ctx->flags + 2, 2 * sizeof(int), cudaMemcpyDeviceToHost));
     info->status = status;
     info->max_iters = mx;
+    info->checks = cnt[0];
+    info->replacements = cnt[1];
   }
   if (status != UNOCG_OK) {
     ctx->err = status == UNOCG_ERR_NOT_CONVERGED ? "not converged within max_iter" : "CG breakdown";
@@ -944,6 +965,53 @@ extern "C" int unocg_get_sensitivity(unocg_ctx* ctx, double* out) {
       }
     }
   return UNOCG_OK;
+}
+
+// Per-kernel CUDA-event timing of the first `reps` CG iterations of a fresh solve (same
+// kernels and launch shapes as the graph); leaves the context without a valid solution.
+template <typename T>
+static int profile_iters(unocg_ctx* ctx, const Plan& pl, int reps, double* ms_out, int n_out) {
+  cudaStream_t s = ctx->stream;
+  LoopCtl ctl{};
+  ctl.tol = pl.o.tol; ctl.max_iter = pl.o.max_iter; ctl.mixed = 0;
+  ctl.replace_every = 0; ctl.flexible = pl.o.flexible;
+  Plan p2 = pl;
+  p2.mixed = 0;
+  CK(enq_pre<T>(ctx, s, p2, ctl));
+  const int nk = 4;
+  std::vector<cudaEvent_t> ev(2 * nk * reps);
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  for (int r = 0; r < reps; ++r) {
+    for (int k = 0; k < nk; ++k) {
+      CK(cudaEventRecord(ev[2 * (r * nk + k)], s));
+      if (k < 2) CK(enq_precond<T>(ctx, s, p2, ctl, k));
+      else if (k == 2) CK(enq_ku<T>(ctx, s));
+      else CK(enq_residual_check<T>(ctx, s, ctl, 0, pl.o.precond));
+      CK(cudaEventRecord(ev[2 * (r * nk + k) + 1], s));
+    }
+  }
+  CK(cudaStreamSynchronize(s));
+  for (int k = 0; k < nk && k < n_out; ++k) {
+    double tot = 0.0;
+    for (int r = 0; r < reps; ++r) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, ev[2 * (r * nk + k)], ev[2 * (r * nk + k) + 1]));
+      tot += ms;
+    }
+    ms_out[k] = tot / reps;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  ctx->solved = false;
+  return UNOCG_OK;
+}
+
+extern "C" int unocg_profile_iteration(unocg_ctx* ctx, const unocg_solve_opts* o, int reps, double* ms_out, int n_out) {
+  if (!ctx || !o || reps < 1 || !ms_out || n_out < 1) return fail(ctx, UNOCG_ERR_INVALID_ARG, "bad arguments");
+  Plan pl;
+  int rc = prepare_solve(ctx, o, &pl);
+  if (rc) return rc;
+  return pl.mixed ? profile_iters<float>(ctx, pl, reps, ms_out, n_out)
+                  : profile_iters<double>(ctx, pl, reps, ms_out, n_out);
 }
 
 extern "C" int unocg_batch_solve(int n_ctx, unocg_ctx* const* ctxs, const unocg_solve_opts* opts,

@@ -18,6 +18,7 @@ struct LoopCtl {
   int set_while, set_if;            // which handles this launch sets
   int* active_flag;                 // optional: 1 while any (instance, load) is still iterating
   int* replace_flag;                // optional: 1 when a residual replacement is due
+  int* counters;                    // optional: [0] residual checks after CG steps, [1] after replacements
 };
 
 // Residual check after r <- r - alpha p (or after a replacement, `after_replace`).  Runs in the
@@ -65,6 +66,7 @@ __device__ inline void residual_decision(CgScal* sc, int BL, const LoopCtl& ctl,
   any_active = __syncthreads_or(any_active);
   any_replace = __syncthreads_or(any_replace);
   if (threadIdx.x == 0) {
+    if (ctl.counters) atomicAdd(ctl.counters + (after_replace ? 1 : 0), 1);
     if (ctl.set_while) cudaGraphSetConditional(ctl.h_while, any_active ? 1u : 0u);
     if (ctl.set_if) cudaGraphSetConditional(ctl.h_if, any_replace ? 1u : 0u);
     if (ctl.active_flag) *ctl.active_flag = any_active;
