@@ -1,0 +1,329 @@
+"""Benchmark: UNO-CG time-to-1e-6 on one GB300 (mixed precision vs FP64, vs Jac-CG).
+
+Workload (default): thermal conduction on a 64^3 periodic voxel grid, two phases with spherical
+inclusions (radius 6 voxels, volume fraction 0.3, seeded periodic RSA), conductivity 1 / 100,
+all 3 macroscopic gradient load cases, relative residual 1e-6.  One step = one complete solve of
+all load cases (right-hand sides, CG loop to tolerance, zero-mean fluctuations, averaged flux),
+inputs resident on the device, the UNO weights (closed-form reference-medium fundamental
+solution) prepared once beforehand.  `value` is the mean device time per step of the
+mixed-precision UNO-CG solve; FP64 UNO-CG and FP64 Jac-CG are timed on the same input.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank solves its own instance (replicas, no collective on the data
+path); rank 0 prints the JSON line with the max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "UNO-CG time-to-1e-6 residual & HBM GB/s, mixed vs FP64, vs Jac-CG, 1×GB300"
+WORKLOAD = ("thermal 64^3 periodic voxels, RSA spheres r=6 vf=0.3, kappa 1/100, 3 gradient loads, "
+            "UNO-CG (closed-form reference-medium weights) to relative residual 1e-6")
+TOL = 1e-6
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-only", action="store_true", help="a few solves, for ncu launch lists")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="profile-only: host-driven loop (kernels inside conditional graph bodies are not visible to ncu)")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.dev = device_index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- helpers
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def algorithmic_bytes(n, nh, c, BL, B, C_q, fb, qb):
+    """Bytes each kernel of one CG iteration must move at least (each array once): field
+    element size fb, complex 2*fb, weights qb per entry."""
+    cb = 2 * fb
+    return {
+        "line": BL * (3 * c * nh * cb) + nh * C_q * qb * B,        # r_hat in, s_hat_old in, s_hat out, Q
+        "plane_inv": BL * (c * nh * cb + 4 * c * n * fb),           # s_hat in, d/u in+out
+        "ku": BL * (2 * c * n * fb) + B * n,                          # d in, p out, phase labels
+        "plane_fwd": BL * (3 * c * n * fb + c * nh * cb),             # r, p in, r out, r_hat out
+    }
+
+
+def launches_per_solve(info, precond_uno=True):
+    bodies = max(int(info.checks) - 1, 0)
+    per_body = 4 if precond_uno else 3
+    return 2 + per_body * bodies + 4 * int(info.replacements) + 5
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import homogenize as hz
+    from synth import workload
+    w = workload(2)
+    cores = len(os.sched_getaffinity(0))
+    times = []
+    iters = []
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        r = hz.solve(w["phase"], w["props"], 1, w["loads"][:1], precond="uno", tol=TOL)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+            iters.append(r["iters"][0])
+    ms = float(np.mean(times)) * 1000.0 * 3.0  # one load per step, scaled to the 3-load workload
+    sample = "one of the 3 load cases (gradient e1) per step, full oracle solve (assembled CSR K, DFT-by-definition UNO, Algorithm 2), scaled x3"
+    line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample,
+                             "iterations": int(np.mean(iters))},
+            "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------- our arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2508_02681_gb300 import _lib, api
+    from paper_2508_02681_gb300.solver import Homogenization
+    from synth import workload
+
+    w = workload(2, instance=rank)
+    shape = w["phase"].shape
+    n = int(np.prod(shape))
+    L = w["loads"].shape[0]
+    # a dedicated (non-default) stream: the solve and the timing events share it
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    h = Homogenization(_lib.THERMAL, shape)
+    api.unocg_set_stream(h.ctx, stream)
+    h.set_microstructure(w["phase"], 2)
+    h.set_phase_properties(w["props"])
+    h.set_macro_load(w["loads"])
+    h.set_uno_weights(_lib.W_REFERENCE_MEDIUM)
+
+    variants = {
+        "mixed_uno": api.make_opts(tol=TOL, max_iter=2000, precond=_lib.PRECOND_UNO, precision=_lib.MIXED,
+                                   replace_every=50, flexible=1),
+        "fp64_uno": api.make_opts(tol=TOL, max_iter=2000, precond=_lib.PRECOND_UNO, precision=_lib.FP64, flexible=0),
+        "fp64_jacobi": api.make_opts(tol=TOL, max_iter=20000, precond=_lib.PRECOND_JACOBI, precision=_lib.FP64, flexible=0),
+    }
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
+
+    def timed(opts, steps, warmup):
+        for _ in range(warmup):
+            api.unocg_solve_async(h.ctx, opts)
+            info = api.unocg_solve_wait(h.ctx, L)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        for i in range(steps):
+            flush.zero_()  # evict the previous solve's working set from L2 (outside the timed pair)
+            ev[i][0].record(stream)
+            api.unocg_solve_async(h.ctx, opts)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        info = api.unocg_solve_wait(h.ctx, L)
+        ms = [a.elapsed_time(b) for a, b in ev]
+        return float(np.mean(ms)), info
+
+    if args.profile_only:
+        opts = variants["mixed_uno"]
+        if args.no_graph:
+            opts.use_graph = 0
+        for _ in range(2):
+            api.unocg_solve_async(h.ctx, opts)
+            api.unocg_solve_wait(h.ctx, L)
+        torch.cuda.synchronize()
+        print("profile-only run done")
+        return 0
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_mixed, info_mixed = timed(variants["mixed_uno"], args.steps, args.warmup)
+    clock_rec = clocks.stop()
+    C_mixed = h.effective_tensor()[0]
+    side_steps = max(3, min(args.steps, 5))
+    t_fp64, info_fp64 = timed(variants["fp64_uno"], side_steps, 1)
+    C_fp64 = h.effective_tensor()[0]
+    t_jac, info_jac = timed(variants["fp64_jacobi"], max(2, min(args.steps, 3)), 1)
+    C_jac = h.effective_tensor()[0]
+
+    # per-kernel event timing of the mixed iteration (same kernels and launch shapes)
+    k_ms = api.unocg_profile_iteration(h.ctx, variants["mixed_uno"], reps=10)
+    k_ms64 = api.unocg_profile_iteration(h.ctx, variants["fp64_uno"], reps=5)
+    nh = shape[0] * shape[1] * (shape[2] // 2 + 1)
+    ab = algorithmic_bytes(n, nh, 1, L, 1, 1, 4, 2)
+    ab64 = algorithmic_bytes(n, nh, 1, L, 1, 1, 8, 8)
+    names = ["line", "plane_inv", "ku", "plane_fwd"]
+    k_gbs = {nm: ab[nm] / (k_ms[i] * 1e-3) / 1e9 for i, nm in enumerate(names)}
+    dom = names[int(np.argmax(k_ms))]
+    peak, peak_kind = peaks()
+    iter_bytes = sum(ab.values())
+    iter_ms = float(np.sum(k_ms))
+
+    # end to end through the host API (host buffers, copies inside the timed region)
+    e2e_steps = max(3, min(args.steps, 10))
+    phase_host = torch.from_numpy(w["phase"]).pin_memory().numpy()
+    e2e_t = []
+    for i in range(e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h.set_microstructure(phase_host, 2)
+        h.set_phase_properties(w["props"])
+        h.set_macro_load(w["loads"])
+        h.set_uno_weights(_lib.W_REFERENCE_MEDIUM)
+        h.solve(tol=TOL, max_iter=2000, precond=_lib.PRECOND_UNO, precision=_lib.MIXED, replace_every=50)
+        for l in range(L):
+            h.fluctuation(0, l)
+        h.effective_tensor()
+        dt = time.perf_counter() - t0
+        if i > 0:
+            e2e_t.append(dt)
+    e2e_ms = float(np.mean(e2e_t)) * 1000.0
+    h2d = n + w["props"].nbytes + w["loads"].nbytes
+    d2h = L * n * 8 + 3 * L * 8
+
+    t_all = torch.tensor([t_mixed, e2e_ms], device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t_all, op=torch.distributed.ReduceOp.MAX)
+    t_mixed_max, e2e_max = float(t_all[0]), float(t_all[1])
+
+    launches = launches_per_solve(info_mixed) * args.steps
+    line = {
+        "metric": METRIC, "value": t_mixed_max, "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_mixed_max, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": list(shape), "loads": L, "precision": "FP32 fields, BF16 weights, FP64 reductions",
+                   "l2": "flushed (256 MB write) before every timed solve", "parallelism": f"replicas x{world}"},
+        "iterations": {"mixed_uno": int(info_mixed.c.max_iters), "fp64_uno": int(info_fp64.c.max_iters),
+                       "fp64_jacobi": int(info_jac.c.max_iters)},
+        "replacements": int(info_mixed.replacements),
+        "true_rel_res": {"mixed_uno": float(np.max(info_mixed.true_rel_res)),
+                         "fp64_uno": float(np.max(info_fp64.true_rel_res)),
+                         "fp64_jacobi": float(np.max(info_jac.true_rel_res))},
+        "fp64_uno_ms": t_fp64, "fp64_jacobi_ms": t_jac,
+        "speedup_mixed_vs_fp64_uno": t_fp64 / t_mixed, "speedup_mixed_vs_fp64_jacobi": t_jac / t_mixed,
+        "iters_per_s_mixed": float(info_mixed.c.max_iters) / (t_mixed * 1e-3),
+        "C_eff_rel_diff_mixed_vs_fp64": float(np.max(np.abs(C_mixed - C_fp64)) / np.max(np.abs(C_fp64))),
+        "C_eff_rel_diff_jacobi_vs_uno": float(np.max(np.abs(C_jac - C_fp64)) / np.max(np.abs(C_fp64))),
+        "kernel_ms_mixed": dict(zip(names, [float(x) for x in k_ms])),
+        "kernel_gbs_mixed": {k: float(v) for k, v in k_gbs.items()},
+        "kernel_ms_fp64": dict(zip(names, [float(x) for x in k_ms64])),
+        "iteration_gbs_mixed": iter_bytes / (iter_ms * 1e-3) / 1e9,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": k_gbs[dom], "peak": peak, "unit": "GB/s",
+                     "frac": k_gbs[dom] / peak, "traffic": None, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": ab[dom]},
+        "e2e": {"value": e2e_max, "unit": "ms", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "clocks": clock_rec,
+    }
+    h.close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import homogenize as hz
+        t0 = time.perf_counter()
+        r = hz.solve(w["phase"], w["props"], 1, w["loads"][:1], precond="uno", tol=TOL)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": dt * 3.0 * 1000.0, "unit": "ms", "cores": len(os.sched_getaffinity(0)),
+                                "kind": "oracle",
+                                "sample": "gradient load e1 only (1 of 3), full FP64 oracle UNO-CG solve, scaled x3",
+                                "iterations": int(r["iters"][0])}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

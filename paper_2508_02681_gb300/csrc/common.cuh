@@ -150,4 +150,14 @@ __device__ __forceinline__ bool last_block(unsigned int* ticket) {
 
 __device__ __forceinline__ double ld_cg(const double* p) { return __ldcg(p); }
 
+// Sum of `count` partials p[0], p[stride], ... by one warp: each lane adds a fixed strided subset
+// in order, then a fixed shuffle tree (deterministic).  Result in every lane.
+__device__ __forceinline__ double warp_sum_partials(const double* p, int count, int stride) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int x = lane; x < count; x += 32) s += ld_cg(p + (long long)x * stride);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
 }  // namespace unocg

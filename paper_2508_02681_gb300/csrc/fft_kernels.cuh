@@ -223,17 +223,14 @@ __global__ void __launch_bounds__(NTH) k_line(LineArgs<T, QT> a) {
     pp[1] = br;
   }
   if (last_block(a.red.ticket)) {
-    for (int b = threadIdx.x; b < a.BL; b += NTH) {
-      CgScal& s = a.sc[b];
-      if (s.done) continue;
-      double sg = 0.0, sr = 0.0;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int b = warp; b < a.BL; b += NTH / 32) {
       const double* pp = a.red.part + (long long)b * gridDim.x * 2;
-      for (int x = 0; x < (int)gridDim.x; ++x) {
-        sg += ld_cg(pp + 2 * x);
-        sr += ld_cg(pp + 2 * x + 1);
-      }
-      direction_update(s, sg, sr, a.flexible);
+      double sg = warp_sum_partials(pp, gridDim.x, 2);
+      double sr = warp_sum_partials(pp + 1, gridDim.x, 2);
+      if (lane == 0 && !a.sc[b].done) direction_update(a.sc[b], sg, sr, a.flexible);
     }
+    __syncthreads();
     if (threadIdx.x == 0) *a.red.ticket = 0u;
   }
 }

@@ -46,14 +46,12 @@ __global__ void __launch_bounds__(256) k_ku(StencilArgs<T> a) {
   double bs = block_sum(dp, red_sh);
   if (threadIdx.x == 0) a.red.part[(long long)bl * gridDim.x + blockIdx.x] = bs;
   if (last_block(a.red.ticket)) {
-    for (int q = threadIdx.x; q < a.BL; q += blockDim.x) {
-      CgScal& s = a.sc[q];
-      if (s.done) continue;
-      double sum = 0.0;
-      const double* pp = a.red.part + (long long)q * gridDim.x;
-      for (int x = 0; x < (int)gridDim.x; ++x) sum += ld_cg(pp + x);
-      step_update(s, sum);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int q = warp; q < a.BL; q += blockDim.x / 32) {
+      double sum = warp_sum_partials(a.red.part + (long long)q * gridDim.x, gridDim.x, 1);
+      if (lane == 0 && !a.sc[q].done) step_update(a.sc[q], sum);
     }
+    __syncthreads();
     if (threadIdx.x == 0) *a.red.ticket = 0u;
   }
 }
@@ -183,14 +181,13 @@ __global__ void __launch_bounds__(256) k_jac_a(JacArgs<T> a) {
   if (last_block(a.red.ticket)) {
     residual_decision(a.sc, a.BL, a.ctl, a.after_replace);
     __syncthreads();
-    for (int q = threadIdx.x; q < a.BL; q += blockDim.x) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int q = warp; q < a.BL; q += blockDim.x / 32) {
+      double sum = warp_sum_partials(a.red.part + (long long)q * gridDim.x, gridDim.x, 1);
       CgScal& t = a.sc[q];
-      if (t.done || t.need_replace) continue;
-      double sum = 0.0;
-      const double* pp = a.red.part + (long long)q * gridDim.x;
-      for (int x = 0; x < (int)gridDim.x; ++x) sum += ld_cg(pp + x);
-      direction_update(t, sum, 0.0, 0);
+      if (lane == 0 && !t.done && !t.need_replace) direction_update(t, sum, 0.0, 0);
     }
+    __syncthreads();
     if (threadIdx.x == 0) *a.red.ticket = 0u;
   }
 }
@@ -262,10 +259,9 @@ __global__ void k_zero_mean(double* u, const double* part, int nparts, int c, lo
   const int bl = blockIdx.y, comp = blockIdx.z;
   const long long f = (long long)bl * c + comp;
   __shared__ double mean;
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int x = 0; x < nparts; ++x) s += part[f * nparts + x];
-    mean = s / (double)n;
+  if (threadIdx.x < 32) {
+    double s = warp_sum_partials(part + f * nparts, nparts, 1);
+    if (threadIdx.x == 0) mean = s / (double)n;
   }
   __syncthreads();
   double* uf = u + f * n;
@@ -305,11 +301,11 @@ __global__ void __launch_bounds__(256) k_average(AvgArgs a) {
 
 __global__ void k_average_finish(double* out, const double* part, int nparts, int B, int L, int dim, double inv_n) {
   int b = blockIdx.x;
-  for (int q = threadIdx.x; q < L * dim; q += blockDim.x) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int q = warp; q < L * dim; q += blockDim.x / 32) {
     int l = q / dim, i = q % dim;
-    double s = 0.0;
-    for (int x = 0; x < nparts; ++x) s += part[((long long)b * nparts + x) * (8 * 6) + q];
-    out[((long long)b * dim + i) * L + l] = s * inv_n;
+    double s = warp_sum_partials(part + (long long)b * nparts * 48 + q, nparts, 48);
+    if (lane == 0) out[((long long)b * dim + i) * L + l] = s * inv_n;
   }
 }
 
@@ -341,10 +337,10 @@ __global__ void __launch_bounds__(128) k_sens(AvgArgs a) {
 
 __global__ void k_sens_finish(double* out, const double* part, int nparts, int tot, double inv_n) {
   int b = blockIdx.x;
-  for (int q = threadIdx.x; q < tot; q += blockDim.x) {
-    double s = 0.0;
-    for (int x = 0; x < nparts; ++x) s += part[((long long)b * nparts + x) * tot + q];
-    out[(long long)b * tot + q] = s * inv_n;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int q = warp; q < tot; q += blockDim.x / 32) {
+    double s = warp_sum_partials(part + (long long)b * nparts * tot + q, nparts, tot);
+    if (lane == 0) out[(long long)b * tot + q] = s * inv_n;
   }
 }
 
@@ -423,7 +419,7 @@ cudaError_t launch_average(const AvgArgs& a, int B, double* out, cudaStream_t s)
   else k_average<3><<<grid, 256, 0, s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_average_finish<<<B, 64, 0, s>>>(out, a.part, grid.x, B, a.L, a.c == 1 ? 3 : 6, 1.0 / (double)a.g.n);
+  k_average_finish<<<B, 256, 0, s>>>(out, a.part, grid.x, B, a.L, a.c == 1 ? 3 : 6, 1.0 / (double)a.g.n);
   return cudaGetLastError();
 }
 cudaError_t launch_sens(const AvgArgs& a, int B, double* out, cudaStream_t s) {
@@ -435,7 +431,7 @@ cudaError_t launch_sens(const AvgArgs& a, int B, double* out, cudaStream_t s) {
   else k_sens<3><<<dim3(grid.x * 2, B), 128, smem, s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_sens_finish<<<B, 128, 0, s>>>(out, a.part, grid.x * 2, tot, 1.0 / (double)a.g.n);
+  k_sens_finish<<<B, 256, 0, s>>>(out, a.part, grid.x * 2, tot, 1.0 / (double)a.g.n);
   return cudaGetLastError();
 }
 int sens_blocks_x(const Grid& g) { return node_grid(g, 1).x * 2; }
