@@ -32,6 +32,7 @@ bool factor_plan(int N, FftPlan* p) {
   p->N = N;
   p->nst = 0;
   int m = N;
+  while (m % 8 == 0) { p->radix[p->nst++] = 8; m /= 8; }
   while (m % 4 == 0) { p->radix[p->nst++] = 4; m /= 4; }
   while (m % 2 == 0) { p->radix[p->nst++] = 2; m /= 2; }
   while (m % 3 == 0) { p->radix[p->nst++] = 3; m /= 3; }
@@ -461,6 +462,7 @@ static int ensure_workspace(unocg_ctx* ctx, int precision, int precond) {
   need = std::max(need, (size_t)BL * line_blocks_x(ctx->g, ctx->c, 8) * 2);
   need = std::max(need, (size_t)BL * line_blocks_x(ctx->g, ctx->c, 16) * 2);
   need = std::max(need, (size_t)BL * node_blocks_x(ctx->g));
+  need = std::max(need, (size_t)BL * ku_blocks_x(ctx->g, ctx->c));
   need = std::max(need, (size_t)BL * jac_blocks_x((long long)ctx->c * n, BL));
   need = std::max(need, (size_t)BL * ctx->c * 1184);
   need = std::max(need, (size_t)ctx->B * node_blocks_x(ctx->g) * 48);

@@ -62,16 +62,46 @@ template <int DIR, typename C> __device__ __forceinline__ void dft5(C* v) {
   v[3] = csub(a2, m2);
 }
 
+// radix 8 = two radix-4 DFTs of the even and odd samples, combined with W_8^k
+template <int DIR, typename C> __device__ __forceinline__ void dft8(C* v) {
+  using T = decltype(v[0].x);
+  const T s = (T)0.70710678118654752440;
+  C a[4] = {v[0], v[2], v[4], v[6]};
+  C b[4] = {v[1], v[3], v[5], v[7]};
+  dft4<DIR>(a);
+  dft4<DIR>(b);
+  // W_8^1 = (1 - i)/sqrt2 (forward), W_8^2 = -i, W_8^3 = (-1 - i)/sqrt2
+  C b1 = mk<T>(s * (b[1].x + b[1].y), s * (b[1].y - b[1].x));
+  if (DIR > 0) b1 = mk<T>(s * (b[1].x - b[1].y), s * (b[1].y + b[1].x));
+  C b2 = cmul_mi<DIR>(b[2]);
+  C b3 = mk<T>(s * (-b[3].x + b[3].y), s * (-b[3].y - b[3].x));
+  if (DIR > 0) b3 = mk<T>(s * (-b[3].x - b[3].y), s * (-b[3].y + b[3].x));
+  v[0] = cadd(a[0], b[0]);
+  v[4] = csub(a[0], b[0]);
+  v[1] = cadd(a[1], b1);
+  v[5] = csub(a[1], b1);
+  v[2] = cadd(a[2], b2);
+  v[6] = csub(a[2], b2);
+  v[3] = cadd(a[3], b3);
+  v[7] = csub(a[3], b3);
+}
+
 template <int DIR, int R, typename C> __device__ __forceinline__ void dftR(C* v) {
   if (R == 2) dft2<DIR>(v);
   else if (R == 3) dft3<DIR>(v);
   else if (R == 4) dft4<DIR>(v);
-  else dft5<DIR>(v);
+  else if (R == 5) dft5<DIR>(v);
+  else dft8<DIR>(v);
 }
+
+// floor(x / d) for 0 <= x < 2^20 and 1 <= d < 2^12 through a float reciprocal: the relative
+// error of (x + 1/2) * (1/d) is below 2^-22, far inside the 1/(2d) margin of the true quotient.
+__device__ __forceinline__ int fdiv(int x, float rd) { return (int)(((float)x + 0.5f) * rd); }
 
 // ---------------------------------------------------------------- one Stockham stage
 // Lines: element (line, idx) at buf[line*ls + idx*es].  Work item = (line, j), j < N/R, with
-// the line index fastest across threads.  Out of place: reads src, writes dst.
+// the line index fastest across threads (conflict-free for both row and column layouts).
+// Out of place: reads src, writes dst.  `tw` holds W_N^m, m < N (shared memory).
 template <typename T, int DIR, int R>
 __device__ __forceinline__ void fft_stage(const cplx<T>* __restrict__ src, cplx<T>* __restrict__ dst,
                                           int nlines, int ls, int es, int N, int Ns,
@@ -80,13 +110,16 @@ __device__ __forceinline__ void fft_stage(const cplx<T>* __restrict__ src, cplx<
   const int NR = N / R;
   const int total = nlines * NR;
   const int stride = N / (Ns * R);
+  const float rl = 1.0f / (float)nlines, rs = 1.0f / (float)Ns;
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int line = idx % nlines, j = idx / nlines;
+    const int j = fdiv(idx, rl);
+    const int line = idx - j * nlines;
     const C* b = src + line * ls;
     C v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = b[(j + r * NR) * es];
-    const int k = j % Ns;
+    const int q = fdiv(j, rs);
+    const int k = j - q * Ns;
     if (Ns > 1) {
 #pragma unroll
       for (int r = 1; r < R; ++r) {
@@ -96,7 +129,7 @@ __device__ __forceinline__ void fft_stage(const cplx<T>* __restrict__ src, cplx<
       }
     }
     dftR<DIR, R>(v);
-    const int base = (j / Ns) * Ns * R + k;
+    const int base = q * Ns * R + k;
     C* o = dst + line * ls;
 #pragma unroll
     for (int r = 0; r < R; ++r) o[(base + r * Ns) * es] = v[r];
@@ -116,7 +149,8 @@ __device__ cplx<T>* fft_lines(cplx<T>* a, cplx<T>* b, int nlines, int ls, int es
       case 2: fft_stage<T, DIR, 2>(a, b, nlines, ls, es, pl.N, Ns, tw); break;
       case 3: fft_stage<T, DIR, 3>(a, b, nlines, ls, es, pl.N, Ns, tw); break;
       case 4: fft_stage<T, DIR, 4>(a, b, nlines, ls, es, pl.N, Ns, tw); break;
-      default: fft_stage<T, DIR, 5>(a, b, nlines, ls, es, pl.N, Ns, tw); break;
+      case 5: fft_stage<T, DIR, 5>(a, b, nlines, ls, es, pl.N, Ns, tw); break;
+      default: fft_stage<T, DIR, 8>(a, b, nlines, ls, es, pl.N, Ns, tw); break;
     }
     Ns *= R;
     cplx<T>* t = a;
@@ -124,6 +158,13 @@ __device__ cplx<T>* fft_lines(cplx<T>* a, cplx<T>* b, int nlines, int ls, int es
     b = t;
   }
   return a;
+}
+
+// Copy a twiddle table W_N^m (m < N) from global to shared memory.
+template <typename T>
+__device__ __forceinline__ void load_tw(cplx<T>* dst, const void* src, int N) {
+  const cplx<T>* s = (const cplx<T>*)src;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) dst[i] = s[i];
 }
 
 // ---------------------------------------------------------------- real <-> half-complex rows
@@ -135,8 +176,9 @@ __device__ void r2c_post(cplx<T>* buf, int nrows, int P, int Nh, const cplx<T>* 
   using C = cplx<T>;
   const int npairs = Nh / 2 + 1;
   const T half = (T)0.5;
+  const float rr = 1.0f / (float)nrows;
   for (int idx = threadIdx.x; idx < nrows * npairs; idx += blockDim.x) {
-    int row = idx % nrows, k = idx / nrows;
+    const int k = fdiv(idx, rr), row = idx - k * nrows;
     C* b = buf + row * P;
     if (k == 0) {
       C z = b[0];
@@ -168,8 +210,9 @@ template <typename T>
 __device__ void c2r_pre(cplx<T>* buf, int nrows, int P, int Nh, const cplx<T>* __restrict__ twN) {
   using C = cplx<T>;
   const int npairs = Nh / 2 + 1;
+  const float rr = 1.0f / (float)nrows;
   for (int idx = threadIdx.x; idx < nrows * npairs; idx += blockDim.x) {
-    int row = idx % nrows, k = idx / nrows;
+    const int k = fdiv(idx, rr), row = idx - k * nrows;
     C* b = buf + row * P;
     if (k == 0) {
       T x0 = b[0].x, xn = b[Nh].x;

@@ -27,10 +27,17 @@ __global__ void __launch_bounds__(NTH) k_plane_fwd(PlaneFwdArgs<T> a) {
   __shared__ double red_sh[32];
   const Grid& g = a.g;
   const int n3h = g.n3h, Nh = g.n3 / 2, P = pitch_of(n3h);
+  const float rNh = 1.0f / (float)Nh, rn3h = 1.0f / (float)n3h;
   const int plane = blockIdx.x;  // comp * n1 + i1
   const int bl = blockIdx.y;
   const int comp = plane / g.n1, i1 = plane % g.n1;
   const long long field = (long long)bl * a.c + comp;
+  C* tw3h = buf + 2 * g.n2 * P;
+  C* tw2 = tw3h + Nh;
+  C* tw3 = tw2 + g.n2;
+  load_tw<T>(tw3h, a.ft.tw3h, Nh);
+  load_tw<T>(tw2, a.ft.tw2, g.n2);
+  load_tw<T>(tw3, a.ft.tw3, g.n3);
   bool active = true;
   double alpha = 0.0;
   if (!a.standalone) {
@@ -44,7 +51,7 @@ __global__ void __launch_bounds__(NTH) k_plane_fwd(PlaneFwdArgs<T> a) {
     if (a.standalone) {
       const C* src = reinterpret_cast<const C*>(a.src + base);
       for (int idx = threadIdx.x; idx < npair; idx += NTH) {
-        int i2 = idx / Nh, m = idx - i2 * Nh;
+        int i2 = fdiv(idx, rNh), m = idx - i2 * Nh;
         buf[i2 * P + m] = src[idx];
       }
     } else {
@@ -52,7 +59,7 @@ __global__ void __launch_bounds__(NTH) k_plane_fwd(PlaneFwdArgs<T> a) {
       const C* p = reinterpret_cast<const C*>(a.p + base);
       const T al = (T)alpha;
       for (int idx = threadIdx.x; idx < npair; idx += NTH) {
-        int i2 = idx / Nh, m = idx - i2 * Nh;
+        int i2 = fdiv(idx, rNh), m = idx - i2 * Nh;
         C v = r[idx];
         if (alpha != 0.0) {
           C q = p[idx];
@@ -67,14 +74,14 @@ __global__ void __launch_bounds__(NTH) k_plane_fwd(PlaneFwdArgs<T> a) {
     __syncthreads();
     // rows: half-length complex FFT, then split into the half spectrum of the real row
     C* alt = buf + g.n2 * P;
-    C* res = fft_lines<T, -1>(buf, alt, g.n2, P, 1, a.ft.p3h, (const C*)a.ft.tw3h);
-    r2c_post<T>(res, g.n2, P, Nh, (const C*)a.ft.tw3);
+    C* res = fft_lines<T, -1>(buf, alt, g.n2, P, 1, a.ft.p3h, tw3h);
+    r2c_post<T>(res, g.n2, P, Nh, tw3);
     // columns (axis 2)
-    res = fft_lines<T, -1>(res, res == buf ? alt : buf, n3h, 1, P, a.ft.p2, (const C*)a.ft.tw2);
+    res = fft_lines<T, -1>(res, res == buf ? alt : buf, n3h, 1, P, a.ft.p2, tw2);
     C* out = a.hat + (field * g.n1 + i1) * (long long)g.n2 * n3h;
     const int nout = g.n2 * n3h;
     for (int idx = threadIdx.x; idx < nout; idx += NTH) {
-      int k2 = idx / n3h, k3 = idx - k2 * n3h;
+      int k2 = fdiv(idx, rn3h), k3 = idx - k2 * n3h;
       out[idx] = res[k2 * P + k3];
     }
   }
@@ -108,10 +115,13 @@ __global__ void __launch_bounds__(NTH) k_line(LineArgs<T, QT> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   const int TB = a.tb;
+  const float rTB = 1.0f / (float)TB, rn3h = 1.0f / (float)a.g.n3h;
   const size_t SZ = (size_t)a.g.n1 * CC * TB;
   C* alt = buf + SZ;
   C* gbuf = buf + 2 * SZ;  // backward: spectra of the gradient
   C* galt = buf + 3 * SZ;
+  C* tw1 = buf + (MODE == 2 ? 4 : 2) * SZ;
+  load_tw<T>(tw1, a.ft.tw1, a.g.n1);
   __shared__ double red_sh[32];
   const Grid& g = a.g;
   const int n1 = g.n1;
@@ -125,7 +135,7 @@ __global__ void __launch_bounds__(NTH) k_line(LineArgs<T, QT> a) {
   if (active) {
     const long long fbase = (long long)bl * CC * n1 * M;
     for (int idx = threadIdx.x; idx < n1 * LW; idx += NTH) {
-      int t = idx % TB, rest = idx / TB;
+      int rest = fdiv(idx, rTB), t = idx - rest * TB;
       int comp = rest % CC, k1 = rest / CC;
       C v = mk<T>((T)0, (T)0), gv = v;
       if (t < nt) {
@@ -134,7 +144,7 @@ __global__ void __launch_bounds__(NTH) k_line(LineArgs<T, QT> a) {
         if (MODE == 2) gv = a.ghat[gi];
         if (MODE == 0 && a.flexible) {
           C so = a.shat[gi];
-          int k3 = (pos0 + t) % g.n3h;
+          int k3 = (pos0 + t) - fdiv(pos0 + t, rn3h) * g.n3h;
           double w = (k3 == 0 || 2 * k3 == g.n3) ? 1.0 : 2.0;
           rso += w * ((double)v.x * (double)so.x + (double)v.y * (double)so.y);
         }
@@ -143,16 +153,16 @@ __global__ void __launch_bounds__(NTH) k_line(LineArgs<T, QT> a) {
       if (MODE == 2) gbuf[k1 * LW + comp * TB + t] = gv;
     }
     __syncthreads();
-    C* res = fft_lines<T, -1>(buf, alt, LW, 1, LW, a.ft.p1, (const C*)a.ft.tw1);
+    C* res = fft_lines<T, -1>(buf, alt, LW, 1, LW, a.ft.p1, tw1);
     C* gres = gbuf;
-    if (MODE == 2) gres = fft_lines<T, -1>(gbuf, galt, LW, 1, LW, a.ft.p1, (const C*)a.ft.tw1);
+    if (MODE == 2) gres = fft_lines<T, -1>(gbuf, galt, LW, 1, LW, a.ft.p1, tw1);
     const long long qb = (long long)(bl / a.L) * a.q_inst_stride;
     const T sc = (T)a.scale;
     for (int idx = threadIdx.x; idx < n1 * TB; idx += NTH) {
-      int t = idx % TB, k1 = idx / TB;
+      int k1 = fdiv(idx, rTB), t = idx - k1 * TB;
       if (t >= nt) continue;
       int pos = pos0 + t;
-      int k3 = pos % g.n3h;
+      int k3 = pos - fdiv(pos, rn3h) * g.n3h;
       double w = (k3 == 0 || 2 * k3 == g.n3) ? 1.0 : 2.0;
       const long long qi = qb + ((long long)k1 * M + pos) * (CC == 1 ? 1 : 6);
       C* bp = res + k1 * LW + t;
@@ -204,9 +214,9 @@ __global__ void __launch_bounds__(NTH) k_line(LineArgs<T, QT> a) {
     __syncthreads();
     C* ob = (MODE == 2) ? gres : res;
     C* oalt = (MODE == 2) ? (gres == gbuf ? galt : gbuf) : (res == buf ? alt : buf);
-    ob = fft_lines<T, +1>(ob, oalt, LW, 1, LW, a.ft.p1, (const C*)a.ft.tw1);
+    ob = fft_lines<T, +1>(ob, oalt, LW, 1, LW, a.ft.p1, tw1);
     for (int idx = threadIdx.x; idx < n1 * LW; idx += NTH) {
-      int t = idx % TB, rest = idx / TB;
+      int rest = fdiv(idx, rTB), t = idx - rest * TB;
       int comp = rest % CC, k1 = rest / CC;
       if (t < nt) {
         long long gi = fbase + ((long long)comp * n1 + k1) * M + pos0 + t;
@@ -243,28 +253,35 @@ __global__ void __launch_bounds__(NTH) k_plane_inv(PlaneInvArgs<T> a) {
   C* buf = reinterpret_cast<C*>(smem_raw);
   const Grid& g = a.g;
   const int n3h = g.n3h, Nh = g.n3 / 2, P = pitch_of(n3h);
+  const float rNh = 1.0f / (float)Nh, rn3h = 1.0f / (float)n3h;
   const int plane = blockIdx.x;
   const int bl = blockIdx.y;
   const int comp = plane / g.n1, i1 = plane % g.n1;
   const long long field = (long long)bl * a.c + comp;
   if (!a.standalone && a.sc[bl].done) return;
+  C* tw3h = buf + 2 * g.n2 * P;
+  C* tw2 = tw3h + Nh;
+  C* tw3 = tw2 + g.n2;
+  load_tw<T>(tw3h, a.ft.tw3h, Nh);
+  load_tw<T>(tw2, a.ft.tw2, g.n2);
+  load_tw<T>(tw3, a.ft.tw3, g.n3);
   const C* in = a.shat + (field * g.n1 + i1) * (long long)g.n2 * n3h;
   const int nin = g.n2 * n3h;
   for (int idx = threadIdx.x; idx < nin; idx += NTH) {
-    int k2 = idx / n3h, k3 = idx - k2 * n3h;
+    int k2 = fdiv(idx, rn3h), k3 = idx - k2 * n3h;
     buf[k2 * P + k3] = in[idx];
   }
   __syncthreads();
   C* alt = buf + g.n2 * P;
-  C* res = fft_lines<T, +1>(buf, alt, n3h, 1, P, a.ft.p2, (const C*)a.ft.tw2);
-  c2r_pre<T>(res, g.n2, P, Nh, (const C*)a.ft.tw3);
-  res = fft_lines<T, +1>(res, res == buf ? alt : buf, g.n2, P, 1, a.ft.p3h, (const C*)a.ft.tw3h);
+  C* res = fft_lines<T, +1>(buf, alt, n3h, 1, P, a.ft.p2, tw2);
+  c2r_pre<T>(res, g.n2, P, Nh, tw3);
+  res = fft_lines<T, +1>(res, res == buf ? alt : buf, g.n2, P, 1, a.ft.p3h, tw3h);
   const long long base = (field * g.n1 + i1) * (long long)g.n2 * g.n3;
   const int npair = g.n2 * Nh;
   if (a.standalone) {
     C* dst = reinterpret_cast<C*>(a.dst + base);
     for (int idx = threadIdx.x; idx < npair; idx += NTH) {
-      int i2 = idx / Nh, m = idx - i2 * Nh;
+      int i2 = fdiv(idx, rNh), m = idx - i2 * Nh;
       dst[idx] = res[i2 * P + m];
     }
     return;
@@ -273,7 +290,7 @@ __global__ void __launch_bounds__(NTH) k_plane_inv(PlaneInvArgs<T> a) {
   C* d = reinterpret_cast<C*>(a.d + base);
   C* u = reinterpret_cast<C*>(a.u + base);
   for (int idx = threadIdx.x; idx < npair; idx += NTH) {
-    int i2 = idx / Nh, m = idx - i2 * Nh;
+    int i2 = fdiv(idx, rNh), m = idx - i2 * Nh;
     C s = res[i2 * P + m];
     C dold = d[idx];
     C uu = u[idx];
@@ -287,7 +304,8 @@ __global__ void __launch_bounds__(NTH) k_plane_inv(PlaneInvArgs<T> a) {
 // ============================================================================ launchers
 static inline int plane_threads(const Grid& g) { return (long long)g.n2 * g.n3h > 4096 ? 512 : 256; }
 static inline size_t plane_smem(const Grid& g, int elem_bytes) {
-  return 2 * (size_t)g.n2 * pitch_of(g.n3h) * elem_bytes;
+  // two plane buffers + the twiddle tables of N3/2, N2 and N3
+  return (2 * (size_t)g.n2 * pitch_of(g.n3h) + g.n3 / 2 + g.n2 + g.n3) * elem_bytes;
 }
 
 #ifdef UNOCG_FFT_HOST_DEFS
@@ -340,7 +358,7 @@ template <typename T, typename QT, int CC, int MODE>
 static cudaError_t launch_line_cc(LineArgs<T, QT> a, cudaStream_t s) {
   const int eb = sizeof(cplx<T>);
   a.tb = line_tb(CC, eb);
-  size_t smem = (size_t)a.g.n1 * CC * a.tb * eb * (MODE == 2 ? 4 : 2);
+  size_t smem = ((size_t)a.g.n1 * CC * a.tb * (MODE == 2 ? 4 : 2) + a.g.n1) * eb;
   dim3 grid(line_blocks_x(a.g, CC, eb), a.BL);
   return launch_k(k_line<T, QT, CC, 256, MODE>, grid, 256, smem, a, s);
 }

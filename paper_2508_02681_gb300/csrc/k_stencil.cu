@@ -16,6 +16,117 @@
 namespace unocg {
 
 // ============================================================================ K d
+// Thermal: every thread marches along i1 over KU_CZ consecutive nodes of one (i2, i3) column,
+// keeping the 3x3 neighbourhoods of the planes i1-1, i1, i1+1 and the conductivities of the
+// element planes i1-1, i1 in registers: 9 loads of d and 4 phase labels per node.
+constexpr int KU_CZ = 8;
+
+__device__ __forceinline__ bool tile_column(const Grid& g, int cz, int& i1, int& i2, int& i3) {
+  const int nt3 = (g.n3 + 31) >> 5, nt2 = (g.n2 + 7) >> 3;
+  int bx = blockIdx.x;
+  const int b3 = bx % nt3;
+  bx /= nt3;
+  const int b2 = bx % nt2;
+  const int b1 = bx / nt2;
+  i3 = b3 * 32 + (threadIdx.x & 31);
+  i2 = b2 * 8 + (threadIdx.x >> 5);
+  i1 = b1 * cz;
+  return i3 < g.n3 && i2 < g.n2 && i1 < g.n1;
+}
+
+template <typename T>
+__device__ __forceinline__ void ku_thermal_column(const T* __restrict__ d, T* __restrict__ p,
+                                                  const uint8_t* __restrict__ ph, const T* mt,
+                                                  const Grid& g, int i1, int i2, int i3, int cz,
+                                                  double& dp) {
+  const int S = g.n2 * g.n3;
+  const int c2[3] = {i2 ? i2 - 1 : g.n2 - 1, i2, (i2 + 1 == g.n2) ? 0 : i2 + 1};
+  const int c3[3] = {i3 ? i3 - 1 : g.n3 - 1, i3, (i3 + 1 == g.n3) ? 0 : i3 + 1};
+  int off[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) off[a][b] = c2[a] * g.n3 + c3[b];
+  // d planes: dm (i1-1), dc (i1), dn (i1+1); element conductivities km (plane i1-1), kc (plane i1)
+  T dm[3][3], dc[3][3], dn[3][3], km[2][2], kc[2][2];
+  int zm = (i1 ? i1 - 1 : g.n1 - 1) * S, zc = i1 * S;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      dm[a][b] = __ldg(d + zm + off[a][b]);
+      dc[a][b] = __ldg(d + zc + off[a][b]);
+    }
+  // element (e1, i2 - o2, i3 - o3) sits at off[1 - o2][1 - o3] of element plane e1
+#pragma unroll
+  for (int o2 = 0; o2 < 2; ++o2)
+#pragma unroll
+    for (int o3 = 0; o3 < 2; ++o3) km[o2][o3] = mt[2 * __ldg(ph + zm + off[1 - o2][1 - o3])];
+  const T hf = (T)(g.h / 12.0);
+  const int zend = min(i1 + cz, g.n1);
+  for (int z = i1; z < zend; ++z) {
+    const int zn = ((z + 1 == g.n1) ? 0 : z + 1) * S;
+    zc = z * S;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) dn[a][b] = __ldg(d + zn + off[a][b]);
+#pragma unroll
+    for (int o2 = 0; o2 < 2; ++o2)
+#pragma unroll
+      for (int o3 = 0; o3 < 2; ++o3) kc[o2][o3] = mt[2 * __ldg(ph + zc + off[1 - o2][1 - o3])];
+    // k[o1][o2][o3]: o1 = 0 -> element plane z (kc), o1 = 1 -> plane z-1 (km)
+    T sk = (kc[0][0] + kc[0][1]) + (kc[1][0] + kc[1][1]) + (km[0][0] + km[0][1]) + (km[1][0] + km[1][1]);
+    T acc = (T)4 * sk * dc[1][1];
+    // edge-diagonal neighbours in the plane (delta1 = 0): elements o1 in {0,1}
+#pragma unroll
+    for (int s2 = 0; s2 < 3; s2 += 2)
+#pragma unroll
+      for (int s3 = 0; s3 < 3; s3 += 2) {
+        const int o2 = s2 == 0, o3 = s3 == 0;
+        acc -= (kc[o2][o3] + km[o2][o3]) * dc[s2][s3];
+      }
+    // delta2 = 0: elements o2 in {0,1}, fixed o1, o3
+#pragma unroll
+    for (int s3 = 0; s3 < 3; s3 += 2) {
+      const int o3 = s3 == 0;
+      acc -= (kc[0][o3] + kc[1][o3]) * dn[1][s3];
+      acc -= (km[0][o3] + km[1][o3]) * dm[1][s3];
+    }
+    // delta3 = 0: elements o3 in {0,1}, fixed o1, o2
+#pragma unroll
+    for (int s2 = 0; s2 < 3; s2 += 2) {
+      const int o2 = s2 == 0;
+      acc -= (kc[o2][0] + kc[o2][1]) * dn[s2][1];
+      acc -= (km[o2][0] + km[o2][1]) * dm[s2][1];
+    }
+    // corners: one element each
+#pragma unroll
+    for (int s2 = 0; s2 < 3; s2 += 2)
+#pragma unroll
+      for (int s3 = 0; s3 < 3; s3 += 2) {
+        const int o2 = s2 == 0, o3 = s3 == 0;
+        acc -= kc[o2][o3] * dn[s2][s3];
+        acc -= km[o2][o3] * dm[s2][s3];
+      }
+    const T out = acc * hf;
+    p[zc + off[1][1]] = out;
+    dp += (double)(out * dc[1][1]);
+    // shift the window
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        dm[a][b] = dc[a][b];
+        dc[a][b] = dn[a][b];
+      }
+#pragma unroll
+    for (int o2 = 0; o2 < 2; ++o2)
+#pragma unroll
+      for (int o3 = 0; o3 < 2; ++o3) km[o2][o3] = kc[o2][o3];
+  }
+}
+
 template <typename T, int CC>
 __global__ void __launch_bounds__(256) k_ku(StencilArgs<T> a) {
   __shared__ T mt[2 * 256];
@@ -27,19 +138,24 @@ __global__ void __launch_bounds__(256) k_ku(StencilArgs<T> a) {
   __syncthreads();
   bool active = a.standalone || !a.sc[bl].done;
   double dp = 0.0;
-  int i1, i2, i3;
-  if (active && tile_node(g, i1, i2, i3)) {
-    const long long n = g.n;
-    const uint8_t* ph = a.phase + (long long)b * n;
-    const T* d = a.d + (long long)bl * CC * n;
-    T* p = a.p + (long long)bl * CC * n;
-    const long long node = ((long long)i1 * g.n2 + i2) * g.n3 + i3;
-    T out[CC];
-    node_Ku<T, CC>(d, ph, mt, g, i1, i2, i3, out);
+  const long long n = g.n;
+  const uint8_t* ph = a.phase + (long long)b * n;
+  const T* d = a.d + (long long)bl * CC * n;
+  T* p = a.p + (long long)bl * CC * n;
+  if (CC == 1) {
+    int i1, i2, i3;
+    if (active && tile_column(g, KU_CZ, i1, i2, i3)) ku_thermal_column<T>(d, p, ph, mt, g, i1, i2, i3, KU_CZ, dp);
+  } else {
+    int i1, i2, i3;
+    if (active && tile_node(g, i1, i2, i3)) {
+      const long long node = ((long long)i1 * g.n2 + i2) * g.n3 + i3;
+      T out[CC];
+      node_Ku<T, CC>(d, ph, mt, g, i1, i2, i3, out);
 #pragma unroll
-    for (int i = 0; i < CC; ++i) {
-      p[i * n + node] = out[i];
-      dp += (double)out[i] * (double)d[i * n + node];
+      for (int i = 0; i < CC; ++i) {
+        p[i * n + node] = out[i];
+        dp += (double)(out[i] * d[i * n + node]);
+      }
     }
   }
   if (a.standalone) return;
@@ -362,8 +478,15 @@ static dim3 node_grid(const Grid& g, int y) {
 }
 int node_blocks_x(const Grid& g) { return node_grid(g, 1).x; }
 
+static dim3 ku_grid(const Grid& g, int c, int y) {
+  if (c != 1) return node_grid(g, y);
+  int tx = (g.n3 + 31) / 32, ty = (g.n2 + 7) / 8, tz = (g.n1 + KU_CZ - 1) / KU_CZ;
+  return dim3(tx * ty * tz, y);
+}
+int ku_blocks_x(const Grid& g, int c) { return ku_grid(g, c, 1).x; }
+
 template <typename T> cudaError_t launch_ku(const StencilArgs<T>& a, cudaStream_t s) {
-  dim3 grid = node_grid(a.g, a.BL);
+  dim3 grid = ku_grid(a.g, a.c, a.BL);
   if (a.c == 1) k_ku<T, 1><<<grid, 256, 0, s>>>(a);
   else k_ku<T, 3><<<grid, 256, 0, s>>>(a);
   return cudaGetLastError();

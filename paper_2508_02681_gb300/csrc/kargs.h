@@ -144,6 +144,7 @@ cudaError_t launch_average(const AvgArgs& a, int B, double* out, cudaStream_t s)
 cudaError_t launch_sens(const AvgArgs& a, int B, double* out, cudaStream_t s);
 cudaError_t launch_interleave(const double* src, double* dst, int c, long long n, cudaStream_t s);
 int node_blocks_x(const Grid& g);
+int ku_blocks_x(const Grid& g, int c);
 int jac_blocks_x(long long m, int BL);
 int sens_blocks_x(const Grid& g);
 
