@@ -238,6 +238,9 @@ def main():
     C_fp64 = h.effective_tensor()[0]
     t_jac, info_jac = timed(variants["fp64_jacobi"], max(2, min(args.steps, 3)), 1)
     C_jac = h.effective_tensor()[0]
+    graph_opts = api.make_opts(tol=TOL, max_iter=2000, precond=_lib.PRECOND_UNO, precision=_lib.MIXED,
+                               replace_every=50, flexible=1, use_graph=1)
+    t_graph, _ = timed(graph_opts, side_steps, 1)
 
     # per-kernel event timing of the mixed iteration (same kernels and launch shapes)
     k_ms = api.unocg_profile_iteration(h.ctx, variants["mixed_uno"], reps=10)
@@ -292,7 +295,8 @@ def main():
         "true_rel_res": {"mixed_uno": float(np.max(info_mixed.true_rel_res)),
                          "fp64_uno": float(np.max(info_fp64.true_rel_res)),
                          "fp64_jacobi": float(np.max(info_jac.true_rel_res))},
-        "fp64_uno_ms": t_fp64, "fp64_jacobi_ms": t_jac,
+        "fp64_uno_ms": t_fp64, "fp64_jacobi_ms": t_jac, "mixed_uno_graph_loop_ms": t_graph,
+        "loop_driver": "persistent cooperative kernel" if variants["mixed_uno"].use_graph in (2, 3) else "graph",
         "speedup_mixed_vs_fp64_uno": t_fp64 / t_mixed, "speedup_mixed_vs_fp64_jacobi": t_jac / t_mixed,
         "iters_per_s_mixed": float(info_mixed.c.max_iters) / (t_mixed * 1e-3),
         "C_eff_rel_diff_mixed_vs_fp64": float(np.max(np.abs(C_mixed - C_fp64)) / np.max(np.abs(C_fp64))),

@@ -83,8 +83,11 @@ typedef struct {
   int precision;     /* UNOCG_FP64 or UNOCG_MIXED                                           */
   int replace_every; /* MIXED: true-residual replacement period (iterations), e.g. 50      */
   int flexible;      /* 1: Polak-Ribiere coefficient (flexible CG), 0: Algorithm 1's        */
-  int use_graph;     /* 1: whole loop in one CUDA graph with device-side control (default);
-                        0: host-driven loop, one residual check per iteration (debugging)  */
+  int use_graph;     /* loop driver: 0 host-driven loop, one residual check per iteration;
+                        1 one CUDA graph with conditional nodes (device-side control);
+                        2 one persistent cooperative kernel with grid barriers (UNO only,
+                          problems whose phase buffers fit in shared memory);
+                        3 automatic: 2 for small problems, else 1                            */
 } unocg_solve_opts;
 
 typedef struct {
@@ -103,6 +106,11 @@ typedef struct {
 int unocg_create(unocg_ctx** out, int physics, int batch, int n1, int n2, int n3, double L0);
 void unocg_destroy(unocg_ctx* ctx);
 const char* unocg_last_error(const unocg_ctx* ctx);
+
+/* Upper bound of any device-side wait of this context (the grid barrier of the persistent
+   loop), in seconds (default 1).  A wait that expires makes every block of the launch return
+   and the solve report UNOCG_ERR_DEVICE_TIMEOUT; the context stays usable.                 */
+int unocg_set_wait_limit(unocg_ctx* ctx, double seconds);
 
 /* Use `stream` (a cudaStream_t) for all work of this context; NULL = the context's own.    */
 int unocg_set_stream(unocg_ctx* ctx, void* stream);

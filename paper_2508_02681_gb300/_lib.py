@@ -60,6 +60,7 @@ SIGNATURES = {
     "unocg_destroy": (None, [_vp]),
     "unocg_last_error": (C.c_char_p, [_vp]),
     "unocg_set_stream": (_i, [_vp, _vp]),
+    "unocg_set_wait_limit": (_i, [_vp, _d]),
     "unocg_set_microstructure": (_i, [_vp, _vp, _i]),
     "unocg_set_microstructure_dev": (_i, [_vp, _vp, _i, _vp]),
     "unocg_set_phase_properties": (_i, [_vp, _vp]),

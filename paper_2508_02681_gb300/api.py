@@ -49,6 +49,10 @@ def unocg_destroy(ctx):
     _lib.load().unocg_destroy(ctx)
 
 
+def unocg_set_wait_limit(ctx, seconds: float):
+    _check(ctx, _lib.load().unocg_set_wait_limit(ctx, seconds))
+
+
 def unocg_set_stream(ctx, stream=None):
     _check(ctx, _lib.load().unocg_set_stream(ctx, _stream(stream) if stream is not None else None))
 
@@ -84,7 +88,7 @@ def unocg_set_uno_weights(ctx, kind: int, w: np.ndarray | None = None, spd_eps: 
 
 
 def make_opts(tol=1e-6, max_iter=10000, precond=_lib.PRECOND_UNO, precision=_lib.FP64,
-              replace_every=50, flexible=None, use_graph=1) -> SolveOpts:
+              replace_every=50, flexible=None, use_graph=3) -> SolveOpts:
     if flexible is None:
         flexible = 1 if precision == _lib.MIXED else 0
     return SolveOpts(tol, max_iter, precond, precision, replace_every, flexible, use_graph)

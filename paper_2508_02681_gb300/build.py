@@ -9,9 +9,11 @@ from concurrent.futures import ThreadPoolExecutor
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
-OUT_DIR = os.path.join(ROOT, "_build")
-LIB = os.path.join(HERE, "libunocg.so")
-SOURCES = ["api.cu", "k_stencil.cu", "k_setup.cu", "k_fft_plane.cu", "k_line64.cu", "k_line32.cu"]
+OUT_DIR = os.environ.get("UNOCG_BUILD_DIR", os.path.join(ROOT, "_build"))
+LIB = os.environ.get("UNOCG_LIB_OUT", os.path.join(HERE, "libunocg.so"))
+SOURCES = ["api.cu", "k_stencil.cu", "k_setup.cu", "k_fft_plane.cu", "k_line64.cu", "k_line32.cu", "k_persist.cu"]
+# loads of data written by other blocks of the same launch must bypass L1
+PER_FILE = {"k_persist.cu": ["-Xptxas", "-dlcm=cg"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
 
@@ -23,7 +25,7 @@ def nvcc() -> str:
 
 def _compile(src: str, extra) -> str:
     obj = os.path.join(OUT_DIR, os.path.splitext(src)[0] + ".o")
-    cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+    cmd = [nvcc(), *ARCH, *FLAGS, *PER_FILE.get(src, []), *extra, "-c", os.path.join(CSRC, src), "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

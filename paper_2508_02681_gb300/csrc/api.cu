@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "kargs.h"
+#include "persist.h"
 #include "setup.h"
 #include "unocg.h"
 
@@ -101,7 +102,10 @@ struct unocg_ctx {
   double* part = nullptr;
   size_t part_n = 0;
   unsigned int* tickets = nullptr;
-  int* flags = nullptr;  // [0] active, [1] replace
+  int* flags = nullptr;  // [0] active, [1] replace, [2..3] loop counters, [4..5] grid barrier, [6] timeout
+  int sm_count = 0;
+  int last_path = 0;     // 0 host loop, 1 graph, 2 persistent
+  long long spin_limit = 2000000000LL;  // grid-barrier wait limit (SM clock cycles)
   unsigned long long* fails = nullptr;
   Fields64 f64;
   Fields32 f32;
@@ -215,6 +219,7 @@ extern "C" int unocg_create(unocg_ctx** out, int physics, int batch, int n1, int
   ctx->g.n = (long long)n1 * n2 * n3;
   ctx->g.nh = (long long)n1 * n2 * (n3 / 2 + 1);
   ctx->g.h = L0 / n1;
+  grid_scales(ctx->g);
   factor_plan(n1, &ctx->p1);
   factor_plan(n2, &ctx->p2);
   factor_plan(n3 / 2, &ctx->p3h);
@@ -226,7 +231,13 @@ extern "C" int unocg_create(unocg_ctx** out, int physics, int batch, int n1, int
   CK(cudaMalloc(&ctx->phase, (size_t)batch * ctx->g.n));
   CK(cudaMalloc(&ctx->tickets, kMaxTickets * sizeof(unsigned int)));
   CK(cudaMemset(ctx->tickets, 0, kMaxTickets * sizeof(unsigned int)));
-  CK(cudaMalloc(&ctx->flags, 4 * sizeof(int)));
+  CK(cudaMalloc(&ctx->flags, 8 * sizeof(int)));
+  CK(cudaMemset(ctx->flags, 0, 8 * sizeof(int)));
+  {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, dev));
+  }
   CK(cudaMalloc(&ctx->fails, sizeof(unsigned long long)));
   CK(cudaMalloc(&ctx->ref, 2 * batch * sizeof(double)));
   return UNOCG_OK;
@@ -258,6 +269,13 @@ extern "C" void unocg_destroy(unocg_ctx* ctx) {
 }
 
 extern "C" const char* unocg_last_error(const unocg_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+extern "C" int unocg_set_wait_limit(unocg_ctx* ctx, double seconds) {
+  if (!ctx || !(seconds >= 0.0)) return fail(ctx, UNOCG_ERR_INVALID_ARG, "wait limit must be >= 0");
+  double cycles = seconds * 2.07e9;  // SM clock upper bound of the target GPU
+  ctx->spin_limit = cycles < 1.0 ? 1LL : (long long)cycles;
+  return UNOCG_OK;
+}
 
 extern "C" int unocg_set_stream(unocg_ctx* ctx, void* stream) {
   if (!ctx) return UNOCG_ERR_INVALID_ARG;
@@ -793,6 +811,74 @@ static int run_host_loop(unocg_ctx* ctx, const Plan& pl) {
   return UNOCG_OK;
 }
 
+// Whole loop in one cooperative launch (k_persist.cu), between the set-up and post kernels.
+static bool persistent_fits(unocg_ctx* ctx, const unocg_solve_opts* o) {
+  if (o->precond != UNOCG_PRECOND_UNO) return false;
+  const int BL = ctx->B * ctx->L;
+  if (BL > 128 || ctx->B * ctx->n_phases * 2 > 4096) return false;
+  const int eb = o->precision == UNOCG_FP64 ? 16 : 8;
+  const int tb = (eb == 8 ? 16 : 8) * (ctx->c == 1 ? 2 : 1);
+  size_t smem = persist_smem_bytes(ctx->g, ctx->c, tb, eb, BL, ctx->B, ctx->n_phases, eb / 2);
+  return smem <= 200 * 1024;
+}
+
+template <typename T>
+static int run_persistent(unocg_ctx* ctx, const Plan& pl) {
+  using QT = typename Sel<T>::QT;
+  cudaStream_t s = ctx->stream;
+  auto& f = Sel<T>::f(ctx);
+  const int BL = ctx->B * ctx->L;
+  CK(cudaMemsetAsync(ctx->sc, 0, BL * sizeof(CgScal), s));
+  CK(cudaMemsetAsync(ctx->flags, 0, 8 * sizeof(int), s));
+  InitArgs<T> ia{};
+  ia.g = ctx->g; ia.c = ctx->c; ia.L = ctx->L; ia.phase = ctx->phase; ia.mat = material(ctx);
+  ia.loads = ctx->loads_d; ia.r = f.r; ia.u = f.u; ia.d = f.d; ia.p = f.p;
+  ia.u64 = pl.mixed ? ctx->f32.u64 : nullptr;
+  CK(launch_init<T>(ia, BL, s));
+  PersistArgs<T, QT> a{};
+  a.pf.g = ctx->g; a.pf.c = ctx->c; a.pf.BL = BL; a.pf.r = f.r; a.pf.p = f.p; a.pf.hat = f.rhat;
+  a.pf.ft = tables(ctx, sizeof(T) == 8); a.pf.standalone = 0;
+  a.la.g = ctx->g; a.la.c = ctx->c; a.la.BL = BL; a.la.L = ctx->L; a.la.hat = f.rhat; a.la.shat = f.shat;
+  a.la.Q = Sel<T>::Q(ctx);
+  a.la.q_inst_stride = ctx->Bq > 1 ? ctx->g.nh * (ctx->c == 1 ? 1 : 6) : 0;
+  a.la.scale = 1.0 / (double)ctx->g.n; a.la.ft = tables(ctx, sizeof(T) == 8);
+  a.la.flexible = pl.o.flexible; a.la.standalone = 0;
+  a.la.tb = (sizeof(T) == 4 ? 16 : 8) * (ctx->c == 1 ? 2 : 1);
+  a.pi.g = ctx->g; a.pi.c = ctx->c; a.pi.BL = BL; a.pi.shat = f.shat; a.pi.d = f.d; a.pi.u = f.u;
+  a.pi.ft = tables(ctx, sizeof(T) == 8); a.pi.standalone = 0;
+  a.ka.g = ctx->g; a.ka.c = ctx->c; a.ka.BL = BL; a.ka.L = ctx->L; a.ka.phase = ctx->phase;
+  a.ka.mat = material(ctx); a.ka.d = f.d; a.ka.p = f.p; a.ka.standalone = 0;
+  a.fo.c = ctx->c; a.fo.n = ctx->g.n; a.fo.u64 = Sel<T>::u64(ctx); a.fo.u32 = Sel<T>::u32(ctx); a.fo.d = f.d;
+  a.loads = ctx->loads_d;
+  a.sc = ctx->sc;
+  a.B = ctx->B; a.L = ctx->L; a.BL = BL;
+  a.n_line_tasks = line_blocks_x(ctx->g, ctx->c, sizeof(T) * 2);
+  a.n_ku_tasks = ku_blocks_x(ctx->g, ctx->c);
+  a.n_tr_tasks = node_blocks_x(ctx->g);
+  a.n_fold_chunks = 64;
+  const long long np = (long long)ctx->c * ctx->g.n1;
+  a.off_max = 0;
+  a.off_line = (long long)BL * np;
+  a.off_ku = a.off_line + (long long)BL * a.n_line_tasks * 2;
+  const size_t need = (size_t)(a.off_ku + (long long)BL * a.n_ku_tasks);
+  if (need > ctx->part_n) {
+    if (ctx->part) cudaFree(ctx->part);
+    ctx->part = nullptr;
+    CK(cudaMalloc(&ctx->part, need * sizeof(double)));
+    ctx->part_n = need;
+  }
+  a.part = ctx->part;
+  a.counters = ctx->flags + 2;
+  a.bar = reinterpret_cast<unsigned int*>(ctx->flags + 4);
+  a.err = ctx->flags + 6;
+  a.ctl.tol = pl.o.tol; a.ctl.max_iter = pl.o.max_iter; a.ctl.mixed = pl.mixed;
+  a.ctl.replace_every = pl.o.replace_every; a.ctl.flexible = pl.o.flexible;
+  a.spin_limit = ctx->spin_limit;
+  CK(launch_persist<T, QT>(a, s, ctx->sm_count));
+  CK(enq_post<T>(ctx, s, pl));
+  return UNOCG_OK;
+}
+
 static int prepare_solve(unocg_ctx* ctx, const unocg_solve_opts* o, Plan* pl) {
   if (!ctx || !o) return fail(ctx, UNOCG_ERR_INVALID_ARG, "null argument");
   if (!ctx->have_phase || !ctx->have_props || !ctx->have_loads)
@@ -822,8 +908,16 @@ extern "C" int unocg_solve_async(unocg_ctx* ctx, const unocg_solve_opts* o) {
   ctx->last_opts = *o;
   ctx->last_precision = o->precision;
   ctx->solved = false;
-  if (!o->use_graph) {
+  int path = o->use_graph;
+  // automatic: the graph loop (a kernel boundary in a graph costs less than a grid barrier)
+  if (path == 3) path = 1;
+  if (path == 2 && !persistent_fits(ctx, o)) return fail(ctx, UNOCG_ERR_INVALID_ARG, "problem too large for the persistent kernel");
+  ctx->last_path = path;
+  if (path == 0) {
     rc = pl.mixed ? run_host_loop<float>(ctx, pl) : run_host_loop<double>(ctx, pl);
+    if (rc) return rc;
+  } else if (path == 2) {
+    rc = pl.mixed ? run_persistent<float>(ctx, pl) : run_persistent<double>(ctx, pl);
     if (rc) return rc;
   } else {
     GraphKey k;
@@ -866,16 +960,21 @@ extern "C" int unocg_solve_wait(unocg_ctx* ctx, unocg_solve_info* info) {
       if (info->load_status) info->load_status[i] = st;
     }
   }
+  int ctl[8];
+  CK(cudaMemcpy(ctl, ctx->flags, 8 * sizeof(int), cudaMemcpyDeviceToHost));
+  if (ctl[6]) {
+    status = UNOCG_ERR_DEVICE_TIMEOUT;
+  }
   if (info) {
-    int cnt[2] = {0, 0};
-    CK(cudaMemcpy(cnt, ctx->flags + 2, 2 * sizeof(int), cudaMemcpyDeviceToHost));
+    int cnt[2] = {ctl[2], ctl[3]};
     info->status = status;
     info->max_iters = mx;
     info->checks = cnt[0];
     info->replacements = cnt[1];
   }
   if (status != UNOCG_OK) {
-    ctx->err = status == UNOCG_ERR_NOT_CONVERGED ? "not converged within max_iter" : "CG breakdown";
+    ctx->err = status == UNOCG_ERR_NOT_CONVERGED ? "not converged within max_iter"
+             : status == UNOCG_ERR_DEVICE_TIMEOUT ? "grid barrier wait expired" : "CG breakdown";
   }
   return status;
 }
@@ -1115,6 +1214,7 @@ static int ufail(unocg_uno* op, int code, const std::string& m) {
 extern "C" int unocg_uno_create(unocg_uno** out, int c, int n1, int n2, int n3) {
   if (!out || (c != 1 && c != 3) || !grid_ok(n1, n2, n3)) return UNOCG_ERR_INVALID_ARG;
   Grid g{n1, n2, n3, n3 / 2 + 1, (long long)n1 * n2 * n3, (long long)n1 * n2 * (n3 / 2 + 1), 1.0 / n1};
+  grid_scales(g);
   if (!plane_fits(g, 8)) return UNOCG_ERR_INVALID_ARG;
   unocg_uno* op = new unocg_uno();
   *out = op;

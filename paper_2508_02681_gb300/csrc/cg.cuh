@@ -24,10 +24,12 @@ struct LoopCtl {
 // Residual check after r <- r - alpha p (or after a replacement, `after_replace`).  Runs in the
 // last block of the residual-update kernel over all (instance, load) pairs.
 __device__ inline void residual_decision(CgScal* sc, int BL, const LoopCtl& ctl, int after_replace) {
-  int any_active = 0, any_replace = 0;
   for (int bl = threadIdx.x; bl < BL; bl += blockDim.x) {
     CgScal& s = sc[bl];
     if (s.done) continue;
+    // a check after a replacement concerns only the replaced pairs
+    if (after_replace && !s.need_replace) continue;
+    s.just_replaced = after_replace;
     double rmax = bits_to_double(s.rmax_bits);
     s.rmax_bits = 0ull;
     s.rmax = rmax;
@@ -48,8 +50,6 @@ __device__ inline void residual_decision(CgScal* sc, int BL, const LoopCtl& ctl,
     if (ctl.mixed && !after_replace && s.iters > 0 &&
         (conv || (ctl.replace_every > 0 && s.iters % ctl.replace_every == 0))) {
       s.need_replace = 1;
-      any_replace = 1;
-      any_active = 1;
       continue;
     }
     if (conv) {
@@ -60,8 +60,13 @@ __device__ inline void residual_decision(CgScal* sc, int BL, const LoopCtl& ctl,
       s.status = UNOCG_ERR_NOT_CONVERGED;
     } else {
       s.iters += 1;
-      any_active = 1;
     }
+  }
+  __syncthreads();
+  int any_active = 0, any_replace = 0;
+  for (int bl = threadIdx.x; bl < BL; bl += blockDim.x) {
+    any_active |= !sc[bl].done;
+    any_replace |= sc[bl].need_replace;
   }
   any_active = __syncthreads_or(any_active);
   any_replace = __syncthreads_or(any_replace);

@@ -46,7 +46,8 @@ struct CgScal {
   int status;         // 0 ok, UNOCG_ERR_* when done
   int need_replace;   // residual replacement requested (mixed precision)
   int started;        // r0max recorded
-  int pad[3];
+  int just_replaced;  // the last residual check followed a replacement of this pair
+  int pad[2];
 };
 
 // ---------------------------------------------------------------- problem descriptor
@@ -55,6 +56,48 @@ struct Grid {
   long long n;              // nodes per field
   long long nh;             // half-grid modes per field
   double h;                 // voxel edge
+  double h12;               // h / 12 (thermal stencil scale)
+  float hf, h12f;           // the same in FP32 (no FP64 arithmetic on per-node paths)
+};
+__host__ __device__ inline void grid_scales(Grid& g) {
+  g.h12 = g.h / 12.0;
+  g.hf = (float)g.h;
+  g.h12f = (float)g.h12;
+}
+template <typename T> __device__ __forceinline__ T grid_h(const Grid& g);
+template <> __device__ __forceinline__ float grid_h<float>(const Grid& g) { return g.hf; }
+template <> __device__ __forceinline__ double grid_h<double>(const Grid& g) { return g.h; }
+template <typename T> __device__ __forceinline__ T grid_h12(const Grid& g);
+template <> __device__ __forceinline__ float grid_h12<float>(const Grid& g) { return g.h12f; }
+template <> __device__ __forceinline__ double grid_h12<double>(const Grid& g) { return g.h12; }
+
+// ---------------------------------------------------------------- dot-product accumulation
+// Per-thread partial sums of the CG dot products.  FP64 fields accumulate in FP64.  FP32 fields
+// accumulate in an error-free float-float pair (products split exactly by FMA, sums by TwoSum):
+// about 44 significant bits on the FP32 pipes, converted to FP64 once per thread for the FP64
+// block and grid reductions (GB300's FP64 pipe is far too narrow for per-element FP64 work).
+template <typename T> struct DotAcc;
+template <> struct DotAcc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add_prod(double a, double b) { s = fma(a, b, s); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct DotAcc<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = __fadd_rn(hi, x);
+    const float bp = __fsub_rn(t, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+    hi = t;
+    lo = __fadd_rn(lo, e);
+  }
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float e = __fmaf_rn(a, b, -p);
+    add(p);
+    lo = __fadd_rn(lo, e);
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
 // Radix plan of one transform length.
@@ -117,6 +160,29 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   }
   return s;
 }
+// Block-wide sum of per-thread accumulators; result valid in thread 0.  The float-float pairs are
+// combined with FP32 operations (TwoSum) and converted to FP64 by one warp only.
+__device__ __forceinline__ double block_sum_acc(const DotAcc<double>& a, double* sh) { return block_sum(a.value(), sh); }
+__device__ __forceinline__ double block_sum_acc(DotAcc<float> a, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, a.hi, o);
+    const float ol = __shfl_xor_sync(0xffffffffu, a.lo, o);
+    a.add(oh);
+    a.lo = __fadd_rn(a.lo, ol);
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) sh[w] = a.value();
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  }
+  return s;
+}
+
 __device__ __forceinline__ double block_max(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -131,6 +197,23 @@ __device__ __forceinline__ double block_max(double v, double* sh) {
   }
   return s;
 }
+
+__device__ __forceinline__ double block_max_f(float v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) sh[w] = (double)v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+  }
+  return s;
+}
+__device__ __forceinline__ double block_max_t(float v, double* sh) { return block_max_f(v, sh); }
+__device__ __forceinline__ double block_max_t(double v, double* sh) { return block_max(v, sh); }
 
 // Returns true in every thread of the block that arrives last at `ticket` (over all blocks
 // of the grid).  Callers write their partials before and read all partials after.

@@ -18,75 +18,134 @@ namespace unocg {
 
 static __host__ __device__ inline int pitch_of(int n3h) { return (n3h % 2 == 0) ? n3h + 1 : n3h; }
 
-// ============================================================================ pass A
-template <typename T, int NTH>
-__global__ void __launch_bounds__(NTH) k_plane_fwd(PlaneFwdArgs<T> a) {
+// ============================================================================ shared-memory layout
+// Plane tasks: two plane buffers of n2 x P complex, then twiddles W_{N3/2}, W_{N2}, W_{N3}.
+template <typename T> struct PlaneSmem {
+  cplx<T>* buf;
+  cplx<T>* alt;
+  cplx<T>* tw3h;
+  cplx<T>* tw2;
+  cplx<T>* tw3;
+};
+template <typename T>
+__device__ __forceinline__ PlaneSmem<T> plane_smem_layout(void* raw, const Grid& g) {
+  PlaneSmem<T> s;
+  const int P = pitch_of(g.n3h);
+  s.buf = reinterpret_cast<cplx<T>*>(raw);
+  s.alt = s.buf + g.n2 * P;
+  s.tw3h = s.alt + g.n2 * P;
+  s.tw2 = s.tw3h + g.n3 / 2;
+  s.tw3 = s.tw2 + g.n2;
+  return s;
+}
+template <typename T>
+__device__ __forceinline__ void plane_load_twiddles(const PlaneSmem<T>& s, const Grid& g, const FftTables& ft) {
+  load_tw<T>(s.tw3h, ft.tw3h, g.n3 / 2);
+  load_tw<T>(s.tw2, ft.tw2, g.n2);
+  load_tw<T>(s.tw3, ft.tw3, g.n3);
+}
+
+// ============================================================================ pass A task
+// One (field, i1) plane: CG mode r <- r - alpha p (alpha != 0), |r| max; standalone mode reads
+// src.  Forward r2c FFT along axis 3 and FFT along axis 2; writes the plane of `hat`.
+// Returns max |r| over the plane (valid in every thread).  Call with the whole block.
+template <typename T>
+__device__ double plane_fwd_task(const PlaneFwdArgs<T>& a, const PlaneSmem<T>& sm, int bl, int plane,
+                                 double alpha, double* red_sh) {
   using C = cplx<T>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);
-  __shared__ double red_sh[32];
   const Grid& g = a.g;
   const int n3h = g.n3h, Nh = g.n3 / 2, P = pitch_of(n3h);
   const float rNh = 1.0f / (float)Nh, rn3h = 1.0f / (float)n3h;
-  const int plane = blockIdx.x;  // comp * n1 + i1
-  const int bl = blockIdx.y;
-  const int comp = plane / g.n1, i1 = plane % g.n1;
+  const int comp = plane / g.n1, i1 = plane - comp * g.n1;
   const long long field = (long long)bl * a.c + comp;
-  C* tw3h = buf + 2 * g.n2 * P;
-  C* tw2 = tw3h + Nh;
-  C* tw3 = tw2 + g.n2;
-  load_tw<T>(tw3h, a.ft.tw3h, Nh);
-  load_tw<T>(tw2, a.ft.tw2, g.n2);
-  load_tw<T>(tw3, a.ft.tw3, g.n3);
+  const long long base = (field * g.n1 + i1) * (long long)g.n2 * g.n3;
+  const int npair = g.n2 * Nh;
+  C* buf = sm.buf;
+  T lmax = (T)0;
+  constexpr int U = 8;  // loads in flight per thread
+  if (a.standalone) {
+    const C* __restrict__ src = reinterpret_cast<const C*>(a.src + base);
+    for (int i0 = threadIdx.x; i0 < npair; i0 += U * blockDim.x) {
+      C v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = i0 + u * blockDim.x;
+        if (idx < npair) v[u] = src[idx];
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = i0 + u * blockDim.x;
+        if (idx < npair) {
+          int i2 = fdiv(idx, rNh), m = idx - i2 * Nh;
+          buf[i2 * P + m] = v[u];
+        }
+      }
+    }
+  } else {
+    C* __restrict__ r = reinterpret_cast<C*>(a.r + base);
+    const C* __restrict__ p = reinterpret_cast<const C*>(a.p + base);
+    const T al = (T)alpha;
+    const bool upd = alpha != 0.0;
+    for (int i0 = threadIdx.x; i0 < npair; i0 += U * blockDim.x) {
+      C v[U], q[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = i0 + u * blockDim.x;
+        if (idx < npair) {
+          v[u] = r[idx];
+          if (upd) q[u] = p[idx];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = i0 + u * blockDim.x;
+        if (idx < npair) {
+          int i2 = fdiv(idx, rNh), m = idx - i2 * Nh;
+          C w = v[u];
+          if (upd) {
+            w.x -= al * q[u].x;
+            w.y -= al * q[u].y;
+            r[idx] = w;
+          }
+          lmax = fmax(lmax, fmax(fabs(w.x), fabs(w.y)));
+          buf[i2 * P + m] = w;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  C* res = fft_lines<T, -1>(buf, sm.alt, g.n2, P, 1, a.ft.p3h, sm.tw3h);
+  r2c_post<T>(res, g.n2, P, Nh, sm.tw3);
+  res = fft_lines<T, -1>(res, res == buf ? sm.alt : buf, n3h, 1, P, a.ft.p2, sm.tw2);
+  C* out = a.hat + (field * g.n1 + i1) * (long long)g.n2 * n3h;
+  const int nout = g.n2 * n3h;
+  for (int idx = threadIdx.x; idx < nout; idx += blockDim.x) {
+    int k2 = fdiv(idx, rn3h), k3 = idx - k2 * n3h;
+    out[idx] = res[k2 * P + k3];
+  }
+  if (a.standalone) {
+    __syncthreads();
+    return 0.0;
+  }
+  return block_max_t(lmax, red_sh);  // contains the barrier that protects the buffers
+}
+
+template <typename T, int NTH>
+__global__ void __launch_bounds__(NTH) k_plane_fwd(PlaneFwdArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red_sh[32];
+  PlaneSmem<T> sm = plane_smem_layout<T>(smem_raw, a.g);
+  plane_load_twiddles<T>(sm, a.g, a.ft);
+  const int bl = blockIdx.y;
   bool active = true;
   double alpha = 0.0;
   if (!a.standalone) {
-    active = !a.sc[bl].done;
+    active = !a.sc[bl].done && (!a.after_replace || a.sc[bl].need_replace);
     alpha = a.after_replace ? 0.0 : a.sc[bl].alpha;
   }
-  double lmax = 0.0;
-  if (active) {
-    const long long base = (field * g.n1 + i1) * (long long)g.n2 * g.n3;
-    const int npair = g.n2 * Nh;
-    if (a.standalone) {
-      const C* src = reinterpret_cast<const C*>(a.src + base);
-      for (int idx = threadIdx.x; idx < npair; idx += NTH) {
-        int i2 = fdiv(idx, rNh), m = idx - i2 * Nh;
-        buf[i2 * P + m] = src[idx];
-      }
-    } else {
-      C* r = reinterpret_cast<C*>(a.r + base);
-      const C* p = reinterpret_cast<const C*>(a.p + base);
-      const T al = (T)alpha;
-      for (int idx = threadIdx.x; idx < npair; idx += NTH) {
-        int i2 = fdiv(idx, rNh), m = idx - i2 * Nh;
-        C v = r[idx];
-        if (alpha != 0.0) {
-          C q = p[idx];
-          v.x -= al * q.x;
-          v.y -= al * q.y;
-          r[idx] = v;
-        }
-        lmax = fmax(lmax, fmax(fabs((double)v.x), fabs((double)v.y)));
-        buf[i2 * P + m] = v;
-      }
-    }
-    __syncthreads();
-    // rows: half-length complex FFT, then split into the half spectrum of the real row
-    C* alt = buf + g.n2 * P;
-    C* res = fft_lines<T, -1>(buf, alt, g.n2, P, 1, a.ft.p3h, tw3h);
-    r2c_post<T>(res, g.n2, P, Nh, tw3);
-    // columns (axis 2)
-    res = fft_lines<T, -1>(res, res == buf ? alt : buf, n3h, 1, P, a.ft.p2, tw2);
-    C* out = a.hat + (field * g.n1 + i1) * (long long)g.n2 * n3h;
-    const int nout = g.n2 * n3h;
-    for (int idx = threadIdx.x; idx < nout; idx += NTH) {
-      int k2 = fdiv(idx, rn3h), k3 = idx - k2 * n3h;
-      out[idx] = res[k2 * P + k3];
-    }
-  }
+  double bmax = 0.0;
+  if (active) bmax = plane_fwd_task<T>(a, sm, bl, blockIdx.x, alpha, red_sh);
   if (a.standalone) return;
-  double bmax = block_max(lmax, red_sh);
   if (threadIdx.x == 0 && active) atomic_max_nonneg(&a.sc[bl].rmax_bits, bmax);
   if (last_block(a.ticket)) {
     residual_decision(a.sc, a.BL, a.ctl, a.after_replace);
@@ -94,7 +153,7 @@ __global__ void __launch_bounds__(NTH) k_plane_fwd(PlaneFwdArgs<T> a) {
   }
 }
 
-// ============================================================================ pass B
+// ============================================================================ pass B task
 template <typename T, typename QT> struct QLoad;
 template <typename T> struct QLoad<T, double> {
   static __device__ __forceinline__ T get(const double* q, long long i) { return (T)__ldg(q + i); }
@@ -104,133 +163,191 @@ template <typename T> struct QLoad<T, float> {
 };
 template <typename T> struct QLoad<T, __nv_bfloat16> {
   static __device__ __forceinline__ T get(const __nv_bfloat16* q, long long i) {
-    return (T)__bfloat162float(q[i]);
+    return (T)__bfloat162float(__ldg(q + i));
   }
 };
 
-// mode: 0 = CG (Parseval dots, scalars), 1 = standalone apply, 2 = backward (weight gradient)
-template <typename T, typename QT, int CC, int NTH, int MODE>
-__global__ void __launch_bounds__(NTH) k_line(LineArgs<T, QT> a) {
+template <typename T> struct LineSmem {
+  cplx<T>* buf;
+  cplx<T>* alt;
+  cplx<T>* gbuf;
+  cplx<T>* galt;
+  cplx<T>* tw1;
+};
+template <typename T, int CC, int MODE>
+__device__ __forceinline__ LineSmem<T> line_smem_layout(void* raw, const Grid& g, int tb) {
+  LineSmem<T> s;
+  const size_t SZ = (size_t)g.n1 * CC * tb;
+  s.buf = reinterpret_cast<cplx<T>*>(raw);
+  s.alt = s.buf + SZ;
+  s.gbuf = s.buf + 2 * SZ;
+  s.galt = s.buf + 3 * SZ;
+  s.tw1 = s.buf + (MODE == 2 ? 4 : 2) * SZ;
+  return s;
+}
+
+// One tile of TB consecutive (k2, k3) positions of one (instance, load), all c components:
+// FFT along axis 1, s_hat = Q r_hat / n, Parseval partial of r . s (and of r . s_old for the
+// flexible variant), inverse FFT along axis 1.  mode 0: CG, 1: apply, 2: backward.
+// Returns (gamma, rs_old) partial sums of the tile, valid in thread 0.
+template <typename T, typename QT, int CC, int MODE>
+__device__ double2 line_task(const LineArgs<T, QT>& a, const LineSmem<T>& sm, int bl, int tile, double* red_sh) {
   using C = cplx<T>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);
   const int TB = a.tb;
   const float rTB = 1.0f / (float)TB, rn3h = 1.0f / (float)a.g.n3h;
-  const size_t SZ = (size_t)a.g.n1 * CC * TB;
-  C* alt = buf + SZ;
-  C* gbuf = buf + 2 * SZ;  // backward: spectra of the gradient
-  C* galt = buf + 3 * SZ;
-  C* tw1 = buf + (MODE == 2 ? 4 : 2) * SZ;
-  load_tw<T>(tw1, a.ft.tw1, a.g.n1);
-  __shared__ double red_sh[32];
   const Grid& g = a.g;
   const int n1 = g.n1;
   const int M = g.n2 * g.n3h;
-  const int bl = blockIdx.y;
-  const int pos0 = blockIdx.x * TB;
+  const int pos0 = tile * TB;
   const int nt = min(TB, M - pos0);
-  const int LW = CC * TB;  // lines per block
-  bool active = (MODE != 0) || !a.sc[bl].done;
-  double gam = 0.0, rso = 0.0;
-  if (active) {
-    const long long fbase = (long long)bl * CC * n1 * M;
-    for (int idx = threadIdx.x; idx < n1 * LW; idx += NTH) {
-      int rest = fdiv(idx, rTB), t = idx - rest * TB;
-      int comp = rest % CC, k1 = rest / CC;
-      C v = mk<T>((T)0, (T)0), gv = v;
-      if (t < nt) {
-        long long gi = fbase + ((long long)comp * n1 + k1) * M + pos0 + t;
-        v = a.hat[gi];
-        if (MODE == 2) gv = a.ghat[gi];
-        if (MODE == 0 && a.flexible) {
-          C so = a.shat[gi];
+  const int LW = CC * TB;
+  DotAcc<T> gam, rso;
+  const long long fbase = (long long)bl * CC * n1 * M;
+  constexpr int U = 8;
+  for (int i0 = threadIdx.x; i0 < n1 * LW; i0 += U * blockDim.x) {
+    C v[U], gv[U], so[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = i0 + u * blockDim.x;
+      v[u] = mk<T>((T)0, (T)0);
+      gv[u] = v[u];
+      so[u] = v[u];
+      if (idx < n1 * LW) {
+        int rest = fdiv(idx, rTB), t = idx - rest * TB;
+        int comp = rest % CC, k1 = rest / CC;
+        if (t < nt) {
+          long long gi = fbase + ((long long)comp * n1 + k1) * M + pos0 + t;
+          v[u] = a.hat[gi];
+          if (MODE == 2) gv[u] = a.ghat[gi];
+          if (MODE == 0 && a.flexible) so[u] = a.shat[gi];
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = i0 + u * blockDim.x;
+      if (idx < n1 * LW) {
+        int rest = fdiv(idx, rTB), t = idx - rest * TB;
+        int comp = rest % CC, k1 = rest / CC;
+        if (MODE == 0 && a.flexible && t < nt) {
           int k3 = (pos0 + t) - fdiv(pos0 + t, rn3h) * g.n3h;
-          double w = (k3 == 0 || 2 * k3 == g.n3) ? 1.0 : 2.0;
-          rso += w * ((double)v.x * (double)so.x + (double)v.y * (double)so.y);
+          const T w = (k3 == 0 || 2 * k3 == g.n3) ? (T)1 : (T)2;
+          rso.add_prod(w * v[u].x, so[u].x);
+          rso.add_prod(w * v[u].y, so[u].y);
         }
-      }
-      buf[k1 * LW + comp * TB + t] = v;
-      if (MODE == 2) gbuf[k1 * LW + comp * TB + t] = gv;
-    }
-    __syncthreads();
-    C* res = fft_lines<T, -1>(buf, alt, LW, 1, LW, a.ft.p1, tw1);
-    C* gres = gbuf;
-    if (MODE == 2) gres = fft_lines<T, -1>(gbuf, galt, LW, 1, LW, a.ft.p1, tw1);
-    const long long qb = (long long)(bl / a.L) * a.q_inst_stride;
-    const T sc = (T)a.scale;
-    for (int idx = threadIdx.x; idx < n1 * TB; idx += NTH) {
-      int k1 = fdiv(idx, rTB), t = idx - k1 * TB;
-      if (t >= nt) continue;
-      int pos = pos0 + t;
-      int k3 = pos - fdiv(pos, rn3h) * g.n3h;
-      double w = (k3 == 0 || 2 * k3 == g.n3) ? 1.0 : 2.0;
-      const long long qi = qb + ((long long)k1 * M + pos) * (CC == 1 ? 1 : 6);
-      C* bp = res + k1 * LW + t;
-      if (MODE == 2) {
-        // dL/dQ_ij(k) = w Re(conj(G_i) R_j) / n with G, R unnormalized spectra
-        C* gp = gres + k1 * LW + t;
-        float* out = a.gq + ((long long)k1 * M + pos) * (CC == 1 ? 1 : 6);
-        if (CC == 1) {
-          C R = bp[0], Gv = gp[0];
-          double gr = w * ((double)Gv.x * R.x + (double)Gv.y * R.y) * a.scale;
-          atomicAdd(out, (float)gr);
-        } else {
-          C R0 = bp[0], R1 = bp[TB], R2 = bp[2 * TB];
-          C G0 = gp[0], G1 = gp[TB], G2 = gp[2 * TB];
-          auto re = [](C x, C y) { return (double)x.x * y.x + (double)x.y * y.y; };
-          double s = w * a.scale;
-          atomicAdd(out + 0, (float)(s * re(G0, R0)));
-          atomicAdd(out + 1, (float)(s * re(G1, R1)));
-          atomicAdd(out + 2, (float)(s * (re(G0, R1) + re(G1, R0))));
-          atomicAdd(out + 3, (float)(s * re(G2, R2)));
-          atomicAdd(out + 4, (float)(s * (re(G1, R2) + re(G2, R1))));
-          atomicAdd(out + 5, (float)(s * (re(G0, R2) + re(G2, R0))));
-        }
-        // the gradient w.r.t. the input is P applied to the upstream gradient
-        bp = gp;
-      }
-      if (CC == 1) {
-        T q = QLoad<T, QT>::get(a.Q, qi) * sc;
-        C R = bp[0];
-        C S = mk<T>(q * R.x, q * R.y);
-        if (MODE == 0) gam += w * ((double)R.x * S.x + (double)R.y * S.y);
-        bp[0] = S;
-      } else {
-        T v1 = QLoad<T, QT>::get(a.Q, qi + 0) * sc, v2 = QLoad<T, QT>::get(a.Q, qi + 1) * sc;
-        T v3 = QLoad<T, QT>::get(a.Q, qi + 2) * sc, v4 = QLoad<T, QT>::get(a.Q, qi + 3) * sc;
-        T v5 = QLoad<T, QT>::get(a.Q, qi + 4) * sc, v6 = QLoad<T, QT>::get(a.Q, qi + 5) * sc;
-        C R0 = bp[0], R1 = bp[TB], R2 = bp[2 * TB];
-        C S0 = mk<T>(v1 * R0.x + v3 * R1.x + v6 * R2.x, v1 * R0.y + v3 * R1.y + v6 * R2.y);
-        C S1 = mk<T>(v3 * R0.x + v2 * R1.x + v5 * R2.x, v3 * R0.y + v2 * R1.y + v5 * R2.y);
-        C S2 = mk<T>(v6 * R0.x + v5 * R1.x + v4 * R2.x, v6 * R0.y + v5 * R1.y + v4 * R2.y);
-        if (MODE == 0)
-          gam += w * ((double)R0.x * S0.x + (double)R0.y * S0.y + (double)R1.x * S1.x +
-                      (double)R1.y * S1.y + (double)R2.x * S2.x + (double)R2.y * S2.y);
-        bp[0] = S0;
-        bp[TB] = S1;
-        bp[2 * TB] = S2;
-      }
-    }
-    __syncthreads();
-    C* ob = (MODE == 2) ? gres : res;
-    C* oalt = (MODE == 2) ? (gres == gbuf ? galt : gbuf) : (res == buf ? alt : buf);
-    ob = fft_lines<T, +1>(ob, oalt, LW, 1, LW, a.ft.p1, tw1);
-    for (int idx = threadIdx.x; idx < n1 * LW; idx += NTH) {
-      int rest = fdiv(idx, rTB), t = idx - rest * TB;
-      int comp = rest % CC, k1 = rest / CC;
-      if (t < nt) {
-        long long gi = fbase + ((long long)comp * n1 + k1) * M + pos0 + t;
-        a.shat[gi] = ob[k1 * LW + comp * TB + t];
+        sm.buf[k1 * LW + comp * TB + t] = v[u];
+        if (MODE == 2) sm.gbuf[k1 * LW + comp * TB + t] = gv[u];
       }
     }
   }
+  __syncthreads();
+  C* res = fft_lines<T, -1>(sm.buf, sm.alt, LW, 1, LW, a.ft.p1, sm.tw1);
+  C* gres = sm.gbuf;
+  if (MODE == 2) gres = fft_lines<T, -1>(sm.gbuf, sm.galt, LW, 1, LW, a.ft.p1, sm.tw1);
+  const long long qb = (long long)(bl / a.L) * a.q_inst_stride;
+  const T sc = (T)a.scale;
+  for (int idx = threadIdx.x; idx < n1 * TB; idx += blockDim.x) {
+    int k1 = fdiv(idx, rTB), t = idx - k1 * TB;
+    if (t >= nt) continue;
+    int pos = pos0 + t;
+    int k3 = pos - fdiv(pos, rn3h) * g.n3h;
+    const T w = (k3 == 0 || 2 * k3 == g.n3) ? (T)1 : (T)2;
+    const long long qi = qb + ((long long)k1 * M + pos) * (CC == 1 ? 1 : 6);
+    C* bp = res + k1 * LW + t;
+    if (MODE == 2) {
+      // dL/dQ_ij(k) = w Re(conj(G_i) R_j) / n with G, R unnormalized spectra
+      C* gp = gres + k1 * LW + t;
+      float* out = a.gq + ((long long)k1 * M + pos) * (CC == 1 ? 1 : 6);
+      if (CC == 1) {
+        C R = bp[0], Gv = gp[0];
+        const T gr = w * (Gv.x * R.x + Gv.y * R.y) * sc;
+        atomicAdd(out, (float)gr);
+      } else {
+        C R0 = bp[0], R1 = bp[TB], R2 = bp[2 * TB];
+        C G0 = gp[0], G1 = gp[TB], G2 = gp[2 * TB];
+        auto re = [](C x, C y) { return x.x * y.x + x.y * y.y; };
+        const T s = w * sc;
+        atomicAdd(out + 0, (float)(s * re(G0, R0)));
+        atomicAdd(out + 1, (float)(s * re(G1, R1)));
+        atomicAdd(out + 2, (float)(s * (re(G0, R1) + re(G1, R0))));
+        atomicAdd(out + 3, (float)(s * re(G2, R2)));
+        atomicAdd(out + 4, (float)(s * (re(G1, R2) + re(G2, R1))));
+        atomicAdd(out + 5, (float)(s * (re(G0, R2) + re(G2, R0))));
+      }
+      // the gradient w.r.t. the input is P applied to the upstream gradient
+      bp = gp;
+    }
+    if (CC == 1) {
+      T q = QLoad<T, QT>::get(a.Q, qi) * sc;
+      C R = bp[0];
+      C S = mk<T>(q * R.x, q * R.y);
+      if (MODE == 0) {
+        gam.add_prod(w * R.x, S.x);
+        gam.add_prod(w * R.y, S.y);
+      }
+      bp[0] = S;
+    } else {
+      T v1 = QLoad<T, QT>::get(a.Q, qi + 0) * sc, v2 = QLoad<T, QT>::get(a.Q, qi + 1) * sc;
+      T v3 = QLoad<T, QT>::get(a.Q, qi + 2) * sc, v4 = QLoad<T, QT>::get(a.Q, qi + 3) * sc;
+      T v5 = QLoad<T, QT>::get(a.Q, qi + 4) * sc, v6 = QLoad<T, QT>::get(a.Q, qi + 5) * sc;
+      C R0 = bp[0], R1 = bp[TB], R2 = bp[2 * TB];
+      C S0 = mk<T>(v1 * R0.x + v3 * R1.x + v6 * R2.x, v1 * R0.y + v3 * R1.y + v6 * R2.y);
+      C S1 = mk<T>(v3 * R0.x + v2 * R1.x + v5 * R2.x, v3 * R0.y + v2 * R1.y + v5 * R2.y);
+      C S2 = mk<T>(v6 * R0.x + v5 * R1.x + v4 * R2.x, v6 * R0.y + v5 * R1.y + v4 * R2.y);
+      if (MODE == 0) {
+        gam.add_prod(w * R0.x, S0.x);
+        gam.add_prod(w * R0.y, S0.y);
+        gam.add_prod(w * R1.x, S1.x);
+        gam.add_prod(w * R1.y, S1.y);
+        gam.add_prod(w * R2.x, S2.x);
+        gam.add_prod(w * R2.y, S2.y);
+      }
+      bp[0] = S0;
+      bp[TB] = S1;
+      bp[2 * TB] = S2;
+    }
+  }
+  __syncthreads();
+  C* ob = (MODE == 2) ? gres : res;
+  C* oalt = (MODE == 2) ? (gres == sm.gbuf ? sm.galt : sm.gbuf) : (res == sm.buf ? sm.alt : sm.buf);
+  ob = fft_lines<T, +1>(ob, oalt, LW, 1, LW, a.ft.p1, sm.tw1);
+  for (int idx = threadIdx.x; idx < n1 * LW; idx += blockDim.x) {
+    int rest = fdiv(idx, rTB), t = idx - rest * TB;
+    int comp = rest % CC, k1 = rest / CC;
+    if (t < nt) {
+      long long gi = fbase + ((long long)comp * n1 + k1) * M + pos0 + t;
+      a.shat[gi] = ob[k1 * LW + comp * TB + t];
+    }
+  }
+  double2 r;
+  r.x = 0.0;
+  r.y = 0.0;
+  if (MODE != 0) {
+    __syncthreads();
+    return r;
+  }
+  r.x = block_sum_acc(gam, red_sh);
+  r.y = block_sum_acc(rso, red_sh);
+  return r;
+}
+
+template <typename T, typename QT, int CC, int NTH, int MODE>
+__global__ void __launch_bounds__(NTH) k_line(LineArgs<T, QT> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red_sh[32];
+  LineSmem<T> sm = line_smem_layout<T, CC, MODE>(smem_raw, a.g, a.tb);
+  load_tw<T>(sm.tw1, a.ft.tw1, a.g.n1);
+  const int bl = blockIdx.y;
+  bool active = (MODE != 0) || !a.sc[bl].done;
+  double2 pr;
+  pr.x = 0.0;
+  pr.y = 0.0;
+  if (active) pr = line_task<T, QT, CC, MODE>(a, sm, bl, blockIdx.x, red_sh);
   if (MODE != 0) return;
-  double bg = block_sum(gam, red_sh);
-  double br = block_sum(rso, red_sh);
   if (threadIdx.x == 0) {
     double* pp = a.red.part + ((long long)bl * gridDim.x + blockIdx.x) * 2;
-    pp[0] = bg;
-    pp[1] = br;
+    pp[0] = pr.x;
+    pp[1] = pr.y;
   }
   if (last_block(a.red.ticket)) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -245,64 +362,106 @@ __global__ void __launch_bounds__(NTH) k_line(LineArgs<T, QT> a) {
   }
 }
 
-// ============================================================================ pass C
-template <typename T, int NTH>
-__global__ void __launch_bounds__(NTH) k_plane_inv(PlaneInvArgs<T> a) {
+// ============================================================================ pass C task
+// Inverse FFT along axis 2 and c2r along axis 3 of one plane; CG mode: u += alpha d_old,
+// d = s + beta d_old; standalone: dst = s.  Call with the whole block.
+template <typename T>
+__device__ void plane_inv_task(const PlaneInvArgs<T>& a, const PlaneSmem<T>& sm, int bl, int plane,
+                               double alpha_d, double beta_d) {
   using C = cplx<T>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);
   const Grid& g = a.g;
   const int n3h = g.n3h, Nh = g.n3 / 2, P = pitch_of(n3h);
   const float rNh = 1.0f / (float)Nh, rn3h = 1.0f / (float)n3h;
-  const int plane = blockIdx.x;
-  const int bl = blockIdx.y;
-  const int comp = plane / g.n1, i1 = plane % g.n1;
+  const int comp = plane / g.n1, i1 = plane - comp * g.n1;
   const long long field = (long long)bl * a.c + comp;
-  if (!a.standalone && a.sc[bl].done) return;
-  C* tw3h = buf + 2 * g.n2 * P;
-  C* tw2 = tw3h + Nh;
-  C* tw3 = tw2 + g.n2;
-  load_tw<T>(tw3h, a.ft.tw3h, Nh);
-  load_tw<T>(tw2, a.ft.tw2, g.n2);
-  load_tw<T>(tw3, a.ft.tw3, g.n3);
-  const C* in = a.shat + (field * g.n1 + i1) * (long long)g.n2 * n3h;
+  C* buf = sm.buf;
+  const C* __restrict__ in = a.shat + (field * g.n1 + i1) * (long long)g.n2 * n3h;
   const int nin = g.n2 * n3h;
-  for (int idx = threadIdx.x; idx < nin; idx += NTH) {
-    int k2 = fdiv(idx, rn3h), k3 = idx - k2 * n3h;
-    buf[k2 * P + k3] = in[idx];
+  constexpr int U = 8;
+  for (int i0 = threadIdx.x; i0 < nin; i0 += U * blockDim.x) {
+    C v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = i0 + u * blockDim.x;
+      if (idx < nin) v[u] = in[idx];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = i0 + u * blockDim.x;
+      if (idx < nin) {
+        int k2 = fdiv(idx, rn3h), k3 = idx - k2 * n3h;
+        buf[k2 * P + k3] = v[u];
+      }
+    }
   }
   __syncthreads();
-  C* alt = buf + g.n2 * P;
-  C* res = fft_lines<T, +1>(buf, alt, n3h, 1, P, a.ft.p2, tw2);
-  c2r_pre<T>(res, g.n2, P, Nh, tw3);
-  res = fft_lines<T, +1>(res, res == buf ? alt : buf, g.n2, P, 1, a.ft.p3h, tw3h);
+  C* res = fft_lines<T, +1>(buf, sm.alt, n3h, 1, P, a.ft.p2, sm.tw2);
+  c2r_pre<T>(res, g.n2, P, Nh, sm.tw3);
+  res = fft_lines<T, +1>(res, res == buf ? sm.alt : buf, g.n2, P, 1, a.ft.p3h, sm.tw3h);
   const long long base = (field * g.n1 + i1) * (long long)g.n2 * g.n3;
   const int npair = g.n2 * Nh;
   if (a.standalone) {
     C* dst = reinterpret_cast<C*>(a.dst + base);
-    for (int idx = threadIdx.x; idx < npair; idx += NTH) {
+    for (int idx = threadIdx.x; idx < npair; idx += blockDim.x) {
       int i2 = fdiv(idx, rNh), m = idx - i2 * Nh;
       dst[idx] = res[i2 * P + m];
     }
-    return;
+  } else {
+    const T alpha = (T)alpha_d, beta = (T)beta_d;
+    C* __restrict__ d = reinterpret_cast<C*>(a.d + base);
+    C* __restrict__ u = reinterpret_cast<C*>(a.u + base);
+    for (int i0 = threadIdx.x; i0 < npair; i0 += U * blockDim.x) {
+      C dv[U], uv[U];
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const int idx = i0 + q * blockDim.x;
+        if (idx < npair) {
+          dv[q] = d[idx];
+          uv[q] = u[idx];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const int idx = i0 + q * blockDim.x;
+        if (idx < npair) {
+          int i2 = fdiv(idx, rNh), m = idx - i2 * Nh;
+          C s = res[i2 * P + m];
+          C uu = uv[q];
+          uu.x += alpha * dv[q].x;
+          uu.y += alpha * dv[q].y;
+          u[idx] = uu;
+          d[idx] = mk<T>(s.x + beta * dv[q].x, s.y + beta * dv[q].y);
+        }
+      }
+    }
   }
-  const T alpha = (T)a.sc[bl].alpha, beta = (T)a.sc[bl].beta;
-  C* d = reinterpret_cast<C*>(a.d + base);
-  C* u = reinterpret_cast<C*>(a.u + base);
-  for (int idx = threadIdx.x; idx < npair; idx += NTH) {
-    int i2 = fdiv(idx, rNh), m = idx - i2 * Nh;
-    C s = res[i2 * P + m];
-    C dold = d[idx];
-    C uu = u[idx];
-    uu.x += alpha * dold.x;
-    uu.y += alpha * dold.y;
-    u[idx] = uu;
-    d[idx] = mk<T>(s.x + beta * dold.x, s.y + beta * dold.y);
-  }
+  __syncthreads();  // buffers are reused by the next task of this block
+}
+
+template <typename T, int NTH>
+__global__ void __launch_bounds__(NTH) k_plane_inv(PlaneInvArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  PlaneSmem<T> sm = plane_smem_layout<T>(smem_raw, a.g);
+  const int bl = blockIdx.y;
+  if (!a.standalone && a.sc[bl].done) return;
+  plane_load_twiddles<T>(sm, a.g, a.ft);
+  double al = a.standalone ? 0.0 : a.sc[bl].alpha, be = a.standalone ? 0.0 : a.sc[bl].beta;
+  plane_inv_task<T>(a, sm, bl, blockIdx.x, al, be);
 }
 
 // ============================================================================ launchers
-static inline int plane_threads(const Grid& g) { return (long long)g.n2 * g.n3h > 4096 ? 512 : 256; }
+// threads per plane block: enough warps per plane to hide shared-memory and L2 latency
+#ifndef UNOCG_PLANE_NTH
+#define UNOCG_PLANE_NTH 0  // 0: by plane size
+#endif
+#ifndef UNOCG_LINE_NTH
+#define UNOCG_LINE_NTH 0
+#endif
+static inline int plane_threads(const Grid& g) {
+  if (UNOCG_PLANE_NTH) return UNOCG_PLANE_NTH;
+  const long long e = (long long)g.n2 * g.n3h;
+  return e >= 2048 ? 1024 : (e >= 1024 ? 512 : 256);
+}
 static inline size_t plane_smem(const Grid& g, int elem_bytes) {
   // two plane buffers + the twiddle tables of N3/2, N2 and N3
   return (2 * (size_t)g.n2 * pitch_of(g.n3h) + g.n3 / 2 + g.n2 + g.n3) * elem_bytes;
@@ -327,8 +486,10 @@ template <typename T> cudaError_t launch_plane_fwd(const PlaneFwdArgs<T>& a, cud
   if (!plane_fits(a.g, eb)) return cudaErrorInvalidValue;
   size_t smem = plane_smem(a.g, eb);
   dim3 grid(a.c * a.g.n1, a.BL);
-  if (plane_threads(a.g) == 256) return launch_k(k_plane_fwd<T, 256>, grid, 256, smem, a, s);
-  return launch_k(k_plane_fwd<T, 512>, grid, 512, smem, a, s);
+  const int nth = plane_threads(a.g);
+  if (nth == 256) return launch_k(k_plane_fwd<T, 256>, grid, 256, smem, a, s);
+  if (nth == 512) return launch_k(k_plane_fwd<T, 512>, grid, 512, smem, a, s);
+  return launch_k(k_plane_fwd<T, 1024>, grid, 1024, smem, a, s);
 }
 
 template <typename T> cudaError_t launch_plane_inv(const PlaneInvArgs<T>& a, cudaStream_t s) {
@@ -336,8 +497,10 @@ template <typename T> cudaError_t launch_plane_inv(const PlaneInvArgs<T>& a, cud
   if (!plane_fits(a.g, eb)) return cudaErrorInvalidValue;
   size_t smem = plane_smem(a.g, eb);
   dim3 grid(a.c * a.g.n1, a.BL);
-  if (plane_threads(a.g) == 256) return launch_k(k_plane_inv<T, 256>, grid, 256, smem, a, s);
-  return launch_k(k_plane_inv<T, 512>, grid, 512, smem, a, s);
+  const int nth = plane_threads(a.g);
+  if (nth == 256) return launch_k(k_plane_inv<T, 256>, grid, 256, smem, a, s);
+  if (nth == 512) return launch_k(k_plane_inv<T, 512>, grid, 512, smem, a, s);
+  return launch_k(k_plane_inv<T, 1024>, grid, 1024, smem, a, s);
 }
 
 static int line_tb(int c, int elem_bytes) {
@@ -360,6 +523,10 @@ static cudaError_t launch_line_cc(LineArgs<T, QT> a, cudaStream_t s) {
   a.tb = line_tb(CC, eb);
   size_t smem = ((size_t)a.g.n1 * CC * a.tb * (MODE == 2 ? 4 : 2) + a.g.n1) * eb;
   dim3 grid(line_blocks_x(a.g, CC, eb), a.BL);
+  long long e = (long long)a.g.n1 * CC * a.tb;
+  if (UNOCG_LINE_NTH) e = UNOCG_LINE_NTH * 2;
+  if (e >= 2048) return launch_k(k_line<T, QT, CC, 1024, MODE>, grid, 1024, smem, a, s);
+  if (e >= 1024) return launch_k(k_line<T, QT, CC, 512, MODE>, grid, 512, smem, a, s);
   return launch_k(k_line<T, QT, CC, 256, MODE>, grid, 256, smem, a, s);
 }
 

@@ -12,154 +12,23 @@
 #include "kargs.h"
 #include "element.cuh"
 #include "stencil.cuh"
+#include "ku_task.cuh"
 
 namespace unocg {
 
 // ============================================================================ K d
-// Thermal: every thread marches along i1 over KU_CZ consecutive nodes of one (i2, i3) column,
-// keeping the 3x3 neighbourhoods of the planes i1-1, i1, i1+1 and the conductivities of the
-// element planes i1-1, i1 in registers: 9 loads of d and 4 phase labels per node.
-constexpr int KU_CZ = 8;
-
-__device__ __forceinline__ bool tile_column(const Grid& g, int cz, int& i1, int& i2, int& i3) {
-  const int nt3 = (g.n3 + 31) >> 5, nt2 = (g.n2 + 7) >> 3;
-  int bx = blockIdx.x;
-  const int b3 = bx % nt3;
-  bx /= nt3;
-  const int b2 = bx % nt2;
-  const int b1 = bx / nt2;
-  i3 = b3 * 32 + (threadIdx.x & 31);
-  i2 = b2 * 8 + (threadIdx.x >> 5);
-  i1 = b1 * cz;
-  return i3 < g.n3 && i2 < g.n2 && i1 < g.n1;
-}
-
-template <typename T>
-__device__ __forceinline__ void ku_thermal_column(const T* __restrict__ d, T* __restrict__ p,
-                                                  const uint8_t* __restrict__ ph, const T* mt,
-                                                  const Grid& g, int i1, int i2, int i3, int cz,
-                                                  double& dp) {
-  const int S = g.n2 * g.n3;
-  const int c2[3] = {i2 ? i2 - 1 : g.n2 - 1, i2, (i2 + 1 == g.n2) ? 0 : i2 + 1};
-  const int c3[3] = {i3 ? i3 - 1 : g.n3 - 1, i3, (i3 + 1 == g.n3) ? 0 : i3 + 1};
-  int off[3][3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) off[a][b] = c2[a] * g.n3 + c3[b];
-  // d planes: dm (i1-1), dc (i1), dn (i1+1); element conductivities km (plane i1-1), kc (plane i1)
-  T dm[3][3], dc[3][3], dn[3][3], km[2][2], kc[2][2];
-  int zm = (i1 ? i1 - 1 : g.n1 - 1) * S, zc = i1 * S;
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      dm[a][b] = __ldg(d + zm + off[a][b]);
-      dc[a][b] = __ldg(d + zc + off[a][b]);
-    }
-  // element (e1, i2 - o2, i3 - o3) sits at off[1 - o2][1 - o3] of element plane e1
-#pragma unroll
-  for (int o2 = 0; o2 < 2; ++o2)
-#pragma unroll
-    for (int o3 = 0; o3 < 2; ++o3) km[o2][o3] = mt[2 * __ldg(ph + zm + off[1 - o2][1 - o3])];
-  const T hf = (T)(g.h / 12.0);
-  const int zend = min(i1 + cz, g.n1);
-  for (int z = i1; z < zend; ++z) {
-    const int zn = ((z + 1 == g.n1) ? 0 : z + 1) * S;
-    zc = z * S;
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) dn[a][b] = __ldg(d + zn + off[a][b]);
-#pragma unroll
-    for (int o2 = 0; o2 < 2; ++o2)
-#pragma unroll
-      for (int o3 = 0; o3 < 2; ++o3) kc[o2][o3] = mt[2 * __ldg(ph + zc + off[1 - o2][1 - o3])];
-    // k[o1][o2][o3]: o1 = 0 -> element plane z (kc), o1 = 1 -> plane z-1 (km)
-    T sk = (kc[0][0] + kc[0][1]) + (kc[1][0] + kc[1][1]) + (km[0][0] + km[0][1]) + (km[1][0] + km[1][1]);
-    T acc = (T)4 * sk * dc[1][1];
-    // edge-diagonal neighbours in the plane (delta1 = 0): elements o1 in {0,1}
-#pragma unroll
-    for (int s2 = 0; s2 < 3; s2 += 2)
-#pragma unroll
-      for (int s3 = 0; s3 < 3; s3 += 2) {
-        const int o2 = s2 == 0, o3 = s3 == 0;
-        acc -= (kc[o2][o3] + km[o2][o3]) * dc[s2][s3];
-      }
-    // delta2 = 0: elements o2 in {0,1}, fixed o1, o3
-#pragma unroll
-    for (int s3 = 0; s3 < 3; s3 += 2) {
-      const int o3 = s3 == 0;
-      acc -= (kc[0][o3] + kc[1][o3]) * dn[1][s3];
-      acc -= (km[0][o3] + km[1][o3]) * dm[1][s3];
-    }
-    // delta3 = 0: elements o3 in {0,1}, fixed o1, o2
-#pragma unroll
-    for (int s2 = 0; s2 < 3; s2 += 2) {
-      const int o2 = s2 == 0;
-      acc -= (kc[o2][0] + kc[o2][1]) * dn[s2][1];
-      acc -= (km[o2][0] + km[o2][1]) * dm[s2][1];
-    }
-    // corners: one element each
-#pragma unroll
-    for (int s2 = 0; s2 < 3; s2 += 2)
-#pragma unroll
-      for (int s3 = 0; s3 < 3; s3 += 2) {
-        const int o2 = s2 == 0, o3 = s3 == 0;
-        acc -= kc[o2][o3] * dn[s2][s3];
-        acc -= km[o2][o3] * dm[s2][s3];
-      }
-    const T out = acc * hf;
-    p[zc + off[1][1]] = out;
-    dp += (double)(out * dc[1][1]);
-    // shift the window
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        dm[a][b] = dc[a][b];
-        dc[a][b] = dn[a][b];
-      }
-#pragma unroll
-    for (int o2 = 0; o2 < 2; ++o2)
-#pragma unroll
-      for (int o3 = 0; o3 < 2; ++o3) km[o2][o3] = kc[o2][o3];
-  }
-}
-
 template <typename T, int CC>
 __global__ void __launch_bounds__(256) k_ku(StencilArgs<T> a) {
   __shared__ T mt[2 * 256];
   __shared__ double red_sh[32];
-  const Grid& g = a.g;
+  __shared__ T tile_smem[CC == 1 ? KU_DN + KU_KN : 1];
   const int bl = blockIdx.y;
-  const int b = bl / a.L;
-  load_material<T>(mt, a.mat, b);
+  load_material<T>(mt, a.mat, bl / a.L);
   __syncthreads();
   bool active = a.standalone || !a.sc[bl].done;
-  double dp = 0.0;
-  const long long n = g.n;
-  const uint8_t* ph = a.phase + (long long)b * n;
-  const T* d = a.d + (long long)bl * CC * n;
-  T* p = a.p + (long long)bl * CC * n;
-  if (CC == 1) {
-    int i1, i2, i3;
-    if (active && tile_column(g, KU_CZ, i1, i2, i3)) ku_thermal_column<T>(d, p, ph, mt, g, i1, i2, i3, KU_CZ, dp);
-  } else {
-    int i1, i2, i3;
-    if (active && tile_node(g, i1, i2, i3)) {
-      const long long node = ((long long)i1 * g.n2 + i2) * g.n3 + i3;
-      T out[CC];
-      node_Ku<T, CC>(d, ph, mt, g, i1, i2, i3, out);
-#pragma unroll
-      for (int i = 0; i < CC; ++i) {
-        p[i * n + node] = out[i];
-        dp += (double)(out[i] * d[i * n + node]);
-      }
-    }
-  }
+  double bs = 0.0;
+  if (active) bs = ku_task<T, CC, false>(a, mt, bl, blockIdx.x, red_sh, tile_smem);
   if (a.standalone) return;
-  double bs = block_sum(dp, red_sh);
   if (threadIdx.x == 0) a.red.part[(long long)bl * gridDim.x + blockIdx.x] = bs;
   if (last_block(a.red.ticket)) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -270,26 +139,29 @@ __global__ void __launch_bounds__(256) k_jac_a(JacArgs<T> a) {
   __shared__ double red_sh[32];
   const int bl = blockIdx.y;
   CgScal& s = a.sc[bl];
-  const bool active = !s.done;
+  const bool active = !s.done && (!a.after_replace || s.need_replace);
   const double al = a.after_replace ? 0.0 : s.alpha;
-  double lmax = 0.0, gam = 0.0;
+  const T alt = (T)al;
+  const bool upd = al != 0.0;
+  T lmax = (T)0;
+  DotAcc<T> gam;
   if (active) {
     const long long m = (long long)a.c * a.n;
     const long long base = (long long)bl * m;
     const long long ib = (long long)(bl / a.L) * m;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x) {
       T r = a.r[base + i];
-      if (al != 0.0) {
-        r -= (T)al * a.p[base + i];
+      if (upd) {
+        r -= alt * a.p[base + i];
         a.r[base + i] = r;
       }
       T sv = a.invdiag ? r * a.invdiag[ib + i] : r;
-      lmax = fmax(lmax, fabs((double)r));
-      gam += (double)r * (double)sv;
+      lmax = fmax(lmax, fabs(r));
+      gam.add_prod(r, sv);
     }
   }
-  double bm = block_max(lmax, red_sh);
-  double bg = block_sum(gam, red_sh);
+  double bm = block_max_t(lmax, red_sh);
+  double bg = block_sum_acc(gam, red_sh);
   if (threadIdx.x == 0) {
     if (active) atomic_max_nonneg(&s.rmax_bits, bm);
     a.red.part[(long long)bl * gridDim.x + blockIdx.x] = bg;
@@ -301,7 +173,8 @@ __global__ void __launch_bounds__(256) k_jac_a(JacArgs<T> a) {
     for (int q = warp; q < a.BL; q += blockDim.x / 32) {
       double sum = warp_sum_partials(a.red.part + (long long)q * gridDim.x, gridDim.x, 1);
       CgScal& t = a.sc[q];
-      if (lane == 0 && !t.done && !t.need_replace) direction_update(t, sum, 0.0, 0);
+      if (lane == 0 && !t.done && !t.need_replace && (!a.after_replace || t.just_replaced))
+        direction_update(t, sum, 0.0, 0);
     }
     __syncthreads();
     if (threadIdx.x == 0) *a.red.ticket = 0u;
@@ -385,34 +258,41 @@ __global__ void k_zero_mean(double* u, const double* part, int nparts, int c, lo
     uf[i] -= mean;
 }
 
-// Averaged flux / stress per (instance, load) with the element-mean gradient, and optionally
-// the energy-form sensitivity sums.  One thread per element, all loads of an instance.
+// Averaged flux / stress per (instance, load) with the element-mean gradient.  One thread per
+// element, all loads of an instance; fixed-order warp and block reductions (deterministic).
 template <int CC>
 __global__ void __launch_bounds__(256) k_average(AvgArgs a) {
   __shared__ double mt[2 * 256];
-  __shared__ double acc_sh[6 * 8];  // [L<=8][dim<=6]
+  __shared__ double wsum[8][48];  // [warp][load * dim + i]
   const Grid& g = a.g;
   const int b = blockIdx.y;
   const int DIM = CC == 1 ? 3 : 6;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   load_material<double>(mt, a.mat, b);
-  for (int i = threadIdx.x; i < 6 * 8; i += blockDim.x) acc_sh[i] = 0.0;
   __syncthreads();
   int i1, i2, i3;
-  if (tile_node(g, i1, i2, i3)) {
-    const long long n = g.n;
-    const uint8_t* ph = a.phase + (long long)b * n;
-    const long long e = ((long long)i1 * g.n2 + i2) * g.n3 + i3;
-    const int p = ph[e];
-    for (int l = 0; l < a.L; ++l) {
+  const bool valid = tile_node(g, i1, i2, i3);
+  const long long n = g.n;
+  for (int l = 0; l < a.L; ++l) {
+    double sig[6] = {0, 0, 0, 0, 0, 0};
+    if (valid) {
+      const long long e = ((long long)i1 * g.n2 + i2) * g.n3 + i3;
+      const int p = a.phase[(long long)b * n + e];
       const double* u = a.u64 + ((long long)b * a.L + l) * CC * n;
-      double sig[6];
       element_mean_flux<CC>(u, mt, p, g, i1, i2, i3, a.loads + l * DIM, sig);
-      for (int i = 0; i < DIM; ++i) atomicAdd(&acc_sh[l * DIM + i], sig[i]);
+    }
+    for (int i = 0; i < DIM; ++i) {
+      double v = sig[i];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) wsum[warp][l * DIM + i] = v;
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < a.L * DIM; i += blockDim.x)
-    a.part[((long long)b * gridDim.x + blockIdx.x) * (8 * 6) + i] = acc_sh[i];
+  for (int q = threadIdx.x; q < a.L * DIM; q += blockDim.x) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += wsum[w][q];
+    a.part[((long long)b * gridDim.x + blockIdx.x) * (8 * 6) + q] = s;
+  }
 }
 
 __global__ void k_average_finish(double* out, const double* part, int nparts, int B, int L, int dim, double inv_n) {
@@ -479,8 +359,13 @@ static dim3 node_grid(const Grid& g, int y) {
 int node_blocks_x(const Grid& g) { return node_grid(g, 1).x; }
 
 static dim3 ku_grid(const Grid& g, int c, int y) {
+  // thermal: 32 x 8 x KU_TZ node tiles; elastic: 32 x 4 x 2 node blocks
   if (c != 1) return node_grid(g, y);
+#if UNOCG_KU_MODE == 0
+  int tx = (g.n3 + 31) / 32, ty = (g.n2 + 7) / 8, tz = (g.n1 + KU_TZ - 1) / KU_TZ;
+#else
   int tx = (g.n3 + 31) / 32, ty = (g.n2 + 7) / 8, tz = (g.n1 + KU_CZ - 1) / KU_CZ;
+#endif
   return dim3(tx * ty * tz, y);
 }
 int ku_blocks_x(const Grid& g, int c) { return ku_grid(g, c, 1).x; }

@@ -9,10 +9,10 @@
 namespace unocg {
 
 // Node handled by this thread: blocks of 32 (i3) x 4 (i2) x blockDim/128 (i1).
-__device__ __forceinline__ bool tile_node(const Grid& g, int& i1, int& i2, int& i3) {
+__device__ __forceinline__ bool tile_node_at(const Grid& g, int tile, int& i1, int& i2, int& i3) {
   const int tz_n = blockDim.x >> 7;
   const int nt3 = (g.n3 + 31) >> 5, nt2 = (g.n2 + 3) >> 2;
-  int bx = blockIdx.x;
+  int bx = tile;
   int b3 = bx % nt3;
   bx /= nt3;
   int b2 = bx % nt2;
@@ -21,6 +21,9 @@ __device__ __forceinline__ bool tile_node(const Grid& g, int& i1, int& i2, int& 
   i2 = b2 * 4 + ((threadIdx.x >> 5) & 3);
   i1 = b1 * tz_n + (threadIdx.x >> 7);
   return i1 < g.n1 && i2 < g.n2 && i3 < g.n3;
+}
+__device__ __forceinline__ bool tile_node(const Grid& g, int& i1, int& i2, int& i3) {
+  return tile_node_at(g, blockIdx.x, i1, i2, i3);
 }
 
 struct Nbr {
@@ -46,7 +49,14 @@ __device__ __forceinline__ long long eidx(const Nbr& nb, int o1, int o2, int o3)
   return nb.row[1 - o1][1 - o2] + nb.c3[1 - o3];
 }
 
-template <typename T, int CC>
+// Loads of fields that other blocks of the same launch may have written (persistent kernel)
+// bypass L1 (ld.global.cg); otherwise the read-only path is used.
+template <bool COH, typename T> __device__ __forceinline__ T ldf(const T* p) {
+  if (COH) return __ldcg(p);
+  return __ldg(p);
+}
+
+template <typename T, int CC, bool COH = false>
 __device__ __forceinline__ void node_Ku(const T* __restrict__ d, const uint8_t* __restrict__ ph,
                                         const T* mt, const Grid& g, int i1, int i2, int i3, T* out) {
   Nbr nb;
@@ -62,27 +72,27 @@ __device__ __forceinline__ void node_Ku(const T* __restrict__ d, const uint8_t* 
         for (int o3 = 0; o3 < 2; ++o3) k[o1][o2][o3] = mt[2 * __ldg(ph + eidx(nb, o1, o2, o3))];
     T sk = (k[0][0][0] + k[0][0][1]) + (k[0][1][0] + k[0][1][1]) + (k[1][0][0] + k[1][0][1]) +
            (k[1][1][0] + k[1][1][1]);
-    T acc = (T)4 * sk * __ldg(d + nidx(nb, 1, 1, 1));
+    T acc = (T)4 * sk * ldf<COH>(d + nidx(nb, 1, 1, 1));
 #pragma unroll
     for (int s2 = 0; s2 < 3; s2 += 2)
 #pragma unroll
       for (int s3 = 0; s3 < 3; s3 += 2) {
         const int o2 = s2 == 0, o3 = s3 == 0;
-        acc -= (k[0][o2][o3] + k[1][o2][o3]) * __ldg(d + nidx(nb, 1, s2, s3));
+        acc -= (k[0][o2][o3] + k[1][o2][o3]) * ldf<COH>(d + nidx(nb, 1, s2, s3));
       }
 #pragma unroll
     for (int s1 = 0; s1 < 3; s1 += 2)
 #pragma unroll
       for (int s3 = 0; s3 < 3; s3 += 2) {
         const int o1 = s1 == 0, o3 = s3 == 0;
-        acc -= (k[o1][0][o3] + k[o1][1][o3]) * __ldg(d + nidx(nb, s1, 1, s3));
+        acc -= (k[o1][0][o3] + k[o1][1][o3]) * ldf<COH>(d + nidx(nb, s1, 1, s3));
       }
 #pragma unroll
     for (int s1 = 0; s1 < 3; s1 += 2)
 #pragma unroll
       for (int s2 = 0; s2 < 3; s2 += 2) {
         const int o1 = s1 == 0, o2 = s2 == 0;
-        acc -= (k[o1][o2][0] + k[o1][o2][1]) * __ldg(d + nidx(nb, s1, s2, 1));
+        acc -= (k[o1][o2][0] + k[o1][o2][1]) * ldf<COH>(d + nidx(nb, s1, s2, 1));
       }
 #pragma unroll
     for (int s1 = 0; s1 < 3; s1 += 2)
@@ -90,8 +100,8 @@ __device__ __forceinline__ void node_Ku(const T* __restrict__ d, const uint8_t* 
       for (int s2 = 0; s2 < 3; s2 += 2)
 #pragma unroll
         for (int s3 = 0; s3 < 3; s3 += 2)
-          acc -= k[s1 == 0][s2 == 0][s3 == 0] * __ldg(d + nidx(nb, s1, s2, s3));
-    out[0] = acc * (T)(g.h / 12.0);
+          acc -= k[s1 == 0][s2 == 0][s3 == 0] * ldf<COH>(d + nidx(nb, s1, s2, s3));
+    out[0] = acc * grid_h12<T>(g);
   } else {
     T lam[8], mu[8];
 #pragma unroll
@@ -111,7 +121,7 @@ __device__ __forceinline__ void node_Ku(const T* __restrict__ d, const uint8_t* 
       const long long q = nidx(nb, s1, s2, s3);
       T dv[3];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) dv[k] = __ldg(d + k * n + q);
+      for (int k = 0; k < 3; ++k) dv[k] = ldf<COH>(d + k * n + q);
 #pragma unroll
       for (int o = 0; o < 8; ++o) {
         const int o1 = (o >> 2) & 1, o2 = (o >> 1) & 1, o3 = o & 1;
@@ -132,7 +142,7 @@ __device__ __forceinline__ void node_Ku(const T* __restrict__ d, const uint8_t* 
       T acc = (T)0;
 #pragma unroll
       for (int o = 0; o < 8; ++o) acc += lam[o] * aL[o][i] + mu[o] * aM[o][i];
-      out[i] = acc * (T)g.h;
+      out[i] = acc * grid_h<T>(g);
     }
   }
 }

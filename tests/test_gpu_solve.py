@@ -36,10 +36,12 @@ def config1():
 
 
 @pytest.mark.parametrize("pc", ["jacobi", "uno"])
-@pytest.mark.parametrize("use_graph", [1, 0])
+@pytest.mark.parametrize("use_graph", [1, 0, 2])
 def test_config1_fp64_matches_oracle(config1, pc, use_graph):
     from paper_2508_02681_gb300 import _lib
     w, ref = config1
+    if use_graph == 2 and pc == "jacobi":
+        pytest.skip("the persistent loop runs the UNO preconditioner")
     h = _solver(1, w["phase"], w["props"], w["loads"])
     precond = _lib.PRECOND_UNO if pc == "uno" else _lib.PRECOND_JACOBI
     info = h.solve(tol=w["tol"], max_iter=2000, precond=precond, precision=_lib.FP64, use_graph=use_graph)
@@ -53,7 +55,7 @@ def test_config1_fp64_matches_oracle(config1, pc, use_graph):
     h.close()
 
 
-@pytest.mark.parametrize("use_graph", [1, 0])
+@pytest.mark.parametrize("use_graph", [1, 0, 2])
 def test_config1_mixed_matches_oracle(config1, use_graph):
     from paper_2508_02681_gb300 import _lib
     w, ref = config1
@@ -66,8 +68,9 @@ def test_config1_mixed_matches_oracle(config1, use_graph):
     h.close()
 
 
+@pytest.mark.parametrize("use_graph", [1, 2])
 @pytest.mark.parametrize("precision", [0, 1])
-def test_elastic_small_matches_oracle(precision):
+def test_elastic_small_matches_oracle(precision, use_graph):
     from paper_2508_02681_gb300 import _lib
     phase, _ = rsa_spheres((8, 8, 8), 2.0, 0.3, seed=77)
     props = np.array([[1.0, 0.3], [10.0, 0.2]])
@@ -76,7 +79,7 @@ def test_elastic_small_matches_oracle(precision):
     ref = hz.solve(phase, props, 3, loads, precond="uno", tol=1e-12)
     Cref = hz.effective_tensor(phase, props, 3, ref["u"], loads)
     h = _solver(3, phase, props, loads)
-    info = h.solve(tol=tol, max_iter=2000, precond=_lib.PRECOND_UNO, precision=precision)
+    info = h.solve(tol=tol, max_iter=2000, precond=_lib.PRECOND_UNO, precision=precision, use_graph=use_graph)
     C = h.effective_tensor()[0]
     assert rel(C, Cref) < (1e-9 if precision == 0 else 1e-6)
     if precision == 0:
@@ -84,4 +87,39 @@ def test_elastic_small_matches_oracle(precision):
         for l in range(6):
             assert rel(h.fluctuation(0, l), ref8["u"][l]) < 1e-9
     assert np.all(info.true_rel_res <= tol)
+    h.close()
+
+
+def test_paths_agree_bitwise_on_fp64():
+    """The graph, host-driven and persistent loops run the same kernels in the same order of
+    reductions, so their FP64 iterates agree exactly."""
+    from paper_2508_02681_gb300 import _lib
+    phase, _ = rsa_spheres((16, 16, 16), 3.0, 0.25, seed=5)
+    props = np.array([1.0, 10.0])
+    h = _solver(1, phase, props, unit_loads(1))
+    out = []
+    for ug in (0, 1, 2):
+        info = h.solve(tol=1e-8, max_iter=500, precond=_lib.PRECOND_UNO, precision=_lib.FP64, use_graph=ug)
+        out.append((list(info.iters), h.fluctuation(0, 1), h.effective_tensor()[0]))
+    for o in out[1:]:
+        assert o[0] == out[0][0]
+        assert np.array_equal(o[1], out[0][1])
+        assert np.array_equal(o[2], out[0][2])
+    h.close()
+
+
+def test_device_wait_limit_reports_timeout_and_context_recovers():
+    """A grid-barrier wait that expires makes the persistent loop return DEVICE_TIMEOUT (no GPU
+    fault, no hang); with the default limit the same context solves normally afterwards."""
+    from paper_2508_02681_gb300 import _lib, api
+    phase, _ = rsa_spheres((16, 16, 16), 3.0, 0.25, seed=6)
+    props = np.array([1.0, 10.0])
+    h = _solver(1, phase, props, unit_loads(1))
+    api.unocg_set_wait_limit(h.ctx, 0.0)  # one clock cycle: every early block gives up
+    info = h.solve(raise_on_error=False, tol=1e-8, max_iter=500, precond=_lib.PRECOND_UNO,
+                   precision=_lib.FP64, use_graph=2)
+    assert info.status == _lib.ERR_DEVICE_TIMEOUT
+    api.unocg_set_wait_limit(h.ctx, 1.0)
+    info = h.solve(tol=1e-8, max_iter=500, precond=_lib.PRECOND_UNO, precision=_lib.FP64, use_graph=2)
+    assert info.status == _lib.OK
     h.close()
