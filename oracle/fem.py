@@ -212,3 +212,32 @@ def to_soa(u: np.ndarray, c: int, shape) -> np.ndarray:
 def from_soa(a: np.ndarray) -> np.ndarray:
     """Array ``[c, N1, N2, N3]`` -> interleaved DOF vector."""
     return np.ascontiguousarray(a.transpose(1, 2, 3, 0)).ravel()
+
+
+def residual_at_nodes(phase: np.ndarray, props, physics: int, u: np.ndarray, load, nodes,
+                      L0: float = 1.0) -> np.ndarray:
+    """``(f - K u)`` at the listed nodes ``[(i1, i2, i3), ...]``, one node at a time from the
+    element matrices of the (up to) 8 elements around it; no global assembly (for full-size
+    spot checks).  ``u`` interleaved; returns ``[len(nodes), c]``."""
+    shape = phase.shape
+    c = 1 if physics == 1 else 3
+    h = spacing(shape, L0)
+    props = np.asarray(props, dtype=np.float64)
+    Ks = [element_stiffness(physics, material_matrix(physics, props[p]), h) for p in range(props.shape[0])]
+    fs = [element_load(physics, material_matrix(physics, props[p]), load, h) for p in range(props.shape[0])]
+    N = np.asarray(shape)
+    out = np.zeros((len(nodes), c))
+    for q, node in enumerate(nodes):
+        node = np.asarray(node)
+        for a, o in enumerate(CORNERS):  # element e = node - o holds the node as corner a
+            e = (node - o) % N
+            p = phase[tuple(e)]
+            idx = []
+            for ob in CORNERS:
+                nb = (e + ob) % N
+                flat = (nb[0] * shape[1] + nb[1]) * shape[2] + nb[2]
+                idx.extend([c * flat + j for j in range(c)])
+            ue = u[np.array(idx)]
+            rows = slice(c * a, c * a + c)
+            out[q] += fs[p][rows] - Ks[p][rows] @ ue
+    return out

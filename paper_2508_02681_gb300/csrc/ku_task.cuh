@@ -127,7 +127,7 @@ __device__ __forceinline__ void ku_thermal_column(const T* __restrict__ d, T* __
 #define UNOCG_KU_TZ 4
 #endif
 #ifndef UNOCG_KU_MODE
-#define UNOCG_KU_MODE 0  // 0: shared-memory tile, 1: register column march
+#define UNOCG_KU_MODE 1  // 0: shared-memory tile, 1: register column march (measured faster)
 #endif
 constexpr int KU_TZ = UNOCG_KU_TZ;
 constexpr int KU_DN = (KU_TZ + 2) * 10 * 34;

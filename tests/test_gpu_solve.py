@@ -123,3 +123,120 @@ def test_device_wait_limit_reports_timeout_and_context_recovers():
     info = h.solve(tol=1e-8, max_iter=500, precond=_lib.PRECOND_UNO, precision=_lib.FP64, use_graph=2)
     assert info.status == _lib.OK
     h.close()
+
+
+@pytest.mark.parametrize("physics", [1, 3])
+def test_sensitivity_matches_oracle(physics):
+    """d(energy averages)/d(phase properties) from the converged fields (K self-adjoint: the
+    adjoint states are the forward solutions) against the oracle's energy-form derivative."""
+    from paper_2508_02681_gb300 import _lib
+    shape = (8, 8, 8) if physics == 1 else (6, 6, 6)
+    phase, _ = rsa_spheres(shape, 2.0, 0.3, seed=90)
+    props = np.array([1.0, 6.0]) if physics == 1 else np.array([[1.0, 0.3], [5.0, 0.2]])
+    loads = unit_loads(physics)[: (3 if physics == 1 else 3)]
+    h = _solver(physics, phase, props, loads)
+    h.solve(tol=1e-12, max_iter=3000, precond=_lib.PRECOND_UNO, precision=_lib.FP64)
+    S = h.sensitivity()[0]
+    us = [h.fluctuation(0, l) for l in range(len(loads))]
+    Sref = hz.sensitivity(phase, props, physics, us, loads)
+    assert rel(S, Sref) < 1e-11
+    h.close()
+
+
+def test_batched_instances_per_instance_weights():
+    """B instances in one context (own microstructure, contrast and reference medium each)."""
+    from paper_2508_02681_gb300 import _lib
+    from paper_2508_02681_gb300.solver import Homogenization
+    shape = (16, 16, 16)
+    B = 3
+    phases = np.stack([rsa_spheres(shape, 3.0, 0.2 + 0.05 * b, seed=100 + b)[0] for b in range(B)])
+    props = np.array([[1.0, 5.0 + 20.0 * b] for b in range(B)])
+    loads = unit_loads(1)
+    h = Homogenization(_lib.THERMAL, shape, batch=B)
+    h.set_microstructure(phases, 2)
+    h.set_phase_properties(props)
+    h.set_macro_load(loads)
+    h.set_uno_weights(_lib.W_REFERENCE_MEDIUM)
+    info = h.solve(tol=1e-10, max_iter=2000, precond=_lib.PRECOND_UNO, precision=_lib.FP64)
+    C = h.effective_tensor()
+    for b in range(B):
+        ref = hz.solve(phases[b], props[b], 1, loads, "uno", tol=1e-10)
+        Cref = hz.effective_tensor(phases[b], props[b], 1, ref["u"], loads)
+        assert rel(C[b], Cref) < 1e-9
+        assert list(info.iters[3 * b:3 * b + 3]) == ref["iters"]
+        assert rel(h.fluctuation(b, 2), ref["u"][2]) < 1e-8
+    h.close()
+
+
+def test_batch_solve_uneven_grid_sizes():
+    """Several contexts of different grid sizes solved together, each with its own masks."""
+    from paper_2508_02681_gb300 import _lib, api
+    from paper_2508_02681_gb300.solver import Homogenization
+    sizes = [16, 24, 32]
+    hs, refs = [], []
+    for i, N in enumerate(sizes):
+        ph, _ = rsa_spheres((N, N, N), 3.0, 0.3, seed=200 + i)
+        props = np.array([1.0, 10.0 * (i + 1)])
+        h = Homogenization(_lib.THERMAL, (N, N, N))
+        h.set_microstructure(ph, 2)
+        h.set_phase_properties(props)
+        h.set_macro_load(unit_loads(1))
+        h.set_uno_weights(_lib.W_REFERENCE_MEDIUM)
+        hs.append(h)
+        refs.append((ph, props))
+    api.unocg_batch_solve([h.ctx for h in hs], api.make_opts(tol=1e-6, max_iter=2000, precision=_lib.MIXED))
+    for h, (ph, props) in zip(hs, refs):
+        ref = hz.solve(ph, props, 1, unit_loads(1), "uno", tol=1e-10)
+        Cref = hz.effective_tensor(ph, props, 1, ref["u"], unit_loads(1))
+        assert rel(h.effective_tensor()[0], Cref) < 1e-6
+        h.close()
+
+
+def _full_size_checks(w, precision, tol):
+    from paper_2508_02681_gb300 import _lib
+    from oracle import fem
+    physics = w["physics"]
+    h = _solver(physics, w["phase"], w["props"], w["loads"])
+    info = h.solve(tol=tol, max_iter=3000, precond=_lib.PRECOND_UNO, precision=precision)
+    C = h.effective_tensor()[0]
+    assert np.all(info.true_rel_res <= tol)
+    # symmetric, inside the Voigt / Reuss bounds
+    Ds = [fem.material_matrix(physics, p) for p in w["props"]]
+    vf = float(w["phase"].mean())
+    voigt = (1 - vf) * Ds[0] + vf * Ds[1]
+    reuss = np.linalg.inv((1 - vf) * np.linalg.inv(Ds[0]) + vf * np.linalg.inv(Ds[1]))
+    Cs = 0.5 * (C + C.T)
+    assert np.max(np.abs(C - C.T)) < 1e-5 * np.max(np.abs(C))
+    assert np.linalg.eigvalsh(voigt - Cs).min() > -1e-8
+    assert np.linalg.eigvalsh(Cs - reuss).min() > -1e-8
+    # oracle, node by node: f - K u at sampled nodes, relative to ||f||_inf
+    rng = np.random.default_rng(5)
+    N = w["phase"].shape
+    nodes = [tuple(int(x) for x in rng.integers(0, N[0], size=3)) for _ in range(24)]
+    for l in range(0, len(w["loads"]), 2):
+        u = h.fluctuation(0, l)
+        f0 = fem.residual_at_nodes(w["phase"], w["props"], physics, np.zeros_like(u), w["loads"][l], nodes)
+        fmax = np.max(np.abs(fem.assemble_f(w["phase"], w["props"], physics, w["loads"][l]))) if physics == 1 else None
+        res = fem.residual_at_nodes(w["phase"], w["props"], physics, u, w["loads"][l], nodes)
+        scale = fmax if fmax is not None else np.max(np.abs(f0))
+        assert np.max(np.abs(res)) <= 2 * tol * max(scale, 1e-300) + 1e-14
+        # the averaged flux of the oracle from the GPU field equals the GPU tensor column
+        if physics == 1:
+            Co = hz.effective_tensor(w["phase"], w["props"], 1, [u], w["loads"][l:l + 1])
+            assert rel(Co[:, 0], C[:, l]) < 1e-12
+    h.close()
+    return C
+
+
+def test_full_size_thermal_64():
+    w = workload(2)
+    C64 = _full_size_checks(w, 0, 1e-6)
+    Cmx = _full_size_checks(w, 1, 1e-6)
+    assert rel(Cmx, C64) < 1e-6
+
+
+def test_full_size_elastic_64():
+    w = workload(3)
+    C64 = _full_size_checks(w, 0, 1e-6)
+    Cmx = _full_size_checks(w, 1, 1e-6)
+    assert rel(Cmx, C64) < 1e-6

@@ -1,0 +1,117 @@
+"""GPU UNO operator for training (Sec. 5.3, Algorithm 3): FP32 apply s = P_theta r and the
+hand-written backward (input gradient P g and weight gradient through psi), against the FP64
+oracle and central finite differences of the loss of Eq. (fnocg-loss)."""
+import numpy as np
+import pytest
+
+from oracle import training, uno
+from synth import random_field
+from tests.gpu_util import rel
+
+pytestmark = pytest.mark.gpu
+
+
+def _theta(shape, c, seed):
+    rng = np.random.default_rng(seed)
+    C = c * (c + 1) // 2
+    th = rng.standard_normal((shape[0], shape[1], shape[2] // 2 + 1, C)) * 0.3
+    th[..., 0] += 1.0
+    if c == 3:
+        th[..., 1] += 1.0
+        th[..., 3] += 1.0
+    return th
+
+
+@pytest.mark.parametrize("c,shape", [(1, (8, 6, 10)), (3, (6, 8, 8)), (1, (32, 32, 32))])
+def test_apply_fp32_matches_oracle(c, shape):
+    import torch
+    from paper_2508_02681_gb300 import api
+    th = _theta(shape, c, 1)
+    B = 2
+    r = np.stack([random_field((c,) + shape, seed=10 + b) for b in range(B)])
+    op = api.unocg_uno_create(c, *shape)
+    tt = torch.tensor(th, dtype=torch.float32, device="cuda")
+    api.unocg_uno_set_theta_dev(op, tt)
+    rr = torch.tensor(r, dtype=torch.float32, device="cuda")
+    ss = torch.empty_like(rr)
+    api.unocg_uno_apply_dev(op, B, rr, ss)
+    torch.cuda.synchronize()
+    Q = uno.symmetrize_half(uno.psi(th.astype(np.float32).astype(np.float64), c), shape[2])
+    for b in range(B):
+        assert rel(ss[b].cpu().numpy().astype(np.float64), uno.uno_apply(Q, r[b])) < 2e-5
+    api.unocg_uno_destroy(op)
+
+
+@pytest.mark.parametrize("c,shape", [(1, (6, 8, 8)), (3, (4, 6, 8))])
+def test_backward_matches_oracle_gradient_and_fd(c, shape):
+    import torch
+    from paper_2508_02681_gb300 import api
+    th = _theta(shape, c, 2).astype(np.float32).astype(np.float64)
+    B = 3
+    f = np.stack([random_field((c,) + shape, seed=20 + b) for b in range(B)])
+    u = np.stack([random_field((c,) + shape, seed=40 + b) for b in range(B)])
+    N3 = shape[2]
+
+    def loss(theta):
+        return training.loss_by_definition(uno.symmetrize_half(uno.psi(theta, c), N3), f, u)
+
+    Q = uno.symmetrize_half(uno.psi(th, c), N3)
+    s = np.stack([uno.uno_apply(Q, f[b]) for b in range(B)])
+    gs = 2.0 * (s - u) / B  # dL/ds
+    op = api.unocg_uno_create(c, *shape)
+    tt = torch.tensor(th, dtype=torch.float32, device="cuda")
+    api.unocg_uno_set_theta_dev(op, tt)
+    fr = torch.tensor(f, dtype=torch.float32, device="cuda")
+    gg = torch.tensor(gs, dtype=torch.float32, device="cuda")
+    gr = torch.empty_like(fr)
+    gt = torch.empty_like(tt)
+    api.unocg_uno_backward_dev(op, B, fr, gg, gr, gt)
+    torch.cuda.synchronize()
+    # input gradient: P is self-adjoint
+    for b in range(B):
+        assert rel(gr[b].cpu().numpy().astype(np.float64), uno.uno_apply(Q, gs[b])) < 2e-5
+    gt = gt.cpu().numpy().astype(np.float64)
+    # weight gradient against central differences of the oracle loss
+    rng = np.random.default_rng(7)
+    flat = th.reshape(-1)
+    for _ in range(6):
+        i = int(rng.integers(flat.size))
+        eps = 1e-4
+        tp, tm = flat.copy(), flat.copy()
+        tp[i] += eps
+        tm[i] -= eps
+        fd = (loss(tp.reshape(th.shape)) - loss(tm.reshape(th.shape))) / (2 * eps)
+        assert gt.reshape(-1)[i] == pytest.approx(fd, rel=2e-3, abs=2e-4 * max(1.0, np.max(np.abs(gt))))
+    api.unocg_uno_destroy(op)
+
+
+def test_autograd_function_trains_toward_the_fundamental_solution():
+    """A few Adam steps of Algorithm 3 on solver data decrease the loss of Eq. (fnocg-loss)."""
+    import torch
+    from paper_2508_02681_gb300 import api
+    from paper_2508_02681_gb300.solver import uno_function
+    shape = (16, 16, 16)
+    c = 1
+    rng = np.random.default_rng(3)
+    # targets: u = P_ref f for a reference-medium preconditioner (a known optimum of the loss)
+    Qref = uno.reference_medium_Q(1, [1.0, 1.0], shape)
+    f = np.stack([random_field((c,) + shape, seed=60 + b) for b in range(4)])
+    f -= f.mean(axis=(1, 2, 3, 4), keepdims=True)
+    u = np.stack([uno.uno_apply(Qref, f[b]) for b in range(4)])
+    theta0 = np.full((16, 16, 9, 1), 0.05) + 0.01 * rng.standard_normal((16, 16, 9, 1))
+    theta = torch.tensor(theta0, dtype=torch.float32, device="cuda", requires_grad=True)
+    F = torch.tensor(f, dtype=torch.float32, device="cuda")
+    U = torch.tensor(u, dtype=torch.float32, device="cuda")
+    op = api.unocg_uno_create(c, *shape)
+    Fn = uno_function()
+    opt = torch.optim.Adam([theta], lr=1e-2)
+    losses = []
+    for _ in range(30):
+        opt.zero_grad()
+        s = Fn.apply(F, theta, op)
+        L = ((s - U) ** 2).sum() / F.shape[0]
+        L.backward()
+        opt.step()
+        losses.append(float(L))
+    api.unocg_uno_destroy(op)
+    assert losses[-1] < 0.5 * losses[0]

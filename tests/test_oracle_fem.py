@@ -152,3 +152,21 @@ def test_thermal_rhs_corner_signs():
                     node = ((i1 + o[0]) % 4, (i2 + o[1]) % 4, (i3 + o[2]) % 4)
                     ref[node] -= kap[phase[i1, i2, i3]] * h * h / 4 * np.dot(2 * o - 1, g)
     assert np.max(np.abs(f - ref.ravel())) < 1e-15
+
+
+@pytest.mark.parametrize("physics,props", [(1, [1.0, 4.0]), (3, [[1.0, 0.3], [4.0, 0.2]])])
+def test_residual_at_nodes_matches_assembly(physics, props):
+    shape = (4, 5, 6)
+    phase = random_phase(shape, 2, seed=21)
+    c = 1 if physics == 1 else 3
+    rng = np.random.default_rng(3)
+    u = rng.standard_normal(c * int(np.prod(shape)))
+    load = rng.standard_normal(3 if physics == 1 else 6)
+    K = fem.assemble_K(phase, props, physics)
+    f = fem.assemble_f(phase, props, physics, load)
+    full = (f - K @ u).reshape(-1, c)
+    nodes = [(0, 0, 0), (3, 4, 5), (1, 2, 3), (2, 0, 5)]
+    got = fem.residual_at_nodes(phase, props, physics, u, load, nodes)
+    for q, nd in enumerate(nodes):
+        flat = (nd[0] * shape[1] + nd[1]) * shape[2] + nd[2]
+        assert np.max(np.abs(got[q] - full[flat])) < 1e-13
