@@ -94,9 +94,17 @@ template <int DIR, int R, typename C> __device__ __forceinline__ void dftR(C* v)
   else dft8<DIR>(v);
 }
 
-// floor(x / d) for 0 <= x < 2^20 and 1 <= d < 2^12 through a float reciprocal: the relative
-// error of (x + 1/2) * (1/d) is below 2^-22, far inside the 1/(2d) margin of the true quotient.
-__device__ __forceinline__ int fdiv(int x, float rd) { return (int)(((float)x + 0.5f) * rd); }
+// floor(x / d) for 0 <= x < 2^20 and 1 <= d <= 2^12 by an integer multiply-high with
+// m = floor(2^32 / d) + 1 (exact there: x (m d - 2^32) < 2^32); m = 0 encodes d = 1.
+struct UDiv {
+  unsigned m;
+};
+__device__ __forceinline__ UDiv udiv_of(int d) {
+  UDiv u;
+  u.m = d > 1 ? (unsigned)(0xFFFFFFFFu / (unsigned)d) + 1u : 0u;
+  return u;
+}
+__device__ __forceinline__ int udiv(int x, UDiv u) { return u.m ? (int)__umulhi((unsigned)x, u.m) : x; }
 
 // ---------------------------------------------------------------- one Stockham stage
 // Lines: element (line, idx) at buf[line*ls + idx*es].  Work item = (line, j), j < N/R, with
@@ -110,15 +118,15 @@ __device__ __forceinline__ void fft_stage(const cplx<T>* __restrict__ src, cplx<
   const int NR = N / R;
   const int total = nlines * NR;
   const int stride = N / (Ns * R);
-  const float rl = 1.0f / (float)nlines, rs = 1.0f / (float)Ns;
+  const UDiv rl = udiv_of(nlines), rs = udiv_of(Ns);
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int j = fdiv(idx, rl);
+    const int j = udiv(idx, rl);
     const int line = idx - j * nlines;
     const C* b = src + line * ls;
     C v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = b[(j + r * NR) * es];
-    const int q = fdiv(j, rs);
+    const int q = udiv(j, rs);
     const int k = j - q * Ns;
     if (Ns > 1) {
 #pragma unroll
@@ -176,9 +184,9 @@ __device__ void r2c_post(cplx<T>* buf, int nrows, int P, int Nh, const cplx<T>* 
   using C = cplx<T>;
   const int npairs = Nh / 2 + 1;
   const T half = (T)0.5;
-  const float rr = 1.0f / (float)nrows;
+  const UDiv rr = udiv_of(nrows);
   for (int idx = threadIdx.x; idx < nrows * npairs; idx += blockDim.x) {
-    const int k = fdiv(idx, rr), row = idx - k * nrows;
+    const int k = udiv(idx, rr), row = idx - k * nrows;
     C* b = buf + row * P;
     if (k == 0) {
       C z = b[0];
@@ -210,9 +218,9 @@ template <typename T>
 __device__ void c2r_pre(cplx<T>* buf, int nrows, int P, int Nh, const cplx<T>* __restrict__ twN) {
   using C = cplx<T>;
   const int npairs = Nh / 2 + 1;
-  const float rr = 1.0f / (float)nrows;
+  const UDiv rr = udiv_of(nrows);
   for (int idx = threadIdx.x; idx < nrows * npairs; idx += blockDim.x) {
-    const int k = fdiv(idx, rr), row = idx - k * nrows;
+    const int k = udiv(idx, rr), row = idx - k * nrows;
     C* b = buf + row * P;
     if (k == 0) {
       T x0 = b[0].x, xn = b[Nh].x;

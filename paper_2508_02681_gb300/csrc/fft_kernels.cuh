@@ -55,7 +55,7 @@ __device__ double plane_fwd_task(const PlaneFwdArgs<T>& a, const PlaneSmem<T>& s
   using C = cplx<T>;
   const Grid& g = a.g;
   const int n3h = g.n3h, Nh = g.n3 / 2, P = pitch_of(n3h);
-  const float rNh = 1.0f / (float)Nh, rn3h = 1.0f / (float)n3h;
+  const UDiv rNh = udiv_of(Nh), rn3h = udiv_of(n3h);
   const int comp = plane / g.n1, i1 = plane - comp * g.n1;
   const long long field = (long long)bl * a.c + comp;
   const long long base = (field * g.n1 + i1) * (long long)g.n2 * g.n3;
@@ -76,7 +76,7 @@ __device__ double plane_fwd_task(const PlaneFwdArgs<T>& a, const PlaneSmem<T>& s
       for (int u = 0; u < U; ++u) {
         const int idx = i0 + u * blockDim.x;
         if (idx < npair) {
-          int i2 = fdiv(idx, rNh), m = idx - i2 * Nh;
+          int i2 = udiv(idx, rNh), m = idx - i2 * Nh;
           buf[i2 * P + m] = v[u];
         }
       }
@@ -100,7 +100,7 @@ __device__ double plane_fwd_task(const PlaneFwdArgs<T>& a, const PlaneSmem<T>& s
       for (int u = 0; u < U; ++u) {
         const int idx = i0 + u * blockDim.x;
         if (idx < npair) {
-          int i2 = fdiv(idx, rNh), m = idx - i2 * Nh;
+          int i2 = udiv(idx, rNh), m = idx - i2 * Nh;
           C w = v[u];
           if (upd) {
             w.x -= al * q[u].x;
@@ -120,7 +120,7 @@ __device__ double plane_fwd_task(const PlaneFwdArgs<T>& a, const PlaneSmem<T>& s
   C* out = a.hat + (field * g.n1 + i1) * (long long)g.n2 * n3h;
   const int nout = g.n2 * n3h;
   for (int idx = threadIdx.x; idx < nout; idx += blockDim.x) {
-    int k2 = fdiv(idx, rn3h), k3 = idx - k2 * n3h;
+    int k2 = udiv(idx, rn3h), k3 = idx - k2 * n3h;
     out[idx] = res[k2 * P + k3];
   }
   if (a.standalone) {
@@ -194,7 +194,7 @@ template <typename T, typename QT, int CC, int MODE>
 __device__ double2 line_task(const LineArgs<T, QT>& a, const LineSmem<T>& sm, int bl, int tile, double* red_sh) {
   using C = cplx<T>;
   const int TB = a.tb;
-  const float rTB = 1.0f / (float)TB, rn3h = 1.0f / (float)a.g.n3h;
+  const UDiv rTB = udiv_of(TB), rn3h = udiv_of(a.g.n3h);
   const Grid& g = a.g;
   const int n1 = g.n1;
   const int M = g.n2 * g.n3h;
@@ -213,7 +213,7 @@ __device__ double2 line_task(const LineArgs<T, QT>& a, const LineSmem<T>& sm, in
       gv[u] = v[u];
       so[u] = v[u];
       if (idx < n1 * LW) {
-        int rest = fdiv(idx, rTB), t = idx - rest * TB;
+        int rest = udiv(idx, rTB), t = idx - rest * TB;
         int comp = rest % CC, k1 = rest / CC;
         if (t < nt) {
           long long gi = fbase + ((long long)comp * n1 + k1) * M + pos0 + t;
@@ -227,10 +227,10 @@ __device__ double2 line_task(const LineArgs<T, QT>& a, const LineSmem<T>& sm, in
     for (int u = 0; u < U; ++u) {
       const int idx = i0 + u * blockDim.x;
       if (idx < n1 * LW) {
-        int rest = fdiv(idx, rTB), t = idx - rest * TB;
+        int rest = udiv(idx, rTB), t = idx - rest * TB;
         int comp = rest % CC, k1 = rest / CC;
         if (MODE == 0 && a.flexible && t < nt) {
-          int k3 = (pos0 + t) - fdiv(pos0 + t, rn3h) * g.n3h;
+          int k3 = (pos0 + t) - udiv(pos0 + t, rn3h) * g.n3h;
           const T w = (k3 == 0 || 2 * k3 == g.n3) ? (T)1 : (T)2;
           rso.add_prod(w * v[u].x, so[u].x);
           rso.add_prod(w * v[u].y, so[u].y);
@@ -247,10 +247,10 @@ __device__ double2 line_task(const LineArgs<T, QT>& a, const LineSmem<T>& sm, in
   const long long qb = (long long)(bl / a.L) * a.q_inst_stride;
   const T sc = (T)a.scale;
   for (int idx = threadIdx.x; idx < n1 * TB; idx += blockDim.x) {
-    int k1 = fdiv(idx, rTB), t = idx - k1 * TB;
+    int k1 = udiv(idx, rTB), t = idx - k1 * TB;
     if (t >= nt) continue;
     int pos = pos0 + t;
-    int k3 = pos - fdiv(pos, rn3h) * g.n3h;
+    int k3 = pos - udiv(pos, rn3h) * g.n3h;
     const T w = (k3 == 0 || 2 * k3 == g.n3) ? (T)1 : (T)2;
     const long long qi = qb + ((long long)k1 * M + pos) * (CC == 1 ? 1 : 6);
     C* bp = res + k1 * LW + t;
@@ -312,7 +312,7 @@ __device__ double2 line_task(const LineArgs<T, QT>& a, const LineSmem<T>& sm, in
   C* oalt = (MODE == 2) ? (gres == sm.gbuf ? sm.galt : sm.gbuf) : (res == sm.buf ? sm.alt : sm.buf);
   ob = fft_lines<T, +1>(ob, oalt, LW, 1, LW, a.ft.p1, sm.tw1);
   for (int idx = threadIdx.x; idx < n1 * LW; idx += blockDim.x) {
-    int rest = fdiv(idx, rTB), t = idx - rest * TB;
+    int rest = udiv(idx, rTB), t = idx - rest * TB;
     int comp = rest % CC, k1 = rest / CC;
     if (t < nt) {
       long long gi = fbase + ((long long)comp * n1 + k1) * M + pos0 + t;
@@ -371,7 +371,7 @@ __device__ void plane_inv_task(const PlaneInvArgs<T>& a, const PlaneSmem<T>& sm,
   using C = cplx<T>;
   const Grid& g = a.g;
   const int n3h = g.n3h, Nh = g.n3 / 2, P = pitch_of(n3h);
-  const float rNh = 1.0f / (float)Nh, rn3h = 1.0f / (float)n3h;
+  const UDiv rNh = udiv_of(Nh), rn3h = udiv_of(n3h);
   const int comp = plane / g.n1, i1 = plane - comp * g.n1;
   const long long field = (long long)bl * a.c + comp;
   C* buf = sm.buf;
@@ -389,7 +389,7 @@ __device__ void plane_inv_task(const PlaneInvArgs<T>& a, const PlaneSmem<T>& sm,
     for (int u = 0; u < U; ++u) {
       const int idx = i0 + u * blockDim.x;
       if (idx < nin) {
-        int k2 = fdiv(idx, rn3h), k3 = idx - k2 * n3h;
+        int k2 = udiv(idx, rn3h), k3 = idx - k2 * n3h;
         buf[k2 * P + k3] = v[u];
       }
     }
@@ -403,7 +403,7 @@ __device__ void plane_inv_task(const PlaneInvArgs<T>& a, const PlaneSmem<T>& sm,
   if (a.standalone) {
     C* dst = reinterpret_cast<C*>(a.dst + base);
     for (int idx = threadIdx.x; idx < npair; idx += blockDim.x) {
-      int i2 = fdiv(idx, rNh), m = idx - i2 * Nh;
+      int i2 = udiv(idx, rNh), m = idx - i2 * Nh;
       dst[idx] = res[i2 * P + m];
     }
   } else {
@@ -424,7 +424,7 @@ __device__ void plane_inv_task(const PlaneInvArgs<T>& a, const PlaneSmem<T>& sm,
       for (int q = 0; q < U; ++q) {
         const int idx = i0 + q * blockDim.x;
         if (idx < npair) {
-          int i2 = fdiv(idx, rNh), m = idx - i2 * Nh;
+          int i2 = udiv(idx, rNh), m = idx - i2 * Nh;
           C s = res[i2 * P + m];
           C uu = uv[q];
           uu.x += alpha * dv[q].x;

@@ -85,33 +85,32 @@ def test_backward_matches_oracle_gradient_and_fd(c, shape):
     api.unocg_uno_destroy(op)
 
 
-def test_autograd_function_trains_toward_the_fundamental_solution():
-    """A few Adam steps of Algorithm 3 on solver data decrease the loss of Eq. (fnocg-loss)."""
+def test_autograd_function_training_decreases_loss():
+    """Adam steps of Algorithm 3 (gradients from the hand-written backward through the
+    autograd Function) reduce the loss of Eq. (fnocg-loss) toward a known optimum."""
     import torch
     from paper_2508_02681_gb300 import api
     from paper_2508_02681_gb300.solver import uno_function
     shape = (16, 16, 16)
     c = 1
     rng = np.random.default_rng(3)
-    # targets: u = P_ref f for a reference-medium preconditioner (a known optimum of the loss)
-    Qref = uno.reference_medium_Q(1, [1.0, 1.0], shape)
+    th_target = 1.0 + 0.3 * rng.standard_normal((16, 16, 9, 1))
+    Qt = uno.symmetrize_half(uno.psi(th_target, 1), 16)
     f = np.stack([random_field((c,) + shape, seed=60 + b) for b in range(4)])
-    f -= f.mean(axis=(1, 2, 3, 4), keepdims=True)
-    u = np.stack([uno.uno_apply(Qref, f[b]) for b in range(4)])
-    theta0 = np.full((16, 16, 9, 1), 0.05) + 0.01 * rng.standard_normal((16, 16, 9, 1))
-    theta = torch.tensor(theta0, dtype=torch.float32, device="cuda", requires_grad=True)
+    u = np.stack([uno.uno_apply(Qt, f[b]) for b in range(4)])
+    theta = torch.tensor(0.5 * th_target, dtype=torch.float32, device="cuda", requires_grad=True)
     F = torch.tensor(f, dtype=torch.float32, device="cuda")
     U = torch.tensor(u, dtype=torch.float32, device="cuda")
     op = api.unocg_uno_create(c, *shape)
     Fn = uno_function()
-    opt = torch.optim.Adam([theta], lr=1e-2)
+    opt = torch.optim.Adam([theta], lr=5e-2)
     losses = []
-    for _ in range(30):
+    for _ in range(60):
         opt.zero_grad()
         s = Fn.apply(F, theta, op)
         L = ((s - U) ** 2).sum() / F.shape[0]
         L.backward()
         opt.step()
-        losses.append(float(L))
+        losses.append(float(L.detach()))
     api.unocg_uno_destroy(op)
-    assert losses[-1] < 0.5 * losses[0]
+    assert losses[-1] < 0.05 * losses[0]
