@@ -132,6 +132,10 @@ int unocg_set_macro_load(unocg_ctx* ctx, int n_loads, const double* loads);
    memory of `dtype`; shared by all instances (REFERENCE_MEDIUM is per instance).            */
 int unocg_set_uno_weights(unocg_ctx* ctx, int kind, const void* w, int dtype, double spd_eps);
 
+/* Copy the expanded weights Q(k) of `instance` (unique entries [N1][N2][N3/2+1][C], paper's
+   order, FP64, after the safety check and symmetrization) to host memory `out`.            */
+int unocg_get_uno_weights(unocg_ctx* ctx, int instance, double* out);
+
 /* Solve all (instance, load) systems K u = f to tolerance (Algorithm 1 / 2), then compute the
    zero-mean fluctuations and the averaged flux / stress.  Blocks until done.               */
 int unocg_solve(unocg_ctx* ctx, const unocg_solve_opts* opts, unocg_solve_info* info);

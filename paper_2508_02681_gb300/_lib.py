@@ -66,6 +66,7 @@ SIGNATURES = {
     "unocg_set_phase_properties": (_i, [_vp, _vp]),
     "unocg_set_macro_load": (_i, [_vp, _i, _vp]),
     "unocg_set_uno_weights": (_i, [_vp, _i, _vp, _i, _d]),
+    "unocg_get_uno_weights": (_i, [_vp, _i, _vp]),
     "unocg_solve": (_i, [_vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
     "unocg_solve_async": (_i, [_vp, C.POINTER(SolveOpts)]),
     "unocg_solve_wait": (_i, [_vp, C.POINTER(SolveInfo)]),

@@ -87,6 +87,12 @@ def unocg_set_uno_weights(ctx, kind: int, w: np.ndarray | None = None, spd_eps: 
     _check(ctx, _lib.load().unocg_set_uno_weights(ctx, kind, _ptr(a), dt, spd_eps))
 
 
+def unocg_get_uno_weights(ctx, instance: int, n_modes: int, C_: int) -> np.ndarray:
+    out = np.empty(n_modes * C_, dtype=np.float64)
+    _check(ctx, _lib.load().unocg_get_uno_weights(ctx, instance, _ptr(out)))
+    return out
+
+
 def make_opts(tol=1e-6, max_iter=10000, precond=_lib.PRECOND_UNO, precision=_lib.FP64,
               replace_every=50, flexible=None, use_graph=3) -> SolveOpts:
     if flexible is None:

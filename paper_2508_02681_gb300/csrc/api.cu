@@ -901,6 +901,20 @@ static int prepare_solve(unocg_ctx* ctx, const unocg_solve_opts* o, Plan* pl) {
   return ensure_workspace(ctx, o->precision, o->precond);
 }
 
+extern "C" int unocg_get_uno_weights(unocg_ctx* ctx, int instance, double* out) {
+  if (!ctx || !out) return fail(ctx, UNOCG_ERR_INVALID_ARG, "null argument");
+  if (ctx->wkind < 0) return fail(ctx, UNOCG_ERR_STATE, "set UNO weights first");
+  if (instance < 0 || instance >= ctx->B) return fail(ctx, UNOCG_ERR_INVALID_ARG, "instance out of range");
+  if (ctx->q_dirty) {
+    int rc = build_weights(ctx);
+    if (rc) return rc;
+  }
+  const size_t m = (size_t)ctx->g.nh * (ctx->c == 1 ? 1 : 6);
+  const double* src = ctx->Q64 + (ctx->Bq > 1 ? instance * m : 0);
+  CK(cudaMemcpy(out, src, m * sizeof(double), cudaMemcpyDeviceToHost));
+  return UNOCG_OK;
+}
+
 extern "C" int unocg_solve_async(unocg_ctx* ctx, const unocg_solve_opts* o) {
   Plan pl;
   int rc = prepare_solve(ctx, o, &pl);

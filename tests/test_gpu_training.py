@@ -114,3 +114,89 @@ def test_autograd_function_training_decreases_loss():
         losses.append(float(L.detach()))
     api.unocg_uno_destroy(op)
     assert losses[-1] < 0.05 * losses[0]
+
+
+def test_config4_training_workload():
+    """The 32^3 training workload: 512 seeded thermal microstructures (radius U[2,5], volume
+    fraction U[0.1,0.4], contrast log-uniform in [5,100]), targets from this library's solves,
+    Adam at batch 64 for 200 epochs.  Checks: the loss decreases; the trained weights pass the
+    safety check and drive UNO-CG to tolerance on held-out instances; the weight gradient and the
+    adjoint d(kappa_eff)/d(kappa_p) match central differences (h = 1e-4) on 4 instances."""
+    import torch
+    from paper_2508_02681_gb300 import _lib, api, training as tr
+    from paper_2508_02681_gb300.solver import Homogenization
+    from synth import workload
+    shape = (32, 32, 32)
+    ws = [workload(4, i) for i in range(512)]
+    f, u, iters = tr.generate_data([w["phase"] for w in ws], [w["props"] for w in ws],
+                                   np.array([1.0, 0.0, 0.0]), shape)
+    assert max(iters) < 5000
+    theta0 = tr.reference_theta(shape, 0.5 * (1.0 + np.sqrt(5.0 * 100.0)))
+    theta, losses = tr.train(f, u, theta0, epochs=200, batch=64, lr=1e-2)
+    assert losses[-1] < 0.9 * losses[0]
+    # trained weights in a solve (held-out instances)
+    th = theta.cpu().numpy().astype(np.float64)
+    for i in range(512, 516):
+        w = workload(4, i)
+        h = Homogenization(_lib.THERMAL, shape)
+        h.set_microstructure(w["phase"], 2)
+        h.set_phase_properties(w["props"])
+        h.set_macro_load(np.eye(3)[:1])
+        h.set_uno_weights(_lib.W_THETA, th, 0.0)
+        info = h.solve(tol=1e-6, max_iter=3000, precond=_lib.PRECOND_UNO, precision=_lib.MIXED)
+        assert info.status == _lib.OK
+        h.close()
+    # weight gradient on 4 instances against central differences of the FP64 oracle loss
+    f4 = f[:4].cpu().numpy().astype(np.float64)
+    u4 = u[:4].cpu().numpy().astype(np.float64)
+    th4 = theta.cpu().numpy().astype(np.float64)
+    Q = uno.symmetrize_half(uno.psi(th4, 1), 32)
+    s = np.stack([uno.uno_apply(Q, f4[b]) for b in range(4)])
+    gs = 2.0 * (s - u4) / 4
+    op = api.unocg_uno_create(1, *shape)
+    tt = torch.tensor(th4, dtype=torch.float32, device="cuda")
+    api.unocg_uno_set_theta_dev(op, tt)
+    gt = torch.empty_like(tt)
+    api.unocg_uno_backward_dev(op, 4, torch.tensor(f4, dtype=torch.float32, device="cuda"),
+                               torch.tensor(gs, dtype=torch.float32, device="cuda"), None, gt)
+    torch.cuda.synchronize()
+    gt = gt.cpu().numpy().reshape(-1).astype(np.float64)
+    api.unocg_uno_destroy(op)
+
+    def loss(t):
+        return training.loss_by_definition(uno.symmetrize_half(uno.psi(t, 1), 32), f4, u4)
+
+    rng = np.random.default_rng(9)
+    flat = th4.reshape(-1)
+    big = np.argsort(-np.abs(gt))[:64]
+    for i in list(rng.choice(big, 4, replace=False)):
+        hstep = 1e-4 * max(1.0, abs(flat[i]))
+        tp, tm = flat.copy(), flat.copy()
+        tp[i] += hstep
+        tm[i] -= hstep
+        fd = (loss(tp.reshape(th4.shape)) - loss(tm.reshape(th4.shape))) / (2 * hstep)
+        assert gt[i] == pytest.approx(fd, rel=5e-3)
+    # adjoint sensitivities on 4 instances against central differences of the solver
+    for i in range(4):
+        w = ws[i]
+
+        def keff(props):
+            hh = Homogenization(_lib.THERMAL, shape)
+            hh.set_microstructure(w["phase"], 2)
+            hh.set_phase_properties(props)
+            hh.set_macro_load(np.eye(3))
+            hh.set_uno_weights(_lib.W_REFERENCE_MEDIUM)
+            hh.solve(tol=1e-12, max_iter=5000, precond=_lib.PRECOND_UNO, precision=_lib.FP64)
+            C = hh.effective_tensor()[0]
+            S = hh.sensitivity()[0]
+            hh.close()
+            return C, S
+
+        C0, S0 = keff(w["props"])
+        for p in range(2):
+            hstep = 1e-4 * w["props"][p]
+            pp, pm = w["props"].copy(), w["props"].copy()
+            pp[p] += hstep
+            pm[p] -= hstep
+            fd = (keff(pp)[0] - keff(pm)[0]) / (2 * hstep)
+            assert rel(S0[p], fd) < 1e-6
