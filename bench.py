@@ -122,6 +122,23 @@ def algorithmic_bytes(n, nh, c, BL, B, C_q, fb, qb):
     }
 
 
+def recorded_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture, or None when the kernel
+    sources changed since that capture."""
+    import glob
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "uno_cg_thermal64_mixed_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    m = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2508_02681_gb300", "csrc", "*"))):
+        m.update(open(f, "rb").read())
+    if m.hexdigest() != d.get("csrc_sha256"):
+        return None
+    return d["traffic_bytes"].get(kernel)
+
+
 def launches_per_solve(info, precond_uno=True):
     bodies = max(int(info.checks) - 1, 0)
     per_body = 4 if precond_uno else 3
@@ -306,7 +323,7 @@ def main():
         "kernel_ms_fp64": dict(zip(names, [float(x) for x in k_ms64])),
         "iteration_gbs_mixed": iter_bytes / (iter_ms * 1e-3) / 1e9,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": k_gbs[dom], "peak": peak, "unit": "GB/s",
-                     "frac": k_gbs[dom] / peak, "traffic": None, "peak_kind": peak_kind,
+                     "frac": k_gbs[dom] / peak, "traffic": recorded_traffic(dom), "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": ab[dom]},
         "e2e": {"value": e2e_max, "unit": "ms", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
