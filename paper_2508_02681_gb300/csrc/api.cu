@@ -205,7 +205,11 @@ extern "C" int unocg_create(unocg_ctx** out, int physics, int batch, int n1, int
   if ((physics != UNOCG_THERMAL && physics != UNOCG_ELASTIC) || batch < 1 || !(L0 > 0.0))
     return UNOCG_ERR_INVALID_ARG;
   if (!grid_ok(n1, n2, n3)) return UNOCG_ERR_INVALID_ARG;
-  if (!plane_fits(Grid{n1, n2, n3, n3 / 2 + 1, 0, 0, 0.0}, 8)) return UNOCG_ERR_INVALID_ARG;
+  {
+    Grid tg{};
+    tg.n1 = n1; tg.n2 = n2; tg.n3 = n3; tg.n3h = n3 / 2 + 1;
+    if (!grid_supported(tg, 8) || !grid_supported(tg, 16)) return UNOCG_ERR_INVALID_ARG;
+  }
   ctx = new unocg_ctx();
   ctx->physics = physics;
   ctx->c = physics == UNOCG_THERMAL ? 1 : 3;
@@ -539,7 +543,11 @@ static cudaError_t enq_plane_fwd(unocg_ctx* ctx, cudaStream_t s, const LoopCtl& 
   a.ft = tables(ctx, sizeof(T) == 8);
   a.ticket = ctx->tickets + ticket;
   a.ctl = ctl; a.after_replace = after_replace; a.standalone = 0;
-  return launch_plane_fwd<T>(a, s);
+  a.rows = plane_rows(ctx->g, sizeof(T) * 2);
+  cudaError_t e = launch_plane_fwd<T>(a, s);
+  if (e != cudaSuccess || a.rows == 0) return e;
+  ColArgs<T> ca{ctx->g, ctx->c, a.BL, f.rhat, ctx->sc, tables(ctx, sizeof(T) == 8), after_replace};
+  return launch_cols<T>(ca, -1, s);
 }
 
 template <typename T>
@@ -606,6 +614,12 @@ static cudaError_t enq_precond(unocg_ctx* ctx, cudaStream_t s, const Plan& pl, c
     PlaneInvArgs<T> pa{};
     pa.g = ctx->g; pa.c = ctx->c; pa.BL = BL; pa.shat = f.shat; pa.d = f.d; pa.u = f.u; pa.dst = nullptr;
     pa.sc = ctx->sc; pa.ft = tables(ctx, sizeof(T) == 8); pa.standalone = 0;
+    pa.rows = plane_rows(ctx->g, sizeof(T) * 2);
+    if (pa.rows) {
+      ColArgs<T> ca{ctx->g, ctx->c, BL, f.shat, ctx->sc, tables(ctx, sizeof(T) == 8), 0};
+      cudaError_t e = launch_cols<T>(ca, +1, s);
+      if (e != cudaSuccess) return e;
+    }
     return launch_plane_inv<T>(pa, s);
   }
   if (part == 1) return cudaSuccess;
@@ -1177,7 +1191,12 @@ extern "C" int unocg_apply_uno_dev(unocg_ctx* ctx, int instance, const double* r
   CK(cudaMallocAsync(&shat, m * sizeof(double2), s));
   PlaneFwdArgs<double> pf{};
   pf.g = ctx->g; pf.c = ctx->c; pf.BL = 1; pf.src = r_dev; pf.hat = hat; pf.ft = tables(ctx, true); pf.standalone = 1;
+  pf.rows = plane_rows(ctx->g, 16);
   cudaError_t e = launch_plane_fwd<double>(pf, s);
+  if (e == cudaSuccess && pf.rows) {
+    ColArgs<double> ca{ctx->g, ctx->c, 1, hat, nullptr, tables(ctx, true), 0};
+    e = launch_cols<double>(ca, -1, s);
+  }
   if (e == cudaSuccess) {
     LineArgs<double, double> la{};
     la.g = ctx->g; la.c = ctx->c; la.BL = 1; la.L = 1; la.hat = hat; la.shat = shat;
@@ -1188,7 +1207,12 @@ extern "C" int unocg_apply_uno_dev(unocg_ctx* ctx, int instance, const double* r
   if (e == cudaSuccess) {
     PlaneInvArgs<double> pi{};
     pi.g = ctx->g; pi.c = ctx->c; pi.BL = 1; pi.shat = shat; pi.dst = s_dev; pi.ft = tables(ctx, true); pi.standalone = 1;
-    e = launch_plane_inv<double>(pi, s);
+    pi.rows = plane_rows(ctx->g, 16);
+    if (pi.rows) {
+      ColArgs<double> ca{ctx->g, ctx->c, 1, shat, nullptr, tables(ctx, true), 0};
+      e = launch_cols<double>(ca, +1, s);
+    }
+    if (e == cudaSuccess) e = launch_plane_inv<double>(pi, s);
   }
   cudaFreeAsync(hat, s);
   cudaFreeAsync(shat, s);

@@ -51,15 +51,17 @@ __device__ __forceinline__ void plane_load_twiddles(const PlaneSmem<T>& s, const
 // Returns max |r| over the plane (valid in every thread).  Call with the whole block.
 template <typename T>
 __device__ double plane_fwd_task(const PlaneFwdArgs<T>& a, const PlaneSmem<T>& sm, int bl, int plane,
-                                 double alpha, double* red_sh) {
+                                 double alpha, double* red_sh, int row0 = 0, int nrows = 0) {
   using C = cplx<T>;
   const Grid& g = a.g;
   const int n3h = g.n3h, Nh = g.n3 / 2, P = pitch_of(n3h);
   const UDiv rNh = udiv_of(Nh), rn3h = udiv_of(n3h);
   const int comp = plane / g.n1, i1 = plane - comp * g.n1;
   const long long field = (long long)bl * a.c + comp;
-  const long long base = (field * g.n1 + i1) * (long long)g.n2 * g.n3;
-  const int npair = g.n2 * Nh;
+  const bool whole = nrows == 0;
+  if (whole) nrows = g.n2;
+  const long long base = (field * g.n1 + i1) * (long long)g.n2 * g.n3 + (long long)row0 * g.n3;
+  const int npair = nrows * Nh;
   C* buf = sm.buf;
   T lmax = (T)0;
   constexpr int U = 8;  // loads in flight per thread
@@ -114,11 +116,11 @@ __device__ double plane_fwd_task(const PlaneFwdArgs<T>& a, const PlaneSmem<T>& s
     }
   }
   __syncthreads();
-  C* res = fft_lines<T, -1>(buf, sm.alt, g.n2, P, 1, a.ft.p3h, sm.tw3h);
-  r2c_post<T>(res, g.n2, P, Nh, sm.tw3);
-  res = fft_lines<T, -1>(res, res == buf ? sm.alt : buf, n3h, 1, P, a.ft.p2, sm.tw2);
-  C* out = a.hat + (field * g.n1 + i1) * (long long)g.n2 * n3h;
-  const int nout = g.n2 * n3h;
+  C* res = fft_lines<T, -1>(buf, sm.alt, nrows, P, 1, a.ft.p3h, sm.tw3h);
+  r2c_post<T>(res, nrows, P, Nh, sm.tw3);
+  if (whole) res = fft_lines<T, -1>(res, res == buf ? sm.alt : buf, n3h, 1, P, a.ft.p2, sm.tw2);
+  C* out = a.hat + (field * g.n1 + i1) * (long long)g.n2 * n3h + (long long)row0 * n3h;
+  const int nout = nrows * n3h;
   for (int idx = threadIdx.x; idx < nout; idx += blockDim.x) {
     int k2 = udiv(idx, rn3h), k3 = idx - k2 * n3h;
     out[idx] = res[k2 * P + k3];
@@ -144,7 +146,15 @@ __global__ void __launch_bounds__(NTH) k_plane_fwd(PlaneFwdArgs<T> a) {
     alpha = a.after_replace ? 0.0 : a.sc[bl].alpha;
   }
   double bmax = 0.0;
-  if (active) bmax = plane_fwd_task<T>(a, sm, bl, blockIdx.x, alpha, red_sh);
+  if (active) {
+    if (a.rows) {
+      const int chunks = a.g.n2 / a.rows;
+      const int plane = blockIdx.x / chunks, ch = blockIdx.x - plane * chunks;
+      bmax = plane_fwd_task<T>(a, sm, bl, plane, alpha, red_sh, ch * a.rows, a.rows);
+    } else {
+      bmax = plane_fwd_task<T>(a, sm, bl, blockIdx.x, alpha, red_sh);
+    }
+  }
   if (a.standalone) return;
   if (threadIdx.x == 0 && active) atomic_max_nonneg(&a.sc[bl].rmax_bits, bmax);
   if (last_block(a.ticket)) {
@@ -367,16 +377,18 @@ __global__ void __launch_bounds__(NTH) k_line(LineArgs<T, QT> a) {
 // d = s + beta d_old; standalone: dst = s.  Call with the whole block.
 template <typename T>
 __device__ void plane_inv_task(const PlaneInvArgs<T>& a, const PlaneSmem<T>& sm, int bl, int plane,
-                               double alpha_d, double beta_d) {
+                               double alpha_d, double beta_d, int row0 = 0, int nrows = 0) {
   using C = cplx<T>;
   const Grid& g = a.g;
   const int n3h = g.n3h, Nh = g.n3 / 2, P = pitch_of(n3h);
   const UDiv rNh = udiv_of(Nh), rn3h = udiv_of(n3h);
   const int comp = plane / g.n1, i1 = plane - comp * g.n1;
   const long long field = (long long)bl * a.c + comp;
+  const bool whole = nrows == 0;
+  if (whole) nrows = g.n2;
   C* buf = sm.buf;
-  const C* __restrict__ in = a.shat + (field * g.n1 + i1) * (long long)g.n2 * n3h;
-  const int nin = g.n2 * n3h;
+  const C* __restrict__ in = a.shat + (field * g.n1 + i1) * (long long)g.n2 * n3h + (long long)row0 * n3h;
+  const int nin = nrows * n3h;
   constexpr int U = 8;
   for (int i0 = threadIdx.x; i0 < nin; i0 += U * blockDim.x) {
     C v[U];
@@ -395,11 +407,12 @@ __device__ void plane_inv_task(const PlaneInvArgs<T>& a, const PlaneSmem<T>& sm,
     }
   }
   __syncthreads();
-  C* res = fft_lines<T, +1>(buf, sm.alt, n3h, 1, P, a.ft.p2, sm.tw2);
-  c2r_pre<T>(res, g.n2, P, Nh, sm.tw3);
-  res = fft_lines<T, +1>(res, res == buf ? sm.alt : buf, g.n2, P, 1, a.ft.p3h, sm.tw3h);
-  const long long base = (field * g.n1 + i1) * (long long)g.n2 * g.n3;
-  const int npair = g.n2 * Nh;
+  C* res = buf;
+  if (whole) res = fft_lines<T, +1>(buf, sm.alt, n3h, 1, P, a.ft.p2, sm.tw2);
+  c2r_pre<T>(res, nrows, P, Nh, sm.tw3);
+  res = fft_lines<T, +1>(res, res == buf ? sm.alt : buf, nrows, P, 1, a.ft.p3h, sm.tw3h);
+  const long long base = (field * g.n1 + i1) * (long long)g.n2 * g.n3 + (long long)row0 * g.n3;
+  const int npair = nrows * Nh;
   if (a.standalone) {
     C* dst = reinterpret_cast<C*>(a.dst + base);
     for (int idx = threadIdx.x; idx < npair; idx += blockDim.x) {
@@ -446,7 +459,45 @@ __global__ void __launch_bounds__(NTH) k_plane_inv(PlaneInvArgs<T> a) {
   if (!a.standalone && a.sc[bl].done) return;
   plane_load_twiddles<T>(sm, a.g, a.ft);
   double al = a.standalone ? 0.0 : a.sc[bl].alpha, be = a.standalone ? 0.0 : a.sc[bl].beta;
-  plane_inv_task<T>(a, sm, bl, blockIdx.x, al, be);
+  if (a.rows) {
+    const int chunks = a.g.n2 / a.rows;
+    const int plane = blockIdx.x / chunks, ch = blockIdx.x - plane * chunks;
+    plane_inv_task<T>(a, sm, bl, plane, al, be, ch * a.rows, a.rows);
+  } else {
+    plane_inv_task<T>(a, sm, bl, blockIdx.x, al, be);
+  }
+}
+
+// ============================================================================ axis-2 pass
+// In-place FFT along axis 2 of (field, i1) planes: a block takes a tile of TB consecutive k3 of
+// one plane, all n2 rows (lines at stride n3h).
+template <typename T, int DIR, int NTH>
+__global__ void __launch_bounds__(NTH) k_cols(ColArgs<T> a) {
+  using C = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int TB = 16;
+  const Grid& g = a.g;
+  const int n2 = g.n2, n3h = g.n3h;
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  C* alt = buf + (size_t)n2 * TB;
+  C* tw = alt + (size_t)n2 * TB;
+  const long long plane = blockIdx.y;  // (bl * c + comp) * n1 + i1
+  const int bl = (int)(plane / ((long long)a.c * g.n1));
+  if (a.sc && (a.sc[bl].done || (a.only_pending && !a.sc[bl].just_replaced))) return;
+  load_tw<T>(tw, a.ft.tw2, n2);
+  const int k0 = blockIdx.x * TB;
+  const int nt = min(TB, n3h - k0);
+  C* base = a.data + plane * (long long)n2 * n3h + k0;
+  for (int idx = threadIdx.x; idx < n2 * TB; idx += NTH) {
+    const int row = idx / TB, t = idx - row * TB;
+    buf[idx] = t < nt ? base[(long long)row * n3h + t] : mk<T>((T)0, (T)0);
+  }
+  __syncthreads();
+  C* res = fft_lines<T, DIR>(buf, alt, TB, 1, TB, a.ft.p2, tw);
+  for (int idx = threadIdx.x; idx < n2 * TB; idx += NTH) {
+    const int row = idx / TB, t = idx - row * TB;
+    if (t < nt) base[(long long)row * n3h + t] = res[idx];
+  }
 }
 
 // ============================================================================ launchers
@@ -467,10 +518,6 @@ static inline size_t plane_smem(const Grid& g, int elem_bytes) {
   return (2 * (size_t)g.n2 * pitch_of(g.n3h) + g.n3 / 2 + g.n2 + g.n3) * elem_bytes;
 }
 
-#ifdef UNOCG_FFT_HOST_DEFS
-bool plane_fits(const Grid& g, int elem_bytes) { return plane_smem(g, elem_bytes) <= 220 * 1024; }
-#endif
-
 template <typename K, typename A>
 static cudaError_t launch_k(K kern, dim3 grid, int nth, size_t smem, const A& a, cudaStream_t s) {
   if (smem > 48 * 1024) {
@@ -481,8 +528,42 @@ static cudaError_t launch_k(K kern, dim3 grid, int nth, size_t smem, const A& a,
   return cudaGetLastError();
 }
 
+static inline size_t rows_smem(const Grid& g, int rows, int elem_bytes) {
+  return (2 * (size_t)rows * pitch_of(g.n3h) + g.n3 / 2 + g.n2 + g.n3) * elem_bytes;
+}
+
+#ifdef UNOCG_FFT_HOST_DEFS
+bool plane_fits(const Grid& g, int elem_bytes) { return plane_smem(g, elem_bytes) <= 220 * 1024; }
+int plane_rows(const Grid& g, int elem_bytes) {
+  if (plane_fits(g, elem_bytes)) return 0;
+  for (int rows = g.n2 / 2; rows >= 1; --rows)
+    if (g.n2 % rows == 0 && rows_smem(g, rows, elem_bytes) <= 200 * 1024) return rows;
+  return -1;
+}
+bool grid_supported(const Grid& g, int elem_bytes) {
+  if (plane_rows(g, elem_bytes) < 0) return false;
+  const size_t cols = (2 * (size_t)g.n2 * 16 + g.n2) * elem_bytes;            // axis-2 pass
+  const size_t line = (2 * (size_t)g.n1 * 3 * (elem_bytes == 8 ? 16 : 8) + g.n1) * elem_bytes;  // axis 1, c = 3
+  return cols <= 220 * 1024 && line <= 220 * 1024;
+}
+template <typename T> cudaError_t launch_cols(const ColArgs<T>& a, int dir, cudaStream_t s) {
+  const int eb = sizeof(cplx<T>);
+  size_t smem = (2 * (size_t)a.g.n2 * 16 + a.g.n2) * eb;
+  dim3 grid((a.g.n3h + 15) / 16, (unsigned)((long long)a.BL * a.c * a.g.n1));
+  if (dir < 0) return launch_k(k_cols<T, -1, 256>, grid, 256, smem, a, s);
+  return launch_k(k_cols<T, +1, 256>, grid, 256, smem, a, s);
+}
+template cudaError_t launch_cols<double>(const ColArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_cols<float>(const ColArgs<float>&, int, cudaStream_t);
+#endif
+
 template <typename T> cudaError_t launch_plane_fwd(const PlaneFwdArgs<T>& a, cudaStream_t s) {
   const int eb = sizeof(cplx<T>);
+  if (a.rows) {
+    size_t smem = rows_smem(a.g, a.rows, eb);
+    dim3 grid(a.c * a.g.n1 * (a.g.n2 / a.rows), a.BL);
+    return launch_k(k_plane_fwd<T, 512>, grid, 512, smem, a, s);
+  }
   if (!plane_fits(a.g, eb)) return cudaErrorInvalidValue;
   size_t smem = plane_smem(a.g, eb);
   dim3 grid(a.c * a.g.n1, a.BL);
@@ -494,6 +575,11 @@ template <typename T> cudaError_t launch_plane_fwd(const PlaneFwdArgs<T>& a, cud
 
 template <typename T> cudaError_t launch_plane_inv(const PlaneInvArgs<T>& a, cudaStream_t s) {
   const int eb = sizeof(cplx<T>);
+  if (a.rows) {
+    size_t smem = rows_smem(a.g, a.rows, eb);
+    dim3 grid(a.c * a.g.n1 * (a.g.n2 / a.rows), a.BL);
+    return launch_k(k_plane_inv<T, 512>, grid, 512, smem, a, s);
+  }
   if (!plane_fits(a.g, eb)) return cudaErrorInvalidValue;
   size_t smem = plane_smem(a.g, eb);
   dim3 grid(a.c * a.g.n1, a.BL);

@@ -20,6 +20,7 @@ template <typename T> struct PlaneFwdArgs {
   LoopCtl ctl;
   int after_replace;    // CG mode: residual was just replaced (no update, alpha = 0)
   int standalone;       // transform src only (no CG bookkeeping)
+  int rows;             // 0: whole planes (axes 3 and 2); else chunks of `rows` rows, axis 3 only
 };
 
 template <typename T, typename QT> struct LineArgs {
@@ -50,6 +51,17 @@ template <typename T> struct PlaneInvArgs {
   CgScal* sc;
   FftTables ft;
   int standalone;
+  int rows;             // 0: whole planes; else chunks of `rows` rows, axis 3 only (axis 2 done)
+};
+
+// In-place FFT along axis 2 of every (field, i1) plane, for planes too large for one block.
+template <typename T> struct ColArgs {
+  Grid g;
+  int c, BL;
+  cplx<T>* data;        // [BL][c][n1][n2][n3h]
+  const CgScal* sc;     // skip finished pairs (null: all)
+  FftTables ft;
+  int only_pending;     // CG after a replacement: only the pairs just replaced
 };
 
 // ---------------------------------------------------------------- material / stencil
@@ -154,5 +166,8 @@ template <typename T, typename QT> cudaError_t launch_line(const LineArgs<T, QT>
 template <typename T> cudaError_t launch_plane_inv(const PlaneInvArgs<T>& a, cudaStream_t s);
 int line_blocks_x(const Grid& g, int c, int elem_bytes);
 bool plane_fits(const Grid& g, int elem_bytes);
+int plane_rows(const Grid& g, int elem_bytes);  // 0 if whole planes fit, else rows per block
+bool grid_supported(const Grid& g, int elem_bytes);
+template <typename T> cudaError_t launch_cols(const ColArgs<T>& a, int dir, cudaStream_t s);
 
 }  // namespace unocg
