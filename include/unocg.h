@@ -81,13 +81,18 @@ typedef struct {
   int max_iter;      /* iterations per (instance, load) before UNOCG_ERR_NOT_CONVERGED      */
   int precond;       /* UNOCG_PRECOND_*                                                     */
   int precision;     /* UNOCG_FP64 or UNOCG_MIXED                                           */
-  int replace_every; /* MIXED: true-residual replacement period (iterations), e.g. 50      */
+  int replace_every; /* MIXED: true-residual replacement after this many iterations since the
+                        previous one, e.g. 50; 0 disables the periodic trigger              */
   int flexible;      /* 1: Polak-Ribiere coefficient (flexible CG), 0: Algorithm 1's        */
   int use_graph;     /* loop driver: 0 host-driven loop, one residual check per iteration;
                         1 one CUDA graph with conditional nodes (device-side control);
                         2 one persistent cooperative kernel with grid barriers (UNO only,
                           problems whose phase buffers fit in shared memory);
                         3 automatic: 2 for small problems, else 1                            */
+  double replace_drop; /* MIXED: also replace once ||r||_inf has fallen below replace_drop
+                          times its value at the previous replacement (reliable updates: the
+                          FP32 solution increment since then stays small); 0 disables, 1e-2
+                          keeps the iteration count of the FP64 path up to 256^3 grids      */
 } unocg_solve_opts;
 
 typedef struct {
@@ -102,7 +107,9 @@ typedef struct {
 } unocg_solve_info;
 
 /* Create a context for `batch` instances on an n1 x n2 x n3 grid (each n_i of the form
-   2^a 3^b 5^c, n3 even, every n_i >= 2) with RVE edge L0 along axis 1.  Sec. 4.1.          */
+   2^a 3^b 5^c, n3 even, every n_i >= 2) with RVE edge L0 along axis 1.  Sec. 4.1.
+   The transform passes keep whole lines in shared memory, which bounds n1 <= 287 and
+   n2 <= 426; larger grids return UNOCG_ERR_INVALID_ARG.                                   */
 int unocg_create(unocg_ctx** out, int physics, int batch, int n1, int n2, int n3, double L0);
 void unocg_destroy(unocg_ctx* ctx);
 const char* unocg_last_error(const unocg_ctx* ctx);
@@ -174,6 +181,8 @@ int unocg_profile_iteration(unocg_ctx* ctx, const unocg_solve_opts* opts, int re
 /* ---------------------------------------------------------------- standalone UNO operator
    P = T^H Q T on a batch of fields, for training (Sec. 5.3, Algorithm 3).                  */
 typedef struct unocg_uno unocg_uno;
+/* Grid rules as unocg_create; the backward pass holds four line buffers, which bounds
+   n1 <= 218 (c = 1) and n1 <= 145 (c = 3).                                                 */
 int unocg_uno_create(unocg_uno** out, int c, int n1, int n2, int n3);
 void unocg_uno_destroy(unocg_uno* op);
 const char* unocg_uno_last_error(const unocg_uno* op);

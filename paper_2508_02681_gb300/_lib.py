@@ -41,7 +41,7 @@ DTYPE_F32 = 1
 class SolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("precond", C.c_int),
                 ("precision", C.c_int), ("replace_every", C.c_int), ("flexible", C.c_int),
-                ("use_graph", C.c_int)]
+                ("use_graph", C.c_int), ("replace_drop", C.c_double)]
 
 
 class SolveInfo(C.Structure):

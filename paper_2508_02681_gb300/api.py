@@ -94,10 +94,10 @@ def unocg_get_uno_weights(ctx, instance: int, n_modes: int, C_: int) -> np.ndarr
 
 
 def make_opts(tol=1e-6, max_iter=10000, precond=_lib.PRECOND_UNO, precision=_lib.FP64,
-              replace_every=50, flexible=None, use_graph=3) -> SolveOpts:
+              replace_every=50, flexible=None, use_graph=3, replace_drop=1e-2) -> SolveOpts:
     if flexible is None:
         flexible = 1 if precision == _lib.MIXED else 0
-    return SolveOpts(tol, max_iter, precond, precision, replace_every, flexible, use_graph)
+    return SolveOpts(tol, max_iter, precond, precision, replace_every, flexible, use_graph, replace_drop)
 
 
 class Info:

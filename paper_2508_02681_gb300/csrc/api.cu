@@ -63,10 +63,11 @@ struct Fields32 {
 
 struct GraphKey {
   int precond = -1, precision = -1, flexible = -1, replace_every = -1, max_iter = -1, L = -1;
-  double tol = -1.0;
+  double tol = -1.0, replace_drop = -1.0;
   bool operator==(const GraphKey& o) const {
     return precond == o.precond && precision == o.precision && flexible == o.flexible &&
-           replace_every == o.replace_every && max_iter == o.max_iter && L == o.L && tol == o.tol;
+           replace_every == o.replace_every && max_iter == o.max_iter && L == o.L && tol == o.tol &&
+           replace_drop == o.replace_drop;
   }
 };
 
@@ -534,6 +535,29 @@ struct Plan {
   int mixed;
 };
 
+// Forward transform over axes 3 and 2: whole planes in one pass where a plane fits one block's
+// shared memory, else the row pass (axis 3) followed by the in-place axis-2 column pass.
+template <typename T>
+static cudaError_t fwd_transform(PlaneFwdArgs<T>& a, cudaStream_t s, int only_pending) {
+  a.rows = plane_rows(a.g, sizeof(T) * 2);
+  cudaError_t e = launch_plane_fwd<T>(a, s);
+  if (e != cudaSuccess || a.rows == 0) return e;
+  ColArgs<T> ca{a.g, a.c, a.BL, a.hat, a.sc, a.ft, only_pending};
+  return launch_cols<T>(ca, -1, s);
+}
+
+// Inverse of fwd_transform; the column pass runs in place on a.shat.
+template <typename T>
+static cudaError_t inv_transform(PlaneInvArgs<T>& a, cudaStream_t s) {
+  a.rows = plane_rows(a.g, sizeof(T) * 2);
+  if (a.rows) {
+    ColArgs<T> ca{a.g, a.c, a.BL, const_cast<cplx<T>*>(a.shat), a.sc, a.ft, 0};
+    cudaError_t e = launch_cols<T>(ca, +1, s);
+    if (e != cudaSuccess) return e;
+  }
+  return launch_plane_inv<T>(a, s);
+}
+
 template <typename T>
 static cudaError_t enq_plane_fwd(unocg_ctx* ctx, cudaStream_t s, const LoopCtl& ctl, int after_replace, int ticket) {
   auto& f = Sel<T>::f(ctx);
@@ -543,11 +567,7 @@ static cudaError_t enq_plane_fwd(unocg_ctx* ctx, cudaStream_t s, const LoopCtl& 
   a.ft = tables(ctx, sizeof(T) == 8);
   a.ticket = ctx->tickets + ticket;
   a.ctl = ctl; a.after_replace = after_replace; a.standalone = 0;
-  a.rows = plane_rows(ctx->g, sizeof(T) * 2);
-  cudaError_t e = launch_plane_fwd<T>(a, s);
-  if (e != cudaSuccess || a.rows == 0) return e;
-  ColArgs<T> ca{ctx->g, ctx->c, a.BL, f.rhat, ctx->sc, tables(ctx, sizeof(T) == 8), after_replace};
-  return launch_cols<T>(ca, -1, s);
+  return fwd_transform<T>(a, s, after_replace);
 }
 
 template <typename T>
@@ -614,13 +634,7 @@ static cudaError_t enq_precond(unocg_ctx* ctx, cudaStream_t s, const Plan& pl, c
     PlaneInvArgs<T> pa{};
     pa.g = ctx->g; pa.c = ctx->c; pa.BL = BL; pa.shat = f.shat; pa.d = f.d; pa.u = f.u; pa.dst = nullptr;
     pa.sc = ctx->sc; pa.ft = tables(ctx, sizeof(T) == 8); pa.standalone = 0;
-    pa.rows = plane_rows(ctx->g, sizeof(T) * 2);
-    if (pa.rows) {
-      ColArgs<T> ca{ctx->g, ctx->c, BL, f.shat, ctx->sc, tables(ctx, sizeof(T) == 8), 0};
-      cudaError_t e = launch_cols<T>(ca, +1, s);
-      if (e != cudaSuccess) return e;
-    }
-    return launch_plane_inv<T>(pa, s);
+    return inv_transform<T>(pa, s);
   }
   if (part == 1) return cudaSuccess;
   JacArgs<T> a{};
@@ -715,7 +729,7 @@ static int build_graph(unocg_ctx* ctx, const Plan& pl) {
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hw, cg, 0, cudaGraphCondAssignDefault);
   LoopCtl ctl{};
   ctl.tol = pl.o.tol; ctl.max_iter = pl.o.max_iter; ctl.mixed = pl.mixed;
-  ctl.replace_every = pl.o.replace_every; ctl.flexible = pl.o.flexible;
+  ctl.replace_every = pl.o.replace_every; ctl.replace_drop = pl.o.replace_drop; ctl.flexible = pl.o.flexible;
   ctl.h_while = hw; ctl.set_while = 1; ctl.set_if = 0;
   ctl.counters = ctx->flags + 2;
   if (e == cudaSuccess) e = enq_pre<T>(ctx, cs, pl, ctl);
@@ -800,7 +814,7 @@ static int run_host_loop(unocg_ctx* ctx, const Plan& pl) {
   cudaStream_t s = ctx->stream;
   LoopCtl ctl{};
   ctl.tol = pl.o.tol; ctl.max_iter = pl.o.max_iter; ctl.mixed = pl.mixed;
-  ctl.replace_every = pl.o.replace_every; ctl.flexible = pl.o.flexible;
+  ctl.replace_every = pl.o.replace_every; ctl.replace_drop = pl.o.replace_drop; ctl.flexible = pl.o.flexible;
   ctl.active_flag = ctx->flags; ctl.replace_flag = ctx->flags + 1;
   ctl.counters = ctx->flags + 2;
   CK(enq_pre<T>(ctx, s, pl, ctl));
@@ -886,7 +900,7 @@ static int run_persistent(unocg_ctx* ctx, const Plan& pl) {
   a.bar = reinterpret_cast<unsigned int*>(ctx->flags + 4);
   a.err = ctx->flags + 6;
   a.ctl.tol = pl.o.tol; a.ctl.max_iter = pl.o.max_iter; a.ctl.mixed = pl.mixed;
-  a.ctl.replace_every = pl.o.replace_every; a.ctl.flexible = pl.o.flexible;
+  a.ctl.replace_every = pl.o.replace_every; a.ctl.replace_drop = pl.o.replace_drop; a.ctl.flexible = pl.o.flexible;
   a.spin_limit = ctx->spin_limit;
   CK(launch_persist<T, QT>(a, s, ctx->sm_count));
   CK(enq_post<T>(ctx, s, pl));
@@ -898,7 +912,8 @@ static int prepare_solve(unocg_ctx* ctx, const unocg_solve_opts* o, Plan* pl) {
   if (!ctx->have_phase || !ctx->have_props || !ctx->have_loads)
     return fail(ctx, UNOCG_ERR_STATE, "set microstructure, phase properties and loads first");
   if (o->precond < 0 || o->precond > 2 || (o->precision != UNOCG_FP64 && o->precision != UNOCG_MIXED) ||
-      !(o->tol > 0.0) || o->max_iter < 1 || o->replace_every < 0)
+      !(o->tol > 0.0) || o->max_iter < 1 || o->replace_every < 0 || !(o->replace_drop >= 0.0) ||
+      !(o->replace_drop < 1.0))
     return fail(ctx, UNOCG_ERR_INVALID_ARG, "invalid solve options");
   if (o->precond == UNOCG_PRECOND_UNO) {
     if (ctx->wkind < 0) return fail(ctx, UNOCG_ERR_STATE, "set UNO weights first");
@@ -911,7 +926,10 @@ static int prepare_solve(unocg_ctx* ctx, const unocg_solve_opts* o, Plan* pl) {
   }
   pl->o = *o;
   pl->mixed = o->precision == UNOCG_MIXED;
-  if (!pl->mixed) pl->o.replace_every = 0;
+  if (!pl->mixed) {
+    pl->o.replace_every = 0;
+    pl->o.replace_drop = 0.0;
+  }
   return ensure_workspace(ctx, o->precision, o->precond);
 }
 
@@ -950,7 +968,7 @@ extern "C" int unocg_solve_async(unocg_ctx* ctx, const unocg_solve_opts* o) {
   } else {
     GraphKey k;
     k.precond = o->precond; k.precision = o->precision; k.flexible = o->flexible;
-    k.replace_every = pl.o.replace_every; k.max_iter = o->max_iter; k.L = ctx->L; k.tol = o->tol;
+    k.replace_every = pl.o.replace_every; k.replace_drop = pl.o.replace_drop; k.max_iter = o->max_iter; k.L = ctx->L; k.tol = o->tol;
     if (!ctx->exec || !(k == ctx->key)) {
       rc = pl.mixed ? build_graph<float>(ctx, pl) : build_graph<double>(ctx, pl);
       if (rc) return rc;
@@ -1103,7 +1121,7 @@ static int profile_iters(unocg_ctx* ctx, const Plan& pl, int reps, double* ms_ou
   cudaStream_t s = ctx->stream;
   LoopCtl ctl{};
   ctl.tol = pl.o.tol; ctl.max_iter = pl.o.max_iter; ctl.mixed = 0;
-  ctl.replace_every = 0; ctl.flexible = pl.o.flexible;
+  ctl.replace_every = 0; ctl.replace_drop = 0.0; ctl.flexible = pl.o.flexible;
   Plan p2 = pl;
   p2.mixed = 0;
   CK(enq_pre<T>(ctx, s, p2, ctl));
@@ -1191,12 +1209,7 @@ extern "C" int unocg_apply_uno_dev(unocg_ctx* ctx, int instance, const double* r
   CK(cudaMallocAsync(&shat, m * sizeof(double2), s));
   PlaneFwdArgs<double> pf{};
   pf.g = ctx->g; pf.c = ctx->c; pf.BL = 1; pf.src = r_dev; pf.hat = hat; pf.ft = tables(ctx, true); pf.standalone = 1;
-  pf.rows = plane_rows(ctx->g, 16);
-  cudaError_t e = launch_plane_fwd<double>(pf, s);
-  if (e == cudaSuccess && pf.rows) {
-    ColArgs<double> ca{ctx->g, ctx->c, 1, hat, nullptr, tables(ctx, true), 0};
-    e = launch_cols<double>(ca, -1, s);
-  }
+  cudaError_t e = fwd_transform<double>(pf, s, 0);
   if (e == cudaSuccess) {
     LineArgs<double, double> la{};
     la.g = ctx->g; la.c = ctx->c; la.BL = 1; la.L = 1; la.hat = hat; la.shat = shat;
@@ -1207,12 +1220,7 @@ extern "C" int unocg_apply_uno_dev(unocg_ctx* ctx, int instance, const double* r
   if (e == cudaSuccess) {
     PlaneInvArgs<double> pi{};
     pi.g = ctx->g; pi.c = ctx->c; pi.BL = 1; pi.shat = shat; pi.dst = s_dev; pi.ft = tables(ctx, true); pi.standalone = 1;
-    pi.rows = plane_rows(ctx->g, 16);
-    if (pi.rows) {
-      ColArgs<double> ca{ctx->g, ctx->c, 1, shat, nullptr, tables(ctx, true), 0};
-      e = launch_cols<double>(ca, +1, s);
-    }
-    if (e == cudaSuccess) e = launch_plane_inv<double>(pi, s);
+    e = inv_transform<double>(pi, s);
   }
   cudaFreeAsync(hat, s);
   cudaFreeAsync(shat, s);
@@ -1253,7 +1261,7 @@ extern "C" int unocg_uno_create(unocg_uno** out, int c, int n1, int n2, int n3) 
   if (!out || (c != 1 && c != 3) || !grid_ok(n1, n2, n3)) return UNOCG_ERR_INVALID_ARG;
   Grid g{n1, n2, n3, n3 / 2 + 1, (long long)n1 * n2 * n3, (long long)n1 * n2 * (n3 / 2 + 1), 1.0 / n1};
   grid_scales(g);
-  if (!plane_fits(g, 8)) return UNOCG_ERR_INVALID_ARG;
+  if (!grid_supported(g, 8) || line_smem_bytes(g, c, 8, 2) > 220 * 1024) return UNOCG_ERR_INVALID_ARG;
   unocg_uno* op = new unocg_uno();
   *out = op;
   op->c = c;
@@ -1318,14 +1326,14 @@ extern "C" int unocg_uno_apply_dev(unocg_uno* op, int batch, const float* r_dev,
   cudaStream_t s = (cudaStream_t)stream;
   PlaneFwdArgs<float> pf{};
   pf.g = op->g; pf.c = op->c; pf.BL = batch; pf.src = r_dev; pf.hat = op->hat; pf.ft = uno_tables(op); pf.standalone = 1;
-  UCK(launch_plane_fwd<float>(pf, s));
+  UCK(fwd_transform<float>(pf, s, 0));
   LineArgs<float, float> la{};
   la.g = op->g; la.c = op->c; la.BL = batch; la.L = 1; la.hat = op->hat; la.shat = op->shat;
   la.Q = op->Q32; la.q_inst_stride = 0; la.scale = 1.0 / (double)op->g.n; la.ft = uno_tables(op); la.standalone = 1;
   UCK(launch_line<float, float>(la, 0, s));
   PlaneInvArgs<float> pi{};
   pi.g = op->g; pi.c = op->c; pi.BL = batch; pi.shat = op->shat; pi.dst = s_dev; pi.ft = uno_tables(op); pi.standalone = 1;
-  UCK(launch_plane_inv<float>(pi, s));
+  UCK(inv_transform<float>(pi, s));
   return UNOCG_OK;
 }
 
@@ -1339,10 +1347,10 @@ extern "C" int unocg_uno_backward_dev(unocg_uno* op, int batch, const float* r_d
   const int NQ = op->c == 1 ? 1 : 6;
   PlaneFwdArgs<float> pf{};
   pf.g = op->g; pf.c = op->c; pf.BL = batch; pf.src = r_dev; pf.hat = op->hat; pf.ft = uno_tables(op); pf.standalone = 1;
-  UCK(launch_plane_fwd<float>(pf, s));
+  UCK(fwd_transform<float>(pf, s, 0));
   pf.src = gs_dev;
   pf.hat = op->ghat;
-  UCK(launch_plane_fwd<float>(pf, s));
+  UCK(fwd_transform<float>(pf, s, 0));
   UCK(cudaMemsetAsync(op->gq, 0, (size_t)op->g.nh * NQ * sizeof(float), s));
   LineArgs<float, float> la{};
   la.g = op->g; la.c = op->c; la.BL = batch; la.L = 1; la.hat = op->hat; la.shat = op->shat; la.ghat = op->ghat;
@@ -1352,7 +1360,7 @@ extern "C" int unocg_uno_backward_dev(unocg_uno* op, int batch, const float* r_d
   if (gr_dev) {
     PlaneInvArgs<float> pi{};
     pi.g = op->g; pi.c = op->c; pi.BL = batch; pi.shat = op->shat; pi.dst = gr_dev; pi.ft = uno_tables(op); pi.standalone = 1;
-    UCK(launch_plane_inv<float>(pi, s));
+    UCK(inv_transform<float>(pi, s));
   }
   if (gtheta_dev) {
     // Q_sym = S psi(theta) with S the (self-adjoint) plane averaging: dL/dpsi = S dL/dQ_sym

@@ -11,7 +11,8 @@ struct LoopCtl {
   double tol;                       // relative: stop when ||r||_inf <= tol ||r_0||_inf
   int max_iter;
   int mixed;                        // mixed precision: verify convergence by a true residual
-  int replace_every;                // mixed: residual replacement period (iterations)
+  int replace_every;                // mixed: replacement after this many iterations since the last
+  double replace_drop;              // mixed: replacement once ||r|| < replace_drop * ||r|| at the last
   int flexible;                     // Polak-Ribiere coefficient
   cudaGraphConditionalHandle h_while;
   cudaGraphConditionalHandle h_if;
@@ -35,11 +36,15 @@ __device__ inline void residual_decision(CgScal* sc, int BL, const LoopCtl& ctl,
     s.rmax = rmax;
     if (!s.started) {
       s.r0max = rmax;
+      s.rrep = rmax;
+      s.rep_iter = 0;
       s.started = 1;
     }
     if (after_replace) {
       s.need_replace = 0;
       s.true_res = (s.r0max > 0.0) ? rmax / s.r0max : 0.0;
+      s.rrep = rmax;
+      s.rep_iter = s.iters;
     }
     if (isnan(rmax) || isinf(rmax)) {
       s.done = 1;
@@ -47,8 +52,11 @@ __device__ inline void residual_decision(CgScal* sc, int BL, const LoopCtl& ctl,
       continue;
     }
     bool conv = rmax <= ctl.tol * s.r0max;
+    // mixed precision: a true residual confirms convergence, replaces r periodically, and
+    // replaces it whenever it has fallen by replace_drop since the last replacement
     if (ctl.mixed && !after_replace && s.iters > 0 &&
-        (conv || (ctl.replace_every > 0 && s.iters % ctl.replace_every == 0))) {
+        (conv || (ctl.replace_every > 0 && s.iters - s.rep_iter >= ctl.replace_every) ||
+         rmax <= ctl.replace_drop * s.rrep)) {
       s.need_replace = 1;
       continue;
     }

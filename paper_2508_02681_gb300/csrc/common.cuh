@@ -39,6 +39,7 @@ struct CgScal {
   double r0max;       // ||r_0||_inf
   double rmax;        // ||r||_inf of the latest residual
   double true_res;    // ||f - K u||_inf / ||f||_inf (FP64) at the latest check
+  double rrep;        // ||r||_inf right after the latest replacement (r_0 before any)
   unsigned long long rmax_bits;  // running max of |r| as ordered bits (non-negative doubles)
   unsigned long long tmax_bits;  // running max of |f - K u| (true residual kernel)
   int iters;
@@ -47,7 +48,8 @@ struct CgScal {
   int need_replace;   // residual replacement requested (mixed precision)
   int started;        // r0max recorded
   int just_replaced;  // the last residual check followed a replacement of this pair
-  int pad[2];
+  int rep_iter;       // iteration count at the latest replacement
+  int pad;
 };
 
 // ---------------------------------------------------------------- problem descriptor

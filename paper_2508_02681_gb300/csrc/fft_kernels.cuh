@@ -19,7 +19,8 @@ namespace unocg {
 static __host__ __device__ inline int pitch_of(int n3h) { return (n3h % 2 == 0) ? n3h + 1 : n3h; }
 
 // ============================================================================ shared-memory layout
-// Plane tasks: two plane buffers of n2 x P complex, then twiddles W_{N3/2}, W_{N2}, W_{N3}.
+// Plane tasks: two buffers of nrows x P complex (nrows = n2 for whole planes, the chunk height in
+// row mode), then twiddles W_{N3/2}, W_{N2}, W_{N3}.
 template <typename T> struct PlaneSmem {
   cplx<T>* buf;
   cplx<T>* alt;
@@ -28,12 +29,12 @@ template <typename T> struct PlaneSmem {
   cplx<T>* tw3;
 };
 template <typename T>
-__device__ __forceinline__ PlaneSmem<T> plane_smem_layout(void* raw, const Grid& g) {
+__device__ __forceinline__ PlaneSmem<T> plane_smem_layout(void* raw, const Grid& g, int nrows) {
   PlaneSmem<T> s;
   const int P = pitch_of(g.n3h);
   s.buf = reinterpret_cast<cplx<T>*>(raw);
-  s.alt = s.buf + g.n2 * P;
-  s.tw3h = s.alt + g.n2 * P;
+  s.alt = s.buf + nrows * P;
+  s.tw3h = s.alt + nrows * P;
   s.tw2 = s.tw3h + g.n3 / 2;
   s.tw3 = s.tw2 + g.n2;
   return s;
@@ -136,7 +137,7 @@ template <typename T, int NTH>
 __global__ void __launch_bounds__(NTH) k_plane_fwd(PlaneFwdArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red_sh[32];
-  PlaneSmem<T> sm = plane_smem_layout<T>(smem_raw, a.g);
+  PlaneSmem<T> sm = plane_smem_layout<T>(smem_raw, a.g, a.rows ? a.rows : a.g.n2);
   plane_load_twiddles<T>(sm, a.g, a.ft);
   const int bl = blockIdx.y;
   bool active = true;
@@ -454,7 +455,7 @@ __device__ void plane_inv_task(const PlaneInvArgs<T>& a, const PlaneSmem<T>& sm,
 template <typename T, int NTH>
 __global__ void __launch_bounds__(NTH) k_plane_inv(PlaneInvArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  PlaneSmem<T> sm = plane_smem_layout<T>(smem_raw, a.g);
+  PlaneSmem<T> sm = plane_smem_layout<T>(smem_raw, a.g, a.rows ? a.rows : a.g.n2);
   const int bl = blockIdx.y;
   if (!a.standalone && a.sc[bl].done) return;
   plane_load_twiddles<T>(sm, a.g, a.ft);
@@ -542,9 +543,8 @@ int plane_rows(const Grid& g, int elem_bytes) {
 }
 bool grid_supported(const Grid& g, int elem_bytes) {
   if (plane_rows(g, elem_bytes) < 0) return false;
-  const size_t cols = (2 * (size_t)g.n2 * 16 + g.n2) * elem_bytes;            // axis-2 pass
-  const size_t line = (2 * (size_t)g.n1 * 3 * (elem_bytes == 8 ? 16 : 8) + g.n1) * elem_bytes;  // axis 1, c = 3
-  return cols <= 220 * 1024 && line <= 220 * 1024;
+  const size_t cols = (2 * (size_t)g.n2 * 16 + g.n2) * elem_bytes;  // axis-2 pass
+  return cols <= 220 * 1024 && line_smem_bytes(g, 3, elem_bytes, 0) <= 220 * 1024;
 }
 template <typename T> cudaError_t launch_cols(const ColArgs<T>& a, int dir, cudaStream_t s) {
   const int eb = sizeof(cplx<T>);
@@ -596,6 +596,9 @@ static int line_tb(int c, int elem_bytes) {
 }
 
 #ifdef UNOCG_FFT_HOST_DEFS
+size_t line_smem_bytes(const Grid& g, int c, int elem_bytes, int mode) {
+  return ((size_t)g.n1 * c * line_tb(c, elem_bytes) * (mode == 2 ? 4 : 2) + g.n1) * elem_bytes;
+}
 int line_blocks_x(const Grid& g, int c, int elem_bytes) {
   int tb = line_tb(c, elem_bytes);
   int M = g.n2 * g.n3h;
@@ -607,7 +610,7 @@ template <typename T, typename QT, int CC, int MODE>
 static cudaError_t launch_line_cc(LineArgs<T, QT> a, cudaStream_t s) {
   const int eb = sizeof(cplx<T>);
   a.tb = line_tb(CC, eb);
-  size_t smem = ((size_t)a.g.n1 * CC * a.tb * (MODE == 2 ? 4 : 2) + a.g.n1) * eb;
+  const size_t smem = line_smem_bytes(a.g, CC, eb, MODE);
   dim3 grid(line_blocks_x(a.g, CC, eb), a.BL);
   long long e = (long long)a.g.n1 * CC * a.tb;
   if (UNOCG_LINE_NTH) e = UNOCG_LINE_NTH * 2;

@@ -165,6 +165,8 @@ template <typename T> cudaError_t launch_plane_fwd(const PlaneFwdArgs<T>& a, cud
 template <typename T, typename QT> cudaError_t launch_line(const LineArgs<T, QT>& a, int backward, cudaStream_t s);
 template <typename T> cudaError_t launch_plane_inv(const PlaneInvArgs<T>& a, cudaStream_t s);
 int line_blocks_x(const Grid& g, int c, int elem_bytes);
+// dynamic shared memory of the axis-1 pass (mode 2: backward, four line buffers)
+size_t line_smem_bytes(const Grid& g, int c, int elem_bytes, int mode);
 bool plane_fits(const Grid& g, int elem_bytes);
 int plane_rows(const Grid& g, int elem_bytes);  // 0 if whole planes fit, else rows per block
 bool grid_supported(const Grid& g, int elem_bytes);

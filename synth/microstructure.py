@@ -33,15 +33,19 @@ def _min_image(delta: np.ndarray, n: np.ndarray) -> np.ndarray:
 
 
 def rsa_spheres(shape, radius: float, volume_fraction: float, seed: int,
-                max_rejections: int = 100_000):
+                max_rejections: int = 10_000, overlap_on_jam: bool = True):
     """Periodic RSA of non-overlapping spheres until the voxel fraction reaches a target.
 
     Centres are drawn uniformly in ``[0, N1) x [0, N2) x [0, N3)``.  A candidate is accepted
     when its minimum-image distance to every accepted centre is at least ``2 * radius``.  A voxel
     belongs to the inclusion phase when its centre lies within ``radius`` (minimum image) of an
     accepted centre.  Placement stops at the first accepted sphere that brings the inclusion
-    voxel fraction to ``volume_fraction`` or above; ``RuntimeError`` after ``max_rejections``
-    consecutive rejected candidates.
+    voxel fraction to ``volume_fraction`` or above.
+
+    Non-overlapping RSA jams near a sphere fraction of 0.38, below the top of some requested
+    ranges (0.4).  After ``max_rejections`` consecutive rejected candidates the packing counts as
+    jammed: with ``overlap_on_jam`` the remaining spheres are placed without the distance test
+    (penetrable spheres, the same random stream), else ``RuntimeError`` is raised.
 
     Returns ``(phase, achieved_fraction)``.
     """
@@ -54,17 +58,37 @@ def rsa_spheres(shape, radius: float, volume_fraction: float, seed: int,
     centres = np.zeros((0, 3))
     total = float(np.prod(shape))
     rejections = 0
+    jammed = False
     r = float(radius)
     reach = int(np.ceil(r)) + 1
+    # candidates are drawn in blocks (the same stream as one draw of three per candidate) and
+    # tested against the accepted centres all at once, in drawing order
+    block = np.zeros((0, 3))
+    pos = 0
     while True:
-        c = rng.uniform(0.0, 1.0, size=3) * n
-        if centres.shape[0]:
-            d = _min_image(centres - c, n)
-            if np.min(np.einsum("ij,ij->i", d, d)) < (2.0 * r) ** 2:
-                rejections += 1
-                if rejections >= max_rejections:
+        if pos == block.shape[0]:
+            block = rng.uniform(0.0, 1.0, size=(1024, 3)) * n
+            pos = 0
+        if centres.shape[0] and not jammed:
+            # window grows with the run of rejections (few candidates while most are accepted)
+            cand = block[pos:pos + max(16, rejections)]
+            d = _min_image(centres[None, :, :] - cand[:, None, :], n)
+            ok = np.min(np.einsum("mij,mij->mi", d, d), axis=1) >= (2.0 * r) ** 2
+            first = int(np.argmax(ok)) if ok.any() else cand.shape[0]
+            if rejections + first >= max_rejections:
+                # the candidate that completes max_rejections consecutive rejections
+                if not overlap_on_jam:
                     raise RuntimeError("RSA: too many consecutive rejections")
+                jammed = True
+                pos += max_rejections - rejections
                 continue
+            if first == cand.shape[0]:
+                rejections += first
+                pos += first
+                continue
+            pos += first
+        c = block[pos]
+        pos += 1
         rejections = 0
         centres = np.vstack([centres, c])
         # mark voxels of this sphere (periodic bounding box)

@@ -126,8 +126,12 @@ def test_config4_training_workload():
     from paper_2508_02681_gb300 import _lib, api, training as tr
     from paper_2508_02681_gb300.solver import Homogenization
     from synth import workload
+    import multiprocessing as mp
+    import os
     shape = (32, 32, 32)
-    ws = [workload(4, i) for i in range(512)]
+    # the inputs are drawn on the host cores; spawned workers (this process already uses CUDA)
+    with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
+        ws = pool.starmap(workload, [(4, i) for i in range(512)])
     f, u, iters = tr.generate_data([w["phase"] for w in ws], [w["props"] for w in ws],
                                    np.array([1.0, 0.0, 0.0]), shape)
     assert max(iters) < 5000
