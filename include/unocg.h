@@ -203,6 +203,19 @@ int unocg_apply_K_dev(unocg_ctx* ctx, int instance, const double* d_dev, double*
 /* s = P r with the context's current UNO weights (Algorithm 2, transform / block multiply /
    inverse transform), in FP64.                                                             */
 int unocg_apply_uno_dev(unocg_ctx* ctx, int instance, const double* r_dev, double* s_dev, void* stream);
+/* s = P r as unocg_apply_uno_dev, without allocating: the two spectra live in a static device
+   scratch of the library (2 x 8 MiB), not in memory from cudaMallocAsync.  The paper has no
+   counterpart; this serves callers that cannot allocate when they apply the preconditioner
+   (device memory held by another allocator, latency-bound loops, fixed footprints).
+   Limit: c*N1*N2*(N3/2+1) <= 524288 (e.g. 64^3 elastic); larger grids return
+   UNOCG_ERR_INVALID_ARG and launch nothing.  The UNO weights must already be prepared on the
+   device (unocg_set_uno_weights after unocg_set_phase_properties), else UNOCG_ERR_STATE.
+   The first call on a device looks up the scratch address (cudaGetSymbolAddress); make that
+   first call before any stream capture.  No part of the scratch needs to start at zero.
+   Every call on a device uses the same scratch: calls whose work overlaps in time (different
+   streams, contexts or host threads without ordering between them) race and corrupt each
+   other's results; order them on one stream or with events.                               */
+int unocg_apply_uno_dev_noalloc(unocg_ctx* ctx, int instance, const double* r_dev, double* s_dev, void* stream);
 /* Right-hand side f of load `load` (Sec. 6): double [c][N1][N2][N3].                        */
 int unocg_rhs_dev(unocg_ctx* ctx, int instance, int load, double* f_dev, void* stream);
 

@@ -84,6 +84,7 @@ SIGNATURES = {
     "unocg_uno_backward_dev": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp]),
     "unocg_apply_K_dev": (_i, [_vp, _i, _vp, _vp, _vp]),
     "unocg_apply_uno_dev": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "unocg_apply_uno_dev_noalloc": (_i, [_vp, _i, _vp, _vp, _vp]),
     "unocg_rhs_dev": (_i, [_vp, _i, _i, _vp, _vp]),
 }
 

@@ -185,6 +185,11 @@ def unocg_apply_uno_dev(ctx, instance: int, r_dev, s_dev, stream=None):
                                                 C.c_void_p(s_dev.data_ptr()), _stream(stream)))
 
 
+def unocg_apply_uno_dev_noalloc(ctx, instance: int, r_dev, s_dev, stream=None):
+    _check(ctx, _lib.load().unocg_apply_uno_dev_noalloc(ctx, instance, C.c_void_p(r_dev.data_ptr()),
+                                                        C.c_void_p(s_dev.data_ptr()), _stream(stream)))
+
+
 def unocg_rhs_dev(ctx, instance: int, load: int, f_dev, stream=None):
     _check(ctx, _lib.load().unocg_rhs_dev(ctx, instance, load, C.c_void_p(f_dev.data_ptr()), _stream(stream)))
 

@@ -1228,6 +1228,81 @@ extern "C" int unocg_apply_uno_dev(unocg_ctx* ctx, int instance, const double* r
   return UNOCG_OK;
 }
 
+// ------------------------------------------------------------------ allocation-free UNO apply
+// unocg_apply_uno_dev takes its two spectra from cudaMallocAsync.  Some callers cannot allocate
+// at the moment they apply the preconditioner: a framework whose caching allocator already owns
+// the device memory (the stream-ordered pool then has no room), a latency-bound loop that must
+// not enter the allocator, or a deployment that needs its device footprint fixed when the
+// library loads.  unocg_apply_uno_dev_noalloc serves them from this file-scope scratch instead.
+// Its two halves hold the forward spectrum T r and the multiplied spectrum Q T r; nothing in it
+// has to start at zero (the forward pass writes every value of the first half before the axis-1
+// pass reads it, and the axis-1 pass writes every value of the second half).
+constexpr size_t kNoAllocSpectrum = 524288;  // complex FP64 values per half (8 MiB each)
+static __device__ __align__(256) double2 g_noalloc_scratch[2 * kNoAllocSpectrum];
+
+namespace {
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double2* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Address of the scratch on the current device, looked up once per device (with that device
+// current) and cached.
+cudaError_t noalloc_scratch(double2** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_addr[dev] = static_cast<double2*>(p);
+  }
+  *out = g_noalloc_addr[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
+extern "C" int unocg_apply_uno_dev_noalloc(unocg_ctx* ctx, int instance, const double* r_dev, double* s_dev,
+                                           void* stream) {
+  if (!ctx || !r_dev || !s_dev) return fail(ctx, UNOCG_ERR_INVALID_ARG, "null argument");
+  if (instance < 0 || instance >= ctx->B) return fail(ctx, UNOCG_ERR_INVALID_ARG, "instance out of range");
+  if (ctx->wkind < 0) return fail(ctx, UNOCG_ERR_STATE, "set UNO weights first");
+  // preparing the weights allocates: they must already be on the device
+  if (ctx->q_dirty)
+    return fail(ctx, UNOCG_ERR_STATE,
+                "UNO weights are not prepared on the device (set the phase properties, then the weights)");
+  const size_t m = (size_t)ctx->c * ctx->g.nh;
+  if (m > kNoAllocSpectrum)
+    return fail(ctx, UNOCG_ERR_INVALID_ARG,
+                "grid too large for the static scratch: c*N1*N2*(N3/2+1) = " + std::to_string(m) +
+                    " complex values, the limit is " + std::to_string(kNoAllocSpectrum));
+  double2* scratch = nullptr;
+  cudaError_t e = noalloc_scratch(&scratch);
+  if (e != cudaSuccess) return fail(ctx, UNOCG_ERR_CUDA, std::string("scratch address: ") + cudaGetErrorString(e));
+  double2* hat = scratch;
+  double2* shat = scratch + kNoAllocSpectrum;
+  cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
+  PlaneFwdArgs<double> pf{};
+  pf.g = ctx->g; pf.c = ctx->c; pf.BL = 1; pf.src = r_dev; pf.hat = hat; pf.ft = tables(ctx, true); pf.standalone = 1;
+  e = fwd_transform<double>(pf, s, 0);
+  if (e == cudaSuccess) {
+    LineArgs<double, double> la{};
+    la.g = ctx->g; la.c = ctx->c; la.BL = 1; la.L = 1; la.hat = hat; la.shat = shat;
+    la.Q = ctx->Q64 + (ctx->Bq > 1 ? (long long)instance * ctx->g.nh * (ctx->c == 1 ? 1 : 6) : 0);
+    la.q_inst_stride = 0; la.scale = 1.0 / (double)ctx->g.n; la.ft = tables(ctx, true); la.standalone = 1;
+    e = launch_line<double, double>(la, 0, s);
+  }
+  if (e == cudaSuccess) {
+    PlaneInvArgs<double> pi{};
+    pi.g = ctx->g; pi.c = ctx->c; pi.BL = 1; pi.shat = shat; pi.dst = s_dev; pi.ft = tables(ctx, true); pi.standalone = 1;
+    e = inv_transform<double>(pi, s);
+  }
+  if (e != cudaSuccess) return fail(ctx, UNOCG_ERR_CUDA, cudaGetErrorString(e));
+  return UNOCG_OK;
+}
+
 extern "C" int unocg_rhs_dev(unocg_ctx* ctx, int instance, int load, double* f_dev, void* stream) {
   if (!ctx || !f_dev) return fail(ctx, UNOCG_ERR_INVALID_ARG, "null argument");
   if (!ctx->have_phase || !ctx->have_props || !ctx->have_loads) return fail(ctx, UNOCG_ERR_STATE, "inputs missing");
