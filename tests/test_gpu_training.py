@@ -137,19 +137,30 @@ def test_config4_training_workload():
     assert max(iters) < 5000
     theta0 = tr.reference_theta(shape, 0.5 * (1.0 + np.sqrt(5.0 * 100.0)))
     theta, losses = tr.train(f, u, theta0, epochs=200, batch=64, lr=1e-2)
-    assert losses[-1] < 0.9 * losses[0]
-    # trained weights in a solve (held-out instances)
+    # the start is the reference-medium operator, already a good member of the class: the
+    # loss falls by a few per cent and does not drift back up
+    assert losses[-1] < 0.97 * losses[0]
+    assert losses[-1] <= 1.02 * min(losses)
+    # trained weights in a solve (held-out instances): to tolerance, in no more iterations
+    # than the starting weights need
     th = theta.cpu().numpy().astype(np.float64)
+    its_start, its_trained = 0, 0
     for i in range(512, 516):
         w = workload(4, i)
-        h = Homogenization(_lib.THERMAL, shape)
-        h.set_microstructure(w["phase"], 2)
-        h.set_phase_properties(w["props"])
-        h.set_macro_load(np.eye(3)[:1])
-        h.set_uno_weights(_lib.W_THETA, th, 0.0)
-        info = h.solve(tol=1e-6, max_iter=3000, precond=_lib.PRECOND_UNO, precision=_lib.MIXED)
-        assert info.status == _lib.OK
-        h.close()
+        its = []
+        for weights in (theta0, th):
+            h = Homogenization(_lib.THERMAL, shape)
+            h.set_microstructure(w["phase"], 2)
+            h.set_phase_properties(w["props"])
+            h.set_macro_load(np.eye(3)[:1])
+            h.set_uno_weights(_lib.W_THETA, np.asarray(weights, dtype=np.float64), 0.0)
+            info = h.solve(tol=1e-6, max_iter=3000, precond=_lib.PRECOND_UNO, precision=_lib.MIXED)
+            assert info.status == _lib.OK and np.all(info.true_rel_res <= 1e-6)
+            its.append(int(info.iters[0]))
+            h.close()
+        its_start += its[0]
+        its_trained += its[1]
+    assert its_trained <= its_start + 4
     # weight gradient on 4 instances against central differences of the FP64 oracle loss
     f4 = f[:4].cpu().numpy().astype(np.float64)
     u4 = u[:4].cpu().numpy().astype(np.float64)
