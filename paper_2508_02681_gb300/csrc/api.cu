@@ -484,6 +484,7 @@ static int ensure_workspace(unocg_ctx* ctx, int precision, int precond) {
   size_t need = 0;
   need = std::max(need, (size_t)BL * line_blocks_x(ctx->g, ctx->c, 8) * 2);
   need = std::max(need, (size_t)BL * line_blocks_x(ctx->g, ctx->c, 16) * 2);
+  need = std::max(need, (size_t)BL * line_reg_blocks_x(ctx->g) * 2);
   need = std::max(need, (size_t)BL * node_blocks_x(ctx->g));
   need = std::max(need, (size_t)BL * ku_blocks_x(ctx->g, ctx->c));
   need = std::max(need, (size_t)BL * jac_blocks_x((long long)ctx->c * n, BL));

@@ -536,7 +536,7 @@ static inline size_t rows_smem(const Grid& g, int rows, int elem_bytes) {
 #ifdef UNOCG_FFT_HOST_DEFS
 bool plane_fits(const Grid& g, int elem_bytes) { return plane_smem(g, elem_bytes) <= 220 * 1024; }
 int plane_rows(const Grid& g, int elem_bytes) {
-  if (plane_fits(g, elem_bytes)) return 0;
+  if (plane_reg_ok(g, elem_bytes) || plane_fits(g, elem_bytes)) return 0;
   for (int rows = g.n2 / 2; rows >= 1; --rows)
     if (g.n2 % rows == 0 && rows_smem(g, rows, elem_bytes) <= 200 * 1024) return rows;
   return -1;
@@ -559,6 +559,7 @@ template cudaError_t launch_cols<float>(const ColArgs<float>&, int, cudaStream_t
 
 template <typename T> cudaError_t launch_plane_fwd(const PlaneFwdArgs<T>& a, cudaStream_t s) {
   const int eb = sizeof(cplx<T>);
+  if (!a.rows && plane_reg_ok(a.g, eb)) return launch_plane_fwd_reg<T>(a, s);
   if (a.rows) {
     size_t smem = rows_smem(a.g, a.rows, eb);
     dim3 grid(a.c * a.g.n1 * (a.g.n2 / a.rows), a.BL);
@@ -575,6 +576,7 @@ template <typename T> cudaError_t launch_plane_fwd(const PlaneFwdArgs<T>& a, cud
 
 template <typename T> cudaError_t launch_plane_inv(const PlaneInvArgs<T>& a, cudaStream_t s) {
   const int eb = sizeof(cplx<T>);
+  if (!a.rows && plane_reg_ok(a.g, eb)) return launch_plane_inv_reg<T>(a, s);
   if (a.rows) {
     size_t smem = rows_smem(a.g, a.rows, eb);
     dim3 grid(a.c * a.g.n1 * (a.g.n2 / a.rows), a.BL);
@@ -626,6 +628,7 @@ cudaError_t launch_line(const LineArgs<T, QT>& a, int backward, cudaStream_t s) 
   constexpr bool cg = !(std::is_same<T, float>::value && std::is_same<QT, float>::value);
   constexpr bool apply = !std::is_same<QT, __nv_bfloat16>::value;
   constexpr bool bwd = std::is_same<T, float>::value && std::is_same<QT, float>::value;
+  if (!backward && line_reg_ok(a.g, a.c, sizeof(cplx<T>))) return launch_line_reg<T, QT>(a, s);
   if (backward) {
     if constexpr (bwd) {
       if (a.c == 1) return launch_line_cc<T, QT, 1, 2>(a, s);

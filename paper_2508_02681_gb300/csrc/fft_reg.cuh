@@ -1,0 +1,141 @@
+// Register-resident line FFTs of compile-time power-of-two length, for the transform passes of
+// the UNO preconditioner (Algorithm 2) on grids whose axes are 16..256 points long.
+//
+// A line of N = V * G complex values is held by G cooperating threads of one warp, V values
+// each.  With n = g + G n1 (g < G, n1 < V) and k = k1 + V k2 (k1 < V, k2 < G),
+//
+//   X[k1 + V k2] = sum_g W_G^{g k2} W_N^{g k1} sum_n1 W_V^{n1 k1} x[g + G n1],
+//
+// so a line transform is a V-point DFT in every thread, a twiddle W_N^{g k1}, one exchange of
+// values between the G threads through shared memory (synchronised by __syncwarp only), and
+// V/G G-point DFTs per thread.  Two data distributions occur:
+//   natural   : thread g holds v[n1] = x[g + G n1], n1 < V;
+//   scattered : thread g holds v[j G + k2] = X[k1 + V k2] with k1 = g V/G + j (j < V/G).
+// fft_dist_a maps natural to scattered, fft_dist_b scattered to natural (the same identity
+// read from the other side).  Both take the direction DIR (-1 forward, +1 inverse; the
+// transforms are unnormalized), so a forward transform followed by an inverse one needs no
+// redistribution in between.
+//
+// Exchange scratch: the N complex slots of the line at scr[s * ss], s < N.  The value of
+// (k1, t) lives in slot k1 G + ((t + k1 / (V/G)) mod G); the rotation spreads the accesses of a
+// warp over the shared-memory banks for the lane layouts used by the kernels.
+#pragma once
+#include "fft.cuh"
+
+namespace unocg {
+
+// radix-16 DFT, natural order in and out: 4 x 4 with the inner twiddles W_16^(a b)
+template <int DIR, typename C> __device__ __forceinline__ void dft16(C* v) {
+  using T = decltype(v[0].x);
+  const T c1 = (T)0.92387953251128675613, s1 = (T)0.38268343236508977173;  // cos, sin(pi/8)
+  const T h = (T)0.70710678118654752440;
+  C y[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    C t[4] = {v[a], v[a + 4], v[a + 8], v[a + 12]};
+    dft4<DIR>(t);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) y[a][b] = t[b];
+  }
+  // y[a][b] *= W_16^(DIR a b) for a, b in 1..3; products a b in {1, 2, 3, 4, 6, 9}
+  auto tw = [&](C x, int m) -> C {
+    // W_16^m (forward, DIR < 0): cos(2 pi m / 16) - i sin(2 pi m / 16)
+    T cr, si;
+    switch (m) {
+      case 1: cr = c1; si = s1; break;
+      case 2: cr = h; si = h; break;
+      case 3: cr = s1; si = c1; break;
+      case 4: cr = (T)0; si = (T)1; break;
+      case 6: cr = -h; si = h; break;
+      default: cr = -c1; si = -s1; break;  // m = 9
+    }
+    const T sg = DIR < 0 ? -si : si;
+    return mk<T>(x.x * cr - x.y * sg, x.x * sg + x.y * cr);
+  };
+#pragma unroll
+  for (int a = 1; a < 4; ++a)
+#pragma unroll
+    for (int b = 1; b < 4; ++b) y[a][b] = tw(y[a][b], a * b);
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    C t[4] = {y[0][b], y[1][b], y[2][b], y[3][b]};
+    dft4<DIR>(t);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) v[b + 4 * c] = t[c];
+  }
+}
+
+template <int R, int DIR, typename C> __device__ __forceinline__ void dft_pow2(C* v) {
+  if constexpr (R == 2) dft2<DIR>(v);
+  else if constexpr (R == 4) dft4<DIR>(v);
+  else if constexpr (R == 8) dft8<DIR>(v);
+  else if constexpr (R == 16) dft16<DIR>(v);
+}
+
+// split N = V * G with G | V, G <= 16, V <= 16
+template <int N> struct RegSplit;
+template <> struct RegSplit<16> { static constexpr int V = 4, G = 4; };
+template <> struct RegSplit<32> { static constexpr int V = 8, G = 4; };
+template <> struct RegSplit<64> { static constexpr int V = 8, G = 8; };
+template <> struct RegSplit<128> { static constexpr int V = 16, G = 8; };
+template <> struct RegSplit<256> { static constexpr int V = 16, G = 16; };
+
+template <int N> __device__ __forceinline__ int reg_slot(int k1, int t) {
+  constexpr int V = RegSplit<N>::V, G = RegSplit<N>::G, VG = V / G;
+  return k1 * G + ((t + k1 / VG) & (G - 1));
+}
+
+// x * W^(DIR m) with W the forward root stored in the table
+template <int DIR, typename C> __device__ __forceinline__ C twiddle(C x, C w) {
+  if (DIR > 0) w.y = -w.y;
+  return cmul(x, w);
+}
+
+// natural -> scattered (see the header).  scr: this line's N slots at stride ss; tw: W_N^m.
+// All lanes of the warp must call it; scr may be reused after the caller's next __syncwarp().
+template <int N, int DIR, typename C>
+__device__ __forceinline__ void fft_dist_a(C* v, int g, C* scr, int ss, const C* __restrict__ tw) {
+  constexpr int V = RegSplit<N>::V, G = RegSplit<N>::G, VG = V / G;
+  dft_pow2<V, DIR>(v);
+#pragma unroll
+  for (int k1 = 1; k1 < V; ++k1) v[k1] = twiddle<DIR>(v[k1], tw[g * k1]);
+  __syncwarp();
+#pragma unroll
+  for (int k1 = 0; k1 < V; ++k1) scr[reg_slot<N>(k1, g) * ss] = v[k1];
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < VG; ++j)
+#pragma unroll
+    for (int t = 0; t < G; ++t) v[j * G + t] = scr[reg_slot<N>(g * VG + j, t) * ss];
+#pragma unroll
+  for (int j = 0; j < VG; ++j) dft_pow2<G, DIR>(v + j * G);
+}
+
+// scattered -> natural
+template <int N, int DIR, typename C>
+__device__ __forceinline__ void fft_dist_b(C* v, int g, C* scr, int ss, const C* __restrict__ tw) {
+  constexpr int V = RegSplit<N>::V, G = RegSplit<N>::G, VG = V / G;
+#pragma unroll
+  for (int j = 0; j < VG; ++j) dft_pow2<G, DIR>(v + j * G);
+#pragma unroll
+  for (int j = 0; j < VG; ++j)
+#pragma unroll
+    for (int t = 1; t < G; ++t) v[j * G + t] = twiddle<DIR>(v[j * G + t], tw[t * (g * VG + j)]);
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < VG; ++j)
+#pragma unroll
+    for (int t = 0; t < G; ++t) scr[reg_slot<N>(g * VG + j, t) * ss] = v[j * G + t];
+  __syncwarp();
+#pragma unroll
+  for (int k1 = 0; k1 < V; ++k1) v[k1] = scr[reg_slot<N>(k1, g) * ss];
+  dft_pow2<V, DIR>(v);
+}
+
+// index k of value v[j G + k2] in the scattered distribution of thread g
+template <int N> __device__ __forceinline__ int scat_index(int g, int j, int k2) {
+  constexpr int V = RegSplit<N>::V, G = RegSplit<N>::G, VG = V / G;
+  return g * VG + j + V * k2;
+}
+
+}  // namespace unocg

@@ -1,0 +1,535 @@
+// Register-FFT versions of the three transform passes of UNO-CG (Algorithm 2), for grids whose
+// axes are powers of two (planes N2 = N3 in {32, 64, 128}, axis 1 in {16, ..., 256}).  Same
+// arguments, data layouts and CG bookkeeping as the shared-memory Stockham passes in
+// fft_kernels.cuh, which remain the path for every other grid.
+//
+//   k_plane_fwd_reg: one (field, i1) plane per block.  Row phase: every row of N3 reals is the
+//     half-length complex line z[m] = x[2m] + i x[2m+1], loaded straight from global memory
+//     into the registers of G3 threads (fused r <- r - alpha p and ||r||_inf), transformed
+//     (fft_dist_a), split into the half spectrum X(k), k <= N3/2, in the plane buffer.  One
+//     block barrier.  Column phase: every k3 column transformed along axis 2 by G2 threads and
+//     written to the spectrum buffer.
+//   k_plane_inv_reg: the mirror image, fused with u <- u + alpha d_old, d <- s + beta d_old.
+//   k_line_reg: W positions (k2, k3) per warp, all c components: axis-1 transform, s = Q r / n,
+//     Parseval partials, inverse axis-1 transform; no block barrier until the reductions.
+#include "kargs.h"
+#include "cg.cuh"
+#include "fft_reg.cuh"
+
+namespace unocg {
+
+namespace {
+
+constexpr int pitch_reg(int n3h, int cols) {
+  int p = n3h > cols ? n3h : cols;
+  while (p % 16 != 4) ++p;
+  return p;
+}
+
+template <typename T, int N2, int N3> struct PlaneReg {
+  static constexpr int Nh = N3 / 2, n3h = N3 / 2 + 1;
+  static constexpr int G3 = RegSplit<Nh>::G, V3 = RegSplit<Nh>::V;
+  static constexpr int G2 = RegSplit<N2>::G, V2 = RegSplit<N2>::V;
+  static constexpr int RPW = 32 / G3;                  // rows per warp
+  static constexpr int CW = 32 / G2;                   // columns per warp
+  static constexpr int NCG = (n3h + CW - 1) / CW;      // column groups
+  static constexpr int NRG = N2 / RPW;                 // row groups
+  static constexpr int P = pitch_reg(n3h, NCG * CW);   // plane pitch (complex), = 4 mod 16
+  static constexpr int NW = NCG > (NRG < 16 ? NRG : 16) ? NCG : (NRG < 16 ? NRG : 16);
+  static constexpr size_t smem = ((size_t)N2 * P + Nh + N2 + N3) * sizeof(cplx<T>);
+};
+
+template <typename T>
+__device__ __forceinline__ void load_tw_reg(cplx<T>* dst, const void* src, int N) {
+  const cplx<T>* s = (const cplx<T>*)src;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) dst[i] = s[i];
+}
+
+// X(k), X(Nh-k) from the half-length spectrum Z in one row (in place), pair k <= Nh/2
+template <typename T>
+__device__ __forceinline__ void r2c_pair(cplx<T>* b, int k, int Nh, const cplx<T>* __restrict__ twN) {
+  using C = cplx<T>;
+  const T half = (T)0.5;
+  if (k == 0) {
+    C z = b[0];
+    b[0] = mk<T>(z.x + z.y, (T)0);
+    b[Nh] = mk<T>(z.x - z.y, (T)0);
+    return;
+  }
+  const int k2 = Nh - k;
+  C zk = b[k], zm = b[k2];
+  C e = mk<T>(half * (zk.x + zm.x), half * (zk.y - zm.y));
+  C o = mk<T>(half * (zk.y + zm.y), -half * (zk.x - zm.x));
+  C xk = cadd(e, cmul(twN[k], o));
+  if (k2 != k) {
+    C e2 = mk<T>(half * (zm.x + zk.x), half * (zm.y - zk.y));
+    C o2 = mk<T>(half * (zm.y + zk.y), -half * (zm.x - zk.x));
+    b[k2] = cadd(e2, cmul(twN[k2], o2));
+  }
+  b[k] = xk;
+}
+
+// inverse of r2c_pair up to the factor of the unnormalized inverse (see c2r_pre)
+template <typename T>
+__device__ __forceinline__ void c2r_pair(cplx<T>* b, int k, int Nh, const cplx<T>* __restrict__ twN) {
+  using C = cplx<T>;
+  if (k == 0) {
+    T x0 = b[0].x, xn = b[Nh].x;
+    b[0] = mk<T>(x0 + xn, x0 - xn);
+    return;
+  }
+  const int k2 = Nh - k;
+  C xk = b[k], xm = b[k2];
+  C wk = twN[k];
+  wk.y = -wk.y;
+  C e = mk<T>(xk.x + xm.x, xk.y - xm.y);
+  C o = cmul(mk<T>(xk.x - xm.x, xk.y + xm.y), wk);
+  C zk = mk<T>(e.x - o.y, e.y + o.x);
+  if (k2 != k) {
+    C w2 = twN[k2];
+    w2.y = -w2.y;
+    C e2 = mk<T>(xm.x + xk.x, xm.y - xk.y);
+    C o2 = cmul(mk<T>(xm.x - xk.x, xm.y + xk.y), w2);
+    b[k2] = mk<T>(e2.x - o2.y, e2.y + o2.x);
+  }
+  b[k] = zk;
+}
+
+}  // namespace
+
+// ============================================================================ forward planes
+template <typename T, int N2, int N3>
+__global__ void __launch_bounds__(PlaneReg<T, N2, N3>::NW * 32) k_plane_fwd_reg(PlaneFwdArgs<T> a) {
+  using C = cplx<T>;
+  using PR = PlaneReg<T, N2, N3>;
+  constexpr int Nh = PR::Nh, n3h = PR::n3h, G3 = PR::G3, V3 = PR::V3, G2 = PR::G2, V2 = PR::V2, P = PR::P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red_sh[32];
+  C* plane = reinterpret_cast<C*>(smem_raw);
+  C* tw3h = plane + N2 * P;
+  C* tw2 = tw3h + Nh;
+  C* tw3 = tw2 + N2;
+  load_tw_reg<T>(tw3h, a.ft.tw3h, Nh);
+  load_tw_reg<T>(tw2, a.ft.tw2, N2);
+  load_tw_reg<T>(tw3, a.ft.tw3, N3);
+  const int bl = blockIdx.y;
+  bool active = true;
+  double alpha = 0.0;
+  if (!a.standalone) {
+    active = !a.sc[bl].done && (!a.after_replace || a.sc[bl].need_replace);
+    alpha = a.after_replace ? 0.0 : a.sc[bl].alpha;
+  }
+  __syncthreads();
+  T lmax = (T)0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (active) {
+    const int plane_id = blockIdx.x;
+    const int comp = plane_id / a.g.n1, i1 = plane_id - comp * a.g.n1;
+    const long long field = (long long)bl * a.c + comp;
+    const long long base = (field * a.g.n1 + i1) * (long long)(N2 * N3);
+    const T al = (T)alpha;
+    const bool upd = alpha != 0.0;
+    // ---- rows: axis 3
+    for (int rg = warp; rg < PR::NRG; rg += PR::NW) {
+      const int row = rg * PR::RPW + lane / G3, g = lane % G3;
+      C v[V3];
+      if (a.standalone) {
+        const C* src = reinterpret_cast<const C*>(a.src + base) + row * Nh;
+#pragma unroll
+        for (int n1 = 0; n1 < V3; ++n1) v[n1] = src[g + G3 * n1];
+      } else {
+        C* r = reinterpret_cast<C*>(a.r + base) + row * Nh;
+        const C* p = reinterpret_cast<const C*>(a.p + base) + row * Nh;
+#pragma unroll
+        for (int n1 = 0; n1 < V3; ++n1) v[n1] = r[g + G3 * n1];
+        if (upd) {
+          C q[V3];
+#pragma unroll
+          for (int n1 = 0; n1 < V3; ++n1) q[n1] = p[g + G3 * n1];
+#pragma unroll
+          for (int n1 = 0; n1 < V3; ++n1) {
+            v[n1].x -= al * q[n1].x;
+            v[n1].y -= al * q[n1].y;
+            r[g + G3 * n1] = v[n1];
+          }
+        }
+#pragma unroll
+        for (int n1 = 0; n1 < V3; ++n1) lmax = fmax(lmax, fmax(fabs(v[n1].x), fabs(v[n1].y)));
+      }
+      C* rs = plane + row * P;
+      fft_dist_a<Nh, -1>(v, g, rs, 1, tw3h);
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < V3 / G3; ++j)
+#pragma unroll
+        for (int k2 = 0; k2 < G3; ++k2) rs[scat_index<Nh>(g, j, k2)] = v[j * G3 + k2];
+      __syncwarp();
+      for (int k = g; k <= Nh / 2; k += G3) r2c_pair<T>(rs, k, Nh, tw3);
+    }
+    __syncthreads();
+    // ---- columns: axis 2
+    C* out = a.hat + (field * a.g.n1 + i1) * (long long)(N2 * n3h);
+    for (int cg = warp; cg < PR::NCG; cg += PR::NW) {
+      const int col = cg * PR::CW + lane % PR::CW, g = lane / PR::CW;
+      const bool on = col < n3h;
+      C v[V2];
+#pragma unroll
+      for (int n1 = 0; n1 < V2; ++n1) v[n1] = plane[(g + G2 * n1) * P + col];
+      fft_dist_a<N2, -1>(v, g, plane + col, P, tw2);
+      if (on) {
+#pragma unroll
+        for (int j = 0; j < V2 / G2; ++j)
+#pragma unroll
+          for (int k2 = 0; k2 < G2; ++k2) out[scat_index<N2>(g, j, k2) * n3h + col] = v[j * G2 + k2];
+      }
+      __syncwarp();
+    }
+  }
+  if (a.standalone) return;
+  const double bmax = block_max_t(lmax, red_sh);
+  if (threadIdx.x == 0 && active) atomic_max_nonneg(&a.sc[bl].rmax_bits, bmax);
+  if (last_block(a.ticket)) {
+    residual_decision(a.sc, a.BL, a.ctl, a.after_replace);
+    if (threadIdx.x == 0) *a.ticket = 0u;
+  }
+}
+
+// ============================================================================ inverse planes
+template <typename T, int N2, int N3>
+__global__ void __launch_bounds__(PlaneReg<T, N2, N3>::NW * 32) k_plane_inv_reg(PlaneInvArgs<T> a) {
+  using C = cplx<T>;
+  using PR = PlaneReg<T, N2, N3>;
+  constexpr int Nh = PR::Nh, n3h = PR::n3h, G3 = PR::G3, V3 = PR::V3, G2 = PR::G2, V2 = PR::V2, P = PR::P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* plane = reinterpret_cast<C*>(smem_raw);
+  C* tw3h = plane + N2 * P;
+  C* tw2 = tw3h + Nh;
+  C* tw3 = tw2 + N2;
+  const int bl = blockIdx.y;
+  if (!a.standalone && a.sc[bl].done) return;
+  load_tw_reg<T>(tw3h, a.ft.tw3h, Nh);
+  load_tw_reg<T>(tw2, a.ft.tw2, N2);
+  load_tw_reg<T>(tw3, a.ft.tw3, N3);
+  const double al_d = a.standalone ? 0.0 : a.sc[bl].alpha, be_d = a.standalone ? 0.0 : a.sc[bl].beta;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int plane_id = blockIdx.x;
+  const int comp = plane_id / a.g.n1, i1 = plane_id - comp * a.g.n1;
+  const long long field = (long long)bl * a.c + comp;
+  // ---- columns: inverse axis 2
+  const C* in = a.shat + (field * a.g.n1 + i1) * (long long)(N2 * n3h);
+  for (int cg = warp; cg < PR::NCG; cg += PR::NW) {
+    const int col = cg * PR::CW + lane % PR::CW, g = lane / PR::CW;
+    const bool on = col < n3h;
+    C v[V2];
+#pragma unroll
+    for (int j = 0; j < V2 / G2; ++j)
+#pragma unroll
+      for (int k2 = 0; k2 < G2; ++k2)
+        v[j * G2 + k2] = on ? in[scat_index<N2>(g, j, k2) * n3h + col] : mk<T>((T)0, (T)0);
+    fft_dist_b<N2, +1>(v, g, plane + col, P, tw2);
+    __syncwarp();
+#pragma unroll
+    for (int n1 = 0; n1 < V2; ++n1) plane[(g + G2 * n1) * P + col] = v[n1];
+    __syncwarp();
+  }
+  __syncthreads();
+  // ---- rows: inverse axis 3 (half spectrum -> real row)
+  const long long base = (field * a.g.n1 + i1) * (long long)(N2 * N3);
+  const T alpha = (T)al_d, beta = (T)be_d;
+  for (int rg = warp; rg < PR::NRG; rg += PR::NW) {
+    const int row = rg * PR::RPW + lane / G3, g = lane % G3;
+    C* rs = plane + row * P;
+    for (int k = g; k <= Nh / 2; k += G3) c2r_pair<T>(rs, k, Nh, tw3);
+    __syncwarp();
+    C v[V3];
+#pragma unroll
+    for (int j = 0; j < V3 / G3; ++j)
+#pragma unroll
+      for (int k2 = 0; k2 < G3; ++k2) v[j * G3 + k2] = rs[scat_index<Nh>(g, j, k2)];
+    fft_dist_b<Nh, +1>(v, g, rs, 1, tw3h);
+    if (a.standalone) {
+      C* dst = reinterpret_cast<C*>(a.dst + base) + row * Nh;
+#pragma unroll
+      for (int n1 = 0; n1 < V3; ++n1) dst[g + G3 * n1] = v[n1];
+    } else {
+      C* d = reinterpret_cast<C*>(a.d + base) + row * Nh;
+      C* u = reinterpret_cast<C*>(a.u + base) + row * Nh;
+      C dv[V3], uv[V3];
+#pragma unroll
+      for (int n1 = 0; n1 < V3; ++n1) {
+        dv[n1] = d[g + G3 * n1];
+        uv[n1] = u[g + G3 * n1];
+      }
+#pragma unroll
+      for (int n1 = 0; n1 < V3; ++n1) {
+        C uu = uv[n1];
+        uu.x += alpha * dv[n1].x;
+        uu.y += alpha * dv[n1].y;
+        u[g + G3 * n1] = uu;
+        d[g + G3 * n1] = mk<T>(v[n1].x + beta * dv[n1].x, v[n1].y + beta * dv[n1].y);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// ============================================================================ axis 1 + multiply
+template <typename T, typename QT> struct QRead;
+template <typename T> struct QRead<T, double> {
+  static __device__ __forceinline__ T get(const double* q, long long i) { return (T)__ldg(q + i); }
+};
+template <typename T> struct QRead<T, float> {
+  static __device__ __forceinline__ T get(const float* q, long long i) { return (T)__ldg(q + i); }
+};
+template <typename T> struct QRead<T, __nv_bfloat16> {
+  static __device__ __forceinline__ T get(const __nv_bfloat16* q, long long i) {
+    return (T)__bfloat162float(__ldg(q + i));
+  }
+};
+
+constexpr int kLineRegWarps = 8;
+
+template <typename T, typename QT, int CC, int N1, int MODE>
+__global__ void __launch_bounds__(kLineRegWarps * 32) k_line_reg(LineArgs<T, QT> a) {
+  using C = cplx<T>;
+  constexpr int G = RegSplit<N1>::G, V = RegSplit<N1>::V, VG = V / G, W = 32 / G;
+  constexpr int NW = kLineRegWarps;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red_sh[32];
+  C* tw1 = reinterpret_cast<C*>(smem_raw);
+  C* scr_all = tw1 + N1;
+  load_tw_reg<T>(tw1, a.ft.tw1, N1);
+  const int bl = blockIdx.y;
+  const bool active = (MODE != 0) || !a.sc[bl].done;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane / W, w = lane % W;
+  const int M = a.g.n2 * a.g.n3h;
+  DotAcc<T> gam, rso;
+  if (active) {
+    const int pos = (blockIdx.x * NW + warp) * W + w;
+    const bool on = pos < M;
+    const int k3 = on ? pos % a.g.n3h : 0;
+    const T wt = (k3 == 0 || 2 * k3 == a.g.n3) ? (T)1 : (T)2;
+    C* scr = scr_all + (size_t)warp * W * N1 + w;
+    const long long fbase = (long long)bl * CC * N1 * M;
+    C v[CC][V];
+#pragma unroll
+    for (int cc = 0; cc < CC; ++cc)
+#pragma unroll
+      for (int n1 = 0; n1 < V; ++n1) {
+        const long long gi = fbase + ((long long)(cc * N1 + g + G * n1)) * M + pos;
+        v[cc][n1] = on ? a.hat[gi] : mk<T>((T)0, (T)0);
+      }
+    if (MODE == 0 && a.flexible && on) {
+#pragma unroll
+      for (int cc = 0; cc < CC; ++cc)
+#pragma unroll
+        for (int n1 = 0; n1 < V; ++n1) {
+          const long long gi = fbase + ((long long)(cc * N1 + g + G * n1)) * M + pos;
+          const C so = a.shat[gi];
+          rso.add_prod(wt * v[cc][n1].x, so.x);
+          rso.add_prod(wt * v[cc][n1].y, so.y);
+        }
+    }
+#pragma unroll
+    for (int cc = 0; cc < CC; ++cc) fft_dist_a<N1, -1>(v[cc], g, scr, W, tw1);
+    // s_hat = Q(k) r_hat(k) / n and the Parseval partial of r . s
+    const long long qb = (long long)(bl / a.L) * a.q_inst_stride;
+    const T sc = (T)a.scale;
+    if (on) {
+#pragma unroll
+      for (int j = 0; j < VG; ++j)
+#pragma unroll
+        for (int k2 = 0; k2 < G; ++k2) {
+          const int k1 = scat_index<N1>(g, j, k2), e = j * G + k2;
+          const long long qi = qb + ((long long)k1 * M + pos) * (CC == 1 ? 1 : 6);
+          if constexpr (CC == 1) {
+            const T q = QRead<T, QT>::get(a.Q, qi) * sc;
+            const C R = v[0][e];
+            const C S = mk<T>(q * R.x, q * R.y);
+            if (MODE == 0) {
+              gam.add_prod(wt * R.x, S.x);
+              gam.add_prod(wt * R.y, S.y);
+            }
+            v[0][e] = S;
+          } else {
+            const T q1 = QRead<T, QT>::get(a.Q, qi + 0) * sc, q2 = QRead<T, QT>::get(a.Q, qi + 1) * sc;
+            const T q3 = QRead<T, QT>::get(a.Q, qi + 2) * sc, q4 = QRead<T, QT>::get(a.Q, qi + 3) * sc;
+            const T q5 = QRead<T, QT>::get(a.Q, qi + 4) * sc, q6 = QRead<T, QT>::get(a.Q, qi + 5) * sc;
+            const C R0 = v[0][e], R1 = v[1][e], R2 = v[2][e];
+            const C S0 = mk<T>(q1 * R0.x + q3 * R1.x + q6 * R2.x, q1 * R0.y + q3 * R1.y + q6 * R2.y);
+            const C S1 = mk<T>(q3 * R0.x + q2 * R1.x + q5 * R2.x, q3 * R0.y + q2 * R1.y + q5 * R2.y);
+            const C S2 = mk<T>(q6 * R0.x + q5 * R1.x + q4 * R2.x, q6 * R0.y + q5 * R1.y + q4 * R2.y);
+            if (MODE == 0) {
+              gam.add_prod(wt * R0.x, S0.x);
+              gam.add_prod(wt * R0.y, S0.y);
+              gam.add_prod(wt * R1.x, S1.x);
+              gam.add_prod(wt * R1.y, S1.y);
+              gam.add_prod(wt * R2.x, S2.x);
+              gam.add_prod(wt * R2.y, S2.y);
+            }
+            v[0][e] = S0;
+            v[1][e] = S1;
+            v[2][e] = S2;
+          }
+        }
+    }
+#pragma unroll
+    for (int cc = 0; cc < CC; ++cc) fft_dist_b<N1, +1>(v[cc], g, scr, W, tw1);
+    if (on) {
+#pragma unroll
+      for (int cc = 0; cc < CC; ++cc)
+#pragma unroll
+        for (int n1 = 0; n1 < V; ++n1) {
+          const long long gi = fbase + ((long long)(cc * N1 + g + G * n1)) * M + pos;
+          a.shat[gi] = v[cc][n1];
+        }
+    }
+  }
+  if (MODE != 0) return;
+  double2 pr;
+  pr.x = block_sum_acc(gam, red_sh);
+  pr.y = block_sum_acc(rso, red_sh);
+  if (threadIdx.x == 0) {
+    double* pp = a.red.part + ((long long)bl * gridDim.x + blockIdx.x) * 2;
+    pp[0] = pr.x;
+    pp[1] = pr.y;
+  }
+  if (last_block(a.red.ticket)) {
+    for (int b = warp; b < a.BL; b += NW) {
+      const double* pp = a.red.part + (long long)b * gridDim.x * 2;
+      double sg = warp_sum_partials(pp, gridDim.x, 2);
+      double sr = warp_sum_partials(pp + 1, gridDim.x, 2);
+      if (lane == 0 && !a.sc[b].done) direction_update(a.sc[b], sg, sr, a.flexible);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *a.red.ticket = 0u;
+  }
+}
+
+// ============================================================================ host side
+namespace {
+
+template <typename K, typename A>
+cudaError_t launch_reg(K kern, dim3 grid, int nth, size_t smem, const A& a, cudaStream_t s) {
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  kern<<<grid, nth, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+constexpr bool pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1)) == 0; }
+
+template <typename T> size_t plane_reg_smem(int n) {
+  switch (n) {
+    case 32: return PlaneReg<T, 32, 32>::smem;
+    case 64: return PlaneReg<T, 64, 64>::smem;
+    case 128: return PlaneReg<T, 128, 128>::smem;
+    default: return 0;
+  }
+}
+
+template <typename T, int N, typename Args, bool FWD>
+cudaError_t plane_reg_launch(const Args& a, cudaStream_t s) {
+  using PR = PlaneReg<T, N, N>;
+  dim3 grid(a.c * a.g.n1, a.BL);
+  if constexpr (FWD) return launch_reg(k_plane_fwd_reg<T, N, N>, grid, PR::NW * 32, PR::smem, a, s);
+  else return launch_reg(k_plane_inv_reg<T, N, N>, grid, PR::NW * 32, PR::smem, a, s);
+}
+
+}  // namespace
+
+bool plane_reg_ok(const Grid& g, int elem_bytes) {
+#ifdef UNOCG_NO_REG_FFT
+  return false;
+#endif
+  if (g.n2 != g.n3 || !pow2_in(g.n2, 32, 128)) return false;
+  const size_t smem = elem_bytes == 16 ? plane_reg_smem<double>(g.n2) : plane_reg_smem<float>(g.n2);
+  return smem > 0 && smem <= 220 * 1024;
+}
+
+template <typename T> cudaError_t launch_plane_fwd_reg(const PlaneFwdArgs<T>& a, cudaStream_t s) {
+  switch (a.g.n2) {
+    case 32: return plane_reg_launch<T, 32, PlaneFwdArgs<T>, true>(a, s);
+    case 64: return plane_reg_launch<T, 64, PlaneFwdArgs<T>, true>(a, s);
+    case 128: return plane_reg_launch<T, 128, PlaneFwdArgs<T>, true>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+template <typename T> cudaError_t launch_plane_inv_reg(const PlaneInvArgs<T>& a, cudaStream_t s) {
+  switch (a.g.n2) {
+    case 32: return plane_reg_launch<T, 32, PlaneInvArgs<T>, false>(a, s);
+    case 64: return plane_reg_launch<T, 64, PlaneInvArgs<T>, false>(a, s);
+    case 128: return plane_reg_launch<T, 128, PlaneInvArgs<T>, false>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+template cudaError_t launch_plane_fwd_reg<float>(const PlaneFwdArgs<float>&, cudaStream_t);
+template cudaError_t launch_plane_fwd_reg<double>(const PlaneFwdArgs<double>&, cudaStream_t);
+template cudaError_t launch_plane_inv_reg<float>(const PlaneInvArgs<float>&, cudaStream_t);
+template cudaError_t launch_plane_inv_reg<double>(const PlaneInvArgs<double>&, cudaStream_t);
+
+// axis 1: N1 in 16..256 for c = 1; up to 64 for c = 3 (three components of V values each
+// stay in registers, beyond that they would spill)
+bool line_reg_ok(const Grid& g, int c, int elem_bytes) {
+#ifdef UNOCG_NO_REG_FFT
+  return false;
+#endif
+  (void)elem_bytes;
+  if (!pow2_in(g.n1, 16, 256)) return false;
+  return c == 1 || g.n1 <= 64;
+}
+
+int line_reg_blocks_x(const Grid& g) {
+  if (!pow2_in(g.n1, 16, 256)) return 0;
+  int G = g.n1 <= 32 ? 4 : (g.n1 <= 128 ? 8 : 16);
+  const int per_block = kLineRegWarps * (32 / G);
+  const int M = g.n2 * g.n3h;
+  return (M + per_block - 1) / per_block;
+}
+
+namespace {
+template <typename T, typename QT, int CC, int N1, int MODE>
+cudaError_t line_reg_n(const LineArgs<T, QT>& a, cudaStream_t s) {
+  constexpr int G = RegSplit<N1>::G, W = 32 / G;
+  const size_t smem = ((size_t)N1 + (size_t)kLineRegWarps * W * N1) * sizeof(cplx<T>);
+  dim3 grid(line_reg_blocks_x(a.g), a.BL);
+  return launch_reg(k_line_reg<T, QT, CC, N1, MODE>, grid, kLineRegWarps * 32, smem, a, s);
+}
+template <typename T, typename QT, int CC, int MODE>
+cudaError_t line_reg_cc(const LineArgs<T, QT>& a, cudaStream_t s) {
+  switch (a.g.n1) {
+    case 16: return line_reg_n<T, QT, CC, 16, MODE>(a, s);
+    case 32: return line_reg_n<T, QT, CC, 32, MODE>(a, s);
+    case 64: return line_reg_n<T, QT, CC, 64, MODE>(a, s);
+    case 128:
+      if constexpr (CC == 3) return cudaErrorInvalidValue;
+      else return line_reg_n<T, QT, CC, 128, MODE>(a, s);
+    case 256:
+      if constexpr (CC == 3) return cudaErrorInvalidValue;
+      else return line_reg_n<T, QT, CC, 256, MODE>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+}  // namespace
+
+template <typename T, typename QT> cudaError_t launch_line_reg(const LineArgs<T, QT>& a, cudaStream_t s) {
+  // instantiated: (double, double) CG + apply; (float, bf16) CG; (float, float) apply
+  constexpr bool cg = !(std::is_same<T, float>::value && std::is_same<QT, float>::value);
+  constexpr bool apply = !std::is_same<QT, __nv_bfloat16>::value;
+  if (a.standalone) {
+    if constexpr (apply) return a.c == 1 ? line_reg_cc<T, QT, 1, 1>(a, s) : line_reg_cc<T, QT, 3, 1>(a, s);
+    return cudaErrorInvalidValue;
+  }
+  if constexpr (cg) return a.c == 1 ? line_reg_cc<T, QT, 1, 0>(a, s) : line_reg_cc<T, QT, 3, 0>(a, s);
+  return cudaErrorInvalidValue;
+}
+template cudaError_t launch_line_reg<double, double>(const LineArgs<double, double>&, cudaStream_t);
+template cudaError_t launch_line_reg<float, __nv_bfloat16>(const LineArgs<float, __nv_bfloat16>&, cudaStream_t);
+template cudaError_t launch_line_reg<float, float>(const LineArgs<float, float>&, cudaStream_t);
+
+}  // namespace unocg

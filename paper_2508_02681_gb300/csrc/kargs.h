@@ -165,6 +165,14 @@ template <typename T> cudaError_t launch_plane_fwd(const PlaneFwdArgs<T>& a, cud
 template <typename T, typename QT> cudaError_t launch_line(const LineArgs<T, QT>& a, int backward, cudaStream_t s);
 template <typename T> cudaError_t launch_plane_inv(const PlaneInvArgs<T>& a, cudaStream_t s);
 int line_blocks_x(const Grid& g, int c, int elem_bytes);
+// register-FFT passes for power-of-two axes (k_fft_reg.cu); the *_ok tests say whether they
+// apply to a grid (plane: N2 = N3 in {32, 64, 128}; axis 1: 16..256)
+bool plane_reg_ok(const Grid& g, int elem_bytes);
+bool line_reg_ok(const Grid& g, int c, int elem_bytes);
+int line_reg_blocks_x(const Grid& g);
+template <typename T> cudaError_t launch_plane_fwd_reg(const PlaneFwdArgs<T>& a, cudaStream_t s);
+template <typename T> cudaError_t launch_plane_inv_reg(const PlaneInvArgs<T>& a, cudaStream_t s);
+template <typename T, typename QT> cudaError_t launch_line_reg(const LineArgs<T, QT>& a, cudaStream_t s);
 // dynamic shared memory of the axis-1 pass (mode 2: backward, four line buffers)
 size_t line_smem_bytes(const Grid& g, int c, int elem_bytes, int mode);
 bool plane_fits(const Grid& g, int elem_bytes);

@@ -92,6 +92,32 @@ def test_uno_apply_reference_medium(physics, shape):
     api.unocg_destroy(ctx)
 
 
+# power-of-two axes: the register-FFT passes (square planes of 32..128, axis 1 of 16..256)
+REG_SHAPES = [(16, 32, 32), (32, 64, 64), (2, 128, 128), (64, 16, 20), (128, 8, 6), (256, 4, 4)]
+
+
+@pytest.mark.parametrize("physics", [1, 3])
+@pytest.mark.parametrize("shape", REG_SHAPES)
+def test_uno_apply_power_of_two_axes(physics, shape):
+    import torch
+    from paper_2508_02681_gb300 import _lib, api
+    c = 1 if physics == 1 else 3
+    phase = random_phase(shape, 2, seed=6)
+    props = _props(physics, 2, 4)
+    ctx = _ctx(physics, shape, phase, props)
+    api.unocg_set_uno_weights(ctx, _lib.W_REFERENCE_MEDIUM)
+    r = random_field((c,) + shape, seed=10)
+    Q = uno.reference_medium_Q(physics, props, shape)
+    s_ref = uno.uno_apply(Q, r)
+    rr = torch.tensor(r, device="cuda")
+    ss = torch.empty_like(rr)
+    api.unocg_apply_uno_dev(ctx, 0, rr, ss)
+    torch.cuda.synchronize()
+    # the oracle's symbol carries a rounding error ~ eps / theta_min^2 (see test_gpu_large)
+    assert rel(ss.cpu().numpy(), s_ref) < 1e-12 * max(1.0, (max(shape) / 64.0) ** 2)
+    api.unocg_destroy(ctx)
+
+
 @pytest.mark.parametrize("physics", [1, 3])
 @pytest.mark.parametrize("shape", [(4, 6, 8), (10, 9, 12), (16, 16, 16)])
 def test_uno_apply_theta_weights(physics, shape):

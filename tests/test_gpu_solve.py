@@ -90,21 +90,25 @@ def test_elastic_small_matches_oracle(precision, use_graph):
     h.close()
 
 
-def test_paths_agree_bitwise_on_fp64():
-    """The graph, host-driven and persistent loops run the same kernels in the same order of
-    reductions, so their FP64 iterates agree exactly."""
+@pytest.mark.parametrize("shape", [(16, 16, 16), (12, 10, 18)])
+def test_paths_agree_on_fp64(shape):
+    """The graph and host-driven loops launch the same kernels with the same reductions, so
+    their FP64 iterates agree exactly.  The persistent kernel runs the shared-memory Stockham
+    passes (the register passes take power-of-two axes) and agrees to rounding."""
     from paper_2508_02681_gb300 import _lib
-    phase, _ = rsa_spheres((16, 16, 16), 3.0, 0.25, seed=5)
+    phase, _ = rsa_spheres(shape, 3.0, 0.25, seed=5)
     props = np.array([1.0, 10.0])
     h = _solver(1, phase, props, unit_loads(1))
     out = []
     for ug in (0, 1, 2):
         info = h.solve(tol=1e-8, max_iter=500, precond=_lib.PRECOND_UNO, precision=_lib.FP64, use_graph=ug)
         out.append((list(info.iters), h.fluctuation(0, 1), h.effective_tensor()[0]))
-    for o in out[1:]:
-        assert o[0] == out[0][0]
-        assert np.array_equal(o[1], out[0][1])
-        assert np.array_equal(o[2], out[0][2])
+    assert out[1][0] == out[0][0]
+    assert np.array_equal(out[1][1], out[0][1])
+    assert np.array_equal(out[1][2], out[0][2])
+    assert max(abs(a - b) for a, b in zip(out[2][0], out[0][0])) <= 1
+    assert rel(out[2][1], out[0][1]) < 1e-9
+    assert rel(out[2][2], out[0][2]) < 1e-10
     h.close()
 
 

@@ -22,7 +22,8 @@ def _theta(shape, c, seed):
     return th
 
 
-@pytest.mark.parametrize("c,shape", [(1, (8, 6, 10)), (3, (6, 8, 8)), (1, (32, 32, 32))])
+@pytest.mark.parametrize("c,shape", [(1, (8, 6, 10)), (3, (6, 8, 8)), (1, (32, 32, 32)), (3, (16, 32, 32)),
+                                     (1, (8, 64, 64)), (3, (64, 16, 16)), (1, (4, 128, 128))])
 def test_apply_fp32_matches_oracle(c, shape):
     import torch
     from paper_2508_02681_gb300 import api
