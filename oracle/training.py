@@ -83,3 +83,16 @@ def grad_theta(theta, grad_entries, c: int):
         dv = (uno.entries_from_blocks(uno.psi(tp, 3)) - uno.entries_from_blocks(uno.psi(tm, 3))) / (2 * eps)
         out[..., m] = np.sum(dv * grad_entries, axis=-1)
     return out
+
+
+def grad_modes(w, M: int, shape, c: int, grad_entries):
+    """Chain rule for the bypass-plus-modes weights: ``dL/dw`` ``[1 + n_modes, C]`` from the
+    gradient w.r.t. the (even) half-grid entries.  The entries are the even part of the raw
+    ones, an averaging that is its own adjoint; the bypass acts on every mode."""
+    g_raw = uno.symmetrize_half(np.asarray(grad_entries, dtype=np.float64), shape[2])
+    w = np.asarray(w, dtype=np.float64)
+    out = np.zeros_like(w)
+    out[0] = grad_theta(w[0], g_raw.reshape(-1, g_raw.shape[-1]).sum(axis=0), c)
+    for i, (k1, k2, k3) in enumerate(uno.mode_list(M)):
+        out[1 + i] = grad_theta(w[1 + i], g_raw[k1 % shape[0], k2 % shape[1], k3], c)
+    return out

@@ -12,6 +12,10 @@
   medium, obtained here by transforming the assembled stencil (a column of K_ref);
   ``Q(0) = 0`` on the null space of the periodic problem (Remark after Algorithm 2).
 * Safety check of the Remark after Algorithm 2: ``lambda_min(Q(k)) > eps`` for all k != 0.
+* The paper's own weight layout (Eq. (fnocg-operator), Eq. (fnocg-parametrization)): an inner
+  bypass ``W = psi(w_0)`` acting on every mode plus a kernel ``psi(w_i)`` on the modes of a
+  set ``K_M = [-M, M]^2 x [0, M] minus {0}`` (periodic row of Table (fnocg-mode-selection-2d)),
+  zero elsewhere; the conjugate modes (negative k3) are the Hermitian half of the spectrum.
 """
 from __future__ import annotations
 
@@ -157,3 +161,32 @@ def min_eigenvalue(Q: np.ndarray, skip_zero_mode: bool = True) -> float:
 def spd_check(Q: np.ndarray, eps: float) -> bool:
     """Safety check of the Remark after Algorithm 2 on all modes k != 0."""
     return min_eigenvalue(Q) > eps
+
+
+def mode_list(M: int):
+    """The modes of ``K_M`` (periodic boundary conditions, d = 3) in the weight order used here:
+    k1 from -M to M (slowest), then k2 from -M to M, then k3 from 0 to M, without k = 0."""
+    return [(k1, k2, k3) for k1 in range(-M, M + 1) for k2 in range(-M, M + 1) for k3 in range(0, M + 1)
+            if (k1, k2, k3) != (0, 0, 0)]
+
+
+def modes_entries(w: np.ndarray, M: int, shape, c: int) -> np.ndarray:
+    """Unique entries ``[N1, N2, N3h, C]`` of ``W + K(k)`` before the self-conjugate planes are
+    made even: ``w[0]`` parametrizes the bypass, ``w[1 + i]`` the i-th mode of ``mode_list(M)``."""
+    N1, N2, N3 = shape
+    w = np.asarray(w, dtype=np.float64)
+    modes = mode_list(M)
+    if w.shape != (1 + len(modes), n_unique(c)):
+        raise ValueError("weights must be [1 + n_modes, C]")
+    if 2 * M + 1 > N1 or 2 * M + 1 > N2 or M > N3 // 2:
+        raise ValueError("mode set larger than the grid")
+    v = np.zeros((N1, N2, N3 // 2 + 1, n_unique(c)))
+    v[...] = entries_from_blocks(psi(w[0], c))
+    for i, (k1, k2, k3) in enumerate(modes):
+        v[k1 % N1, k2 % N2, k3] += entries_from_blocks(psi(w[1 + i], c))
+    return v
+
+
+def modes_Q(w: np.ndarray, M: int, shape, c: int) -> np.ndarray:
+    """Half-grid blocks of the paper's parametrization, even on the self-conjugate planes."""
+    return symmetrize_half(blocks_from_entries(modes_entries(w, M, shape, c), c), shape[2])

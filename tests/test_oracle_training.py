@@ -69,3 +69,28 @@ def test_c3_gradient_and_theta_chain_match_fd():
         tm[idx] -= eps
         fd = (L(tp) - L(tm)) / (2 * eps)
         assert gt[idx] == pytest.approx(fd, rel=1e-6, abs=1e-8)
+
+
+@pytest.mark.parametrize("c,shape,M", [(1, (6, 6, 6), 2), (3, (4, 6, 6), 1)])
+def test_grad_modes_matches_central_differences(c, shape, M):
+    """Bypass-plus-modes weights: the chained gradient against central differences of the loss
+    evaluated by definition (real-space application of P)."""
+    rng = np.random.default_rng(11)
+    w = rng.standard_normal((1 + len(uno.mode_list(M)), uno.n_unique(c))) * 0.4 + 0.7
+    B = 2
+    f = rng.standard_normal((B, c) + shape)
+    u = rng.standard_normal((B, c) + shape)
+
+    def loss(wv):
+        return training.loss_by_definition(uno.modes_Q(wv, M, shape, c), f, u)
+
+    Q = uno.modes_Q(w, M, shape, c)
+    R, U = training.spectra(f), training.spectra(u)
+    g = training.grad_modes(w, M, shape, c, training.grad_entries_general(Q, R, U, shape))
+    for (i, m) in [(0, 0), (1, 0), (len(w) - 1, 0), (len(w) // 2, uno.n_unique(c) - 1), (3, c - 1)]:
+        h = 1e-6
+        wp, wm = w.copy(), w.copy()
+        wp[i, m] += h
+        wm[i, m] -= h
+        fd = (loss(wp) - loss(wm)) / (2 * h)
+        assert g[i, m] == pytest.approx(fd, rel=1e-6, abs=1e-8)

@@ -152,3 +152,56 @@ def test_spd_check():
     Q2 = Q.copy()
     Q2[1, 2, 1] = -1e-3
     assert not uno.spd_check(Q2, 1e-12)
+
+
+# ---------------------------------------------------------------- bypass + limited mode set
+def _w_modes(M, c, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((1 + len(uno.mode_list(M)), uno.n_unique(c))) * 0.5 + 0.8
+
+
+def test_mode_list_is_the_periodic_row_of_the_mode_table():
+    # (2M+1)^(d-1) (M+1) - 1 modes, k3 >= 0, no k = 0, all distinct
+    for M in range(0, 4):
+        m = uno.mode_list(M)
+        assert len(m) == (2 * M + 1) ** 2 * (M + 1) - 1 == len(set(m))
+        assert all(k[2] >= 0 and max(abs(x) for x in k) <= M for k in m) and (0, 0, 0) not in m
+
+
+@pytest.mark.parametrize("c", [1, 3])
+def test_modes_M0_is_the_bypass_alone(c):
+    # M = 0: no kernel modes, P r = W r node by node with W = psi(w_0)
+    shape = (4, 6, 8)
+    w = _w_modes(0, c, 1)
+    Q = uno.modes_Q(w, 0, shape, c)
+    r = random_field((c,) + shape, seed=2)
+    W = uno.psi(w[0], c)
+    assert np.max(np.abs(uno.uno_apply(Q, r) - np.einsum("ij,jxyz->ixyz", W, r))) < 1e-13
+
+
+def test_modes_single_fourier_mode_closed_form():
+    # a real Fourier mode cos(2 pi k.x / N) is an eigenfunction: P multiplies it by
+    # W + K(k) (k3 > 0), by W + (K(k) + K(-k)) / 2 on the k3 = 0 plane, by W outside K_M
+    shape = (8, 8, 8)
+    M = 2
+    w = _w_modes(M, 1, 3)
+    Q = uno.modes_Q(w, M, shape, 1)
+    idx = {k: i for i, k in enumerate(uno.mode_list(M))}
+    x = np.stack(np.meshgrid(*[np.arange(n) for n in shape], indexing="ij"))
+    W = w[0, 0] ** 2
+    cases = [((1, -2, 1), W + w[1 + idx[(1, -2, 1)], 0] ** 2),
+             ((2, 1, 0), W + 0.5 * (w[1 + idx[(2, 1, 0)], 0] ** 2 + w[1 + idx[(-2, -1, 0)], 0] ** 2)),
+             ((3, 0, 1), W), ((0, 0, 3), W)]
+    for k, lam in cases:
+        ph = 2 * np.pi * sum(k[a] * x[a] / shape[a] for a in range(3))
+        r = np.cos(ph)[None]
+        assert np.max(np.abs(uno.uno_apply(Q, r) - lam * r)) < 1e-12
+
+
+@pytest.mark.parametrize("c", [1, 3])
+def test_modes_spectrum_bounded_below_by_the_bypass(c):
+    shape = (6, 6, 6)
+    w = _w_modes(2, c, 4)
+    Q = uno.modes_Q(w, 2, shape, c)
+    lw = np.linalg.eigvalsh(uno.psi(w[0], c)).min()
+    assert uno.min_eigenvalue(Q, skip_zero_mode=False) >= lw - 1e-12
