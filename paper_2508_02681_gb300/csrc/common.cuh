@@ -217,15 +217,24 @@ __device__ __forceinline__ double block_max_f(float v, double* sh) {
 __device__ __forceinline__ double block_max_t(float v, double* sh) { return block_max_f(v, sh); }
 __device__ __forceinline__ double block_max_t(double v, double* sh) { return block_max(v, sh); }
 
+// Programmatic dependent launch: a kernel launched with launch_pdl may start while the kernel
+// before it in the stream is still running.  pdl_wait() blocks until that kernel has completed
+// and its memory is visible: call it before touching anything the previous kernels wrote.
+// pdl_trigger() lets the next kernel start launching (its blocks then wait in pdl_wait()).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Returns true in every thread of the block that arrives last at `ticket` (over all blocks
 // of the grid).  Callers write their partials before and read all partials after.
+// Thread 0 publishes its own earlier writes (the block's partials) with a release increment
+// of the ticket; the last block acquires all of them before reading.
 __device__ __forceinline__ bool last_block(unsigned int* ticket) {
   __shared__ bool am_last;
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    unsigned total = gridDim.x * gridDim.y * gridDim.z;
-    unsigned t = atomicAdd(ticket, 1u);
+    const unsigned total = gridDim.x * gridDim.y * gridDim.z;
+    unsigned t;
+    asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(t) : "l"(ticket) : "memory");
     am_last = (t == total - 1);
   }
   __syncthreads();

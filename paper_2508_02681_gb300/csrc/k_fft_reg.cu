@@ -37,6 +37,8 @@ template <typename T, int N2, int N3> struct PlaneReg {
   static constexpr int P = pitch_reg(n3h, NCG * CW);   // plane pitch (complex), = 4 mod 16
   static constexpr int NW = NCG > (NRG < 16 ? NRG : 16) ? NCG : (NRG < 16 ? NRG : 16);
   static constexpr size_t smem = ((size_t)N2 * P + Nh + N2 + N3) * sizeof(cplx<T>);
+  // first-group data requested with the loop state; off where it would exceed the registers
+  static constexpr bool prefetch = !(sizeof(T) == 8 && N2 >= 128);
 };
 
 template <typename T>
@@ -112,40 +114,60 @@ __global__ void __launch_bounds__(PlaneReg<T, N2, N3>::NW * 32) k_plane_fwd_reg(
   load_tw_reg<T>(tw3h, a.ft.tw3h, Nh);
   load_tw_reg<T>(tw2, a.ft.tw2, N2);
   load_tw_reg<T>(tw3, a.ft.tw3, N3);
+  pdl_wait();
   const int bl = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int plane_id = blockIdx.x;
+  const int comp = plane_id / a.g.n1, i1 = plane_id - comp * a.g.n1;
+  const long long field = (long long)bl * a.c + comp;
+  const long long base = (field * a.g.n1 + i1) * (long long)(N2 * N3);
+  // row data of one row group: z[g + G3 n1] of r (or src) and of p
+  auto load_rows = [&](int rg, C* v, C* q) {
+    const int row = rg * PR::RPW + lane / G3, g = lane % G3;
+    if (a.standalone) {
+      const C* src = reinterpret_cast<const C*>(a.src + base) + row * Nh;
+#pragma unroll
+      for (int n1 = 0; n1 < V3; ++n1) v[n1] = src[g + G3 * n1];
+    } else {
+      const C* r = reinterpret_cast<const C*>(a.r + base) + row * Nh;
+      const C* p = reinterpret_cast<const C*>(a.p + base) + row * Nh;
+#pragma unroll
+      for (int n1 = 0; n1 < V3; ++n1) v[n1] = r[g + G3 * n1];
+#pragma unroll
+      for (int n1 = 0; n1 < V3; ++n1) q[n1] = p[g + G3 * n1];
+    }
+  };
+  // the first row group's data is requested together with the loop state (one memory latency)
+  C v0[V3], q0[V3];
+  if (PR::prefetch && warp < PR::NRG) load_rows(warp, v0, q0);
   bool active = true;
   double alpha = 0.0;
   if (!a.standalone) {
-    active = !a.sc[bl].done && (!a.after_replace || a.sc[bl].need_replace);
-    alpha = a.after_replace ? 0.0 : a.sc[bl].alpha;
+    const CgScal& st = a.sc[bl];
+    active = !st.done && (!a.after_replace || st.need_replace);
+    alpha = a.after_replace ? 0.0 : st.alpha;
   }
   __syncthreads();
   T lmax = (T)0;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (active) {
-    const int plane_id = blockIdx.x;
-    const int comp = plane_id / a.g.n1, i1 = plane_id - comp * a.g.n1;
-    const long long field = (long long)bl * a.c + comp;
-    const long long base = (field * a.g.n1 + i1) * (long long)(N2 * N3);
     const T al = (T)alpha;
     const bool upd = alpha != 0.0;
     // ---- rows: axis 3
     for (int rg = warp; rg < PR::NRG; rg += PR::NW) {
       const int row = rg * PR::RPW + lane / G3, g = lane % G3;
-      C v[V3];
-      if (a.standalone) {
-        const C* src = reinterpret_cast<const C*>(a.src + base) + row * Nh;
+      C v[V3], q[V3];
+      if (PR::prefetch && rg == warp) {
 #pragma unroll
-        for (int n1 = 0; n1 < V3; ++n1) v[n1] = src[g + G3 * n1];
+        for (int n1 = 0; n1 < V3; ++n1) {
+          v[n1] = v0[n1];
+          q[n1] = q0[n1];
+        }
       } else {
-        C* r = reinterpret_cast<C*>(a.r + base) + row * Nh;
-        const C* p = reinterpret_cast<const C*>(a.p + base) + row * Nh;
-#pragma unroll
-        for (int n1 = 0; n1 < V3; ++n1) v[n1] = r[g + G3 * n1];
+        load_rows(rg, v, q);
+      }
+      if (!a.standalone) {
         if (upd) {
-          C q[V3];
-#pragma unroll
-          for (int n1 = 0; n1 < V3; ++n1) q[n1] = p[g + G3 * n1];
+          C* r = reinterpret_cast<C*>(a.r + base) + row * Nh;
 #pragma unroll
           for (int n1 = 0; n1 < V3; ++n1) {
             v[n1].x -= al * q[n1].x;
@@ -185,6 +207,7 @@ __global__ void __launch_bounds__(PlaneReg<T, N2, N3>::NW * 32) k_plane_fwd_reg(
       __syncwarp();
     }
   }
+  pdl_trigger();
   if (a.standalone) return;
   const double bmax = block_max_t(lmax, red_sh);
   if (threadIdx.x == 0 && active) atomic_max_nonneg(&a.sc[bl].rmax_bits, bmax);
@@ -205,28 +228,54 @@ __global__ void __launch_bounds__(PlaneReg<T, N2, N3>::NW * 32) k_plane_inv_reg(
   C* tw3h = plane + N2 * P;
   C* tw2 = tw3h + Nh;
   C* tw3 = tw2 + N2;
-  const int bl = blockIdx.y;
-  if (!a.standalone && a.sc[bl].done) return;
   load_tw_reg<T>(tw3h, a.ft.tw3h, Nh);
   load_tw_reg<T>(tw2, a.ft.tw2, N2);
   load_tw_reg<T>(tw3, a.ft.tw3, N3);
-  const double al_d = a.standalone ? 0.0 : a.sc[bl].alpha, be_d = a.standalone ? 0.0 : a.sc[bl].beta;
-  __syncthreads();
+  pdl_wait();
+  const int bl = blockIdx.y;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int plane_id = blockIdx.x;
   const int comp = plane_id / a.g.n1, i1 = plane_id - comp * a.g.n1;
   const long long field = (long long)bl * a.c + comp;
-  // ---- columns: inverse axis 2
   const C* in = a.shat + (field * a.g.n1 + i1) * (long long)(N2 * n3h);
-  for (int cg = warp; cg < PR::NCG; cg += PR::NW) {
+  const long long base = (field * a.g.n1 + i1) * (long long)(N2 * N3);
+  auto load_cols = [&](int cg, C* v) {
     const int col = cg * PR::CW + lane % PR::CW, g = lane / PR::CW;
     const bool on = col < n3h;
-    C v[V2];
 #pragma unroll
     for (int j = 0; j < V2 / G2; ++j)
 #pragma unroll
       for (int k2 = 0; k2 < G2; ++k2)
         v[j * G2 + k2] = on ? in[scat_index<N2>(g, j, k2) * n3h + col] : mk<T>((T)0, (T)0);
+  };
+  auto load_du = [&](int rg, C* dv, C* uv) {
+    const int row = rg * PR::RPW + lane / G3, g = lane % G3;
+    const C* d = reinterpret_cast<const C*>(a.d + base) + row * Nh;
+    const C* u = reinterpret_cast<const C*>(a.u + base) + row * Nh;
+#pragma unroll
+    for (int n1 = 0; n1 < V3; ++n1) {
+      dv[n1] = d[g + G3 * n1];
+      uv[n1] = u[g + G3 * n1];
+    }
+  };
+  // the first column group's spectrum and the first row group's d and u are requested together
+  // with the loop state (one memory latency)
+  C cv0[V2], dv0[V3], uv0[V3];
+  if (PR::prefetch && warp < PR::NCG) load_cols(warp, cv0);
+  if (PR::prefetch && !a.standalone && warp < PR::NRG) load_du(warp, dv0, uv0);
+  if (!a.standalone && a.sc[bl].done) return;
+  const double al_d = a.standalone ? 0.0 : a.sc[bl].alpha, be_d = a.standalone ? 0.0 : a.sc[bl].beta;
+  __syncthreads();
+  // ---- columns: inverse axis 2
+  for (int cg = warp; cg < PR::NCG; cg += PR::NW) {
+    const int col = cg * PR::CW + lane % PR::CW, g = lane / PR::CW;
+    C v[V2];
+    if (PR::prefetch && cg == warp) {
+#pragma unroll
+      for (int i = 0; i < V2; ++i) v[i] = cv0[i];
+    } else {
+      load_cols(cg, v);
+    }
     fft_dist_b<N2, +1>(v, g, plane + col, P, tw2);
     __syncwarp();
 #pragma unroll
@@ -235,7 +284,6 @@ __global__ void __launch_bounds__(PlaneReg<T, N2, N3>::NW * 32) k_plane_inv_reg(
   }
   __syncthreads();
   // ---- rows: inverse axis 3 (half spectrum -> real row)
-  const long long base = (field * a.g.n1 + i1) * (long long)(N2 * N3);
   const T alpha = (T)al_d, beta = (T)be_d;
   for (int rg = warp; rg < PR::NRG; rg += PR::NW) {
     const int row = rg * PR::RPW + lane / G3, g = lane % G3;
@@ -256,10 +304,14 @@ __global__ void __launch_bounds__(PlaneReg<T, N2, N3>::NW * 32) k_plane_inv_reg(
       C* d = reinterpret_cast<C*>(a.d + base) + row * Nh;
       C* u = reinterpret_cast<C*>(a.u + base) + row * Nh;
       C dv[V3], uv[V3];
+      if (PR::prefetch && rg == warp) {
 #pragma unroll
-      for (int n1 = 0; n1 < V3; ++n1) {
-        dv[n1] = d[g + G3 * n1];
-        uv[n1] = u[g + G3 * n1];
+        for (int n1 = 0; n1 < V3; ++n1) {
+          dv[n1] = dv0[n1];
+          uv[n1] = uv0[n1];
+        }
+      } else {
+        load_du(rg, dv, uv);
       }
 #pragma unroll
       for (int n1 = 0; n1 < V3; ++n1) {
@@ -301,43 +353,53 @@ __global__ void __launch_bounds__(kLineRegWarps * 32) k_line_reg(LineArgs<T, QT>
   C* scr_all = tw1 + N1;
   load_tw_reg<T>(tw1, a.ft.tw1, N1);
   const int bl = blockIdx.y;
-  const bool active = (MODE != 0) || !a.sc[bl].done;
-  __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane / W, w = lane % W;
   const int M = a.g.n2 * a.g.n3h;
+  const int pos = (blockIdx.x * NW + warp) * W + w;
+  const bool on = pos < M;
+  const long long fbase = (long long)bl * CC * N1 * M;
+  const long long qb = (long long)(bl / a.L) * a.q_inst_stride;
+  const T sc = (T)a.scale;
+  // the weights do not change during a solve: thermal ones are fetched before the wait
+  T qpre[CC == 1 ? V : 1];
+  if constexpr (CC == 1) {
+#pragma unroll
+    for (int j = 0; j < VG; ++j)
+#pragma unroll
+      for (int k2 = 0; k2 < G; ++k2)
+        qpre[j * G + k2] = on ? QRead<T, QT>::get(a.Q, qb + (long long)scat_index<N1>(g, j, k2) * M + pos) : (T)0;
+  }
+  pdl_wait();
+  // the spectra are requested together with the loop state (one memory latency)
+  C v[CC][V], so[CC][V];
+#pragma unroll
+  for (int cc = 0; cc < CC; ++cc)
+#pragma unroll
+    for (int n1 = 0; n1 < V; ++n1) {
+      const long long gi = fbase + ((long long)(cc * N1 + g + G * n1)) * M + pos;
+      v[cc][n1] = on ? a.hat[gi] : mk<T>((T)0, (T)0);
+      if (MODE == 0) so[cc][n1] = (on && a.flexible) ? a.shat[gi] : mk<T>((T)0, (T)0);
+    }
+  const bool active = (MODE != 0) || !a.sc[bl].done;
+  __syncthreads();
   DotAcc<T> gam, rso;
   if (active) {
-    const int pos = (blockIdx.x * NW + warp) * W + w;
-    const bool on = pos < M;
     const int k3 = on ? pos % a.g.n3h : 0;
     const T wt = (k3 == 0 || 2 * k3 == a.g.n3) ? (T)1 : (T)2;
     C* scr = scr_all + (size_t)warp * W * N1 + w;
-    const long long fbase = (long long)bl * CC * N1 * M;
-    C v[CC][V];
-#pragma unroll
-    for (int cc = 0; cc < CC; ++cc)
-#pragma unroll
-      for (int n1 = 0; n1 < V; ++n1) {
-        const long long gi = fbase + ((long long)(cc * N1 + g + G * n1)) * M + pos;
-        v[cc][n1] = on ? a.hat[gi] : mk<T>((T)0, (T)0);
-      }
     if (MODE == 0 && a.flexible && on) {
 #pragma unroll
       for (int cc = 0; cc < CC; ++cc)
 #pragma unroll
         for (int n1 = 0; n1 < V; ++n1) {
-          const long long gi = fbase + ((long long)(cc * N1 + g + G * n1)) * M + pos;
-          const C so = a.shat[gi];
-          rso.add_prod(wt * v[cc][n1].x, so.x);
-          rso.add_prod(wt * v[cc][n1].y, so.y);
+          rso.add_prod(wt * v[cc][n1].x, so[cc][n1].x);
+          rso.add_prod(wt * v[cc][n1].y, so[cc][n1].y);
         }
     }
 #pragma unroll
     for (int cc = 0; cc < CC; ++cc) fft_dist_a<N1, -1>(v[cc], g, scr, W, tw1);
     // s_hat = Q(k) r_hat(k) / n and the Parseval partial of r . s
-    const long long qb = (long long)(bl / a.L) * a.q_inst_stride;
-    const T sc = (T)a.scale;
     if (on) {
 #pragma unroll
       for (int j = 0; j < VG; ++j)
@@ -346,7 +408,7 @@ __global__ void __launch_bounds__(kLineRegWarps * 32) k_line_reg(LineArgs<T, QT>
           const int k1 = scat_index<N1>(g, j, k2), e = j * G + k2;
           const long long qi = qb + ((long long)k1 * M + pos) * (CC == 1 ? 1 : 6);
           if constexpr (CC == 1) {
-            const T q = QRead<T, QT>::get(a.Q, qi) * sc;
+            const T q = qpre[e] * sc;
             const C R = v[0][e];
             const C S = mk<T>(q * R.x, q * R.y);
             if (MODE == 0) {
@@ -388,6 +450,7 @@ __global__ void __launch_bounds__(kLineRegWarps * 32) k_line_reg(LineArgs<T, QT>
         }
     }
   }
+  pdl_trigger();
   if (MODE != 0) return;
   double2 pr;
   pr.x = block_sum_acc(gam, red_sh);
@@ -418,8 +481,7 @@ cudaError_t launch_reg(K kern, dim3 grid, int nth, size_t smem, const A& a, cuda
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  kern<<<grid, nth, smem, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(kern, grid, dim3(nth), smem, s, a);
 }
 
 constexpr bool pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1)) == 0; }

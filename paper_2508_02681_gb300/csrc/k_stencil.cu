@@ -25,9 +25,10 @@ __global__ void __launch_bounds__(256) k_ku(StencilArgs<T> a) {
   const int bl = blockIdx.y;
   load_material<T>(mt, a.mat, bl / a.L);
   __syncthreads();
-  bool active = a.standalone || !a.sc[bl].done;
-  double bs = 0.0;
-  if (active) bs = ku_task<T, CC, false>(a, mt, bl, blockIdx.x, red_sh, tile_smem);
+  pdl_wait();
+  const double bs = ku_task<T, CC, false>(a, mt, bl, blockIdx.x, red_sh, tile_smem,
+                                          a.standalone ? nullptr : &a.sc[bl].done);
+  pdl_trigger();
   if (a.standalone) return;
   if (threadIdx.x == 0) a.red.part[(long long)bl * gridDim.x + blockIdx.x] = bs;
   if (last_block(a.red.ticket)) {
@@ -372,9 +373,8 @@ int ku_blocks_x(const Grid& g, int c) { return ku_grid(g, c, 1).x; }
 
 template <typename T> cudaError_t launch_ku(const StencilArgs<T>& a, cudaStream_t s) {
   dim3 grid = ku_grid(a.g, a.c, a.BL);
-  if (a.c == 1) k_ku<T, 1><<<grid, 256, 0, s>>>(a);
-  else k_ku<T, 3><<<grid, 256, 0, s>>>(a);
-  return cudaGetLastError();
+  if (a.c == 1) return launch_pdl(k_ku<T, 1>, grid, dim3(256), 0, s, a);
+  return launch_pdl(k_ku<T, 3>, grid, dim3(256), 0, s, a);
 }
 template <typename T> cudaError_t launch_init(const InitArgs<T>& a, int BL, cudaStream_t s) {
   dim3 grid = node_grid(a.g, BL);

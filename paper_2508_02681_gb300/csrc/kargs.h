@@ -5,6 +5,29 @@
 #include "cg.cuh"
 
 namespace unocg {
+// Launch with the programmatic-stream-serialization attribute (the kernel must call pdl_wait()
+// before reading what earlier kernels wrote).  UNOCG_PDL=0 at build time launches plainly.
+#ifndef UNOCG_PDL
+#define UNOCG_PDL 1
+#endif
+template <typename... KArgs, typename... Args>
+static inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                     cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = UNOCG_PDL ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+}  // namespace unocg
+
+namespace unocg {
 
 // ---------------------------------------------------------------- FFT passes
 template <typename T> struct PlaneFwdArgs {

@@ -29,7 +29,7 @@ template <typename T, bool COH = false>
 __device__ __forceinline__ void ku_thermal_column(const T* __restrict__ d, T* __restrict__ p,
                                                   const uint8_t* __restrict__ ph, const T* mt,
                                                   const Grid& g, int i1, int i2, int i3, int cz,
-                                                  DotAcc<T>& dp) {
+                                                  DotAcc<T>& dp, const int* skip = nullptr) {
   const int S = g.n2 * g.n3;
   const int c2[3] = {i2 ? i2 - 1 : g.n2 - 1, i2, (i2 + 1 == g.n2) ? 0 : i2 + 1};
   const int c3[3] = {i3 ? i3 - 1 : g.n3 - 1, i3, (i3 + 1 == g.n3) ? 0 : i3 + 1};
@@ -53,9 +53,11 @@ __device__ __forceinline__ void ku_thermal_column(const T* __restrict__ d, T* __
   for (int o2 = 0; o2 < 2; ++o2)
 #pragma unroll
     for (int o3 = 0; o3 < 2; ++o3) km[o2][o3] = mt[2 * __ldg(ph + zm + off[1 - o2][1 - o3])];
+  // a finished (instance, load) is skipped; the flag is read after the first loads are issued
+  if (skip && *skip) return;
   const T hf = grid_h12<T>(g);
   const int zend = min(i1 + cz, g.n1);
-  for (int z = i1; z < zend; ++z) {
+  auto step = [&](int z) {
     const int zn = ((z + 1 == g.n1) ? 0 : z + 1) * S;
     zc = z * S;
 #pragma unroll
@@ -115,6 +117,13 @@ __device__ __forceinline__ void ku_thermal_column(const T* __restrict__ d, T* __
     for (int o2 = 0; o2 < 2; ++o2)
 #pragma unroll
       for (int o3 = 0; o3 < 2; ++o3) km[o2][o3] = kc[o2][o3];
+  };
+  if (zend - i1 == KU_CZ) {
+    // full column: unrolled, so that the loads of later planes are issued ahead
+#pragma unroll
+    for (int zz = 0; zz < KU_CZ; ++zz) step(i1 + zz);
+  } else {
+    for (int z = i1; z < zend; ++z) step(z);
   }
 }
 
@@ -247,8 +256,10 @@ __device__ __forceinline__ void ku_thermal_tile(const T* __restrict__ d, T* __re
 
 // K d of one tile of (instance, load) bl: thermal = one 32 x 8 x KU_CZ column block, elastic =
 // one 32 x 4 x 2 node block.  Returns the block sum of d . p (valid in thread 0).
+// skip: optional flag of the pair (nonzero = finished, no work), read as late as possible.
 template <typename T, int CC, bool COH>
-__device__ double ku_task(const StencilArgs<T>& a, const T* mt, int bl, int tile, double* red_sh, T* tile_smem) {
+__device__ double ku_task(const StencilArgs<T>& a, const T* mt, int bl, int tile, double* red_sh, T* tile_smem,
+                          const int* skip = nullptr) {
   const Grid& g = a.g;
   const int b = bl / a.L;
   const long long n = g.n;
@@ -261,11 +272,12 @@ __device__ double ku_task(const StencilArgs<T>& a, const T* mt, int bl, int tile
     ku_thermal_tile<T, COH>(d, p, ph, mt, g, tile, tile_smem, tile_smem + KU_DN, dp);
 #else
     int i1, i2, i3;
-    if (tile_column_at(g, tile, KU_CZ, i1, i2, i3)) ku_thermal_column<T, COH>(d, p, ph, mt, g, i1, i2, i3, KU_CZ, dp);
+    if (tile_column_at(g, tile, KU_CZ, i1, i2, i3))
+      ku_thermal_column<T, COH>(d, p, ph, mt, g, i1, i2, i3, KU_CZ, dp, skip);
 #endif
   } else {
     int i1, i2, i3;
-    if (tile_node_at(g, tile, i1, i2, i3)) {
+    if (tile_node_at(g, tile, i1, i2, i3) && !(skip && *skip)) {
       const long long node = ((long long)i1 * g.n2 + i2) * g.n3 + i3;
       T out[CC];
       node_Ku<T, CC, COH>(d, ph, mt, g, i1, i2, i3, out);
