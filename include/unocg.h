@@ -69,6 +69,9 @@ extern "C" {
                                       v1=Q11 v2=Q22 v3=Q12 v4=Q33 v5=Q23 v6=Q13 (C = 1 or 6) */
 #define UNOCG_W_THETA 2            /* parameters theta [N1][N2][N3/2+1][C] mapped through the
                                       local parametrization psi (Sec. 5.2.2, App. B.1)        */
+#define UNOCG_W_MODES 3            /* the paper's layout (Eq. (fnocg-parametrization)): inner
+                                      bypass psi(w_0) on every mode plus psi(w_i) on the
+                                      modes of K_M; set with unocg_set_uno_modes             */
 
 /* dtypes of weight arrays */
 #define UNOCG_DTYPE_F64 0
@@ -139,6 +142,15 @@ int unocg_set_macro_load(unocg_ctx* ctx, int n_loads, const double* loads);
    memory of `dtype`; shared by all instances (REFERENCE_MEDIUM is per instance).            */
 int unocg_set_uno_weights(unocg_ctx* ctx, int kind, const void* w, int dtype, double spd_eps);
 
+/* UNO weights in the paper's layout (Eq. (fnocg-operator), Eq. (fnocg-parametrization)):
+   Q(k) = psi(w_0) + psi(w_i) if k is the i-th mode of K_M = [-M,M]^2 x [0,M] minus {0}
+   (periodic row of Table (fnocg-mode-selection-2d); order: k1 slowest from -M, then k2 from
+   -M, then k3 from 0), else psi(w_0).  w: host array [1 + n_modes][C] of `dtype`,
+   n_modes = (2M+1)^2 (M+1) - 1; requires 2M+1 <= N1, 2M+1 <= N2, 2M <= N3, else
+   UNOCG_ERR_INVALID_ARG.  Then as unocg_set_uno_weights (symmetrization of the
+   self-conjugate planes, safety check with spd_eps, BF16 copy).                          */
+int unocg_set_uno_modes(unocg_ctx* ctx, int M, const void* w, int dtype, double spd_eps);
+
 /* Copy the expanded weights Q(k) of `instance` (unique entries [N1][N2][N3/2+1][C], paper's
    order, FP64, after the safety check and symmetrization) to host memory `out`.            */
 int unocg_get_uno_weights(unocg_ctx* ctx, int instance, double* out);
@@ -188,10 +200,15 @@ void unocg_uno_destroy(unocg_uno* op);
 const char* unocg_uno_last_error(const unocg_uno* op);
 /* theta_dev: device float [N1][N2][N3/2+1][C], mapped through psi on every call.            */
 int unocg_uno_set_theta_dev(unocg_uno* op, const float* theta_dev, void* stream);
+/* The paper's layout instead (see unocg_set_uno_modes): w_dev device float
+   [1 + n_modes][C]; the backward then returns dL/dw in the same layout.  The operator keeps
+   the pointer: w_dev must stay valid until the next set call.                              */
+int unocg_uno_set_modes_dev(unocg_uno* op, int M, const float* w_dev, void* stream);
 /* s = P r for a batch: r_dev, s_dev device float [batch][c][N1][N2][N3].                    */
 int unocg_uno_apply_dev(unocg_uno* op, int batch, const float* r_dev, float* s_dev, void* stream);
 /* Backward of s = P r: gr = P gs (P is self-adjoint) and gtheta = dL/dtheta (device float,
-   [N1][N2][N3/2+1][C]; overwritten) from dL/dQ(k) = sum_b w_k Re(conj(T gs_b) (T r_b)^T).   */
+   [N1][N2][N3/2+1][C], or [1 + n_modes][C] after unocg_uno_set_modes_dev; overwritten) from
+   dL/dQ(k) = sum_b w_k Re(conj(T gs_b) (T r_b)^T).                                         */
 int unocg_uno_backward_dev(unocg_uno* op, int batch, const float* r_dev, const float* gs_dev,
                            float* gr_dev, float* gtheta_dev, void* stream);
 

@@ -34,6 +34,7 @@ MIXED = 1
 W_REFERENCE_MEDIUM = 0
 W_BLOCKS = 1
 W_THETA = 2
+W_MODES = 3
 DTYPE_F64 = 0
 DTYPE_F32 = 1
 
@@ -66,6 +67,7 @@ SIGNATURES = {
     "unocg_set_phase_properties": (_i, [_vp, _vp]),
     "unocg_set_macro_load": (_i, [_vp, _i, _vp]),
     "unocg_set_uno_weights": (_i, [_vp, _i, _vp, _i, _d]),
+    "unocg_set_uno_modes": (_i, [_vp, _i, _vp, _i, _d]),
     "unocg_get_uno_weights": (_i, [_vp, _i, _vp]),
     "unocg_solve": (_i, [_vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
     "unocg_solve_async": (_i, [_vp, C.POINTER(SolveOpts)]),
@@ -80,6 +82,7 @@ SIGNATURES = {
     "unocg_uno_destroy": (None, [_vp]),
     "unocg_uno_last_error": (C.c_char_p, [_vp]),
     "unocg_uno_set_theta_dev": (_i, [_vp, _vp, _vp]),
+    "unocg_uno_set_modes_dev": (_i, [_vp, _i, _vp, _vp]),
     "unocg_uno_apply_dev": (_i, [_vp, _i, _vp, _vp, _vp]),
     "unocg_uno_backward_dev": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp]),
     "unocg_apply_K_dev": (_i, [_vp, _i, _vp, _vp, _vp]),

@@ -87,6 +87,14 @@ def unocg_set_uno_weights(ctx, kind: int, w: np.ndarray | None = None, spd_eps: 
     _check(ctx, _lib.load().unocg_set_uno_weights(ctx, kind, _ptr(a), dt, spd_eps))
 
 
+def unocg_set_uno_modes(ctx, M: int, w: np.ndarray, spd_eps: float = 0.0):
+    a = np.ascontiguousarray(w)
+    dt = _lib.DTYPE_F64 if a.dtype == np.float64 else _lib.DTYPE_F32
+    if dt == _lib.DTYPE_F32:
+        a = a.astype(np.float32)
+    _check(ctx, _lib.load().unocg_set_uno_modes(ctx, M, _ptr(a), dt, spd_eps))
+
+
 def unocg_get_uno_weights(ctx, instance: int, n_modes: int, C_: int) -> np.ndarray:
     out = np.empty(n_modes * C_, dtype=np.float64)
     _check(ctx, _lib.load().unocg_get_uno_weights(ctx, instance, _ptr(out)))
@@ -218,6 +226,10 @@ def unocg_uno_destroy(op):
 
 def unocg_uno_set_theta_dev(op, theta_dev, stream=None):
     _ucheck(op, _lib.load().unocg_uno_set_theta_dev(op, C.c_void_p(theta_dev.data_ptr()), _stream(stream)))
+
+
+def unocg_uno_set_modes_dev(op, M: int, w_dev, stream=None):
+    _ucheck(op, _lib.load().unocg_uno_set_modes_dev(op, M, C.c_void_p(w_dev.data_ptr()), _stream(stream)))
 
 
 def unocg_uno_apply_dev(op, batch: int, r_dev, s_dev, stream=None):

@@ -82,7 +82,8 @@ struct unocg_ctx {
   int wkind = -1;
   bool q_dirty = true, bf16_spd_ok = true;
   double spd_eps = 0.0;
-  std::vector<double> w_host;  // user weights (BLOCKS / THETA), FP64
+  std::vector<double> w_host;  // user weights (BLOCKS / THETA / MODES), FP64
+  int modes_M = -1;            // MODES: mode-set parameter M
   cudaStream_t stream = nullptr, own_stream = nullptr;
   std::string err;
   // device data
@@ -136,8 +137,13 @@ struct unocg_uno {
   size_t cap = 0;  // fields of capacity
   float* gq = nullptr;
   float* gq2 = nullptr;
+  int modes_M = -1;            // >= 0: theta holds bypass + mode weights [1 + n_modes][C]
+  double* mscratch = nullptr;  // partial sums of the bypass gradient
   std::string err;
 };
+
+static int n_modes_of(int M) { return (2 * M + 1) * (2 * M + 1) * (M + 1) - 1; }
+static bool modes_fit(const Grid& g, int M) { return M >= 0 && 2 * M + 1 <= g.n1 && 2 * M + 1 <= g.n2 && 2 * M <= g.n3; }
 
 // ------------------------------------------------------------------ helpers
 static int fail(unocg_ctx* ctx, int code, const std::string& msg) {
@@ -425,7 +431,8 @@ static int build_weights(unocg_ctx* ctx) {
     CK(launch_ref_q(a, ctx->B, ctx->stream));
     return finish_weights(ctx);
   }
-  // user weights: host FP64 copy -> device, psi (THETA), symmetrize the self-conjugate planes
+  // user weights: host FP64 copy -> device, psi (THETA) or bypass + modes (MODES), symmetrize the
+  // self-conjugate planes
   if (ctx->Bq != 1 && ctx->Q64) {
     cudaFree(ctx->Q64); cudaFree(ctx->Q32); cudaFree(ctx->Q16);
     ctx->Q64 = nullptr; ctx->Q32 = nullptr; ctx->Q16 = nullptr;
@@ -435,12 +442,16 @@ static int build_weights(unocg_ctx* ctx) {
   CK(dalloc(&ctx->Q64, m));
   double* tmp = nullptr;
   double* tmp2 = nullptr;
-  CK(cudaMalloc(&tmp, m * sizeof(double)));
+  const size_t mw = std::max(m, ctx->w_host.size());
+  CK(cudaMalloc(&tmp, mw * sizeof(double)));
   cudaError_t e = cudaMalloc(&tmp2, m * sizeof(double));
   if (e != cudaSuccess) { cudaFree(tmp); return fail(ctx, UNOCG_ERR_OOM, "weights buffer"); }
-  e = cudaMemcpyAsync(tmp, ctx->w_host.data(), m * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+  e = cudaMemcpyAsync(tmp, ctx->w_host.data(), ctx->w_host.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess && ctx->wkind == UNOCG_W_THETA) {
     e = launch_psi64(tmp, tmp2, ctx->g.nh, ctx->c, ctx->stream);
+    std::swap(tmp, tmp2);
+  } else if (e == cudaSuccess && ctx->wkind == UNOCG_W_MODES) {
+    e = launch_modes_expand64(tmp, ctx->modes_M, ctx->g, ctx->c, tmp2, ctx->stream);
     std::swap(tmp, tmp2);
   }
   if (e == cudaSuccess) e = launch_symmetrize64(tmp, ctx->Q64, ctx->g, NQ, 1, ctx->stream);
@@ -449,6 +460,23 @@ static int build_weights(unocg_ctx* ctx) {
   cudaFree(tmp2);
   if (e != cudaSuccess) return fail(ctx, UNOCG_ERR_CUDA, std::string("weights: ") + cudaGetErrorString(e));
   return finish_weights(ctx);
+}
+
+extern "C" int unocg_set_uno_modes(unocg_ctx* ctx, int M, const void* w, int dtype, double spd_eps) {
+  if (!ctx) return UNOCG_ERR_INVALID_ARG;
+  if (!modes_fit(ctx->g, M)) return fail(ctx, UNOCG_ERR_INVALID_ARG, "mode set [-M,M]^2 x [0,M] does not fit the grid");
+  if (!w || (dtype != UNOCG_DTYPE_F64 && dtype != UNOCG_DTYPE_F32))
+    return fail(ctx, UNOCG_ERR_INVALID_ARG, "weights need a host array of dtype F64 or F32");
+  if (!(spd_eps >= 0.0)) return fail(ctx, UNOCG_ERR_INVALID_ARG, "spd_eps must be >= 0");
+  ctx->spd_eps = spd_eps;
+  ctx->wkind = UNOCG_W_MODES;
+  ctx->modes_M = M;
+  ctx->q_dirty = true;
+  const size_t m = (size_t)(1 + n_modes_of(M)) * (ctx->c == 1 ? 1 : 6);
+  ctx->w_host.resize(m);
+  for (size_t i = 0; i < m; ++i)
+    ctx->w_host[i] = dtype == UNOCG_DTYPE_F64 ? ((const double*)w)[i] : (double)((const float*)w)[i];
+  return build_weights(ctx);
 }
 
 extern "C" int unocg_set_uno_weights(unocg_ctx* ctx, int kind, const void* w, int dtype, double spd_eps) {
@@ -1351,13 +1379,14 @@ extern "C" int unocg_uno_create(unocg_uno** out, int c, int n1, int n2, int n3) 
   UCK(cudaMalloc(&op->Qtmp, m * sizeof(float)));
   UCK(cudaMalloc(&op->gq, m * sizeof(float)));
   UCK(cudaMalloc(&op->gq2, m * sizeof(float)));
+  UCK(cudaMalloc(&op->mscratch, modes_grad_scratch_doubles() * sizeof(double)));
   return UNOCG_OK;
 }
 
 extern "C" void unocg_uno_destroy(unocg_uno* op) {
   if (!op) return;
   cudaDeviceSynchronize();
-  void* ptrs[] = {op->Q32, op->Qtmp, op->hat, op->shat, op->ghat, op->gq, op->gq2,
+  void* ptrs[] = {op->Q32, op->Qtmp, op->hat, op->shat, op->ghat, op->gq, op->gq2, op->mscratch,
                   op->tw32[0], op->tw32[1], op->tw32[2], op->tw32[3]};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -1377,7 +1406,19 @@ extern "C" int unocg_uno_set_theta_dev(unocg_uno* op, const float* theta_dev, vo
   if (!op || !theta_dev) return UNOCG_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   op->theta = theta_dev;
+  op->modes_M = -1;
   UCK(launch_psi32(theta_dev, op->Qtmp, op->g.nh, op->c, s));
+  UCK(launch_symmetrize32(op->Qtmp, op->Q32, op->g, op->c == 1 ? 1 : 6, 1, s));
+  return UNOCG_OK;
+}
+
+extern "C" int unocg_uno_set_modes_dev(unocg_uno* op, int M, const float* w_dev, void* stream) {
+  if (!op || !w_dev) return UNOCG_ERR_INVALID_ARG;
+  if (!modes_fit(op->g, M)) return ufail(op, UNOCG_ERR_INVALID_ARG, "mode set [-M,M]^2 x [0,M] does not fit the grid");
+  cudaStream_t s = (cudaStream_t)stream;
+  op->theta = w_dev;
+  op->modes_M = M;
+  UCK(launch_modes_expand32(w_dev, M, op->g, op->c, op->Qtmp, s));
   UCK(launch_symmetrize32(op->Qtmp, op->Q32, op->g, op->c == 1 ? 1 : 6, 1, s));
   return UNOCG_OK;
 }
@@ -1441,7 +1482,10 @@ extern "C" int unocg_uno_backward_dev(unocg_uno* op, int batch, const float* r_d
   if (gtheta_dev) {
     // Q_sym = S psi(theta) with S the (self-adjoint) plane averaging: dL/dpsi = S dL/dQ_sym
     UCK(launch_symmetrize32(op->gq, op->gq2, op->g, NQ, 1, s));
-    UCK(launch_psi_grad(op->theta, op->gq2, gtheta_dev, op->g.nh, op->c, s));
+    if (op->modes_M >= 0)
+      UCK(launch_modes_grad(op->theta, op->modes_M, op->g, op->c, op->gq2, op->mscratch, gtheta_dev, s));
+    else
+      UCK(launch_psi_grad(op->theta, op->gq2, gtheta_dev, op->g.nh, op->c, s));
   }
   return UNOCG_OK;
 }

@@ -115,6 +115,114 @@ __global__ void k_psi_grad(const float* theta, const float* gq, float* gtheta, l
   }
 }
 
+// ---------------------------------------------------------------- bypass + limited mode set
+// Eq. (fnocg-parametrization) with the periodic mode set K_M = [-M, M]^2 x [0, M] minus {0}:
+// weights w[0] (bypass W = psi(w[0]), every mode) and w[1 + i] (mode i, order: k1 slowest from
+// -M, then k2 from -M, then k3 from 0).  Mode index of a half-grid position, or -1.
+__device__ __forceinline__ int mode_index(int k1, int k2, int k3, const Grid& g, int M) {
+  const int s1 = 2 * k1 <= g.n1 ? k1 : k1 - g.n1;
+  const int s2 = 2 * k2 <= g.n2 ? k2 : k2 - g.n2;
+  if (s1 < -M || s1 > M || s2 < -M || s2 > M || k3 > M) return -1;
+  if (s1 == 0 && s2 == 0 && k3 == 0) return -1;
+  const int lin = ((s1 + M) * (2 * M + 1) + (s2 + M)) * (M + 1) + k3;
+  const int zero = (M * (2 * M + 1) + M) * (M + 1);
+  return lin > zero ? lin - 1 : lin;
+}
+
+// unique entries of psi(th) (paper order) added to q
+template <typename TI>
+__device__ __forceinline__ void psi_add(const TI* th, int c, double* q) {
+  if (c == 1) {
+    const double t = (double)th[0];
+    q[0] += t * t;
+    return;
+  }
+  const double t1 = th[0], t2 = th[1], t3 = th[2], t4 = th[3], t5 = th[4], t6 = th[5];
+  q[0] += t1 * t1;
+  q[1] += t3 * t3 + t2 * t2;
+  q[2] += t1 * t3;
+  q[3] += t6 * t6 + t5 * t5 + t4 * t4;
+  q[4] += t3 * t6 + t2 * t5;
+  q[5] += t1 * t6;
+}
+
+// raw entries W + K(k) on the half grid (made even on the self-conjugate planes afterwards)
+template <typename TI, typename TO>
+__global__ void k_modes_expand(const TI* w, int M, Grid g, int c, TO* Q) {
+  const int NQ = c == 1 ? 1 : 6;
+  const long long MM = (long long)g.n2 * g.n3h;
+  for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < g.nh; m += (long long)gridDim.x * blockDim.x) {
+    const int k1 = (int)(m / MM), rem = (int)(m % MM);
+    const int k2 = rem / g.n3h, k3 = rem % g.n3h;
+    double q[6] = {0, 0, 0, 0, 0, 0};
+    psi_add(w, c, q);
+    const int i = mode_index(k1, k2, k3, g, M);
+    if (i >= 0) psi_add(w + (long long)(1 + i) * NQ, c, q);
+    for (int e = 0; e < NQ; ++e) Q[m * NQ + e] = (TO)q[e];
+  }
+}
+
+// (d entries / d theta)^T g for one weight vector
+__device__ __forceinline__ void psi_grad_one(const float* th, const float* gv, int c, float* o) {
+  if (c == 1) {
+    o[0] = 2.0f * th[0] * gv[0];
+    return;
+  }
+  const float t1 = th[0], t2 = th[1], t3 = th[2], t4 = th[3], t5 = th[4], t6 = th[5];
+  o[0] = 2.f * t1 * gv[0] + t3 * gv[2] + t6 * gv[5];
+  o[1] = 2.f * t2 * gv[1] + t5 * gv[4];
+  o[2] = 2.f * t3 * gv[1] + t1 * gv[2] + t6 * gv[4];
+  o[3] = 2.f * t4 * gv[3];
+  o[4] = 2.f * t5 * gv[3] + t2 * gv[4];
+  o[5] = 2.f * t6 * gv[3] + t3 * gv[4] + t1 * gv[5];
+}
+
+// per-block sums of the entry gradients over all half-grid modes (the bypass acts on each)
+constexpr int kModesGradParts = 128;
+__global__ void __launch_bounds__(256) k_modes_grad_sum(const float* gq, long long nh, int NQ, double* part) {
+  __shared__ double red[6][8];
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < nh; m += (long long)gridDim.x * blockDim.x)
+    for (int e = 0; e < NQ; ++e) acc[e] += (double)gq[m * NQ + e];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int e = 0; e < NQ; ++e) {
+    double v = acc[e];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[e][warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < NQ) {
+    double v = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) v += red[threadIdx.x][k];
+    part[blockIdx.x * 6 + threadIdx.x] = v;
+  }
+}
+
+// gw[0] from the summed gradient, gw[1 + i] from the gradient at mode i
+__global__ void k_modes_grad(const float* w, int M, Grid g, int c, const float* gq, const double* part, int nparts,
+                             float* gw) {
+  const int NQ = c == 1 ? 1 : 6;
+  const int n_modes = (2 * M + 1) * (2 * M + 1) * (M + 1) - 1;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_modes; i += gridDim.x * blockDim.x) {
+    int lin = i;
+    if (lin >= (M * (2 * M + 1) + M) * (M + 1)) ++lin;  // skip k = 0
+    const int k3 = lin % (M + 1), t = lin / (M + 1);
+    const int s2 = t % (2 * M + 1) - M, s1 = t / (2 * M + 1) - M;
+    const int k1 = s1 < 0 ? s1 + g.n1 : s1, k2 = s2 < 0 ? s2 + g.n2 : s2;
+    const long long m = ((long long)k1 * g.n2 + k2) * g.n3h + k3;
+    psi_grad_one(w + (long long)(1 + i) * NQ, gq + m * NQ, c, gw + (long long)(1 + i) * NQ);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    float sum[6];
+    for (int e = 0; e < NQ; ++e) {
+      double v = 0.0;
+      for (int k = 0; k < nparts; ++k) v += part[k * 6 + e];
+      sum[e] = (float)v;
+    }
+    psi_grad_one(w, sum, c, gw);
+  }
+}
+
 // Average the entries of (k1, k2) and (-k1, -k2) on the planes k3 = 0 and k3 = N3/2.
 template <typename TQ>
 __global__ void k_symmetrize(const TQ* in, TQ* out, Grid g, int NQ, int nb) {
@@ -226,6 +334,24 @@ cudaError_t launch_psi64(const double* theta, double* Q, long long nh, int c, cu
 }
 cudaError_t launch_psi32(const float* theta, float* Q, long long nh, int c, cudaStream_t s) {
   k_psi<float, float><<<blocks_for(nh), 256, 0, s>>>(theta, Q, nh, c);
+  return cudaGetLastError();
+}
+cudaError_t launch_modes_expand64(const double* w, int M, const Grid& g, int c, double* Q, cudaStream_t s) {
+  k_modes_expand<double, double><<<blocks_for(g.nh), 256, 0, s>>>(w, M, g, c, Q);
+  return cudaGetLastError();
+}
+cudaError_t launch_modes_expand32(const float* w, int M, const Grid& g, int c, float* Q, cudaStream_t s) {
+  k_modes_expand<float, float><<<blocks_for(g.nh), 256, 0, s>>>(w, M, g, c, Q);
+  return cudaGetLastError();
+}
+size_t modes_grad_scratch_doubles() { return (size_t)kModesGradParts * 6; }
+cudaError_t launch_modes_grad(const float* w, int M, const Grid& g, int c, const float* gq, double* scratch, float* gw,
+                              cudaStream_t s) {
+  k_modes_grad_sum<<<kModesGradParts, 256, 0, s>>>(gq, g.nh, c == 1 ? 1 : 6, scratch);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int n_modes = (2 * M + 1) * (2 * M + 1) * (M + 1) - 1;
+  k_modes_grad<<<(n_modes + 255) / 256 + 1, 256, 0, s>>>(w, M, g, c, gq, scratch, kModesGradParts, gw);
   return cudaGetLastError();
 }
 cudaError_t launch_psi_grad(const float* theta, const float* gq, float* gtheta, long long nh, int c, cudaStream_t s) {

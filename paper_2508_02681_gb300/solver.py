@@ -50,6 +50,10 @@ class Homogenization:
     def set_uno_weights(self, kind=_lib.W_REFERENCE_MEDIUM, w=None, spd_eps: float = 0.0):
         api.unocg_set_uno_weights(self.ctx, kind, w, spd_eps)
 
+    def set_uno_modes(self, M: int, w, spd_eps: float = 0.0):
+        """The paper's weight layout: bypass ``w[0]`` plus ``w[1 + i]`` on the i-th mode of K_M."""
+        api.unocg_set_uno_modes(self.ctx, M, w, spd_eps)
+
     def solve(self, raise_on_error: bool = True, **opts) -> api.Info:
         return api.unocg_solve(self.ctx, api.make_opts(**opts), self.batch * self.n_loads, raise_on_error)
 
@@ -65,15 +69,23 @@ class Homogenization:
         return api.unocg_get_sensitivity(self.ctx, self.batch, n_props, self.n_loads)
 
 
-def uno_function():
-    """``torch.autograd.Function`` for ``s = P_theta r`` on a batch ``[B, c, N1, N2, N3]``."""
+def uno_function(modes_M: int | None = None):
+    """``torch.autograd.Function`` for ``s = P_theta r`` on a batch ``[B, c, N1, N2, N3]``.
+    theta: per-mode parameters ``[N1, N2, N3/2+1, C]``, or with ``modes_M`` the paper's layout
+    ``[1 + n_modes, C]`` (bypass, then the modes of K_M)."""
     import torch
+
+    def set_weights(op, theta):
+        if modes_M is None:
+            api.unocg_uno_set_theta_dev(op, theta)
+        else:
+            api.unocg_uno_set_modes_dev(op, modes_M, theta)
 
     class UnoApply(torch.autograd.Function):
         @staticmethod
         def forward(ctx, r, theta, op):
             r = r.contiguous()
-            api.unocg_uno_set_theta_dev(op, theta)
+            set_weights(op, theta)
             s = torch.empty_like(r)
             api.unocg_uno_apply_dev(op, r.shape[0], r, s)
             ctx.save_for_backward(r, theta)
@@ -86,7 +98,7 @@ def uno_function():
             gs = gs.contiguous()
             gr = torch.empty_like(r) if ctx.needs_input_grad[0] else None
             gt = torch.empty_like(theta) if ctx.needs_input_grad[1] else None
-            api.unocg_uno_set_theta_dev(ctx.op, theta)
+            set_weights(ctx.op, theta)
             api.unocg_uno_backward_dev(ctx.op, r.shape[0], r, gs, gr, gt)
             return gr, gt, None
 

@@ -58,13 +58,35 @@ def reference_theta(shape, kappa_ref: float) -> np.ndarray:
     return np.sqrt(q).reshape(shape[0], shape[1], shape[2] // 2 + 1, 1)
 
 
-def train(f, u, theta0, epochs: int, batch: int = 64, lr: float = 1e-2, seed: int = 0):
-    """Adam on the MSE loss; returns (theta tensor, per-epoch mean losses)."""
+def mode_set(M: int):
+    """Modes of K_M = [-M, M]^2 x [0, M] without k = 0, in the weight order of the library
+    (k1 slowest from -M, then k2 from -M, then k3 from 0)."""
+    return [(k1, k2, k3) for k1 in range(-M, M + 1) for k2 in range(-M, M + 1) for k3 in range(M + 1)
+            if (k1, k2, k3) != (0, 0, 0)]
+
+
+def reference_modes(shape, M: int, kappa_ref: float) -> np.ndarray:
+    """Weights ``[1 + n_modes, 1]`` of the paper's layout that reproduce the reference-medium
+    operator on K_M: the bypass is the smallest reference weight (its value at the highest
+    frequencies), each mode adds the rest of its reference weight."""
+    q = reference_theta(shape, kappa_ref)[..., 0] ** 2
+    qb = float(q.reshape(-1)[1:].min())
+    w = np.zeros((1 + len(mode_set(M)), 1))
+    w[0, 0] = np.sqrt(qb)
+    for i, (k1, k2, k3) in enumerate(mode_set(M)):
+        w[1 + i, 0] = np.sqrt(max(q[k1 % shape[0], k2 % shape[1], k3] - qb, 0.0))
+    return w
+
+
+def train(f, u, theta0, epochs: int, batch: int = 64, lr: float = 1e-2, seed: int = 0,
+          modes_M: int | None = None):
+    """Adam on the MSE loss; returns (theta tensor, per-epoch mean losses).  With ``modes_M``
+    theta0 is in the paper's layout ``[1 + n_modes, 1]`` (see ``reference_modes``)."""
     import torch
 
     shape = tuple(f.shape[2:])
     op = api.unocg_uno_create(1, *shape)
-    Fn = uno_function()
+    Fn = uno_function(modes_M)
     theta = torch.tensor(theta0, dtype=torch.float32, device="cuda", requires_grad=True)
     opt = torch.optim.Adam([theta], lr=lr)
     g = torch.Generator(device="cpu").manual_seed(seed)
