@@ -59,6 +59,7 @@ struct Fields32 {
   float *r = nullptr, *d = nullptr, *p = nullptr, *u = nullptr;
   float2 *rhat = nullptr, *shat = nullptr;
   double* u64 = nullptr;
+  double* f64 = nullptr;  // FP64 right-hand side of the true residual (written once per solve)
 };
 
 struct GraphKey {
@@ -270,7 +271,7 @@ extern "C" void unocg_destroy(unocg_ctx* ctx) {
                   ctx->Q32, ctx->Q16, ctx->sc, ctx->part, ctx->tickets, ctx->flags, ctx->fails,
                   ctx->f64.r, ctx->f64.d, ctx->f64.p, ctx->f64.u, ctx->f64.rhat, ctx->f64.shat,
                   ctx->f32.r, ctx->f32.d, ctx->f32.p, ctx->f32.u, ctx->f32.rhat, ctx->f32.shat,
-                  ctx->f32.u64, ctx->invdiag64, ctx->invdiag32, ctx->ceff, ctx->sens, ctx->stage,
+                  ctx->f32.u64, ctx->f32.f64, ctx->invdiag64, ctx->invdiag32, ctx->ceff, ctx->sens, ctx->stage,
                   ctx->tw64[0], ctx->tw64[1], ctx->tw64[2], ctx->tw64[3],
                   ctx->tw32[0], ctx->tw32[1], ctx->tw32[2], ctx->tw32[3]};
   for (void* p : ptrs)
@@ -534,6 +535,7 @@ static int ensure_workspace(unocg_ctx* ctx, int precision, int precond) {
     Fields32& f = ctx->f32;
     CK(dalloc(&f.r, fld)); CK(dalloc(&f.d, fld)); CK(dalloc(&f.p, fld)); CK(dalloc(&f.u, fld));
     CK(dalloc(&f.u64, fld));
+    CK(dalloc(&f.f64, fld));
     if (precond == UNOCG_PRECOND_UNO) { CK(dalloc(&f.rhat, hat)); CK(dalloc(&f.shat, hat)); }
     if (precond == UNOCG_PRECOND_JACOBI) CK(dalloc(&ctx->invdiag32, (size_t)ctx->B * ctx->c * n));
   }
@@ -549,6 +551,7 @@ template <> struct Sel<double> {
   static double* invdiag(unocg_ctx* c) { return c->invdiag64; }
   static double* u64(unocg_ctx* c) { return c->f64.u; }
   static double* u32(unocg_ctx*) { return nullptr; }
+  static const double* f64(unocg_ctx*) { return nullptr; }
 };
 template <> struct Sel<float> {
   using QT = __nv_bfloat16;
@@ -556,6 +559,7 @@ template <> struct Sel<float> {
   static const __nv_bfloat16* Q(unocg_ctx* c) { return c->Q16; }
   static float* invdiag(unocg_ctx* c) { return c->invdiag32; }
   static double* u64(unocg_ctx* c) { return c->f32.u64; }
+  static const double* f64(unocg_ctx* c) { return c->f32.f64; }
   static float* u32(unocg_ctx* c) { return c->f32.u; }
 };
 
@@ -630,6 +634,7 @@ static cudaError_t enq_pre(unocg_ctx* ctx, cudaStream_t s, const Plan& pl, const
   ia.g = ctx->g; ia.c = ctx->c; ia.L = ctx->L; ia.phase = ctx->phase; ia.mat = material(ctx);
   ia.loads = ctx->loads_d; ia.r = f.r; ia.u = f.u; ia.d = f.d; ia.p = f.p;
   ia.u64 = pl.mixed ? ctx->f32.u64 : nullptr;
+  ia.f64 = pl.mixed ? ctx->f32.f64 : nullptr;
   e = launch_init<T>(ia, BL, s);
   if (e != cudaSuccess) return e;
   if (pl.o.precond == UNOCG_PRECOND_JACOBI) {
@@ -706,7 +711,7 @@ static cudaError_t enq_replace(unocg_ctx* ctx, cudaStream_t s, const Plan& pl, c
   if (e != cudaSuccess) return e;
   TrueResArgs<T> ta{};
   ta.g = ctx->g; ta.c = ctx->c; ta.L = ctx->L; ta.phase = ctx->phase; ta.mat = material(ctx);
-  ta.loads = ctx->loads_d; ta.u64 = Sel<T>::u64(ctx); ta.r = f.r; ta.sc = ctx->sc;
+  ta.loads = ctx->loads_d; ta.u64 = Sel<T>::u64(ctx); ta.f64 = Sel<T>::f64(ctx); ta.r = f.r; ta.sc = ctx->sc;
   ta.only_pending = 1; ta.require_started = 0; ta.into_rmax = 1;
   e = launch_true_res<T>(ta, BL, s);
   if (e != cudaSuccess) return e;
@@ -717,7 +722,7 @@ template <typename T>
 static cudaError_t enq_post(unocg_ctx* ctx, cudaStream_t s, const Plan& pl) {
   auto& f = Sel<T>::f(ctx);
   const int BL = ctx->B * ctx->L;
-  const int nparts = 64;
+  const int nparts = 256;  // blocks per field of the final fold and the mean
   FoldArgs<T> fa{};
   fa.c = ctx->c; fa.n = ctx->g.n; fa.u64 = Sel<T>::u64(ctx); fa.u32 = Sel<T>::u32(ctx); fa.d = f.d;
   fa.sc = ctx->sc; fa.only_pending = 0; fa.part = ctx->part;
@@ -726,7 +731,7 @@ static cudaError_t enq_post(unocg_ctx* ctx, cudaStream_t s, const Plan& pl) {
   // true FP64 residual of the final iterate (reported), then zero mean, then averages
   TrueResArgs<T> ta{};
   ta.g = ctx->g; ta.c = ctx->c; ta.L = ctx->L; ta.phase = ctx->phase; ta.mat = material(ctx);
-  ta.loads = ctx->loads_d; ta.u64 = Sel<T>::u64(ctx); ta.r = nullptr; ta.sc = ctx->sc;
+  ta.loads = ctx->loads_d; ta.u64 = Sel<T>::u64(ctx); ta.f64 = Sel<T>::f64(ctx); ta.r = nullptr; ta.sc = ctx->sc;
   ta.only_pending = 0; ta.require_started = 0; ta.into_rmax = 0;
   e = launch_true_res<T>(ta, BL, s);
   if (e != cudaSuccess) return e;
@@ -891,6 +896,7 @@ static int run_persistent(unocg_ctx* ctx, const Plan& pl) {
   ia.g = ctx->g; ia.c = ctx->c; ia.L = ctx->L; ia.phase = ctx->phase; ia.mat = material(ctx);
   ia.loads = ctx->loads_d; ia.r = f.r; ia.u = f.u; ia.d = f.d; ia.p = f.p;
   ia.u64 = pl.mixed ? ctx->f32.u64 : nullptr;
+  ia.f64 = pl.mixed ? ctx->f32.f64 : nullptr;
   CK(launch_init<T>(ia, BL, s));
   PersistArgs<T, QT> a{};
   a.pf.g = ctx->g; a.pf.c = ctx->c; a.pf.BL = BL; a.pf.r = f.r; a.pf.p = f.p; a.pf.hat = f.rhat;

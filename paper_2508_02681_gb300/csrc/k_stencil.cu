@@ -91,7 +91,12 @@ __global__ void __launch_bounds__(256) k_true_res(TrueResArgs<T> a) {
     const double* u = a.u64 + (long long)bl * CC * n;
     const long long node = ((long long)i1 * g.n2 + i2) * g.n3 + i3;
     double f[CC], ku[CC];
-    node_rhs<CC>(ph, mt, g, i1, i2, i3, a.loads + l * (CC == 1 ? 3 : 6), f);
+    if (a.f64) {
+#pragma unroll
+      for (int i = 0; i < CC; ++i) f[i] = a.f64[(long long)bl * CC * n + i * n + node];
+    } else {
+      node_rhs<CC>(ph, mt, g, i1, i2, i3, a.loads + l * (CC == 1 ? 3 : 6), f);
+    }
     node_Ku<double, CC>(u, ph, mt, g, i1, i2, i3, ku);
 #pragma unroll
     for (int i = 0; i < CC; ++i) {

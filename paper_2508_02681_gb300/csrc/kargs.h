@@ -119,6 +119,7 @@ template <typename T> struct TrueResArgs {
   Material mat;
   const double* loads;
   const double* u64;    // [BL][c][n]
+  const double* f64;    // optional: the FP64 right-hand side [BL][c][n] (else recomputed)
   T* r;                 // optional: store f - K u
   CgScal* sc;
   int only_pending;     // only (instance, load) with need_replace set
