@@ -40,4 +40,28 @@ __host__ __device__ constexpr double Kmu(int a, int i, int b, int k) {
   return (i == k ? Klap(a, b) : 0.0) + Gpq(k, i, a, b);
 }
 
+// The same entries as tables evaluated at compile time, in the arithmetic type of the kernel:
+// the stencil loops index them with unrolled constants, so no coefficient is computed at run
+// time (an evaluation of Klam / Kmu in device code would run in FP64).
+template <typename T> struct ElasticTable {
+  T lam[8][3][8][3];
+  T mu[8][3][8][3];
+};
+template <typename T> constexpr ElasticTable<T> make_elastic_table() {
+  ElasticTable<T> t{};
+  for (int a = 0; a < 8; ++a)
+    for (int i = 0; i < 3; ++i)
+      for (int b = 0; b < 8; ++b)
+        for (int k = 0; k < 3; ++k) {
+          t.lam[a][i][b][k] = (T)Klam(a, i, b, k);
+          t.mu[a][i][b][k] = (T)Kmu(a, i, b, k);
+        }
+  return t;
+}
+__constant__ constexpr ElasticTable<float> kElastic32 = make_elastic_table<float>();
+__constant__ constexpr ElasticTable<double> kElastic64 = make_elastic_table<double>();
+template <typename T> __device__ __forceinline__ const ElasticTable<T>& elastic_table();
+template <> __device__ __forceinline__ const ElasticTable<float>& elastic_table<float>() { return kElastic32; }
+template <> __device__ __forceinline__ const ElasticTable<double>& elastic_table<double>() { return kElastic64; }
+
 }  // namespace unocg

@@ -132,8 +132,8 @@ __device__ __forceinline__ void node_Ku(const T* __restrict__ d, const uint8_t* 
         for (int i = 0; i < 3; ++i)
 #pragma unroll
           for (int k = 0; k < 3; ++k) {
-            aL[o][i] += (T)Klam(o, i, bc, k) * dv[k];
-            aM[o][i] += (T)Kmu(o, i, bc, k) * dv[k];
+            aL[o][i] += elastic_table<T>().lam[o][i][bc][k] * dv[k];
+            aM[o][i] += elastic_table<T>().mu[o][i][bc][k] * dv[k];
           }
       }
     }
