@@ -40,6 +40,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the uneven-batch measurement")
     ap.add_argument("--profile-only", action="store_true", help="a few solves, for ncu launch lists")
     ap.add_argument("--no-graph", action="store_true",
                     help="profile-only: host-driven loop (kernels inside conditional graph bodies are not visible to ncu)")
@@ -177,6 +178,43 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- our arm
+def batched_uneven(n_inst: int = 256, reps: int = 3):
+    """The serving-style uneven batch: 256 thermal instances with grids drawn from 32^3..128^3,
+    contrast log-uniform in [5, 1000], 3 loads, mixed precision to 1e-6.  The instances of one
+    size share a batched context; all sizes are solved together.  Inputs (tens of GB of fields)
+    exceed L2, so no flush is needed between solves."""
+    import multiprocessing as mp
+    import torch
+    from paper_2508_02681_gb300 import _lib
+    from paper_2508_02681_gb300.solver import UnevenBatch
+    from synth import unit_loads, workload
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
+        ws = pool.starmap(workload, [(5, i) for i in range(n_inst)])
+    t_gen = time.perf_counter() - t0
+    ub = UnevenBatch(_lib.THERMAL, [w["phase"] for w in ws], [w["props"] for w in ws], unit_loads(1))
+    opts = dict(tol=TOL, max_iter=3000, precision=_lib.MIXED)
+    res = ub.solve(**opts)  # warm-up: captures the graphs
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        t1 = time.perf_counter()
+        res = ub.solve(**opts)
+        ts.append(time.perf_counter() - t1)
+    ub.close()
+    sizes = {}
+    for w in ws:
+        sizes[str(w["phase"].shape[0])] = sizes.get(str(w["phase"].shape[0]), 0) + 1
+    ms = float(np.median(ts)) * 1000.0
+    dofs = sum(int(np.prod(w["phase"].shape)) for w in ws) * 3
+    return {"instances": n_inst, "grid_sizes": sizes, "loads": 3, "unknowns": dofs, "ms": ms,
+            "instances_per_s": n_inst / (ms * 1e-3), "reps": reps,
+            "max_iters": int(max(int(r[0].max()) for r in res)),
+            "all_converged": bool(all(np.all(r[2] == 0) and np.all(r[1] <= TOL) for r in res)),
+            "max_true_rel_res": float(max(float(r[1].max()) for r in res)),
+            "contexts": len(sizes), "input_generation_s": t_gen}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -330,6 +368,8 @@ def main():
         "clocks": clock_rec,
     }
     h.close()
+    if rank == 0 and world == 1 and not args.no_batch and not args.profile_only:
+        line["batched_uneven"] = batched_uneven()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import homogenize as hz
         t0 = time.perf_counter()

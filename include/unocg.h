@@ -94,7 +94,7 @@ typedef struct {
                         3 automatic: 2 for small problems, else 1                            */
   double replace_drop; /* MIXED: also replace once ||r||_inf has fallen below replace_drop
                           times its value at the previous replacement (reliable updates: the
-                          FP32 solution increment since then stays small); 0 disables, 1e-2
+                          FP32 solution increment since then stays small); 0 disables, 1e-3
                           keeps the iteration count of the FP64 path up to 256^3 grids      */
 } unocg_solve_opts;
 
@@ -178,8 +178,10 @@ int unocg_get_effective_tensor(unocg_ctx* ctx, double* out);
    self-adjoint, so the adjoint states are the forward solutions; needs a converged solve.  */
 int unocg_get_sensitivity(unocg_ctx* ctx, double* out);
 
-/* Solve several contexts (different grid sizes) in one device-resident loop with
-   per-(instance, load) convergence masks.  infos may be NULL or hold n_ctx entries.        */
+/* Solve several contexts together (e.g. one per grid size of an uneven batch): each
+   context's device-resident loop, with its per-(instance, load) convergence masks, is one
+   graph launch on the context's stream, and the launches run concurrently.  Blocks until
+   all are done.  infos may be NULL or hold n_ctx entries.                                  */
 int unocg_batch_solve(int n_ctx, unocg_ctx* const* ctxs, const unocg_solve_opts* opts,
                       unocg_solve_info* infos);
 

@@ -102,7 +102,7 @@ def unocg_get_uno_weights(ctx, instance: int, n_modes: int, C_: int) -> np.ndarr
 
 
 def make_opts(tol=1e-6, max_iter=10000, precond=_lib.PRECOND_UNO, precision=_lib.FP64,
-              replace_every=50, flexible=None, use_graph=3, replace_drop=1e-2) -> SolveOpts:
+              replace_every=50, flexible=None, use_graph=3, replace_drop=1e-3) -> SolveOpts:
     if flexible is None:
         flexible = 1 if precision == _lib.MIXED else 0
     return SolveOpts(tol, max_iter, precond, precision, replace_every, flexible, use_graph, replace_drop)
@@ -176,11 +176,22 @@ def unocg_get_sensitivity(ctx, batch: int, n_props: int, n_loads: int) -> np.nda
     return out
 
 
-def unocg_batch_solve(ctxs, opts: SolveOpts):
+def unocg_batch_solve(ctxs, opts: SolveOpts, n_results=None):
+    """Solve several contexts together; with ``n_results`` (results per context) returns their
+    ``Info`` objects."""
     arr = (C.c_void_p * len(ctxs))(*[c.value for c in ctxs])
-    rc = _lib.load().unocg_batch_solve(len(ctxs), arr, C.byref(opts), None)
+    infos = None
+    carr = None
+    if n_results is not None:
+        infos = [Info(n) for n in n_results]
+        carr = (SolveInfo * len(ctxs))(*[i.c for i in infos])
+    rc = _lib.load().unocg_batch_solve(len(ctxs), arr, C.byref(opts), carr)
     if rc != _lib.OK:
         raise UnocgError(rc, "batch solve failed")
+    if infos is not None:
+        for i, ci in zip(infos, carr):
+            i.c = ci
+    return infos
 
 
 def unocg_apply_K_dev(ctx, instance: int, d_dev, p_dev, stream=None):

@@ -69,6 +69,54 @@ class Homogenization:
         return api.unocg_get_sensitivity(self.ctx, self.batch, n_props, self.n_loads)
 
 
+class UnevenBatch:
+    """Many instances of possibly different grid sizes (the serving-style batch): the instances
+    of one size share a batched context (per-(instance, load) convergence masks), and the
+    contexts of all sizes are solved together by ``unocg_batch_solve``."""
+
+    def __init__(self, physics: int, phases, props, loads, n_phases: int = 2):
+        self.physics = physics
+        self.loads = np.atleast_2d(np.asarray(loads, dtype=np.float64))
+        groups: dict[tuple, list[int]] = {}
+        for i, ph in enumerate(phases):
+            groups.setdefault(tuple(ph.shape), []).append(i)
+        self.n = len(phases)
+        self.groups = []
+        for shape, idx in sorted(groups.items()):
+            h = Homogenization(physics, shape, batch=len(idx))
+            h.set_microstructure(np.stack([np.asarray(phases[i], dtype=np.uint8) for i in idx]), n_phases)
+            h.set_phase_properties(np.stack([np.asarray(props[i], dtype=np.float64) for i in idx]))
+            h.set_macro_load(self.loads)
+            h.set_uno_weights(_lib.W_REFERENCE_MEDIUM)
+            self.groups.append((idx, h))
+
+    def solve(self, **opts):
+        """Returns per-instance (iterations [L], true relative residuals [L], status)."""
+        hs = [h for _, h in self.groups]
+        infos = api.unocg_batch_solve([h.ctx for h in hs], api.make_opts(**opts),
+                                      [h.batch * self.loads.shape[0] for h in hs])
+        L = self.loads.shape[0]
+        out = [None] * self.n
+        for (idx, _), info in zip(self.groups, infos):
+            for j, i in enumerate(idx):
+                out[i] = (info.iters[j * L:(j + 1) * L].copy(), info.true_rel_res[j * L:(j + 1) * L].copy(),
+                          info.load_status[j * L:(j + 1) * L].copy())
+        return out
+
+    def effective_tensors(self) -> np.ndarray:
+        res = [None] * self.n
+        for idx, h in self.groups:
+            C = h.effective_tensor()
+            for j, i in enumerate(idx):
+                res[i] = C[j]
+        return np.stack(res)
+
+    def close(self):
+        for _, h in self.groups:
+            h.close()
+        self.groups = []
+
+
 def uno_function(modes_M: int | None = None):
     """``torch.autograd.Function`` for ``s = P_theta r`` on a batch ``[B, c, N1, N2, N3]``.
     theta: per-mode parameters ``[N1, N2, N3/2+1, C]``, or with ``modes_M`` the paper's layout
