@@ -699,42 +699,58 @@ static cudaError_t enq_body(unocg_ctx* ctx, cudaStream_t s, const Plan& pl, cons
   return e;
 }
 
-// FP64 residual replacement for the pending (instance, load) pairs, then a fresh residual check
+// Mixed precision: the FP64 residual rref = f - K u64 (f32.f64, written with f by the set-up)
+// is brought up to date, rref -= K (u32 + alpha d), in float-pair arithmetic; the pending
+// increment is folded into u64 afterwards.
+static ReplaceArgs replace_args(unocg_ctx* ctx, int only_pending, int into_rmax) {
+  ReplaceArgs ra{};
+  ra.g = ctx->g; ra.c = ctx->c; ra.L = ctx->L; ra.phase = ctx->phase; ra.mat = material(ctx);
+  ra.u32 = ctx->f32.u; ra.d = ctx->f32.d; ra.rref = ctx->f32.f64; ra.r = into_rmax ? ctx->f32.r : nullptr;
+  ra.sc = ctx->sc; ra.only_pending = only_pending; ra.into_rmax = into_rmax;
+  return ra;
+}
+
+// Residual replacement for the pending (instance, load) pairs, then a fresh residual check
 template <typename T>
 static cudaError_t enq_replace(unocg_ctx* ctx, cudaStream_t s, const Plan& pl, const LoopCtl& ctl) {
   auto& f = Sel<T>::f(ctx);
   const int BL = ctx->B * ctx->L;
+  cudaError_t e = launch_replace(replace_args(ctx, 1, 1), BL, s);
+  if (e != cudaSuccess) return e;
   FoldArgs<T> fa{};
   fa.c = ctx->c; fa.n = ctx->g.n; fa.u64 = Sel<T>::u64(ctx); fa.u32 = Sel<T>::u32(ctx); fa.d = f.d;
   fa.sc = ctx->sc; fa.only_pending = 1; fa.part = nullptr;
-  cudaError_t e = launch_fold<T>(fa, BL, s);
-  if (e != cudaSuccess) return e;
-  TrueResArgs<T> ta{};
-  ta.g = ctx->g; ta.c = ctx->c; ta.L = ctx->L; ta.phase = ctx->phase; ta.mat = material(ctx);
-  ta.loads = ctx->loads_d; ta.u64 = Sel<T>::u64(ctx); ta.f64 = Sel<T>::f64(ctx); ta.r = f.r; ta.sc = ctx->sc;
-  ta.only_pending = 1; ta.require_started = 0; ta.into_rmax = 1;
-  e = launch_true_res<T>(ta, BL, s);
+  e = launch_fold<T>(fa, BL, s);
   if (e != cudaSuccess) return e;
   return enq_residual_check<T>(ctx, s, ctl, 1, pl.o.precond);
 }
 
+// rref_kept: the loop maintained the FP64 residual rref (graph and host loops; the persistent
+// kernel replaces residuals by FP64 evaluations of its own and does not)
 template <typename T>
-static cudaError_t enq_post(unocg_ctx* ctx, cudaStream_t s, const Plan& pl) {
+static cudaError_t enq_post(unocg_ctx* ctx, cudaStream_t s, const Plan& pl, bool rref_kept = true) {
+  const bool inc = pl.mixed && rref_kept;
   auto& f = Sel<T>::f(ctx);
   const int BL = ctx->B * ctx->L;
   const int nparts = 256;  // blocks per field of the final fold and the mean
+  // reported true residual of the final iterate: mixed precision brings rref up to date with the
+  // last increment (before the final fold); FP64 evaluates f - K u directly (after it)
+  cudaError_t e = cudaSuccess;
+  if (inc) e = launch_replace(replace_args(ctx, 0, 0), BL, s);
+  if (e != cudaSuccess) return e;
   FoldArgs<T> fa{};
   fa.c = ctx->c; fa.n = ctx->g.n; fa.u64 = Sel<T>::u64(ctx); fa.u32 = Sel<T>::u32(ctx); fa.d = f.d;
   fa.sc = ctx->sc; fa.only_pending = 0; fa.part = ctx->part;
-  cudaError_t e = launch_final<T>(fa, BL, nparts, s);
+  e = launch_final<T>(fa, BL, nparts, s);
   if (e != cudaSuccess) return e;
-  // true FP64 residual of the final iterate (reported), then zero mean, then averages
-  TrueResArgs<T> ta{};
-  ta.g = ctx->g; ta.c = ctx->c; ta.L = ctx->L; ta.phase = ctx->phase; ta.mat = material(ctx);
-  ta.loads = ctx->loads_d; ta.u64 = Sel<T>::u64(ctx); ta.f64 = Sel<T>::f64(ctx); ta.r = nullptr; ta.sc = ctx->sc;
-  ta.only_pending = 0; ta.require_started = 0; ta.into_rmax = 0;
-  e = launch_true_res<T>(ta, BL, s);
-  if (e != cudaSuccess) return e;
+  if (!inc) {
+    TrueResArgs<T> ta{};
+    ta.g = ctx->g; ta.c = ctx->c; ta.L = ctx->L; ta.phase = ctx->phase; ta.mat = material(ctx);
+    ta.loads = ctx->loads_d; ta.u64 = Sel<T>::u64(ctx); ta.f64 = Sel<T>::f64(ctx); ta.r = nullptr; ta.sc = ctx->sc;
+    ta.only_pending = 0; ta.require_started = 0; ta.into_rmax = 0;
+    e = launch_true_res<T>(ta, BL, s);
+    if (e != cudaSuccess) return e;
+  }
   e = launch_zero_mean(Sel<T>::u64(ctx), ctx->part, nparts, ctx->c, ctx->g.n, BL, s);
   if (e != cudaSuccess) return e;
   AvgArgs aa{};
@@ -938,7 +954,7 @@ static int run_persistent(unocg_ctx* ctx, const Plan& pl) {
   a.ctl.replace_every = pl.o.replace_every; a.ctl.replace_drop = pl.o.replace_drop; a.ctl.flexible = pl.o.flexible;
   a.spin_limit = ctx->spin_limit;
   CK(launch_persist<T, QT>(a, s, ctx->sm_count));
-  CK(enq_post<T>(ctx, s, pl));
+  CK(enq_post<T>(ctx, s, pl, false));
   return UNOCG_OK;
 }
 

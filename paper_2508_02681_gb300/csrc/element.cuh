@@ -59,6 +59,19 @@ template <typename T> constexpr ElasticTable<T> make_elastic_table() {
   return t;
 }
 __constant__ constexpr ElasticTable<float> kElastic32 = make_elastic_table<float>();
+// 72 Klam and 72 Kmu are integers (denominators of the 1D integrals: 3, 6, 2), exact in FP32
+template <int S> constexpr ElasticTable<float> make_scaled_table() {
+  ElasticTable<float> t{};
+  for (int a = 0; a < 8; ++a)
+    for (int i = 0; i < 3; ++i)
+      for (int b = 0; b < 8; ++b)
+        for (int k = 0; k < 3; ++k) {
+          t.lam[a][i][b][k] = (float)(S * Klam(a, i, b, k));
+          t.mu[a][i][b][k] = (float)(S * Kmu(a, i, b, k));
+        }
+  return t;
+}
+__constant__ constexpr ElasticTable<float> kElastic72 = make_scaled_table<72>();
 __constant__ constexpr ElasticTable<double> kElastic64 = make_elastic_table<double>();
 template <typename T> __device__ __forceinline__ const ElasticTable<T>& elastic_table();
 template <> __device__ __forceinline__ const ElasticTable<float>& elastic_table<float>() { return kElastic32; }

@@ -11,6 +11,7 @@
 //  * true residual f - K u in FP64, post-processing (averaged flux/stress, sensitivities)
 #include "kargs.h"
 #include "element.cuh"
+#include "df64.cuh"
 #include "stencil.cuh"
 #include "ku_task.cuh"
 
@@ -107,6 +108,108 @@ __global__ void __launch_bounds__(256) k_true_res(TrueResArgs<T> a) {
   }
   __shared__ double red_sh[32];
   double bm = block_max(lmax, red_sh);
+  if (threadIdx.x == 0) atomic_max_nonneg(a.into_rmax ? &a.sc[bl].rmax_bits : &a.sc[bl].tmax_bits, bm);
+}
+
+// ============================================================================ residual replacement
+// rref <- rref - K w with w = u32 + alpha d, all products and sums in float pairs (df64.cuh):
+// the FP32 inputs are exact, the stencil coefficients are integers (thermal: 12 x the unit-cube
+// Laplacian, elastic: 72 x Klam / Kmu) times the phase constants as pairs, and the result is
+// rounded to FP64 once per node.  Element e = node - o holds the node as its corner o; its
+// corner b is the neighbour at offset b - o.
+template <int CC>
+__global__ void __launch_bounds__(256) k_replace(ReplaceArgs a) {
+  __shared__ float2 mp[2 * 256];  // phase constants (kappa, 0) or (lambda, mu) as pairs
+  const Grid& g = a.g;
+  const int bl = blockIdx.y;
+  const int b = bl / a.L;
+  const int np2 = 2 * a.mat.n_phases;
+  for (int i = threadIdx.x; i < np2; i += blockDim.x) {
+    const df32 v = df_from_double(a.mat.m64[(long long)b * np2 + i]);
+    mp[i] = make_float2(v.hi, v.lo);
+  }
+  __syncthreads();
+  if (a.only_pending && !a.sc[bl].need_replace) return;
+  const df32 al = df_from_double(a.sc[bl].alpha);
+  int i1, i2, i3;
+  double lmax = 0.0;
+  if (tile_node(g, i1, i2, i3)) {
+    const long long n = g.n;
+    const uint8_t* ph = a.phase + (long long)b * n;
+    const float* u32 = a.u32 + (long long)bl * CC * n;
+    const float* dd = a.d + (long long)bl * CC * n;
+    Nbr nb;
+    neighbours(g, i1, i2, i3, nb);
+    auto W = [&](int k, long long q) { return df_axpy(al, __ldg(dd + k * n + q), __ldg(u32 + k * n + q)); };
+    double kw[CC];
+    if (CC == 1) {
+      df32 w[3][3][3];
+#pragma unroll
+      for (int s1 = 0; s1 < 3; ++s1)
+#pragma unroll
+        for (int s2 = 0; s2 < 3; ++s2)
+#pragma unroll
+          for (int s3 = 0; s3 < 3; ++s3) w[s1][s2][s3] = W(0, nidx(nb, s1, s2, s3));
+      df32 acc = df_make(0.0f);
+#pragma unroll
+      for (int o = 0; o < 8; ++o) {
+        const int o1 = (o >> 2) & 1, o2 = (o >> 1) & 1, o3 = o & 1;
+        // 12 x (unit-cube Laplacian row): 4 on the node, -1 on the corners that differ from it in
+        // two or three coordinates, 0 on those that differ in one
+        df32 t = df_make(0.0f);
+        df_add_mul(t, 4.0f, w[1][1][1]);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int c1 = (c >> 2) & 1, c2 = (c >> 1) & 1, c3 = c & 1;
+          const int diff = (c1 != o1) + (c2 != o2) + (c3 != o3);
+          if (diff >= 2) df_add_mul(t, -1.0f, w[c1 - o1 + 1][c2 - o2 + 1][c3 - o3 + 1]);
+        }
+        const float2 kp = mp[2 * ph[eidx(nb, o1, o2, o3)]];
+        acc = df_add(acc, df_mul({kp.x, kp.y}, t));
+      }
+      kw[0] = df_to_double(acc) * (g.h / 12.0);
+    } else {
+      df32 out[3] = {df_make(0.0f), df_make(0.0f), df_make(0.0f)};
+      // one element at a time (not unrolled: the registers hold one element's 24 values)
+#pragma unroll 1
+      for (int o = 0; o < 8; ++o) {
+        const int o1 = (o >> 2) & 1, o2 = (o >> 1) & 1, o3 = o & 1;
+        df32 aL[3] = {df_make(0.0f), df_make(0.0f), df_make(0.0f)};
+        df32 aM[3] = {df_make(0.0f), df_make(0.0f), df_make(0.0f)};
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int c1 = (c >> 2) & 1, c2 = (c >> 1) & 1, c3 = c & 1;
+          const long long q = nidx(nb, c1 - o1 + 1, c2 - o2 + 1, c3 - o3 + 1);
+          const df32 wk[3] = {W(0, q), W(1, q), W(2, q)};
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+              df_add_mul(aL[i], kElastic72.lam[o][i][c][k], wk[k]);
+              df_add_mul(aM[i], kElastic72.mu[o][i][c][k], wk[k]);
+            }
+        }
+        const int p = ph[eidx(nb, o1, o2, o3)];
+        const float2 lp = mp[2 * p], mu = mp[2 * p + 1];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+          out[i] = df_add(out[i], df_add(df_mul({lp.x, lp.y}, aL[i]), df_mul({mu.x, mu.y}, aM[i])));
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i) kw[i] = df_to_double(out[i]) * (g.h / 72.0);
+    }
+    const long long node = ((long long)i1 * g.n2 + i2) * g.n3 + i3;
+#pragma unroll
+    for (int i = 0; i < CC; ++i) {
+      const long long x = (long long)bl * CC * n + i * n + node;
+      const double rr = a.rref[x] - kw[i];
+      a.rref[x] = rr;
+      if (a.r) a.r[x] = (float)rr;
+      lmax = fmax(lmax, fabs(rr));
+    }
+  }
+  __shared__ double red_sh[32];
+  const double bm = block_max(lmax, red_sh);
   if (threadIdx.x == 0) atomic_max_nonneg(a.into_rmax ? &a.sc[bl].rmax_bits : &a.sc[bl].tmax_bits, bm);
 }
 
@@ -397,6 +500,12 @@ static int pw_blocks(long long m) {
   long long b = (m + 255) / 256;
   if (b > 1184) b = 1184;  // 8 blocks per SM on 148+ SMs, grid-stride beyond
   return (int)(b < 1 ? 1 : b);
+}
+cudaError_t launch_replace(const ReplaceArgs& a, int BL, cudaStream_t s) {
+  dim3 grid = node_grid(a.g, BL);
+  if (a.c == 1) k_replace<1><<<grid, 256, 0, s>>>(a);
+  else k_replace<3><<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
 }
 template <typename T> cudaError_t launch_fold(const FoldArgs<T>& a, int BL, cudaStream_t s) {
   k_fold<T><<<dim3(pw_blocks((long long)a.c * a.n), BL), 256, 0, s>>>(a);

@@ -127,6 +127,25 @@ template <typename T> struct TrueResArgs {
   int into_rmax;        // accumulate into rmax_bits (replacement) instead of tmax_bits (report)
 };
 
+// Mixed-precision residual replacement: rref <- rref - K (u32 + alpha d) with FP64 accuracy
+// (float-pair arithmetic from the FP32 fields), r = rref in FP32, max |rref| per pair.  rref is
+// the FP64 residual f - K u64 of the FP64 solution (f before the first replacement); the fold
+// u64 += u32 + alpha d follows.
+struct ReplaceArgs {
+  Grid g;
+  int c, L;
+  const uint8_t* phase;
+  Material mat;
+  const float* u32;     // [BL][c][n] increment since the last replacement
+  const float* d;       // [BL][c][n] search direction of the pending step alpha d
+  double* rref;         // [BL][c][n] FP64 residual, updated in place
+  float* r;             // optional: the FP32 residual of the iteration
+  CgScal* sc;
+  int only_pending;     // only pairs with need_replace set
+  int into_rmax;        // accumulate into rmax_bits (replacement) or tmax_bits (final report)
+};
+cudaError_t launch_replace(const ReplaceArgs& a, int BL, cudaStream_t s);
+
 template <typename T> struct FoldArgs {
   int c;
   long long n;
