@@ -96,3 +96,53 @@ def grad_modes(w, M: int, shape, c: int, grad_entries):
     for i, (k1, k2, k3) in enumerate(uno.mode_list(M)):
         out[1 + i] = grad_theta(w[1 + i], g_raw[k1 % shape[0], k2 % shape[1], k3], c)
     return out
+
+
+def modes_loss_c1(w, M: int, shape, a, b):
+    """Loss of Eq. (loss-precomputed) for c = 1 from the features a, b (without the constant
+    delta) for the bypass-plus-modes weights ``w`` [1 + n_modes, 1]."""
+    v = uno.entries_from_blocks(uno.modes_Q(w, M, shape, 1))[..., 0]
+    return float(np.sum(a * v * v - b * v))
+
+
+def optimum_modes_c1(a, b, M: int, shape):
+    """Global minimizer of the c = 1 loss over the bypass-plus-modes weights (Sec. 5.4 for the
+    layout of Eq. (fnocg-parametrization)).  With beta = psi(w_0) and v_k = beta + psi(w_k) on
+    K_M, the loss sum_k a_k v_k^2 - b_k v_k separates: for fixed beta each mode of K_M takes
+    v_k = max(beta, b_k / (2 a_k)), every other mode v_k = beta, and the remaining function of
+    beta is convex with a nondecreasing piecewise-linear derivative whose root is bracketed and
+    found by bisection.  The k = 0 mode (a = b = 0 for zero-mean data) does not take part.
+    Returns w [1 + n_modes, 1]."""
+    N1, N2, N3 = shape
+    modes = uno.mode_list(M)
+    inK = np.zeros(a.shape, dtype=bool)
+    for (k1, k2, k3) in modes:
+        inK[k1 % N1, k2 % N2, k3] = True
+    # the mode set is even on the self-conjugate planes (its (k1, k2) range is symmetric), so
+    # the features there pair up and the optimum is even without the averaging step
+    with np.errstate(divide="ignore", invalid="ignore"):
+        c = np.where(a > 0, b / (2.0 * a), -np.inf)
+
+    def dphi(beta):
+        active = (~inK) | (c < beta)
+        return float(np.sum((2.0 * a * beta - b)[active]))
+
+    lo, hi = 0.0, 1.0
+    while dphi(hi) < 0:
+        hi *= 2.0
+    if dphi(lo) >= 0:
+        beta = 0.0
+    else:
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            if dphi(mid) < 0:
+                lo = mid
+            else:
+                hi = mid
+        beta = 0.5 * (lo + hi)
+    w = np.zeros((1 + len(modes), 1))
+    w[0, 0] = np.sqrt(beta)
+    for i, (k1, k2, k3) in enumerate(modes):
+        ck = c[k1 % N1, k2 % N2, k3]
+        w[1 + i, 0] = np.sqrt(max(ck - beta, 0.0)) if np.isfinite(ck) else 0.0
+    return w

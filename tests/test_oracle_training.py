@@ -94,3 +94,31 @@ def test_grad_modes_matches_central_differences(c, shape, M):
         wm[i, m] -= h
         fd = (loss(wp) - loss(wm)) / (2 * h)
         assert g[i, m] == pytest.approx(fd, rel=1e-6, abs=1e-8)
+
+
+def test_optimum_modes_c1_is_the_global_minimizer():
+    """The bypass-plus-modes optimum from the features: the loss from the features equals the
+    loss by definition up to its constant, the gradient vanishes wherever the weight is free,
+    and no perturbation lowers the loss."""
+    shape = (6, 6, 8)
+    M = 1
+    rng = np.random.default_rng(12)
+    f, u = _data(1, shape, 6, 40)
+    f -= f.mean(axis=(2, 3, 4), keepdims=True)  # zero-mean data: the k = 0 features vanish
+    R, U = training.spectra(f), training.spectra(u)
+    a, b = training.features_c1(R, U, shape)
+    w = training.optimum_modes_c1(a, b, M, shape)
+    delta = np.mean(np.sum(u ** 2, axis=(1, 2, 3, 4)))
+    # features reproduce the loss of Eq. (fnocg-loss)
+    lf = training.modes_loss_c1(w, M, shape, a, b) + delta
+    ld = training.loss_by_definition(uno.modes_Q(w, M, shape, 1), f, u)
+    assert lf == pytest.approx(ld, rel=1e-10)
+    # stationary in every weight (a weight at zero sits on the boundary psi = 0 with psi' = 0)
+    Q = uno.modes_Q(w, M, shape, 1)
+    g = training.grad_modes(w, M, shape, 1, training.grad_entries_general(Q, R, U, shape))
+    assert np.max(np.abs(g)) < 1e-7 * max(1.0, float(np.max(np.abs(b))))
+    # no perturbation lowers the loss
+    l0 = training.modes_loss_c1(w, M, shape, a, b)
+    for _ in range(50):
+        wp = w + 1e-3 * rng.standard_normal(w.shape)
+        assert training.modes_loss_c1(wp, M, shape, a, b) >= l0 - 1e-12 * abs(l0)
