@@ -213,6 +213,14 @@ int unocg_uno_apply_dev(unocg_uno* op, int batch, const float* r_dev, float* s_d
    dL/dQ(k) = sum_b w_k Re(conj(T gs_b) (T r_b)^T).                                         */
 int unocg_uno_backward_dev(unocg_uno* op, int batch, const float* r_dev, const float* gs_dev,
                            float* gr_dev, float* gtheta_dev, void* stream);
+/* Features of the second-order training (Sec. 5.4, Eq. (features-c-1); c = 1 only): for a
+   batch of right-hand sides f_dev and solutions u_dev (device float [batch][N1][N2][N3]) adds
+   sum_b w_k |(T f_b)(k)|^2 to ab_dev[0 .. nh) and sum_b w_k Re(conj((T u_b)(k)) (T f_b)(k)) to
+   ab_dev[nh .. 2 nh) (device float, nh = N1 N2 (N3/2+1), unitary T, w_k the half-grid
+   multiplicity); accumulate = 0 zeroes ab_dev first.  a = first / n_samples and
+   b = 2 second / n_samples.  The weights set on the operator are not used.                */
+int unocg_uno_features_dev(unocg_uno* op, int batch, const float* f_dev, const float* u_dev, float* ab_dev,
+                           int accumulate, void* stream);
 
 /* ---------------------------------------------------------------- operator-level entry points
    Device-pointer access to single steps of the hot path, on a context's microstructure and

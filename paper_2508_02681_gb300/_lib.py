@@ -83,6 +83,7 @@ SIGNATURES = {
     "unocg_uno_last_error": (C.c_char_p, [_vp]),
     "unocg_uno_set_theta_dev": (_i, [_vp, _vp, _vp]),
     "unocg_uno_set_modes_dev": (_i, [_vp, _i, _vp, _vp]),
+    "unocg_uno_features_dev": (_i, [_vp, _i, _vp, _vp, _vp, _i, _vp]),
     "unocg_uno_apply_dev": (_i, [_vp, _i, _vp, _vp, _vp]),
     "unocg_uno_backward_dev": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp]),
     "unocg_apply_K_dev": (_i, [_vp, _i, _vp, _vp, _vp]),

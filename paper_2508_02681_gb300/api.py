@@ -243,6 +243,12 @@ def unocg_uno_set_modes_dev(op, M: int, w_dev, stream=None):
     _ucheck(op, _lib.load().unocg_uno_set_modes_dev(op, M, C.c_void_p(w_dev.data_ptr()), _stream(stream)))
 
 
+def unocg_uno_features_dev(op, batch: int, f_dev, u_dev, ab_dev, accumulate: bool = False, stream=None):
+    _ucheck(op, _lib.load().unocg_uno_features_dev(op, batch, C.c_void_p(f_dev.data_ptr()),
+                                                   C.c_void_p(u_dev.data_ptr()), C.c_void_p(ab_dev.data_ptr()),
+                                                   1 if accumulate else 0, _stream(stream)))
+
+
 def unocg_uno_apply_dev(op, batch: int, r_dev, s_dev, stream=None):
     _ucheck(op, _lib.load().unocg_uno_apply_dev(op, batch, C.c_void_p(r_dev.data_ptr()),
                                                 C.c_void_p(s_dev.data_ptr()), _stream(stream)))

@@ -107,3 +107,85 @@ def train(f, u, theta0, epochs: int, batch: int = 64, lr: float = 1e-2, seed: in
         losses.append(tot / n)
     api.unocg_uno_destroy(op)
     return theta.detach(), losses
+
+
+def features(f, u, chunk: int = 64):
+    """Features a, b of Eq. (features-c-1) on the half grid [N1, N2, N3/2+1] (numpy float64) from
+    training data f, u (torch float32 [N_s, 1, N1, N2, N3] on the GPU): every sample is
+    transformed once (Sec. 5.4)."""
+    import torch
+
+    shape = tuple(f.shape[2:])
+    nh = shape[0] * shape[1] * (shape[2] // 2 + 1)
+    op = api.unocg_uno_create(1, *shape)
+    ab = torch.zeros(2 * nh, dtype=torch.float32, device=f.device)
+    n = f.shape[0]
+    for s0 in range(0, n, chunk):
+        fb = f[s0:s0 + chunk].contiguous()
+        ub = u[s0:s0 + chunk].contiguous()
+        api.unocg_uno_features_dev(op, fb.shape[0], fb, ub, ab, accumulate=s0 > 0)
+    torch.cuda.synchronize()
+    api.unocg_uno_destroy(op)
+    abh = ab.cpu().numpy().astype(np.float64).reshape(2, shape[0], shape[1], shape[2] // 2 + 1)
+    return abh[0] / n, 2.0 * abh[1] / n
+
+
+def _mode_index(shape, M: int):
+    N1, N2, _ = shape
+    ms = mode_set(M)
+    return (np.array([k1 % N1 for k1, _, _ in ms]), np.array([k2 % N2 for _, k2, _ in ms]),
+            np.array([k3 for _, _, k3 in ms]))
+
+
+def second_order_modes(a, b, M: int, w0, iters: int = 100, tol: float = 1e-12):
+    """Algorithm 4 (second-order training, c = 1) for the paper's layout: Newton-Raphson on the
+    weights w = [w_0; w_1 .. w_n] with gradient and Hessian of L = sum_k a_k v_k^2 - b_k v_k
+    (v_k = w_0^2 + w_i^2 on the i-th mode of K_M, w_0^2 elsewhere) from the features.  The
+    Hessian is an arrow matrix (the bypass couples to every mode): each step is an O(n) solve by
+    its Schur complement.  A step that does not lower the loss is damped (Levenberg-Marquardt).
+    Returns (w [1 + n_modes, 1], loss history without the constant delta)."""
+    shape = a.shape[:2] + (2 * (a.shape[2] - 1),)
+    i1, i2, i3 = _mode_index(shape, M)
+    ak, bk = a[i1, i2, i3], b[i1, i2, i3]
+    a_rest = a.sum() - ak.sum()
+    b_rest = b.sum() - bk.sum()
+    w = np.asarray(w0, dtype=np.float64).reshape(-1).copy()
+
+    def loss(x):
+        beta = x[0] ** 2
+        v = beta + x[1:] ** 2
+        return float(a_rest * beta * beta - b_rest * beta + np.sum(ak * v * v - bk * v))
+
+    hist = [loss(w)]
+    lam = 0.0
+    for _ in range(iters):
+        wb, wm = w[0], w[1:]
+        beta = wb * wb
+        v = beta + wm * wm
+        gk = 2.0 * ak * v - bk                    # dL/dv on the modes of K_M
+        g_rest = 2.0 * a_rest * beta - b_rest     # summed over all other modes
+        gb = 2.0 * wb * (g_rest + gk.sum())
+        gm = 2.0 * wm * gk
+        hbb = 8.0 * wb * wb * (a_rest + ak.sum()) + 2.0 * (g_rest + gk.sum())
+        hmm = 8.0 * ak * wm * wm + 2.0 * gk
+        hbm = 8.0 * ak * wb * wm
+        while True:
+            D = hmm + lam
+            if np.all(D > 0):
+                schur = hbb + lam - np.sum(hbm * hbm / D)
+                if schur > 0:
+                    xb = (gb - np.sum(hbm * gm / D)) / schur
+                    xm = (gm - hbm * xb) / D
+                    trial = w - np.concatenate(([xb], xm))
+                    lt = loss(trial)
+                    if lt <= hist[-1]:
+                        break
+            lam = max(2.0 * lam, 1e-12 * max(1.0, float(np.max(np.abs(hmm)))))
+            if lam > 1e30:
+                return w.reshape(-1, 1), hist
+        w = trial
+        hist.append(lt)
+        lam *= 0.1 if lam > 0 else 0.0
+        if abs(hist[-2] - hist[-1]) <= tol * max(1.0, abs(hist[-1])):
+            break
+    return w.reshape(-1, 1), hist

@@ -165,6 +165,13 @@ def test_config4_training_workload():
                     its_trained += int(info.iters[0])
             h.close()
     assert its_trained <= 1.1 * its_start + 2
+    # second-order training (Algorithm 4) from the features of the same data reaches the
+    # global optimum of the loss: at or below what Adam reached
+    a_f, b_f = tr.features(f, u)
+    w2, hist = tr.second_order_modes(a_f, b_f, M, w0)
+    delta = float((u.double() ** 2).sum()) / u.shape[0]
+    assert hist[-1] + delta <= losses[-1] * (1 + 1e-3)
+    assert all(h1 <= h0 + 1e-9 * abs(h0) for h0, h1 in zip(hist, hist[1:]))
     # weight gradient on 4 instances against central differences of the FP64 oracle loss
     f4 = f[:4].cpu().numpy().astype(np.float64)
     u4 = u[:4].cpu().numpy().astype(np.float64)
@@ -280,3 +287,20 @@ def test_solver_modes_weights_match_oracle_and_converge(physics):
         info = h.solve(tol=1e-6, max_iter=5000, precond=_lib.PRECOND_UNO, precision=prec)
         assert info.status == _lib.OK and np.all(info.true_rel_res <= 1e-6)
     h.close()
+
+
+@pytest.mark.parametrize("shape", [(8, 6, 10), (16, 32, 32), (32, 32, 32)])
+def test_features_match_oracle(shape):
+    """Features of Eq. (features-c-1) from the GPU transform passes against the oracle."""
+    import torch
+    from paper_2508_02681_gb300 import training as tr
+    B = 5
+    f = np.stack([random_field((1,) + shape, seed=300 + b) for b in range(B)])
+    u = np.stack([random_field((1,) + shape, seed=400 + b) for b in range(B)])
+    a, b = tr.features(torch.tensor(f, dtype=torch.float32, device="cuda"),
+                       torch.tensor(u, dtype=torch.float32, device="cuda"), chunk=2)
+    fr = f.astype(np.float32).astype(np.float64)
+    ur = u.astype(np.float32).astype(np.float64)
+    a_ref, b_ref = training.features_c1(training.spectra(fr), training.spectra(ur), shape)
+    assert rel(a, a_ref) < 1e-5
+    assert rel(b, b_ref) < 1e-5

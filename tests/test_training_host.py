@@ -1,0 +1,25 @@
+"""Host side of the second-order training (Algorithm 4, c = 1): the Newton-Raphson iteration on
+the bypass-plus-modes weights reaches the oracle's global optimum from the features."""
+import numpy as np
+import pytest
+
+from oracle import training as ot
+from paper_2508_02681_gb300 import training as pt
+from synth import random_field
+
+
+@pytest.mark.parametrize("shape,M,seed", [((8, 8, 8), 2, 0), ((6, 10, 8), 1, 1), ((12, 12, 16), 4, 2)])
+def test_newton_reaches_the_global_optimum(shape, M, seed):
+    rng = np.random.default_rng(seed)
+    f = np.stack([random_field((1,) + shape, seed=100 * seed + b) for b in range(5)])
+    f -= f.mean(axis=(2, 3, 4), keepdims=True)
+    u = np.stack([random_field((1,) + shape, seed=100 * seed + 50 + b) for b in range(5)])
+    R, U = ot.spectra(f), ot.spectra(u)
+    a, b = ot.features_c1(R, U, shape)
+    w_opt = ot.optimum_modes_c1(a, b, M, shape)
+    w0 = 0.5 + rng.random(w_opt.shape)
+    w, hist = pt.second_order_modes(a, b, M, w0)
+    l_opt = ot.modes_loss_c1(w_opt, M, shape, a, b)
+    assert ot.modes_loss_c1(w, M, shape, a, b) == pytest.approx(l_opt, rel=1e-9, abs=1e-12)
+    assert all(h1 <= h0 + 1e-12 * abs(h0) for h0, h1 in zip(hist, hist[1:]))  # monotone
+    assert len(hist) < 60
