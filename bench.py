@@ -52,6 +52,17 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def max_over_ranks(values, device):
+    """Element-wise maximum of `values` over all ranks (each rank solves its own instances: the
+    job time is the slowest rank's)."""
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if torch.distributed.is_available() and torch.distributed.is_initialized() and \
+            torch.distributed.get_world_size() > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
 # ----------------------------------------------------------------------------- clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -334,10 +345,7 @@ def main():
     h2d = n + w["props"].nbytes + w["loads"].nbytes
     d2h = L * n * 8 + 3 * L * 8
 
-    t_all = torch.tensor([t_mixed, e2e_ms], device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t_all, op=torch.distributed.ReduceOp.MAX)
-    t_mixed_max, e2e_max = float(t_all[0]), float(t_all[1])
+    t_mixed_max, e2e_max = max_over_ranks([t_mixed, e2e_ms], "cuda")
 
     launches = launches_per_solve(info_mixed) * args.steps
     line = {
