@@ -78,6 +78,67 @@ def reference_modes(shape, M: int, kappa_ref: float) -> np.ndarray:
     return w
 
 
+# unique entries of a symmetric 3 x 3 block in the paper's order (App. B.2)
+_ORDER3 = ((0, 0), (1, 1), (0, 1), (2, 2), (1, 2), (0, 2))
+# psi for c = 3 (Eq. (local-param-3)): Q = L L^T, L lower triangular with
+# L00 = w1, L11 = w2, L10 = w3, L22 = w4, L21 = w5, L20 = w6
+_L3 = ((0, 0), (1, 1), (1, 0), (2, 2), (2, 1), (2, 0))
+
+
+def psi(w, c: int) -> np.ndarray:
+    """Local SPD parametrization (Sec. 5.2.2) on the host: weights ``[..., C]`` -> blocks
+    ``[..., c, c]`` (``w^2`` for c = 1, ``L L^T`` for c = 3)."""
+    w = np.asarray(w, dtype=np.float64)
+    if c == 1:
+        return (w[..., 0] ** 2)[..., None, None]
+    L = np.zeros(w.shape[:-1] + (3, 3))
+    for i, (r, q) in enumerate(_L3):
+        L[..., r, q] = w[..., i]
+    return L @ np.swapaxes(L, -1, -2)
+
+
+def psi_inverse(Q) -> np.ndarray:
+    """Weights w with psi(w) = Q for symmetric positive semi-definite blocks ``[..., c, c]``
+    (square root for c = 1, the Cholesky factor with a non-negative diagonal for c = 3; a
+    semi-definite block is factored after shifting it by 1e-14 of its trace)."""
+    Q = np.asarray(Q, dtype=np.float64)
+    c = Q.shape[-1]
+    if c == 1:
+        return np.sqrt(np.maximum(Q[..., 0, :], 0.0))
+    shift = 1e-14 * np.trace(Q, axis1=-2, axis2=-1)[..., None, None] * np.eye(3)
+    L = np.linalg.cholesky(Q + shift)
+    return np.stack([L[..., r, q] for (r, q) in _L3], axis=-1)
+
+
+def reference_modes_blocks(physics: int, shape, M: int, ref_props) -> np.ndarray:
+    """Weights ``[1 + n_modes, C]`` of the paper's layout from the reference-medium weights of
+    a homogeneous phase ``ref_props`` (kappa, or (E, nu)): the bypass is lambda I with lambda
+    the smallest eigenvalue of Q_ref(k) over k != 0, each mode of K_M adds
+    Q_ref(k) - lambda I.  For c = 1 this is ``reference_modes``."""
+    c = 1 if physics == _lib.THERMAL else 3
+    C = c * (c + 1) // 2
+    h = Homogenization(physics, shape)
+    h.set_microstructure(np.zeros(shape, np.uint8), 1)
+    h.set_phase_properties(np.atleast_2d(np.asarray(ref_props, dtype=np.float64)).reshape(1, -1)
+                           if c == 3 else np.array([float(ref_props)]))
+    h.set_uno_weights(_lib.W_REFERENCE_MEDIUM)
+    nh = shape[0] * shape[1] * (shape[2] // 2 + 1)
+    v = api.unocg_get_uno_weights(h.ctx, 0, nh, C).reshape(shape[0], shape[1], -1, C)
+    h.close()
+    Q = np.zeros(v.shape[:3] + (c, c))
+    if c == 1:
+        Q[..., 0, 0] = v[..., 0]
+    else:
+        for i, (r, q) in enumerate(_ORDER3):
+            Q[..., r, q] = Q[..., q, r] = v[..., i]
+    lam = float(np.linalg.eigvalsh(Q.reshape(-1, c, c)[1:]).min())
+    w = np.zeros((1 + len(mode_set(M)), C))
+    w[0] = psi_inverse(lam * np.eye(c))
+    i1, i2, i3 = _mode_index(shape, M)
+    w[1:] = psi_inverse(Q[i1, i2, i3] - lam * np.eye(c))
+    return w
+
+
 def train(f, u, theta0, epochs: int, batch: int = 64, lr: float = 1e-2, seed: int = 0,
           modes_M: int | None = None):
     """Adam on the MSE loss; returns (theta tensor, per-epoch mean losses).  With ``modes_M``

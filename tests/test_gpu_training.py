@@ -304,3 +304,104 @@ def test_features_match_oracle(shape):
     a_ref, b_ref = training.features_c1(training.spectra(fr), training.spectra(ur), shape)
     assert rel(a, a_ref) < 1e-5
     assert rel(b, b_ref) < 1e-5
+
+
+@pytest.mark.parametrize("physics,M,shape", [(1, 3, (12, 10, 12)), (3, 2, (8, 10, 6))])
+def test_reference_modes_blocks_match_oracle(physics, M, shape):
+    """Bypass-plus-modes weights built from the reference medium (c = 1 and c = 3): Q equals the
+    oracle's FANS weights S_ref(k)^{-1} on the modes of K_M and lambda_min I elsewhere."""
+    from paper_2508_02681_gb300 import _lib, training as tr
+    c = 1 if physics == 1 else 3
+    ref = 2.0 if physics == 1 else (5.0, 0.25)
+    w = tr.reference_modes_blocks(physics, shape, M, ref)
+    Qref = uno.reference_medium_Q(physics, [ref] if physics == 1 else [list(ref)], shape)
+    lam = uno.min_eigenvalue(Qref)
+    Qm = uno.modes_Q(w, M, shape, c)
+    in_set = np.zeros(Qm.shape[:3], bool)
+    for k1, k2, k3 in uno.mode_list(M):
+        in_set[k1 % shape[0], k2 % shape[1], k3] = True
+    scale = np.max(np.abs(Qref))
+    assert np.max(np.abs(Qm[in_set] - Qref[in_set])) < 1e-12 * scale
+    assert np.max(np.abs(Qm[~in_set] - lam * np.eye(c))) < 1e-12 * scale
+    if physics == 1:
+        assert np.max(np.abs(w - tr.reference_modes(shape, M, ref))) < 1e-12 * np.max(np.abs(w))
+
+
+def _band_limited(c, n, M, seed):
+    """Samples on an n^3 grid of a real zero-mean field whose Fourier modes lie in [-M, M]^3."""
+    rng = np.random.default_rng(seed)
+    x = np.arange(n) / n
+    X = np.meshgrid(x, x, x, indexing="ij")
+    out = np.zeros((c, n, n, n))
+    for comp in range(c):
+        for _ in range(12):
+            k = rng.integers(-M, M + 1, 3)
+            if not k.any():
+                continue
+            a, b = rng.standard_normal(2)
+            ph = 2 * np.pi * (k[0] * X[0] + k[1] * X[1] + k[2] * X[2])
+            out[comp] += a * np.cos(ph) + b * np.sin(ph)
+    return out
+
+
+@pytest.mark.parametrize("physics,M", [(1, 4), (3, 3)])
+def test_modes_weights_resolution_invariant_on_band_limited_fields(physics, M):
+    """Sec. 5.2.2: the learned modes act on the continuous operator, so one set of weights
+    preconditions every resolution.  For a field band-limited to [-M, M]^3 the unitary
+    transform carries its Fourier coefficients scaled by sqrt(n), Q(k) multiplies them and the
+    inverse transform undoes the scale: s = P r samples the same continuous field on a 16^3 and
+    a 32^3 grid."""
+    import torch
+    from paper_2508_02681_gb300 import _lib, api
+    from paper_2508_02681_gb300.solver import Homogenization
+    c = 1 if physics == 1 else 3
+    rng = np.random.default_rng(11)
+    w = rng.standard_normal((1 + len(uno.mode_list(M)), uno.n_unique(c))) * 0.3 + 0.9
+    out = {}
+    for n in (16, 32):
+        shape = (n, n, n)
+        h = Homogenization(physics, shape)
+        h.set_microstructure(np.zeros(shape, np.uint8), 1)
+        h.set_phase_properties(np.array([1.0]) if c == 1 else np.array([[1.0, 0.3]]))
+        h.set_macro_load(np.eye(3 if c == 1 else 6)[:1])
+        h.set_uno_modes(M, w)
+        r = torch.tensor(_band_limited(c, n, M, seed=5), dtype=torch.float64, device="cuda")
+        s = torch.empty_like(r)
+        api.unocg_apply_uno_dev(h.ctx, 0, r, s)
+        torch.cuda.synchronize()
+        out[n] = s.cpu().numpy()
+        h.close()
+    fine = out[32][:, ::2, ::2, ::2]
+    assert np.max(np.abs(fine - out[16])) < 1e-12 * np.max(np.abs(out[16]))
+    assert np.max(np.abs(out[16])) > 1.0
+
+
+@pytest.mark.parametrize("physics,M", [(1, 8), (3, 4)])
+def test_weights_from_32_solve_at_64(physics, M):
+    """Resolution transfer (Sec. 5.2.2): bypass-plus-modes weights built at 32^3 precondition the
+    same cell at 64^3 (spheres of radius 6 voxels, volume fraction 0.3) to the true residual
+    1e-6 in FP64 and mixed precision, in at most 10 % more iterations than the weights built at
+    64^3."""
+    from paper_2508_02681_gb300 import _lib, training as tr
+    from paper_2508_02681_gb300.solver import Homogenization
+    from synth import rsa_spheres, unit_loads
+    c = 1 if physics == 1 else 3
+    ref = 5.5 if physics == 1 else (5.5, 0.25)
+    props = np.array([1.0, 100.0]) if physics == 1 else np.array([[1.0, 0.3], [10.0, 0.2]])
+    shape = (64, 64, 64)
+    phase, _ = rsa_spheres(shape, 6.0, 0.3, seed=77)
+    w32 = tr.reference_modes_blocks(physics, (32, 32, 32), M, ref)
+    w64 = tr.reference_modes_blocks(physics, shape, M, ref)
+    its = {}
+    for name, w in (("from32", w32), ("native", w64)):
+        for prec in ((_lib.FP64, _lib.MIXED) if name == "from32" else (_lib.FP64,)):
+            h = Homogenization(physics, shape)
+            h.set_microstructure(phase, 2)
+            h.set_phase_properties(props)
+            h.set_macro_load(unit_loads(physics)[:1])
+            h.set_uno_modes(M, w)
+            info = h.solve(tol=1e-6, max_iter=3000, precond=_lib.PRECOND_UNO, precision=prec)
+            assert info.status == _lib.OK and np.all(info.true_rel_res <= 1e-6)
+            its[name, prec] = int(info.iters[0])
+            h.close()
+    assert its["from32", _lib.FP64] <= 1.1 * its["native", _lib.FP64] + 2

@@ -23,3 +23,26 @@ def test_newton_reaches_the_global_optimum(shape, M, seed):
     assert ot.modes_loss_c1(w, M, shape, a, b) == pytest.approx(l_opt, rel=1e-9, abs=1e-12)
     assert all(h1 <= h0 + 1e-12 * abs(h0) for h0, h1 in zip(hist, hist[1:]))  # monotone
     assert len(hist) < 60
+
+
+@pytest.mark.parametrize("c", [1, 3])
+def test_host_psi_and_its_inverse(c):
+    # the host parametrization agrees with the oracle's psi (Sec. 5.2.2), and psi_inverse
+    # recovers weights whose psi is a given SPD block
+    from oracle import uno
+    rng = np.random.default_rng(c)
+    C = c * (c + 1) // 2
+    w = rng.standard_normal((7, C))
+    assert np.max(np.abs(pt.psi(w, c) - uno.psi(w, c))) < 1e-15
+    A = rng.standard_normal((7, c, c))
+    Q = A @ np.swapaxes(A, -1, -2) + 0.1 * np.eye(c)
+    w2 = pt.psi_inverse(Q)
+    assert np.max(np.abs(uno.psi(w2, c) - Q)) < 1e-12 * np.max(np.abs(Q))
+    if c == 3:  # the Cholesky factor has a non-negative diagonal (w1, w2, w4)
+        assert np.all(w2[:, [0, 1, 3]] > 0)
+
+
+def test_mode_set_order_matches_oracle():
+    from oracle import uno
+    for M in (1, 2, 5):
+        assert pt.mode_set(M) == [tuple(k) for k in uno.mode_list(M)]
