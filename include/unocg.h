@@ -246,6 +246,57 @@ int unocg_apply_uno_dev_noalloc(unocg_ctx* ctx, int instance, const double* r_de
 /* Right-hand side f of load `load` (Sec. 6): double [c][N1][N2][N3].                        */
 int unocg_rhs_dev(unocg_ctx* ctx, int instance, int load, double* f_dev, void* stream);
 
+/* ---------------------------------------------------------------- Dirichlet boundary conditions
+   The fluctuation vanishes on the boundary of the cell (Sec. 6.1 / 6.2, "Dirichlet BC"; also
+   called kinematic uniform BC): on an N1 x N2 x N3 voxel grid only the M_a = N_a - 1 interior
+   nodes per axis are free (Sec. 4.1), and the unitary transform of the UNO preconditioner is
+   the orthonormal sine transform (DST-I) on every component, real, with no conjugate modes
+   (Dirichlet row of Table (fnocg-mode-selection-2d)).  Mode k = (k1, k2, k3), 0 <= k_a < M_a,
+   is the sine basis vector sqrt(2/N_a) sin(pi (j+1)(k_a+1)/N_a) per axis.
+   Same conventions as the periodic context: voxel edge h = L0 / N1, phase labels per voxel
+   [B][N1][N2][N3], loads, properties, status codes, unocg_solve_opts / unocg_solve_info.
+   Fields on the free nodes: device layout [c][M1][M2][M3] (double); host I/O interleaved
+   [M1*M2*M3*c].  No zero-mean projection (the Dirichlet fluctuation is unique).
+   Limits: 2 <= N_a <= 256, each N_a of the form 2^a 3^b 5^c.  The loop always runs as one
+   CUDA graph (use_graph is ignored); flexible CG is not available (UNOCG_ERR_INVALID_ARG).
+   MIXED precision: FP32 fields, transforms, K.u and FP32 weights; FP64 solution, reductions
+   and residual replacement r = f - K u, with the triggers of unocg_solve_opts.             */
+typedef struct unocg_dir unocg_dir;
+
+int unocg_dir_create(unocg_dir** out, int physics, int batch, int n1, int n2, int n3, double L0);
+void unocg_dir_destroy(unocg_dir* ctx);
+const char* unocg_dir_last_error(const unocg_dir* ctx);
+int unocg_dir_set_stream(unocg_dir* ctx, void* stream);
+int unocg_dir_set_microstructure(unocg_dir* ctx, const uint8_t* phase, int n_phases);
+int unocg_dir_set_phase_properties(unocg_dir* ctx, const double* props);
+int unocg_dir_set_macro_load(unocg_dir* ctx, int n_loads, const double* loads);
+/* UNO weights on the sine modes.  UNOCG_W_REFERENCE_MEDIUM (per instance, `w` unused):
+   Q(k) = (t_k^T K_ref t_k)^-1, the inverse of the c x c diagonal block of the sine-transformed
+   stiffness of the homogeneous medium with the arithmetic-mean conductivity / Lame constants
+   (exact inverse of that operator for c = 1; for c = 3 the transform does not decouple the
+   components and the off-diagonal blocks vanish on the diagonal k).  UNOCG_W_BLOCKS /
+   UNOCG_W_THETA: [M1][M2][M3][C] unique entries / psi parameters (shared by all instances).
+   Safety check lambda_min(Q(k)) > spd_eps on every mode (also after rounding to FP32 for the
+   mixed path), else UNOCG_ERR_NOT_SPD.                                                      */
+int unocg_dir_set_uno_weights(unocg_dir* ctx, int kind, const void* w, int dtype, double spd_eps);
+/* The paper's Dirichlet layout: Q(k) = psi(w_0) + psi(w_i) for the i-th mode of
+   [0, 2M]^3 (k1 slowest, then k2, then k3), psi(w_0) elsewhere; w: [1 + (2M+1)^3][C].
+   Requires 2M + 1 <= M_a on every axis.                                                    */
+int unocg_dir_set_uno_modes(unocg_dir* ctx, int M, const void* w, int dtype, double spd_eps);
+/* Q of `instance` (unscaled unique entries [M1][M2][M3][C], FP64) to host memory `out`.      */
+int unocg_dir_get_uno_weights(unocg_dir* ctx, int instance, double* out);
+int unocg_dir_solve(unocg_dir* ctx, const unocg_solve_opts* opts, unocg_solve_info* info);
+int unocg_dir_solve_async(unocg_dir* ctx, const unocg_solve_opts* opts);
+int unocg_dir_solve_wait(unocg_dir* ctx, unocg_solve_info* info);
+/* Fluctuation on the free nodes: host interleaved [M1*M2*M3*c] / device [c][M1][M2][M3].    */
+int unocg_dir_get_fluctuation(unocg_dir* ctx, int instance, int load, double* out);
+int unocg_dir_get_fluctuation_dev(unocg_dir* ctx, int instance, int load, double* out_dev, void* stream);
+/* Averaged flux / stress [B][dim][n_loads] over all voxels, as unocg_get_effective_tensor.  */
+int unocg_dir_get_effective_tensor(unocg_dir* ctx, double* out);
+/* q = K p and s = T^T Q T r (FP64, device [c][M1][M2][M3]) for one instance.                 */
+int unocg_dir_apply_K_dev(unocg_dir* ctx, int instance, const double* p_dev, double* q_dev, void* stream);
+int unocg_dir_apply_uno_dev(unocg_dir* ctx, int instance, const double* r_dev, double* s_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

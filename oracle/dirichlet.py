@@ -219,6 +219,31 @@ def reference_Q(physics: int, props, shape, L0: float = 1.0) -> np.ndarray:
     return np.linalg.inv(B)
 
 
+def mode_list(M: int):
+    """Modes of the Dirichlet set [0, 2M]^3 (Table (fnocg-mode-selection-2d)), k1 slowest; mode
+    index k_a is the sine basis vector of frequency k_a + 1."""
+    K = 2 * M + 1
+    return [(k1, k2, k3) for k1 in range(K) for k2 in range(K) for k3 in range(K)]
+
+
+def modes_Q(w: np.ndarray, M: int, shape, c: int) -> np.ndarray:
+    """Blocks ``[M1, M2, M3, c, c]`` of the paper's layout for Dirichlet BC: the bypass
+    ``psi(w[0])`` on every mode plus ``psi(w[1 + i])`` on the i-th mode of [0, 2M]^3
+    (Eq. (fnocg-parametrization); no conjugate modes for the sine transform)."""
+    from . import uno
+    w = np.asarray(w, dtype=np.float64)
+    modes = mode_list(M)
+    if w.shape != (1 + len(modes), uno.n_unique(c)):
+        raise ValueError("weights must be [1 + n_modes, C]")
+    Ms = free_shape(shape)
+    if any(2 * M + 1 > m for m in Ms):
+        raise ValueError("mode set larger than the free grid")
+    Q = np.broadcast_to(uno.psi(w[0], c), Ms + (c, c)).copy()
+    for i, (k1, k2, k3) in enumerate(modes):
+        Q[k1, k2, k3] += uno.psi(w[1 + i], c)
+    return Q
+
+
 # ---------------------------------------------------------------- solves
 
 def solve(phase, props, physics: int, loads, precond: str = "uno", tol: float = 1e-8,

@@ -90,6 +90,25 @@ SIGNATURES = {
     "unocg_apply_uno_dev": (_i, [_vp, _i, _vp, _vp, _vp]),
     "unocg_apply_uno_dev_noalloc": (_i, [_vp, _i, _vp, _vp, _vp]),
     "unocg_rhs_dev": (_i, [_vp, _i, _i, _vp, _vp]),
+    # Dirichlet boundary conditions (sine transform)
+    "unocg_dir_create": (_i, [C.POINTER(_vp), _i, _i, _i, _i, _i, _d]),
+    "unocg_dir_destroy": (None, [_vp]),
+    "unocg_dir_last_error": (C.c_char_p, [_vp]),
+    "unocg_dir_set_stream": (_i, [_vp, _vp]),
+    "unocg_dir_set_microstructure": (_i, [_vp, _vp, _i]),
+    "unocg_dir_set_phase_properties": (_i, [_vp, _vp]),
+    "unocg_dir_set_macro_load": (_i, [_vp, _i, _vp]),
+    "unocg_dir_set_uno_weights": (_i, [_vp, _i, _vp, _i, _d]),
+    "unocg_dir_set_uno_modes": (_i, [_vp, _i, _vp, _i, _d]),
+    "unocg_dir_get_uno_weights": (_i, [_vp, _i, _vp]),
+    "unocg_dir_solve": (_i, [_vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
+    "unocg_dir_solve_async": (_i, [_vp, C.POINTER(SolveOpts)]),
+    "unocg_dir_solve_wait": (_i, [_vp, C.POINTER(SolveInfo)]),
+    "unocg_dir_get_fluctuation": (_i, [_vp, _i, _i, _vp]),
+    "unocg_dir_get_fluctuation_dev": (_i, [_vp, _i, _i, _vp, _vp]),
+    "unocg_dir_get_effective_tensor": (_i, [_vp, _vp]),
+    "unocg_dir_apply_K_dev": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "unocg_dir_apply_uno_dev": (_i, [_vp, _i, _vp, _vp, _vp]),
 }
 
 _LIB = None

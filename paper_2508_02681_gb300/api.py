@@ -259,3 +259,112 @@ def unocg_uno_backward_dev(op, batch: int, r_dev, gs_dev, gr_dev, gtheta_dev, st
         op, batch, C.c_void_p(r_dev.data_ptr()), C.c_void_p(gs_dev.data_ptr()),
         C.c_void_p(gr_dev.data_ptr()) if gr_dev is not None else None,
         C.c_void_p(gtheta_dev.data_ptr()) if gtheta_dev is not None else None, _stream(stream)))
+
+
+# ---------------------------------------------------------------- Dirichlet boundary conditions
+def _dcheck(ctx, rc):
+    if rc != _lib.OK:
+        lib = _lib.load()
+        msg = lib.unocg_dir_last_error(ctx).decode() if ctx else ""
+        raise UnocgError(rc, msg)
+
+
+def unocg_dir_create(physics: int, batch: int, n1: int, n2: int, n3: int, L0: float = 1.0):
+    lib = _lib.load()
+    h = C.c_void_p()
+    rc = lib.unocg_dir_create(C.byref(h), physics, batch, n1, n2, n3, L0)
+    if rc != _lib.OK:
+        msg = lib.unocg_dir_last_error(h).decode() if h.value else "invalid arguments or unsupported grid"
+        if h.value:
+            lib.unocg_dir_destroy(h)
+        raise UnocgError(rc, msg)
+    return h
+
+
+def unocg_dir_destroy(ctx):
+    _lib.load().unocg_dir_destroy(ctx)
+
+
+def unocg_dir_set_stream(ctx, stream):
+    _dcheck(ctx, _lib.load().unocg_dir_set_stream(ctx, _stream(stream)))
+
+
+def unocg_dir_set_microstructure(ctx, phase: np.ndarray, n_phases: int):
+    a = np.ascontiguousarray(phase, dtype=np.uint8)
+    _dcheck(ctx, _lib.load().unocg_dir_set_microstructure(ctx, _ptr(a), n_phases))
+
+
+def unocg_dir_set_phase_properties(ctx, props: np.ndarray):
+    a = np.ascontiguousarray(props, dtype=np.float64)
+    _dcheck(ctx, _lib.load().unocg_dir_set_phase_properties(ctx, _ptr(a)))
+
+
+def unocg_dir_set_macro_load(ctx, loads: np.ndarray):
+    a = np.ascontiguousarray(np.atleast_2d(loads), dtype=np.float64)
+    _dcheck(ctx, _lib.load().unocg_dir_set_macro_load(ctx, a.shape[0], _ptr(a)))
+
+
+def unocg_dir_set_uno_weights(ctx, kind: int, w=None, spd_eps: float = 0.0):
+    if w is None:
+        _dcheck(ctx, _lib.load().unocg_dir_set_uno_weights(ctx, kind, None, _lib.DTYPE_F64, spd_eps))
+        return
+    a = np.ascontiguousarray(w, dtype=np.float64)
+    _dcheck(ctx, _lib.load().unocg_dir_set_uno_weights(ctx, kind, _ptr(a), _lib.DTYPE_F64, spd_eps))
+
+
+def unocg_dir_set_uno_modes(ctx, M: int, w, spd_eps: float = 0.0):
+    a = np.ascontiguousarray(w, dtype=np.float64)
+    _dcheck(ctx, _lib.load().unocg_dir_set_uno_modes(ctx, M, _ptr(a), _lib.DTYPE_F64, spd_eps))
+
+
+def unocg_dir_get_uno_weights(ctx, instance: int, n_modes: int, C_: int) -> np.ndarray:
+    out = np.empty(n_modes * C_, dtype=np.float64)
+    _dcheck(ctx, _lib.load().unocg_dir_get_uno_weights(ctx, instance, _ptr(out)))
+    return out
+
+
+def unocg_dir_solve(ctx, opts: SolveOpts, n_results: int, raise_on_error: bool = True) -> Info:
+    info = Info(n_results)
+    rc = _lib.load().unocg_dir_solve(ctx, C.byref(opts), C.byref(info.c))
+    if raise_on_error:
+        _dcheck(ctx, rc)
+    return info
+
+
+def unocg_dir_solve_async(ctx, opts: SolveOpts):
+    _dcheck(ctx, _lib.load().unocg_dir_solve_async(ctx, C.byref(opts)))
+
+
+def unocg_dir_solve_wait(ctx, n_results: int, raise_on_error: bool = True) -> Info:
+    info = Info(n_results)
+    rc = _lib.load().unocg_dir_solve_wait(ctx, C.byref(info.c))
+    if raise_on_error:
+        _dcheck(ctx, rc)
+    return info
+
+
+def unocg_dir_get_fluctuation(ctx, instance: int, load: int, n_values: int) -> np.ndarray:
+    out = np.empty(n_values, dtype=np.float64)
+    _dcheck(ctx, _lib.load().unocg_dir_get_fluctuation(ctx, instance, load, _ptr(out)))
+    return out
+
+
+def unocg_dir_get_fluctuation_dev(ctx, instance: int, load: int, out_dev, stream=None):
+    _dcheck(ctx, _lib.load().unocg_dir_get_fluctuation_dev(ctx, instance, load, C.c_void_p(out_dev.data_ptr()),
+                                                           _stream(stream)))
+
+
+def unocg_dir_get_effective_tensor(ctx, batch: int, dim: int, n_loads: int) -> np.ndarray:
+    out = np.empty((batch, dim, n_loads), dtype=np.float64)
+    _dcheck(ctx, _lib.load().unocg_dir_get_effective_tensor(ctx, _ptr(out)))
+    return out
+
+
+def unocg_dir_apply_K_dev(ctx, instance: int, p_dev, q_dev, stream=None):
+    _dcheck(ctx, _lib.load().unocg_dir_apply_K_dev(ctx, instance, C.c_void_p(p_dev.data_ptr()),
+                                                   C.c_void_p(q_dev.data_ptr()), _stream(stream)))
+
+
+def unocg_dir_apply_uno_dev(ctx, instance: int, r_dev, s_dev, stream=None):
+    _dcheck(ctx, _lib.load().unocg_dir_apply_uno_dev(ctx, instance, C.c_void_p(r_dev.data_ptr()),
+                                                     C.c_void_p(s_dev.data_ptr()), _stream(stream)))

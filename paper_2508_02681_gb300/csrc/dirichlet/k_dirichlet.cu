@@ -1,0 +1,586 @@
+// Kernels of the Dirichlet-BC solver: the sine-transform passes of the UNO preconditioner
+// (Algorithm 2 with T the DST, Dirichlet row of Table (fnocg-mode-selection-2d)) fused with the
+// CG vector updates of Algorithm 1, the non-periodic K d, the residual evaluations and the
+// post-processing.  Layouts and the two-lines-per-complex-transform scheme: dargs.h.
+//
+// One UNO-CG iteration is six kernels:
+//   k_dpass<DP_MID>    DST axis 2 of r_hat
+//   k_dpass<DP_QMUL>   DST axis 1, s_hat = Q r_hat, gamma = r.s (Parseval), DST axis 1, beta
+//   k_dpass<DP_MID>    DST axis 2
+//   k_dpass<DP_LAST>   DST axis 3, p = s + beta p
+//   k_dku              q = K p, p.q, alpha
+//   k_dpass<DP_FIRST>  r -= alpha q, u += alpha p, ||r||_inf, stopping test, DST axis 3 of r
+#include "../fft.cuh"
+#include "dargs.h"
+
+namespace unocg {
+
+constexpr int kDThreads = 256;
+
+// line addressing of one pass: `lines` lines per block, line l of length M = N_axis - 1
+struct DTile {
+  long long base;   // first element of this (instance, load)
+  int ax, M, lines, W;
+  // axis 3: rows [row0, row0 + lines) of the c M1 M2 rows
+  long long row0, rows;
+  // axes 1, 2: positions i3 in [i30, i30 + W)
+  int i1, i2, comp, i30;
+};
+
+__device__ __forceinline__ DTile dtile(const DGrid& g, int c, int ax, int lines, int bl, int t) {
+  DTile d;
+  d.base = (long long)bl * c * g.nf;
+  d.ax = ax;
+  d.lines = ax == 1 ? c * lines : lines;
+  d.W = lines;
+  d.M = (ax == 3 ? g.n3 : ax == 2 ? g.n2 : g.n1) - 1;
+  d.row0 = 0; d.rows = 0; d.i1 = d.i2 = d.comp = d.i30 = 0;
+  const int nb3 = (g.m3 + lines - 1) / lines;
+  if (ax == 3) {
+    d.row0 = (long long)t * lines;
+    d.rows = (long long)c * g.m1 * g.m2;
+  } else if (ax == 2) {
+    d.i30 = (t % nb3) * lines;
+    const int rest = t / nb3;
+    d.i1 = rest % g.m1;
+    d.comp = rest / g.m1;
+  } else {
+    d.i30 = (t % nb3) * lines;
+    d.i2 = t / nb3;
+  }
+  return d;
+}
+
+// global index of element j of line l, or -1 when the line lies outside the field
+__device__ __forceinline__ long long daddr(const DGrid& g, const DTile& d, int l, int j) {
+  if (d.ax == 3) {
+    const long long row = d.row0 + l;
+    return row < d.rows ? d.base + row * g.m3 + j : -1LL;
+  }
+  const int w = l % d.W, grp = l / d.W;
+  const int i3 = d.i30 + w;
+  if (i3 >= g.m3) return -1LL;
+  if (d.ax == 2) return d.base + (((long long)d.comp * g.m1 + d.i1) * g.m2 + j) * g.m3 + i3;
+  return d.base + (((long long)grp * g.m1 + j) * g.m2 + d.i2) * g.m3 + i3;
+}
+
+// element (l, j) of the loop over a tile: j fastest along axis 3 (contiguous rows), the
+// position fastest along axes 1 and 2 (contiguous i3) -- coalesced either way
+__device__ __forceinline__ void dtile_item(const DTile& d, int idx, int& l, int& j) {
+  if (d.ax == 3) {
+    l = idx / d.M;
+    j = idx - l * d.M;
+  } else {
+    const int w = idx % d.W, rest = idx / d.W;
+    j = rest % d.M;
+    l = (rest / d.M) * d.W + w;
+  }
+}
+
+// store value x of line l at point j (0 <= j < N - 1) into the odd-extended pair buffer
+template <typename T>
+__device__ __forceinline__ void dput(cplx<T>* buf, int P, int N, int l, int j, T x) {
+  T* a = reinterpret_cast<T*>(buf + (long long)(j + 1) * P + (l >> 1)) + (l & 1);
+  T* b = reinterpret_cast<T*>(buf + (long long)(2 * N - 1 - j) * P + (l >> 1)) + (l & 1);
+  *a = x;
+  *b = -x;
+}
+// unnormalized DST coefficient k of line l from the transformed pair buffer
+template <typename T>
+__device__ __forceinline__ T dget(const cplx<T>* buf, int P, int l, int k) {
+  const cplx<T> z = buf[(long long)(k + 1) * P + (l >> 1)];
+  return (l & 1) ? (T)0.5 * z.x : (T)-0.5 * z.y;
+}
+template <typename T>
+__device__ __forceinline__ void dzero_ends(cplx<T>* buf, int P, int N) {
+  for (int m = threadIdx.x; m < P; m += blockDim.x) {
+    buf[m] = mk<T>((T)0, (T)0);
+    buf[(long long)N * P + m] = mk<T>((T)0, (T)0);
+  }
+}
+
+template <typename T> __device__ __forceinline__ T dabs(T x) { return x < (T)0 ? -x : x; }
+
+template <typename T, int CC>
+__device__ __forceinline__ void qmul(const T* __restrict__ q, const T* x, T* y) {
+  if (CC == 1) {
+    y[0] = q[0] * x[0];
+  } else {
+    // paper order v1 = Q11, v2 = Q22, v3 = Q12, v4 = Q33, v5 = Q23, v6 = Q13
+    y[0] = q[0] * x[0] + q[2] * x[1] + q[5] * x[2];
+    y[1] = q[2] * x[0] + q[1] * x[1] + q[4] * x[2];
+    y[2] = q[5] * x[0] + q[4] * x[1] + q[3] * x[2];
+  }
+}
+
+// ============================================================================ transform passes
+template <typename T, int MODE, int CC>
+__global__ void __launch_bounds__(kDThreads) k_dpass(DPassArgs<T> a) {
+  using C = cplx<T>;
+  constexpr int AX = (MODE == DP_FIRST || MODE == DP_LAST) ? 3 : (MODE == DP_MID ? 2 : 1);
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ double red_sh[32];
+  const DGrid& g = a.g;
+  const int bl = blockIdx.y;
+  const int N = AX == 3 ? g.n3 : (AX == 2 ? g.n2 : g.n1);
+  const DTile d = dtile(g, CC, AX, a.lines, bl, blockIdx.x);
+  const int P = d.lines >> 1;
+  C* A = reinterpret_cast<C*>(dsm);
+  C* B = A + (long long)2 * N * P;
+  C* tw = B + (long long)2 * N * P;
+
+  bool active = true;
+  if (!a.standalone) {
+    const CgScal& s = a.sc[bl];
+    active = !s.done && (MODE != DP_FIRST || !a.after_replace || s.need_replace);
+  }
+  double bval = 0.0;  // rmax (DP_FIRST) or gamma partial (DP_QMUL)
+  if (active) {
+    load_tw<T>(tw, a.t.tw[AX - 1], 2 * N);
+    dzero_ends<T>(A, P, N);
+    const int total = d.lines * d.M;
+    if (MODE == DP_FIRST && !a.standalone) {
+      const CgScal& s = a.sc[bl];
+      const T alpha = (T)s.alpha;
+      const bool upd = !a.after_replace && s.started;
+      T rm = (T)0;
+      for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        int l, j;
+        dtile_item(d, idx, l, j);
+        const long long ga = daddr(g, d, l, j);
+        T x = (T)0;
+        if (ga >= 0) {
+          x = a.r[ga];
+          if (upd) {
+            x -= alpha * a.q[ga];
+            a.r[ga] = x;
+            a.u64[ga] += s.alpha * (double)a.p[ga];
+          }
+          rm = rm > dabs(x) ? rm : dabs(x);
+        }
+        dput<T>(A, P, N, l, j, x);
+      }
+      bval = (double)rm;
+    } else {
+      const T* src = (MODE == DP_FIRST && a.standalone) ? a.src : a.hat;
+      for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        int l, j;
+        dtile_item(d, idx, l, j);
+        const long long ga = daddr(g, d, l, j);
+        dput<T>(A, P, N, l, j, ga >= 0 ? src[ga] : (T)0);
+      }
+    }
+    __syncthreads();
+    C* res = fft_lines<T, -1>(A, B, P, 1, P, a.t.p[AX - 1], tw);
+    if (MODE == DP_QMUL) {
+      // block multiply on the modes (k1, k2 = i2, k3 = i3) of this tile, then the second DST
+      C* oth = res == A ? B : A;
+      dzero_ends<T>(oth, P, N);
+      DotAcc<T> acc;
+      const int W = d.W;
+      for (int idx = threadIdx.x; idx < W * d.M; idx += blockDim.x) {
+        const int w = idx % W, k = idx / W;
+        T x[CC], y[CC];
+#pragma unroll
+        for (int i = 0; i < CC; ++i) x[i] = dget<T>(res, P, i * W + w, k);
+        const int i3 = d.i30 + w;
+        if (i3 < g.m3) {
+          const long long mode = ((long long)k * g.m2 + d.i2) * g.m3 + i3;
+          const T* qp = reinterpret_cast<const T*>(a.Q) + (long long)(bl / a.L) * a.q_inst_stride +
+                        mode * (CC == 1 ? 1 : 6);
+          qmul<T, CC>(qp, x, y);
+#pragma unroll
+          for (int i = 0; i < CC; ++i) acc.add_prod(x[i], y[i]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < CC; ++i) y[i] = (T)0;
+        }
+#pragma unroll
+        for (int i = 0; i < CC; ++i) dput<T>(oth, P, N, i * W + w, k, y[i]);
+      }
+      bval = block_sum_acc(acc, red_sh);
+      __syncthreads();
+      res = fft_lines<T, -1>(oth, res, P, 1, P, a.t.p[AX - 1], tw);
+    }
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+      int l, j;
+      dtile_item(d, idx, l, j);
+      const long long ga = daddr(g, d, l, j);
+      if (ga < 0) continue;
+      const T x = dget<T>(res, P, l, j);
+      if (MODE == DP_LAST) {
+        if (a.standalone) a.out[ga] = x;
+        else a.p[ga] = x + (T)a.sc[bl].beta * a.p[ga];
+      } else {
+        a.hat[ga] = x;
+      }
+    }
+  }
+  if (a.standalone) return;
+  if (MODE == DP_FIRST) {
+    const double bm = block_max(active ? bval : 0.0, red_sh);
+    if (threadIdx.x == 0 && active) atomic_max_nonneg(&a.sc[bl].rmax_bits, bm);
+    if (last_block(a.red.ticket)) {
+      residual_decision(a.sc, a.BL, a.ctl, a.after_replace);
+      if (threadIdx.x == 0) *a.red.ticket = 0u;
+    }
+  } else if (MODE == DP_QMUL) {
+    if (threadIdx.x == 0) a.red.part[(long long)bl * gridDim.x + blockIdx.x] = bval;
+    if (last_block(a.red.ticket)) {
+      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      for (int q = warp; q < a.BL; q += blockDim.x / 32) {
+        if (a.sc[q].done) continue;
+        const double gam = warp_sum_partials(a.red.part + (long long)q * gridDim.x, gridDim.x, 1);
+        if (lane == 0) direction_update(a.sc[q], gam, 0.0, 0);
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) *a.red.ticket = 0u;
+    }
+  }
+}
+
+// ============================================================================ K p
+template <typename T, int CC>
+__global__ void __launch_bounds__(kDThreads) k_dku(DKuArgs<T> a) {
+  __shared__ T mt[2 * 256];
+  __shared__ double red_sh[32];
+  const DGrid& g = a.g;
+  const int bl = blockIdx.y;
+  const int b = bl / a.L;
+  load_material<T>(mt, a.mat, b);
+  __syncthreads();
+  const bool active = a.standalone || !a.sc[bl].done;
+  DotAcc<T> acc;
+  if (active) {
+    const uint8_t* ph = a.phase + (long long)b * g.ne;
+    const T* p = a.p + (long long)bl * CC * g.nf;
+    T* q = a.q + (long long)bl * CC * g.nf;
+    for (long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x; node < g.nf;
+         node += (long long)gridDim.x * blockDim.x) {
+      const int j3 = (int)(node % g.m3);
+      const long long r = node / g.m3;
+      const int j2 = (int)(r % g.m2), j1 = (int)(r / g.m2);
+      T out[CC];
+      dnode_Ku<T, CC>(p, ph, mt, g, j1, j2, j3, out);
+#pragma unroll
+      for (int i = 0; i < CC; ++i) {
+        q[i * g.nf + node] = out[i];
+        acc.add_prod(p[i * g.nf + node], out[i]);
+      }
+    }
+  }
+  if (a.standalone) return;
+  const double bs = block_sum_acc(acc, red_sh);
+  if (threadIdx.x == 0) a.red.part[(long long)bl * gridDim.x + blockIdx.x] = bs;
+  if (last_block(a.red.ticket)) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int q = warp; q < a.BL; q += blockDim.x / 32) {
+      if (a.sc[q].done) continue;
+      const double sum = warp_sum_partials(a.red.part + (long long)q * gridDim.x, gridDim.x, 1);
+      if (lane == 0) step_update(a.sc[q], sum);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *a.red.ticket = 0u;
+  }
+}
+
+// ============================================================================ f - K u (FP64)
+template <typename T, int CC>
+__global__ void __launch_bounds__(kDThreads) k_dres(DResArgs<T> a) {
+  __shared__ double mt[2 * 256];
+  __shared__ double red_sh[32];
+  const DGrid& g = a.g;
+  const int bl = blockIdx.y;
+  const int b = bl / a.L;
+  load_material<double>(mt, a.mat, b);
+  __syncthreads();
+  if (a.only_pending && !a.sc[bl].need_replace) return;
+  const uint8_t* ph = a.phase + (long long)b * g.ne;
+  const double* u = a.u64 + (long long)bl * CC * g.nf;
+  const double* f = a.f64 + (long long)bl * CC * g.nf;
+  double lmax = 0.0;
+  for (long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x; node < g.nf;
+       node += (long long)gridDim.x * blockDim.x) {
+    const int j3 = (int)(node % g.m3);
+    const long long r = node / g.m3;
+    const int j2 = (int)(r % g.m2), j1 = (int)(r / g.m2);
+    double ku[CC];
+    dnode_Ku<double, CC>(u, ph, mt, g, j1, j2, j3, ku);
+#pragma unroll
+    for (int i = 0; i < CC; ++i) {
+      const double rr = f[i * g.nf + node] - ku[i];
+      lmax = fmax(lmax, fabs(rr));
+      if (a.r) a.r[(long long)bl * CC * g.nf + i * g.nf + node] = (T)rr;
+    }
+  }
+  const double bm = block_max(lmax, red_sh);
+  if (threadIdx.x == 0 && !a.r) atomic_max_nonneg(&a.sc[bl].tmax_bits, bm);
+}
+
+// ============================================================================ Jacobi / plain CG
+// part 0: r -= alpha q, u += alpha p, ||r||_inf, stopping test
+// part 1: gamma = r . z with z = D^-1 r (or r), beta
+// part 2: p = z + beta p
+template <typename T, int PART>
+__global__ void __launch_bounds__(kDThreads) k_djac(DJacArgs<T> a) {
+  __shared__ double red_sh[32];
+  const DGrid& g = a.g;
+  const int bl = blockIdx.y;
+  const CgScal& s = a.sc[bl];
+  const bool active = !s.done && (PART != 0 || !a.after_replace || s.need_replace);
+  const long long n = (long long)a.c * g.nf;
+  const long long off = (long long)bl * n;
+  const T* idg = a.invdiag ? a.invdiag + (long long)(bl / a.L) * n : nullptr;
+  double bval = 0.0;
+  DotAcc<T> acc;
+  T rm = (T)0;
+  if (active) {
+    const T alpha = (T)s.alpha, beta = (T)s.beta;
+    const bool upd = !a.after_replace && s.started;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+      if (PART == 0) {
+        T x = a.r[off + i];
+        if (upd) {
+          x -= alpha * a.q[off + i];
+          a.r[off + i] = x;
+          a.u64[off + i] += s.alpha * (double)a.p[off + i];
+        }
+        rm = rm > dabs(x) ? rm : dabs(x);
+      } else {
+        const T x = a.r[off + i];
+        const T z = idg ? idg[i] * x : x;
+        if (PART == 1) acc.add_prod(x, z);
+        else a.p[off + i] = z + beta * a.p[off + i];
+      }
+    }
+  }
+  if (PART == 0) {
+    const double bm = block_max(active ? (double)rm : 0.0, red_sh);
+    if (threadIdx.x == 0 && active) atomic_max_nonneg(&a.sc[bl].rmax_bits, bm);
+    if (last_block(a.red.ticket)) {
+      residual_decision(a.sc, a.BL, a.ctl, a.after_replace);
+      if (threadIdx.x == 0) *a.red.ticket = 0u;
+    }
+  } else if (PART == 1) {
+    bval = block_sum_acc(acc, red_sh);
+    if (threadIdx.x == 0) a.red.part[(long long)bl * gridDim.x + blockIdx.x] = bval;
+    if (last_block(a.red.ticket)) {
+      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      for (int q = warp; q < a.BL; q += blockDim.x / 32) {
+        if (a.sc[q].done) continue;
+        const double gam = warp_sum_partials(a.red.part + (long long)q * gridDim.x, gridDim.x, 1);
+        if (lane == 0) direction_update(a.sc[q], gam, 0.0, 0);
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) *a.red.ticket = 0u;
+    }
+  }
+}
+
+// ============================================================================ set-up, post
+template <int CC>
+__global__ void __launch_bounds__(kDThreads) k_dinit(DInitArgs a) {
+  __shared__ double mt[2 * 256];
+  const DGrid& g = a.g;
+  const int bl = blockIdx.y;
+  const int b = bl / a.L, l = bl % a.L;
+  load_material<double>(mt, a.mat, b);
+  __syncthreads();
+  const uint8_t* ph = a.phase + (long long)b * g.ne;
+  for (long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x; node < g.nf;
+       node += (long long)gridDim.x * blockDim.x) {
+    const int j3 = (int)(node % g.m3);
+    const long long r = node / g.m3;
+    const int j2 = (int)(r % g.m2), j1 = (int)(r / g.m2);
+    double f[CC];
+    dnode_rhs<CC>(ph, mt, g, j1, j2, j3, a.loads + l * (CC == 1 ? 3 : 6), f);
+    const long long o = (long long)bl * CC * g.nf + node;
+#pragma unroll
+    for (int i = 0; i < CC; ++i) {
+      const long long k = o + i * g.nf;
+      a.f64[k] = f[i];
+      a.u64[k] = 0.0;
+      if (a.fp64) {
+        ((double*)a.r)[k] = f[i];
+        ((double*)a.p)[k] = 0.0;
+        ((double*)a.q)[k] = 0.0;
+      } else {
+        ((float*)a.r)[k] = (float)f[i];
+        ((float*)a.p)[k] = 0.f;
+        ((float*)a.q)[k] = 0.f;
+      }
+    }
+  }
+}
+
+template <int CC>
+__global__ void __launch_bounds__(kDThreads) k_ddiag(DDiagArgs a) {
+  __shared__ double mt[2 * 256];
+  const DGrid& g = a.g;
+  const int b = blockIdx.y;
+  load_material<double>(mt, a.mat, b);
+  __syncthreads();
+  const uint8_t* ph = a.phase + (long long)b * g.ne;
+  for (long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x; node < g.nf;
+       node += (long long)gridDim.x * blockDim.x) {
+    const int j3 = (int)(node % g.m3);
+    const long long r = node / g.m3;
+    const int j2 = (int)(r % g.m2), j1 = (int)(r / g.m2);
+    double dg[CC];
+    dnode_diag<CC>(ph, mt, g, j1, j2, j3, dg);
+#pragma unroll
+    for (int i = 0; i < CC; ++i) {
+      const long long k = (long long)b * CC * g.nf + i * g.nf + node;
+      if (a.fp64) ((double*)a.invdiag)[k] = 1.0 / dg[i];
+      else ((float*)a.invdiag)[k] = (float)(1.0 / dg[i]);
+    }
+  }
+}
+
+// averaged flux / stress: out[b][i][l] += sum over voxels / n_voxels
+template <int CC>
+__global__ void __launch_bounds__(kDThreads) k_davg(DAvgArgs a) {
+  constexpr int DIM = CC == 1 ? 3 : 6;
+  __shared__ double mt[2 * 256];
+  __shared__ double red_sh[32];
+  const DGrid& g = a.g;
+  const int b = blockIdx.y / a.L, l = blockIdx.y % a.L;
+  load_material<double>(mt, a.mat, b);
+  __syncthreads();
+  const uint8_t* ph = a.phase + (long long)b * g.ne;
+  const double* u = a.u64 + (long long)(b * a.L + l) * CC * g.nf;
+  double acc[DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) acc[i] = 0.0;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < g.ne; e += (long long)gridDim.x * blockDim.x) {
+    const int e3 = (int)(e % g.n3);
+    const long long r = e / g.n3;
+    const int e2 = (int)(r % g.n2), e1 = (int)(r / g.n2);
+    double sig[DIM];
+    delement_mean_flux<CC>(u, mt, ph[e], g, e1, e2, e3, a.loads + l * DIM, sig);
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) acc[i] += sig[i];
+  }
+  for (int i = 0; i < DIM; ++i) {
+    const double s = block_sum(acc[i], red_sh);
+    if (threadIdx.x == 0) atomicAdd(a.out + ((long long)b * DIM + i) * a.L + l, s / (double)g.ne);
+  }
+}
+
+// ============================================================================ launchers
+size_t dst_smem_bytes(int N, int lines, int elem_bytes) {
+  // two pair buffers of 2N x lines/2 complex values and the twiddle table
+  return (size_t)elem_bytes * 2 * ((size_t)2 * 2 * N * (lines / 2) + 2 * N);
+}
+
+// largest even line count <= cap whose buffers fit 96 KB (at least 2)
+int dst_lines_for(int N, int elem_bytes, int cap) {
+  int l = cap & ~1;
+  while (l > 2 && dst_smem_bytes(N, l, elem_bytes) > 96 * 1024) l -= 2;
+  return l < 2 ? 2 : l;
+}
+
+int dpass_blocks(const DGrid& g, int c, int mode, int lines) {
+  const int nb3 = (g.m3 + lines - 1) / lines;
+  if (mode == DP_FIRST || mode == DP_LAST) {
+    const long long rows = (long long)c * g.m1 * g.m2;
+    return (int)((rows + lines - 1) / lines);
+  }
+  if (mode == DP_MID) return c * g.m1 * nb3;
+  return g.m2 * nb3;
+}
+
+int dku_blocks(const DGrid& g) {
+  const long long b = (g.nf + kDThreads - 1) / kDThreads;
+  return (int)(b < 1024 ? b : 1024);
+}
+int djac_blocks(const DGrid& g) { return dku_blocks(g); }
+
+template <typename T, int MODE, int CC>
+static cudaError_t dpass_go(const DPassArgs<T>& a, cudaStream_t s) {
+  const int ax = (MODE == DP_FIRST || MODE == DP_LAST) ? 3 : (MODE == DP_MID ? 2 : 1);
+  const int N = ax == 3 ? a.g.n3 : (ax == 2 ? a.g.n2 : a.g.n1);
+  const int lines = ax == 1 ? CC * a.lines : a.lines;
+  const size_t smem = dst_smem_bytes(N, lines, sizeof(T));
+  cudaError_t e = cudaFuncSetAttribute(k_dpass<T, MODE, CC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(dpass_blocks(a.g, CC, MODE, a.lines), a.BL);
+  k_dpass<T, MODE, CC><<<grid, kDThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_dpass(const DPassArgs<T>& a, int mode, cudaStream_t s) {
+  if (a.c == 1) {
+    switch (mode) {
+      case DP_FIRST: return dpass_go<T, DP_FIRST, 1>(a, s);
+      case DP_MID: return dpass_go<T, DP_MID, 1>(a, s);
+      case DP_QMUL: return dpass_go<T, DP_QMUL, 1>(a, s);
+      default: return dpass_go<T, DP_LAST, 1>(a, s);
+    }
+  }
+  switch (mode) {
+    case DP_FIRST: return dpass_go<T, DP_FIRST, 3>(a, s);
+    case DP_MID: return dpass_go<T, DP_MID, 3>(a, s);
+    case DP_QMUL: return dpass_go<T, DP_QMUL, 3>(a, s);
+    default: return dpass_go<T, DP_LAST, 3>(a, s);
+  }
+}
+
+template <typename T>
+cudaError_t launch_dku(const DKuArgs<T>& a, cudaStream_t s) {
+  dim3 grid(dku_blocks(a.g), a.BL);
+  if (a.c == 1) k_dku<T, 1><<<grid, kDThreads, 0, s>>>(a);
+  else k_dku<T, 3><<<grid, kDThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_dres(const DResArgs<T>& a, cudaStream_t s) {
+  dim3 grid(dku_blocks(a.g), a.BL);
+  if (a.c == 1) k_dres<T, 1><<<grid, kDThreads, 0, s>>>(a);
+  else k_dres<T, 3><<<grid, kDThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_djac(const DJacArgs<T>& a, int part, cudaStream_t s) {
+  dim3 grid(djac_blocks(a.g), a.BL);
+  if (part == 0) k_djac<T, 0><<<grid, kDThreads, 0, s>>>(a);
+  else if (part == 1) k_djac<T, 1><<<grid, kDThreads, 0, s>>>(a);
+  else k_djac<T, 2><<<grid, kDThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dinit(const DInitArgs& a, int BL, cudaStream_t s) {
+  dim3 grid(dku_blocks(a.g), BL);
+  if (a.c == 1) k_dinit<1><<<grid, kDThreads, 0, s>>>(a);
+  else k_dinit<3><<<grid, kDThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ddiag(const DDiagArgs& a, int B, cudaStream_t s) {
+  dim3 grid(dku_blocks(a.g), B);
+  if (a.c == 1) k_ddiag<1><<<grid, kDThreads, 0, s>>>(a);
+  else k_ddiag<3><<<grid, kDThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_davg(const DAvgArgs& a, int B, cudaStream_t s) {
+  const long long nb = (a.g.ne + kDThreads - 1) / kDThreads;
+  dim3 grid((int)(nb < 512 ? nb : 512), B * a.L);
+  if (a.c == 1) k_davg<1><<<grid, kDThreads, 0, s>>>(a);
+  else k_davg<3><<<grid, kDThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_dpass<double>(const DPassArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_dpass<float>(const DPassArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_dku<double>(const DKuArgs<double>&, cudaStream_t);
+template cudaError_t launch_dku<float>(const DKuArgs<float>&, cudaStream_t);
+template cudaError_t launch_dres<double>(const DResArgs<double>&, cudaStream_t);
+template cudaError_t launch_dres<float>(const DResArgs<float>&, cudaStream_t);
+template cudaError_t launch_djac<double>(const DJacArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_djac<float>(const DJacArgs<float>&, int, cudaStream_t);
+
+}  // namespace unocg

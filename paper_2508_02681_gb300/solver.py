@@ -69,6 +69,67 @@ class Homogenization:
         return api.unocg_get_sensitivity(self.ctx, self.batch, n_props, self.n_loads)
 
 
+
+class DirichletHomogenization:
+    """One context of the Dirichlet problem (fluctuation zero on the boundary, sine transform):
+    ``batch`` instances of an ``n1 x n2 x n3`` voxel grid with ``(n1-1)(n2-1)(n3-1)`` free nodes."""
+
+    def __init__(self, physics: int, shape, batch: int = 1, L0: float = 1.0):
+        self.physics = physics
+        self.c = 1 if physics == _lib.THERMAL else 3
+        self.dim = 3 if physics == _lib.THERMAL else 6
+        self.shape = tuple(int(s) for s in shape)
+        self.free_shape = tuple(s - 1 for s in self.shape)
+        self.nf = int(np.prod(self.free_shape))
+        self.batch = batch
+        self.ctx = api.unocg_dir_create(physics, batch, *self.shape, L0)
+        self.n_loads = 0
+
+    def close(self):
+        if self.ctx is not None:
+            api.unocg_dir_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_microstructure(self, phase, n_phases: int):
+        api.unocg_dir_set_microstructure(self.ctx, phase, n_phases)
+
+    def set_phase_properties(self, props):
+        api.unocg_dir_set_phase_properties(self.ctx, props)
+
+    def set_macro_load(self, loads):
+        loads = np.atleast_2d(np.asarray(loads, dtype=np.float64))
+        api.unocg_dir_set_macro_load(self.ctx, loads)
+        self.n_loads = loads.shape[0]
+
+    def set_uno_weights(self, kind=_lib.W_REFERENCE_MEDIUM, w=None, spd_eps: float = 0.0):
+        api.unocg_dir_set_uno_weights(self.ctx, kind, w, spd_eps)
+
+    def set_uno_modes(self, M: int, w, spd_eps: float = 0.0):
+        """Bypass ``w[0]`` plus ``w[1 + i]`` on the i-th mode of [0, 2M]^3."""
+        api.unocg_dir_set_uno_modes(self.ctx, M, w, spd_eps)
+
+    def uno_weights(self, instance: int = 0) -> np.ndarray:
+        C_ = 1 if self.c == 1 else 6
+        return api.unocg_dir_get_uno_weights(self.ctx, instance, self.nf, C_).reshape(self.free_shape + (C_,))
+
+    def solve(self, raise_on_error: bool = True, **opts) -> api.Info:
+        opts.setdefault("flexible", 0)
+        return api.unocg_dir_solve(self.ctx, api.make_opts(**opts), self.batch * self.n_loads, raise_on_error)
+
+    def fluctuation(self, instance: int = 0, load: int = 0) -> np.ndarray:
+        """Fluctuation on the free nodes, interleaved ``[nf * c]``."""
+        return api.unocg_dir_get_fluctuation(self.ctx, instance, load, self.nf * self.c)
+
+    def effective_tensor(self) -> np.ndarray:
+        return api.unocg_dir_get_effective_tensor(self.ctx, self.batch, self.dim, self.n_loads)
+
+
 class UnevenBatch:
     """Many instances of possibly different grid sizes (the serving-style batch): the instances
     of one size share a batched context (per-(instance, load) convergence masks), and the

@@ -159,3 +159,22 @@ def test_homogeneous_returns_its_own_tensor():
         out = dr.solve(phase, props, physics, loads, tol=1e-10)
         C = dr.effective_tensor(phase, props, physics, out["u"], loads)
         assert np.max(np.abs(C - fem.material_matrix(physics, props[0]))) < 1e-13
+
+
+def test_modes_layout_counts_and_bypass():
+    # Table (fnocg-mode-selection-2d), Dirichlet row: (2M+1)^d learned modes, no conjugates;
+    # off the mode set Q is the bypass, on it bypass plus mode block
+    from oracle import uno
+    shape = (8, 9, 10)
+    for c in (1, 3):
+        M = 2
+        modes = dr.mode_list(M)
+        assert len(modes) == (2 * M + 1) ** 3 and len(set(modes)) == len(modes)
+        rng = np.random.default_rng(c)
+        w = rng.standard_normal((1 + len(modes), uno.n_unique(c)))
+        Q = dr.modes_Q(w, M, shape, c)
+        W0 = uno.psi(w[0], c)
+        assert np.max(np.abs(Q[5:, :, :] - W0)) == 0.0
+        k = modes[17]
+        assert np.max(np.abs(Q[k] - W0 - uno.psi(w[18], c))) < 1e-14
+        assert np.all(np.linalg.eigvalsh(Q.reshape(-1, c, c)) > -1e-12)
