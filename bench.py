@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the uneven-batch measurement")
     ap.add_argument("--profile-only", action="store_true", help="a few solves, for ncu launch lists")
+    ap.add_argument("--bc", default="periodic", choices=["periodic", "dirichlet"],
+                    help="with --profile-only: boundary conditions of the profiled solves")
+    ap.add_argument("--no-dirichlet", action="store_true", help="skip the Dirichlet-BC measurement")
     ap.add_argument("--no-graph", action="store_true",
                     help="profile-only: host-driven loop (kernels inside conditional graph bodies are not visible to ncu)")
     return ap.parse_args()
@@ -136,7 +139,8 @@ def algorithmic_bytes(n, nh, c, BL, B, C_q, fb, qb):
 
 def recorded_traffic(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu capture, or None when the device
-    sources (every file of csrc/ but the host-side api.cu) changed since that capture."""
+    sources of the periodic path (every file directly in csrc/ but the host-side api.cu)
+    changed since that capture."""
     import glob
     import hashlib
     p = os.path.join(ROOT, "profiles", "uno_cg_thermal64_mixed_traffic.json")
@@ -145,7 +149,9 @@ def recorded_traffic(kernel):
     d = json.load(open(p))
     m = hashlib.sha256()
     for f in sorted(glob.glob(os.path.join(ROOT, "paper_2508_02681_gb300", "csrc", "*"))):
-        if os.path.basename(f) == "api.cu":  # host-side entry points only
+        # host-side entry points only; the Dirichlet-BC kernels (csrc/dirichlet/) are separate
+        # translation units that none of the periodic kernels include
+        if os.path.basename(f) == "api.cu" or not os.path.isfile(f):
             continue
         m.update(open(f, "rb").read())
     if m.hexdigest() != d.get("csrc_sha256"):
@@ -228,6 +234,50 @@ def batched_uneven(n_inst: int = 256, reps: int = 3):
             "contexts": len(sizes), "input_generation_s": t_gen}
 
 
+def dirichlet_solver(w, stream):
+    """The 64^3 thermal workload with Dirichlet BC (fluctuation zero on the boundary, sine
+    transform in the UNO preconditioner)."""
+    from paper_2508_02681_gb300 import _lib, api
+    from paper_2508_02681_gb300.solver import DirichletHomogenization
+    h = DirichletHomogenization(_lib.THERMAL, w["phase"].shape)
+    api.unocg_dir_set_stream(h.ctx, stream)
+    h.set_microstructure(w["phase"], 2)
+    h.set_phase_properties(w["props"])
+    h.set_macro_load(w["loads"])
+    h.set_uno_weights(_lib.W_REFERENCE_MEDIUM)
+    return h
+
+
+def dirichlet(w, stream, steps: int = 5):
+    """Time-to-tolerance of the same workload with Dirichlet BC: mixed and FP64 UNO-CG (sine
+    transform) and FP64 Jac-CG, CUDA events on the solve stream, L2 flushed before each solve."""
+    import torch
+    from paper_2508_02681_gb300 import _lib, api
+    h = dirichlet_solver(w, stream)
+    L = w["loads"].shape[0]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    out = {"bc": "Dirichlet (fluctuation zero on the boundary), sine-transform UNO"}
+    for name, pc, prec in (("mixed_uno", _lib.PRECOND_UNO, _lib.MIXED), ("fp64_uno", _lib.PRECOND_UNO, _lib.FP64),
+                           ("fp64_jacobi", _lib.PRECOND_JACOBI, _lib.FP64)):
+        opts = api.make_opts(tol=TOL, max_iter=20000, precond=pc, precision=prec, flexible=0)
+        api.unocg_dir_solve_async(h.ctx, opts)
+        api.unocg_dir_solve_wait(h.ctx, L)
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            api.unocg_dir_solve_async(h.ctx, opts)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        info = api.unocg_dir_solve_wait(h.ctx, L)
+        out[name] = {"ms": float(np.mean(ms)), "iterations": int(info.c.max_iters),
+                     "true_rel_res": float(np.max(info.true_rel_res))}
+    h.close()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -285,6 +335,18 @@ def main():
         ms = [a.elapsed_time(b) for a, b in ev]
         return float(np.mean(ms)), info
 
+    if args.profile_only and args.bc == "dirichlet":
+        h.close()
+        hd = dirichlet_solver(w, stream)
+        opts = api.make_opts(tol=TOL, max_iter=2000, precond=_lib.PRECOND_UNO, precision=_lib.MIXED, flexible=0,
+                             use_graph=0 if args.no_graph else 1)
+        for _ in range(2):
+            api.unocg_dir_solve_async(hd.ctx, opts)
+            api.unocg_dir_solve_wait(hd.ctx, L)
+        torch.cuda.synchronize()
+        hd.close()
+        print("profile-only run done")
+        return 0
     if args.profile_only:
         opts = variants["mixed_uno"]
         if args.no_graph:
@@ -380,6 +442,8 @@ def main():
     h.close()
     if rank == 0 and world == 1 and not args.no_batch and not args.profile_only:
         line["batched_uneven"] = batched_uneven()
+    if rank == 0 and world == 1 and not args.no_dirichlet:
+        line["dirichlet"] = dirichlet(w, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import homogenize as hz
         t0 = time.perf_counter()

@@ -9,6 +9,7 @@
 #include <string>
 #include <vector>
 
+#include "../element.cuh"
 #include "dargs.h"
 #include "unocg.h"
 
@@ -86,7 +87,9 @@ struct unocg_dir {
   unsigned int* tickets = nullptr;
   int* flags = nullptr;
   double* ceff = nullptr;
+  double *stage_a = nullptr, *stage_b = nullptr, *stage_f = nullptr;  // operator-level I/O
   int lines3[2], w2[2], w1[2];  // [0] FP64, [1] FP32
+  bool plane[2];                // axes 3 and 2 in one plane pass (the plane fits a block)
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   DKey key;
@@ -197,7 +200,7 @@ void reference_weights(const DGrid& g, int c, const double* mt, double* out) {
       for (int i = 0; i < c; ++i)
         for (int k = 0; k < c; ++k) {
           const double v = c == 1 ? mt[0] * Klap(o, ob) : mt[0] * Klam(o, i, ob, k) + mt[1] * Kmu(o, i, ob, k);
-          sten[d1 + 1][d2 + 1][d3 + 1][i][k] += v * g.h;
+          sten[d1 + 1][d2 + 1][d3 + 1][i][k] += v * g.pg.h;
         }
     }
   const int m[3] = {g.m1, g.m2, g.m3};
@@ -280,7 +283,7 @@ int finish_weights(unocg_dir* d, double spd_eps) {
 
 int ensure_workspace(unocg_dir* d, int precision, int precond) {
   const int BL = d->B * d->L;
-  const size_t n = (size_t)BL * d->c * d->g.nf;
+  const size_t n = (size_t)BL * d->c * d->g.ne;
   const bool fp64 = precision == UNOCG_FP64;
   DFields& f = fp64 ? d->f64f : d->f32f;
   const size_t eb = fp64 ? 8 : 4;
@@ -291,8 +294,8 @@ int ensure_workspace(unocg_dir* d, int precision, int precond) {
   if (!f.q) DCK(cudaMalloc(&f.q, n * eb));
   if (precond == UNOCG_PRECOND_UNO && !f.hat) DCK(cudaMalloc(&f.hat, n * eb));
   if (precond == UNOCG_PRECOND_JACOBI && !f.invdiag)
-    DCK(cudaMalloc(&f.invdiag, (size_t)d->B * d->c * d->g.nf * eb));
-  size_t need = (size_t)BL * std::max({(size_t)dku_blocks(d->g), (size_t)djac_blocks(d->g),
+    DCK(cudaMalloc(&f.invdiag, (size_t)d->B * d->c * d->g.ne * eb));
+  size_t need = (size_t)BL * std::max({(size_t)dku_blocks(d->g, d->c), (size_t)djac_blocks(d->g),
                                        (size_t)dpass_blocks(d->g, d->c, DP_QMUL, std::min(d->w1[0], d->w1[1]))});
   if (d->part_len < need) {
     cudaFree(d->part);
@@ -343,7 +346,10 @@ DJacArgs<T> jac_args(unocg_dir* d, const DPlan& pl, const LoopCtl& ctl, int part
 
 template <typename T>
 cudaError_t enq_check(unocg_dir* d, cudaStream_t s, const DPlan& pl, const LoopCtl& ctl, int after_replace) {
-  if (pl.o.precond == UNOCG_PRECOND_UNO) return launch_dpass<T>(pass_args<T>(d, DP_FIRST, ctl, after_replace), DP_FIRST, s);
+  if (pl.o.precond == UNOCG_PRECOND_UNO) {
+    if (d->plane[pidx<T>()]) return launch_dplane<T>(pass_args<T>(d, DP_FIRST, ctl, after_replace), 1, s);
+    return launch_dpass<T>(pass_args<T>(d, DP_FIRST, ctl, after_replace), DP_FIRST, s);
+  }
   return launch_djac<T>(jac_args<T>(d, pl, ctl, 0, after_replace), 0, s);
 }
 
@@ -381,7 +387,10 @@ cudaError_t enq_ku(unocg_dir* d, cudaStream_t s) {
 template <typename T>
 cudaError_t enq_body(unocg_dir* d, cudaStream_t s, const DPlan& pl, const LoopCtl& ctl) {
   cudaError_t e = cudaSuccess;
-  if (pl.o.precond == UNOCG_PRECOND_UNO) {
+  if (pl.o.precond == UNOCG_PRECOND_UNO && d->plane[pidx<T>()]) {
+    e = launch_dpass<T>(pass_args<T>(d, DP_QMUL, ctl, 0), DP_QMUL, s);
+    if (e == cudaSuccess) e = launch_dplane<T>(pass_args<T>(d, DP_LAST, ctl, 0), 0, s);
+  } else if (pl.o.precond == UNOCG_PRECOND_UNO) {
     e = launch_dpass<T>(pass_args<T>(d, DP_MID, ctl, 0), DP_MID, s);
     if (e == cudaSuccess) e = launch_dpass<T>(pass_args<T>(d, DP_QMUL, ctl, 0), DP_QMUL, s);
     if (e == cudaSuccess) e = launch_dpass<T>(pass_args<T>(d, DP_MID, ctl, 0), DP_MID, s);
@@ -519,6 +528,38 @@ int build_graph(unocg_dir* d, const DPlan& pl) {
   return UNOCG_OK;
 }
 
+// Host-driven loop (use_graph = 0; profiling tools see every launch): one residual check per
+// iteration read back by the host.
+template <typename T>
+int run_host_loop(unocg_dir* d, const DPlan& pl) {
+  cudaStream_t s = d->stream;
+  LoopCtl ctl{};
+  ctl.tol = pl.o.tol; ctl.max_iter = pl.o.max_iter; ctl.mixed = pl.mixed;
+  ctl.replace_every = pl.o.replace_every; ctl.replace_drop = pl.o.replace_drop; ctl.flexible = 0;
+  ctl.active_flag = d->flags; ctl.replace_flag = d->flags + 1;
+  ctl.counters = d->flags + 2;
+  DCK(enq_pre<T>(d, s, pl, ctl));
+  int hf[2] = {0, 0};
+  const long long cap = 4LL * pl.o.max_iter + 16;
+  for (long long it = 0; it < cap; ++it) {
+    DCK(cudaMemcpyAsync(hf, d->flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    DCK(cudaStreamSynchronize(s));
+    if (!hf[0]) break;
+    DCK(enq_body<T>(d, s, pl, ctl));
+    if (pl.mixed) {
+      DCK(cudaMemcpyAsync(hf, d->flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+      DCK(cudaStreamSynchronize(s));
+      if (hf[1]) {
+        LoopCtl rctl = ctl;
+        rctl.active_flag = nullptr;  // keep the loop running; the next check decides
+        DCK(enq_replace<T>(d, s, pl, rctl));
+      }
+    }
+  }
+  DCK(enq_post<T>(d, s));
+  return UNOCG_OK;
+}
+
 bool have_inputs(unocg_dir* d) { return d->phase_set && d->mat64 && d->L > 0; }
 
 }  // namespace
@@ -540,10 +581,11 @@ extern "C" int unocg_dir_create(unocg_dir** out, int physics, int batch, int n1,
   g.m1 = n1 - 1; g.m2 = n2 - 1; g.m3 = n3 - 1;
   g.ne = (long long)n1 * n2 * n3;
   g.nf = (long long)g.m1 * g.m2 * g.m3;
-  g.h = L0 / n1;
-  g.h12 = g.h / 12.0;
-  g.hf = (float)g.h;
-  g.h12f = (float)g.h12;
+  g.pg.n1 = n1; g.pg.n2 = n2; g.pg.n3 = n3; g.pg.n3h = n3 / 2 + 1;
+  g.pg.n = g.ne;
+  g.pg.nh = (long long)n1 * n2 * (n3 / 2 + 1);
+  g.pg.h = L0 / n1;
+  grid_scales(g.pg);
   const int ns[3] = {n1, n2, n3};
   for (int a = 0; a < 3; ++a) {
     dfactor_plan(2 * ns[a], &d->plan[a]);
@@ -555,6 +597,9 @@ extern "C" int unocg_dir_create(unocg_dir** out, int physics, int batch, int n1,
     d->lines3[p] = dst_lines_for(n3, eb, 32);
     d->w2[p] = fit_w(n2, 1, eb, 32);
     d->w1[p] = fit_w(n1, d->c, eb, d->c == 1 ? 32 : 16);
+    // one plane per block pays while two blocks fit an SM (measured: FP32 64^3 7.5 vs 8.6 ms per
+    // solve; FP64 64^3 with 130 KB planes 30.0 vs 26.4 ms)
+    d->plane[p] = dplane_smem_bytes(g, eb) <= 110 * 1024;
   }
   DCK(cudaStreamCreateWithFlags(&d->own_stream, cudaStreamNonBlocking));
   d->stream = d->own_stream;
@@ -580,6 +625,7 @@ extern "C" void unocg_dir_destroy(unocg_dir* d) {
   cudaFree(d->phase); cudaFree(d->mat64); cudaFree(d->mat32); cudaFree(d->loads_d);
   cudaFree(d->Q64); cudaFree(d->Q32); cudaFree(d->f64); cudaFree(d->u64);
   cudaFree(d->sc); cudaFree(d->part); cudaFree(d->tickets); cudaFree(d->flags); cudaFree(d->ceff);
+  cudaFree(d->stage_a); cudaFree(d->stage_b); cudaFree(d->stage_f);
   if (d->own_stream) cudaStreamDestroy(d->own_stream);
   delete d;
 }
@@ -779,15 +825,20 @@ extern "C" int unocg_dir_solve_async(unocg_dir* d, const unocg_solve_opts* o) {
   }
   int rc = ensure_workspace(d, o->precision, o->precond);
   if (rc) return rc;
-  DKey k;
-  k.precond = o->precond; k.precision = o->precision; k.max_iter = o->max_iter;
-  k.replace_every = pl.o.replace_every; k.replace_drop = pl.o.replace_drop; k.L = d->L; k.tol = o->tol;
-  if (!d->exec || !(k == d->key)) {
-    rc = pl.mixed ? build_graph<float>(d, pl) : build_graph<double>(d, pl);
+  if (o->use_graph == 0) {
+    rc = pl.mixed ? run_host_loop<float>(d, pl) : run_host_loop<double>(d, pl);
     if (rc) return rc;
-    d->key = k;
+  } else {
+    DKey k;
+    k.precond = o->precond; k.precision = o->precision; k.max_iter = o->max_iter;
+    k.replace_every = pl.o.replace_every; k.replace_drop = pl.o.replace_drop; k.L = d->L; k.tol = o->tol;
+    if (!d->exec || !(k == d->key)) {
+      rc = pl.mixed ? build_graph<float>(d, pl) : build_graph<double>(d, pl);
+      if (rc) return rc;
+      d->key = k;
+    }
+    DCK(cudaGraphLaunch(d->exec, d->stream));
   }
-  DCK(cudaGraphLaunch(d->exec, d->stream));
   d->last_precision = o->precision;
   d->solved = true;
   return UNOCG_OK;
@@ -838,14 +889,21 @@ extern "C" int unocg_dir_solve(unocg_dir* d, const unocg_solve_opts* o, unocg_so
 }
 
 // ------------------------------------------------------------------ outputs
+static int ensure_stage(unocg_dir* d) {
+  const size_t ne = (size_t)d->c * d->g.ne, nf = (size_t)d->c * d->g.nf;
+  if (!d->stage_a) DCK(cudaMalloc(&d->stage_a, ne * sizeof(double)));
+  if (!d->stage_b) DCK(cudaMalloc(&d->stage_b, ne * sizeof(double)));
+  if (!d->stage_f) DCK(cudaMalloc(&d->stage_f, nf * sizeof(double)));
+  return UNOCG_OK;
+}
+
 extern "C" int unocg_dir_get_fluctuation_dev(unocg_dir* d, int instance, int load, double* out_dev, void* stream) {
   if (!d || !out_dev) return dfail(d, UNOCG_ERR_INVALID_ARG, "null argument");
   if (!d->solved) return dfail(d, UNOCG_ERR_STATE, "no solution");
   if (instance < 0 || instance >= d->B || load < 0 || load >= d->L)
     return dfail(d, UNOCG_ERR_INVALID_ARG, "instance/load out of range");
-  const size_t n = (size_t)d->c * d->g.nf;
-  const double* src = d->u64 + ((size_t)instance * d->L + load) * n;
-  DCK(cudaMemcpyAsync(out_dev, src, n * sizeof(double), cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  const double* src = d->u64 + ((size_t)instance * d->L + load) * d->c * d->g.ne;
+  DCK(launch_dgather(d->g, d->c, src, out_dev, (cudaStream_t)stream));
   return UNOCG_OK;
 }
 
@@ -854,11 +912,14 @@ extern "C" int unocg_dir_get_fluctuation(unocg_dir* d, int instance, int load, d
   if (!d->solved) return dfail(d, UNOCG_ERR_STATE, "no solution");
   if (instance < 0 || instance >= d->B || load < 0 || load >= d->L)
     return dfail(d, UNOCG_ERR_INVALID_ARG, "instance/load out of range");
+  int rc = ensure_stage(d);
+  if (rc) return rc;
   const size_t n = (size_t)d->g.nf;
   std::vector<double> soa((size_t)d->c * n);
+  const double* src = d->u64 + ((size_t)instance * d->L + load) * d->c * d->g.ne;
+  DCK(launch_dgather(d->g, d->c, src, d->stage_f, d->stream));
+  DCK(cudaMemcpyAsync(soa.data(), d->stage_f, soa.size() * sizeof(double), cudaMemcpyDeviceToHost, d->stream));
   DCK(cudaStreamSynchronize(d->stream));
-  DCK(cudaMemcpy(soa.data(), d->u64 + ((size_t)instance * d->L + load) * d->c * n, soa.size() * sizeof(double),
-                 cudaMemcpyDeviceToHost));
   for (size_t i = 0; i < n; ++i)
     for (int k = 0; k < d->c; ++k) out[i * d->c + k] = soa[k * n + i];
   return UNOCG_OK;
@@ -877,6 +938,10 @@ extern "C" int unocg_dir_apply_K_dev(unocg_dir* d, int instance, const double* p
   if (!d || !p_dev || !q_dev) return dfail(d, UNOCG_ERR_INVALID_ARG, "null argument");
   if (!d->phase_set || !d->mat64) return dfail(d, UNOCG_ERR_STATE, "set microstructure and phase properties first");
   if (instance < 0 || instance >= d->B) return dfail(d, UNOCG_ERR_INVALID_ARG, "instance out of range");
+  int rc = ensure_stage(d);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  DCK(launch_dscatter(d->g, d->c, p_dev, d->stage_a, s));
   DKuArgs<double> ka{};
   ka.g = d->g; ka.c = d->c; ka.BL = 1; ka.L = 1;
   ka.phase = d->phase + (size_t)instance * d->g.ne;
@@ -884,8 +949,9 @@ extern "C" int unocg_dir_apply_K_dev(unocg_dir* d, int instance, const double* p
   m.m64 += (size_t)instance * d->n_phases * 2;
   m.m32 += (size_t)instance * d->n_phases * 2;
   ka.mat = m;
-  ka.p = p_dev; ka.q = q_dev; ka.standalone = 1;
-  DCK(launch_dku<double>(ka, (cudaStream_t)stream));
+  ka.p = d->stage_a; ka.q = d->stage_b; ka.standalone = 1;
+  DCK(launch_dku<double>(ka, s));
+  DCK(launch_dgather(d->g, d->c, d->stage_b, q_dev, s));
   return UNOCG_OK;
 }
 
@@ -897,23 +963,32 @@ extern "C" int unocg_dir_apply_uno_dev(unocg_dir* d, int instance, const double*
   }
   if (d->wkind < 0) return dfail(d, UNOCG_ERR_STATE, "set UNO weights first");
   if (instance < 0 || instance >= d->B) return dfail(d, UNOCG_ERR_INVALID_ARG, "instance out of range");
-  const size_t n = (size_t)d->c * d->g.nf;
-  if (!d->f64f.hat) DCK(cudaMalloc(&d->f64f.hat, std::max(n, (size_t)d->B * d->L * n) * sizeof(double)));
+  int rc = ensure_stage(d);
+  if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
+  DCK(launch_dscatter(d->g, d->c, r_dev, d->stage_a, s));
   LoopCtl ctl{};
   DPassArgs<double> a = pass_args<double>(d, DP_FIRST, ctl, 0);
-  a.BL = 1; a.L = 1; a.standalone = 1; a.src = r_dev; a.out = s_dev;
+  a.BL = 1; a.L = 1; a.standalone = 1; a.src = d->stage_a; a.hat = d->stage_b; a.out = d->stage_a;
   a.Q = d->Q64 + (d->Bq > 1 ? (size_t)instance * d->g.nf * (d->c == 1 ? 1 : 6) : 0);
   a.q_inst_stride = 0;
-  a.lines = d->lines3[0];
-  DCK(launch_dpass<double>(a, DP_FIRST, s));
-  a.lines = d->w2[0];
-  DCK(launch_dpass<double>(a, DP_MID, s));
-  a.lines = d->w1[0];
-  DCK(launch_dpass<double>(a, DP_QMUL, s));
-  a.lines = d->w2[0];
-  DCK(launch_dpass<double>(a, DP_MID, s));
-  a.lines = d->lines3[0];
-  DCK(launch_dpass<double>(a, DP_LAST, s));
+  if (d->plane[0]) {
+    DCK(launch_dplane<double>(a, 1, s));
+    a.lines = d->w1[0];
+    DCK(launch_dpass<double>(a, DP_QMUL, s));
+    DCK(launch_dplane<double>(a, 0, s));
+  } else {
+    a.lines = d->lines3[0];
+    DCK(launch_dpass<double>(a, DP_FIRST, s));
+    a.lines = d->w2[0];
+    DCK(launch_dpass<double>(a, DP_MID, s));
+    a.lines = d->w1[0];
+    DCK(launch_dpass<double>(a, DP_QMUL, s));
+    a.lines = d->w2[0];
+    DCK(launch_dpass<double>(a, DP_MID, s));
+    a.lines = d->lines3[0];
+    DCK(launch_dpass<double>(a, DP_LAST, s));
+  }
+  DCK(launch_dgather(d->g, d->c, d->stage_a, s_dev, s));
   return UNOCG_OK;
 }

@@ -1,7 +1,8 @@
 // Kernel arguments and launchers of the Dirichlet-BC solver (sine transform, Sec. 5.2.2 and the
 // Dirichlet row of Table (fnocg-mode-selection-2d)); kernels in k_dirichlet.cu.
 //
-// Fields: real arrays [BL][c][M1][M2][M3] over the free nodes (BL = instances x loads).
+// Fields: real arrays [BL][c][N1][N2][N3] on the embedding grid of dgrid.cuh (BL = instances x
+// loads): the free nodes plus zero boundary nodes.
 // The sine transform along one axis of N voxels (N - 1 free nodes) is computed for two lines at
 // once: line a in the real and line b in the imaginary part of one complex sequence of length
 // 2N, odd-extended (z[0] = z[N] = 0, z[2N - j] = -z[j]); its DFT is -2i X_a + 2 X_b with
@@ -56,8 +57,8 @@ template <typename T> struct DKuArgs {
   int c, BL, L;
   const uint8_t* phase;    // [B][N1][N2][N3]
   Material mat;
-  const T* p;              // direction
-  T* q;                    // K p
+  const T* p;              // direction (zero on the boundary nodes)
+  T* q;                    // K p (rows of the boundary nodes are not used)
   CgScal* sc;
   Reduce red;
   int standalone;
@@ -84,7 +85,7 @@ template <typename T> struct DJacArgs {
   const T* q;
   T* p;
   double* u64;
-  const T* invdiag;        // [B][c][nf] or nullptr (no preconditioner)
+  const T* invdiag;        // [B][c][N1][N2][N3] (zero on the boundary) or nullptr (none)
   int L;
   CgScal* sc;
   Reduce red;
@@ -98,7 +99,7 @@ struct DInitArgs {
   const uint8_t* phase;
   Material mat;
   const double* loads;     // [L][dim]
-  double* f64;             // [BL][c][nf]
+  double* f64;             // [BL][c][N1][N2][N3]
   double* u64;
   void* r;                 // T: r = f
   void* p;                 // T: 0
@@ -121,7 +122,7 @@ struct DDiagArgs {
   int c;
   const uint8_t* phase;
   Material mat;
-  void* invdiag;           // T [B][c][nf]
+  void* invdiag;           // T [B][c][N1][N2][N3]
   int fp64;
 };
 
@@ -129,14 +130,20 @@ size_t dst_smem_bytes(int N, int lines, int elem_bytes);
 int dst_lines_for(int N, int elem_bytes, int cap);
 
 template <typename T> cudaError_t launch_dpass(const DPassArgs<T>& a, int mode, cudaStream_t s);
+// axes 3 and 2 of whole planes in one pass (fwd: DP_FIRST + DP_MID, else DP_MID + DP_LAST) when
+// dplane_smem_bytes fits a block
+size_t dplane_smem_bytes(const DGrid& g, int elem_bytes);
+template <typename T> cudaError_t launch_dplane(const DPassArgs<T>& a, int fwd, cudaStream_t s);
 template <typename T> cudaError_t launch_dku(const DKuArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_dres(const DResArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_djac(const DJacArgs<T>& a, int part, cudaStream_t s);
 cudaError_t launch_dinit(const DInitArgs& a, int BL, cudaStream_t s);
 cudaError_t launch_davg(const DAvgArgs& a, int B, cudaStream_t s);
 cudaError_t launch_ddiag(const DDiagArgs& a, int B, cudaStream_t s);
-int dku_blocks(const DGrid& g);
+int dku_blocks(const DGrid& g, int c);
 int djac_blocks(const DGrid& g);
+cudaError_t launch_dscatter(const DGrid& g, int cnt, const double* src, double* dst, cudaStream_t s);
+cudaError_t launch_dgather(const DGrid& g, int cnt, const double* src, double* dst, cudaStream_t s);
 int dpass_blocks(const DGrid& g, int c, int mode, int lines);
 
 }  // namespace unocg

@@ -8,9 +8,13 @@
 //   k_dpass<DP_QMUL>   DST axis 1, s_hat = Q r_hat, gamma = r.s (Parseval), DST axis 1, beta
 //   k_dpass<DP_MID>    DST axis 2
 //   k_dpass<DP_LAST>   DST axis 3, p = s + beta p
-//   k_dku              q = K p, p.q, alpha
+//   k_ku               q = K p, p.q, alpha (the periodic kernel on the embedding grid)
 //   k_dpass<DP_FIRST>  r -= alpha q, u += alpha p, ||r||_inf, stopping test, DST axis 3 of r
+#include <algorithm>
+
 #include "../fft.cuh"
+#include "../kargs.h"
+#include "../stencil.cuh"
 #include "dargs.h"
 
 namespace unocg {
@@ -29,7 +33,7 @@ struct DTile {
 
 __device__ __forceinline__ DTile dtile(const DGrid& g, int c, int ax, int lines, int bl, int t) {
   DTile d;
-  d.base = (long long)bl * c * g.nf;
+  d.base = (long long)bl * c * g.ne;
   d.ax = ax;
   d.lines = ax == 1 ? c * lines : lines;
   d.W = lines;
@@ -51,17 +55,22 @@ __device__ __forceinline__ DTile dtile(const DGrid& g, int c, int ax, int lines,
   return d;
 }
 
-// global index of element j of line l, or -1 when the line lies outside the field
+// embedding-grid index of interior point j of line l, or -1 when the line lies outside the
+// field (free node j is node j + 1 on every axis)
 __device__ __forceinline__ long long daddr(const DGrid& g, const DTile& d, int l, int j) {
   if (d.ax == 3) {
     const long long row = d.row0 + l;
-    return row < d.rows ? d.base + row * g.m3 + j : -1LL;
+    if (row >= d.rows) return -1LL;
+    const int comp = (int)(row / ((long long)g.m1 * g.m2));
+    const int r2 = (int)(row - (long long)comp * g.m1 * g.m2);
+    const int j1 = r2 / g.m2, j2 = r2 - j1 * g.m2;
+    return d.base + (((long long)comp * g.n1 + j1 + 1) * g.n2 + j2 + 1) * g.n3 + j + 1;
   }
   const int w = l % d.W, grp = l / d.W;
   const int i3 = d.i30 + w;
   if (i3 >= g.m3) return -1LL;
-  if (d.ax == 2) return d.base + (((long long)d.comp * g.m1 + d.i1) * g.m2 + j) * g.m3 + i3;
-  return d.base + (((long long)grp * g.m1 + j) * g.m2 + d.i2) * g.m3 + i3;
+  if (d.ax == 2) return d.base + (((long long)d.comp * g.n1 + d.i1 + 1) * g.n2 + j + 1) * g.n3 + i3 + 1;
+  return d.base + (((long long)grp * g.n1 + j + 1) * g.n2 + d.i2 + 1) * g.n3 + i3 + 1;
 }
 
 // element (l, j) of the loop over a tile: j fastest along axis 3 (contiguous rows), the
@@ -239,52 +248,132 @@ __global__ void __launch_bounds__(kDThreads) k_dpass(DPassArgs<T> a) {
   }
 }
 
-// ============================================================================ K p
-template <typename T, int CC>
-__global__ void __launch_bounds__(kDThreads) k_dku(DKuArgs<T> a) {
-  __shared__ T mt[2 * 256];
+// ============================================================================ plane passes
+// Axes 3 and 2 of one interior plane (instance-load, component, i1) in one block, the plane held
+// in shared memory between the two transforms.  FWD: rows (axis 3; with the residual update,
+// ||r||_inf and the stopping test in loop mode), then columns (axis 2), written to hat.  INV:
+// columns of hat, then rows, written as p = s + beta p (or to out).  The row pairs (j2, j2+1)
+// and column pairs (k3, k3+1) are odd-extended lines of length 2 N3 and 2 N2.
+constexpr int kDPlaneThreads = 512;
+
+template <typename T, int FWD>
+__global__ void __launch_bounds__(kDPlaneThreads) k_dplane(DPassArgs<T> a) {
+  using C = cplx<T>;
+  extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ double red_sh[32];
   const DGrid& g = a.g;
   const int bl = blockIdx.y;
-  const int b = bl / a.L;
-  load_material<T>(mt, a.mat, b);
-  __syncthreads();
-  const bool active = a.standalone || !a.sc[bl].done;
-  DotAcc<T> acc;
+  const int c = a.c;
+  const int comp = blockIdx.x / g.m1, j1 = blockIdx.x - comp * g.m1;
+  const int N2 = g.n2, N3 = g.n3, M2 = g.m2, M3 = g.m3;
+  const int Pr = (M2 + 1) >> 1, Pc = (M3 + 1) >> 1;
+  const long long half = (long long)(2 * N3 * Pr > 2 * N2 * Pc ? 2 * N3 * Pr : 2 * N2 * Pc);
+  C* A = reinterpret_cast<C*>(dsm);
+  C* B = A + half;
+  C* tw3 = B + half;
+  C* tw2 = tw3 + 2 * N3;
+  // element (j2, j3) of the plane
+  const long long base = (long long)bl * c * g.ne + ((long long)comp * g.n1 + j1 + 1) * g.n2 * g.n3;
+  auto at = [&](int j2, int j3) { return base + (long long)(j2 + 1) * N3 + j3 + 1; };
+
+  bool active = true;
+  if (!a.standalone) {
+    const CgScal& s = a.sc[bl];
+    active = !s.done && (!FWD || !a.after_replace || s.need_replace);
+  }
+  double bval = 0.0;
   if (active) {
-    const uint8_t* ph = a.phase + (long long)b * g.ne;
-    const T* p = a.p + (long long)bl * CC * g.nf;
-    T* q = a.q + (long long)bl * CC * g.nf;
-    for (long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x; node < g.nf;
-         node += (long long)gridDim.x * blockDim.x) {
-      const int j3 = (int)(node % g.m3);
-      const long long r = node / g.m3;
-      const int j2 = (int)(r % g.m2), j1 = (int)(r / g.m2);
-      T out[CC];
-      dnode_Ku<T, CC>(p, ph, mt, g, j1, j2, j3, out);
-#pragma unroll
-      for (int i = 0; i < CC; ++i) {
-        q[i * g.nf + node] = out[i];
-        acc.add_prod(p[i * g.nf + node], out[i]);
+    load_tw<T>(tw3, a.t.tw[2], 2 * N3);
+    load_tw<T>(tw2, a.t.tw[1], 2 * N2);
+    const int total = M2 * M3;
+    if (FWD) {
+      // rows into A: line j2 (pair j2 / 2), point j3
+      dzero_ends<T>(A, Pr, N3);
+      if (M2 & 1)  // the unpaired last row: its partner line is zero
+        for (int j = threadIdx.x; j < M3; j += blockDim.x) dput<T>(A, Pr, N3, M2, j, (T)0);
+      if (!a.standalone) {
+        const CgScal& s = a.sc[bl];
+        const T alpha = (T)s.alpha;
+        const bool upd = !a.after_replace && s.started;
+        T rm = (T)0;
+        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+          const int j2 = idx / M3, j3 = idx - j2 * M3;
+          const long long ga = at(j2, j3);
+          T x = a.r[ga];
+          if (upd) {
+            x -= alpha * a.q[ga];
+            a.r[ga] = x;
+            a.u64[ga] += s.alpha * (double)a.p[ga];
+          }
+          rm = rm > dabs(x) ? rm : dabs(x);
+          dput<T>(A, Pr, N3, j2, j3, x);
+        }
+        bval = (double)rm;
+      } else {
+        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+          const int j2 = idx / M3, j3 = idx - j2 * M3;
+          dput<T>(A, Pr, N3, j2, j3, a.src[at(j2, j3)]);
+        }
+      }
+      __syncthreads();
+      C* res = fft_lines<T, -1>(A, B, Pr, 1, Pr, a.t.p[2], tw3);
+      C* oth = res == A ? B : A;
+      // columns: line k3 (pair k3 / 2), point j2
+      dzero_ends<T>(oth, Pc, N2);
+      if (M3 & 1)
+        for (int j = threadIdx.x; j < M2; j += blockDim.x) dput<T>(oth, Pc, N2, M3, j, (T)0);
+      for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int j2 = idx / M3, k3 = idx - j2 * M3;
+        dput<T>(oth, Pc, N2, k3, j2, dget<T>(res, Pr, j2, k3));
+      }
+      __syncthreads();
+      res = fft_lines<T, -1>(oth, res, Pc, 1, Pc, a.t.p[1], tw2);
+      for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int k2 = idx / M3, k3 = idx - k2 * M3;
+        a.hat[at(k2, k3)] = dget<T>(res, Pc, k3, k2);
+      }
+    } else {
+      // columns of hat into A: line k3, point k2
+      dzero_ends<T>(A, Pc, N2);
+      if (M3 & 1)
+        for (int j = threadIdx.x; j < M2; j += blockDim.x) dput<T>(A, Pc, N2, M3, j, (T)0);
+      for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int k2 = idx / M3, k3 = idx - k2 * M3;
+        dput<T>(A, Pc, N2, k3, k2, a.hat[at(k2, k3)]);
+      }
+      __syncthreads();
+      C* res = fft_lines<T, -1>(A, B, Pc, 1, Pc, a.t.p[1], tw2);
+      C* oth = res == A ? B : A;
+      dzero_ends<T>(oth, Pr, N3);
+      if (M2 & 1)
+        for (int j = threadIdx.x; j < M3; j += blockDim.x) dput<T>(oth, Pr, N3, M2, j, (T)0);
+      for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int j2 = idx / M3, k3 = idx - j2 * M3;
+        dput<T>(oth, Pr, N3, j2, k3, dget<T>(res, Pc, k3, j2));
+      }
+      __syncthreads();
+      res = fft_lines<T, -1>(oth, res, Pr, 1, Pr, a.t.p[2], tw3);
+      const T beta = a.standalone ? (T)0 : (T)a.sc[bl].beta;
+      for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int j2 = idx / M3, j3 = idx - j2 * M3;
+        const long long ga = at(j2, j3);
+        const T x = dget<T>(res, Pr, j2, j3);
+        if (a.standalone) a.out[ga] = x;
+        else a.p[ga] = x + beta * a.p[ga];
       }
     }
   }
-  if (a.standalone) return;
-  const double bs = block_sum_acc(acc, red_sh);
-  if (threadIdx.x == 0) a.red.part[(long long)bl * gridDim.x + blockIdx.x] = bs;
+  if (a.standalone || !FWD) return;
+  const double bm = block_max(active ? bval : 0.0, red_sh);
+  if (threadIdx.x == 0 && active) atomic_max_nonneg(&a.sc[bl].rmax_bits, bm);
   if (last_block(a.red.ticket)) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int q = warp; q < a.BL; q += blockDim.x / 32) {
-      if (a.sc[q].done) continue;
-      const double sum = warp_sum_partials(a.red.part + (long long)q * gridDim.x, gridDim.x, 1);
-      if (lane == 0) step_update(a.sc[q], sum);
-    }
-    __syncthreads();
+    residual_decision(a.sc, a.BL, a.ctl, a.after_replace);
     if (threadIdx.x == 0) *a.red.ticket = 0u;
   }
 }
 
 // ============================================================================ f - K u (FP64)
+// r = f - K u on the free nodes (replacement into r), or max |f - K u| into tmax (report)
 template <typename T, int CC>
 __global__ void __launch_bounds__(kDThreads) k_dres(DResArgs<T> a) {
   __shared__ double mt[2 * 256];
@@ -296,21 +385,20 @@ __global__ void __launch_bounds__(kDThreads) k_dres(DResArgs<T> a) {
   __syncthreads();
   if (a.only_pending && !a.sc[bl].need_replace) return;
   const uint8_t* ph = a.phase + (long long)b * g.ne;
-  const double* u = a.u64 + (long long)bl * CC * g.nf;
-  const double* f = a.f64 + (long long)bl * CC * g.nf;
+  const double* u = a.u64 + (long long)bl * CC * g.ne;
+  const double* f = a.f64 + (long long)bl * CC * g.ne;
   double lmax = 0.0;
-  for (long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x; node < g.nf;
-       node += (long long)gridDim.x * blockDim.x) {
-    const int j3 = (int)(node % g.m3);
-    const long long r = node / g.m3;
-    const int j2 = (int)(r % g.m2), j1 = (int)(r / g.m2);
+  for (long long fi = (long long)blockIdx.x * blockDim.x + threadIdx.x; fi < g.nf;
+       fi += (long long)gridDim.x * blockDim.x) {
+    int i1, i2, i3;
+    const long long node = dnode_of_free(g, fi, i1, i2, i3);
     double ku[CC];
-    dnode_Ku<double, CC>(u, ph, mt, g, j1, j2, j3, ku);
+    node_Ku<double, CC>(u, ph, mt, g.pg, i1, i2, i3, ku);
 #pragma unroll
     for (int i = 0; i < CC; ++i) {
-      const double rr = f[i * g.nf + node] - ku[i];
+      const double rr = f[i * g.ne + node] - ku[i];
       lmax = fmax(lmax, fabs(rr));
-      if (a.r) a.r[(long long)bl * CC * g.nf + i * g.nf + node] = (T)rr;
+      if (a.r) a.r[(long long)bl * CC * g.ne + i * g.ne + node] = (T)rr;
     }
   }
   const double bm = block_max(lmax, red_sh);
@@ -321,6 +409,7 @@ __global__ void __launch_bounds__(kDThreads) k_dres(DResArgs<T> a) {
 // part 0: r -= alpha q, u += alpha p, ||r||_inf, stopping test
 // part 1: gamma = r . z with z = D^-1 r (or r), beta
 // part 2: p = z + beta p
+// (free nodes only; the boundary entries stay zero)
 template <typename T, int PART>
 __global__ void __launch_bounds__(kDThreads) k_djac(DJacArgs<T> a) {
   __shared__ double red_sh[32];
@@ -328,16 +417,16 @@ __global__ void __launch_bounds__(kDThreads) k_djac(DJacArgs<T> a) {
   const int bl = blockIdx.y;
   const CgScal& s = a.sc[bl];
   const bool active = !s.done && (PART != 0 || !a.after_replace || s.need_replace);
-  const long long n = (long long)a.c * g.nf;
+  const long long n = (long long)a.c * g.ne;
   const long long off = (long long)bl * n;
   const T* idg = a.invdiag ? a.invdiag + (long long)(bl / a.L) * n : nullptr;
-  double bval = 0.0;
   DotAcc<T> acc;
   T rm = (T)0;
   if (active) {
     const T alpha = (T)s.alpha, beta = (T)s.beta;
     const bool upd = !a.after_replace && s.started;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+      if (!dinterior(g, i % g.ne)) continue;
       if (PART == 0) {
         T x = a.r[off + i];
         if (upd) {
@@ -362,7 +451,7 @@ __global__ void __launch_bounds__(kDThreads) k_djac(DJacArgs<T> a) {
       if (threadIdx.x == 0) *a.red.ticket = 0u;
     }
   } else if (PART == 1) {
-    bval = block_sum_acc(acc, red_sh);
+    const double bval = block_sum_acc(acc, red_sh);
     if (threadIdx.x == 0) a.red.part[(long long)bl * gridDim.x + blockIdx.x] = bval;
     if (last_block(a.red.ticket)) {
       const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -378,6 +467,7 @@ __global__ void __launch_bounds__(kDThreads) k_djac(DJacArgs<T> a) {
 }
 
 // ============================================================================ set-up, post
+// f (FP64) on the free nodes, zero on the boundary; r = f, u = p = q = 0 everywhere
 template <int CC>
 __global__ void __launch_bounds__(kDThreads) k_dinit(DInitArgs a) {
   __shared__ double mt[2 * 256];
@@ -387,17 +477,22 @@ __global__ void __launch_bounds__(kDThreads) k_dinit(DInitArgs a) {
   load_material<double>(mt, a.mat, b);
   __syncthreads();
   const uint8_t* ph = a.phase + (long long)b * g.ne;
-  for (long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x; node < g.nf;
+  for (long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x; node < g.ne;
        node += (long long)gridDim.x * blockDim.x) {
-    const int j3 = (int)(node % g.m3);
-    const long long r = node / g.m3;
-    const int j2 = (int)(r % g.m2), j1 = (int)(r / g.m2);
+    const int i3 = (int)(node % g.n3);
+    const long long r = node / g.n3;
+    const int i2 = (int)(r % g.n2), i1 = (int)(r / g.n2);
     double f[CC];
-    dnode_rhs<CC>(ph, mt, g, j1, j2, j3, a.loads + l * (CC == 1 ? 3 : 6), f);
-    const long long o = (long long)bl * CC * g.nf + node;
+    if (i1 && i2 && i3) {
+      node_rhs<CC>(ph, mt, g.pg, i1, i2, i3, a.loads + l * (CC == 1 ? 3 : 6), f);
+    } else {
+#pragma unroll
+      for (int i = 0; i < CC; ++i) f[i] = 0.0;
+    }
+    const long long o = (long long)bl * CC * g.ne + node;
 #pragma unroll
     for (int i = 0; i < CC; ++i) {
-      const long long k = o + i * g.nf;
+      const long long k = o + i * g.ne;
       a.f64[k] = f[i];
       a.u64[k] = 0.0;
       if (a.fp64) {
@@ -413,6 +508,7 @@ __global__ void __launch_bounds__(kDThreads) k_dinit(DInitArgs a) {
   }
 }
 
+// D^-1 on the free nodes, zero on the boundary
 template <int CC>
 __global__ void __launch_bounds__(kDThreads) k_ddiag(DDiagArgs a) {
   __shared__ double mt[2 * 256];
@@ -421,23 +517,26 @@ __global__ void __launch_bounds__(kDThreads) k_ddiag(DDiagArgs a) {
   load_material<double>(mt, a.mat, b);
   __syncthreads();
   const uint8_t* ph = a.phase + (long long)b * g.ne;
-  for (long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x; node < g.nf;
+  for (long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x; node < g.ne;
        node += (long long)gridDim.x * blockDim.x) {
-    const int j3 = (int)(node % g.m3);
-    const long long r = node / g.m3;
-    const int j2 = (int)(r % g.m2), j1 = (int)(r / g.m2);
+    const int i3 = (int)(node % g.n3);
+    const long long r = node / g.n3;
+    const int i2 = (int)(r % g.n2), i1 = (int)(r / g.n2);
     double dg[CC];
-    dnode_diag<CC>(ph, mt, g, j1, j2, j3, dg);
+    const bool in = i1 && i2 && i3;
+    if (in) node_diag<CC>(ph, mt, g.pg, i1, i2, i3, dg);
 #pragma unroll
     for (int i = 0; i < CC; ++i) {
-      const long long k = (long long)b * CC * g.nf + i * g.nf + node;
-      if (a.fp64) ((double*)a.invdiag)[k] = 1.0 / dg[i];
-      else ((float*)a.invdiag)[k] = (float)(1.0 / dg[i]);
+      const long long k = (long long)b * CC * g.ne + i * g.ne + node;
+      const double v = in ? 1.0 / dg[i] : 0.0;
+      if (a.fp64) ((double*)a.invdiag)[k] = v;
+      else ((float*)a.invdiag)[k] = (float)v;
     }
   }
 }
 
-// averaged flux / stress: out[b][i][l] += sum over voxels / n_voxels
+// averaged flux / stress: out[b][i][l] += sum over voxels / n_voxels (the corner nodes on the
+// far faces wrap to the zero boundary nodes)
 template <int CC>
 __global__ void __launch_bounds__(kDThreads) k_davg(DAvgArgs a) {
   constexpr int DIM = CC == 1 ? 3 : 6;
@@ -448,7 +547,7 @@ __global__ void __launch_bounds__(kDThreads) k_davg(DAvgArgs a) {
   load_material<double>(mt, a.mat, b);
   __syncthreads();
   const uint8_t* ph = a.phase + (long long)b * g.ne;
-  const double* u = a.u64 + (long long)(b * a.L + l) * CC * g.nf;
+  const double* u = a.u64 + (long long)(b * a.L + l) * CC * g.ne;
   double acc[DIM];
 #pragma unroll
   for (int i = 0; i < DIM; ++i) acc[i] = 0.0;
@@ -457,13 +556,36 @@ __global__ void __launch_bounds__(kDThreads) k_davg(DAvgArgs a) {
     const long long r = e / g.n3;
     const int e2 = (int)(r % g.n2), e1 = (int)(r / g.n2);
     double sig[DIM];
-    delement_mean_flux<CC>(u, mt, ph[e], g, e1, e2, e3, a.loads + l * DIM, sig);
+    element_mean_flux<CC>(u, mt, ph[e], g.pg, e1, e2, e3, a.loads + l * DIM, sig);
 #pragma unroll
     for (int i = 0; i < DIM; ++i) acc[i] += sig[i];
   }
   for (int i = 0; i < DIM; ++i) {
     const double s = block_sum(acc[i], red_sh);
     if (threadIdx.x == 0) atomicAdd(a.out + ((long long)b * DIM + i) * a.L + l, s / (double)g.ne);
+  }
+}
+
+// free-node fields [cnt][M1][M2][M3] <-> embedding-grid fields [cnt][N1][N2][N3] (zero boundary)
+__global__ void __launch_bounds__(kDThreads) k_dscatter(DGrid g, int cnt, const double* src, double* dst) {
+  const long long total = (long long)cnt * g.ne;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long comp = i / g.ne, node = i - comp * g.ne;
+    const int i3 = (int)(node % g.n3);
+    const long long r = node / g.n3;
+    const int i2 = (int)(r % g.n2), i1 = (int)(r / g.n2);
+    double v = 0.0;
+    if (i1 && i2 && i3) v = src[comp * g.nf + (((long long)(i1 - 1) * g.m2 + (i2 - 1)) * g.m3 + (i3 - 1))];
+    dst[i] = v;
+  }
+}
+__global__ void __launch_bounds__(kDThreads) k_dgather(DGrid g, int cnt, const double* src, double* dst) {
+  const long long total = (long long)cnt * g.nf;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long comp = i / g.nf, f = i - comp * g.nf;
+    int i1, i2, i3;
+    const long long node = dnode_of_free(g, f, i1, i2, i3);
+    dst[i] = src[comp * g.ne + node];
   }
 }
 
@@ -490,11 +612,12 @@ int dpass_blocks(const DGrid& g, int c, int mode, int lines) {
   return g.m2 * nb3;
 }
 
-int dku_blocks(const DGrid& g) {
-  const long long b = (g.nf + kDThreads - 1) / kDThreads;
-  return (int)(b < 1024 ? b : 1024);
+static int dgrid_blocks(long long m) {
+  const long long b = (m + kDThreads - 1) / kDThreads;
+  return (int)(b < 1024 ? (b < 1 ? 1 : b) : 1024);
 }
-int djac_blocks(const DGrid& g) { return dku_blocks(g); }
+int dku_blocks(const DGrid& g, int c) { return ku_blocks_x(g.pg, c); }
+int djac_blocks(const DGrid& g) { return dgrid_blocks(g.ne); }
 
 template <typename T, int MODE, int CC>
 static cudaError_t dpass_go(const DPassArgs<T>& a, cudaStream_t s) {
@@ -529,15 +652,15 @@ cudaError_t launch_dpass(const DPassArgs<T>& a, int mode, cudaStream_t s) {
 
 template <typename T>
 cudaError_t launch_dku(const DKuArgs<T>& a, cudaStream_t s) {
-  dim3 grid(dku_blocks(a.g), a.BL);
-  if (a.c == 1) k_dku<T, 1><<<grid, kDThreads, 0, s>>>(a);
-  else k_dku<T, 3><<<grid, kDThreads, 0, s>>>(a);
-  return cudaGetLastError();
+  StencilArgs<T> ka{};
+  ka.g = a.g.pg; ka.c = a.c; ka.BL = a.BL; ka.L = a.L; ka.phase = a.phase; ka.mat = a.mat;
+  ka.d = a.p; ka.p = a.q; ka.sc = a.sc; ka.red = a.red; ka.standalone = a.standalone;
+  return launch_ku<T>(ka, s);
 }
 
 template <typename T>
 cudaError_t launch_dres(const DResArgs<T>& a, cudaStream_t s) {
-  dim3 grid(dku_blocks(a.g), a.BL);
+  dim3 grid(dgrid_blocks(a.g.nf), a.BL);
   if (a.c == 1) k_dres<T, 1><<<grid, kDThreads, 0, s>>>(a);
   else k_dres<T, 3><<<grid, kDThreads, 0, s>>>(a);
   return cudaGetLastError();
@@ -553,14 +676,14 @@ cudaError_t launch_djac(const DJacArgs<T>& a, int part, cudaStream_t s) {
 }
 
 cudaError_t launch_dinit(const DInitArgs& a, int BL, cudaStream_t s) {
-  dim3 grid(dku_blocks(a.g), BL);
+  dim3 grid(dgrid_blocks(a.g.ne), BL);
   if (a.c == 1) k_dinit<1><<<grid, kDThreads, 0, s>>>(a);
   else k_dinit<3><<<grid, kDThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ddiag(const DDiagArgs& a, int B, cudaStream_t s) {
-  dim3 grid(dku_blocks(a.g), B);
+  dim3 grid(dgrid_blocks(a.g.ne), B);
   if (a.c == 1) k_ddiag<1><<<grid, kDThreads, 0, s>>>(a);
   else k_ddiag<3><<<grid, kDThreads, 0, s>>>(a);
   return cudaGetLastError();
@@ -574,6 +697,34 @@ cudaError_t launch_davg(const DAvgArgs& a, int B, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+size_t dplane_smem_bytes(const DGrid& g, int elem_bytes) {
+  const long long Pr = (g.m2 + 1) / 2, Pc = (g.m3 + 1) / 2;
+  const long long half = std::max(2LL * g.n3 * Pr, 2LL * g.n2 * Pc);
+  return (size_t)elem_bytes * 2 * (2 * half + 2LL * g.n3 + 2LL * g.n2);
+}
+
+template <typename T>
+cudaError_t launch_dplane(const DPassArgs<T>& a, int fwd, cudaStream_t s) {
+  const size_t smem = dplane_smem_bytes(a.g, sizeof(T));
+  auto kern = fwd ? k_dplane<T, 1> : k_dplane<T, 0>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(a.c * a.g.m1, a.BL);
+  kern<<<grid, kDPlaneThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dscatter(const DGrid& g, int cnt, const double* src, double* dst, cudaStream_t s) {
+  k_dscatter<<<dgrid_blocks((long long)cnt * g.ne), kDThreads, 0, s>>>(g, cnt, src, dst);
+  return cudaGetLastError();
+}
+cudaError_t launch_dgather(const DGrid& g, int cnt, const double* src, double* dst, cudaStream_t s) {
+  k_dgather<<<dgrid_blocks((long long)cnt * g.nf), kDThreads, 0, s>>>(g, cnt, src, dst);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_dplane<double>(const DPassArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_dplane<float>(const DPassArgs<float>&, int, cudaStream_t);
 template cudaError_t launch_dpass<double>(const DPassArgs<double>&, int, cudaStream_t);
 template cudaError_t launch_dpass<float>(const DPassArgs<float>&, int, cudaStream_t);
 template cudaError_t launch_dku<double>(const DKuArgs<double>&, cudaStream_t);

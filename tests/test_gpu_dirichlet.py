@@ -52,8 +52,9 @@ def test_apply_K_matches_oracle(physics, shape):
 
 
 @pytest.mark.parametrize("physics", [1, 3])
-@pytest.mark.parametrize("shape", SHAPES + [(32, 32, 32), (64, 48, 40)])
+@pytest.mark.parametrize("shape", SHAPES + [(32, 32, 32), (64, 48, 40), (8, 128, 128)])
 def test_reference_weights_and_apply_match_oracle(physics, shape):
+    # (8, 128, 128): planes too large for one block, separate axis-3 and axis-2 passes
     import torch
     from paper_2508_02681_gb300 import _lib, api
     c = 1 if physics == 1 else 3
@@ -132,7 +133,7 @@ def test_fp64_solve_matches_oracle(physics, shape, precond):
     h.close()
 
 
-@pytest.mark.parametrize("physics,shape", [(1, (16, 16, 16)), (3, (16, 16, 16)), (1, (32, 32, 32))])
+@pytest.mark.parametrize("physics,shape", [(1, (16, 16, 16)), (3, (16, 16, 16)), (1, (32, 32, 32)), (1, (8, 128, 128))])
 def test_mixed_solve_matches_oracle(physics, shape):
     from paper_2508_02681_gb300 import _lib
     phase, _ = rsa_spheres(shape, shape[0] / 5.0, 0.25, seed=13)
@@ -242,4 +243,23 @@ def test_invalid_arguments():
     bad[3, 3, 3, 0] = -1.0
     with pytest.raises(UnocgError):
         h.set_uno_weights(_lib.W_BLOCKS, bad)
+    h.close()
+
+
+def test_host_loop_matches_graph_loop():
+    from paper_2508_02681_gb300 import _lib
+    shape = (16, 16, 16)
+    phase, _ = rsa_spheres(shape, 3.0, 0.25, seed=41)
+    h = _ctx(1, phase, _props(1), unit_loads(1))
+    h.set_uno_weights(_lib.W_REFERENCE_MEDIUM)
+    out = {}
+    for g in (0, 1):
+        for prec in (_lib.FP64, _lib.MIXED):
+            info = h.solve(tol=1e-8, max_iter=5000, precond=_lib.PRECOND_UNO, precision=prec, use_graph=g)
+            out[g, prec] = (info.iters.copy(), h.effective_tensor()[0], info.checks, info.replacements)
+    for prec in (_lib.FP64, _lib.MIXED):
+        assert np.array_equal(out[0, prec][0], out[1, prec][0])
+        # the voxel averages are summed with atomics: equal up to the order of the additions
+        assert rel(out[0, prec][1], out[1, prec][1]) < 1e-14
+        assert out[0, prec][2:] == out[1, prec][2:]
     h.close()
