@@ -45,6 +45,7 @@ cudaError_t dupload_twiddles(void** dst, int N) {
 
 struct DFields {
   void *r = nullptr, *p = nullptr, *q = nullptr, *hat = nullptr, *invdiag = nullptr;
+  void* u = nullptr;  // FP32 solution increment (mixed precision only)
 };
 
 struct DKey {
@@ -90,6 +91,8 @@ struct unocg_dir {
   double *stage_a = nullptr, *stage_b = nullptr, *stage_f = nullptr;  // operator-level I/O
   int lines3[2], w2[2], w1[2];  // [0] FP64, [1] FP32
   bool plane[2];                // axes 3 and 2 in one plane pass (the plane fits a block)
+  bool plane_reg = false;       // register-resident plane passes (N2 = N3 a power of two)
+  bool line_reg = false;        // register-resident axis-1 pass with Q (c = 1, N1 a power of two)
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   DKey key;
@@ -150,7 +153,7 @@ void dfree_graph(unocg_dir* d) {
 }
 
 void free_fields(DFields& f) {
-  cudaFree(f.r); cudaFree(f.p); cudaFree(f.q); cudaFree(f.hat); cudaFree(f.invdiag);
+  cudaFree(f.r); cudaFree(f.p); cudaFree(f.q); cudaFree(f.hat); cudaFree(f.invdiag); cudaFree(f.u);
   f = DFields{};
 }
 
@@ -292,10 +295,12 @@ int ensure_workspace(unocg_dir* d, int precision, int precond) {
   if (!f.r) DCK(cudaMalloc(&f.r, n * eb));
   if (!f.p) DCK(cudaMalloc(&f.p, n * eb));
   if (!f.q) DCK(cudaMalloc(&f.q, n * eb));
+  if (!fp64 && !f.u) DCK(cudaMalloc(&f.u, n * eb));
   if (precond == UNOCG_PRECOND_UNO && !f.hat) DCK(cudaMalloc(&f.hat, n * eb));
   if (precond == UNOCG_PRECOND_JACOBI && !f.invdiag)
     DCK(cudaMalloc(&f.invdiag, (size_t)d->B * d->c * d->g.ne * eb));
   size_t need = (size_t)BL * std::max({(size_t)dku_blocks(d->g, d->c), (size_t)djac_blocks(d->g),
+                                       (size_t)(d->line_reg ? dline_reg_blocks(d->g) : 0),
                                        (size_t)dpass_blocks(d->g, d->c, DP_QMUL, std::min(d->w1[0], d->w1[1]))});
   if (d->part_len < need) {
     cudaFree(d->part);
@@ -321,7 +326,8 @@ DPassArgs<T> pass_args(unocg_dir* d, int mode, const LoopCtl& ctl, int after_rep
   DPassArgs<T> a{};
   a.g = d->g; a.c = d->c; a.BL = d->B * d->L; a.L = d->L;
   a.lines = mode == DP_MID ? d->w2[pidx<T>()] : mode == DP_QMUL ? d->w1[pidx<T>()] : d->lines3[pidx<T>()];
-  a.hat = (T*)f.hat; a.r = (T*)f.r; a.q = (const T*)f.q; a.p = (T*)f.p; a.u64 = d->u64;
+  a.hat = (T*)f.hat; a.r = (T*)f.r; a.q = (const T*)f.q; a.p = (T*)f.p;
+  a.u = sizeof(T) == 8 ? (T*)d->u64 : (T*)f.u;
   a.Q = sizeof(T) == 8 ? (const void*)d->Q64 : (const void*)d->Q32;
   a.q_inst_stride = d->Bq > 1 ? d->g.nf * (d->c == 1 ? 1 : 6) : 0;
   a.sc = d->sc;
@@ -336,7 +342,8 @@ DJacArgs<T> jac_args(unocg_dir* d, const DPlan& pl, const LoopCtl& ctl, int part
   DFields& f = dfields<T>(d);
   DJacArgs<T> a{};
   a.g = d->g; a.c = d->c; a.BL = d->B * d->L; a.L = d->L;
-  a.r = (T*)f.r; a.q = (const T*)f.q; a.p = (T*)f.p; a.u64 = d->u64;
+  a.r = (T*)f.r; a.q = (const T*)f.q; a.p = (T*)f.p;
+  a.u = sizeof(T) == 8 ? (T*)d->u64 : (T*)f.u;
   a.invdiag = pl.o.precond == UNOCG_PRECOND_JACOBI ? (const T*)f.invdiag : nullptr;
   a.sc = d->sc;
   a.red = Reduce{d->part, d->tickets + (part == 1 ? DT_JAC : after_replace ? DT_CHECK2 : DT_CHECK)};
@@ -347,6 +354,7 @@ DJacArgs<T> jac_args(unocg_dir* d, const DPlan& pl, const LoopCtl& ctl, int part
 template <typename T>
 cudaError_t enq_check(unocg_dir* d, cudaStream_t s, const DPlan& pl, const LoopCtl& ctl, int after_replace) {
   if (pl.o.precond == UNOCG_PRECOND_UNO) {
+    if (d->plane_reg) return launch_dplane_reg<T>(pass_args<T>(d, DP_FIRST, ctl, after_replace), 1, s);
     if (d->plane[pidx<T>()]) return launch_dplane<T>(pass_args<T>(d, DP_FIRST, ctl, after_replace), 1, s);
     return launch_dpass<T>(pass_args<T>(d, DP_FIRST, ctl, after_replace), DP_FIRST, s);
   }
@@ -363,7 +371,8 @@ cudaError_t enq_pre(unocg_dir* d, cudaStream_t s, const DPlan& pl, const LoopCtl
   if (e != cudaSuccess) return e;
   DInitArgs ia{};
   ia.g = d->g; ia.c = d->c; ia.L = d->L; ia.phase = d->phase; ia.mat = dmaterial(d); ia.loads = d->loads_d;
-  ia.f64 = d->f64; ia.u64 = d->u64; ia.r = f.r; ia.p = f.p; ia.q = f.q; ia.fp64 = sizeof(T) == 8;
+  ia.f64 = d->f64; ia.u64 = d->u64; ia.u32 = sizeof(T) == 8 ? nullptr : f.u;
+  ia.r = f.r; ia.p = f.p; ia.q = f.q; ia.fp64 = sizeof(T) == 8;
   e = launch_dinit(ia, BL, s);
   if (e != cudaSuccess) return e;
   if (pl.o.precond == UNOCG_PRECOND_JACOBI) {
@@ -387,9 +396,13 @@ cudaError_t enq_ku(unocg_dir* d, cudaStream_t s) {
 template <typename T>
 cudaError_t enq_body(unocg_dir* d, cudaStream_t s, const DPlan& pl, const LoopCtl& ctl) {
   cudaError_t e = cudaSuccess;
-  if (pl.o.precond == UNOCG_PRECOND_UNO && d->plane[pidx<T>()]) {
-    e = launch_dpass<T>(pass_args<T>(d, DP_QMUL, ctl, 0), DP_QMUL, s);
-    if (e == cudaSuccess) e = launch_dplane<T>(pass_args<T>(d, DP_LAST, ctl, 0), 0, s);
+  if (pl.o.precond == UNOCG_PRECOND_UNO && (d->plane_reg || d->plane[pidx<T>()])) {
+    if (d->line_reg) e = launch_dline_reg<T>(pass_args<T>(d, DP_QMUL, ctl, 0), s);
+    else e = launch_dpass<T>(pass_args<T>(d, DP_QMUL, ctl, 0), DP_QMUL, s);
+    if (e == cudaSuccess) {
+      if (d->plane_reg) e = launch_dplane_reg<T>(pass_args<T>(d, DP_LAST, ctl, 0), 0, s);
+      else e = launch_dplane<T>(pass_args<T>(d, DP_LAST, ctl, 0), 0, s);
+    }
   } else if (pl.o.precond == UNOCG_PRECOND_UNO) {
     e = launch_dpass<T>(pass_args<T>(d, DP_MID, ctl, 0), DP_MID, s);
     if (e == cudaSuccess) e = launch_dpass<T>(pass_args<T>(d, DP_QMUL, ctl, 0), DP_QMUL, s);
@@ -415,7 +428,9 @@ DResArgs<T> res_args(unocg_dir* d, T* r, int only_pending) {
 // mixed precision: r = f - K u in FP64 for the pending pairs, then their residual check
 template <typename T>
 cudaError_t enq_replace(unocg_dir* d, cudaStream_t s, const DPlan& pl, const LoopCtl& ctl) {
-  cudaError_t e = launch_dres<T>(res_args<T>(d, (T*)dfields<T>(d).r, 1), s);
+  cudaError_t e = cudaSuccess;
+  if (sizeof(T) == 4) e = launch_dfold(d->g, d->c, d->B * d->L, d->u64, (float*)d->f32f.u, d->sc, 1, s);
+  if (e == cudaSuccess) e = launch_dres<T>(res_args<T>(d, (T*)dfields<T>(d).r, 1), s);
   if (e != cudaSuccess) return e;
   return enq_check<T>(d, s, pl, ctl, 1);
 }
@@ -423,7 +438,9 @@ cudaError_t enq_replace(unocg_dir* d, cudaStream_t s, const DPlan& pl, const Loo
 // reported true residual (max |f - K u| of the final iterate) and the averaged flux / stress
 template <typename T>
 cudaError_t enq_post(unocg_dir* d, cudaStream_t s) {
-  cudaError_t e = launch_dres<T>(res_args<T>(d, (T*)nullptr, 0), s);
+  cudaError_t e = cudaSuccess;
+  if (sizeof(T) == 4) e = launch_dfold(d->g, d->c, d->B * d->L, d->u64, (float*)d->f32f.u, d->sc, 0, s);
+  if (e == cudaSuccess) e = launch_dres<T>(res_args<T>(d, (T*)nullptr, 0), s);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(d->ceff, 0, (size_t)d->B * d->dim * d->L * sizeof(double), s);
   if (e != cudaSuccess) return e;
@@ -601,6 +618,8 @@ extern "C" int unocg_dir_create(unocg_dir** out, int physics, int batch, int n1,
     // solve; FP64 64^3 with 130 KB planes 30.0 vs 26.4 ms)
     d->plane[p] = dplane_smem_bytes(g, eb) <= 110 * 1024;
   }
+  d->plane_reg = dplane_reg_ok(g);
+  d->line_reg = dline_reg_ok(g, d->c);
   DCK(cudaStreamCreateWithFlags(&d->own_stream, cudaStreamNonBlocking));
   d->stream = d->own_stream;
   DCK(cudaMalloc(&d->phase, (size_t)batch * g.ne));
@@ -972,11 +991,14 @@ extern "C" int unocg_dir_apply_uno_dev(unocg_dir* d, int instance, const double*
   a.BL = 1; a.L = 1; a.standalone = 1; a.src = d->stage_a; a.hat = d->stage_b; a.out = d->stage_a;
   a.Q = d->Q64 + (d->Bq > 1 ? (size_t)instance * d->g.nf * (d->c == 1 ? 1 : 6) : 0);
   a.q_inst_stride = 0;
-  if (d->plane[0]) {
-    DCK(launch_dplane<double>(a, 1, s));
+  if (d->plane_reg || d->plane[0]) {
+    if (d->plane_reg) DCK(launch_dplane_reg<double>(a, 1, s));
+    else DCK(launch_dplane<double>(a, 1, s));
     a.lines = d->w1[0];
-    DCK(launch_dpass<double>(a, DP_QMUL, s));
-    DCK(launch_dplane<double>(a, 0, s));
+    if (d->line_reg) DCK(launch_dline_reg<double>(a, s));
+    else DCK(launch_dpass<double>(a, DP_QMUL, s));
+    if (d->plane_reg) DCK(launch_dplane_reg<double>(a, 0, s));
+    else DCK(launch_dplane<double>(a, 0, s));
   } else {
     a.lines = d->lines3[0];
     DCK(launch_dpass<double>(a, DP_FIRST, s));

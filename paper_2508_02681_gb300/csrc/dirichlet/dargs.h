@@ -41,7 +41,7 @@ template <typename T> struct DPassArgs {
   T* r;
   const T* q;
   T* p;
-  double* u64;
+  T* u;                    // solution (FP64 path) or its FP32 increment since the last fold
   const void* Q;           // unique entries [Bq][M1][M2][M3][C], type T (scaled, see above)
   long long q_inst_stride; // entries between instances (0: shared)
   CgScal* sc;
@@ -84,7 +84,7 @@ template <typename T> struct DJacArgs {
   T* r;
   const T* q;
   T* p;
-  double* u64;
+  T* u;                    // as DPassArgs::u
   const T* invdiag;        // [B][c][N1][N2][N3] (zero on the boundary) or nullptr (none)
   int L;
   CgScal* sc;
@@ -101,6 +101,7 @@ struct DInitArgs {
   const double* loads;     // [L][dim]
   double* f64;             // [BL][c][N1][N2][N3]
   double* u64;
+  void* u32;               // mixed precision: FP32 increment, zeroed (nullptr for FP64)
   void* r;                 // T: r = f
   void* p;                 // T: 0
   void* q;                 // T: 0
@@ -134,10 +135,20 @@ template <typename T> cudaError_t launch_dpass(const DPassArgs<T>& a, int mode, 
 // dplane_smem_bytes fits a block
 size_t dplane_smem_bytes(const DGrid& g, int elem_bytes);
 template <typename T> cudaError_t launch_dplane(const DPassArgs<T>& a, int fwd, cudaStream_t s);
+// register-resident versions (k_dirichlet_reg.cu): planes with N2 = N3 in {8, ..., 128}; axis 1
+// with the block multiply for c = 1 and N1 in {8, ..., 128}
+bool dplane_reg_ok(const DGrid& g);
+bool dline_reg_ok(const DGrid& g, int c);
+int dline_reg_blocks(const DGrid& g);
+template <typename T> cudaError_t launch_dplane_reg(const DPassArgs<T>& a, int fwd, cudaStream_t s);
+template <typename T> cudaError_t launch_dline_reg(const DPassArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_dku(const DKuArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_dres(const DResArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_djac(const DJacArgs<T>& a, int part, cudaStream_t s);
 cudaError_t launch_dinit(const DInitArgs& a, int BL, cudaStream_t s);
+// mixed precision: u64 += u32, u32 = 0 for the pending (only_pending) or all pairs
+cudaError_t launch_dfold(const DGrid& g, int c, int BL, double* u64, float* u32, const CgScal* sc, int only_pending,
+                         cudaStream_t s);
 cudaError_t launch_davg(const DAvgArgs& a, int B, cudaStream_t s);
 cudaError_t launch_ddiag(const DDiagArgs& a, int B, cudaStream_t s);
 int dku_blocks(const DGrid& g, int c);

@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kDThreads) k_dpass(DPassArgs<T> a) {
           if (upd) {
             x -= alpha * a.q[ga];
             a.r[ga] = x;
-            a.u64[ga] += s.alpha * (double)a.p[ga];
+            a.u[ga] += alpha * a.p[ga];
           }
           rm = rm > dabs(x) ? rm : dabs(x);
         }
@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(kDPlaneThreads) k_dplane(DPassArgs<T> a) {
           if (upd) {
             x -= alpha * a.q[ga];
             a.r[ga] = x;
-            a.u64[ga] += s.alpha * (double)a.p[ga];
+            a.u[ga] += alpha * a.p[ga];
           }
           rm = rm > dabs(x) ? rm : dabs(x);
           dput<T>(A, Pr, N3, j2, j3, x);
@@ -432,7 +432,7 @@ __global__ void __launch_bounds__(kDThreads) k_djac(DJacArgs<T> a) {
         if (upd) {
           x -= alpha * a.q[off + i];
           a.r[off + i] = x;
-          a.u64[off + i] += s.alpha * (double)a.p[off + i];
+          a.u[off + i] += alpha * a.p[off + i];
         }
         rm = rm > dabs(x) ? rm : dabs(x);
       } else {
@@ -495,6 +495,7 @@ __global__ void __launch_bounds__(kDThreads) k_dinit(DInitArgs a) {
       const long long k = o + i * g.ne;
       a.f64[k] = f[i];
       a.u64[k] = 0.0;
+      if (a.u32) ((float*)a.u32)[k] = 0.f;
       if (a.fp64) {
         ((double*)a.r)[k] = f[i];
         ((double*)a.p)[k] = 0.0;
@@ -563,6 +564,18 @@ __global__ void __launch_bounds__(kDThreads) k_davg(DAvgArgs a) {
   for (int i = 0; i < DIM; ++i) {
     const double s = block_sum(acc[i], red_sh);
     if (threadIdx.x == 0) atomicAdd(a.out + ((long long)b * DIM + i) * a.L + l, s / (double)g.ne);
+  }
+}
+
+// u64 += u32, u32 = 0 (mixed precision, before a replacement and at the end)
+__global__ void __launch_bounds__(kDThreads) k_dfold(DGrid g, int c, double* u64, float* u32, const CgScal* sc,
+                                                     int only_pending) {
+  const int bl = blockIdx.y;
+  if (only_pending && !sc[bl].need_replace) return;
+  const long long n = (long long)c * g.ne, off = (long long)bl * n;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    u64[off + i] += (double)u32[off + i];
+    u32[off + i] = 0.f;
   }
 }
 
@@ -711,6 +724,12 @@ cudaError_t launch_dplane(const DPassArgs<T>& a, int fwd, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   dim3 grid(a.c * a.g.m1, a.BL);
   kern<<<grid, kDPlaneThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dfold(const DGrid& g, int c, int BL, double* u64, float* u32, const CgScal* sc, int only_pending,
+                         cudaStream_t s) {
+  k_dfold<<<dim3(dgrid_blocks((long long)c * g.ne), BL), kDThreads, 0, s>>>(g, c, u64, u32, sc, only_pending);
   return cudaGetLastError();
 }
 

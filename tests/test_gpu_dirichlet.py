@@ -52,9 +52,11 @@ def test_apply_K_matches_oracle(physics, shape):
 
 
 @pytest.mark.parametrize("physics", [1, 3])
-@pytest.mark.parametrize("shape", SHAPES + [(32, 32, 32), (64, 48, 40), (8, 128, 128)])
+@pytest.mark.parametrize("shape", SHAPES + [(32, 32, 32), (64, 48, 40), (8, 128, 128), (6, 96, 160)])
 def test_reference_weights_and_apply_match_oracle(physics, shape):
-    # (8, 128, 128): planes too large for one block, separate axis-3 and axis-2 passes
+    # pass variants: register planes / axis 1 for power-of-two axes ((16,16,16), (32,32,32),
+    # (8,128,128)), shared-memory plane passes where a plane fits a block, separate axis-3 and
+    # axis-2 passes for the large non-power-of-two planes of (6, 96, 160)
     import torch
     from paper_2508_02681_gb300 import _lib, api
     c = 1 if physics == 1 else 3
@@ -133,7 +135,8 @@ def test_fp64_solve_matches_oracle(physics, shape, precond):
     h.close()
 
 
-@pytest.mark.parametrize("physics,shape", [(1, (16, 16, 16)), (3, (16, 16, 16)), (1, (32, 32, 32)), (1, (8, 128, 128))])
+@pytest.mark.parametrize("physics,shape", [(1, (16, 16, 16)), (3, (16, 16, 16)), (1, (32, 32, 32)), (1, (8, 128, 128)),
+                                           (1, (24, 20, 30)), (1, (6, 96, 160))])
 def test_mixed_solve_matches_oracle(physics, shape):
     from paper_2508_02681_gb300 import _lib
     phase, _ = rsa_spheres(shape, shape[0] / 5.0, 0.25, seed=13)
