@@ -265,6 +265,18 @@ int unocg_rhs_dev(unocg_ctx* ctx, int instance, int load, double* f_dev, void* s
 typedef struct unocg_dir unocg_dir;
 
 int unocg_dir_create(unocg_dir** out, int physics, int batch, int n1, int n2, int n3, double L0);
+/* Mixed boundary conditions (Sec. 6.2; Table (fnocg-mode-selection-2d), mixed row): bc[a] = 1
+   gives axis a Dirichlet faces, bc[a] = 0 makes the fluctuation periodic across them (at least
+   one axis Dirichlet; all periodic is unocg_create).  A periodic axis has N_a free nodes and
+   the Fourier transform as the UNO's transform along it, the paper's FFT^x o DST^y; the library
+   applies it through Hartley passes, which give the same operator T^H Q T for real blocks with
+   Q(-k) = Q(k) (k negated on every periodic axis): BLOCKS / THETA weights are made even that
+   way when set, and with two periodic axes a pass converts the separable Hartley spectrum to
+   the two-dimensional one around the block multiply.  unocg_dir_create is bc = {1, 1, 1}.
+   Reference weights: Q(k) = (t_k^H K_ref t_k)^-1 with t_k the Fourier x sine basis vector.
+   The mode layout (unocg_dir_set_uno_modes) needs bc = {1, 1, 1}.                          */
+int unocg_dir_create_bc(unocg_dir** out, int physics, int batch, int n1, int n2, int n3, double L0,
+                        const int* bc);
 void unocg_dir_destroy(unocg_dir* ctx);
 const char* unocg_dir_last_error(const unocg_dir* ctx);
 int unocg_dir_set_stream(unocg_dir* ctx, void* stream);

@@ -92,6 +92,7 @@ SIGNATURES = {
     "unocg_rhs_dev": (_i, [_vp, _i, _i, _vp, _vp]),
     # Dirichlet boundary conditions (sine transform)
     "unocg_dir_create": (_i, [C.POINTER(_vp), _i, _i, _i, _i, _i, _d]),
+    "unocg_dir_create_bc": (_i, [C.POINTER(_vp), _i, _i, _i, _i, _i, _d, _vp]),
     "unocg_dir_destroy": (None, [_vp]),
     "unocg_dir_last_error": (C.c_char_p, [_vp]),
     "unocg_dir_set_stream": (_i, [_vp, _vp]),

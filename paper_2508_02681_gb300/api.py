@@ -269,10 +269,15 @@ def _dcheck(ctx, rc):
         raise UnocgError(rc, msg)
 
 
-def unocg_dir_create(physics: int, batch: int, n1: int, n2: int, n3: int, L0: float = 1.0):
+def unocg_dir_create(physics: int, batch: int, n1: int, n2: int, n3: int, L0: float = 1.0, bc=None):
+    """``bc``: per axis 1 (Dirichlet faces) or 0 (periodic); None = Dirichlet on every axis."""
     lib = _lib.load()
     h = C.c_void_p()
-    rc = lib.unocg_dir_create(C.byref(h), physics, batch, n1, n2, n3, L0)
+    if bc is None:
+        rc = lib.unocg_dir_create(C.byref(h), physics, batch, n1, n2, n3, L0)
+    else:
+        b = np.ascontiguousarray([int(x) for x in bc], dtype=np.int32)
+        rc = lib.unocg_dir_create_bc(C.byref(h), physics, batch, n1, n2, n3, L0, _ptr(b))
     if rc != _lib.OK:
         msg = lib.unocg_dir_last_error(h).decode() if h.value else "invalid arguments or unsupported grid"
         if h.value:

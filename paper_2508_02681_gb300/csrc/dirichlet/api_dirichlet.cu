@@ -5,6 +5,7 @@
 // node; mixed precision adds a conditional IF node for the FP64 residual replacement.
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -92,6 +93,7 @@ struct unocg_dir {
   int lines3[2], w2[2], w1[2];  // [0] FP64, [1] FP32
   bool plane[2];                // axes 3 and 2 in one plane pass (the plane fits a block)
   bool plane_reg = false;       // register-resident plane passes (N2 = N3 a power of two)
+  int np = 0, pa = -1, pb = -1; // periodic axes (two: k_dmixq between the axis-1 passes)
   bool line_reg = false;        // register-resident axis-1 pass with Q (c = 1, N1 a power of two)
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -208,15 +210,19 @@ void reference_weights(const DGrid& g, int c, const double* mt, double* out) {
     }
   const int m[3] = {g.m1, g.m2, g.m3};
   const int n[3] = {g.n1, g.n2, g.n3};
-  std::vector<double> gd[3];
+  // per axis and offset d in {-1, 0, 1}: sum_j conj(t_k[j]) t_k[j + d] of the basis vector of
+  // mode k; sine basis (Dirichlet axis): 1 and cos(pi (k+1) / N); Fourier basis (periodic
+  // axis, the paper's transform): exp(-2 pi i k d / N)
+  std::vector<std::complex<double>> gd[3];
   for (int a = 0; a < 3; ++a) {
     gd[a].resize((size_t)m[a] * 3);
-    for (int k = 0; k < m[a]; ++k) {
-      const double cs = std::cos(M_PI * (double)(k + 1) / (double)n[a]);
-      gd[a][k * 3 + 0] = cs;
-      gd[a][k * 3 + 1] = 1.0;
-      gd[a][k * 3 + 2] = cs;
-    }
+    for (int k = 0; k < m[a]; ++k)
+      for (int d = -1; d <= 1; ++d) {
+        std::complex<double> v;
+        if (g.bc[a]) v = d == 0 ? 1.0 : std::cos(M_PI * (double)(k + 1) / (double)n[a]);
+        else v = std::polar(1.0, -2.0 * M_PI * (double)((long long)k * d) / (double)n[a]);
+        gd[a][k * 3 + d + 1] = v;
+      }
   }
   for (int k1 = 0; k1 < g.m1; ++k1)
     for (int k2 = 0; k2 < g.m2; ++k2)
@@ -225,7 +231,8 @@ void reference_weights(const DGrid& g, int c, const double* mt, double* out) {
         for (int s1 = 0; s1 < 3; ++s1)
           for (int s2 = 0; s2 < 3; ++s2)
             for (int s3 = 0; s3 < 3; ++s3) {
-              const double w = gd[0][k1 * 3 + s1] * gd[1][k2 * 3 + s2] * gd[2][k3 * 3 + s3];
+              // the imaginary parts cancel over +-d (symmetric stencil)
+              const double w = (gd[0][k1 * 3 + s1] * gd[1][k2 * 3 + s2] * gd[2][k3 * 3 + s3]).real();
               for (int i = 0; i < c; ++i)
                 for (int k = 0; k < c; ++k) Bk[i][k] += w * sten[s1][s2][s3][i][k];
             }
@@ -252,7 +259,10 @@ void reference_weights(const DGrid& g, int c, const double* mt, double* out) {
 int finish_weights(unocg_dir* d, double spd_eps) {
   const int C = d->c == 1 ? 1 : 6;
   const size_t m = (size_t)d->g.nf * C;
-  const double scale = 8.0 / ((double)d->g.n1 * d->g.n2 * d->g.n3);
+  // normalization of T^T Q T: 2 / N per sine axis, 1 / N per Hartley axis
+  double scale = 1.0;
+  const int ns[3] = {d->g.n1, d->g.n2, d->g.n3};
+  for (int a = 0; a < 3; ++a) scale *= (d->g.bc[a] ? 2.0 : 1.0) / ns[a];
   std::vector<double> s64(d->Qh.size());
   std::vector<float> s32(d->Qh.size());
   bool ok64 = true, ok32 = true;
@@ -300,6 +310,7 @@ int ensure_workspace(unocg_dir* d, int precision, int precond) {
   if (precond == UNOCG_PRECOND_JACOBI && !f.invdiag)
     DCK(cudaMalloc(&f.invdiag, (size_t)d->B * d->c * d->g.ne * eb));
   size_t need = (size_t)BL * std::max({(size_t)dku_blocks(d->g, d->c), (size_t)djac_blocks(d->g),
+                                       (size_t)(d->np == 2 ? dmixq_blocks(d->g, d->pa, d->pb) : 0),
                                        (size_t)(d->line_reg ? dline_reg_blocks(d->g) : 0),
                                        (size_t)dpass_blocks(d->g, d->c, DP_QMUL, std::min(d->w1[0], d->w1[1]))});
   if (d->part_len < need) {
@@ -325,7 +336,8 @@ DPassArgs<T> pass_args(unocg_dir* d, int mode, const LoopCtl& ctl, int after_rep
   DFields& f = dfields<T>(d);
   DPassArgs<T> a{};
   a.g = d->g; a.c = d->c; a.BL = d->B * d->L; a.L = d->L;
-  a.lines = mode == DP_MID ? d->w2[pidx<T>()] : mode == DP_QMUL ? d->w1[pidx<T>()] : d->lines3[pidx<T>()];
+  a.lines = mode == DP_MID ? d->w2[pidx<T>()]
+          : (mode == DP_QMUL || mode == DP_MID1) ? d->w1[pidx<T>()] : d->lines3[pidx<T>()];
   a.hat = (T*)f.hat; a.r = (T*)f.r; a.q = (const T*)f.q; a.p = (T*)f.p;
   a.u = sizeof(T) == 8 ? (T*)d->u64 : (T*)f.u;
   a.Q = sizeof(T) == 8 ? (const void*)d->Q64 : (const void*)d->Q32;
@@ -393,21 +405,37 @@ cudaError_t enq_ku(unocg_dir* d, cudaStream_t s) {
   return launch_dku<T>(ka, s);
 }
 
+// the transform passes between the forward plane pass (end of the previous iteration) and K p
+template <typename T>
+cudaError_t enq_precond(unocg_dir* d, cudaStream_t s, const LoopCtl& ctl, int standalone_lines_dummy = 0) {
+  (void)standalone_lines_dummy;
+  cudaError_t e = cudaSuccess;
+  const bool plane = d->plane_reg || d->plane[pidx<T>()];
+  if (!plane) e = launch_dpass<T>(pass_args<T>(d, DP_MID, ctl, 0), DP_MID, s);
+  if (e != cudaSuccess) return e;
+  if (d->np == 2) {
+    DPassArgs<T> m1 = pass_args<T>(d, DP_MID1, ctl, 0);
+    e = launch_dpass<T>(m1, DP_MID1, s);
+    if (e == cudaSuccess) e = launch_dmixq<T>(pass_args<T>(d, DP_QMUL, ctl, 0), d->pa, d->pb, s);
+    if (e == cudaSuccess) e = launch_dpass<T>(m1, DP_MID1, s);
+  } else if (d->line_reg) {
+    e = launch_dline_reg<T>(pass_args<T>(d, DP_QMUL, ctl, 0), s);
+  } else {
+    e = launch_dpass<T>(pass_args<T>(d, DP_QMUL, ctl, 0), DP_QMUL, s);
+  }
+  if (e != cudaSuccess) return e;
+  if (d->plane_reg) return launch_dplane_reg<T>(pass_args<T>(d, DP_LAST, ctl, 0), 0, s);
+  if (plane) return launch_dplane<T>(pass_args<T>(d, DP_LAST, ctl, 0), 0, s);
+  e = launch_dpass<T>(pass_args<T>(d, DP_MID, ctl, 0), DP_MID, s);
+  if (e == cudaSuccess) e = launch_dpass<T>(pass_args<T>(d, DP_LAST, ctl, 0), DP_LAST, s);
+  return e;
+}
+
 template <typename T>
 cudaError_t enq_body(unocg_dir* d, cudaStream_t s, const DPlan& pl, const LoopCtl& ctl) {
   cudaError_t e = cudaSuccess;
-  if (pl.o.precond == UNOCG_PRECOND_UNO && (d->plane_reg || d->plane[pidx<T>()])) {
-    if (d->line_reg) e = launch_dline_reg<T>(pass_args<T>(d, DP_QMUL, ctl, 0), s);
-    else e = launch_dpass<T>(pass_args<T>(d, DP_QMUL, ctl, 0), DP_QMUL, s);
-    if (e == cudaSuccess) {
-      if (d->plane_reg) e = launch_dplane_reg<T>(pass_args<T>(d, DP_LAST, ctl, 0), 0, s);
-      else e = launch_dplane<T>(pass_args<T>(d, DP_LAST, ctl, 0), 0, s);
-    }
-  } else if (pl.o.precond == UNOCG_PRECOND_UNO) {
-    e = launch_dpass<T>(pass_args<T>(d, DP_MID, ctl, 0), DP_MID, s);
-    if (e == cudaSuccess) e = launch_dpass<T>(pass_args<T>(d, DP_QMUL, ctl, 0), DP_QMUL, s);
-    if (e == cudaSuccess) e = launch_dpass<T>(pass_args<T>(d, DP_MID, ctl, 0), DP_MID, s);
-    if (e == cudaSuccess) e = launch_dpass<T>(pass_args<T>(d, DP_LAST, ctl, 0), DP_LAST, s);
+  if (pl.o.precond == UNOCG_PRECOND_UNO) {
+    e = enq_precond<T>(d, s, ctl);
   } else {
     e = launch_djac<T>(jac_args<T>(d, pl, ctl, 1, 0), 1, s);
     if (e == cudaSuccess) e = launch_djac<T>(jac_args<T>(d, pl, ctl, 2, 0), 2, s);
@@ -582,11 +610,15 @@ bool have_inputs(unocg_dir* d) { return d->phase_set && d->mat64 && d->L > 0; }
 }  // namespace
 
 // ------------------------------------------------------------------ create / destroy
-extern "C" int unocg_dir_create(unocg_dir** out, int physics, int batch, int n1, int n2, int n3, double L0) {
-  if (!out) return UNOCG_ERR_INVALID_ARG;
+extern "C" int unocg_dir_create_bc(unocg_dir** out, int physics, int batch, int n1, int n2, int n3, double L0,
+                                   const int* bc) {
+  if (!out || !bc) return UNOCG_ERR_INVALID_ARG;
   *out = nullptr;
   if ((physics != UNOCG_THERMAL && physics != UNOCG_ELASTIC) || batch < 1 || !(L0 > 0.0)) return UNOCG_ERR_INVALID_ARG;
   if (!dim_ok(n1) || !dim_ok(n2) || !dim_ok(n3)) return UNOCG_ERR_INVALID_ARG;
+  for (int a = 0; a < 3; ++a)
+    if (bc[a] != 0 && bc[a] != 1) return UNOCG_ERR_INVALID_ARG;
+  if (!bc[0] && !bc[1] && !bc[2]) return UNOCG_ERR_INVALID_ARG;  // all periodic: unocg_create
   unocg_dir* d = new unocg_dir();
   *out = d;
   d->physics = physics;
@@ -595,7 +627,17 @@ extern "C" int unocg_dir_create(unocg_dir** out, int physics, int batch, int n1,
   d->B = batch;
   DGrid& g = d->g;
   g.n1 = n1; g.n2 = n2; g.n3 = n3;
-  g.m1 = n1 - 1; g.m2 = n2 - 1; g.m3 = n3 - 1;
+  const int ns[3] = {n1, n2, n3};
+  for (int a = 0; a < 3; ++a) {
+    g.bc[a] = bc[a];
+    g.o[a] = bc[a];
+    if (!bc[a]) {
+      if (d->np == 0) d->pa = a;
+      else d->pb = a;
+      ++d->np;
+    }
+  }
+  g.m1 = n1 - bc[0]; g.m2 = n2 - bc[1]; g.m3 = n3 - bc[2];
   g.ne = (long long)n1 * n2 * n3;
   g.nf = (long long)g.m1 * g.m2 * g.m3;
   g.pg.n1 = n1; g.pg.n2 = n2; g.pg.n3 = n3; g.pg.n3h = n3 / 2 + 1;
@@ -603,11 +645,11 @@ extern "C" int unocg_dir_create(unocg_dir** out, int physics, int batch, int n1,
   g.pg.nh = (long long)n1 * n2 * (n3 / 2 + 1);
   g.pg.h = L0 / n1;
   grid_scales(g.pg);
-  const int ns[3] = {n1, n2, n3};
   for (int a = 0; a < 3; ++a) {
-    dfactor_plan(2 * ns[a], &d->plan[a]);
-    DCK(dupload_twiddles<double>(&d->tw64[a], 2 * ns[a]));
-    DCK(dupload_twiddles<float>(&d->tw32[a], 2 * ns[a]));
+    const int Lt = bc[a] ? 2 * ns[a] : ns[a];  // sine: odd-extended pairs; Hartley: plain pairs
+    dfactor_plan(Lt, &d->plan[a]);
+    DCK(dupload_twiddles<double>(&d->tw64[a], Lt));
+    DCK(dupload_twiddles<float>(&d->tw32[a], Lt));
   }
   for (int p = 0; p < 2; ++p) {
     const int eb = p == 0 ? 8 : 4;
@@ -618,8 +660,9 @@ extern "C" int unocg_dir_create(unocg_dir** out, int physics, int batch, int n1,
     // solve; FP64 64^3 with 130 KB planes 30.0 vs 26.4 ms)
     d->plane[p] = dplane_smem_bytes(g, eb) <= 110 * 1024;
   }
-  d->plane_reg = dplane_reg_ok(g);
-  d->line_reg = dline_reg_ok(g, d->c);
+  const bool all_dir = bc[0] && bc[1] && bc[2];
+  d->plane_reg = all_dir && dplane_reg_ok(g);
+  d->line_reg = all_dir && dline_reg_ok(g, d->c);
   DCK(cudaStreamCreateWithFlags(&d->own_stream, cudaStreamNonBlocking));
   d->stream = d->own_stream;
   DCK(cudaMalloc(&d->phase, (size_t)batch * g.ne));
@@ -627,8 +670,12 @@ extern "C" int unocg_dir_create(unocg_dir** out, int physics, int batch, int n1,
   DCK(cudaMemset(d->tickets, 0, DT_N * sizeof(unsigned int)));
   DCK(cudaMalloc(&d->flags, 8 * sizeof(int)));
   DCK(cudaMemset(d->flags, 0, 8 * sizeof(int)));
-  d->phase_set = false;
   return UNOCG_OK;
+}
+
+extern "C" int unocg_dir_create(unocg_dir** out, int physics, int batch, int n1, int n2, int n3, double L0) {
+  const int bc[3] = {1, 1, 1};
+  return unocg_dir_create_bc(out, physics, batch, n1, n2, n3, L0, bc);
 }
 
 extern "C" void unocg_dir_destroy(unocg_dir* d) {
@@ -770,12 +817,31 @@ extern "C" int unocg_dir_set_uno_weights(unocg_dir* d, int kind, const void* w, 
       for (int k = 0; k < C; ++k) d->Qh[i + k] = v[k];
     }
   }
+  if (d->np > 0) {
+    // conjugate modes of the periodic axes: Q(k) <- (Q(k) + Q(-k)) / 2, -k negating every
+    // periodic index (the condition for a real output of the paper's Fourier-domain operator,
+    // under which the Hartley passes apply the same operator)
+    const int m[3] = {d->g.m1, d->g.m2, d->g.m3};
+    std::vector<double> sym(d->Qh.size());
+    for (int k1 = 0; k1 < m[0]; ++k1)
+      for (int k2 = 0; k2 < m[1]; ++k2)
+        for (int k3 = 0; k3 < m[2]; ++k3) {
+          const int q1 = d->g.bc[0] ? k1 : (m[0] - k1) % m[0];
+          const int q2 = d->g.bc[1] ? k2 : (m[1] - k2) % m[1];
+          const int q3 = d->g.bc[2] ? k3 : (m[2] - k3) % m[2];
+          const size_t i = (((size_t)k1 * m[1] + k2) * m[2] + k3) * C;
+          const size_t j = (((size_t)q1 * m[1] + q2) * m[2] + q3) * C;
+          for (int e = 0; e < C; ++e) sym[i + e] = 0.5 * (d->Qh[i + e] + d->Qh[j + e]);
+        }
+    d->Qh.swap(sym);
+  }
   d->wkind = kind;
   return finish_weights(d, spd_eps);
 }
 
 extern "C" int unocg_dir_set_uno_modes(unocg_dir* d, int M, const void* w, int dtype, double spd_eps) {
   if (!d || !w || (dtype != UNOCG_DTYPE_F64 && dtype != UNOCG_DTYPE_F32)) return dfail(d, UNOCG_ERR_INVALID_ARG, "invalid weights");
+  if (d->np > 0) return dfail(d, UNOCG_ERR_INVALID_ARG, "the mode layout needs Dirichlet faces on every axis");
   if (M < 0 || 2 * M + 1 > d->g.m1 || 2 * M + 1 > d->g.m2 || 2 * M + 1 > d->g.m3)
     return dfail(d, UNOCG_ERR_INVALID_ARG, "mode set [0, 2M]^3 larger than the free grid");
   const int C = d->c == 1 ? 1 : 6;
@@ -991,25 +1057,32 @@ extern "C" int unocg_dir_apply_uno_dev(unocg_dir* d, int instance, const double*
   a.BL = 1; a.L = 1; a.standalone = 1; a.src = d->stage_a; a.hat = d->stage_b; a.out = d->stage_a;
   a.Q = d->Q64 + (d->Bq > 1 ? (size_t)instance * d->g.nf * (d->c == 1 ? 1 : 6) : 0);
   a.q_inst_stride = 0;
-  if (d->plane_reg || d->plane[0]) {
-    if (d->plane_reg) DCK(launch_dplane_reg<double>(a, 1, s));
-    else DCK(launch_dplane<double>(a, 1, s));
-    a.lines = d->w1[0];
-    if (d->line_reg) DCK(launch_dline_reg<double>(a, s));
-    else DCK(launch_dpass<double>(a, DP_QMUL, s));
-    if (d->plane_reg) DCK(launch_dplane_reg<double>(a, 0, s));
-    else DCK(launch_dplane<double>(a, 0, s));
+  auto with = [&](int lines) {
+    DPassArgs<double> b = a;
+    b.lines = lines;
+    return b;
+  };
+  const bool plane = d->plane_reg || d->plane[0];
+  if (d->plane_reg) DCK(launch_dplane_reg<double>(a, 1, s));
+  else if (plane) DCK(launch_dplane<double>(a, 1, s));
+  else {
+    DCK(launch_dpass<double>(with(d->lines3[0]), DP_FIRST, s));
+    DCK(launch_dpass<double>(with(d->w2[0]), DP_MID, s));
+  }
+  if (d->np == 2) {
+    DCK(launch_dpass<double>(with(d->w1[0]), DP_MID1, s));
+    DCK(launch_dmixq<double>(a, d->pa, d->pb, s));
+    DCK(launch_dpass<double>(with(d->w1[0]), DP_MID1, s));
+  } else if (d->line_reg) {
+    DCK(launch_dline_reg<double>(a, s));
   } else {
-    a.lines = d->lines3[0];
-    DCK(launch_dpass<double>(a, DP_FIRST, s));
-    a.lines = d->w2[0];
-    DCK(launch_dpass<double>(a, DP_MID, s));
-    a.lines = d->w1[0];
-    DCK(launch_dpass<double>(a, DP_QMUL, s));
-    a.lines = d->w2[0];
-    DCK(launch_dpass<double>(a, DP_MID, s));
-    a.lines = d->lines3[0];
-    DCK(launch_dpass<double>(a, DP_LAST, s));
+    DCK(launch_dpass<double>(with(d->w1[0]), DP_QMUL, s));
+  }
+  if (d->plane_reg) DCK(launch_dplane_reg<double>(a, 0, s));
+  else if (plane) DCK(launch_dplane<double>(a, 0, s));
+  else {
+    DCK(launch_dpass<double>(with(d->w2[0]), DP_MID, s));
+    DCK(launch_dpass<double>(with(d->lines3[0]), DP_LAST, s));
   }
   DCK(launch_dgather(d->g, d->c, d->stage_a, s_dev, s));
   return UNOCG_OK;

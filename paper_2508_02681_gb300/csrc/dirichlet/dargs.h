@@ -28,6 +28,7 @@ enum DPassMode {
   DP_MID = 1,    // axis 2, either direction: DST in place
   DP_QMUL = 2,   // axis 1: DST, s_hat = Q r_hat, gamma = r.s, DST, beta
   DP_LAST = 3,   // axis 3, inverse: DST, p = s + beta p (or s written out)
+  DP_MID1 = 4,   // axis 1 without the block multiply (two periodic axes: see k_dmixq)
 };
 
 template <typename T> struct DPassArgs {
@@ -143,6 +144,9 @@ int dline_reg_blocks(const DGrid& g);
 template <typename T> cudaError_t launch_dplane_reg(const DPassArgs<T>& a, int fwd, cudaStream_t s);
 template <typename T> cudaError_t launch_dline_reg(const DPassArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_dku(const DKuArgs<T>& a, cudaStream_t s);
+// two periodic axes pa < pb: s_hat = B Q B r_hat on the separable Hartley spectrum (k_dmixq)
+int dmixq_blocks(const DGrid& g, int pa, int pb);
+template <typename T> cudaError_t launch_dmixq(const DPassArgs<T>& a, int pa, int pb, cudaStream_t s);
 template <typename T> cudaError_t launch_dres(const DResArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_djac(const DJacArgs<T>& a, int part, cudaStream_t s);
 cudaError_t launch_dinit(const DInitArgs& a, int BL, cudaStream_t s);

@@ -15,9 +15,14 @@
 
 namespace unocg {
 
+// Boundary conditions per axis (mixed BC, Sec. 6.2): an axis with bc[a] = 1 has Dirichlet faces
+// (node 0 held at zero, N_a - 1 free nodes, offset o_a = 1); bc[a] = 0 is periodic (all N_a
+// nodes free, o_a = 0).  The same embedding serves every combination.
 struct DGrid {
   int n1, n2, n3;   // voxels per axis (= nodes per axis of the embedding grid)
-  int m1, m2, m3;   // free nodes per axis
+  int m1, m2, m3;   // free nodes per axis (N - 1 Dirichlet, N periodic)
+  int bc[3];        // 1: Dirichlet faces along the axis, 0: periodic
+  int o[3];         // free index j is node j + o (o = bc)
   long long ne;     // voxels = nodes of the embedding grid (field stride per component)
   long long nf;     // free nodes
   Grid pg;          // the embedding grid as a periodic grid (stencil functions)
@@ -27,17 +32,21 @@ struct DGrid {
 __device__ __forceinline__ long long dnode_of_free(const DGrid& g, long long f, int& i1, int& i2, int& i3) {
   const int j3 = (int)(f % g.m3);
   const long long r = f / g.m3;
-  i2 = (int)(r % g.m2) + 1;
-  i1 = (int)(r / g.m2) + 1;
-  i3 = j3 + 1;
+  i2 = (int)(r % g.m2) + g.o[1];
+  i1 = (int)(r / g.m2) + g.o[0];
+  i3 = j3 + g.o[2];
   return ((long long)i1 * g.n2 + i2) * g.n3 + i3;
+}
+
+__device__ __forceinline__ bool dfree_node(const DGrid& g, int i1, int i2, int i3) {
+  return !(g.bc[0] && i1 == 0) && !(g.bc[1] && i2 == 0) && !(g.bc[2] && i3 == 0);
 }
 
 __device__ __forceinline__ bool dinterior(const DGrid& g, long long node) {
   const int i3 = (int)(node % g.n3);
   const long long r = node / g.n3;
   const int i2 = (int)(r % g.n2), i1 = (int)(r / g.n2);
-  return i1 != 0 && i2 != 0 && i3 != 0;
+  return dfree_node(g, i1, i2, i3);
 }
 
 }  // namespace unocg

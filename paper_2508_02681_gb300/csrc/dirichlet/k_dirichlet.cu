@@ -37,7 +37,7 @@ __device__ __forceinline__ DTile dtile(const DGrid& g, int c, int ax, int lines,
   d.ax = ax;
   d.lines = ax == 1 ? c * lines : lines;
   d.W = lines;
-  d.M = (ax == 3 ? g.n3 : ax == 2 ? g.n2 : g.n1) - 1;
+  d.M = ax == 3 ? g.m3 : ax == 2 ? g.m2 : g.m1;  // free points per line
   d.row0 = 0; d.rows = 0; d.i1 = d.i2 = d.comp = d.i30 = 0;
   const int nb3 = (g.m3 + lines - 1) / lines;
   if (ax == 3) {
@@ -55,22 +55,23 @@ __device__ __forceinline__ DTile dtile(const DGrid& g, int c, int ax, int lines,
   return d;
 }
 
-// embedding-grid index of interior point j of line l, or -1 when the line lies outside the
-// field (free node j is node j + 1 on every axis)
+// embedding-grid index of free point j of line l, or -1 when the line lies outside the field
+// (free index j is node j + o_a on axis a)
 __device__ __forceinline__ long long daddr(const DGrid& g, const DTile& d, int l, int j) {
+  const int o1 = g.o[0], o2 = g.o[1], o3 = g.o[2];
   if (d.ax == 3) {
     const long long row = d.row0 + l;
     if (row >= d.rows) return -1LL;
     const int comp = (int)(row / ((long long)g.m1 * g.m2));
     const int r2 = (int)(row - (long long)comp * g.m1 * g.m2);
     const int j1 = r2 / g.m2, j2 = r2 - j1 * g.m2;
-    return d.base + (((long long)comp * g.n1 + j1 + 1) * g.n2 + j2 + 1) * g.n3 + j + 1;
+    return d.base + (((long long)comp * g.n1 + j1 + o1) * g.n2 + j2 + o2) * g.n3 + j + o3;
   }
   const int w = l % d.W, grp = l / d.W;
   const int i3 = d.i30 + w;
   if (i3 >= g.m3) return -1LL;
-  if (d.ax == 2) return d.base + (((long long)d.comp * g.n1 + d.i1 + 1) * g.n2 + j + 1) * g.n3 + i3 + 1;
-  return d.base + (((long long)grp * g.n1 + j + 1) * g.n2 + d.i2 + 1) * g.n3 + i3 + 1;
+  if (d.ax == 2) return d.base + (((long long)d.comp * g.n1 + d.i1 + o1) * g.n2 + j + o2) * g.n3 + i3 + o3;
+  return d.base + (((long long)grp * g.n1 + j + o1) * g.n2 + d.i2 + o2) * g.n3 + i3 + o3;
 }
 
 // element (l, j) of the loop over a tile: j fastest along axis 3 (contiguous rows), the
@@ -86,22 +87,30 @@ __device__ __forceinline__ void dtile_item(const DTile& d, int idx, int& l, int&
   }
 }
 
-// store value x of line l at point j (0 <= j < N - 1) into the odd-extended pair buffer
+// Pair buffers of one axis with N voxels: line l of a pair in the real (l even) or imaginary
+// (l odd) part.  Sine transform (Dirichlet axis, dst = true): N - 1 points odd-extended to a
+// complex sequence of 2N, X[k] = -Im Z[k+1] / 2 (even l), Re Z[k+1] / 2 (odd l).  Hartley
+// transform (periodic axis): N points as they are, H = Re A - Im A of the line's own DFT A,
+// A = (Z[k] + conj Z[-k]) / 2 (even l) or (Z[k] - conj Z[-k]) / 2i (odd l).
 template <typename T>
-__device__ __forceinline__ void dput(cplx<T>* buf, int P, int N, int l, int j, T x) {
-  T* a = reinterpret_cast<T*>(buf + (long long)(j + 1) * P + (l >> 1)) + (l & 1);
-  T* b = reinterpret_cast<T*>(buf + (long long)(2 * N - 1 - j) * P + (l >> 1)) + (l & 1);
+__device__ __forceinline__ void dput(cplx<T>* buf, int P, int N, int l, int j, T x, bool dst = true) {
+  T* a = reinterpret_cast<T*>(buf + (long long)(dst ? j + 1 : j) * P + (l >> 1)) + (l & 1);
   *a = x;
-  *b = -x;
-}
-// unnormalized DST coefficient k of line l from the transformed pair buffer
-template <typename T>
-__device__ __forceinline__ T dget(const cplx<T>* buf, int P, int l, int k) {
-  const cplx<T> z = buf[(long long)(k + 1) * P + (l >> 1)];
-  return (l & 1) ? (T)0.5 * z.x : (T)-0.5 * z.y;
+  if (dst) *(reinterpret_cast<T*>(buf + (long long)(2 * N - 1 - j) * P + (l >> 1)) + (l & 1)) = -x;
 }
 template <typename T>
-__device__ __forceinline__ void dzero_ends(cplx<T>* buf, int P, int N) {
+__device__ __forceinline__ T dget(const cplx<T>* buf, int P, int l, int k, bool dst = true, int N = 0) {
+  if (dst) {
+    const cplx<T> z = buf[(long long)(k + 1) * P + (l >> 1)];
+    return (l & 1) ? (T)0.5 * z.x : (T)-0.5 * z.y;
+  }
+  const cplx<T> z = buf[(long long)k * P + (l >> 1)];
+  const cplx<T> w = buf[(long long)(k == 0 ? 0 : N - k) * P + (l >> 1)];
+  return (l & 1) ? (T)0.5 * ((z.y + w.y) - (w.x - z.x)) : (T)0.5 * ((z.x + w.x) - (z.y - w.y));
+}
+template <typename T>
+__device__ __forceinline__ void dzero_ends(cplx<T>* buf, int P, int N, bool dst = true) {
+  if (!dst) return;
   for (int m = threadIdx.x; m < P; m += blockDim.x) {
     buf[m] = mk<T>((T)0, (T)0);
     buf[(long long)N * P + m] = mk<T>((T)0, (T)0);
@@ -127,11 +136,14 @@ template <typename T, int MODE, int CC>
 __global__ void __launch_bounds__(kDThreads) k_dpass(DPassArgs<T> a) {
   using C = cplx<T>;
   constexpr int AX = (MODE == DP_FIRST || MODE == DP_LAST) ? 3 : (MODE == DP_MID ? 2 : 1);
+  static_assert(MODE != DP_MID1 || AX == 1, "axis of the plain axis-1 pass");
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ double red_sh[32];
   const DGrid& g = a.g;
   const int bl = blockIdx.y;
   const int N = AX == 3 ? g.n3 : (AX == 2 ? g.n2 : g.n1);
+  const bool dst = g.bc[AX - 1] != 0;  // sine (Dirichlet axis) or Hartley (periodic axis)
+  const int Lt = dst ? 2 * N : N;      // transform length
   const DTile d = dtile(g, CC, AX, a.lines, bl, blockIdx.x);
   const int P = d.lines >> 1;
   C* A = reinterpret_cast<C*>(dsm);
@@ -145,8 +157,8 @@ __global__ void __launch_bounds__(kDThreads) k_dpass(DPassArgs<T> a) {
   }
   double bval = 0.0;  // rmax (DP_FIRST) or gamma partial (DP_QMUL)
   if (active) {
-    load_tw<T>(tw, a.t.tw[AX - 1], 2 * N);
-    dzero_ends<T>(A, P, N);
+    load_tw<T>(tw, a.t.tw[AX - 1], Lt);
+    dzero_ends<T>(A, P, N, dst);
     const int total = d.lines * d.M;
     if (MODE == DP_FIRST && !a.standalone) {
       const CgScal& s = a.sc[bl];
@@ -167,7 +179,7 @@ __global__ void __launch_bounds__(kDThreads) k_dpass(DPassArgs<T> a) {
           }
           rm = rm > dabs(x) ? rm : dabs(x);
         }
-        dput<T>(A, P, N, l, j, x);
+        dput<T>(A, P, N, l, j, x, dst);
       }
       bval = (double)rm;
     } else {
@@ -176,22 +188,22 @@ __global__ void __launch_bounds__(kDThreads) k_dpass(DPassArgs<T> a) {
         int l, j;
         dtile_item(d, idx, l, j);
         const long long ga = daddr(g, d, l, j);
-        dput<T>(A, P, N, l, j, ga >= 0 ? src[ga] : (T)0);
+        dput<T>(A, P, N, l, j, ga >= 0 ? src[ga] : (T)0, dst);
       }
     }
     __syncthreads();
     C* res = fft_lines<T, -1>(A, B, P, 1, P, a.t.p[AX - 1], tw);
     if (MODE == DP_QMUL) {
-      // block multiply on the modes (k1, k2 = i2, k3 = i3) of this tile, then the second DST
+      // block multiply on the modes (k1, k2 = i2, k3 = i3) of this tile, then the second transform
       C* oth = res == A ? B : A;
-      dzero_ends<T>(oth, P, N);
+      dzero_ends<T>(oth, P, N, dst);
       DotAcc<T> acc;
       const int W = d.W;
       for (int idx = threadIdx.x; idx < W * d.M; idx += blockDim.x) {
         const int w = idx % W, k = idx / W;
         T x[CC], y[CC];
 #pragma unroll
-        for (int i = 0; i < CC; ++i) x[i] = dget<T>(res, P, i * W + w, k);
+        for (int i = 0; i < CC; ++i) x[i] = dget<T>(res, P, i * W + w, k, dst, N);
         const int i3 = d.i30 + w;
         if (i3 < g.m3) {
           const long long mode = ((long long)k * g.m2 + d.i2) * g.m3 + i3;
@@ -205,7 +217,7 @@ __global__ void __launch_bounds__(kDThreads) k_dpass(DPassArgs<T> a) {
           for (int i = 0; i < CC; ++i) y[i] = (T)0;
         }
 #pragma unroll
-        for (int i = 0; i < CC; ++i) dput<T>(oth, P, N, i * W + w, k, y[i]);
+        for (int i = 0; i < CC; ++i) dput<T>(oth, P, N, i * W + w, k, y[i], dst);
       }
       bval = block_sum_acc(acc, red_sh);
       __syncthreads();
@@ -216,7 +228,7 @@ __global__ void __launch_bounds__(kDThreads) k_dpass(DPassArgs<T> a) {
       dtile_item(d, idx, l, j);
       const long long ga = daddr(g, d, l, j);
       if (ga < 0) continue;
-      const T x = dget<T>(res, P, l, j);
+      const T x = dget<T>(res, P, l, j, dst, N);
       if (MODE == DP_LAST) {
         if (a.standalone) a.out[ga] = x;
         else a.p[ga] = x + (T)a.sc[bl].beta * a.p[ga];
@@ -266,6 +278,7 @@ __global__ void __launch_bounds__(kDPlaneThreads) k_dplane(DPassArgs<T> a) {
   const int c = a.c;
   const int comp = blockIdx.x / g.m1, j1 = blockIdx.x - comp * g.m1;
   const int N2 = g.n2, N3 = g.n3, M2 = g.m2, M3 = g.m3;
+  const bool d2 = g.bc[1] != 0, d3 = g.bc[2] != 0;  // sine or Hartley per axis
   const int Pr = (M2 + 1) >> 1, Pc = (M3 + 1) >> 1;
   const long long half = (long long)(2 * N3 * Pr > 2 * N2 * Pc ? 2 * N3 * Pr : 2 * N2 * Pc);
   C* A = reinterpret_cast<C*>(dsm);
@@ -273,8 +286,8 @@ __global__ void __launch_bounds__(kDPlaneThreads) k_dplane(DPassArgs<T> a) {
   C* tw3 = B + half;
   C* tw2 = tw3 + 2 * N3;
   // element (j2, j3) of the plane
-  const long long base = (long long)bl * c * g.ne + ((long long)comp * g.n1 + j1 + 1) * g.n2 * g.n3;
-  auto at = [&](int j2, int j3) { return base + (long long)(j2 + 1) * N3 + j3 + 1; };
+  const long long base = (long long)bl * c * g.ne + ((long long)comp * g.n1 + j1 + g.o[0]) * g.n2 * g.n3;
+  auto at = [&](int j2, int j3) { return base + (long long)(j2 + g.o[1]) * N3 + j3 + g.o[2]; };
 
   bool active = true;
   if (!a.standalone) {
@@ -283,14 +296,14 @@ __global__ void __launch_bounds__(kDPlaneThreads) k_dplane(DPassArgs<T> a) {
   }
   double bval = 0.0;
   if (active) {
-    load_tw<T>(tw3, a.t.tw[2], 2 * N3);
-    load_tw<T>(tw2, a.t.tw[1], 2 * N2);
+    load_tw<T>(tw3, a.t.tw[2], d3 ? 2 * N3 : N3);
+    load_tw<T>(tw2, a.t.tw[1], d2 ? 2 * N2 : N2);
     const int total = M2 * M3;
     if (FWD) {
       // rows into A: line j2 (pair j2 / 2), point j3
-      dzero_ends<T>(A, Pr, N3);
+      dzero_ends<T>(A, Pr, N3, d3);
       if (M2 & 1)  // the unpaired last row: its partner line is zero
-        for (int j = threadIdx.x; j < M3; j += blockDim.x) dput<T>(A, Pr, N3, M2, j, (T)0);
+        for (int j = threadIdx.x; j < M3; j += blockDim.x) dput<T>(A, Pr, N3, M2, j, (T)0, d3);
       if (!a.standalone) {
         const CgScal& s = a.sc[bl];
         const T alpha = (T)s.alpha;
@@ -306,50 +319,50 @@ __global__ void __launch_bounds__(kDPlaneThreads) k_dplane(DPassArgs<T> a) {
             a.u[ga] += alpha * a.p[ga];
           }
           rm = rm > dabs(x) ? rm : dabs(x);
-          dput<T>(A, Pr, N3, j2, j3, x);
+          dput<T>(A, Pr, N3, j2, j3, x, d3);
         }
         bval = (double)rm;
       } else {
         for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
           const int j2 = idx / M3, j3 = idx - j2 * M3;
-          dput<T>(A, Pr, N3, j2, j3, a.src[at(j2, j3)]);
+          dput<T>(A, Pr, N3, j2, j3, a.src[at(j2, j3)], d3);
         }
       }
       __syncthreads();
       C* res = fft_lines<T, -1>(A, B, Pr, 1, Pr, a.t.p[2], tw3);
       C* oth = res == A ? B : A;
       // columns: line k3 (pair k3 / 2), point j2
-      dzero_ends<T>(oth, Pc, N2);
+      dzero_ends<T>(oth, Pc, N2, d2);
       if (M3 & 1)
-        for (int j = threadIdx.x; j < M2; j += blockDim.x) dput<T>(oth, Pc, N2, M3, j, (T)0);
+        for (int j = threadIdx.x; j < M2; j += blockDim.x) dput<T>(oth, Pc, N2, M3, j, (T)0, d2);
       for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
         const int j2 = idx / M3, k3 = idx - j2 * M3;
-        dput<T>(oth, Pc, N2, k3, j2, dget<T>(res, Pr, j2, k3));
+        dput<T>(oth, Pc, N2, k3, j2, dget<T>(res, Pr, j2, k3, d3, N3), d2);
       }
       __syncthreads();
       res = fft_lines<T, -1>(oth, res, Pc, 1, Pc, a.t.p[1], tw2);
       for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
         const int k2 = idx / M3, k3 = idx - k2 * M3;
-        a.hat[at(k2, k3)] = dget<T>(res, Pc, k3, k2);
+        a.hat[at(k2, k3)] = dget<T>(res, Pc, k3, k2, d2, N2);
       }
     } else {
       // columns of hat into A: line k3, point k2
-      dzero_ends<T>(A, Pc, N2);
+      dzero_ends<T>(A, Pc, N2, d2);
       if (M3 & 1)
-        for (int j = threadIdx.x; j < M2; j += blockDim.x) dput<T>(A, Pc, N2, M3, j, (T)0);
+        for (int j = threadIdx.x; j < M2; j += blockDim.x) dput<T>(A, Pc, N2, M3, j, (T)0, d2);
       for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
         const int k2 = idx / M3, k3 = idx - k2 * M3;
-        dput<T>(A, Pc, N2, k3, k2, a.hat[at(k2, k3)]);
+        dput<T>(A, Pc, N2, k3, k2, a.hat[at(k2, k3)], d2);
       }
       __syncthreads();
       C* res = fft_lines<T, -1>(A, B, Pc, 1, Pc, a.t.p[1], tw2);
       C* oth = res == A ? B : A;
-      dzero_ends<T>(oth, Pr, N3);
+      dzero_ends<T>(oth, Pr, N3, d3);
       if (M2 & 1)
-        for (int j = threadIdx.x; j < M3; j += blockDim.x) dput<T>(oth, Pr, N3, M2, j, (T)0);
+        for (int j = threadIdx.x; j < M3; j += blockDim.x) dput<T>(oth, Pr, N3, M2, j, (T)0, d3);
       for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
         const int j2 = idx / M3, k3 = idx - j2 * M3;
-        dput<T>(oth, Pr, N3, j2, k3, dget<T>(res, Pc, k3, j2));
+        dput<T>(oth, Pr, N3, j2, k3, dget<T>(res, Pc, k3, j2, d2, N2), d3);
       }
       __syncthreads();
       res = fft_lines<T, -1>(oth, res, Pr, 1, Pr, a.t.p[2], tw3);
@@ -357,7 +370,7 @@ __global__ void __launch_bounds__(kDPlaneThreads) k_dplane(DPassArgs<T> a) {
       for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
         const int j2 = idx / M3, j3 = idx - j2 * M3;
         const long long ga = at(j2, j3);
-        const T x = dget<T>(res, Pr, j2, j3);
+        const T x = dget<T>(res, Pr, j2, j3, d3, N3);
         if (a.standalone) a.out[ga] = x;
         else a.p[ga] = x + beta * a.p[ga];
       }
@@ -368,6 +381,95 @@ __global__ void __launch_bounds__(kDPlaneThreads) k_dplane(DPassArgs<T> a) {
   if (threadIdx.x == 0 && active) atomic_max_nonneg(&a.sc[bl].rmax_bits, bm);
   if (last_block(a.red.ticket)) {
     residual_decision(a.sc, a.BL, a.ctl, a.after_replace);
+    if (threadIdx.x == 0) *a.red.ticket = 0u;
+  }
+}
+
+// ============================================================================ two periodic axes
+// With periodic axes a < b the separable Hartley passes give H = (H_a x H_b) r, whose basis
+// functions cas(k_a x_a) cas(k_b x_b) are not those of the Fourier transform the paper uses
+// along both axes.  The true two-dimensional Hartley coefficients, cas(k_a x_a + k_b x_b), are
+// T = B H over the four modes (+-k_a, +-k_b) with the orthogonal involution
+// B = 1/2 [[1, 1, 1, -1], [1, 1, -1, 1], [1, -1, 1, 1], [-1, 1, 1, 1]] in the order
+// (++, -+, +-, --).  For real blocks with Q(-k) = Q(k) (conjugate modes) T^T Q T equals the
+// Fourier-domain F^H Q F, so this pass applies s_hat = B Q B r_hat with gamma = r.s (Parseval;
+// coinciding mirror modes counted once).  One thread per canonical quadruple and third-axis mode.
+template <typename T, int CC>
+__global__ void __launch_bounds__(kDThreads) k_dmixq(DPassArgs<T> a, int pa, int pb) {
+  __shared__ double red_sh[32];
+  const DGrid& g = a.g;
+  const int bl = blockIdx.y;
+  const int n[3] = {g.n1, g.n2, g.n3};
+  const int m[3] = {g.m1, g.m2, g.m3};
+  const int pc = 3 - pa - pb;  // the Dirichlet axis
+  const int ha = n[pa] / 2 + 1, hb = n[pb] / 2 + 1;
+  const long long total = (long long)ha * hb * m[pc];
+  const bool active = a.standalone || !a.sc[bl].done;
+  DotAcc<T> acc;
+  if (active) {
+    const T* Qb = reinterpret_cast<const T*>(a.Q) + (long long)(bl / a.L) * a.q_inst_stride;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+      const int kc = (int)(t % m[pc]);
+      const long long r = t / m[pc];
+      const int kb = (int)(r % hb), ka = (int)(r / hb);
+      const int kam = ka ? n[pa] - ka : 0, kbm = kb ? n[pb] - kb : 0;
+      const T wgt = (T)((ka == kam ? 0.5 : 1.0) * (kb == kbm ? 0.5 : 1.0));
+      long long node[4], mode[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        int k[3];
+        k[pa] = (q & 1) ? kam : ka;
+        k[pb] = (q & 2) ? kbm : kb;
+        k[pc] = kc;
+        mode[q] = ((long long)k[0] * g.m2 + k[1]) * g.m3 + k[2];
+        node[q] = ((long long)(k[0] + g.o[0]) * g.n2 + k[1] + g.o[1]) * g.n3 + k[2] + g.o[2];
+      }
+      const long long fb = (long long)bl * CC * g.ne;
+      T h[4][CC], y[4][CC];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int i = 0; i < CC; ++i) h[q][i] = a.hat[fb + i * g.ne + node[q]];
+      // T = B H
+      T tt[4][CC];
+#pragma unroll
+      for (int i = 0; i < CC; ++i) {
+        tt[0][i] = (T)0.5 * (h[0][i] + h[1][i] + h[2][i] - h[3][i]);
+        tt[1][i] = (T)0.5 * (h[0][i] + h[1][i] - h[2][i] + h[3][i]);
+        tt[2][i] = (T)0.5 * (h[0][i] - h[1][i] + h[2][i] + h[3][i]);
+        tt[3][i] = (T)0.5 * (-h[0][i] + h[1][i] + h[2][i] + h[3][i]);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        qmul<T, CC>(Qb + mode[q] * (CC == 1 ? 1 : 6), tt[q], y[q]);
+#pragma unroll
+        for (int i = 0; i < CC; ++i) acc.add_prod(tt[q][i], wgt * y[q][i]);
+      }
+      // s_hat = B Y (coinciding modes receive identical values)
+#pragma unroll
+      for (int i = 0; i < CC; ++i) {
+        const T s0 = (T)0.5 * (y[0][i] + y[1][i] + y[2][i] - y[3][i]);
+        const T s1 = (T)0.5 * (y[0][i] + y[1][i] - y[2][i] + y[3][i]);
+        const T s2 = (T)0.5 * (y[0][i] - y[1][i] + y[2][i] + y[3][i]);
+        const T s3 = (T)0.5 * (-y[0][i] + y[1][i] + y[2][i] + y[3][i]);
+        a.hat[fb + i * g.ne + node[0]] = s0;
+        a.hat[fb + i * g.ne + node[1]] = s1;
+        a.hat[fb + i * g.ne + node[2]] = s2;
+        a.hat[fb + i * g.ne + node[3]] = s3;
+      }
+    }
+  }
+  if (a.standalone) return;
+  const double bs = block_sum_acc(acc, red_sh);
+  if (threadIdx.x == 0) a.red.part[(long long)bl * gridDim.x + blockIdx.x] = bs;
+  if (last_block(a.red.ticket)) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int q = warp; q < a.BL; q += blockDim.x / 32) {
+      if (a.sc[q].done) continue;
+      const double gam = warp_sum_partials(a.red.part + (long long)q * gridDim.x, gridDim.x, 1);
+      if (lane == 0) direction_update(a.sc[q], gam, 0.0, 0);
+    }
+    __syncthreads();
     if (threadIdx.x == 0) *a.red.ticket = 0u;
   }
 }
@@ -483,7 +585,7 @@ __global__ void __launch_bounds__(kDThreads) k_dinit(DInitArgs a) {
     const long long r = node / g.n3;
     const int i2 = (int)(r % g.n2), i1 = (int)(r / g.n2);
     double f[CC];
-    if (i1 && i2 && i3) {
+    if (dfree_node(g, i1, i2, i3)) {
       node_rhs<CC>(ph, mt, g.pg, i1, i2, i3, a.loads + l * (CC == 1 ? 3 : 6), f);
     } else {
 #pragma unroll
@@ -524,7 +626,7 @@ __global__ void __launch_bounds__(kDThreads) k_ddiag(DDiagArgs a) {
     const long long r = node / g.n3;
     const int i2 = (int)(r % g.n2), i1 = (int)(r / g.n2);
     double dg[CC];
-    const bool in = i1 && i2 && i3;
+    const bool in = dfree_node(g, i1, i2, i3);
     if (in) node_diag<CC>(ph, mt, g.pg, i1, i2, i3, dg);
 #pragma unroll
     for (int i = 0; i < CC; ++i) {
@@ -588,7 +690,8 @@ __global__ void __launch_bounds__(kDThreads) k_dscatter(DGrid g, int cnt, const 
     const long long r = node / g.n3;
     const int i2 = (int)(r % g.n2), i1 = (int)(r / g.n2);
     double v = 0.0;
-    if (i1 && i2 && i3) v = src[comp * g.nf + (((long long)(i1 - 1) * g.m2 + (i2 - 1)) * g.m3 + (i3 - 1))];
+    if (dfree_node(g, i1, i2, i3))
+      v = src[comp * g.nf + (((long long)(i1 - g.o[0]) * g.m2 + (i2 - g.o[1])) * g.m3 + (i3 - g.o[2]))];
     dst[i] = v;
   }
 }
@@ -622,7 +725,7 @@ int dpass_blocks(const DGrid& g, int c, int mode, int lines) {
     return (int)((rows + lines - 1) / lines);
   }
   if (mode == DP_MID) return c * g.m1 * nb3;
-  return g.m2 * nb3;
+  return g.m2 * nb3;  // DP_QMUL, DP_MID1
 }
 
 static int dgrid_blocks(long long m) {
@@ -652,6 +755,7 @@ cudaError_t launch_dpass(const DPassArgs<T>& a, int mode, cudaStream_t s) {
       case DP_FIRST: return dpass_go<T, DP_FIRST, 1>(a, s);
       case DP_MID: return dpass_go<T, DP_MID, 1>(a, s);
       case DP_QMUL: return dpass_go<T, DP_QMUL, 1>(a, s);
+      case DP_MID1: return dpass_go<T, DP_MID1, 1>(a, s);
       default: return dpass_go<T, DP_LAST, 1>(a, s);
     }
   }
@@ -659,6 +763,7 @@ cudaError_t launch_dpass(const DPassArgs<T>& a, int mode, cudaStream_t s) {
     case DP_FIRST: return dpass_go<T, DP_FIRST, 3>(a, s);
     case DP_MID: return dpass_go<T, DP_MID, 3>(a, s);
     case DP_QMUL: return dpass_go<T, DP_QMUL, 3>(a, s);
+    case DP_MID1: return dpass_go<T, DP_MID1, 3>(a, s);
     default: return dpass_go<T, DP_LAST, 3>(a, s);
   }
 }
@@ -726,6 +831,21 @@ cudaError_t launch_dplane(const DPassArgs<T>& a, int fwd, cudaStream_t s) {
   kern<<<grid, kDPlaneThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
+
+int dmixq_blocks(const DGrid& g, int pa, int pb) {
+  const int n[3] = {g.n1, g.n2, g.n3}, m[3] = {g.m1, g.m2, g.m3};
+  return dgrid_blocks((long long)(n[pa] / 2 + 1) * (n[pb] / 2 + 1) * m[3 - pa - pb]);
+}
+
+template <typename T>
+cudaError_t launch_dmixq(const DPassArgs<T>& a, int pa, int pb, cudaStream_t s) {
+  dim3 grid(dmixq_blocks(a.g, pa, pb), a.BL);
+  if (a.c == 1) k_dmixq<T, 1><<<grid, kDThreads, 0, s>>>(a, pa, pb);
+  else k_dmixq<T, 3><<<grid, kDThreads, 0, s>>>(a, pa, pb);
+  return cudaGetLastError();
+}
+template cudaError_t launch_dmixq<double>(const DPassArgs<double>&, int, int, cudaStream_t);
+template cudaError_t launch_dmixq<float>(const DPassArgs<float>&, int, int, cudaStream_t);
 
 cudaError_t launch_dfold(const DGrid& g, int c, int BL, double* u64, float* u32, const CgScal* sc, int only_pending,
                          cudaStream_t s) {

@@ -72,17 +72,19 @@ class Homogenization:
 
 class DirichletHomogenization:
     """One context of the Dirichlet problem (fluctuation zero on the boundary, sine transform):
-    ``batch`` instances of an ``n1 x n2 x n3`` voxel grid with ``(n1-1)(n2-1)(n3-1)`` free nodes."""
+    ``batch`` instances of an ``n1 x n2 x n3`` voxel grid with ``(n1-1)(n2-1)(n3-1)`` free nodes.
+    ``bc`` (per axis 1 = Dirichlet faces, 0 = periodic) selects mixed boundary conditions."""
 
-    def __init__(self, physics: int, shape, batch: int = 1, L0: float = 1.0):
+    def __init__(self, physics: int, shape, batch: int = 1, L0: float = 1.0, bc=(1, 1, 1)):
         self.physics = physics
         self.c = 1 if physics == _lib.THERMAL else 3
         self.dim = 3 if physics == _lib.THERMAL else 6
         self.shape = tuple(int(s) for s in shape)
-        self.free_shape = tuple(s - 1 for s in self.shape)
+        self.bc = tuple(int(b) for b in bc)
+        self.free_shape = tuple(s - b for s, b in zip(self.shape, self.bc))
         self.nf = int(np.prod(self.free_shape))
         self.batch = batch
-        self.ctx = api.unocg_dir_create(physics, batch, *self.shape, L0)
+        self.ctx = api.unocg_dir_create(physics, batch, *self.shape, L0, bc=self.bc)
         self.n_loads = 0
 
     def close(self):
