@@ -234,12 +234,12 @@ def batched_uneven(n_inst: int = 256, reps: int = 3):
             "contexts": len(sizes), "input_generation_s": t_gen}
 
 
-def dirichlet_solver(w, stream):
+def dirichlet_solver(w, stream, bc=(1, 1, 1)):
     """The 64^3 thermal workload with Dirichlet BC (fluctuation zero on the boundary, sine
-    transform in the UNO preconditioner)."""
+    transform in the UNO preconditioner), or mixed BC with ``bc`` per axis."""
     from paper_2508_02681_gb300 import _lib, api
     from paper_2508_02681_gb300.solver import DirichletHomogenization
-    h = DirichletHomogenization(_lib.THERMAL, w["phase"].shape)
+    h = DirichletHomogenization(_lib.THERMAL, w["phase"].shape, bc=bc)
     api.unocg_dir_set_stream(h.ctx, stream)
     h.set_microstructure(w["phase"], 2)
     h.set_phase_properties(w["props"])
@@ -248,15 +248,16 @@ def dirichlet_solver(w, stream):
     return h
 
 
-def dirichlet(w, stream, steps: int = 5):
-    """Time-to-tolerance of the same workload with Dirichlet BC: mixed and FP64 UNO-CG (sine
-    transform) and FP64 Jac-CG, CUDA events on the solve stream, L2 flushed before each solve."""
+def dirichlet(w, stream, steps: int = 5, bc=(1, 1, 1)):
+    """Time-to-tolerance of the same workload with Dirichlet (or mixed) BC: mixed and FP64
+    UNO-CG and FP64 Jac-CG, CUDA events on the solve stream, L2 flushed before each solve."""
     import torch
     from paper_2508_02681_gb300 import _lib, api
-    h = dirichlet_solver(w, stream)
+    h = dirichlet_solver(w, stream, bc)
     L = w["loads"].shape[0]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    out = {"bc": "Dirichlet (fluctuation zero on the boundary), sine-transform UNO"}
+    out = {"bc": "Dirichlet (fluctuation zero on the boundary), sine-transform UNO" if all(bc) else
+           f"mixed, Dirichlet faces per axis {list(bc)}, Fourier x sine UNO"}
     for name, pc, prec in (("mixed_uno", _lib.PRECOND_UNO, _lib.MIXED), ("fp64_uno", _lib.PRECOND_UNO, _lib.FP64),
                            ("fp64_jacobi", _lib.PRECOND_JACOBI, _lib.FP64)):
         opts = api.make_opts(tol=TOL, max_iter=20000, precond=pc, precision=prec, flexible=0)
@@ -444,6 +445,7 @@ def main():
         line["batched_uneven"] = batched_uneven()
     if rank == 0 and world == 1 and not args.no_dirichlet:
         line["dirichlet"] = dirichlet(w, stream)
+        line["mixed_bc"] = dirichlet(w, stream, bc=(0, 1, 0))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import homogenize as hz
         t0 = time.perf_counter()
