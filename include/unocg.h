@@ -257,7 +257,7 @@ int unocg_rhs_dev(unocg_ctx* ctx, int instance, int load, double* f_dev, void* s
    [B][N1][N2][N3], loads, properties, status codes, unocg_solve_opts / unocg_solve_info.
    Fields on the free nodes: device layout [c][M1][M2][M3] (double); host I/O interleaved
    [M1*M2*M3*c].  No zero-mean projection (the Dirichlet fluctuation is unique).
-   Limits: 2 <= N_a <= 256, each N_a of the form 2^a 3^b 5^c.  use_graph: 0 host-driven
+   Limits: 2 <= N_a <= 512, each N_a of the form 2^a 3^b 5^c.  use_graph: 0 host-driven
    loop (one residual check read back per iteration), any other value one CUDA graph with
    conditional nodes; flexible CG is not available (UNOCG_ERR_INVALID_ARG).
    MIXED precision: FP32 fields, transforms, K.u and FP32 weights; FP64 solution, reductions

@@ -119,7 +119,7 @@ int dfail(unocg_dir* d, int code, const std::string& msg) {
 
 bool dim_ok(int n) {
   FftPlan p;
-  return n >= 2 && n <= 256 && dfactor_plan(n, &p) && dfactor_plan(2 * n, &p);
+  return n >= 2 && n <= 512 && dfactor_plan(n, &p) && dfactor_plan(2 * n, &p);
 }
 
 // even position count W <= cap with c W lines of length 2N in the shared-memory budget

@@ -132,6 +132,74 @@ class DirichletHomogenization:
         return api.unocg_dir_get_effective_tensor(self.ctx, self.batch, self.dim, self.n_loads)
 
 
+
+class Homogenization2D:
+    """2D cells (Sec. 6 with d = 2: thermal, or plane-strain elasticity with (E, nu) per phase)
+    solved as the x3-invariant 3D problem: the cell becomes axes 2 and 3 of a 3D grid with
+    ``layers`` voxels along a periodic axis 1.  By uniqueness the 3D solution does not vary
+    along that axis, equals the bilinear 2D solution on every layer (plane strain: u along the
+    extrusion vanishes), and the in-plane averages are the 2D ones; the UNO restricted to the
+    x3-invariant fields (Fourier mode 0 along the extrusion) is the 2D one.
+
+    ``bc``: per 2D axis 1 (Dirichlet faces) or 0 (periodic).  Loads: thermal (g1, g2); elastic
+    Mandel (eps11, eps22, sqrt2 eps12).  Microstructures [batch][N1][N2]."""
+
+    def __init__(self, physics: int, shape, batch: int = 1, L0: float = 1.0, bc=(0, 0), layers=None):
+        self.physics = physics
+        self.shape2 = tuple(int(s) for s in shape)
+        self.bc2 = tuple(int(b) for b in bc)
+        self.c2 = 1 if physics == _lib.THERMAL else 2
+        self.dim2 = 2 if physics == _lib.THERMAL else 3
+        self.batch = batch
+        periodic = not any(self.bc2)
+        self.layers = layers or (4 if periodic else 2)
+        shape3 = (self.layers,) + self.shape2
+        # the voxel edge follows the 2D axis 1 (axis 2 of the 3D grid): h = L0 / N1
+        L03 = L0 * self.layers / self.shape2[0]
+        if periodic:
+            self.h = Homogenization(physics, shape3, batch=batch, L0=L03)
+        else:
+            self.h = DirichletHomogenization(physics, shape3, batch=batch, L0=L03, bc=(0,) + self.bc2)
+        self.free2 = tuple(n - b for n, b in zip(self.shape2, self.bc2))
+        # 2D components / Mandel rows inside the 3D ones (axes 2 and 3)
+        self._comp = [0] if self.c2 == 1 else [1, 2]
+        self._rows = [1, 2] if self.c2 == 1 else [1, 2, 5]
+
+    def close(self):
+        self.h.close()
+
+    def set_microstructure(self, phase, n_phases: int):
+        ph = np.asarray(phase, dtype=np.uint8).reshape((self.batch,) + self.shape2)
+        self.h.set_microstructure(np.repeat(ph[:, None], self.layers, axis=1), n_phases)
+
+    def set_phase_properties(self, props):
+        self.h.set_phase_properties(props)
+
+    def set_macro_load(self, loads):
+        loads = np.atleast_2d(np.asarray(loads, dtype=np.float64))
+        l3 = np.zeros((loads.shape[0], 3 if self.c2 == 1 else 6))
+        l3[:, self._rows] = loads
+        self.h.set_macro_load(l3)
+        self.n_loads = loads.shape[0]
+
+    def set_uno_weights(self, kind=_lib.W_REFERENCE_MEDIUM, w=None, spd_eps: float = 0.0):
+        self.h.set_uno_weights(kind, w, spd_eps)
+
+    def solve(self, raise_on_error: bool = True, **opts) -> api.Info:
+        return self.h.solve(raise_on_error=raise_on_error, **opts)
+
+    def fluctuation(self, instance: int = 0, load: int = 0) -> np.ndarray:
+        """2D fluctuation on the free nodes (layer 0), interleaved ``[n2d * c]``."""
+        u = self.h.fluctuation(instance, load)
+        c3 = 1 if self.c2 == 1 else 3
+        free3 = (self.layers,) + self.free2
+        return np.ascontiguousarray(u.reshape(free3 + (c3,))[0][..., self._comp]).ravel()
+
+    def effective_tensor(self) -> np.ndarray:
+        """``[batch][dim2][n_loads]`` in-plane averaged flux / stress."""
+        return self.h.effective_tensor()[:, self._rows, :]
+
+
 class UnevenBatch:
     """Many instances of possibly different grid sizes (the serving-style batch): the instances
     of one size share a batched context (per-(instance, load) convergence masks), and the

@@ -6,6 +6,7 @@ oracle and the CUDA path stay independent while reading the same inputs.
 """
 from .microstructure import (  # noqa: F401
     rsa_spheres,
+    rsa_disks,
     random_phase,
     laminate,
     random_field,

@@ -108,6 +108,42 @@ def rsa_spheres(shape, radius: float, volume_fraction: float, seed: int,
             return phase, frac
 
 
+def rsa_disks(shape, radius: float, area_fraction: float, seed: int, max_rejections: int = 10_000):
+    """2D periodic RSA of non-overlapping disks (the 2D counterpart of ``rsa_spheres``): centres
+    uniform in [0, N1) x [0, N2), accepted at a minimum-image distance of at least 2 radius from
+    every accepted centre, pixels whose centre lies within the radius belong to the inclusion
+    phase; stops at the first disk that reaches the area fraction, or after ``max_rejections``
+    consecutive rejections (jammed).  Returns ``(phase uint8 [N1, N2], achieved_fraction)``."""
+    shape = tuple(int(s) for s in shape)
+    n = np.asarray(shape, dtype=np.float64)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    phase = np.zeros(shape, dtype=np.uint8)
+    if area_fraction <= 0.0:
+        return phase, 0.0
+    centres = np.zeros((0, 2))
+    total = float(np.prod(shape))
+    r = float(radius)
+    reach = int(np.ceil(r)) + 1
+    rejections = 0
+    while rejections < max_rejections:
+        c = rng.uniform(0.0, 1.0, size=2) * n
+        if centres.shape[0]:
+            d = _min_image(centres - c[None, :], n)
+            if np.min(np.einsum("ij,ij->i", d, d)) < (2.0 * r) ** 2:
+                rejections += 1
+                continue
+        rejections = 0
+        centres = np.vstack([centres, c])
+        g1, g2 = np.meshgrid(*[np.arange(int(np.floor(c[a] - r)) - 1, int(np.floor(c[a] - r)) + 2 * reach + 1)
+                               for a in range(2)], indexing="ij")
+        inside = ((g1 + 0.5) - c[0]) ** 2 + ((g2 + 0.5) - c[1]) ** 2 <= r * r
+        phase[g1[inside] % shape[0], g2[inside] % shape[1]] = 1
+        frac = float(phase.sum()) / total
+        if frac >= area_fraction:
+            return phase, frac
+    return phase, float(phase.sum()) / total
+
+
 def random_phase(shape, n_phases: int, seed: int) -> np.ndarray:
     """Voxel-wise independent uniform phase labels in ``[0, n_phases)`` (a rough test image)."""
     rng = np.random.Generator(np.random.PCG64(seed))

@@ -237,7 +237,7 @@ def test_uno_reduces_iterations_like_periodic():
 def test_invalid_arguments():
     from paper_2508_02681_gb300 import _lib, api
     from paper_2508_02681_gb300._lib import UnocgError
-    for bad in [(1, 0, 8, 8, 8), (1, 1, 7, 8, 8), (1, 1, 512, 8, 8), (2, 1, 8, 8, 8)]:
+    for bad in [(1, 0, 8, 8, 8), (1, 1, 7, 8, 8), (1, 1, 1024, 8, 8), (2, 1, 8, 8, 8)]:
         with pytest.raises(UnocgError):
             api.unocg_dir_create(*bad)
     h = _ctx(1, np.zeros((8, 8, 8), np.uint8), np.array([1.0]), unit_loads(1))

@@ -53,3 +53,14 @@ def test_training_workload_ranges():
         assert w["phase"].shape == (32, 32, 32)
         assert 0.1 <= w["vf"] <= 0.45
         assert 5.0 <= w["props"][1] <= 100.0
+
+
+def test_rsa_disks_seeded_non_overlapping_and_periodic():
+    from synth import rsa_disks
+    p1, f1 = rsa_disks((40, 50), 3.0, 0.3, seed=4)
+    p2, f2 = rsa_disks((40, 50), 3.0, 0.3, seed=4)
+    assert np.array_equal(p1, p2) and f1 == f2
+    assert 0.3 <= f1 < 0.36 and p1.dtype == np.uint8
+    # a disk near the edge wraps: the inclusion set is invariant under no shift but touches edges
+    p3, _ = rsa_disks((16, 16), 2.5, 0.5, seed=9)
+    assert p3[0].any() or p3[:, 0].any()
