@@ -46,6 +46,37 @@ def features_c1(R, U, shape):
     return a, b
 
 
+def features_general(R, U, shape):
+    """Features a_m, b_m of Sec. 5.4 for any c, per half-grid mode with multiplicity, m over the
+    unique entries (i, j) in the paper's order (Eq. (features-c-1), Eq. (features-c-2), App. C):
+    a_m = mean conj(R_i) R_j (+ conj(R_j) R_i for i != j), b_m = 2 mean Re of the same with the
+    second factor taken from U.  Returns ``[N1, N2, N3h, C]`` arrays."""
+    c = R.shape[1]
+    w = dft.half_multiplicity(shape)
+    pairs = [(0, 0)] if c == 1 else uno.PAPER_ORDER
+    a = np.zeros(R.shape[2:] + (len(pairs),))
+    b = np.zeros_like(a)
+    for m, (i, j) in enumerate(pairs):
+        ta = np.conj(R[:, i]) * R[:, j]
+        tb = np.conj(R[:, i]) * U[:, j]
+        if i != j:
+            ta = ta + np.conj(R[:, j]) * R[:, i]
+            tb = tb + np.conj(R[:, j]) * U[:, i]
+        a[..., m] = w * np.mean(ta.real, axis=0)
+        b[..., m] = w * 2.0 * np.mean(tb.real, axis=0)
+    return a, b
+
+
+def loss_from_features(v, a, b) -> float:
+    """Loss without delta from the features (Sec. 5.4, App. C): with Q(v) the symmetric block of
+    the unique entries v, sum_k sum_m a_m (Q^2)_m - b_m v_m, (Q^2)_m the entry (i, j) of Q Q."""
+    C = v.shape[-1]
+    c = 1 if C == 1 else 3
+    Q = uno.blocks_from_entries(v, c)
+    Q2 = uno.entries_from_blocks(Q @ Q)
+    return float(np.sum(a * Q2) - np.sum(b * v))
+
+
 def grad_v_c1(v, R, U, shape):
     """``dL/dv = 2 a * v - b`` (Sec. 5.4, c = 1)."""
     a, b = features_c1(R, U, shape)

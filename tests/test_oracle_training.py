@@ -122,3 +122,39 @@ def test_optimum_modes_c1_is_the_global_minimizer():
     for _ in range(50):
         wp = w + 1e-3 * rng.standard_normal(w.shape)
         assert training.modes_loss_c1(wp, M, shape, a, b) >= l0 - 1e-12 * abs(l0)
+
+
+@pytest.mark.parametrize("c,shape", [(1, (6, 8, 4)), (3, (4, 6, 6))])
+def test_general_features_give_the_loss_and_gradient(c, shape):
+    # Sec. 5.4 / App. C: the loss is a quadratic in the block entries whose coefficients are the
+    # features; its value equals the loss by definition up to delta = mean ||u||^2, and its
+    # gradient equals the pinned per-entry gradient of the definition
+    rng = np.random.default_rng(c)
+    B = 3
+    f = rng.standard_normal((B, c) + shape)
+    u = rng.standard_normal((B, c) + shape)
+    R, U = training.spectra(f), training.spectra(u)
+    a, b = training.features_general(R, U, shape)
+    C = 1 if c == 1 else 6
+    th = rng.standard_normal(shape[:2] + (shape[2] // 2 + 1, C)) * 0.4
+    th[..., 0] += 1.0
+    if c == 3:
+        th[..., 1] += 1.0
+        th[..., 3] += 1.0
+    Q = uno.psi(th, c)
+    v = uno.entries_from_blocks(Q)
+    delta = float(np.sum(u ** 2)) / B
+    assert training.loss_from_features(v, a, b) + delta == pytest.approx(training.loss_from_spectra(Q, R, U, shape), rel=1e-12)
+    g = training.grad_entries_general(Q, R, U, shape)
+    rng2 = np.random.default_rng(5)
+    for _ in range(6):
+        idx = tuple(rng2.integers(0, s) for s in v.shape)
+        hs = 1e-6
+        vp, vm = v.copy(), v.copy()
+        vp[idx] += hs
+        vm[idx] -= hs
+        fd = (training.loss_from_features(vp, a, b) - training.loss_from_features(vm, a, b)) / (2 * hs)
+        assert fd == pytest.approx(g[idx], rel=1e-6, abs=1e-9)
+    if c == 1:
+        a1, b1 = training.features_c1(R, U, shape)
+        assert np.max(np.abs(a[..., 0] - a1)) < 1e-14 and np.max(np.abs(b[..., 0] - b1)) < 1e-14
