@@ -213,12 +213,16 @@ int unocg_uno_apply_dev(unocg_uno* op, int batch, const float* r_dev, float* s_d
    dL/dQ(k) = sum_b w_k Re(conj(T gs_b) (T r_b)^T).                                         */
 int unocg_uno_backward_dev(unocg_uno* op, int batch, const float* r_dev, const float* gs_dev,
                            float* gr_dev, float* gtheta_dev, void* stream);
-/* Features of the second-order training (Sec. 5.4, Eq. (features-c-1); c = 1 only): for a
-   batch of right-hand sides f_dev and solutions u_dev (device float [batch][N1][N2][N3]) adds
-   sum_b w_k |(T f_b)(k)|^2 to ab_dev[0 .. nh) and sum_b w_k Re(conj((T u_b)(k)) (T f_b)(k)) to
-   ab_dev[nh .. 2 nh) (device float, nh = N1 N2 (N3/2+1), unitary T, w_k the half-grid
-   multiplicity); accumulate = 0 zeroes ab_dev first.  a = first / n_samples and
-   b = 2 second / n_samples.  The weights set on the operator are not used.                */
+/* Features of the second-order training (Sec. 5.4, Eq. (features-c-1), Eq. (features-c-2) and
+   the c = 3 features of App. C): for a batch of right-hand sides f_dev and solutions u_dev
+   (device float [batch][c][N1][N2][N3]) adds, per half-grid mode k and unique entry (i, j) of
+   the paper's order (C = 1 or 6),
+     sum_b w_k Re(conj(F_i) F_j) [+ Re(conj(F_j) F_i) for i != j]   to ab_dev[0 .. nh*C) and
+     sum_b w_k Re(conj(U_i) F_j) [+ Re(conj(U_j) F_i) for i != j]   to ab_dev[nh*C .. 2 nh*C)
+   (layout [nh][C] each; F = T f_b, U = T u_b unitary; w_k the half-grid multiplicity;
+   nh = N1 N2 (N3/2+1)); accumulate = 0 zeroes ab_dev first.  The features of the paper are
+   a = first / n_samples and b = 2 second / n_samples.  The weights set on the operator are
+   not used.                                                                                */
 int unocg_uno_features_dev(unocg_uno* op, int batch, const float* f_dev, const float* u_dev, float* ab_dev,
                            int accumulate, void* stream);
 

@@ -1476,31 +1476,34 @@ extern "C" int unocg_uno_apply_dev(unocg_uno* op, int batch, const float* r_dev,
   return UNOCG_OK;
 }
 
-// Features of the second-order training (Sec. 5.4, c = 1): raw sums over the batch of
-// w_k |T f|^2 and w_k Re(conj(T u) T f) per half-grid mode (unitary transform, multiplicity w_k),
-// from the same transform passes and the same per-mode accumulation as the weight gradient.
+// Features of the second-order training (Sec. 5.4; Eq. (features-c-1), Eq. (features-c-2) and
+// the c = 3 set of App. C): raw sums over the batch, per half-grid mode (unitary transform,
+// multiplicity w_k), in the order of the unique block entries: for the pair (i, j) of the entry,
+// w_k Re(conj(T f)_i (T f)_j) (+ the (j, i) term off the diagonal) -- the a features -- and the
+// same with conj(T u)_i -- half the b features.  These are the per-mode accumulations of the
+// weight gradient with the adjoint field replaced by T f or T u, from the same kernels.
 extern "C" int unocg_uno_features_dev(unocg_uno* op, int batch, const float* f_dev, const float* u_dev, float* ab_dev,
                                       int accumulate, void* stream) {
   if (!op || batch < 1 || !f_dev || !u_dev || !ab_dev) return UNOCG_ERR_INVALID_ARG;
-  if (op->c != 1) return ufail(op, UNOCG_ERR_INVALID_ARG, "features are defined here for one nodal DOF");
   int rc = uno_ensure(op, batch);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   const size_t nh = (size_t)op->g.nh;
-  if (!accumulate) UCK(cudaMemsetAsync(ab_dev, 0, 2 * nh * sizeof(float), s));
+  const size_t NQ = op->c == 1 ? 1 : 6;
+  if (!accumulate) UCK(cudaMemsetAsync(ab_dev, 0, 2 * nh * NQ * sizeof(float), s));
   PlaneFwdArgs<float> pf{};
-  pf.g = op->g; pf.c = 1; pf.BL = batch; pf.src = f_dev; pf.hat = op->hat; pf.ft = uno_tables(op); pf.standalone = 1;
+  pf.g = op->g; pf.c = op->c; pf.BL = batch; pf.src = f_dev; pf.hat = op->hat; pf.ft = uno_tables(op); pf.standalone = 1;
   UCK(fwd_transform<float>(pf, s, 0));
   pf.src = u_dev;
   pf.hat = op->ghat;
   UCK(fwd_transform<float>(pf, s, 0));
   LineArgs<float, float> la{};
-  la.g = op->g; la.c = 1; la.BL = batch; la.L = 1; la.hat = op->hat; la.shat = op->shat; la.ghat = op->ghat;
+  la.g = op->g; la.c = op->c; la.BL = batch; la.L = 1; la.hat = op->hat; la.shat = op->shat; la.ghat = op->ghat;
   la.Q = op->Q32; la.q_inst_stride = 0; la.scale = 1.0 / (double)op->g.n; la.ft = uno_tables(op);
-  la.standalone = 1; la.gq = ab_dev + nh;  // sum w Re(conj(T u) T f)
+  la.standalone = 1; la.gq = ab_dev + nh * NQ;  // sums of w Re(conj(T u)_i (T f)_j) per entry
   UCK(launch_line<float, float>(la, 1, s));
   la.ghat = op->hat;
-  la.gq = ab_dev;  // sum w |T f|^2
+  la.gq = ab_dev;  // sums of w Re(conj(T f)_i (T f)_j) per entry
   UCK(launch_line<float, float>(la, 1, s));
   return UNOCG_OK;
 }

@@ -171,15 +171,18 @@ def train(f, u, theta0, epochs: int, batch: int = 64, lr: float = 1e-2, seed: in
 
 
 def features(f, u, chunk: int = 64):
-    """Features a, b of Eq. (features-c-1) on the half grid [N1, N2, N3/2+1] (numpy float64) from
-    training data f, u (torch float32 [N_s, 1, N1, N2, N3] on the GPU): every sample is
-    transformed once (Sec. 5.4)."""
+    """Features a, b of Sec. 5.4 on the half grid from training data f, u (torch float32
+    [N_s, c, N1, N2, N3] on the GPU): c = 1 (Eq. (features-c-1)) returns numpy float64 arrays
+    [N1, N2, N3/2+1]; c = 3 (App. C) returns [N1, N2, N3/2+1, 6] in the paper's entry order
+    (a_1..a_6 and b_1..b_6).  Every sample is transformed once."""
     import torch
 
     shape = tuple(f.shape[2:])
+    c = int(f.shape[1])
+    C = 1 if c == 1 else 6
     nh = shape[0] * shape[1] * (shape[2] // 2 + 1)
-    op = api.unocg_uno_create(1, *shape)
-    ab = torch.zeros(2 * nh, dtype=torch.float32, device=f.device)
+    op = api.unocg_uno_create(c, *shape)
+    ab = torch.zeros(2 * nh * C, dtype=torch.float32, device=f.device)
     n = f.shape[0]
     for s0 in range(0, n, chunk):
         fb = f[s0:s0 + chunk].contiguous()
@@ -187,7 +190,9 @@ def features(f, u, chunk: int = 64):
         api.unocg_uno_features_dev(op, fb.shape[0], fb, ub, ab, accumulate=s0 > 0)
     torch.cuda.synchronize()
     api.unocg_uno_destroy(op)
-    abh = ab.cpu().numpy().astype(np.float64).reshape(2, shape[0], shape[1], shape[2] // 2 + 1)
+    abh = ab.cpu().numpy().astype(np.float64).reshape(2, shape[0], shape[1], shape[2] // 2 + 1, C)
+    if c == 1:
+        abh = abh[..., 0]
     return abh[0] / n, 2.0 * abh[1] / n
 
 
@@ -196,6 +201,102 @@ def _mode_index(shape, M: int):
     ms = mode_set(M)
     return (np.array([k1 % N1 for k1, _, _ in ms]), np.array([k2 % N2 for _, k2, _ in ms]),
             np.array([k3 for _, _, k3 in ms]))
+
+
+def _entry_mats():
+    """Symmetric unit matrices E_e = dQ/dv_e of the six unique entries (paper order)."""
+    E = np.zeros((6, 3, 3))
+    for e, (i, j) in enumerate(_ORDER3):
+        E[e, i, j] = E[e, j, i] = 1.0
+    return E
+
+
+def _entries(Mx):
+    return np.stack([Mx[..., i, j] for (i, j) in _ORDER3], axis=-1)
+
+
+_E6 = _entry_mats()
+# d^2 (Q Q)_m / dv_e dv_f = (E_e E_f + E_f E_e)_m
+_T6 = _entries(np.einsum("eij,fjk->efik", _E6, _E6) + np.einsum("fij,ejk->efik", _E6, _E6))
+# psi: F_p = dL/dw_p (unit matrix at the position of parameter p in L)
+_F6 = np.zeros((6, 3, 3))
+for _p, (_r, _q) in enumerate(_L3):
+    _F6[_p, _r, _q] = 1.0
+# d^2 v / dw_p dw_q = entries(F_p F_q^T + F_q F_p^T), constant
+_D2 = np.moveaxis(_entries(np.einsum("pij,qkj->pqik", _F6, _F6) + np.einsum("qij,pkj->pqik", _F6, _F6)), -1, 0)
+
+
+def _psi_jac(w):
+    """v = entries(L L^T) and J = dv/dw for weights [..., 6] (c = 3)."""
+    L = np.zeros(w.shape[:-1] + (3, 3))
+    for i, (r, q) in enumerate(_L3):
+        L[..., r, q] = w[..., i]
+    v = _entries(L @ np.swapaxes(L, -1, -2))
+    dQ = np.einsum("pij,...kj->...pik", _F6, L)
+    J = np.swapaxes(_entries(dQ + np.swapaxes(dQ, -1, -2)), -1, -2)  # [..., e, p]
+    return v, J
+
+
+def second_order_modes_c3(a, b, M: int, w0, iters: int = 100, tol: float = 1e-12):
+    """Algorithm 4 for c = 3 (App. C) on the paper's weight layout: Newton-Raphson on
+    w = [w_0; w_1 .. w_n] (six psi parameters each, Q = L L^T) for the loss
+    L = sum_k sum_m a_m (Q^2)_m - b_m v_m with v = psi(w_0) + psi(w_i) on the i-th mode of K_M
+    and psi(w_0) elsewhere.  Gradient and Hessian by the chain rule through psi (Sec. 5.4);
+    the Hessian is an arrow of 6 x 6 blocks (the bypass couples to every mode), each step an
+    O(n) block Schur-complement solve with Levenberg-Marquardt damping when a step does not
+    lower the loss.  Returns (w [1 + n_modes, 6], loss history without delta)."""
+    shape = a.shape[:2] + (2 * (a.shape[2] - 1),)
+    i1, i2, i3 = _mode_index(shape, M)
+    ak, bk = a[i1, i2, i3], b[i1, i2, i3]            # [n, 6]
+    a_rest = a.reshape(-1, 6).sum(axis=0) - ak.sum(axis=0)
+    b_rest = b.reshape(-1, 6).sum(axis=0) - bk.sum(axis=0)
+    Hk = np.einsum("efm,nm->nef", _T6, ak)           # Hessian of L in v per mode
+    Hr = np.einsum("efm,m->ef", _T6, a_rest)
+    w = np.asarray(w0, dtype=np.float64).reshape(-1, 6).copy()
+
+    def loss(x):
+        v0, _ = _psi_jac(x[0])
+        vi = v0 + _psi_jac(x[1:])[0]
+        return float(0.5 * v0 @ Hr @ v0 - b_rest @ v0
+                     + np.sum(0.5 * np.einsum("ne,nef,nf->n", vi, Hk, vi) - np.sum(bk * vi, axis=1)))
+
+    hist = [loss(w)]
+    lam = 0.0
+    I6 = np.eye(6)
+    for _ in range(iters):
+        v0, J0 = _psi_jac(w[0])
+        u, Ji = _psi_jac(w[1:])
+        vi = v0 + u
+        Gi = np.einsum("nef,nf->ne", Hk, vi) - bk     # dL_i / dv
+        Gall = Hr @ v0 - b_rest + Gi.sum(axis=0)
+        g0 = J0.T @ Gall
+        gi = np.einsum("nep,ne->np", Ji, Gi)
+        H00 = J0.T @ (Hr + Hk.sum(axis=0)) @ J0 + np.einsum("e,epq->pq", Gall, _D2)
+        H0i = np.einsum("ep,nef,nfq->npq", J0, Hk, Ji)              # [n, 6(w0), 6(wi)]
+        Hii = np.einsum("nep,nef,nfq->npq", Ji, Hk, Ji) + np.einsum("ne,epq->npq", Gi, _D2)
+        while True:
+            D = Hii + lam * I6
+            ok = np.all(np.linalg.eigvalsh(D) > 0)
+            if ok:
+                Dinv_g = np.linalg.solve(D, gi[..., None])[..., 0]
+                Dinv_H = np.linalg.solve(D, np.swapaxes(H0i, -1, -2))    # D_i^-1 H_i0
+                S = H00 + lam * I6 - np.einsum("npq,nqr->pr", H0i, Dinv_H)
+                if np.all(np.linalg.eigvalsh(S) > 0):
+                    x0 = np.linalg.solve(S, g0 - np.einsum("npq,nq->p", H0i, Dinv_g))
+                    xi = Dinv_g - np.einsum("nqp,p->nq", Dinv_H, x0)
+                    trial = w - np.vstack([x0[None], xi])
+                    lt = loss(trial)
+                    if lt <= hist[-1]:
+                        break
+            lam = max(2.0 * lam, 1e-12 * max(1.0, float(np.max(np.abs(Hii)))))
+            if lam > 1e30:
+                return w, hist
+        w = trial
+        hist.append(lt)
+        lam *= 0.1
+        if abs(hist[-2] - hist[-1]) <= tol * max(1.0, abs(hist[-1])):
+            break
+    return w, hist
 
 
 def second_order_modes(a, b, M: int, w0, iters: int = 100, tol: float = 1e-12):

@@ -46,3 +46,30 @@ def test_mode_set_order_matches_oracle():
     from oracle import uno
     for M in (1, 2, 5):
         assert pt.mode_set(M) == [tuple(k) for k in uno.mode_list(M)]
+
+
+def test_newton_c3_recovers_a_generating_preconditioner():
+    """Algorithm 4 for c = 3: data u = P* f from a bypass-plus-modes preconditioner P* (the
+    oracle applies it); the loss from the features reaches -delta (zero residual), and the
+    expanded Q equals Q* on the half grid."""
+    from oracle import training as ot, uno
+    shape, M, B = (6, 6, 6), 1, 4
+    rng = np.random.default_rng(11)
+    n_modes = len(uno.mode_list(M))
+    ws = rng.standard_normal((1 + n_modes, 6)) * 0.2
+    ws[:, [0, 1, 3]] += 1.0
+    Qs = uno.modes_Q(ws, M, shape, 3)
+    f = np.stack([random_field((3,) + shape, seed=40 + b) for b in range(B)])
+    u = np.stack([uno.uno_apply(Qs, f[b]) for b in range(B)])
+    R, U = ot.spectra(f), ot.spectra(u)
+    a, b = ot.features_general(R, U, shape)
+    delta = float(np.sum(u ** 2)) / B
+    w0 = ws + rng.standard_normal(ws.shape) * 0.05
+    w, hist = pt.second_order_modes_c3(a, b, M, w0)
+    assert all(h1 <= h0 + 1e-12 * abs(h0) for h0, h1 in zip(hist, hist[1:]))
+    assert hist[-1] + delta < 1e-9 * delta
+    Q = uno.modes_Q(w, M, shape, 3)
+    assert np.max(np.abs(Q - Qs)) < 1e-5 * np.max(np.abs(Qs))
+    # the features-based loss of the result equals the oracle's loss from features
+    v = uno.entries_from_blocks(Q)
+    assert ot.loss_from_features(v, a, b) == pytest.approx(hist[-1], rel=1e-8, abs=1e-10 * delta)
