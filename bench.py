@@ -42,8 +42,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the uneven-batch measurement")
     ap.add_argument("--profile-only", action="store_true", help="a few solves, for ncu launch lists")
-    ap.add_argument("--bc", default="periodic", choices=["periodic", "dirichlet"],
-                    help="with --profile-only: boundary conditions of the profiled solves")
+    ap.add_argument("--bc", default="periodic", choices=["periodic", "dirichlet", "mixed"],
+                    help="with --profile-only: boundary conditions of the profiled solves (mixed: Dirichlet faces on axis 2)")
+    ap.add_argument("--elastic", action="store_true",
+                    help="with --profile-only and --bc dirichlet/mixed: the 64^3 elastic workload (six loads)")
     ap.add_argument("--no-dirichlet", action="store_true", help="skip the Dirichlet-BC measurement")
     ap.add_argument("--no-graph", action="store_true",
                     help="profile-only: host-driven loop (kernels inside conditional graph bodies are not visible to ncu)")
@@ -234,12 +236,12 @@ def batched_uneven(n_inst: int = 256, reps: int = 3):
             "contexts": len(sizes), "input_generation_s": t_gen}
 
 
-def dirichlet_solver(w, stream, bc=(1, 1, 1)):
-    """The 64^3 thermal workload with Dirichlet BC (fluctuation zero on the boundary, sine
-    transform in the UNO preconditioner), or mixed BC with ``bc`` per axis."""
+def dirichlet_solver(w, stream, bc=(1, 1, 1), physics=1):
+    """A 64^3 workload with Dirichlet BC (fluctuation zero on the boundary, sine transform in
+    the UNO preconditioner), or mixed BC with ``bc`` per axis."""
     from paper_2508_02681_gb300 import _lib, api
     from paper_2508_02681_gb300.solver import DirichletHomogenization
-    h = DirichletHomogenization(_lib.THERMAL, w["phase"].shape, bc=bc)
+    h = DirichletHomogenization(physics, w["phase"].shape, bc=bc)
     api.unocg_dir_set_stream(h.ctx, stream)
     h.set_microstructure(w["phase"], 2)
     h.set_phase_properties(w["props"])
@@ -336,9 +338,13 @@ def main():
         ms = [a.elapsed_time(b) for a, b in ev]
         return float(np.mean(ms)), info
 
-    if args.profile_only and args.bc == "dirichlet":
+    if args.profile_only and args.bc in ("dirichlet", "mixed"):
         h.close()
-        hd = dirichlet_solver(w, stream)
+        bc = (1, 1, 1) if args.bc == "dirichlet" else (0, 1, 0)
+        if args.elastic:
+            w = workload(3)
+            L = w["loads"].shape[0]
+        hd = dirichlet_solver(w, stream, bc, physics=w["physics"])
         opts = api.make_opts(tol=TOL, max_iter=2000, precond=_lib.PRECOND_UNO, precision=_lib.MIXED, flexible=0,
                              use_graph=0 if args.no_graph else 1)
         for _ in range(2):

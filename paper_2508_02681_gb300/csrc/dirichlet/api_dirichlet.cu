@@ -454,10 +454,18 @@ DResArgs<T> res_args(unocg_dir* d, T* r, int only_pending) {
 }
 
 // mixed precision: r = f - K u in FP64 for the pending pairs, then their residual check
+// mixed precision keeps rref = f - K u64 in the f64 field (FP64; f at the start): a replacement
+// brings it up to date with the FP32 increment in float-pair arithmetic, writes r = rref, then
+// folds the increment into u64.  FP64 recomputes r = f - K u64.
 template <typename T>
 cudaError_t enq_replace(unocg_dir* d, cudaStream_t s, const DPlan& pl, const LoopCtl& ctl) {
   cudaError_t e = cudaSuccess;
-  if (sizeof(T) == 4) e = launch_dfold(d->g, d->c, d->B * d->L, d->u64, (float*)d->f32f.u, d->sc, 1, s);
+  if (sizeof(T) == 4) {
+    e = launch_dreplace(res_args<float>(d, (float*)d->f32f.r, 1), (const float*)d->f32f.u, 1, s);
+    if (e == cudaSuccess) e = launch_dfold(d->g, d->c, d->B * d->L, d->u64, (float*)d->f32f.u, d->sc, 1, s);
+    if (e == cudaSuccess) e = enq_check<T>(d, s, pl, ctl, 1);
+    return e;
+  }
   if (e == cudaSuccess) e = launch_dres<T>(res_args<T>(d, (T*)dfields<T>(d).r, 1), s);
   if (e != cudaSuccess) return e;
   return enq_check<T>(d, s, pl, ctl, 1);
@@ -467,8 +475,13 @@ cudaError_t enq_replace(unocg_dir* d, cudaStream_t s, const DPlan& pl, const Loo
 template <typename T>
 cudaError_t enq_post(unocg_dir* d, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
-  if (sizeof(T) == 4) e = launch_dfold(d->g, d->c, d->B * d->L, d->u64, (float*)d->f32f.u, d->sc, 0, s);
-  if (e == cudaSuccess) e = launch_dres<T>(res_args<T>(d, (T*)nullptr, 0), s);
+  if (sizeof(T) == 4) {
+    // reported true residual: rref brought up to date with the last increment, then the fold
+    e = launch_dreplace(res_args<float>(d, nullptr, 0), (const float*)d->f32f.u, 0, s);
+    if (e == cudaSuccess) e = launch_dfold(d->g, d->c, d->B * d->L, d->u64, (float*)d->f32f.u, d->sc, 0, s);
+  } else {
+    e = launch_dres<T>(res_args<T>(d, (T*)nullptr, 0), s);
+  }
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(d->ceff, 0, (size_t)d->B * d->dim * d->L * sizeof(double), s);
   if (e != cudaSuccess) return e;

@@ -150,6 +150,9 @@ template <typename T> cudaError_t launch_dmixq(const DPassArgs<T>& a, int pa, in
 template <typename T> cudaError_t launch_dres(const DResArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_djac(const DJacArgs<T>& a, int part, cudaStream_t s);
 cudaError_t launch_dinit(const DInitArgs& a, int BL, cudaStream_t s);
+// mixed precision: rref (the f64 field of DResArgs, f - K u64) -= K u32 in float pairs on the
+// free nodes, r = rref when a.r is set, max |rref| into rmax (into_rmax) or tmax
+cudaError_t launch_dreplace(const DResArgs<float>& a, const float* u32, int into_rmax, cudaStream_t s);
 // mixed precision: u64 += u32, u32 = 0 for the pending (only_pending) or all pairs
 cudaError_t launch_dfold(const DGrid& g, int c, int BL, double* u64, float* u32, const CgScal* sc, int only_pending,
                          cudaStream_t s);

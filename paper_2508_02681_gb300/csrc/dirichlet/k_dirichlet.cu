@@ -13,6 +13,7 @@
 #include <algorithm>
 
 #include "../fft.cuh"
+#include "../df64.cuh"
 #include "../kargs.h"
 #include "../stencil.cuh"
 #include "dargs.h"
@@ -507,6 +508,103 @@ __global__ void __launch_bounds__(kDThreads) k_dres(DResArgs<T> a) {
   if (threadIdx.x == 0 && !a.r) atomic_max_nonneg(&a.sc[bl].tmax_bits, bm);
 }
 
+// ============================================================================ replacement (mixed)
+// rref <- rref - K u32 on the free nodes (rref = f - K u64 before, the FP32 increment u32 since
+// the last fold), every product and sum in float pairs (df64.cuh): u32 is exact, the stencil
+// coefficients are integers (12 x the unit-cube Laplacian, 72 x Klam / Kmu) times the phase
+// constants as pairs, and the result is rounded to FP64 once per node.  Writes r = rref (FP32)
+// and max |rref| into rmax (replacement) or tmax (report).  The fold u64 += u32 follows.
+template <int CC>
+__global__ void __launch_bounds__(kDThreads) k_dreplace(DResArgs<float> a, const float* u32all, int into_rmax) {
+  __shared__ float2 mp[2 * 256];
+  __shared__ double red_sh[32];
+  const DGrid& g = a.g;
+  const int bl = blockIdx.y;
+  const int b = bl / a.L;
+  const int np2 = 2 * a.mat.n_phases;
+  for (int i = threadIdx.x; i < np2; i += blockDim.x) {
+    const df32 v = df_from_double(a.mat.m64[(long long)b * np2 + i]);
+    mp[i] = make_float2(v.hi, v.lo);
+  }
+  __syncthreads();
+  if (a.only_pending && !a.sc[bl].need_replace) return;
+  const long long n = g.ne;
+  const uint8_t* ph = a.phase + (long long)b * n;
+  const float* u32 = u32all + (long long)bl * CC * n;
+  double* rref = const_cast<double*>(a.f64) + (long long)bl * CC * n;
+  double lmax = 0.0;
+  for (long long fi = (long long)blockIdx.x * blockDim.x + threadIdx.x; fi < g.nf;
+       fi += (long long)gridDim.x * blockDim.x) {
+    int i1, i2, i3;
+    const long long node = dnode_of_free(g, fi, i1, i2, i3);
+    Nbr nb;
+    neighbours(g.pg, i1, i2, i3, nb);
+    double kw[CC];
+    if (CC == 1) {
+      df32 w[3][3][3];
+#pragma unroll
+      for (int s1 = 0; s1 < 3; ++s1)
+#pragma unroll
+        for (int s2 = 0; s2 < 3; ++s2)
+#pragma unroll
+          for (int s3 = 0; s3 < 3; ++s3) w[s1][s2][s3] = df_make(__ldg(u32 + nidx(nb, s1, s2, s3)));
+      df32 acc = df_make(0.0f);
+#pragma unroll
+      for (int o = 0; o < 8; ++o) {
+        const int o1 = (o >> 2) & 1, o2 = (o >> 1) & 1, o3 = o & 1;
+        df32 t = df_make(0.0f);
+        df_add_mul(t, 4.0f, w[1][1][1]);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int c1 = (c >> 2) & 1, c2 = (c >> 1) & 1, c3 = c & 1;
+          const int diff = (c1 != o1) + (c2 != o2) + (c3 != o3);
+          if (diff >= 2) df_add_mul(t, -1.0f, w[c1 - o1 + 1][c2 - o2 + 1][c3 - o3 + 1]);
+        }
+        const float2 kp = mp[2 * ph[eidx(nb, o1, o2, o3)]];
+        acc = df_add(acc, df_mul({kp.x, kp.y}, t));
+      }
+      kw[0] = df_to_double(acc) * (g.pg.h / 12.0);
+    } else {
+      df32 out[3] = {df_make(0.0f), df_make(0.0f), df_make(0.0f)};
+#pragma unroll 1
+      for (int o = 0; o < 8; ++o) {
+        const int o1 = (o >> 2) & 1, o2 = (o >> 1) & 1, o3 = o & 1;
+        df32 aL[3] = {df_make(0.0f), df_make(0.0f), df_make(0.0f)};
+        df32 aM[3] = {df_make(0.0f), df_make(0.0f), df_make(0.0f)};
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int c1 = (c >> 2) & 1, c2 = (c >> 1) & 1, c3 = c & 1;
+          const long long q = nidx(nb, c1 - o1 + 1, c2 - o2 + 1, c3 - o3 + 1);
+          const df32 wk[3] = {df_make(__ldg(u32 + q)), df_make(__ldg(u32 + n + q)), df_make(__ldg(u32 + 2 * n + q))};
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+              df_add_mul(aL[i], kElastic72.lam[o][i][c][k], wk[k]);
+              df_add_mul(aM[i], kElastic72.mu[o][i][c][k], wk[k]);
+            }
+        }
+        const int p = ph[eidx(nb, o1, o2, o3)];
+        const float2 lp = mp[2 * p], mu = mp[2 * p + 1];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+          out[i] = df_add(out[i], df_add(df_mul({lp.x, lp.y}, aL[i]), df_mul({mu.x, mu.y}, aM[i])));
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i) kw[i] = df_to_double(out[i]) * (g.pg.h / 72.0);
+    }
+#pragma unroll
+    for (int i = 0; i < CC; ++i) {
+      const double rr = rref[i * n + node] - kw[i];
+      rref[i * n + node] = rr;
+      if (a.r) a.r[(long long)bl * CC * n + i * n + node] = (float)rr;
+      lmax = fmax(lmax, fabs(rr));
+    }
+  }
+  const double bm = block_max(lmax, red_sh);
+  if (threadIdx.x == 0) atomic_max_nonneg(into_rmax ? &a.sc[bl].rmax_bits : &a.sc[bl].tmax_bits, bm);
+}
+
 // ============================================================================ Jacobi / plain CG
 // part 0: r -= alpha q, u += alpha p, ||r||_inf, stopping test
 // part 1: gamma = r . z with z = D^-1 r (or r), beta
@@ -846,6 +944,13 @@ cudaError_t launch_dmixq(const DPassArgs<T>& a, int pa, int pb, cudaStream_t s) 
 }
 template cudaError_t launch_dmixq<double>(const DPassArgs<double>&, int, int, cudaStream_t);
 template cudaError_t launch_dmixq<float>(const DPassArgs<float>&, int, int, cudaStream_t);
+
+cudaError_t launch_dreplace(const DResArgs<float>& a, const float* u32, int into_rmax, cudaStream_t s) {
+  dim3 grid(dgrid_blocks(a.g.nf), a.BL);
+  if (a.c == 1) k_dreplace<1><<<grid, kDThreads, 0, s>>>(a, u32, into_rmax);
+  else k_dreplace<3><<<grid, kDThreads, 0, s>>>(a, u32, into_rmax);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_dfold(const DGrid& g, int c, int BL, double* u64, float* u32, const CgScal* sc, int only_pending,
                          cudaStream_t s) {
