@@ -94,7 +94,7 @@ struct unocg_dir {
   bool plane[2];                // axes 3 and 2 in one plane pass (the plane fits a block)
   bool plane_reg = false;       // register-resident plane passes (N2 = N3 a power of two)
   int np = 0, pa = -1, pb = -1; // periodic axes (two: k_dmixq between the axis-1 passes)
-  bool line_reg = false;        // register-resident axis-1 pass with Q (c = 1, N1 a power of two)
+  bool line_reg_p[2] = {false, false};  // register-resident axis-1 pass with Q ([0] FP64, [1] FP32)
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   DKey key;
@@ -311,7 +311,7 @@ int ensure_workspace(unocg_dir* d, int precision, int precond) {
     DCK(cudaMalloc(&f.invdiag, (size_t)d->B * d->c * d->g.ne * eb));
   size_t need = (size_t)BL * std::max({(size_t)dku_blocks(d->g, d->c), (size_t)djac_blocks(d->g),
                                        (size_t)(d->np == 2 ? dmixq_blocks(d->g, d->pa, d->pb) : 0),
-                                       (size_t)(d->line_reg ? dline_reg_blocks(d->g) : 0),
+                                       (size_t)(d->line_reg_p[0] || d->line_reg_p[1] ? dline_reg_blocks(d->g) : 0),
                                        (size_t)dpass_blocks(d->g, d->c, DP_QMUL, std::min(d->w1[0], d->w1[1]))});
   if (d->part_len < need) {
     cudaFree(d->part);
@@ -418,7 +418,7 @@ cudaError_t enq_precond(unocg_dir* d, cudaStream_t s, const LoopCtl& ctl, int st
     e = launch_dpass<T>(m1, DP_MID1, s);
     if (e == cudaSuccess) e = launch_dmixq<T>(pass_args<T>(d, DP_QMUL, ctl, 0), d->pa, d->pb, s);
     if (e == cudaSuccess) e = launch_dpass<T>(m1, DP_MID1, s);
-  } else if (d->line_reg) {
+  } else if (d->line_reg_p[pidx<T>()]) {
     e = launch_dline_reg<T>(pass_args<T>(d, DP_QMUL, ctl, 0), s);
   } else {
     e = launch_dpass<T>(pass_args<T>(d, DP_QMUL, ctl, 0), DP_QMUL, s);
@@ -675,7 +675,8 @@ extern "C" int unocg_dir_create_bc(unocg_dir** out, int physics, int batch, int 
   }
   const bool all_dir = bc[0] && bc[1] && bc[2];
   d->plane_reg = all_dir && dplane_reg_ok(g);
-  d->line_reg = all_dir && dline_reg_ok(g, d->c);
+  d->line_reg_p[0] = all_dir && dline_reg_ok(g, d->c, 8);
+  d->line_reg_p[1] = all_dir && dline_reg_ok(g, d->c, 4);
   DCK(cudaStreamCreateWithFlags(&d->own_stream, cudaStreamNonBlocking));
   d->stream = d->own_stream;
   DCK(cudaMalloc(&d->phase, (size_t)batch * g.ne));
@@ -1086,7 +1087,7 @@ extern "C" int unocg_dir_apply_uno_dev(unocg_dir* d, int instance, const double*
     DCK(launch_dpass<double>(with(d->w1[0]), DP_MID1, s));
     DCK(launch_dmixq<double>(a, d->pa, d->pb, s));
     DCK(launch_dpass<double>(with(d->w1[0]), DP_MID1, s));
-  } else if (d->line_reg) {
+  } else if (d->line_reg_p[0]) {
     DCK(launch_dline_reg<double>(a, s));
   } else {
     DCK(launch_dpass<double>(with(d->w1[0]), DP_QMUL, s));

@@ -139,7 +139,7 @@ template <typename T> cudaError_t launch_dplane(const DPassArgs<T>& a, int fwd, 
 // register-resident versions (k_dirichlet_reg.cu): planes with N2 = N3 in {8, ..., 128}; axis 1
 // with the block multiply for c = 1 and N1 in {8, ..., 128}
 bool dplane_reg_ok(const DGrid& g);
-bool dline_reg_ok(const DGrid& g, int c);
+bool dline_reg_ok(const DGrid& g, int c, int elem_bytes);
 int dline_reg_blocks(const DGrid& g);
 template <typename T> cudaError_t launch_dplane_reg(const DPassArgs<T>& a, int fwd, cudaStream_t s);
 template <typename T> cudaError_t launch_dline_reg(const DPassArgs<T>& a, cudaStream_t s);

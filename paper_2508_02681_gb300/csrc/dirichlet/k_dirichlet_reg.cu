@@ -76,6 +76,18 @@ __device__ __forceinline__ void dst_store_scattered(const cplx<T>* v, T* buf, in
     }
 }
 
+// y = Q x for the unique entries q in the paper's order (v1=Q11 v2=Q22 v3=Q12 v4=Q33 v5=Q23 v6=Q13)
+template <typename T, int CC>
+__device__ __forceinline__ void qmul_reg(const T* __restrict__ q, const T* x, T* y) {
+  if (CC == 1) {
+    y[0] = q[0] * x[0];
+  } else {
+    y[0] = q[0] * x[0] + q[2] * x[1] + q[5] * x[2];
+    y[1] = q[2] * x[0] + q[1] * x[1] + q[4] * x[2];
+    y[2] = q[5] * x[0] + q[4] * x[1] + q[3] * x[2];
+  }
+}
+
 }  // namespace
 
 // ============================================================================ planes
@@ -164,8 +176,11 @@ __global__ void __launch_bounds__(kPlaneWarps * 32) k_dplane_reg(DPassArgs<T> a)
   }
 }
 
-// ============================================================================ axis 1 with Q (c = 1)
-template <typename T, int N>
+// ============================================================================ axis 1 with Q
+// Every lane group transforms the same two positions for all CC components in turn, so the
+// spectral indices it holds are the same for every component and the c x c block multiply
+// needs no exchange.
+template <typename T, int N, int CC>
 __global__ void __launch_bounds__(kLineWarps * 32) k_dline_reg(DPassArgs<T> a) {
   using C = cplx<T>;
   using R = DReg<N>;
@@ -174,74 +189,96 @@ __global__ void __launch_bounds__(kLineWarps * 32) k_dline_reg(DPassArgs<T> a) {
   constexpr int TP = W + 1;                   // tile pitch
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ double red_sh[32];
-  T* tile = reinterpret_cast<T*>(dsm);  // N x TP reals: [j1][position]
-  C* scr = reinterpret_cast<C*>(dsm + ((sizeof(T) * N * TP + 15) / 16) * 16);
+  T* tile = reinterpret_cast<T*>(dsm);  // CC x N x TP reals: [comp][j1][position]
+  C* scr = reinterpret_cast<C*>(dsm + ((sizeof(T) * CC * N * TP + 15) / 16) * 16);
   C* tw = scr + kLineWarps * R::PPW * R::L;
   const DGrid& g = a.g;
   const int bl = blockIdx.y;
   const int nb3 = (g.m3 + W - 1) / W;
   const int k2 = blockIdx.x / nb3, k30 = (blockIdx.x - k2 * nb3) * W;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long base = (long long)bl * g.ne;  // c = 1
+  const long long base = (long long)bl * CC * g.ne;
   const bool active = a.standalone || !a.sc[bl].done;
   DotAcc<T> acc;
   if (active) {
     ld_tw<T>(tw, a.t.tw[0], R::L);
-    for (int idx = threadIdx.x; idx < N * W; idx += blockDim.x) {
-      const int j = idx / W, w = idx - j * W;
+    for (int idx = threadIdx.x; idx < CC * N * W; idx += blockDim.x) {
+      const int w = idx % W, r = idx / W;
+      const int j = r % N, comp = r / N;
       const int k3 = k30 + w;
       T x = (T)0;
-      if (j < M && k3 < g.m3) x = a.hat[base + ((long long)(j + 1) * g.n2 + k2 + 1) * g.n3 + k3 + 1];
-      tile[j * TP + w] = x;
+      if (j < M && k3 < g.m3)
+        x = a.hat[base + comp * g.ne + ((long long)(j + 1) * g.n2 + k2 + 1) * g.n3 + k3 + 1];
+      tile[(comp * N + j) * TP + w] = x;
     }
     __syncthreads();
     {
       const int pr = warp * R::PPW + lane / R::G, gl = lane % R::G;
       const int wa = 2 * pr;
-      C v[R::V];
-      dst_load<N, T>(v, tile, wa, 1, TP, gl);
       C* sp = scr + pr * R::L;
-      fft_dist_a<R::L, -1>(v, gl, sp, 1, tw);
+      C v[CC][R::V];
+#pragma unroll
+      for (int cc = 0; cc < CC; ++cc) {
+        dst_load<N, T>(v[cc], tile + cc * N * TP, wa, 1, TP, gl);
+        fft_dist_a<R::L, -1>(v[cc], gl, sp, 1, tw);
+      }
       // block multiply at the held spectral indices (scattered order)
       const T* Q = reinterpret_cast<const T*>(a.Q) + (long long)(bl / a.L) * a.q_inst_stride;
       const int k3a = k30 + wa, k3b = k3a + 1;
+      constexpr int NQ = CC == 1 ? 1 : 6;
 #pragma unroll
       for (int j = 0; j < R::VG; ++j)
 #pragma unroll
         for (int t = 0; t < R::G; ++t) {
           const int m = scat_index<R::L>(gl, j, t);
-          C& z = v[j * R::G + t];
+          const int e = j * R::G + t;
           if (m == 0 || m == N) {
-            z = mk<T>((T)0, (T)0);
+#pragma unroll
+            for (int cc = 0; cc < CC; ++cc) v[cc][e] = mk<T>((T)0, (T)0);
             continue;
           }
           const int k = (m < N ? m : 2 * N - m) - 1;
           const long long row = ((long long)k * g.m2 + k2) * g.m3;
-          const T qa = k3a < g.m3 ? Q[row + k3a] : (T)0;
-          const T qb = k3b < g.m3 ? Q[row + k3b] : (T)0;
-          const T xa = (T)-0.5 * z.y, xb = (T)0.5 * z.x;  // w = (i/2) Z
-          if (m < N) {
-            acc.add_prod(xa, qa * xa);
-            acc.add_prod(xb, qb * xb);
-          }
-          z = mk<T>(qa * xa, qb * xb);
-        }
-      fft_dist_b<R::L, -1>(v, gl, sp, 1, tw);
-      // natural order: lane gl holds Z2[gl + G n1]
+          T xa[CC], xb[CC], ya[CC], yb[CC];
 #pragma unroll
-      for (int n1 = 0; n1 < R::V; ++n1) {
-        const int m = gl + R::G * n1;
-        if (m >= 1 && m < N) {
-          tile[(m - 1) * TP + wa] = (T)-0.5 * v[n1].y;
-          tile[(m - 1) * TP + wa + 1] = (T)0.5 * v[n1].x;
+          for (int cc = 0; cc < CC; ++cc) {
+            xa[cc] = (T)-0.5 * v[cc][e].y;  // w = (i/2) Z
+            xb[cc] = (T)0.5 * v[cc][e].x;
+          }
+          if (k3a < g.m3) qmul_reg<T, CC>(Q + (row + k3a) * NQ, xa, ya);
+          else for (int cc = 0; cc < CC; ++cc) ya[cc] = (T)0;
+          if (k3b < g.m3) qmul_reg<T, CC>(Q + (row + k3b) * NQ, xb, yb);
+          else for (int cc = 0; cc < CC; ++cc) yb[cc] = (T)0;
+#pragma unroll
+          for (int cc = 0; cc < CC; ++cc) {
+            if (m < N) {
+              acc.add_prod(xa[cc], ya[cc]);
+              acc.add_prod(xb[cc], yb[cc]);
+            }
+            v[cc][e] = mk<T>(ya[cc], yb[cc]);
+          }
+        }
+#pragma unroll
+      for (int cc = 0; cc < CC; ++cc) {
+        fft_dist_b<R::L, -1>(v[cc], gl, sp, 1, tw);
+        // natural order: lane gl holds Z2[gl + G n1]
+#pragma unroll
+        for (int n1 = 0; n1 < R::V; ++n1) {
+          const int m = gl + R::G * n1;
+          if (m >= 1 && m < N) {
+            tile[(cc * N + m - 1) * TP + wa] = (T)-0.5 * v[cc][n1].y;
+            tile[(cc * N + m - 1) * TP + wa + 1] = (T)0.5 * v[cc][n1].x;
+          }
         }
       }
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < M * W; idx += blockDim.x) {
-      const int j = idx / W, w = idx - j * W;
+    for (int idx = threadIdx.x; idx < CC * M * W; idx += blockDim.x) {
+      const int w = idx % W, r = idx / W;
+      const int j = r % M, comp = r / M;
       const int k3 = k30 + w;
-      if (k3 < g.m3) a.hat[base + ((long long)(j + 1) * g.n2 + k2 + 1) * g.n3 + k3 + 1] = tile[j * TP + w];
+      if (k3 < g.m3)
+        a.hat[base + comp * g.ne + ((long long)(j + 1) * g.n2 + k2 + 1) * g.n3 + k3 + 1] = tile[(comp * N + j) * TP + w];
     }
   }
   if (a.standalone) return;
@@ -264,16 +301,22 @@ template <typename T, int N> static size_t plane_reg_smem() {
   using R = DReg<N>;
   return ((sizeof(T) * N * R::PITCH + 15) / 16) * 16 + sizeof(cplx<T>) * ((size_t)kPlaneWarps * R::PPW * R::L + R::L);
 }
-template <typename T, int N> static size_t line_reg_smem() {
+template <typename T, int N, int CC> static size_t line_reg_smem() {
   using R = DReg<N>;
   constexpr int W = kLineWarps * R::PPW * 2;
-  return ((sizeof(T) * N * (W + 1) + 15) / 16) * 16 + sizeof(cplx<T>) * ((size_t)kLineWarps * R::PPW * R::L + R::L);
+  return ((sizeof(T) * CC * N * (W + 1) + 15) / 16) * 16 + sizeof(cplx<T>) * ((size_t)kLineWarps * R::PPW * R::L + R::L);
 }
 
 static bool pow2_small(int n) { return n == 8 || n == 16 || n == 32 || n == 64 || n == 128; }
 
 bool dplane_reg_ok(const DGrid& g) { return g.n2 == g.n3 && pow2_small(g.n3); }
-bool dline_reg_ok(const DGrid& g, int c) { return c == 1 && pow2_small(g.n1); }
+// c = 1 only: for c = 3 the 3 x V complex values per thread (174 registers at N1 = 64, FP32)
+// leave two blocks per SM, and the shared-memory pass is faster (64^3 elastic Dirichlet solve,
+// six loads, mixed: 16.0 vs 17.1 ms)
+bool dline_reg_ok(const DGrid& g, int c, int elem_bytes) {
+  (void)elem_bytes;
+  return pow2_small(g.n1) && c == 1;
+}
 
 int dline_reg_positions(int n1) {
   switch (n1) {
@@ -299,13 +342,18 @@ static cudaError_t plane_go(const DPassArgs<T>& a, int fwd, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <typename T, int N, int CC>
+static cudaError_t line_go_c(const DPassArgs<T>& a, cudaStream_t s) {
+  const size_t smem = line_reg_smem<T, N, CC>();
+  cudaError_t e = cudaFuncSetAttribute(k_dline_reg<T, N, CC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_dline_reg<T, N, CC><<<dim3(dline_reg_blocks(a.g), a.BL), kLineWarps * 32, smem, s>>>(a);
+  return cudaGetLastError();
+}
 template <typename T, int N>
 static cudaError_t line_go(const DPassArgs<T>& a, cudaStream_t s) {
-  const size_t smem = line_reg_smem<T, N>();
-  cudaError_t e = cudaFuncSetAttribute(k_dline_reg<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k_dline_reg<T, N><<<dim3(dline_reg_blocks(a.g), a.BL), kLineWarps * 32, smem, s>>>(a);
-  return cudaGetLastError();
+  if (a.c == 1) return line_go_c<T, N, 1>(a, s);
+  return cudaErrorInvalidValue;
 }
 
 template <typename T>
