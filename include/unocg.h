@@ -91,7 +91,8 @@ typedef struct {
                         1 one CUDA graph with conditional nodes (device-side control);
                         2 one persistent cooperative kernel with grid barriers (UNO only,
                           problems whose phase buffers fit in shared memory);
-                        3 automatic: 2 for small problems, else 1                            */
+                        3 automatic: the driver chosen by unocg_autotune / unocg_set_tuning,
+                          else 1                                                             */
   double replace_drop; /* MIXED: also replace once ||r||_inf has fallen below replace_drop
                           times its value at the previous replacement (reliable updates: the
                           FP32 solution increment since then stays small); 0 disables, 1e-3
@@ -116,6 +117,17 @@ typedef struct {
 int unocg_create(unocg_ctx** out, int physics, int batch, int n1, int n2, int n3, double L0);
 void unocg_destroy(unocg_ctx* ctx);
 const char* unocg_last_error(const unocg_ctx* ctx);
+
+/* Tuning of the periodic solver: radix_order of the shared-memory Stockham plans (0: radix 8,
+   4, 2, then 3, 5; 1: radix 4, 2, 3, 5; 2: radix 5, 3, then 4, 2; the register FFT passes of
+   power-of-two axes have no radix choice) and the loop driver that use_graph = 3 takes (1 graph,
+   2 persistent kernel when it fits).  Invalidates the captured graph.                       */
+int unocg_set_tuning(unocg_ctx* ctx, int radix_order, int path);
+/* Autotuner (batched solves, config sweeps): times `reps` solves of `opts` (after one warm-up
+   solve each) for every radix order and loop driver, writes the mean ms to
+   times[radix_order * 2 + (path - 1)] (double[6]; NaN where the persistent kernel does not
+   fit) and keeps the fastest setting.  Needs the inputs and weights set.                    */
+int unocg_autotune(unocg_ctx* ctx, const unocg_solve_opts* opts, int reps, double* times);
 
 /* Upper bound of any device-side wait of this context (the grid barrier of the persistent
    loop), in seconds (default 1).  A wait that expires makes every block of the launch return
@@ -313,6 +325,17 @@ int unocg_dir_get_effective_tensor(unocg_dir* ctx, double* out);
 /* q = K p and s = T^T Q T r (FP64, device [c][M1][M2][M3]) for one instance.                 */
 int unocg_dir_apply_K_dev(unocg_dir* ctx, int instance, const double* p_dev, double* q_dev, void* stream);
 int unocg_dir_apply_uno_dev(unocg_dir* ctx, int instance, const double* r_dev, double* s_dev, void* stream);
+/* Pass engines of one precision (UNOCG_FP64 / UNOCG_MIXED): plane_engine 0 register plane
+   passes (Dirichlet faces everywhere, N2 = N3 a power of two <= 128), 1 shared-memory plane
+   passes (the plane fits a block), 2 separate axis-3 and axis-2 passes; line_engine 0 register
+   axis-1 pass with the block multiply (Dirichlet faces everywhere, c = 1, N1 a power of two
+   <= 128), 1 shared-memory pass.  UNOCG_ERR_INVALID_ARG when not applicable.  Defaults at
+   creation: the register engines where they apply, else shared-memory planes up to 110 KB.  */
+int unocg_dir_set_tuning(unocg_dir* ctx, int precision, int plane_engine, int line_engine);
+/* Autotuner: times `reps` solves of `opts` (after one warm-up solve each) for every applicable
+   engine pair of opts->precision, writes the mean ms to times[plane_engine * 2 + line_engine]
+   (double[6]; NaN where not applicable) and keeps the fastest pair.  Needs the inputs set.   */
+int unocg_dir_autotune(unocg_dir* ctx, const unocg_solve_opts* opts, int reps, double* times);
 
 #ifdef __cplusplus
 }

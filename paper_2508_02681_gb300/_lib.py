@@ -78,6 +78,8 @@ SIGNATURES = {
     "unocg_get_sensitivity": (_i, [_vp, _vp]),
     "unocg_batch_solve": (_i, [_i, C.POINTER(_vp), C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
     "unocg_profile_iteration": (_i, [_vp, C.POINTER(SolveOpts), _i, _vp, _i]),
+    "unocg_set_tuning": (_i, [_vp, _i, _i]),
+    "unocg_autotune": (_i, [_vp, C.POINTER(SolveOpts), _i, _vp]),
     "unocg_uno_create": (_i, [C.POINTER(_vp), _i, _i, _i, _i]),
     "unocg_uno_destroy": (None, [_vp]),
     "unocg_uno_last_error": (C.c_char_p, [_vp]),
@@ -110,6 +112,8 @@ SIGNATURES = {
     "unocg_dir_get_effective_tensor": (_i, [_vp, _vp]),
     "unocg_dir_apply_K_dev": (_i, [_vp, _i, _vp, _vp, _vp]),
     "unocg_dir_apply_uno_dev": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "unocg_dir_set_tuning": (_i, [_vp, _i, _i, _i]),
+    "unocg_dir_autotune": (_i, [_vp, C.POINTER(SolveOpts), _i, _vp]),
 }
 
 _LIB = None

@@ -373,3 +373,26 @@ def unocg_dir_apply_K_dev(ctx, instance: int, p_dev, q_dev, stream=None):
 def unocg_dir_apply_uno_dev(ctx, instance: int, r_dev, s_dev, stream=None):
     _dcheck(ctx, _lib.load().unocg_dir_apply_uno_dev(ctx, instance, C.c_void_p(r_dev.data_ptr()),
                                                      C.c_void_p(s_dev.data_ptr()), _stream(stream)))
+
+
+# ---------------------------------------------------------------- tuning
+def unocg_set_tuning(ctx, radix_order: int, path: int):
+    _check(ctx, _lib.load().unocg_set_tuning(ctx, radix_order, path))
+
+
+def unocg_autotune(ctx, opts: SolveOpts, reps: int = 3) -> np.ndarray:
+    """Mean ms per solve for [radix_order][driver] (driver 0 graph, 1 persistent; NaN: n/a)."""
+    out = np.zeros(6)
+    _check(ctx, _lib.load().unocg_autotune(ctx, C.byref(opts), reps, _ptr(out)))
+    return out.reshape(3, 2)
+
+
+def unocg_dir_set_tuning(ctx, precision: int, plane_engine: int, line_engine: int):
+    _dcheck(ctx, _lib.load().unocg_dir_set_tuning(ctx, precision, plane_engine, line_engine))
+
+
+def unocg_dir_autotune(ctx, opts: SolveOpts, reps: int = 3) -> np.ndarray:
+    """Mean ms per solve for [plane_engine][line_engine] (NaN: not applicable)."""
+    out = np.zeros(6)
+    _dcheck(ctx, _lib.load().unocg_dir_autotune(ctx, C.byref(opts), reps, _ptr(out)))
+    return out.reshape(3, 2)

@@ -29,15 +29,22 @@ namespace {
 constexpr int kMaxTickets = 8;
 enum Ticket { T_PLANE = 0, T_LINE = 1, T_KU = 2, T_JAC = 3, T_PLANE2 = 4, T_JAC2 = 5 };
 
-bool factor_plan(int N, FftPlan* p) {
+// Radix plans of the shared-memory Stockham passes.  order 0: radix 8, 4, 2, then 3, 5 (fewest
+// stages, the default); 1: radix 4, 2, 3, 5 (no radix 8: fewer registers per butterfly);
+// 2: radix 5, 3 first, then 4, 2.  The autotuner picks one per context.
+bool factor_plan(int N, FftPlan* p, int order = 0) {
   p->N = N;
   p->nst = 0;
   int m = N;
-  while (m % 8 == 0) { p->radix[p->nst++] = 8; m /= 8; }
-  while (m % 4 == 0) { p->radix[p->nst++] = 4; m /= 4; }
-  while (m % 2 == 0) { p->radix[p->nst++] = 2; m /= 2; }
-  while (m % 3 == 0) { p->radix[p->nst++] = 3; m /= 3; }
-  while (m % 5 == 0) { p->radix[p->nst++] = 5; m /= 5; }
+  auto take = [&](int r) {
+    while (m % r == 0 && p->nst < 12) { p->radix[p->nst++] = r; m /= r; }
+  };
+  if (order == 2) { take(5); take(3); }
+  if (order == 0) take(8);
+  take(4);
+  take(2);
+  take(3);
+  take(5);
   return m == 1 && p->nst <= 12;
 }
 
@@ -124,6 +131,9 @@ struct unocg_ctx {
   cudaGraphExec_t exec = nullptr;
   GraphKey key;
   unocg_solve_opts last_opts{};
+  // tuning (unocg_set_tuning / unocg_autotune): radix order of the Stockham plans and the loop
+  // driver taken by use_graph = 3
+  int radix_order = 0, tuned_path = 1;
 };
 
 struct unocg_uno {
@@ -1006,8 +1016,9 @@ extern "C" int unocg_solve_async(unocg_ctx* ctx, const unocg_solve_opts* o) {
   ctx->last_precision = o->precision;
   ctx->solved = false;
   int path = o->use_graph;
-  // automatic: the graph loop (a kernel boundary in a graph costs less than a grid barrier)
-  if (path == 3) path = 1;
+  // automatic: the driver chosen by the autotuner, else the graph loop (a kernel boundary in a
+  // graph costs less than a grid barrier)
+  if (path == 3) path = (ctx->tuned_path == 2 && persistent_fits(ctx, o)) ? 2 : 1;
   if (path == 2 && !persistent_fits(ctx, o)) return fail(ctx, UNOCG_ERR_INVALID_ARG, "problem too large for the persistent kernel");
   ctx->last_path = path;
   if (path == 0) {
@@ -1542,4 +1553,62 @@ extern "C" int unocg_uno_backward_dev(unocg_uno* op, int batch, const float* r_d
       UCK(launch_psi_grad(op->theta, op->gq2, gtheta_dev, op->g.nh, op->c, s));
   }
   return UNOCG_OK;
+}
+
+
+// ------------------------------------------------------------------ tuning
+extern "C" int unocg_set_tuning(unocg_ctx* ctx, int radix_order, int path) {
+  if (!ctx || radix_order < 0 || radix_order > 2 || (path != 1 && path != 2)) return fail(ctx, UNOCG_ERR_INVALID_ARG, "invalid tuning");
+  FftPlan p1{}, p2{}, p3h{};
+  if (!factor_plan(ctx->g.n1, &p1, radix_order) || !factor_plan(ctx->g.n2, &p2, radix_order) ||
+      !factor_plan(ctx->g.n3 / 2, &p3h, radix_order))
+    return fail(ctx, UNOCG_ERR_INVALID_ARG, "radix plan");
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->p1 = p1;
+  ctx->p2 = p2;
+  ctx->p3h = p3h;
+  ctx->radix_order = radix_order;
+  ctx->tuned_path = path;
+  free_graph(ctx);  // the captured launches hold the old plans
+  return UNOCG_OK;
+}
+
+// Times `reps` solves (CUDA events on the context stream, after one warm-up solve that also
+// builds the graph) for each radix order (0..2) and loop driver (graph, persistent); writes the
+// mean milliseconds to times[order * 2 + (driver == persistent)] (NaN where the persistent
+// kernel does not fit) and keeps the fastest setting.
+extern "C" int unocg_autotune(unocg_ctx* ctx, const unocg_solve_opts* o, int reps, double* times) {
+  if (!ctx || !o || reps < 1 || !times) return fail(ctx, UNOCG_ERR_INVALID_ARG, "invalid autotune arguments");
+  double best = 1e300;
+  int bo = 0, bp = 1;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int rc = UNOCG_OK;
+  for (int order = 0; order < 3 && rc == UNOCG_OK; ++order)
+    for (int path = 1; path <= 2 && rc == UNOCG_OK; ++path) {
+      double* t = times + order * 2 + (path - 1);
+      *t = std::nan("");
+      unocg_solve_opts oo = *o;
+      oo.use_graph = path;
+      if (path == 2 && !persistent_fits(ctx, &oo)) continue;
+      rc = unocg_set_tuning(ctx, order, path);
+      if (rc) break;
+      rc = unocg_solve(ctx, &oo, nullptr);
+      if (rc) break;
+      float ms = 0.f;
+      if (cudaEventRecord(e0, ctx->stream) != cudaSuccess) { rc = fail(ctx, UNOCG_ERR_CUDA, "event"); break; }
+      for (int r = 0; r < reps && rc == UNOCG_OK; ++r) rc = unocg_solve_async(ctx, &oo);
+      if (rc) break;
+      if (cudaEventRecord(e1, ctx->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) { rc = fail(ctx, UNOCG_ERR_CUDA, "event timing"); break; }
+      rc = unocg_solve_wait(ctx, nullptr);
+      if (rc) break;
+      *t = ms / reps;
+      if (*t < best) { best = *t; bo = order; bp = path; }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  return unocg_set_tuning(ctx, bo, bp);
 }

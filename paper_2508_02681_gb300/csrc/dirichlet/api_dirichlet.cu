@@ -91,8 +91,10 @@ struct unocg_dir {
   double* ceff = nullptr;
   double *stage_a = nullptr, *stage_b = nullptr, *stage_f = nullptr;  // operator-level I/O
   int lines3[2], w2[2], w1[2];  // [0] FP64, [1] FP32
-  bool plane[2];                // axes 3 and 2 in one plane pass (the plane fits a block)
-  bool plane_reg = false;       // register-resident plane passes (N2 = N3 a power of two)
+  // pass engines per precision ([0] FP64, [1] FP32): axes 3 and 2 as register plane passes (0,
+  // N2 = N3 a power of two, Dirichlet faces everywhere), shared-memory plane passes (1, the plane
+  // fits a block) or separate axis-3 and axis-2 passes (2); set at creation, or by the autotuner
+  int plane_engine[2] = {2, 2};
   int np = 0, pa = -1, pb = -1; // periodic axes (two: k_dmixq between the axis-1 passes)
   bool line_reg_p[2] = {false, false};  // register-resident axis-1 pass with Q ([0] FP64, [1] FP32)
   cudaGraph_t graph = nullptr;
@@ -366,8 +368,8 @@ DJacArgs<T> jac_args(unocg_dir* d, const DPlan& pl, const LoopCtl& ctl, int part
 template <typename T>
 cudaError_t enq_check(unocg_dir* d, cudaStream_t s, const DPlan& pl, const LoopCtl& ctl, int after_replace) {
   if (pl.o.precond == UNOCG_PRECOND_UNO) {
-    if (d->plane_reg) return launch_dplane_reg<T>(pass_args<T>(d, DP_FIRST, ctl, after_replace), 1, s);
-    if (d->plane[pidx<T>()]) return launch_dplane<T>(pass_args<T>(d, DP_FIRST, ctl, after_replace), 1, s);
+    if (d->plane_engine[pidx<T>()] == 0) return launch_dplane_reg<T>(pass_args<T>(d, DP_FIRST, ctl, after_replace), 1, s);
+    if (d->plane_engine[pidx<T>()] == 1) return launch_dplane<T>(pass_args<T>(d, DP_FIRST, ctl, after_replace), 1, s);
     return launch_dpass<T>(pass_args<T>(d, DP_FIRST, ctl, after_replace), DP_FIRST, s);
   }
   return launch_djac<T>(jac_args<T>(d, pl, ctl, 0, after_replace), 0, s);
@@ -410,7 +412,7 @@ template <typename T>
 cudaError_t enq_precond(unocg_dir* d, cudaStream_t s, const LoopCtl& ctl, int standalone_lines_dummy = 0) {
   (void)standalone_lines_dummy;
   cudaError_t e = cudaSuccess;
-  const bool plane = d->plane_reg || d->plane[pidx<T>()];
+  const bool plane = d->plane_engine[pidx<T>()] != 2;
   if (!plane) e = launch_dpass<T>(pass_args<T>(d, DP_MID, ctl, 0), DP_MID, s);
   if (e != cudaSuccess) return e;
   if (d->np == 2) {
@@ -424,7 +426,7 @@ cudaError_t enq_precond(unocg_dir* d, cudaStream_t s, const LoopCtl& ctl, int st
     e = launch_dpass<T>(pass_args<T>(d, DP_QMUL, ctl, 0), DP_QMUL, s);
   }
   if (e != cudaSuccess) return e;
-  if (d->plane_reg) return launch_dplane_reg<T>(pass_args<T>(d, DP_LAST, ctl, 0), 0, s);
+  if (d->plane_engine[pidx<T>()] == 0) return launch_dplane_reg<T>(pass_args<T>(d, DP_LAST, ctl, 0), 0, s);
   if (plane) return launch_dplane<T>(pass_args<T>(d, DP_LAST, ctl, 0), 0, s);
   e = launch_dpass<T>(pass_args<T>(d, DP_MID, ctl, 0), DP_MID, s);
   if (e == cudaSuccess) e = launch_dpass<T>(pass_args<T>(d, DP_LAST, ctl, 0), DP_LAST, s);
@@ -671,10 +673,10 @@ extern "C" int unocg_dir_create_bc(unocg_dir** out, int physics, int batch, int 
     d->w1[p] = fit_w(n1, d->c, eb, d->c == 1 ? 32 : 16);
     // one plane per block pays while two blocks fit an SM (measured: FP32 64^3 7.5 vs 8.6 ms per
     // solve; FP64 64^3 with 130 KB planes 30.0 vs 26.4 ms)
-    d->plane[p] = dplane_smem_bytes(g, eb) <= 110 * 1024;
+    d->plane_engine[p] = dplane_smem_bytes(g, eb) <= 110 * 1024 ? 1 : 2;
   }
   const bool all_dir = bc[0] && bc[1] && bc[2];
-  d->plane_reg = all_dir && dplane_reg_ok(g);
+  if (all_dir && dplane_reg_ok(g)) d->plane_engine[0] = d->plane_engine[1] = 0;
   d->line_reg_p[0] = all_dir && dline_reg_ok(g, d->c, 8);
   d->line_reg_p[1] = all_dir && dline_reg_ok(g, d->c, 4);
   DCK(cudaStreamCreateWithFlags(&d->own_stream, cudaStreamNonBlocking));
@@ -1076,8 +1078,8 @@ extern "C" int unocg_dir_apply_uno_dev(unocg_dir* d, int instance, const double*
     b.lines = lines;
     return b;
   };
-  const bool plane = d->plane_reg || d->plane[0];
-  if (d->plane_reg) DCK(launch_dplane_reg<double>(a, 1, s));
+  const bool plane = d->plane_engine[0] != 2;
+  if (d->plane_engine[0] == 0) DCK(launch_dplane_reg<double>(a, 1, s));
   else if (plane) DCK(launch_dplane<double>(a, 1, s));
   else {
     DCK(launch_dpass<double>(with(d->lines3[0]), DP_FIRST, s));
@@ -1092,7 +1094,7 @@ extern "C" int unocg_dir_apply_uno_dev(unocg_dir* d, int instance, const double*
   } else {
     DCK(launch_dpass<double>(with(d->w1[0]), DP_QMUL, s));
   }
-  if (d->plane_reg) DCK(launch_dplane_reg<double>(a, 0, s));
+  if (d->plane_engine[0] == 0) DCK(launch_dplane_reg<double>(a, 0, s));
   else if (plane) DCK(launch_dplane<double>(a, 0, s));
   else {
     DCK(launch_dpass<double>(with(d->w2[0]), DP_MID, s));
@@ -1100,4 +1102,74 @@ extern "C" int unocg_dir_apply_uno_dev(unocg_dir* d, int instance, const double*
   }
   DCK(launch_dgather(d->g, d->c, d->stage_a, s_dev, s));
   return UNOCG_OK;
+}
+
+
+// ------------------------------------------------------------------ tuning
+extern "C" int unocg_dir_set_tuning(unocg_dir* d, int precision, int plane_engine, int line_engine) {
+  if (!d || (precision != UNOCG_FP64 && precision != UNOCG_MIXED) || plane_engine < 0 || plane_engine > 2 ||
+      line_engine < 0 || line_engine > 1)
+    return dfail(d, UNOCG_ERR_INVALID_ARG, "invalid tuning");
+  const int p = precision == UNOCG_FP64 ? 0 : 1;
+  const int eb = p == 0 ? 8 : 4;
+  const bool all_dir = d->g.bc[0] && d->g.bc[1] && d->g.bc[2];
+  int dev = 0, smem_max = 0;
+  DCK(cudaGetDevice(&dev));
+  DCK(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (plane_engine == 0 && !(all_dir && dplane_reg_ok(d->g)))
+    return dfail(d, UNOCG_ERR_INVALID_ARG, "register plane passes need Dirichlet faces and N2 = N3 a power of two <= 128");
+  if (plane_engine == 1 && dplane_smem_bytes(d->g, eb) > (size_t)smem_max)
+    return dfail(d, UNOCG_ERR_INVALID_ARG, "the plane does not fit a block's shared memory");
+  if (line_engine == 0 && !(all_dir && dline_reg_ok(d->g, d->c, eb)))
+    return dfail(d, UNOCG_ERR_INVALID_ARG, "register axis-1 pass needs Dirichlet faces, c = 1 and N1 a power of two <= 128");
+  DCK(cudaStreamSynchronize(d->stream));
+  d->plane_engine[p] = plane_engine;
+  d->line_reg_p[p] = line_engine == 0;
+  size_t need = (size_t)d->B * d->L * (size_t)(d->line_reg_p[p] ? dline_reg_blocks(d->g) : 0);
+  if (need > d->part_len) {
+    cudaFree(d->part);
+    d->part = nullptr;
+    DCK(cudaMalloc(&d->part, need * sizeof(double)));
+    d->part_len = need;
+  }
+  dfree_graph(d);
+  return UNOCG_OK;
+}
+
+// Times `reps` solves of `opts` (events on the context stream, after a warm-up solve that builds
+// the graph) for every applicable pair (plane engine 0..2, axis-1 engine 0..1) of the solve's
+// precision; times[plane * 2 + line] = mean milliseconds (NaN where not applicable); keeps the
+// fastest.
+extern "C" int unocg_dir_autotune(unocg_dir* d, const unocg_solve_opts* o, int reps, double* times) {
+  if (!d || !o || reps < 1 || !times) return dfail(d, UNOCG_ERR_INVALID_ARG, "invalid autotune arguments");
+  double best = 1e300;
+  int bpl = -1, bli = -1;
+  cudaEvent_t e0, e1;
+  DCK(cudaEventCreate(&e0));
+  DCK(cudaEventCreate(&e1));
+  int rc = UNOCG_OK;
+  for (int pe = 0; pe < 3 && rc == UNOCG_OK; ++pe)
+    for (int le = 0; le < 2 && rc == UNOCG_OK; ++le) {
+      double* t = times + pe * 2 + le;
+      *t = std::nan("");
+      if (d->np == 2 && le == 0) continue;  // two periodic axes: the axis-1 passes are fixed
+      if (unocg_dir_set_tuning(d, o->precision, pe, le) != UNOCG_OK) continue;
+      rc = unocg_dir_solve(d, o, nullptr);
+      if (rc) break;
+      float ms = 0.f;
+      if (cudaEventRecord(e0, d->stream) != cudaSuccess) { rc = dfail(d, UNOCG_ERR_CUDA, "event"); break; }
+      for (int r = 0; r < reps && rc == UNOCG_OK; ++r) rc = unocg_dir_solve_async(d, o);
+      if (rc) break;
+      if (cudaEventRecord(e1, d->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) { rc = dfail(d, UNOCG_ERR_CUDA, "event timing"); break; }
+      rc = unocg_dir_solve_wait(d, nullptr);
+      if (rc) break;
+      *t = ms / reps;
+      if (*t < best) { best = *t; bpl = pe; bli = le; }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  if (bpl < 0) return dfail(d, UNOCG_ERR_STATE, "no applicable pass engine");
+  return unocg_dir_set_tuning(d, o->precision, bpl, bli);
 }

@@ -7,6 +7,30 @@ import numpy as np
 from . import _lib, api
 
 
+def _tuning_cache(path, key, measure, apply):
+    """Autotune cache (a JSON file of key -> chosen setting): apply the stored setting for
+    ``key``, else ``measure()`` -> (setting, table), store and apply it.  Returns (setting,
+    table or None)."""
+    import json
+    import os
+    cache = {}
+    if path and os.path.exists(path):
+        with open(path) as fh:
+            cache = json.load(fh)
+    if key in cache:
+        apply(cache[key])
+        return cache[key], None
+    setting, table = measure()
+    apply(setting)
+    if path:
+        cache[key] = setting
+        tmp = path + ".tmp"
+        with open(tmp, "w") as fh:
+            json.dump(cache, fh, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    return setting, table
+
+
 class Homogenization:
     """One context: ``batch`` instances of an ``n1 x n2 x n3`` periodic voxel problem.
 
@@ -56,6 +80,19 @@ class Homogenization:
 
     def solve(self, raise_on_error: bool = True, **opts) -> api.Info:
         return api.unocg_solve(self.ctx, api.make_opts(**opts), self.batch * self.n_loads, raise_on_error)
+
+    def autotune(self, cache: str | None = None, reps: int = 3, **opts):
+        """Radix order of the Stockham plans and loop driver (``use_graph=3`` then takes it),
+        measured on this context's inputs or read from the JSON ``cache``."""
+        o = api.make_opts(**opts)
+        key = f"periodic:{self.physics}:{list(self.shape)}:{self.batch}x{self.n_loads}:{o.precision}:{o.precond}"
+
+        def measure():
+            t = api.unocg_autotune(self.ctx, o, reps)
+            i = int(np.nanargmin(t))
+            return [i // 2, i % 2 + 1], t
+
+        return _tuning_cache(cache, key, measure, lambda s: api.unocg_set_tuning(self.ctx, int(s[0]), int(s[1])))
 
     def fluctuation(self, instance: int = 0, load: int = 0) -> np.ndarray:
         """Zero-mean fluctuation, interleaved ``[n * c]`` (the paper's DOF order)."""
@@ -123,6 +160,22 @@ class DirichletHomogenization:
     def solve(self, raise_on_error: bool = True, **opts) -> api.Info:
         opts.setdefault("flexible", 0)
         return api.unocg_dir_solve(self.ctx, api.make_opts(**opts), self.batch * self.n_loads, raise_on_error)
+
+    def autotune(self, cache: str | None = None, reps: int = 3, **opts):
+        """Pass engines (register / shared-memory plane / separate passes; register or
+        shared-memory axis-1 pass) for the solve's precision, measured or read from ``cache``."""
+        opts.setdefault("flexible", 0)
+        o = api.make_opts(**opts)
+        key = (f"dirichlet:{self.physics}:{list(self.shape)}:{list(self.bc)}:{self.batch}x{self.n_loads}:"
+               f"{o.precision}:{o.precond}")
+
+        def measure():
+            t = api.unocg_dir_autotune(self.ctx, o, reps)
+            i = int(np.nanargmin(t))
+            return [i // 2, i % 2], t
+
+        return _tuning_cache(cache, key, measure,
+                             lambda s: api.unocg_dir_set_tuning(self.ctx, o.precision, int(s[0]), int(s[1])))
 
     def fluctuation(self, instance: int = 0, load: int = 0) -> np.ndarray:
         """Fluctuation on the free nodes, interleaved ``[nf * c]``."""

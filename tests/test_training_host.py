@@ -73,3 +73,23 @@ def test_newton_c3_recovers_a_generating_preconditioner():
     # the features-based loss of the result equals the oracle's loss from features
     v = uno.entries_from_blocks(Q)
     assert ot.loss_from_features(v, a, b) == pytest.approx(hist[-1], rel=1e-8, abs=1e-10 * delta)
+
+
+def test_autotune_cache_round_trip(tmp_path):
+    """The autotune cache stores the measured setting per key and applies it without measuring
+    on the next call (host logic; the measurement itself runs on the GPU)."""
+    from paper_2508_02681_gb300.solver import _tuning_cache
+    path = str(tmp_path / "tune.json")
+    applied, measured = [], []
+
+    def measure():
+        measured.append(1)
+        return [2, 1], np.array([[3.0, np.nan], [2.0, 2.5], [1.0, np.nan]])
+
+    s1, t1 = _tuning_cache(path, "k1", measure, applied.append)
+    s2, t2 = _tuning_cache(path, "k1", measure, applied.append)
+    s3, _ = _tuning_cache(path, "k2", measure, applied.append)
+    assert s1 == s2 == s3 == [2, 1] and t1 is not None and t2 is None
+    assert len(measured) == 2 and applied == [[2, 1]] * 3
+    import json
+    assert set(json.load(open(path))) == {"k1", "k2"}
