@@ -145,7 +145,8 @@ int unocg_set_microstructure_dev(unocg_ctx* ctx, const uint8_t* phase_dev, int n
 /* Phase properties [B][n_phases] kappa (thermal) or [B][n_phases][2] (E, nu) (elastic).    */
 int unocg_set_phase_properties(unocg_ctx* ctx, const double* props);
 
-/* Macroscopic load cases: [n_loads][3] gradients or [n_loads][6] Mandel strains.            */
+/* Macroscopic load cases: [n_loads][3] gradients or [n_loads][6] Mandel strains (finite, else
+   UNOCG_ERR_INVALID_ARG).                                                                  */
 int unocg_set_macro_load(unocg_ctx* ctx, int n_loads, const double* loads);
 
 /* UNO weights (Eq. (fnocg-parametrization), Eq. (prec-sparse-def)); performs the safety check

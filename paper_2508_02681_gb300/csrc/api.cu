@@ -17,6 +17,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "kargs.h"
 #include "persist.h"
 #include "setup.h"
@@ -25,6 +27,12 @@
 using namespace unocg;
 
 namespace {
+
+// NVTX range for the duration of an entry point (visible to Nsight tools, inert otherwise)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 constexpr int kMaxTickets = 8;
 enum Ticket { T_PLANE = 0, T_LINE = 1, T_KU = 2, T_JAC = 3, T_PLANE2 = 4, T_JAC2 = 5 };
@@ -375,6 +383,10 @@ extern "C" int unocg_set_phase_properties(unocg_ctx* ctx, const double* props) {
 extern "C" int unocg_set_macro_load(unocg_ctx* ctx, int n_loads, const double* loads) {
   if (!ctx || !loads || n_loads < 1 || n_loads > 8)
     return fail(ctx, UNOCG_ERR_INVALID_ARG, "need 1 <= n_loads <= 8 and a load array");
+  // a non-finite load would give a right-hand side without a finite entry, whose max-norm
+  // reduction (fmax drops NaN) would read as zero: reject it here
+  for (int i = 0; i < n_loads * ctx->dim; ++i)
+    if (!std::isfinite(loads[i])) return fail(ctx, UNOCG_ERR_INVALID_ARG, "non-finite load");
   if (ctx->loads_d && n_loads != ctx->L) {
     cudaFree(ctx->loads_d);
     ctx->loads_d = nullptr;
@@ -491,6 +503,7 @@ extern "C" int unocg_set_uno_modes(unocg_ctx* ctx, int M, const void* w, int dty
 }
 
 extern "C" int unocg_set_uno_weights(unocg_ctx* ctx, int kind, const void* w, int dtype, double spd_eps) {
+  NvtxRange nvtx_("unocg_set_uno_weights");
   if (!ctx) return UNOCG_ERR_INVALID_ARG;
   if (kind != UNOCG_W_REFERENCE_MEDIUM && kind != UNOCG_W_BLOCKS && kind != UNOCG_W_THETA)
     return fail(ctx, UNOCG_ERR_INVALID_ARG, "unknown weight kind");
@@ -1009,6 +1022,7 @@ extern "C" int unocg_get_uno_weights(unocg_ctx* ctx, int instance, double* out) 
 }
 
 extern "C" int unocg_solve_async(unocg_ctx* ctx, const unocg_solve_opts* o) {
+  NvtxRange nvtx_("unocg_solve_async");
   Plan pl;
   int rc = prepare_solve(ctx, o, &pl);
   if (rc) return rc;
@@ -1241,6 +1255,7 @@ extern "C" int unocg_batch_solve(int n_ctx, unocg_ctx* const* ctxs, const unocg_
 
 // ------------------------------------------------------------------ operator-level entry points
 extern "C" int unocg_apply_K_dev(unocg_ctx* ctx, int instance, const double* d_dev, double* p_dev, void* stream) {
+  NvtxRange nvtx_("unocg_apply_K_dev");
   if (!ctx || !d_dev || !p_dev) return fail(ctx, UNOCG_ERR_INVALID_ARG, "null argument");
   if (!ctx->have_phase || !ctx->have_props) return fail(ctx, UNOCG_ERR_STATE, "microstructure/properties missing");
   if (instance < 0 || instance >= ctx->B) return fail(ctx, UNOCG_ERR_INVALID_ARG, "instance out of range");
@@ -1256,6 +1271,7 @@ extern "C" int unocg_apply_K_dev(unocg_ctx* ctx, int instance, const double* d_d
 }
 
 extern "C" int unocg_apply_uno_dev(unocg_ctx* ctx, int instance, const double* r_dev, double* s_dev, void* stream) {
+  NvtxRange nvtx_("unocg_apply_uno_dev");
   if (!ctx || !r_dev || !s_dev) return fail(ctx, UNOCG_ERR_INVALID_ARG, "null argument");
   if (instance < 0 || instance >= ctx->B) return fail(ctx, UNOCG_ERR_INVALID_ARG, "instance out of range");
   if (ctx->wkind < 0) return fail(ctx, UNOCG_ERR_STATE, "set UNO weights first");
@@ -1469,6 +1485,7 @@ static int uno_ensure(unocg_uno* op, int batch) {
 }
 
 extern "C" int unocg_uno_apply_dev(unocg_uno* op, int batch, const float* r_dev, float* s_dev, void* stream) {
+  NvtxRange nvtx_("unocg_uno_apply_dev");
   if (!op || batch < 1 || !r_dev || !s_dev) return UNOCG_ERR_INVALID_ARG;
   if (!op->theta) return ufail(op, UNOCG_ERR_STATE, "set theta first");
   int rc = uno_ensure(op, batch);
@@ -1521,6 +1538,7 @@ extern "C" int unocg_uno_features_dev(unocg_uno* op, int batch, const float* f_d
 
 extern "C" int unocg_uno_backward_dev(unocg_uno* op, int batch, const float* r_dev, const float* gs_dev,
                                       float* gr_dev, float* gtheta_dev, void* stream) {
+  NvtxRange nvtx_("unocg_uno_backward_dev");
   if (!op || batch < 1 || !r_dev || !gs_dev) return UNOCG_ERR_INVALID_ARG;
   if (!op->theta) return ufail(op, UNOCG_ERR_STATE, "set theta first");
   int rc = uno_ensure(op, batch);

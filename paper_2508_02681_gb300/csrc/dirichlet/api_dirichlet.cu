@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../element.cuh"
 #include "dargs.h"
 #include "unocg.h"
@@ -17,6 +19,11 @@
 using namespace unocg;
 
 namespace {
+
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 enum DTicket { DT_CHECK = 0, DT_QMUL = 1, DT_KU = 2, DT_CHECK2 = 3, DT_JAC = 4, DT_N = 8 };
 
@@ -775,6 +782,8 @@ extern "C" int unocg_dir_set_phase_properties(unocg_dir* d, const double* props)
 
 extern "C" int unocg_dir_set_macro_load(unocg_dir* d, int n_loads, const double* loads) {
   if (!d || !loads || n_loads < 1) return dfail(d, UNOCG_ERR_INVALID_ARG, "invalid loads");
+  for (int i = 0; i < n_loads * d->dim; ++i)
+    if (!std::isfinite(loads[i])) return dfail(d, UNOCG_ERR_INVALID_ARG, "non-finite load");
   if (n_loads != d->L) {
     dfree_graph(d);
     free_fields(d->f64f);
@@ -902,6 +911,7 @@ extern "C" int unocg_dir_get_uno_weights(unocg_dir* d, int instance, double* out
 
 // ------------------------------------------------------------------ solve
 extern "C" int unocg_dir_solve_async(unocg_dir* d, const unocg_solve_opts* o) {
+  NvtxRange nvtx_("unocg_dir_solve_async");
   if (!d || !o) return dfail(d, UNOCG_ERR_INVALID_ARG, "null argument");
   if (!have_inputs(d)) return dfail(d, UNOCG_ERR_STATE, "set microstructure, phase properties and loads first");
   if (o->precond < 0 || o->precond > 2 || (o->precision != UNOCG_FP64 && o->precision != UNOCG_MIXED) ||
@@ -1036,6 +1046,7 @@ extern "C" int unocg_dir_get_effective_tensor(unocg_dir* d, double* out) {
 
 // ------------------------------------------------------------------ operator-level entry points
 extern "C" int unocg_dir_apply_K_dev(unocg_dir* d, int instance, const double* p_dev, double* q_dev, void* stream) {
+  NvtxRange nvtx_("unocg_dir_apply_K_dev");
   if (!d || !p_dev || !q_dev) return dfail(d, UNOCG_ERR_INVALID_ARG, "null argument");
   if (!d->phase_set || !d->mat64) return dfail(d, UNOCG_ERR_STATE, "set microstructure and phase properties first");
   if (instance < 0 || instance >= d->B) return dfail(d, UNOCG_ERR_INVALID_ARG, "instance out of range");
@@ -1057,6 +1068,7 @@ extern "C" int unocg_dir_apply_K_dev(unocg_dir* d, int instance, const double* p
 }
 
 extern "C" int unocg_dir_apply_uno_dev(unocg_dir* d, int instance, const double* r_dev, double* s_dev, void* stream) {
+  NvtxRange nvtx_("unocg_dir_apply_uno_dev");
   if (!d || !r_dev || !s_dev) return dfail(d, UNOCG_ERR_INVALID_ARG, "null argument");
   if (d->wkind == -2) {
     int rc = build_reference(d, 0.0);

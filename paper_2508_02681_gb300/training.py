@@ -139,21 +139,51 @@ def reference_modes_blocks(physics: int, shape, M: int, ref_props) -> np.ndarray
     return w
 
 
+def save_checkpoint(path: str, theta, optimizer=None, **meta):
+    """Training checkpoint: the weights (theta or the paper's layout), the optimizer state (Adam
+    moments and step counts) and free-form metadata (epoch, losses, M, ...)."""
+    import torch
+    torch.save({"theta": theta.detach().cpu(), "optimizer": optimizer.state_dict() if optimizer is not None else None,
+                "meta": meta}, path)
+
+
+def load_checkpoint(path: str, device="cuda"):
+    """Returns (theta tensor on ``device`` with requires_grad, optimizer state dict or None, meta);
+    resume with ``torch.optim.Adam([theta]).load_state_dict(state)``."""
+    import torch
+    ck = torch.load(path, map_location="cpu", weights_only=False)
+    theta = ck["theta"].to(device).requires_grad_(True)
+    return theta, ck["optimizer"], ck["meta"]
+
+
 def train(f, u, theta0, epochs: int, batch: int = 64, lr: float = 1e-2, seed: int = 0,
-          modes_M: int | None = None):
+          modes_M: int | None = None, checkpoint: str | None = None, resume: str | None = None):
     """Adam on the MSE loss; returns (theta tensor, per-epoch mean losses).  With ``modes_M``
-    theta0 is in the paper's layout ``[1 + n_modes, 1]`` (see ``reference_modes``)."""
+    theta0 is in the paper's layout ``[1 + n_modes, 1]`` (see ``reference_modes``).  With
+    ``checkpoint`` the weights, Adam state, shuffling state and losses are saved after every
+    epoch; ``resume`` continues from such a file (epochs counts the total)."""
     import torch
 
     shape = tuple(f.shape[2:])
     op = api.unocg_uno_create(1, *shape)
     Fn = uno_function(modes_M)
-    theta = torch.tensor(theta0, dtype=torch.float32, device="cuda", requires_grad=True)
-    opt = torch.optim.Adam([theta], lr=lr)
     g = torch.Generator(device="cpu").manual_seed(seed)
     losses = []
+    start = 0
+    if resume is not None:
+        theta, state, meta = load_checkpoint(resume)
+        opt = torch.optim.Adam([theta], lr=lr)
+        if state is not None:
+            opt.load_state_dict(state)
+        losses = list(meta.get("losses", []))
+        start = int(meta.get("epoch", 0))
+        if "rng" in meta:
+            g.set_state(meta["rng"])
+    else:
+        theta = torch.tensor(theta0, dtype=torch.float32, device="cuda", requires_grad=True)
+        opt = torch.optim.Adam([theta], lr=lr)
     n = f.shape[0]
-    for _ in range(epochs):
+    for ep in range(start, epochs):
         perm = torch.randperm(n, generator=g)
         tot = 0.0
         for s0 in range(0, n, batch):
@@ -166,6 +196,8 @@ def train(f, u, theta0, epochs: int, batch: int = 64, lr: float = 1e-2, seed: in
             opt.step()
             tot += float(loss.detach()) * fb.shape[0]
         losses.append(tot / n)
+        if checkpoint is not None:
+            save_checkpoint(checkpoint, theta, opt, epoch=ep + 1, losses=losses, rng=g.get_state(), modes_M=modes_M)
     api.unocg_uno_destroy(op)
     return theta.detach(), losses
 

@@ -497,3 +497,22 @@ def test_second_order_training_elastic():
             its[i, prec] = int(info.c.max_iters)
         h.close()
     print("held-out iterations", its)
+
+
+def test_training_checkpoint_resume(tmp_path):
+    """Adam training resumed from the checkpoint of epoch 2 continues as the uninterrupted run."""
+    import torch
+    from paper_2508_02681_gb300 import training as tr
+    shape = (8, 8, 8)
+    f = torch.tensor(np.stack([random_field((1,) + shape, seed=800 + b) for b in range(16)]), dtype=torch.float32,
+                     device="cuda")
+    u = torch.tensor(np.stack([random_field((1,) + shape, seed=900 + b) for b in range(16)]), dtype=torch.float32,
+                     device="cuda")
+    th0 = _theta(shape, 1, 3)
+    full, lf = tr.train(f, u, th0, epochs=4, batch=8, lr=1e-2)
+    path = str(tmp_path / "ck.pt")
+    tr.train(f, u, th0, epochs=2, batch=8, lr=1e-2, checkpoint=path)
+    res, lr_ = tr.train(f, u, None, epochs=4, batch=8, lr=1e-2, resume=path)
+    assert len(lr_) == 4
+    assert np.allclose(lr_, lf, rtol=1e-5)
+    assert torch.allclose(res, full, rtol=1e-5, atol=1e-7)

@@ -93,3 +93,28 @@ def test_autotune_cache_round_trip(tmp_path):
     assert len(measured) == 2 and applied == [[2, 1]] * 3
     import json
     assert set(json.load(open(path))) == {"k1", "k2"}
+
+
+def test_checkpoint_round_trip(tmp_path):
+    """Checkpoint / resume of the training state: weights, Adam moments and metadata."""
+    import torch
+    th = torch.tensor(np.arange(6.0).reshape(3, 2), dtype=torch.float32, requires_grad=True)
+    opt = torch.optim.Adam([th], lr=0.1)
+    for _ in range(3):
+        opt.zero_grad()
+        (th ** 2).sum().backward()
+        opt.step()
+    path = str(tmp_path / "ck.pt")
+    pt.save_checkpoint(path, th, opt, epoch=3, losses=[3.0, 2.0, 1.0])
+    th2, state, meta = pt.load_checkpoint(path, device="cpu")
+    assert torch.equal(th2.detach(), th.detach()) and th2.requires_grad
+    assert meta["epoch"] == 3 and meta["losses"] == [3.0, 2.0, 1.0]
+    opt2 = torch.optim.Adam([th2], lr=0.1)
+    opt2.load_state_dict(state)
+    for o in (opt, opt2):
+        o.zero_grad()
+    (th ** 2).sum().backward()
+    (th2 ** 2).sum().backward()
+    opt.step()
+    opt2.step()
+    assert torch.allclose(th.detach(), th2.detach())
