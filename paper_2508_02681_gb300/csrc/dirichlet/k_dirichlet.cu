@@ -405,14 +405,26 @@ __global__ void __launch_bounds__(kDThreads) k_dmixq(DPassArgs<T> a, int pa, int
   const int pc = 3 - pa - pb;  // the Dirichlet axis
   const int ha = n[pa] / 2 + 1, hb = n[pb] / 2 + 1;
   const long long total = (long long)ha * hb * m[pc];
+  // consecutive threads step along axis 3 (contiguous in memory): the mirrored entries of a
+  // warp then fall into a few segments (reversed order for -k3)
+  const bool c_fast = pc == 2;
   const bool active = a.standalone || !a.sc[bl].done;
   DotAcc<T> acc;
   if (active) {
     const T* Qb = reinterpret_cast<const T*>(a.Q) + (long long)(bl / a.L) * a.q_inst_stride;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
-      const int kc = (int)(t % m[pc]);
-      const long long r = t / m[pc];
-      const int kb = (int)(r % hb), ka = (int)(r / hb);
+      int ka, kb, kc;
+      if (c_fast) {
+        kc = (int)(t % m[pc]);
+        const long long r = t / m[pc];
+        kb = (int)(r % hb);
+        ka = (int)(r / hb);
+      } else {  // pb == 2: axis 3 periodic
+        kb = (int)(t % hb);
+        const long long r = t / hb;
+        kc = (int)(r % m[pc]);
+        ka = (int)(r / m[pc]);
+      }
       const int kam = ka ? n[pa] - ka : 0, kbm = kb ? n[pb] - kb : 0;
       const T wgt = (T)((ka == kam ? 0.5 : 1.0) * (kb == kbm ? 0.5 : 1.0));
       long long node[4], mode[4];
