@@ -678,6 +678,46 @@ __global__ void __launch_bounds__(kDThreads) k_djac(DJacArgs<T> a) {
   }
 }
 
+// f at free node i (the element loads of Sec. 6.1 / 6.2, as node_rhs of the periodic path) with
+// exact cancellation made exact: a component whose eight element terms cancel to within
+// 64 ulp of their absolute sum is the zero of a homogeneous neighbourhood and is set to 0, so
+// that a homogeneous cell has a zero right-hand side instead of rounding noise (which the
+// relative stopping test would otherwise iterate on, and which FP32 fields cannot resolve).
+template <int CC>
+__device__ __forceinline__ void dnode_rhs(const uint8_t* __restrict__ ph, const double* mt, const Grid& g,
+                                          int i1, int i2, int i3, const double* load, double* f) {
+  Nbr nb;
+  neighbours(g, i1, i2, i3, nb);
+  const double q = 0.25 * g.h * g.h;
+  double acc[3] = {0.0, 0.0, 0.0}, mag[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int o = 0; o < 8; ++o) {
+    const int o1 = (o >> 2) & 1, o2 = (o >> 1) & 1, o3 = o & 1;
+    const int p = ph[eidx(nb, o1, o2, o3)];
+    const double g1 = 2 * o1 - 1, g2 = 2 * o2 - 1, g3 = 2 * o3 - 1;
+    if (CC == 1) {
+      const double t = mt[2 * p] * (g1 * load[0] + g2 * load[1] + g3 * load[2]);
+      acc[0] += t;
+      mag[0] += fabs(t);
+    } else {
+      const double is2 = 0.70710678118654752440;
+      const double e11 = load[0], e22 = load[1], e33 = load[2];
+      const double e12 = load[3] * is2, e13 = load[4] * is2, e23 = load[5] * is2;
+      const double tr = e11 + e22 + e33;
+      const double la = mt[2 * p], m2 = 2.0 * mt[2 * p + 1];
+      const double s11 = la * tr + m2 * e11, s22 = la * tr + m2 * e22, s33 = la * tr + m2 * e33;
+      const double s12 = m2 * e12, s13 = m2 * e13, s23 = m2 * e23;
+      const double t0 = s11 * g1 + s12 * g2 + s13 * g3;
+      const double t1 = s12 * g1 + s22 * g2 + s23 * g3;
+      const double t2 = s13 * g1 + s23 * g2 + s33 * g3;
+      acc[0] += t0; acc[1] += t1; acc[2] += t2;
+      mag[0] += fabs(t0); mag[1] += fabs(t1); mag[2] += fabs(t2);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < CC; ++i) f[i] = fabs(acc[i]) <= 64.0 * 2.220446049250313e-16 * mag[i] ? 0.0 : -q * acc[i];
+}
+
 // ============================================================================ set-up, post
 // f (FP64) on the free nodes, zero on the boundary; r = f, u = p = q = 0 everywhere
 template <int CC>
@@ -696,7 +736,7 @@ __global__ void __launch_bounds__(kDThreads) k_dinit(DInitArgs a) {
     const int i2 = (int)(r % g.n2), i1 = (int)(r / g.n2);
     double f[CC];
     if (dfree_node(g, i1, i2, i3)) {
-      node_rhs<CC>(ph, mt, g.pg, i1, i2, i3, a.loads + l * (CC == 1 ? 3 : 6), f);
+      dnode_rhs<CC>(ph, mt, g.pg, i1, i2, i3, a.loads + l * (CC == 1 ? 3 : 6), f);
     } else {
 #pragma unroll
       for (int i = 0; i < CC; ++i) f[i] = 0.0;
