@@ -602,14 +602,15 @@ static cudaError_t fwd_transform(PlaneFwdArgs<T>& a, cudaStream_t s, int only_pe
   return launch_cols<T>(ca, -1, s);
 }
 
-// Inverse of fwd_transform; the column pass runs in place on a.shat.
+// Inverse of fwd_transform; the column pass runs in place on a.shat, or into a.cols_out.
 template <typename T>
 static cudaError_t inv_transform(PlaneInvArgs<T>& a, cudaStream_t s) {
   a.rows = plane_rows(a.g, sizeof(T) * 2);
   if (a.rows) {
-    ColArgs<T> ca{a.g, a.c, a.BL, const_cast<cplx<T>*>(a.shat), a.sc, a.ft, 0};
+    ColArgs<T> ca{a.g, a.c, a.BL, const_cast<cplx<T>*>(a.shat), a.sc, a.ft, 0, a.cols_out};
     cudaError_t e = launch_cols<T>(ca, +1, s);
     if (e != cudaSuccess) return e;
+    if (a.cols_out) a.shat = a.cols_out;
   }
   return launch_plane_inv<T>(a, s);
 }
@@ -691,6 +692,9 @@ static cudaError_t enq_precond(unocg_ctx* ctx, cudaStream_t s, const Plan& pl, c
     PlaneInvArgs<T> pa{};
     pa.g = ctx->g; pa.c = ctx->c; pa.BL = BL; pa.shat = f.shat; pa.d = f.d; pa.u = f.u; pa.dst = nullptr;
     pa.sc = ctx->sc; pa.ft = tables(ctx, sizeof(T) == 8); pa.standalone = 0;
+    // r_hat is free until the next forward pass: the axis-2 pass of large planes writes there
+    // and leaves s_hat for the flexible r . s_old of the next block multiply
+    pa.cols_out = f.rhat;
     return inv_transform<T>(pa, s);
   }
   if (part == 1) return cudaSuccess;

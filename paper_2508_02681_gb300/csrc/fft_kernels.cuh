@@ -470,8 +470,8 @@ __global__ void __launch_bounds__(NTH) k_plane_inv(PlaneInvArgs<T> a) {
 }
 
 // ============================================================================ axis-2 pass
-// In-place FFT along axis 2 of (field, i1) planes: a block takes a tile of TB consecutive k3 of
-// one plane, all n2 rows (lines at stride n3h).
+// FFT along axis 2 of (field, i1) planes, in place or into a.out: a block takes a tile of TB
+// consecutive k3 of one plane, all n2 rows (lines at stride n3h).
 template <typename T, int DIR, int NTH>
 __global__ void __launch_bounds__(NTH) k_cols(ColArgs<T> a) {
   using C = cplx<T>;
@@ -489,6 +489,7 @@ __global__ void __launch_bounds__(NTH) k_cols(ColArgs<T> a) {
   const int k0 = blockIdx.x * TB;
   const int nt = min(TB, n3h - k0);
   C* base = a.data + plane * (long long)n2 * n3h + k0;
+  C* obase = (a.out ? a.out : a.data) + plane * (long long)n2 * n3h + k0;
   for (int idx = threadIdx.x; idx < n2 * TB; idx += NTH) {
     const int row = idx / TB, t = idx - row * TB;
     buf[idx] = t < nt ? base[(long long)row * n3h + t] : mk<T>((T)0, (T)0);
@@ -497,7 +498,7 @@ __global__ void __launch_bounds__(NTH) k_cols(ColArgs<T> a) {
   C* res = fft_lines<T, DIR>(buf, alt, TB, 1, TB, a.ft.p2, tw);
   for (int idx = threadIdx.x; idx < n2 * TB; idx += NTH) {
     const int row = idx / TB, t = idx - row * TB;
-    if (t < nt) base[(long long)row * n3h + t] = res[idx];
+    if (t < nt) obase[(long long)row * n3h + t] = res[idx];
   }
 }
 

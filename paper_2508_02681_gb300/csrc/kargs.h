@@ -75,6 +75,8 @@ template <typename T> struct PlaneInvArgs {
   FftTables ft;
   int standalone;
   int rows;             // 0: whole planes; else chunks of `rows` rows, axis 3 only (axis 2 done)
+  cplx<T>* cols_out;    // rows mode: the axis-2 pass writes here (null: in place over shat), so
+                        // that shat keeps s_hat for the r . s_old term of the flexible variant
 };
 
 // In-place FFT along axis 2 of every (field, i1) plane, for planes too large for one block.
@@ -85,6 +87,7 @@ template <typename T> struct ColArgs {
   const CgScal* sc;     // skip finished pairs (null: all)
   FftTables ft;
   int only_pending;     // CG after a replacement: only the pairs just replaced
+  cplx<T>* out;         // destination, same layout (null: in place)
 };
 
 // ---------------------------------------------------------------- material / stencil
