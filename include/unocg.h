@@ -19,8 +19,11 @@
  * Ownership and errors
  *   - Host pointers are read or written synchronously during the call and never retained.
  *   - The library owns every device buffer it allocates; `_dev` entry points take caller-owned
- *     device pointers plus a cudaStream_t (passed as void*), never free them, and enqueue work
- *     on that stream without synchronizing.
+ *     device pointers plus a cudaStream_t (passed as void*; NULL is the legacy default stream),
+ *     never free them, and enqueue work on that stream without blocking the host.  For the
+ *     contexts (unocg_ctx, unocg_dir) that stream is ordered by events after the work already
+ *     enqueued on the context's stream, and the context's later work after it; no event is
+ *     added while either stream captures a CUDA graph (the capture then orders the work).
  *   - Every int-returning call returns UNOCG_OK (0) or a negative UNOCG_ERR_* code; the message
  *     of the last failure of a context is returned by unocg_last_error().
  */

@@ -101,6 +101,7 @@ struct unocg_ctx {
   std::vector<double> w_host;  // user weights (BLOCKS / THETA / MODES), FP64
   int modes_M = -1;            // MODES: mode-set parameter M
   cudaStream_t stream = nullptr, own_stream = nullptr;
+  cudaEvent_t join_ev = nullptr;  // orders the `_dev` entry points against the context stream
   std::string err;
   // device data
   uint8_t* phase = nullptr;
@@ -295,6 +296,7 @@ extern "C" void unocg_destroy(unocg_ctx* ctx) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+  if (ctx->join_ev) cudaEventDestroy(ctx->join_ev);
   delete ctx;
 }
 
@@ -340,15 +342,10 @@ extern "C" int unocg_set_microstructure_dev(unocg_ctx* ctx, const uint8_t* phase
   if (!ctx || !phase_dev) return fail(ctx, UNOCG_ERR_INVALID_ARG, "null argument");
   int rc = check_phase_range(ctx, n_phases);
   if (rc) return rc;
-  cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(order_after(&ctx->join_ev, ctx->stream, s));
   CK(cudaMemcpyAsync(ctx->phase, phase_dev, (size_t)ctx->B * ctx->g.n, cudaMemcpyDeviceToDevice, s));
-  if (s != ctx->stream) {
-    cudaEvent_t ev;
-    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-    CK(cudaEventRecord(ev, s));
-    CK(cudaStreamWaitEvent(ctx->stream, ev, 0));
-    cudaEventDestroy(ev);
-  }
+  CK(order_after(&ctx->join_ev, s, ctx->stream));
   ctx->have_phase = true;
   return UNOCG_OK;
 }
@@ -411,6 +408,7 @@ extern "C" int unocg_set_macro_load(unocg_ctx* ctx, int n_loads, const double* l
   }
   ctx->L = n_loads;
   CK(dalloc(&ctx->loads_d, (size_t)n_loads * ctx->dim));
+  CK(cudaStreamSynchronize(ctx->stream));  // a solve in flight may still read the previous loads
   CK(cudaMemcpy(ctx->loads_d, loads, (size_t)n_loads * ctx->dim * sizeof(double), cudaMemcpyHostToDevice));
   ctx->have_loads = true;
   return UNOCG_OK;
@@ -539,6 +537,7 @@ static int ensure_workspace(unocg_ctx* ctx, int precision, int precond) {
   need = std::max(need, (size_t)BL * line_reg_blocks_x(ctx->g) * 2);
   need = std::max(need, (size_t)BL * node_blocks_x(ctx->g));
   need = std::max(need, (size_t)BL * ku_blocks_x(ctx->g, ctx->c));
+  need = std::max(need, (size_t)BL * ku_tasks_x(ctx->g, ctx->c));
   need = std::max(need, (size_t)BL * jac_blocks_x((long long)ctx->c * n, BL));
   need = std::max(need, (size_t)BL * ctx->c * 1184);
   need = std::max(need, (size_t)ctx->B * node_blocks_x(ctx->g) * 48);
@@ -959,7 +958,7 @@ static int run_persistent(unocg_ctx* ctx, const Plan& pl) {
   a.sc = ctx->sc;
   a.B = ctx->B; a.L = ctx->L; a.BL = BL;
   a.n_line_tasks = line_blocks_x(ctx->g, ctx->c, sizeof(T) * 2);
-  a.n_ku_tasks = ku_blocks_x(ctx->g, ctx->c);
+  a.n_ku_tasks = ku_tasks_x(ctx->g, ctx->c);
   a.n_tr_tasks = node_blocks_x(ctx->g);
   a.n_fold_chunks = 64;
   const long long np = (long long)ctx->c * ctx->g.n1;
@@ -1021,7 +1020,9 @@ extern "C" int unocg_get_uno_weights(unocg_ctx* ctx, int instance, double* out) 
   }
   const size_t m = (size_t)ctx->g.nh * (ctx->c == 1 ? 1 : 6);
   const double* src = ctx->Q64 + (ctx->Bq > 1 ? instance * m : 0);
-  CK(cudaMemcpy(out, src, m * sizeof(double), cudaMemcpyDeviceToHost));
+  // the weights are built on the context stream (non-blocking: a plain cudaMemcpy would not wait)
+  CK(cudaMemcpyAsync(out, src, m * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
   return UNOCG_OK;
 }
 
@@ -1137,8 +1138,10 @@ extern "C" int unocg_get_fluctuation_dev(unocg_ctx* ctx, int instance, int load,
     return fail(ctx, UNOCG_ERR_INVALID_ARG, "instance/load out of range");
   const long long n = ctx->g.n;
   const double* src = final_u(ctx) + ((long long)instance * ctx->L + load) * ctx->c * n;
-  CK(cudaMemcpyAsync(out_dev, src, (size_t)ctx->c * n * sizeof(double), cudaMemcpyDeviceToDevice,
-                     stream ? (cudaStream_t)stream : ctx->stream));
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(order_after(&ctx->join_ev, ctx->stream, s));
+  CK(cudaMemcpyAsync(out_dev, src, (size_t)ctx->c * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(order_after(&ctx->join_ev, s, ctx->stream));
   return UNOCG_OK;
 }
 
@@ -1270,7 +1273,10 @@ extern "C" int unocg_apply_K_dev(unocg_ctx* ctx, int instance, const double* d_d
   a.mat.m64 += (long long)instance * ctx->n_phases * 2;
   a.mat.m32 += (long long)instance * ctx->n_phases * 2;
   a.d = d_dev; a.p = p_dev; a.sc = nullptr; a.standalone = 1;
-  CK(launch_ku<double>(a, stream ? (cudaStream_t)stream : ctx->stream));
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(order_after(&ctx->join_ev, ctx->stream, s));
+  CK(launch_ku<double>(a, s));
+  CK(order_after(&ctx->join_ev, s, ctx->stream));
   return UNOCG_OK;
 }
 
@@ -1283,7 +1289,8 @@ extern "C" int unocg_apply_uno_dev(unocg_ctx* ctx, int instance, const double* r
     int rc = build_weights(ctx);
     if (rc) return rc;
   }
-  cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(order_after(&ctx->join_ev, ctx->stream, s));
   double2* hat = nullptr;
   double2* shat = nullptr;
   const size_t m = (size_t)ctx->c * ctx->g.nh;
@@ -1307,6 +1314,7 @@ extern "C" int unocg_apply_uno_dev(unocg_ctx* ctx, int instance, const double* r
   cudaFreeAsync(hat, s);
   cudaFreeAsync(shat, s);
   if (e != cudaSuccess) return fail(ctx, UNOCG_ERR_CUDA, cudaGetErrorString(e));
+  CK(order_after(&ctx->join_ev, s, ctx->stream));
   return UNOCG_OK;
 }
 
@@ -1365,7 +1373,9 @@ extern "C" int unocg_apply_uno_dev_noalloc(unocg_ctx* ctx, int instance, const d
   if (e != cudaSuccess) return fail(ctx, UNOCG_ERR_CUDA, std::string("scratch address: ") + cudaGetErrorString(e));
   double2* hat = scratch;
   double2* shat = scratch + kNoAllocSpectrum;
-  cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
+  cudaStream_t s = (cudaStream_t)stream;
+  e = order_after(&ctx->join_ev, ctx->stream, s);
+  if (e != cudaSuccess) return fail(ctx, UNOCG_ERR_CUDA, cudaGetErrorString(e));
   PlaneFwdArgs<double> pf{};
   pf.g = ctx->g; pf.c = ctx->c; pf.BL = 1; pf.src = r_dev; pf.hat = hat; pf.ft = tables(ctx, true); pf.standalone = 1;
   e = fwd_transform<double>(pf, s, 0);
@@ -1381,6 +1391,7 @@ extern "C" int unocg_apply_uno_dev_noalloc(unocg_ctx* ctx, int instance, const d
     pi.g = ctx->g; pi.c = ctx->c; pi.BL = 1; pi.shat = shat; pi.dst = s_dev; pi.ft = tables(ctx, true); pi.standalone = 1;
     e = inv_transform<double>(pi, s);
   }
+  if (e == cudaSuccess) e = order_after(&ctx->join_ev, s, ctx->stream);
   if (e != cudaSuccess) return fail(ctx, UNOCG_ERR_CUDA, cudaGetErrorString(e));
   return UNOCG_OK;
 }
@@ -1398,7 +1409,10 @@ extern "C" int unocg_rhs_dev(unocg_ctx* ctx, int instance, int load, double* f_d
   ia.mat.m32 += (long long)instance * ctx->n_phases * 2;
   ia.loads = ctx->loads_d + (long long)load * ctx->dim;
   ia.f64 = f_dev;
-  CK(launch_init<double>(ia, 1, stream ? (cudaStream_t)stream : ctx->stream));
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(order_after(&ctx->join_ev, ctx->stream, s));
+  CK(launch_init<double>(ia, 1, s));
+  CK(order_after(&ctx->join_ev, s, ctx->stream));
   return UNOCG_OK;
 }
 

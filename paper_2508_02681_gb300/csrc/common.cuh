@@ -217,6 +217,28 @@ __device__ __forceinline__ double block_max_f(float v, double* sh) {
 __device__ __forceinline__ double block_max_t(float v, double* sh) { return block_max_f(v, sh); }
 __device__ __forceinline__ double block_max_t(double v, double* sh) { return block_max(v, sh); }
 
+// Stream order of the `_dev` entry points: they enqueue on the caller's stream (NULL: the
+// legacy default stream), after the work already enqueued on the context's stream, and the
+// context's later work runs after theirs.  Each direction is one event record + wait; nothing
+// is added while either stream captures a graph (the capture then owns the ordering).
+static inline bool stream_capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &st) != cudaSuccess) {
+    (void)cudaGetLastError();  // e.g. the legacy stream while another stream captures globally
+    return true;
+  }
+  return st != cudaStreamCaptureStatusNone;
+}
+static inline cudaError_t order_after(cudaEvent_t* ev, cudaStream_t from, cudaStream_t to) {
+  if (from == to || stream_capturing(from) || stream_capturing(to)) return cudaSuccess;
+  if (!*ev) {
+    cudaError_t e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e = cudaEventRecord(*ev, from);
+  return e == cudaSuccess ? cudaStreamWaitEvent(to, *ev, 0) : e;
+}
+
 // Programmatic dependent launch: a kernel launched with launch_pdl may start while the kernel
 // before it in the stream is still running.  pdl_wait() blocks until that kernel has completed
 // and its memory is visible: call it before touching anything the previous kernels wrote.

@@ -71,6 +71,7 @@ struct unocg_dir {
   int physics = 0, c = 1, dim = 3, B = 1, L = 0, n_phases = 0;
   DGrid g{};
   cudaStream_t stream = nullptr, own_stream = nullptr;
+  cudaEvent_t join_ev = nullptr;  // orders the `_dev` entry points against the context stream
   std::string err;
   FftPlan plan[3]{};
   void* tw64[3] = {nullptr, nullptr, nullptr};
@@ -716,6 +717,7 @@ extern "C" void unocg_dir_destroy(unocg_dir* d) {
   cudaFree(d->sc); cudaFree(d->part); cudaFree(d->tickets); cudaFree(d->flags); cudaFree(d->ceff);
   cudaFree(d->stage_a); cudaFree(d->stage_b); cudaFree(d->stage_f);
   if (d->own_stream) cudaStreamDestroy(d->own_stream);
+  if (d->join_ev) cudaEventDestroy(d->join_ev);
   delete d;
 }
 
@@ -741,6 +743,7 @@ extern "C" int unocg_dir_set_microstructure(unocg_dir* d, const uint8_t* phase, 
     d->props.clear();
   }
   d->n_phases = n_phases;
+  DCK(cudaStreamSynchronize(d->stream));  // a solve in flight may still read the previous inputs
   DCK(cudaMemcpy(d->phase, phase, n, cudaMemcpyHostToDevice));
   d->phase_set = true;
   d->solved = false;
@@ -771,6 +774,7 @@ extern "C" int unocg_dir_set_phase_properties(unocg_dir* d, const double* props)
   }
   if (!d->mat64) DCK(cudaMalloc(&d->mat64, 2 * cnt * sizeof(double)));
   if (!d->mat32) DCK(cudaMalloc(&d->mat32, 2 * cnt * sizeof(float)));
+  DCK(cudaStreamSynchronize(d->stream));
   DCK(cudaMemcpy(d->mat64, m64.data(), 2 * cnt * sizeof(double), cudaMemcpyHostToDevice));
   DCK(cudaMemcpy(d->mat32, m32.data(), 2 * cnt * sizeof(float), cudaMemcpyHostToDevice));
   d->props = m64;
@@ -798,6 +802,7 @@ extern "C" int unocg_dir_set_macro_load(unocg_dir* d, int n_loads, const double*
   d->loads.assign(loads, loads + (size_t)n_loads * d->dim);
   if (!d->loads_d) DCK(cudaMalloc(&d->loads_d, d->loads.size() * sizeof(double)));
   if (!d->ceff) DCK(cudaMalloc(&d->ceff, (size_t)d->B * d->dim * d->L * sizeof(double)));
+  DCK(cudaStreamSynchronize(d->stream));
   DCK(cudaMemcpy(d->loads_d, d->loads.data(), d->loads.size() * sizeof(double), cudaMemcpyHostToDevice));
   d->solved = false;
   return UNOCG_OK;
@@ -1014,7 +1019,10 @@ extern "C" int unocg_dir_get_fluctuation_dev(unocg_dir* d, int instance, int loa
   if (instance < 0 || instance >= d->B || load < 0 || load >= d->L)
     return dfail(d, UNOCG_ERR_INVALID_ARG, "instance/load out of range");
   const double* src = d->u64 + ((size_t)instance * d->L + load) * d->c * d->g.ne;
-  DCK(launch_dgather(d->g, d->c, src, out_dev, (cudaStream_t)stream));
+  cudaStream_t s = (cudaStream_t)stream;
+  DCK(order_after(&d->join_ev, d->stream, s));
+  DCK(launch_dgather(d->g, d->c, src, out_dev, s));
+  DCK(order_after(&d->join_ev, s, d->stream));
   return UNOCG_OK;
 }
 
@@ -1053,6 +1061,7 @@ extern "C" int unocg_dir_apply_K_dev(unocg_dir* d, int instance, const double* p
   int rc = ensure_stage(d);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
+  DCK(order_after(&d->join_ev, d->stream, s));
   DCK(launch_dscatter(d->g, d->c, p_dev, d->stage_a, s));
   DKuArgs<double> ka{};
   ka.g = d->g; ka.c = d->c; ka.BL = 1; ka.L = 1;
@@ -1064,6 +1073,7 @@ extern "C" int unocg_dir_apply_K_dev(unocg_dir* d, int instance, const double* p
   ka.p = d->stage_a; ka.q = d->stage_b; ka.standalone = 1;
   DCK(launch_dku<double>(ka, s));
   DCK(launch_dgather(d->g, d->c, d->stage_b, q_dev, s));
+  DCK(order_after(&d->join_ev, s, d->stream));
   return UNOCG_OK;
 }
 
@@ -1079,6 +1089,7 @@ extern "C" int unocg_dir_apply_uno_dev(unocg_dir* d, int instance, const double*
   int rc = ensure_stage(d);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
+  DCK(order_after(&d->join_ev, d->stream, s));
   DCK(launch_dscatter(d->g, d->c, r_dev, d->stage_a, s));
   LoopCtl ctl{};
   DPassArgs<double> a = pass_args<double>(d, DP_FIRST, ctl, 0);
@@ -1113,6 +1124,7 @@ extern "C" int unocg_dir_apply_uno_dev(unocg_dir* d, int instance, const double*
     DCK(launch_dpass<double>(with(d->lines3[0]), DP_LAST, s));
   }
   DCK(launch_dgather(d->g, d->c, d->stage_a, s_dev, s));
+  DCK(order_after(&d->join_ev, s, d->stream));
   return UNOCG_OK;
 }
 

@@ -14,10 +14,27 @@
 #include "df64.cuh"
 #include "stencil.cuh"
 #include "ku_task.cuh"
+#include "ku_elastic.cuh"
 
 namespace unocg {
 
 // ============================================================================ K d
+// Block partial of d . p; the last block of the grid forms alpha = gamma / (d . p) per pair.
+template <typename T>
+__device__ __forceinline__ void ku_finish(const StencilArgs<T>& a, int bl, double bs) {
+  if (a.standalone) return;
+  if (threadIdx.x == 0) a.red.part[(long long)bl * gridDim.x + blockIdx.x] = bs;
+  if (last_block(a.red.ticket)) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int q = warp; q < a.BL; q += blockDim.x / 32) {
+      double sum = warp_sum_partials(a.red.part + (long long)q * gridDim.x, gridDim.x, 1);
+      if (lane == 0 && !a.sc[q].done) step_update(a.sc[q], sum);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *a.red.ticket = 0u;
+  }
+}
+
 template <typename T, int CC>
 __global__ void __launch_bounds__(256) k_ku(StencilArgs<T> a) {
   __shared__ T mt[2 * 256];
@@ -30,17 +47,23 @@ __global__ void __launch_bounds__(256) k_ku(StencilArgs<T> a) {
   const double bs = ku_task<T, CC, false>(a, mt, bl, blockIdx.x, red_sh, tile_smem,
                                           a.standalone ? nullptr : &a.sc[bl].done);
   pdl_trigger();
-  if (a.standalone) return;
-  if (threadIdx.x == 0) a.red.part[(long long)bl * gridDim.x + blockIdx.x] = bs;
-  if (last_block(a.red.ticket)) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int q = warp; q < a.BL; q += blockDim.x / 32) {
-      double sum = warp_sum_partials(a.red.part + (long long)q * gridDim.x, gridDim.x, 1);
-      if (lane == 0 && !a.sc[q].done) step_update(a.sc[q], sum);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) *a.red.ticket = 0u;
-  }
+  ku_finish<T>(a, bl, bs);
+}
+
+// Elastic K d, element by element in the Walsh basis (ku_elastic.cuh)
+template <typename T>
+__global__ void __launch_bounds__(KE_THREADS) k_ku_el(StencilArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char ke_raw[];
+  __shared__ T mt[2 * 256];
+  __shared__ double red_sh[32];
+  const int bl = blockIdx.y;
+  load_material<T>(mt, a.mat, bl / a.L);
+  __syncthreads();
+  pdl_wait();
+  const double bs = ku_elastic_tile<T, false>(a, mt, bl, blockIdx.x, red_sh, reinterpret_cast<T*>(ke_raw),
+                                              a.standalone ? nullptr : &a.sc[bl].done);
+  pdl_trigger();
+  ku_finish<T>(a, bl, bs);
 }
 
 // ============================================================================ init: r = f, u = d = 0
@@ -467,8 +490,9 @@ static dim3 node_grid(const Grid& g, int y) {
 }
 int node_blocks_x(const Grid& g) { return node_grid(g, 1).x; }
 
-static dim3 ku_grid(const Grid& g, int c, int y) {
-  // thermal: 32 x 8 x KU_TZ node tiles; elastic: 32 x 4 x 2 node blocks
+// Node tiles of the per-node K d tasks (persistent kernel): thermal 32 x 8 x KU_CZ columns,
+// elastic 32 x 4 x 2 node blocks
+static dim3 ku_task_grid(const Grid& g, int c, int y) {
   if (c != 1) return node_grid(g, y);
 #if UNOCG_KU_MODE == 0
   int tx = (g.n3 + 31) / 32, ty = (g.n2 + 7) / 8, tz = (g.n1 + KU_TZ - 1) / KU_TZ;
@@ -477,12 +501,22 @@ static dim3 ku_grid(const Grid& g, int c, int y) {
 #endif
   return dim3(tx * ty * tz, y);
 }
-int ku_blocks_x(const Grid& g, int c) { return ku_grid(g, c, 1).x; }
+int ku_tasks_x(const Grid& g, int c) { return ku_task_grid(g, c, 1).x; }
+// blocks of k_ku (thermal) / k_ku_el (elastic: 32 x 8 x KE_CZ node tiles)
+int ku_blocks_x(const Grid& g, int c) { return c == 1 ? ku_tasks_x(g, c) : ke_tiles(g); }
 
 template <typename T> cudaError_t launch_ku(const StencilArgs<T>& a, cudaStream_t s) {
-  dim3 grid = ku_grid(a.g, a.c, a.BL);
-  if (a.c == 1) return launch_pdl(k_ku<T, 1>, grid, dim3(256), 0, s, a);
-  return launch_pdl(k_ku<T, 3>, grid, dim3(256), 0, s, a);
+  if (a.c == 1) return launch_pdl(k_ku<T, 1>, ku_task_grid(a.g, 1, a.BL), dim3(256), 0, s, a);
+  const size_t smem = ke_smem_bytes<T>();
+  if (smem > 48 * 1024) {
+    static bool attr_set = false;
+    if (!attr_set) {
+      cudaError_t e = cudaFuncSetAttribute(k_ku_el<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      attr_set = true;
+    }
+  }
+  return launch_pdl(k_ku_el<T>, dim3(ke_tiles(a.g), a.BL), dim3(KE_THREADS), smem, s, a);
 }
 template <typename T> cudaError_t launch_init(const InitArgs<T>& a, int BL, cudaStream_t s) {
   dim3 grid = node_grid(a.g, BL);

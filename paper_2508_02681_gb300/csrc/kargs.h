@@ -25,6 +25,7 @@ static inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 blo
   cfg.numAttrs = UNOCG_PDL ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, kern, args...);
 }
+
 }  // namespace unocg
 
 namespace unocg {
@@ -202,7 +203,8 @@ cudaError_t launch_average(const AvgArgs& a, int B, double* out, cudaStream_t s)
 cudaError_t launch_sens(const AvgArgs& a, int B, double* out, cudaStream_t s);
 cudaError_t launch_interleave(const double* src, double* dst, int c, long long n, cudaStream_t s);
 int node_blocks_x(const Grid& g);
-int ku_blocks_x(const Grid& g, int c);
+int ku_blocks_x(const Grid& g, int c);  // blocks of one K d launch per (instance, load)
+int ku_tasks_x(const Grid& g, int c);   // K d tasks of the persistent kernel per (instance, load)
 int jac_blocks_x(long long m, int BL);
 int sens_blocks_x(const Grid& g);
 
