@@ -45,7 +45,8 @@ def parse():
     ap.add_argument("--bc", default="periodic", choices=["periodic", "dirichlet", "mixed"],
                     help="with --profile-only: boundary conditions of the profiled solves (mixed: Dirichlet faces on axis 2)")
     ap.add_argument("--elastic", action="store_true",
-                    help="with --profile-only and --bc dirichlet/mixed: the 64^3 elastic workload (six loads)")
+                    help="with --profile-only: the 64^3 elastic workload (six loads) instead of the thermal one")
+    ap.add_argument("--no-elastic", action="store_true", help="skip the elastic measurement")
     ap.add_argument("--no-dirichlet", action="store_true", help="skip the Dirichlet-BC measurement")
     ap.add_argument("--no-graph", action="store_true",
                     help="profile-only: host-driven loop (kernels inside conditional graph bodies are not visible to ncu)")
@@ -236,6 +237,60 @@ def batched_uneven(n_inst: int = 256, reps: int = 3):
             "contexts": len(sizes), "input_generation_s": t_gen}
 
 
+def periodic_solver(w, stream):
+    """A periodic context on the workload ``w`` with closed-form reference-medium weights."""
+    from paper_2508_02681_gb300 import _lib, api
+    from paper_2508_02681_gb300.solver import Homogenization
+    h = Homogenization(w["physics"], w["phase"].shape)
+    api.unocg_set_stream(h.ctx, stream)
+    h.set_microstructure(w["phase"], 2)
+    h.set_phase_properties(w["props"])
+    h.set_macro_load(w["loads"])
+    h.set_uno_weights(_lib.W_REFERENCE_MEDIUM)
+    return h
+
+
+def elastic(stream, steps: int = 5):
+    """Time-to-tolerance of the 64^3 elastic workload (E 1 / 10, nu 0.3 / 0.2, spheres r = 6 at
+    volume fraction 0.3, the six Mandel unit strains): mixed and FP64 UNO-CG and Jac-CG, CUDA
+    events on the solve stream, L2 flushed before each solve, and the 6 x 6 effective stiffness."""
+    import torch
+    from paper_2508_02681_gb300 import _lib, api
+    from synth import workload
+    w = workload(3)
+    h = periodic_solver(w, stream)
+    L = w["loads"].shape[0]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    out = {"workload": "elastic 64^3 periodic, RSA spheres r=6 vf=0.3, E 1/10, nu 0.3/0.2, 6 Mandel unit strains, "
+                       "relative residual 1e-6"}
+    C = {}
+    for name, pc, prec, reps in (("mixed_uno", _lib.PRECOND_UNO, _lib.MIXED, steps),
+                                 ("fp64_uno", _lib.PRECOND_UNO, _lib.FP64, max(2, steps // 2)),
+                                 ("mixed_jacobi", _lib.PRECOND_JACOBI, _lib.MIXED, 2),
+                                 ("fp64_jacobi", _lib.PRECOND_JACOBI, _lib.FP64, 2)):
+        opts = api.make_opts(tol=TOL, max_iter=20000, precond=pc, precision=prec, replace_every=50)
+        api.unocg_solve_async(h.ctx, opts)
+        api.unocg_solve_wait(h.ctx, L)
+        ms = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            api.unocg_solve_async(h.ctx, opts)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        info = api.unocg_solve_wait(h.ctx, L)
+        C[name] = h.effective_tensor()[0]
+        out[name] = {"ms": float(np.mean(ms)), "iterations": int(info.c.max_iters),
+                     "true_rel_res": float(np.max(info.true_rel_res))}
+    out["C_eff_rel_diff_mixed_vs_fp64"] = float(np.max(np.abs(C["mixed_uno"] - C["fp64_uno"])) /
+                                                np.max(np.abs(C["fp64_uno"])))
+    out["C_eff_fp64_uno"] = np.round(C["fp64_uno"], 6).tolist()
+    h.close()
+    return out
+
+
 def dirichlet_solver(w, stream, bc=(1, 1, 1), physics=1):
     """A 64^3 workload with Dirichlet BC (fluctuation zero on the boundary, sine transform in
     the UNO preconditioner), or mixed BC with ``bc`` per axis."""
@@ -358,10 +413,17 @@ def main():
         opts = variants["mixed_uno"]
         if args.no_graph:
             opts.use_graph = 0
+        hp = h
+        if args.elastic:
+            h.close()
+            we = workload(3)
+            L = we["loads"].shape[0]
+            hp = periodic_solver(we, stream)
         for _ in range(2):
-            api.unocg_solve_async(h.ctx, opts)
-            api.unocg_solve_wait(h.ctx, L)
+            api.unocg_solve_async(hp.ctx, opts)
+            api.unocg_solve_wait(hp.ctx, L)
         torch.cuda.synchronize()
+        hp.close()
         print("profile-only run done")
         return 0
 
@@ -449,6 +511,8 @@ def main():
     h.close()
     if rank == 0 and world == 1 and not args.no_batch and not args.profile_only:
         line["batched_uneven"] = batched_uneven()
+    if rank == 0 and world == 1 and not args.no_elastic:
+        line["elastic"] = elastic(stream)
     if rank == 0 and world == 1 and not args.no_dirichlet:
         line["dirichlet"] = dirichlet(w, stream)
         line["mixed_bc"] = dirichlet(w, stream, bc=(0, 1, 0))

@@ -15,6 +15,12 @@
 #include "stencil.cuh"
 #include "ku_task.cuh"
 #include "ku_elastic.cuh"
+#include "replace_elastic.cuh"
+#include <cstdlib>
+#include <cstring>
+#ifndef UNOCG_THERMAL_ELEMENT_DEFAULT
+#define UNOCG_THERMAL_ELEMENT_DEFAULT 0
+#endif
 
 namespace unocg {
 
@@ -50,8 +56,8 @@ __global__ void __launch_bounds__(256) k_ku(StencilArgs<T> a) {
   ku_finish<T>(a, bl, bs);
 }
 
-// Elastic K d, element by element in the Walsh basis (ku_elastic.cuh)
-template <typename T>
+// K d element by element in the Walsh basis (ku_elastic.cuh)
+template <typename T, int CC>
 __global__ void __launch_bounds__(KE_THREADS) k_ku_el(StencilArgs<T> a) {
   extern __shared__ __align__(16) unsigned char ke_raw[];
   __shared__ T mt[2 * 256];
@@ -60,7 +66,7 @@ __global__ void __launch_bounds__(KE_THREADS) k_ku_el(StencilArgs<T> a) {
   load_material<T>(mt, a.mat, bl / a.L);
   __syncthreads();
   pdl_wait();
-  const double bs = ku_elastic_tile<T, false>(a, mt, bl, blockIdx.x, red_sh, reinterpret_cast<T*>(ke_raw),
+  const double bs = ku_element_tile<T, CC, false>(a, mt, bl, blockIdx.x, red_sh, reinterpret_cast<T*>(ke_raw),
                                               a.standalone ? nullptr : &a.sc[bl].done);
   pdl_trigger();
   ku_finish<T>(a, bl, bs);
@@ -233,6 +239,31 @@ __global__ void __launch_bounds__(256) k_replace(ReplaceArgs a) {
   }
   __shared__ double red_sh[32];
   const double bm = block_max(lmax, red_sh);
+  if (threadIdx.x == 0) atomic_max_nonneg(a.into_rmax ? &a.sc[bl].rmax_bits : &a.sc[bl].tmax_bits, bm);
+}
+
+// Elastic replacement element by element in float pairs (replace_elastic.cuh)
+__global__ void __launch_bounds__(KE_THREADS) k_replace_el(ReplaceArgs a) {
+  extern __shared__ __align__(16) unsigned char re_raw[];
+  __shared__ float2 kc[6 * 256];  // element constants of every phase as pairs
+  __shared__ double red_sh[32];
+  const int bl = blockIdx.y;
+  const int b = bl / a.L;
+  const int np = a.mat.n_phases;
+  const double h = a.g.h;
+  for (int p = threadIdx.x; p < np; p += blockDim.x) {
+    const double lam = a.mat.m64[(long long)b * 2 * np + 2 * p], mu = a.mat.m64[(long long)b * 2 * np + 2 * p + 1];
+    const double k[6] = {h * mu / 8.0, h * lam / 16.0, h * mu / 48.0, h * lam / 48.0, h * (3.0 * mu + lam) / 48.0,
+                         h * (4.0 * mu + lam) / 144.0};
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const df32 v = df_from_double(k[j]);
+      kc[6 * p + j] = make_float2(v.hi, v.lo);
+    }
+  }
+  __syncthreads();
+  if (a.only_pending && !a.sc[bl].need_replace) return;
+  const double bm = replace_elastic_tile(a, kc, bl, blockIdx.x, red_sh, reinterpret_cast<float2*>(re_raw));
   if (threadIdx.x == 0) atomic_max_nonneg(a.into_rmax ? &a.sc[bl].rmax_bits : &a.sc[bl].tmax_bits, bm);
 }
 
@@ -502,21 +533,37 @@ static dim3 ku_task_grid(const Grid& g, int c, int y) {
   return dim3(tx * ty * tz, y);
 }
 int ku_tasks_x(const Grid& g, int c) { return ku_task_grid(g, c, 1).x; }
-// blocks of k_ku (thermal) / k_ku_el (elastic: 32 x 8 x KE_CZ node tiles)
-int ku_blocks_x(const Grid& g, int c) { return c == 1 ? ku_tasks_x(g, c) : ke_tiles(g); }
 
-template <typename T> cudaError_t launch_ku(const StencilArgs<T>& a, cudaStream_t s) {
-  if (a.c == 1) return launch_pdl(k_ku<T, 1>, ku_task_grid(a.g, 1, a.BL), dim3(256), 0, s, a);
-  const size_t smem = ke_smem_bytes<T>();
+// Thermal K d: register column march (k_ku) or element scheme (k_ku_el); elastic: element
+// scheme.  UNOCG_THERMAL_KU=element|column overrides the thermal choice.
+static bool thermal_element() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = std::getenv("UNOCG_THERMAL_KU");
+    v = e ? (std::strcmp(e, "element") == 0 ? 1 : 0) : UNOCG_THERMAL_ELEMENT_DEFAULT;
+  }
+  return v == 1;
+}
+// blocks of one K d launch per (instance, load)
+int ku_blocks_x(const Grid& g, int c) { return (c == 1 && !thermal_element()) ? ku_tasks_x(g, c) : ke_tiles(g); }
+
+template <typename T, int CC> static cudaError_t launch_ku_el(const StencilArgs<T>& a, cudaStream_t s) {
+  const size_t smem = ke_smem_bytes<T, CC>();
   if (smem > 48 * 1024) {
     static bool attr_set = false;
     if (!attr_set) {
-      cudaError_t e = cudaFuncSetAttribute(k_ku_el<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaError_t e = cudaFuncSetAttribute(k_ku_el<T, CC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
       attr_set = true;
     }
   }
-  return launch_pdl(k_ku_el<T>, dim3(ke_tiles(a.g), a.BL), dim3(KE_THREADS), smem, s, a);
+  return launch_pdl(k_ku_el<T, CC>, dim3(ke_tiles(a.g), a.BL), dim3(KE_THREADS), smem, s, a);
+}
+
+template <typename T> cudaError_t launch_ku(const StencilArgs<T>& a, cudaStream_t s) {
+  if (a.c != 1) return launch_ku_el<T, 3>(a, s);
+  if (thermal_element()) return launch_ku_el<T, 1>(a, s);
+  return launch_pdl(k_ku<T, 1>, ku_task_grid(a.g, 1, a.BL), dim3(256), 0, s, a);
 }
 template <typename T> cudaError_t launch_init(const InitArgs<T>& a, int BL, cudaStream_t s) {
   dim3 grid = node_grid(a.g, BL);
@@ -536,9 +583,17 @@ static int pw_blocks(long long m) {
   return (int)(b < 1 ? 1 : b);
 }
 cudaError_t launch_replace(const ReplaceArgs& a, int BL, cudaStream_t s) {
-  dim3 grid = node_grid(a.g, BL);
-  if (a.c == 1) k_replace<1><<<grid, 256, 0, s>>>(a);
-  else k_replace<3><<<grid, 256, 0, s>>>(a);
+  if (a.c == 1) {
+    k_replace<1><<<node_grid(a.g, BL), 256, 0, s>>>(a);
+    return cudaGetLastError();
+  }
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_replace_el, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kReplaceElSmem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  k_replace_el<<<dim3(ke_tiles(a.g), BL), KE_THREADS, kReplaceElSmem, s>>>(a);
   return cudaGetLastError();
 }
 template <typename T> cudaError_t launch_fold(const FoldArgs<T>& a, int BL, cudaStream_t s) {

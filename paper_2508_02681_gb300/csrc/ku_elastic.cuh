@@ -1,4 +1,4 @@
-// Elastic K d element by element (Sec. 4.1, "matrix-free implementations" of Sec. 5.5).
+// K d element by element (Sec. 4.1, "matrix-free implementations" of Sec. 5.5).
 //
 // The force of one brick on its corners, K_e u_e = h int_unit B^T C B u dxi, is evaluated in the
 // Walsh basis of the trilinear field instead of as a 24 x 24 product.  With centred unit-cube
@@ -15,7 +15,9 @@
 //   G[{j,k}][m] = h mu (2 c[jk][m] + c[km][j] + c[jm][k]) / 48
 //   G[{1,2,3}][i] = h (4 mu + lam) c[123][i] / 144.
 // (Isotropic C = lam tr(eps) I + 2 mu eps; the constant mode M = {} carries no force.)  About 190
-// additions and multiplications per element instead of 1,152 multiply-adds per node.
+// additions and multiplications per element instead of 1,152 multiply-adds per node.  Thermal
+// conduction (c = 1, K_e = h kappa int grad N . grad N) in the same basis is diagonal:
+//   G[M] = h kappa c[M] / 16, / 24, / 48 for |M| = 1, 2, 3.
 //
 // Work layout: a block of KE_THREADS threads computes a node tile of 32 (i3) x 8 (i2) nodes over
 // KE_CZ consecutive node planes.  Its first 33 x 9 threads each own one element column (the tile's
@@ -38,8 +40,8 @@ constexpr int KE_THREADS = 320;
 #endif
 constexpr int KE_CZ = UNOCG_KE_CZ;                    // node planes per block
 
-// two buffers of 4 corners x 3 components per element column
-template <typename T> constexpr size_t ke_smem_bytes() { return 2 * 12 * KE_SLOTS * sizeof(T); }
+// two buffers of 4 corners x CC components per element column
+template <typename T, int CC> constexpr size_t ke_smem_bytes() { return 2 * 4 * CC * KE_SLOTS * sizeof(T); }
 
 __host__ __device__ inline int ke_tiles(const Grid& g) {
   return ((g.n3 + KE_T3 - 1) / KE_T3) * ((g.n2 + KE_T2 - 1) / KE_T2) * ((g.n1 + KE_CZ - 1) / KE_CZ);
@@ -59,6 +61,23 @@ __device__ __forceinline__ KeW2<T> ke_walsh2(T u00, T u01, T u10, T u11) {
 // Corner forces of one element from the Walsh sums of its lower (a1 = 0) and upper (a1 = 1)
 // node planes: flo[a2 * 2 + a3][i] at a1 = 0, fhi at a1 = 1.  k = (h mu / 8, h lam / 16,
 // h mu / 48, h lam / 48, h (3 mu + lam) / 48, h (4 mu + lam) / 144), see the header comment.
+template <typename T>
+__device__ __forceinline__ void ke_element(const KeW2<T> (&L)[1], const KeW2<T> (&H)[1], const T (&k)[6],
+                                           T (&flo)[4][1], T (&fhi)[4][1]) {
+  // thermal: k = (h kappa / 16, h kappa / 24, h kappa / 48)
+  const T G1 = k[0] * (H[0].e - L[0].e), G2 = k[0] * (L[0].k2 + H[0].k2), G3 = k[0] * (L[0].k3 + H[0].k3);
+  const T G12 = k[1] * (H[0].k2 - L[0].k2), G13 = k[1] * (H[0].k3 - L[0].k3), G23 = k[1] * (L[0].k23 + H[0].k23);
+  const T G123 = k[2] * (H[0].k23 - L[0].k23);
+  const T ex0 = -G2, ey0 = G3 - G23, ex1 = G2, ey1 = G3 + G23;
+  const T E00 = ex0 - ey0, E01 = ex0 + ey0, E10 = ex1 - ey1, E11 = ex1 + ey1;
+  const T fx0 = G1 - G12, fy0 = G13 - G123, fx1 = G1 + G12, fy1 = G13 + G123;
+  const T F00 = fx0 - fy0, F01 = fx0 + fy0, F10 = fx1 - fy1, F11 = fx1 + fy1;
+  flo[0][0] = E00 - F00; fhi[0][0] = E00 + F00;
+  flo[1][0] = E01 - F01; fhi[1][0] = E01 + F01;
+  flo[2][0] = E10 - F10; fhi[2][0] = E10 + F10;
+  flo[3][0] = E11 - F11; fhi[3][0] = E11 + F11;
+}
+
 template <typename T>
 __device__ __forceinline__ void ke_element(const KeW2<T> (&L)[3], const KeW2<T> (&H)[3], const T (&k)[6],
                                            T (&flo)[4][3], T (&fhi)[4][3]) {
@@ -117,8 +136,16 @@ __device__ __forceinline__ int ke_wrap(int v, int n) {
 }
 
 // Element constants of phase p (see ke_element)
-template <typename T>
+template <typename T, int CC>
 __device__ __forceinline__ void ke_consts(const T* mt, int p, T h, T (&k)[6]) {
+  if (CC == 1) {
+    const T hk = h * mt[2 * p];
+    k[0] = hk * (T)0.0625;
+    k[1] = hk * (T)(1.0 / 24.0);
+    k[2] = hk * (T)(1.0 / 48.0);
+    k[3] = k[4] = k[5] = (T)0;
+    return;
+  }
   const T lam = mt[2 * p], mu = mt[2 * p + 1];
   k[0] = h * mu * (T)0.125;
   k[1] = h * lam * (T)0.0625;
@@ -129,16 +156,16 @@ __device__ __forceinline__ void ke_consts(const T* mt, int p, T h, T (&k)[6]) {
 }
 
 // p = K d on node tile `tile` of (instance, load) bl; block of KE_THREADS threads, `sm` holds
-// ke_smem_bytes<T>().  Returns the block sum of d . p (thread 0) unless a.standalone.
+// ke_smem_bytes<T, CC>().  Returns the block sum of d . p (thread 0) unless a.standalone.
 // skip: optional flag of the pair (nonzero = finished), uniform over the block.
-template <typename T, bool COH>
-__device__ double ku_elastic_tile(const StencilArgs<T>& a, const T* mt, int bl, int tile, double* red_sh, T* sm,
+template <typename T, int CC, bool COH>
+__device__ double ku_element_tile(const StencilArgs<T>& a, const T* mt, int bl, int tile, double* red_sh, T* sm,
                                   const int* skip) {
   const Grid& g = a.g;
   const long long n = g.n;
   const uint8_t* ph = a.phase + (long long)(bl / a.L) * n;
-  const T* d = a.d + (long long)bl * 3 * n;
-  T* p = a.p + (long long)bl * 3 * n;
+  const T* d = a.d + (long long)bl * CC * n;
+  T* p = a.p + (long long)bl * CC * n;
   const int nt3 = (g.n3 + KE_T3 - 1) / KE_T3, nt2 = (g.n2 + KE_T2 - 1) / KE_T2;
   int bx = tile;
   const int b3 = bx % nt3;
@@ -167,12 +194,12 @@ __device__ double ku_elastic_tile(const StencilArgs<T>& a, const T* mt, int bl, 
   const int noff = (t2 + r2) * g.n3 + t3 + r3;
   const T h = grid_h<T>(g);
   DotAcc<T> dp;
-  KeW2<T> L[3], H[3];
-  T carry[4][3];
-  auto load_plane = [&](int z, KeW2<T>(&W)[3]) {
+  KeW2<T> L[CC], H[CC];
+  T carry[4][CC];
+  auto load_plane = [&](int z, KeW2<T>(&W)[CC]) {
     const T* dz = d + (long long)z * S;
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < CC; ++i) {
       const T* di = dz + (long long)i * n;
       W[i] = ke_walsh2<T>(ldf<COH>(di + o00), ldf<COH>(di + o01), ldf<COH>(di + o10), ldf<COH>(di + o11));
     }
@@ -182,24 +209,24 @@ __device__ double ku_elastic_tile(const StencilArgs<T>& a, const T* mt, int bl, 
     const int zm = z0 ? z0 - 1 : g.n1 - 1;
     load_plane(zm, L);
     load_plane(z0, H);
-    T k[6], flo[4][3];
-    ke_consts<T>(mt, __ldg(ph + (long long)zm * S + o00), h, k);
+    T k[6], flo[4][CC];
+    ke_consts<T, CC>(mt, __ldg(ph + (long long)zm * S + o00), h, k);
     ke_element<T>(L, H, k, flo, carry);
   }
   if (skip && *skip) return 0.0;
   for (int z = z0; z < zend; ++z) {
-    T* buf = sm + ((z - z0) & 1) * (12 * KE_SLOTS);
+    T* buf = sm + ((z - z0) & 1) * (4 * CC * KE_SLOTS);
     if (is_el) {
 #pragma unroll
-      for (int i = 0; i < 3; ++i) L[i] = H[i];
+      for (int i = 0; i < CC; ++i) L[i] = H[i];
       load_plane(z + 1 == g.n1 ? 0 : z + 1, H);
-      T k[6], flo[4][3], fhi[4][3];
-      ke_consts<T>(mt, __ldg(ph + (long long)z * S + o00), h, k);
+      T k[6], flo[4][CC], fhi[4][CC];
+      ke_consts<T, CC>(mt, __ldg(ph + (long long)z * S + o00), h, k);
       ke_element<T>(L, H, k, flo, fhi);
 #pragma unroll
       for (int c = 0; c < 4; ++c)
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
+        for (int i = 0; i < CC; ++i) {
           buf[(i * 4 + c) * KE_SLOTS + tid] = flo[c][i] + carry[c][i];
           carry[c][i] = fhi[c][i];
         }
@@ -210,7 +237,7 @@ __device__ double ku_elastic_tile(const StencilArgs<T>& a, const T* mt, int bl, 
       const int sA = (r2 + 1) * KE_S3 + r3 + 1, sB = r2 * KE_S3 + r3;
       const long long q = (long long)z * S + noff;
 #pragma unroll
-      for (int i = 0; i < 3; ++i) {
+      for (int i = 0; i < CC; ++i) {
         const T* bi = buf + i * 4 * KE_SLOTS;
         const T v = (bi[sA] + bi[KE_SLOTS + sA - 1]) + (bi[2 * KE_SLOTS + sB + 1] + bi[3 * KE_SLOTS + sB]);
         p[(long long)i * n + q] = v;
