@@ -16,6 +16,7 @@
 #include "../df64.cuh"
 #include "../kargs.h"
 #include "../stencil.cuh"
+#include "../replace_elastic.cuh"
 #include "dargs.h"
 
 namespace unocg {
@@ -617,6 +618,26 @@ __global__ void __launch_bounds__(kDThreads) k_dreplace(DResArgs<float> a, const
   if (threadIdx.x == 0) atomic_max_nonneg(into_rmax ? &a.sc[bl].rmax_bits : &a.sc[bl].tmax_bits, bm);
 }
 
+// Elastic replacement element by element in float pairs (the periodic element scheme on the
+// embedding grid: u32 is zero on the Dirichlet nodes, so the forces at the free nodes are the
+// Dirichlet ones); only free nodes are updated.
+__global__ void __launch_bounds__(KE_THREADS) k_dreplace_el(DResArgs<float> a, const float* u32all, int into_rmax) {
+  extern __shared__ __align__(16) unsigned char re_raw[];
+  __shared__ float2 kc[6 * 256];
+  __shared__ double red_sh[32];
+  const DGrid& g = a.g;
+  const int bl = blockIdx.y;
+  replace_elastic_consts(a.mat, bl / a.L, g.pg.h, kc);
+  __syncthreads();
+  if (a.only_pending && !a.sc[bl].need_replace) return;
+  const long long off = (long long)bl * 3 * g.ne;
+  const double bm = replace_elastic_tile(
+      g.pg, a.phase + (long long)(bl / a.L) * g.ne, u32all + off, nullptr, df32{0.0f, 0.0f},
+      const_cast<double*>(a.f64) + off, a.r ? a.r + off : nullptr, kc, blockIdx.x, red_sh,
+      reinterpret_cast<float2*>(re_raw), [&](int i1, int i2, int i3) { return dfree_node(g, i1, i2, i3); });
+  if (threadIdx.x == 0) atomic_max_nonneg(into_rmax ? &a.sc[bl].rmax_bits : &a.sc[bl].tmax_bits, bm);
+}
+
 // ============================================================================ Jacobi / plain CG
 // part 0: r -= alpha q, u += alpha p, ||r||_inf, stopping test
 // part 1: gamma = r . z with z = D^-1 r (or r), beta
@@ -998,9 +1019,17 @@ template cudaError_t launch_dmixq<double>(const DPassArgs<double>&, int, int, cu
 template cudaError_t launch_dmixq<float>(const DPassArgs<float>&, int, int, cudaStream_t);
 
 cudaError_t launch_dreplace(const DResArgs<float>& a, const float* u32, int into_rmax, cudaStream_t s) {
-  dim3 grid(dgrid_blocks(a.g.nf), a.BL);
-  if (a.c == 1) k_dreplace<1><<<grid, kDThreads, 0, s>>>(a, u32, into_rmax);
-  else k_dreplace<3><<<grid, kDThreads, 0, s>>>(a, u32, into_rmax);
+  if (a.c == 1) {
+    k_dreplace<1><<<dim3(dgrid_blocks(a.g.nf), a.BL), kDThreads, 0, s>>>(a, u32, into_rmax);
+    return cudaGetLastError();
+  }
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_dreplace_el, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kReplaceElSmem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  k_dreplace_el<<<dim3(ke_tiles(a.g.pg), a.BL), KE_THREADS, kReplaceElSmem, s>>>(a, u32, into_rmax);
   return cudaGetLastError();
 }
 

@@ -248,22 +248,14 @@ __global__ void __launch_bounds__(KE_THREADS) k_replace_el(ReplaceArgs a) {
   __shared__ float2 kc[6 * 256];  // element constants of every phase as pairs
   __shared__ double red_sh[32];
   const int bl = blockIdx.y;
-  const int b = bl / a.L;
-  const int np = a.mat.n_phases;
-  const double h = a.g.h;
-  for (int p = threadIdx.x; p < np; p += blockDim.x) {
-    const double lam = a.mat.m64[(long long)b * 2 * np + 2 * p], mu = a.mat.m64[(long long)b * 2 * np + 2 * p + 1];
-    const double k[6] = {h * mu / 8.0, h * lam / 16.0, h * mu / 48.0, h * lam / 48.0, h * (3.0 * mu + lam) / 48.0,
-                         h * (4.0 * mu + lam) / 144.0};
-#pragma unroll
-    for (int j = 0; j < 6; ++j) {
-      const df32 v = df_from_double(k[j]);
-      kc[6 * p + j] = make_float2(v.hi, v.lo);
-    }
-  }
+  replace_elastic_consts(a.mat, bl / a.L, a.g.h, kc);
   __syncthreads();
   if (a.only_pending && !a.sc[bl].need_replace) return;
-  const double bm = replace_elastic_tile(a, kc, bl, blockIdx.x, red_sh, reinterpret_cast<float2*>(re_raw));
+  const long long off = (long long)bl * 3 * a.g.n;
+  const double bm = replace_elastic_tile(a.g, a.phase + (long long)(bl / a.L) * a.g.n, a.u32 + off, a.d + off,
+                                         df_from_double(a.sc[bl].alpha), a.rref + off, a.r ? a.r + off : nullptr, kc,
+                                         blockIdx.x, red_sh, reinterpret_cast<float2*>(re_raw),
+                                         [](int, int, int) { return true; });
   if (threadIdx.x == 0) atomic_max_nonneg(a.into_rmax ? &a.sc[bl].rmax_bits : &a.sc[bl].tmax_bits, bm);
 }
 

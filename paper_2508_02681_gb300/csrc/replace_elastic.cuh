@@ -24,17 +24,31 @@ __device__ __forceinline__ dfv operator*(dfv a, dfv b) { return df_mul(a.v, b.v)
 
 constexpr size_t kReplaceElSmem = 2 * 4 * 3 * KE_SLOTS * sizeof(float2);  // double buffer, c = 3
 
-// One node tile of one (instance, load); block of KE_THREADS threads; `kc` holds the six element
-// constants of every phase as pairs, `sm` kReplaceElSmem bytes.  Returns the tile's max |rref|
-// (thread 0).
-__device__ double replace_elastic_tile(const ReplaceArgs& a, const float2* kc, int bl, int tile, double* red_sh,
-                                       float2* sm) {
-  const Grid& g = a.g;
+// Six element constants of every phase as pairs (see ke_element), for instance b.
+__device__ __forceinline__ void replace_elastic_consts(const Material& mat, int b, double h, float2* kc) {
+  const int np = mat.n_phases;
+  for (int p = threadIdx.x; p < np; p += blockDim.x) {
+    const double lam = mat.m64[(long long)b * 2 * np + 2 * p], mu = mat.m64[(long long)b * 2 * np + 2 * p + 1];
+    const double k[6] = {h * mu / 8.0, h * lam / 16.0, h * mu / 48.0, h * lam / 48.0, h * (3.0 * mu + lam) / 48.0,
+                         h * (4.0 * mu + lam) / 144.0};
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const df32 v = df_from_double(k[j]);
+      kc[6 * p + j] = make_float2(v.hi, v.lo);
+    }
+  }
+}
+
+// One node tile of one (instance, load) on the periodic node grid g: rref -= K w with
+// w = u32 + alpha d (dd null: w = u32), r = (float) rref, at the nodes where is_free(i1, i2, i3)
+// holds (the others are left as they are).  ph, u32, dd, rref, r point at this pair's fields;
+// block of KE_THREADS threads; `kc` from replace_elastic_consts, `sm` kReplaceElSmem bytes.
+// Returns the max |rref| over the tile's free nodes (thread 0).
+template <class FreeFn>
+__device__ double replace_elastic_tile(const Grid& g, const uint8_t* ph, const float* u32, const float* dd, df32 al,
+                                       double* rref, float* r, const float2* kc, int tile, double* red_sh,
+                                       float2* sm, FreeFn is_free) {
   const long long n = g.n;
-  const uint8_t* ph = a.phase + (long long)(bl / a.L) * n;
-  const float* u32 = a.u32 + (long long)bl * 3 * n;
-  const float* dd = a.d + (long long)bl * 3 * n;
-  const df32 al = df_from_double(a.sc[bl].alpha);
   const int nt3 = (g.n3 + KE_T3 - 1) / KE_T3, nt2 = (g.n2 + KE_T2 - 1) / KE_T2;
   int bx = tile;
   const int b3 = bx % nt3;
@@ -62,7 +76,9 @@ __device__ double replace_elastic_tile(const ReplaceArgs& a, const float2* kc, i
   double lmax = 0.0;
   KeW2<dfv> L[3], H[3];
   dfv carry[4][3];
-  auto w_at = [&](int i, long long q) { return dfv(df_axpy(al, __ldg(dd + i * n + q), __ldg(u32 + i * n + q))); };
+  auto w_at = [&](int i, long long q) {
+    return dd ? dfv(df_axpy(al, __ldg(dd + i * n + q), __ldg(u32 + i * n + q))) : dfv(__ldg(u32 + i * n + q));
+  };
   auto load_plane = [&](int z, KeW2<dfv>(&W)[3]) {
     const long long zq = (long long)z * S;
 #pragma unroll
@@ -101,7 +117,7 @@ __device__ double replace_elastic_tile(const ReplaceArgs& a, const float2* kc, i
         }
     }
     __syncthreads();
-    if (is_node) {
+    if (is_node && is_free(z, t2 + r2, t3 + r3)) {
       const int sA = (r2 + 1) * KE_S3 + r3 + 1, sB = r2 * KE_S3 + r3;
       const long long q = (long long)z * S + noff;
 #pragma unroll
@@ -109,10 +125,10 @@ __device__ double replace_elastic_tile(const ReplaceArgs& a, const float2* kc, i
         const float2* bi = buf + i * 4 * KE_SLOTS;
         auto at = [&](int j) { return dfv(df32{bi[j].x, bi[j].y}); };
         const dfv v = (at(sA) + at(KE_SLOTS + sA - 1)) + (at(2 * KE_SLOTS + sB + 1) + at(3 * KE_SLOTS + sB));
-        const long long x = (long long)bl * 3 * n + i * n + q;
-        const double rr = a.rref[x] - df_to_double(v.v);
-        a.rref[x] = rr;
-        if (a.r) a.r[x] = (float)rr;
+        const long long x = i * n + q;
+        const double rr = rref[x] - df_to_double(v.v);
+        rref[x] = rr;
+        if (r) r[x] = (float)rr;
         lmax = fmax(lmax, fabs(rr));
       }
     }
