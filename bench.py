@@ -19,6 +19,7 @@ import argparse
 import json
 import os
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -78,11 +79,13 @@ class ClockSampler:
     def __init__(self, device_index: int):
         self.proc = None
         self.dev = device_index
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+        # the samples go to a temporary file (UNOCG_CLOCKS_CSV keeps them at a chosen path)
+        self.path = os.environ.get("UNOCG_CLOCKS_CSV") or os.path.join(
+            tempfile.gettempdir(), f"unocg_clocks_{os.getpid()}_rank{device_index}.csv")
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            os.makedirs(os.path.dirname(os.path.abspath(self.path)), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "50"],
