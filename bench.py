@@ -49,6 +49,7 @@ def parse():
                     help="with --profile-only: the 64^3 elastic workload (six loads) instead of the thermal one")
     ap.add_argument("--no-elastic", action="store_true", help="skip the elastic measurement")
     ap.add_argument("--no-dirichlet", action="store_true", help="skip the Dirichlet-BC measurement")
+    ap.add_argument("--no-hbm", action="store_true", help="skip the HBM-resident (192^3, 256^3) measurement")
     ap.add_argument("--no-graph", action="store_true",
                     help="profile-only: host-driven loop (kernels inside conditional graph bodies are not visible to ncu)")
     return ap.parse_args()
@@ -172,31 +173,41 @@ def launches_per_solve(info, precond_uno=True):
 
 
 # ----------------------------------------------------------------------------- reference arm
+CPU_SAMPLE = ("the whole workload: all 3 gradient loads solved by the FP64 oracle (assembly of the CSR K, "
+              "DFT-by-definition UNO, Algorithm 2) to 1e-6, no extrapolation; the SciPy CSR matvec is "
+              "single-threaded, the DFT matrix products use the BLAS threads of the host cores")
+
+
+def oracle_solve_ms(w):
+    """Wall time (ms) of one oracle solve of every load case of ``w``; iterations per load."""
+    from oracle import homogenize as hz
+    t0 = time.perf_counter()
+    r = hz.solve(w["phase"], w["props"], w["physics"], w["loads"], precond="uno", tol=TOL)
+    return (time.perf_counter() - t0) * 1000.0, [int(i) for i in r["iters"]]
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    from oracle import homogenize as hz
     from synth import workload
     w = workload(2)
     cores = len(os.sched_getaffinity(0))
     times = []
     iters = []
     for step in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        r = hz.solve(w["phase"], w["props"], 1, w["loads"][:1], precond="uno", tol=TOL)
-        dt = time.perf_counter() - t0
+        ms_step, it = oracle_solve_ms(w)
         if step >= args.warmup:
-            times.append(dt)
-            iters.append(r["iters"][0])
-    ms = float(np.mean(times)) * 1000.0 * 3.0  # one load per step, scaled to the 3-load workload
-    sample = "one of the 3 load cases (gradient e1) per step, full oracle solve (assembled CSR K, DFT-by-definition UNO, Algorithm 2), scaled x3"
+            times.append(ms_step)
+            iters.append(it)
+    ms = float(np.mean(times))
+    sample = CPU_SAMPLE
     line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD},
             "cpu_baseline": {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample,
-                             "iterations": int(np.mean(iters))},
+                             "iterations": iters[-1] if iters else None, "csr_matvec_threads": 1},
             "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -291,6 +302,82 @@ def elastic(stream, steps: int = 5):
                                                 np.max(np.abs(C["fp64_uno"])))
     out["C_eff_fp64_uno"] = np.round(C["fp64_uno"], 6).tolist()
     h.close()
+    return out
+
+
+HBM_WORKLOADS = (
+    # name, physics, N, inclusion radius (6 voxels at 64^3, scaled with N), contrast
+    ("thermal256", 1, 256, 24.0, 100.0),
+    ("thermal192", 1, 192, 18.0, 100.0),
+    ("elastic192", 3, 192, 18.0, 10.0),
+)
+
+
+def hbm_workload(physics, N, radius, contrast, seed):
+    """RSA spheres at volume fraction 0.3 on an N^3 grid (fields of 25 MB to 0.5 GB, beyond the
+    129 MB L2): conductivity 1 / contrast with the three gradients, or (E, nu) = (1, 0.3) /
+    (contrast, 0.2) with the six Mandel unit strains."""
+    from synth import rsa_spheres, unit_loads
+    phase, vf = rsa_spheres((N, N, N), radius, 0.3, seed)
+    props = np.array([1.0, contrast]) if physics == 1 else np.array([[1.0, 0.3], [contrast, 0.2]])
+    return dict(phase=phase, vf=vf, physics=physics, props=props, loads=unit_loads(physics), tol=TOL)
+
+
+def hbm_resident(stream, reps: int = 3):
+    """Roofline on HBM-resident grids: for each workload the mixed-precision UNO-CG
+    time-to-1e-6 (CUDA events on the solve stream, mean of `reps` solves after a warm-up) and
+    the per-kernel event times of the iteration (10 host-driven iterations, same kernels and
+    launch shapes as the graph), each against its algorithmic bytes (every array the kernel
+    must touch, once) and the measured HBM copy bandwidth."""
+    import torch
+    from paper_2508_02681_gb300 import _lib, api
+    from synth import config_seed
+    peak, peak_kind = peaks()
+    names = ["line", "plane_inv", "ku", "plane_fwd"]
+    out = {"peak_gbs": peak, "peak_kind": peak_kind}
+    for k, (name, physics, N, radius, contrast) in enumerate(HBM_WORKLOADS):
+        w = hbm_workload(physics, N, radius, contrast, config_seed(6, k))
+        h = periodic_solver(w, stream)
+        c = 1 if physics == 1 else 3
+        L = w["loads"].shape[0]
+        opts = api.make_opts(tol=TOL, max_iter=5000, precond=_lib.PRECOND_UNO, precision=_lib.MIXED,
+                             replace_every=50, flexible=1)
+        api.unocg_solve_async(h.ctx, opts)
+        api.unocg_solve_wait(h.ctx, L)
+        ms = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            api.unocg_solve_async(h.ctx, opts)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        info = api.unocg_solve_wait(h.ctx, L)
+        k_ms = api.unocg_profile_iteration(h.ctx, opts, reps=10)
+        h.close()
+        n = N ** 3
+        nh = N * N * (N // 2 + 1)
+        ab = algorithmic_bytes(n, nh, c, L, 1, 1 if c == 1 else 6, 4, 2)
+        kern = {}
+        for i, nm in enumerate(names):
+            gbs = ab[nm] / (k_ms[i] * 1e-3) / 1e9
+            kern[nm] = {"ms": float(k_ms[i]), "algorithmic_bytes": int(ab[nm]), "gbs": float(gbs),
+                        "frac": float(gbs / peak)}
+        it_bytes = sum(ab.values())
+        it_ms = float(np.sum(k_ms))
+        solve_ms = float(np.mean(ms))
+        iters = int(info.c.max_iters)
+        out[name] = {
+            "grid": [N, N, N], "physics": "thermal" if physics == 1 else "elastic", "loads": L,
+            "contrast": contrast, "inclusion_radius": radius, "volume_fraction": round(float(w["vf"]), 4),
+            "mixed_uno_ms": solve_ms, "iterations": iters,
+            "true_rel_res": float(np.max(info.true_rel_res)), "status": int(info.status),
+            "kernels": kern,
+            "iteration_ms": it_ms, "iteration_algorithmic_bytes": int(it_bytes),
+            "iteration_gbs": it_bytes / (it_ms * 1e-3) / 1e9,
+            "iteration_frac": it_bytes / (it_ms * 1e-3) / 1e9 / peak,
+            "solve_gbs_per_iteration": it_bytes * iters / (solve_ms * 1e-3) / 1e9,
+        }
     return out
 
 
@@ -516,18 +603,16 @@ def main():
         line["batched_uneven"] = batched_uneven()
     if rank == 0 and world == 1 and not args.no_elastic:
         line["elastic"] = elastic(stream)
+    if rank == 0 and world == 1 and not args.no_hbm:
+        line["hbm_resident"] = hbm_resident(stream)
     if rank == 0 and world == 1 and not args.no_dirichlet:
         line["dirichlet"] = dirichlet(w, stream)
         line["mixed_bc"] = dirichlet(w, stream, bc=(0, 1, 0))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        from oracle import homogenize as hz
-        t0 = time.perf_counter()
-        r = hz.solve(w["phase"], w["props"], 1, w["loads"][:1], precond="uno", tol=TOL)
-        dt = time.perf_counter() - t0
-        line["cpu_baseline"] = {"value": dt * 3.0 * 1000.0, "unit": "ms", "cores": len(os.sched_getaffinity(0)),
-                                "kind": "oracle",
-                                "sample": "gradient load e1 only (1 of 3), full FP64 oracle UNO-CG solve, scaled x3",
-                                "iterations": int(r["iters"][0])}
+        ms, iters = oracle_solve_ms(w)
+        line["cpu_baseline"] = {"value": ms, "unit": "ms", "cores": len(os.sched_getaffinity(0)),
+                                "kind": "oracle", "sample": CPU_SAMPLE, "iterations": iters,
+                                "csr_matvec_threads": 1}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

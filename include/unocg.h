@@ -257,8 +257,10 @@ int unocg_apply_uno_dev(unocg_ctx* ctx, int instance, const double* r_dev, doubl
    Limit: c*N1*N2*(N3/2+1) <= 524288 (e.g. 64^3 elastic); larger grids return
    UNOCG_ERR_INVALID_ARG and launch nothing.  The UNO weights must already be prepared on the
    device (unocg_set_uno_weights after unocg_set_phase_properties), else UNOCG_ERR_STATE.
-   The first call on a device looks up the scratch address (cudaGetSymbolAddress); make that
-   first call before any stream capture.  No part of the scratch needs to start at zero.
+   The first call in a CUDA context of a device looks up the scratch address
+   (cudaGetSymbolAddress) and caches it under that context's id; a context created again
+   (e.g. after cudaDeviceReset) is looked up anew.  Make the first call of each context before
+   any stream capture.  No part of the scratch needs to start at zero.
    Every call on a device uses the same scratch: calls whose work overlaps in time (different
    streams, contexts or host threads without ordering between them) race and corrupt each
    other's results; order them on one stream or with events.                               */

@@ -33,6 +33,27 @@ def _stream(stream):
     return C.c_void_p(stream.cuda_stream)
 
 
+# values per field of each live periodic context (c * N1 * N2 * N3), for the checks of the
+# device-pointer entry points
+_FIELD_VALUES: dict[int, int] = {}
+
+
+def _device_field(ctx, t, name: str):
+    """Raise ValueError unless ``t`` is a contiguous float64 CUDA tensor of one field of ``ctx``
+    (c * N1 * N2 * N3 values): the library reads and writes exactly that many values."""
+    need = _FIELD_VALUES.get(ctx.value)
+    if not getattr(t, "is_cuda", False):
+        raise ValueError(f"{name}: a CUDA tensor is required")
+    import torch
+    if t.dtype != torch.float64:
+        raise ValueError(f"{name}: float64 required, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: a contiguous tensor is required")
+    if need is not None and t.numel() != need:
+        raise ValueError(f"{name}: {t.numel()} values, the context's field has {need}")
+    return C.c_void_p(t.data_ptr())
+
+
 def unocg_create(physics: int, batch: int, n1: int, n2: int, n3: int, L0: float = 1.0):
     lib = _lib.load()
     h = C.c_void_p()
@@ -42,10 +63,12 @@ def unocg_create(physics: int, batch: int, n1: int, n2: int, n3: int, L0: float 
         if h.value:
             lib.unocg_destroy(h)
         raise UnocgError(rc, msg)
+    _FIELD_VALUES[h.value] = (1 if physics == _lib.THERMAL else 3) * n1 * n2 * n3
     return h
 
 
 def unocg_destroy(ctx):
+    _FIELD_VALUES.pop(ctx.value, None)
     _lib.load().unocg_destroy(ctx)
 
 
@@ -161,7 +184,8 @@ def unocg_get_fluctuation(ctx, instance: int, load: int, n_values: int) -> np.nd
 
 
 def unocg_get_fluctuation_dev(ctx, instance: int, load: int, out_dev, stream=None):
-    _check(ctx, _lib.load().unocg_get_fluctuation_dev(ctx, instance, load, C.c_void_p(out_dev.data_ptr()), _stream(stream)))
+    out = _device_field(ctx, out_dev, "out_dev")
+    _check(ctx, _lib.load().unocg_get_fluctuation_dev(ctx, instance, load, out, _stream(stream)))
 
 
 def unocg_get_effective_tensor(ctx, batch: int, dim: int, n_loads: int) -> np.ndarray:
@@ -195,22 +219,26 @@ def unocg_batch_solve(ctxs, opts: SolveOpts, n_results=None):
 
 
 def unocg_apply_K_dev(ctx, instance: int, d_dev, p_dev, stream=None):
-    _check(ctx, _lib.load().unocg_apply_K_dev(ctx, instance, C.c_void_p(d_dev.data_ptr()),
-                                              C.c_void_p(p_dev.data_ptr()), _stream(stream)))
+    d = _device_field(ctx, d_dev, "d_dev")
+    p = _device_field(ctx, p_dev, "p_dev")
+    _check(ctx, _lib.load().unocg_apply_K_dev(ctx, instance, d, p, _stream(stream)))
 
 
 def unocg_apply_uno_dev(ctx, instance: int, r_dev, s_dev, stream=None):
-    _check(ctx, _lib.load().unocg_apply_uno_dev(ctx, instance, C.c_void_p(r_dev.data_ptr()),
-                                                C.c_void_p(s_dev.data_ptr()), _stream(stream)))
+    r = _device_field(ctx, r_dev, "r_dev")
+    s = _device_field(ctx, s_dev, "s_dev")
+    _check(ctx, _lib.load().unocg_apply_uno_dev(ctx, instance, r, s, _stream(stream)))
 
 
 def unocg_apply_uno_dev_noalloc(ctx, instance: int, r_dev, s_dev, stream=None):
-    _check(ctx, _lib.load().unocg_apply_uno_dev_noalloc(ctx, instance, C.c_void_p(r_dev.data_ptr()),
-                                                        C.c_void_p(s_dev.data_ptr()), _stream(stream)))
+    r = _device_field(ctx, r_dev, "r_dev")
+    s = _device_field(ctx, s_dev, "s_dev")
+    _check(ctx, _lib.load().unocg_apply_uno_dev_noalloc(ctx, instance, r, s, _stream(stream)))
 
 
 def unocg_rhs_dev(ctx, instance: int, load: int, f_dev, stream=None):
-    _check(ctx, _lib.load().unocg_rhs_dev(ctx, instance, load, C.c_void_p(f_dev.data_ptr()), _stream(stream)))
+    f = _device_field(ctx, f_dev, "f_dev")
+    _check(ctx, _lib.load().unocg_rhs_dev(ctx, instance, load, f, _stream(stream)))
 
 
 def unocg_profile_iteration(ctx, opts: SolveOpts, reps: int = 10) -> np.ndarray:

@@ -19,6 +19,7 @@
 
 #include <nvtx3/nvToolsExt.h>
 
+#include "driver_api.h"
 #include "kargs.h"
 #include "persist.h"
 #include "setup.h"
@@ -1332,24 +1333,39 @@ static __device__ __align__(256) double2 g_noalloc_scratch[2 * kNoAllocSpectrum]
 
 namespace {
 constexpr int kNoAllocMaxDevices = 64;
+struct NoAllocAddr {
+  unsigned long long ctx_id;
+  double2* addr;
+};
 std::mutex g_noalloc_mu;
-double2* g_noalloc_addr[kNoAllocMaxDevices] = {};
+NoAllocAddr g_noalloc_addr[kNoAllocMaxDevices] = {};
 
-// Address of the scratch on the current device, looked up once per device (with that device
-// current) and cached.
+// Address of the scratch in the current context of the current device, looked up once per
+// context (with that device current) and cached under the context's id: a context destroyed
+// and created again (cudaDeviceReset) loads the module again, and the address is looked up anew.
 cudaError_t noalloc_scratch(double2** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+  // the context current on this thread; none yet if this thread has made no runtime call that
+  // needs one (the symbol lookup below then binds the device's primary context)
+  unsigned long long id = 0;
+  const bool have_id = current_context_id(&id) == cudaSuccess;
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
+  NoAllocAddr& c = g_noalloc_addr[dev];
+  if (!have_id || !c.addr || c.ctx_id != id) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    g_noalloc_addr[dev] = static_cast<double2*>(p);
+    if (!have_id) {
+      e = current_context_id(&id);
+      if (e != cudaSuccess) return e;
+    }
+    c.addr = static_cast<double2*>(p);
+    c.ctx_id = id;
   }
-  *out = g_noalloc_addr[dev];
+  *out = c.addr;
   return cudaSuccess;
 }
 }  // namespace

@@ -58,3 +58,18 @@ def test_create_rejects_bad_grids(libpath):
     assert lib.unocg_create(ctypes.byref(h), 1, 1, 8, 8, 9, 1.0) == _lib.ERR_INVALID_ARG
     assert lib.unocg_create(ctypes.byref(h), 2, 1, 8, 8, 8, 1.0) == _lib.ERR_INVALID_ARG
     assert lib.unocg_create(ctypes.byref(h), 1, 0, 8, 8, 8, 1.0) == _lib.ERR_INVALID_ARG
+
+
+def test_device_pointer_bindings_check_their_tensors():
+    """The device-pointer entry points refuse tensors the library would read or write out of
+    bounds (host memory, another dtype, a strided view, another size), before any library call."""
+    import torch
+    from paper_2508_02681_gb300 import api
+    ctx = ctypes.c_void_p(12345)
+    api._FIELD_VALUES[ctx.value] = 8
+    try:
+        for bad in (torch.zeros(8, dtype=torch.float64),):  # host tensor
+            with pytest.raises(ValueError, match="CUDA"):
+                api._device_field(ctx, bad, "r_dev")
+    finally:
+        api._FIELD_VALUES.pop(ctx.value, None)

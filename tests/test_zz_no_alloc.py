@@ -62,3 +62,33 @@ def test_noalloc_needs_prepared_weights():
         api.unocg_apply_uno_dev_noalloc(ctx, 0, r, torch.zeros_like(r))
     assert ei.value.code == _lib.ERR_STATE
     api.unocg_destroy(ctx)
+
+
+def test_noalloc_back_to_back_on_a_side_stream():
+    """Two allocation-free applies with different inputs, enqueued back to back on a side stream
+    with no synchronisation between them: the second reuses the scratch after the first in
+    stream order, and both results match the allocating apply."""
+    import torch
+    from paper_2508_02681_gb300 import _lib, api
+    c, shape = 3, (16, 16, 24)
+    phase = random_phase(shape, 2, seed=8)
+    ctx = api.unocg_create(3, 1, *shape, 1.0)
+    api.unocg_set_microstructure(ctx, phase, 2)
+    api.unocg_set_phase_properties(ctx, np.array([[1.0, 0.3], [20.0, 0.2]]))
+    api.unocg_set_uno_weights(ctx, _lib.W_REFERENCE_MEDIUM)
+    rs = [torch.tensor(random_field((c,) + shape, seed=70 + k), device="cuda") for k in range(2)]
+    outs = [torch.full_like(r, float("nan")) for r in rs]
+    refs = [torch.empty_like(r) for r in rs]
+    for r, ref in zip(rs, refs):
+        api.unocg_apply_uno_dev(ctx, 0, r, ref)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())  # inputs written before the side stream reads them
+    for r, out in zip(rs, outs):
+        api.unocg_apply_uno_dev_noalloc(ctx, 0, r, out, stream=side)
+    side.synchronize()
+    torch.cuda.synchronize()
+    for out, ref in zip(outs, refs):
+        a, b = out.cpu().numpy(), ref.cpu().numpy()
+        assert np.all(np.isfinite(a))
+        assert np.max(np.abs(a - b)) <= 1e-13 * np.max(np.abs(b))
+    api.unocg_destroy(ctx)
