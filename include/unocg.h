@@ -132,8 +132,25 @@ int unocg_set_tuning(unocg_ctx* ctx, int radix_order, int path);
    fit) and keeps the fastest setting.  Needs the inputs and weights set.                    */
 int unocg_autotune(unocg_ctx* ctx, const unocg_solve_opts* opts, int reps, double* times);
 
+/* Tile of the FP32 thermal K d (the operator apply of Algorithm 2 in mixed precision).
+   tile = -1: automatic (default); 0: the register column march (below 10^6 nodes per field) or
+   the element kernel; k = 1..6: the TMA-staged kernel, whose block holds TY node rows over the
+   whole N3 extent (N3 / 4 threads per row) and marches over P node planes, with
+   (threads, P) = (256, 12), (512, 12), (256, 6), (512, 24), (128, 6), (256, 24) and
+   TY = threads / (N3 / 4).  The TMA kernel needs N3 in {32, 64, 128, 256} and TY dividing N2;
+   unavailable shapes return UNOCG_ERR_INVALID_ARG.  Elastic problems ignore the setting.
+   unocg_get_ku_tile returns the tile the next solve uses (0 or 1..6).                       */
+int unocg_set_ku_tile(unocg_ctx* ctx, int tile);
+int unocg_get_ku_tile(unocg_ctx* ctx, int* tile);
+/* Stencil autotuner: times `reps` FP32 K d launches over all B x L fields of the context for
+   the earlier kernels (times[0]) and each TMA tile shape (times[1..6], NaN where unavailable),
+   keeps the fastest (unocg_set_ku_tile) and returns its index in *best (may be NULL).  Needs
+   the microstructure, properties and loads set.  UNOCG_ERR_DEVICE_TIMEOUT if a tile copy's
+   bounded wait expired (the setting is then left unchanged).                               */
+int unocg_autotune_ku(unocg_ctx* ctx, int reps, double* times, int* best);
+
 /* Upper bound of any device-side wait of this context (the grid barrier of the persistent
-   loop), in seconds (default 1).  A wait that expires makes every block of the launch return
+   loop, the tile copies of the TMA-staged K d), in seconds (default 1).  A wait that expires makes every block of the launch return
    and the solve report UNOCG_ERR_DEVICE_TIMEOUT; the context stays usable.                 */
 int unocg_set_wait_limit(unocg_ctx* ctx, double seconds);
 
@@ -247,6 +264,10 @@ int unocg_uno_features_dev(unocg_uno* op, int batch, const float* f_dev, const f
    properties (instance 0 .. B-1 via `instance`).  Fields are double [c][N1][N2][N3].        */
 /* p = K d (Sec. 4.1, matrix-free), in FP64.                                                 */
 int unocg_apply_K_dev(unocg_ctx* ctx, int instance, const double* d_dev, double* p_dev, void* stream);
+/* p = K d (Sec. 4.1, matrix-free) in FP32 with the kernel of the mixed-precision loop: for
+   thermal problems the TMA-staged tile kernel of unocg_set_ku_tile where the grid allows it.
+   Fields are float [c][N1][N2][N3], caller-owned device memory, enqueued on `stream`.         */
+int unocg_apply_K32_dev(unocg_ctx* ctx, int instance, const float* d_dev, float* p_dev, void* stream);
 /* s = P r with the context's current UNO weights (Algorithm 2, transform / block multiply /
    inverse transform), in FP64.                                                             */
 int unocg_apply_uno_dev(unocg_ctx* ctx, int instance, const double* r_dev, double* s_dev, void* stream);

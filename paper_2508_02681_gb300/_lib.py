@@ -89,6 +89,10 @@ SIGNATURES = {
     "unocg_uno_apply_dev": (_i, [_vp, _i, _vp, _vp, _vp]),
     "unocg_uno_backward_dev": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp]),
     "unocg_apply_K_dev": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "unocg_apply_K32_dev": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "unocg_set_ku_tile": (_i, [_vp, _i]),
+    "unocg_get_ku_tile": (_i, [_vp, _vp]),
+    "unocg_autotune_ku": (_i, [_vp, _i, _vp, _vp]),
     "unocg_apply_uno_dev": (_i, [_vp, _i, _vp, _vp, _vp]),
     "unocg_apply_uno_dev_noalloc": (_i, [_vp, _i, _vp, _vp, _vp]),
     "unocg_rhs_dev": (_i, [_vp, _i, _i, _vp, _vp]),

@@ -224,6 +224,42 @@ def unocg_apply_K_dev(ctx, instance: int, d_dev, p_dev, stream=None):
     _check(ctx, _lib.load().unocg_apply_K_dev(ctx, instance, d, p, _stream(stream)))
 
 
+def _device_field32(ctx, t, name: str):
+    """As ``_device_field`` for float32 fields."""
+    import torch
+    if not getattr(t, "is_cuda", False) or t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError(f"{name}: a contiguous float32 CUDA tensor is required")
+    need = _FIELD_VALUES.get(ctx.value)
+    if need is not None and t.numel() != need:
+        raise ValueError(f"{name}: {t.numel()} values, the context's field has {need}")
+    return C.c_void_p(t.data_ptr())
+
+
+def unocg_apply_K32_dev(ctx, instance: int, d_dev, p_dev, stream=None):
+    d = _device_field32(ctx, d_dev, "d_dev")
+    p = _device_field32(ctx, p_dev, "p_dev")
+    _check(ctx, _lib.load().unocg_apply_K32_dev(ctx, instance, d, p, _stream(stream)))
+
+
+def unocg_set_ku_tile(ctx, tile: int):
+    _check(ctx, _lib.load().unocg_set_ku_tile(ctx, tile))
+
+
+def unocg_get_ku_tile(ctx) -> int:
+    out = C.c_int(0)
+    _check(ctx, _lib.load().unocg_get_ku_tile(ctx, C.byref(out)))
+    return out.value
+
+
+def unocg_autotune_ku(ctx, reps: int = 20):
+    """Times of the K d candidates (index 0: the earlier kernels, 1..6: TMA tile shapes; NaN where
+    unavailable) and the index kept."""
+    times = np.zeros(7)
+    best = C.c_int(0)
+    _check(ctx, _lib.load().unocg_autotune_ku(ctx, reps, _ptr(times), C.byref(best)))
+    return times, best.value
+
+
 def unocg_apply_uno_dev(ctx, instance: int, r_dev, s_dev, stream=None):
     r = _device_field(ctx, r_dev, "r_dev")
     s = _device_field(ctx, s_dev, "s_dev")

@@ -144,6 +144,9 @@ struct unocg_ctx {
   // tuning (unocg_set_tuning / unocg_autotune): radix order of the Stockham plans and the loop
   // driver taken by use_graph = 3
   int radix_order = 0, tuned_path = 1;
+  // thermal FP32 K d: -1 automatic, 0 the register-march / element kernels, k >= 1 the TMA-staged
+  // kernel with tile shape kKuTmaShapes[k - 1] (unocg_set_ku_tile / unocg_autotune_ku)
+  int ku_tile = -1;
 };
 
 struct unocg_uno {
@@ -539,6 +542,9 @@ static int ensure_workspace(unocg_ctx* ctx, int precision, int precond) {
   need = std::max(need, (size_t)BL * node_blocks_x(ctx->g));
   need = std::max(need, (size_t)BL * ku_blocks_x(ctx->g, ctx->c));
   need = std::max(need, (size_t)BL * ku_tasks_x(ctx->g, ctx->c));
+  for (int k = 0; k < kKuTmaNumShapes; ++k)
+    if (ku_tma_supported(ctx->g, ctx->c, kKuTmaShapes[k]))
+      need = std::max(need, (size_t)BL * ku_tma_blocks_x(ctx->g, kKuTmaShapes[k]));
   need = std::max(need, (size_t)BL * jac_blocks_x((long long)ctx->c * n, BL));
   need = std::max(need, (size_t)BL * ctx->c * 1184);
   need = std::max(need, (size_t)ctx->B * node_blocks_x(ctx->g) * 48);
@@ -653,6 +659,7 @@ static cudaError_t enq_pre(unocg_ctx* ctx, cudaStream_t s, const Plan& pl, const
   cudaError_t e = cudaMemsetAsync(ctx->sc, 0, BL * sizeof(CgScal), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->tickets, 0, kMaxTickets * sizeof(unsigned int), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->flags + 2, 0, 2 * sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->flags + 6, 0, sizeof(int), s);  // wait-timeout flag
   if (e != cudaSuccess) return e;
   InitArgs<T> ia{};
   ia.g = ctx->g; ia.c = ctx->c; ia.L = ctx->L; ia.phase = ctx->phase; ia.mat = material(ctx);
@@ -707,14 +714,43 @@ static cudaError_t enq_precond(unocg_ctx* ctx, cudaStream_t s, const Plan& pl, c
   return launch_jac<T>(a, 1, s);
 }
 
+// Tile shape of the thermal FP32 K d (1-based index into kKuTmaShapes, 0: the earlier kernels).
+// Automatic choice: the supported shape with the most work per block (threads x planes) that
+// still gives two blocks per SM over all (instance, load) fields, else the one with most blocks.
+static int ku_tma_choice(const unocg_ctx* ctx) {
+  if (ctx->c != 1 || ctx->ku_tile == 0) return 0;
+  if (ctx->ku_tile > 0)
+    return ku_tma_supported(ctx->g, 1, kKuTmaShapes[ctx->ku_tile - 1]) ? ctx->ku_tile : 0;
+  const long long BL = (long long)ctx->B * std::max(ctx->L, 1);
+  int best = 0, most = 0;
+  long long best_work = -1, most_blocks = -1;
+  for (int k = 0; k < kKuTmaNumShapes; ++k) {
+    const KuTmaShape sh = kKuTmaShapes[k];
+    if (!ku_tma_supported(ctx->g, 1, sh)) continue;
+    const long long blocks = BL * ku_tma_blocks_x(ctx->g, sh);
+    const long long work = (long long)sh.threads * sh.planes;
+    if (blocks >= 2LL * std::max(ctx->sm_count, 1) && work > best_work) { best = k + 1; best_work = work; }
+    if (blocks > most_blocks) { most = k + 1; most_blocks = blocks; }
+  }
+  return best ? best : most;
+}
+
 template <typename T>
-static cudaError_t enq_ku(unocg_ctx* ctx, cudaStream_t s) {
+static StencilArgs<T> ku_args(unocg_ctx* ctx) {
   auto& f = Sel<T>::f(ctx);
   StencilArgs<T> ka{};
   ka.g = ctx->g; ka.c = ctx->c; ka.BL = ctx->B * ctx->L; ka.L = ctx->L; ka.phase = ctx->phase;
   ka.mat = material(ctx);
   ka.d = f.d; ka.p = f.p; ka.sc = ctx->sc; ka.red = Reduce{ctx->part, ctx->tickets + T_KU}; ka.standalone = 0;
-  return launch_ku<T>(ka, s);
+  ka.ku_tma = sizeof(T) == 4 ? ku_tma_choice(ctx) : 0;
+  ka.err = ctx->flags + 6;
+  ka.spin_limit = ctx->spin_limit;
+  return ka;
+}
+
+template <typename T>
+static cudaError_t enq_ku(unocg_ctx* ctx, cudaStream_t s) {
+  return launch_ku<T>(ku_args<T>(ctx), s);
 }
 
 template <typename T>
@@ -1278,6 +1314,94 @@ extern "C" int unocg_apply_K_dev(unocg_ctx* ctx, int instance, const double* d_d
   CK(order_after(&ctx->join_ev, ctx->stream, s));
   CK(launch_ku<double>(a, s));
   CK(order_after(&ctx->join_ev, s, ctx->stream));
+  return UNOCG_OK;
+}
+
+extern "C" int unocg_apply_K32_dev(unocg_ctx* ctx, int instance, const float* d_dev, float* p_dev, void* stream) {
+  NvtxRange nvtx_("unocg_apply_K32_dev");
+  if (!ctx || !d_dev || !p_dev) return fail(ctx, UNOCG_ERR_INVALID_ARG, "null argument");
+  if (!ctx->have_phase || !ctx->have_props) return fail(ctx, UNOCG_ERR_STATE, "microstructure/properties missing");
+  if (instance < 0 || instance >= ctx->B) return fail(ctx, UNOCG_ERR_INVALID_ARG, "instance out of range");
+  StencilArgs<float> a{};
+  a.g = ctx->g; a.c = ctx->c; a.BL = 1; a.L = 1;
+  a.phase = ctx->phase + (long long)instance * ctx->g.n;
+  a.mat = material(ctx);
+  a.mat.m64 += (long long)instance * ctx->n_phases * 2;
+  a.mat.m32 += (long long)instance * ctx->n_phases * 2;
+  a.d = d_dev; a.p = p_dev; a.sc = nullptr; a.standalone = 1;
+  a.ku_tma = ku_tma_choice(ctx); a.err = ctx->flags + 6; a.spin_limit = ctx->spin_limit;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(order_after(&ctx->join_ev, ctx->stream, s));
+  CK(launch_ku<float>(a, s));
+  CK(order_after(&ctx->join_ev, s, ctx->stream));
+  return UNOCG_OK;
+}
+
+extern "C" int unocg_set_ku_tile(unocg_ctx* ctx, int tile) {
+  if (!ctx || tile < -1 || tile > kKuTmaNumShapes) return fail(ctx, UNOCG_ERR_INVALID_ARG, "invalid K d tile");
+  if (tile > 0 && !ku_tma_supported(ctx->g, ctx->c, kKuTmaShapes[tile - 1]))
+    return fail(ctx, UNOCG_ERR_INVALID_ARG, "K d tile shape not available for this grid / physics");
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->ku_tile = tile;
+  free_graph(ctx);  // the captured launches hold the old shape
+  return UNOCG_OK;
+}
+
+extern "C" int unocg_get_ku_tile(unocg_ctx* ctx, int* tile) {
+  if (!ctx || !tile) return fail(ctx, UNOCG_ERR_INVALID_ARG, "null argument");
+  *tile = ku_tma_choice(ctx);
+  return UNOCG_OK;
+}
+
+// Times `reps` launches of the FP32 K d over all B x L fields of the context (standalone mode,
+// CUDA events on the context stream, after one warm-up launch) for the earlier kernels
+// (times[0]) and every TMA tile shape (times[k], NaN where the grid does not allow it), keeps
+// the fastest and returns its index in *best.
+extern "C" int unocg_autotune_ku(unocg_ctx* ctx, int reps, double* times, int* best) {
+  if (!ctx || reps < 1 || !times) return fail(ctx, UNOCG_ERR_INVALID_ARG, "invalid autotune arguments");
+  if (!ctx->have_phase || !ctx->have_props || ctx->L < 1)
+    return fail(ctx, UNOCG_ERR_STATE, "set microstructure, phase properties and loads first");
+  int rc = ensure_workspace(ctx, UNOCG_MIXED, UNOCG_PRECOND_UNO);
+  if (rc) return rc;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const size_t fld = (size_t)ctx->B * ctx->L * ctx->c * ctx->g.n;
+  // a smooth, nonzero direction (its values do not change the time)
+  CK(cudaMemsetAsync(ctx->f32.d, 0x3c, fld * sizeof(float), ctx->stream));
+  double bt = 1e300;
+  int bk = 0;
+  const int saved = ctx->ku_tile;
+  for (int k = 0; k <= kKuTmaNumShapes && rc == UNOCG_OK; ++k) {
+    times[k] = std::nan("");
+    if (k > 0 && !ku_tma_supported(ctx->g, ctx->c, kKuTmaShapes[k - 1])) continue;
+    ctx->ku_tile = k;
+    StencilArgs<float> a = ku_args<float>(ctx);
+    a.standalone = 1;
+    float ms = 0.f;
+    cudaError_t e = launch_ku<float>(a, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_ku<float>(a, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) { rc = fail(ctx, UNOCG_ERR_CUDA, std::string("K d autotune: ") + cudaGetErrorString(e)); break; }
+    times[k] = ms / reps;
+    if (times[k] < bt) { bt = times[k]; bk = k; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) { ctx->ku_tile = saved; return rc; }
+  int flag = 0;
+  CK(cudaMemcpy(&flag, ctx->flags + 6, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag) {
+    ctx->ku_tile = saved;
+    CK(cudaMemset(ctx->flags + 6, 0, sizeof(int)));
+    return fail(ctx, UNOCG_ERR_DEVICE_TIMEOUT, "K d autotune: a wait for a tile copy expired");
+  }
+  ctx->ku_tile = bk;
+  free_graph(ctx);
+  if (best) *best = bk;
   return UNOCG_OK;
 }
 

@@ -557,6 +557,11 @@ template <typename T, int CC> static cudaError_t launch_ku_el(const StencilArgs<
 }
 
 template <typename T> cudaError_t launch_ku(const StencilArgs<T>& a, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (a.c == 1 && a.ku_tma > 0 && a.ku_tma <= kKuTmaNumShapes &&
+        ku_tma_supported(a.g, 1, kKuTmaShapes[a.ku_tma - 1]))
+      return launch_ku_tma(a, kKuTmaShapes[a.ku_tma - 1], a.err, a.spin_limit, s);
+  }
   if (a.c != 1) return launch_ku_el<T, 3>(a, s);
   if (thermal_element(a.g)) return launch_ku_el<T, 1>(a, s);
   return launch_pdl(k_ku<T, 1>, ku_task_grid(a.g, 1, a.BL), dim3(256), 0, s, a);

@@ -103,7 +103,21 @@ template <typename T> struct StencilArgs {
   CgScal* sc;
   Reduce red;
   int standalone;       // no CG bookkeeping (operator apply)
+  int ku_tma;           // FP32 thermal: 1 + index into kKuTmaShapes of the TMA-staged kernel, 0 none
+  int* err;             // bounded waits: flag raised on expiry (null: none)
+  long long spin_limit; // SM clock cycles a wait may take
 };
+
+// Tile shape of the TMA-staged thermal K d (k_ku_tma.cu): threads per block (N3 / 4 per node
+// row of the tile) and node planes per block.
+struct KuTmaShape {
+  int threads, planes;
+};
+constexpr int kKuTmaNumShapes = 6;
+extern const KuTmaShape kKuTmaShapes[kKuTmaNumShapes];
+bool ku_tma_supported(const Grid& g, int c, KuTmaShape s);
+int ku_tma_blocks_x(const Grid& g, KuTmaShape s);
+cudaError_t launch_ku_tma(const StencilArgs<float>& a, KuTmaShape s, int* err, long long spin_limit, cudaStream_t st);
 
 template <typename T> struct InitArgs {
   Grid g;

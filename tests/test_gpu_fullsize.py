@@ -3,15 +3,18 @@
 solved to a relative residual of 1e-6 by the GPU and by the FP64 oracle (assembled K, DFT by
 definition, Algorithm 2) on the same seeded inputs.
 
-Bars: FP64 GPU fields within 1e-9 (relative to the largest entry) of the oracle fields at the
-oracle's stopping iteration, FP64 effective tensors within 1e-10 of the oracle's; mixed precision
-(FP32 fields and transforms, BF16 weights, FP64 reductions, residual replacement, flexible CG)
-effective tensors within 1e-6 of the oracle's, with a true FP64 residual of at most 1e-6.
+Bars: FP64 GPU fields within 1e-9 (relative to the largest entry) of the oracle fields, both
+converged to a relative residual of 1e-10, where each lies within about 1e-10 of the discrete
+solution; at the workload tolerance of 1e-6 the FP64 iteration counts agree within one and the
+FP64 effective tensors lie within 1e-10 of the oracle's; mixed precision (FP32 fields and
+transforms, BF16 weights, FP64 reductions, residual replacement, flexible CG) gives effective
+tensors within 1e-6 of the oracle's, with a true FP64 residual of at most 1e-6.
 
-Where the GPU's FP64 loop stops one iteration away from the oracle (the residual is compared with
-the threshold in a different summation order), the oracle is re-run on that load for exactly the
-GPU's iteration count, so both fields are the same CG iterate (the fixed-iteration comparison of
-the oracle's stopping rule)."""
+Fields are not compared at a fixed CG iteration of the 1e-6 solve: the iterates of CG depend on
+rounding far more than the converged solution does.  On this workload a relative perturbation of
+1e-16 of the preconditioner output (the oracle run twice) moves the 71st iterate by 3e-10
+relative, and one more iteration moves it by 1.3e-7, so two correct FP64 implementations agree
+there only to about 1e-9 - 1e-8."""
 import numpy as np
 import pytest
 
@@ -22,10 +25,11 @@ from tests.gpu_util import rel
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-6
+TIGHT = 1e-10
 
 
-def _oracle(w):
-    ref = hz.solve(w["phase"], w["props"], w["physics"], w["loads"], precond="uno", tol=TOL)
+def _oracle(w, tol):
+    ref = hz.solve(w["phase"], w["props"], w["physics"], w["loads"], precond="uno", tol=tol)
     ref["C"] = hz.effective_tensor(w["phase"], w["props"], w["physics"], ref["u"], w["loads"])
     return ref
 
@@ -33,16 +37,16 @@ def _oracle(w):
 @pytest.fixture(scope="module")
 def thermal64():
     w = workload(2)
-    return w, _oracle(w)
+    return w, _oracle(w, TOL), _oracle(w, TIGHT)
 
 
 @pytest.fixture(scope="module")
 def elastic64():
     w = workload(3)
-    return w, _oracle(w)
+    return w, _oracle(w, TOL), _oracle(w, TIGHT)
 
 
-def _gpu(w, precision, use_graph=3):
+def _gpu(w, precision, use_graph=3, tol=TOL):
     from paper_2508_02681_gb300 import _lib
     from paper_2508_02681_gb300.solver import Homogenization
     h = Homogenization(w["physics"], w["phase"].shape)
@@ -50,27 +54,28 @@ def _gpu(w, precision, use_graph=3):
     h.set_phase_properties(w["props"])
     h.set_macro_load(w["loads"])
     h.set_uno_weights(_lib.W_REFERENCE_MEDIUM)
-    info = h.solve(tol=TOL, max_iter=3000, precond=_lib.PRECOND_UNO, precision=precision, use_graph=use_graph)
+    info = h.solve(tol=tol, max_iter=3000, precond=_lib.PRECOND_UNO, precision=precision, use_graph=use_graph)
     return h, info
 
 
-def _fp64_parity(w, ref, use_graph):
+def _fp64_parity(w, ref, ref_tight, use_graph):
     from paper_2508_02681_gb300 import _lib
+    # the workload tolerance: iteration counts and the effective tensor
     h, info = _gpu(w, _lib.FP64, use_graph)
     assert info.status == _lib.OK
     assert np.all(info.true_rel_res <= TOL)
     for l in range(len(w["loads"])):
-        it = int(info.iters[l])
-        assert abs(it - ref["iters"][l]) <= 1, (l, it, ref["iters"][l])
-        u_ref = ref["u"][l]
-        if it != ref["iters"][l]:
-            u_ref = hz.solve(w["phase"], w["props"], w["physics"], w["loads"][l:l + 1], precond="uno",
-                             tol=0.0, max_iter=it)["u"][0]
-        assert rel(h.fluctuation(0, l), u_ref) < 1e-9, l
+        assert abs(int(info.iters[l]) - ref["iters"][l]) <= 1, (l, int(info.iters[l]), ref["iters"][l])
     C = h.effective_tensor()[0]
     h.close()
     assert rel(C, ref["C"]) < 1e-10
-    return C
+    # converged fields
+    h, info = _gpu(w, _lib.FP64, use_graph, TIGHT)
+    assert info.status == _lib.OK
+    for l in range(len(w["loads"])):
+        assert rel(h.fluctuation(0, l), ref_tight["u"][l]) < 1e-9, l
+    assert rel(h.effective_tensor()[0], ref_tight["C"]) < 1e-10
+    h.close()
 
 
 def _mixed_parity(w, ref, use_graph=3):
@@ -86,21 +91,21 @@ def _mixed_parity(w, ref, use_graph=3):
 
 @pytest.mark.parametrize("use_graph", [1, 0])
 def test_thermal64_fp64_matches_oracle(thermal64, use_graph):
-    w, ref = thermal64
-    _fp64_parity(w, ref, use_graph)
+    w, ref, ref_tight = thermal64
+    _fp64_parity(w, ref, ref_tight, use_graph)
 
 
 @pytest.mark.parametrize("use_graph", [1, 0])
 def test_thermal64_mixed_matches_oracle(thermal64, use_graph):
-    w, ref = thermal64
+    w, ref, _ = thermal64
     _mixed_parity(w, ref, use_graph)
 
 
 def test_elastic64_fp64_matches_oracle(elastic64):
-    w, ref = elastic64
-    _fp64_parity(w, ref, 1)
+    w, ref, ref_tight = elastic64
+    _fp64_parity(w, ref, ref_tight, 1)
 
 
 def test_elastic64_mixed_matches_oracle(elastic64):
-    w, ref = elastic64
+    w, ref, _ = elastic64
     _mixed_parity(w, ref, 1)
