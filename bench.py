@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--no-elastic", action="store_true", help="skip the elastic measurement")
     ap.add_argument("--no-dirichlet", action="store_true", help="skip the Dirichlet-BC measurement")
     ap.add_argument("--no-hbm", action="store_true", help="skip the HBM-resident (192^3, 256^3) measurement")
+    ap.add_argument("--grid", type=int, default=0,
+                    help="with --profile-only: a thermal N^3 workload (inclusions of radius 6 N / 64, contrast 100) "
+                         "in place of the 64^3 one")
     ap.add_argument("--no-graph", action="store_true",
                     help="profile-only: host-driven loop (kernels inside conditional graph bodies are not visible to ncu)")
     return ap.parse_args()
@@ -508,6 +511,11 @@ def main():
             h.close()
             we = workload(3)
             L = we["loads"].shape[0]
+            hp = periodic_solver(we, stream)
+        elif args.grid:
+            h.close()
+            from synth import config_seed
+            we = hbm_workload(1, args.grid, 6.0 * args.grid / 64.0, 100.0, config_seed(6, 0))
             hp = periodic_solver(we, stream)
         for _ in range(2):
             api.unocg_solve_async(hp.ctx, opts)

@@ -11,8 +11,7 @@ import pytest
 from oracle import fem
 from synth import random_field, random_phase
 
-# the tile shapes of kKuTmaShapes (threads, planes per block) and the kernel's constants
-SHAPES = [(256, 12), (512, 12), (256, 6), (512, 24), (128, 6), (256, 24)]
+# the kernel's constants: nodes per thread along i3, node-plane and phase-plane ring depths
 NV, DS, PS = 4, 4, 3
 
 
@@ -99,7 +98,6 @@ def emulate(shape, threads, planes, d, phase, kappa):
         i2_0 = tile2 * ty_rows
         z0 = zc * planes
         nsteps = min(planes, n1 - z0)
-        D = {0: None, 1: None, 2: None}
         bufs = [node_plane(z0 - 1, i2_0), node_plane(z0, i2_0)]
         assert bufs[0].shape == (ty_rows + 2, n3)
         D_m = [row_vals(bufs[0], r) for r in (rm, rc, rp)]
