@@ -240,13 +240,16 @@ def reference_Q(physics: int, props, shape, bc) -> np.ndarray:
 
 
 def solve(phase, props, physics: int, bc, loads, precond: str = "uno", tol: float = 1e-8,
-          max_iter: int = 100000):
+          max_iter: int = 100000, Q=None):
+    """PCG (Algorithm 1) for every load; ``precond="uno"`` with the blocks ``Q [M1, M2, c, c]``
+    (default: the reference medium, ``reference_Q``)."""
     shape = phase.shape
     c = n_comp(physics)
     K = assemble_K(phase, props, physics, bc)
     fs_ = free_shape(shape, bc)
     if precond == "uno":
-        Q = reference_Q(physics, props, shape, bc)
+        if Q is None:
+            Q = reference_Q(physics, props, shape, bc)
         to_soa = lambda v: v.reshape(fs_ + (c,)).transpose(2, 0, 1)
         from_soa = lambda a: np.ascontiguousarray(a.transpose(1, 2, 0)).ravel()
         P = lambda r: from_soa(uno_apply(Q, to_soa(r), shape, bc))

@@ -383,3 +383,247 @@ def second_order_modes(a, b, M: int, w0, iters: int = 100, tol: float = 1e-12):
         if abs(hist[-2] - hist[-1]) <= tol * max(1.0, abs(hist[-1])):
             break
     return w.reshape(-1, 1), hist
+
+
+# ---------------------------------------------------------------------------------------------
+# 2D problems (Sec. 6 with d = 2), c = 1 (thermal) and c = 2 (plane strain, Eq. (local-param-2)).
+# The library solves a 2D cell as the x1-invariant 3D problem on `layers` voxels along a
+# periodic axis 1 (solver.Homogenization2D: 2D axes 1, 2 are 3D axes 2, 3; 2D components x, y
+# are 3D components 2, 3).  Every field of such a solve has Fourier content only at k1 = 0,
+# where the unitary 3D transform is sqrt(layers) times the 2D one; the 2D UNO is therefore the
+# 3D operator whose blocks at (0, k1', k2') are the 2D blocks (embedded, with the extrusion
+# component decoupled) and whose other blocks are the embedded bypass.
+
+_L2 = ((0, 0), (1, 1), (1, 0))   # positions of w1, w2, w3 in L (Eq. (local-param-2))
+_ORDER2 = ((0, 0), (1, 1), (0, 1))  # entries v1 = Q_xx, v2 = Q_yy, v3 = Q_xy (Sec. 5.4)
+
+
+def mode_set_2d(M: int):
+    """Learned modes of the periodic row of Table (fnocg-mode-selection-2d), d = 2:
+    [-M, M] x [0, M] minus {0}, ordered k1 (from -M), then k2."""
+    return [(k1, k2) for k1 in range(-M, M + 1) for k2 in range(0, M + 1) if (k1, k2) != (0, 0)]
+
+
+def psi2(w, c: int) -> np.ndarray:
+    """Local parametrization for c = 1 (w^2) and c = 2 (L L^T, L = [[w1, 0], [w3, w2]])."""
+    w = np.asarray(w, dtype=np.float64)
+    if c == 1:
+        return (w[..., 0] ** 2)[..., None, None]
+    L = np.zeros(w.shape[:-1] + (2, 2))
+    for i, (r, q) in enumerate(_L2):
+        L[..., r, q] = w[..., i]
+    return L @ np.swapaxes(L, -1, -2)
+
+
+def _blocks_2d_full(w, M: int, shape2, c: int) -> np.ndarray:
+    """2D blocks [N1, N2, c, c] of the bypass-plus-modes weights on the full grid: modes with
+    k2 > 0 give their block to the conjugate (-k1, -k2); on the line k2 = 0 the blocks of
+    (k1, 0) and (-k1, 0) are averaged so that the operator is real."""
+    N1, N2 = shape2
+    if not (2 * M < N1 and 2 * M < N2):
+        raise ValueError("mode set larger than the 2D grid")
+    C = 1 if c == 1 else 3
+    w = np.asarray(w, dtype=np.float64).reshape(-1, C)
+    B0 = psi2(w[0], c)
+    Q = np.broadcast_to(B0, (N1, N2, c, c)).copy()
+    ms = mode_set_2d(M)
+    if len(ms) != w.shape[0] - 1:
+        raise ValueError("weights do not match the mode set")
+    for i, (k1, k2) in enumerate(ms):
+        B = B0 + psi2(w[1 + i], c)
+        Q[k1 % N1, k2] = B
+        if k2 > 0:
+            Q[(-k1) % N1, (-k2) % N2] = B
+    line = Q[:, 0].copy()
+    Q[:, 0] = 0.5 * (line + line[(-np.arange(N1)) % N1])
+    return Q
+
+
+def modes2d_blocks3d(w, M: int, shape2, layers: int, c: int, extrusion_weight=None) -> np.ndarray:
+    """Block entries [layers, N1, N2/2+1, C3] (C3 = 1 or 6, the 3D paper order) of the extruded
+    3D operator carrying the 2D bypass-plus-modes weights ``w`` (for ``unocg_set_uno_weights``
+    with BLOCKS_HALFGRID on the extruded context).  c = 2: the extrusion component gets the
+    diagonal entry ``extrusion_weight`` (default: half the trace of the 2D bypass block) and no
+    coupling; plane-strain residuals have no such component, so it never acts."""
+    N1, N2 = shape2
+    n3h = N2 // 2 + 1
+    Q2 = _blocks_2d_full(w, M, shape2, c)
+    C = 1 if c == 1 else 3
+    B0 = psi2(np.asarray(w, dtype=np.float64).reshape(-1, C)[0], c)
+    if c == 1:
+        out = np.broadcast_to(B0[0, 0], (layers, N1, n3h)).copy()
+        out[0] = Q2[:, :n3h, 0, 0]
+        return out[..., None]
+    qe = 0.5 * float(np.trace(B0)) if extrusion_weight is None else float(extrusion_weight)
+    Q3 = np.zeros((layers, N1, n3h, 3, 3))
+    Q3[..., 0, 0] = qe
+    Q3[..., 1:, 1:] = B0
+    Q3[0, :, :, 1:, 1:] = Q2[:, :n3h]
+    return np.stack([Q3[..., i, j] for (i, j) in _ORDER3], axis=-1)
+
+
+def features_2d(f3, u3, layers: int, c: int, chunk: int = 64):
+    """Features of Eq. (features-c-1) / Eq. (features-c-2) of 2D training data given as extruded
+    3D fields (torch float32 [N_s, 1 or 3, layers, N1, N2] on the GPU, x1-invariant), from the
+    GPU transform passes: the 3D features at k1 = 0, restricted to the in-plane entries and
+    divided by `layers`.  Returns a, b [N1, N2/2+1, C] on the 2D half grid (multiplicity of the
+    conjugate modes included: summing over it sums over the full 2D grid)."""
+    a3, b3 = features(f3, u3, chunk=chunk)
+    if c == 1:
+        return a3[0][..., None] / layers, b3[0][..., None] / layers
+    sel = [_ORDER3.index((1, 1)), _ORDER3.index((2, 2)), _ORDER3.index((1, 2))]
+    return a3[0][..., sel] / layers, b3[0][..., sel] / layers
+
+
+def _hess_2d(a):
+    """Hessian in the entries per mode (Sec. 5.4): 2a for c = 1; the printed 3 x 3 for c = 2."""
+    if a.shape[-1] == 1:
+        return 2.0 * a[..., None]
+    a1, a2, a3 = a[..., 0], a[..., 1], a[..., 2]
+    H = np.zeros(a.shape[:-1] + (3, 3))
+    H[..., 0, 0] = 2 * a1
+    H[..., 1, 1] = 2 * a2
+    H[..., 2, 2] = 2 * (a1 + a2)
+    H[..., 0, 2] = H[..., 2, 0] = a3
+    H[..., 1, 2] = H[..., 2, 1] = a3
+    return H
+
+
+def _psi_jac_2d(w, c: int):
+    """v = entries(psi(w)) and J = dv/dw, and the constant d^2 v / dw^2 [C, P, P]."""
+    if c == 1:
+        return w ** 2, (2.0 * w)[..., None], np.full((1, 1, 1), 2.0)
+    w1, w2, w3 = w[..., 0], w[..., 1], w[..., 2]
+    v = np.stack([w1 * w1, w2 * w2 + w3 * w3, w1 * w3], axis=-1)
+    z = np.zeros_like(w1)
+    J = np.stack([np.stack([2 * w1, z, z], -1),
+                  np.stack([z, 2 * w2, 2 * w3], -1),
+                  np.stack([w3, z, w1], -1)], axis=-2)     # [..., entry, param]
+    D2 = np.zeros((3, 3, 3))
+    D2[0, 0, 0] = 2.0
+    D2[1, 1, 1] = D2[1, 2, 2] = 2.0
+    D2[2, 0, 2] = D2[2, 2, 0] = 1.0
+    return v, J, D2
+
+
+def second_order_modes_2d(a, b, M: int, w0, c: int, iters: int = 100, tol: float = 1e-12):
+    """Algorithm 4 for 2D problems (c = 1, c = 2) on the paper's weight layout with the 2D mode
+    set: Newton-Raphson on w = [w_0; w_1 .. w_n] for L = sum_k (1/2) v_k^T H_k v_k - b_k . v_k
+    (H_k the Hessian in the entries of Sec. 5.4), v = psi(w_0) + psi(w_i) on the i-th mode of
+    K_M and psi(w_0) elsewhere; gradient and Hessian by the chain rule through psi, an arrow of
+    C x C blocks solved by its Schur complement (O(n) per step), Levenberg-Marquardt damping
+    when a step does not lower the loss.  ``a, b``: features on the 2D half grid
+    [N1, N2/2+1, C] with multiplicities (``features_2d``).  Returns (w [1 + n, C], loss history
+    without delta)."""
+    N1 = a.shape[0]
+    C = a.shape[-1]
+    ms = mode_set_2d(M)
+    i1 = np.array([k1 % N1 for k1, _ in ms])
+    i2 = np.array([k2 for _, k2 in ms])
+    # the line k2 = 0 of the half grid holds (k1, 0) and (-k1, 0) with multiplicity 1 each;
+    # the other columns carry the conjugates through multiplicity 2
+    ak, bk = a[i1, i2], b[i1, i2]
+    a_rest = a.reshape(-1, C).sum(axis=0) - ak.sum(axis=0)
+    b_rest = b.reshape(-1, C).sum(axis=0) - bk.sum(axis=0)
+    Hk = _hess_2d(ak)
+    Hr = _hess_2d(a_rest)
+    w = np.asarray(w0, dtype=np.float64).reshape(-1, C).copy()
+    I = np.eye(C)
+
+    def loss(x):
+        v0, _, _ = _psi_jac_2d(x[0], c)
+        vi = v0 + _psi_jac_2d(x[1:], c)[0]
+        return float(0.5 * v0 @ Hr @ v0 - b_rest @ v0
+                     + np.sum(0.5 * np.einsum("ne,nef,nf->n", vi, Hk, vi) - np.sum(bk * vi, axis=1)))
+
+    hist = [loss(w)]
+    lam = 0.0
+    for _ in range(iters):
+        v0, J0, D2 = _psi_jac_2d(w[0], c)
+        u, Ji, _ = _psi_jac_2d(w[1:], c)
+        vi = v0 + u
+        Gi = np.einsum("nef,nf->ne", Hk, vi) - bk
+        Gall = Hr @ v0 - b_rest + Gi.sum(axis=0)
+        g0 = J0.T @ Gall
+        gi = np.einsum("nep,ne->np", Ji, Gi)
+        H00 = J0.T @ (Hr + Hk.sum(axis=0)) @ J0 + np.einsum("e,epq->pq", Gall, D2)
+        H0i = np.einsum("ep,nef,nfq->npq", J0, Hk, Ji)
+        Hii = np.einsum("nep,nef,nfq->npq", Ji, Hk, Ji) + np.einsum("ne,epq->npq", Gi, D2)
+        while True:
+            Dm = Hii + lam * I
+            if np.all(np.linalg.eigvalsh(Dm) > 0):
+                Dinv_g = np.linalg.solve(Dm, gi[..., None])[..., 0]
+                Dinv_H = np.linalg.solve(Dm, np.swapaxes(H0i, -1, -2))
+                S = H00 + lam * I - np.einsum("npq,nqr->pr", H0i, Dinv_H)
+                if np.all(np.linalg.eigvalsh(S) > 0):
+                    x0 = np.linalg.solve(S, g0 - np.einsum("npq,nq->p", H0i, Dinv_g))
+                    xi = Dinv_g - np.einsum("nqp,p->nq", Dinv_H, x0)
+                    trial = w - np.vstack([x0[None], xi])
+                    lt = loss(trial)
+                    if lt <= hist[-1]:
+                        break
+            lam = max(2.0 * lam, 1e-12 * max(1.0, float(np.max(np.abs(Hii)))))
+            if lam > 1e30:
+                return w, hist
+        w = trial
+        hist.append(lt)
+        lam *= 0.1
+        if abs(hist[-2] - hist[-1]) <= tol * max(1.0, abs(hist[-1])):
+            break
+    return w, hist
+
+
+def reference_modes_2d(physics: int, props, shape2, M: int, layers: int = 4) -> np.ndarray:
+    """Start weights for 2D training: the bypass from the smallest reference-medium block of the
+    extruded grid's in-plane entries over k != 0 (c = 1: the smallest weight; c = 2: lambda I with
+    lambda the smallest eigenvalue), each mode of K_M the rest of its reference block through the
+    inverse of psi (Cholesky)."""
+    h = reference_blocks_extruded(physics, props, shape2, layers)
+    c = 1 if physics == _lib.THERMAL else 2
+    N1, N2 = shape2
+    ms = mode_set_2d(M)
+    if c == 1:
+        q = h[0, :, :, 0].copy()                # [N1, N2h] at k_ext = 0
+        q[0, 0] = np.inf
+        qmin = float(np.min(q))
+        w = [np.sqrt(qmin)]
+        for (k1, k2) in ms:
+            w.append(np.sqrt(max(q[k1 % N1, k2] - qmin, 0.0)))
+        return np.array(w)[:, None]
+    Q = np.zeros(h.shape[:3] + (3, 3))
+    for e, (i, j) in enumerate(_ORDER3):
+        Q[..., i, j] = Q[..., j, i] = h[..., e]
+    B = Q[0][..., 1:, 1:]                        # [N1, N2h, 2, 2] in-plane blocks at k_ext = 0
+    ev = np.linalg.eigvalsh(B.reshape(-1, 2, 2))[1:]
+    lam = float(ev.min())
+    out = [[np.sqrt(lam), np.sqrt(lam), 0.0]]
+    for (k1, k2) in ms:
+        R = B[k1 % N1, k2] - lam * np.eye(2)
+        R = 0.5 * (R + R.T) + 1e-300 * np.eye(2)
+        ev2, V = np.linalg.eigh(R)
+        R = (V * np.maximum(ev2, 0.0)) @ V.T + 1e-14 * lam * np.eye(2)
+        L = np.linalg.cholesky(R)
+        out.append([L[0, 0], L[1, 1], L[1, 0]])
+    return np.array(out)
+
+
+def reference_blocks_extruded(physics: int, props, shape2, layers: int = 4) -> np.ndarray:
+    """Reference-medium block entries [layers, N1, N2/2+1, C3] of the extruded grid of a 2D cell
+    (arithmetic-mean medium of the phase properties), read back from the library."""
+    from .solver import Homogenization2D
+    h = Homogenization2D(physics, shape2, layers=layers)
+    h.set_microstructure(np.zeros(shape2, dtype=np.uint8), 1)
+    p = np.asarray(props, dtype=np.float64)
+    if physics == _lib.THERMAL:
+        h.set_phase_properties(np.array([float(np.mean(p))]))
+    else:
+        # the arithmetic means of the Lame constants, as (E, nu) of one phase
+        lam = np.mean([E * nu / ((1 + nu) * (1 - 2 * nu)) for E, nu in p])
+        mu = np.mean([E / (2 * (1 + nu)) for E, nu in p])
+        h.set_phase_properties(np.array([[mu * (3 * lam + 2 * mu) / (lam + mu), lam / (2 * (lam + mu))]]))
+    h.set_uno_weights(_lib.W_REFERENCE_MEDIUM)
+    C3 = 1 if physics == _lib.THERMAL else 6
+    n3h = shape2[1] // 2 + 1
+    out = api.unocg_get_uno_weights(h.h.ctx, 0, layers * shape2[0] * n3h, C3)
+    h.close()
+    return np.asarray(out).reshape(layers, shape2[0], n3h, C3)
