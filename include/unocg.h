@@ -211,10 +211,18 @@ int unocg_get_effective_tensor(unocg_ctx* ctx, double* out);
    self-adjoint, so the adjoint states are the forward solutions; needs a converged solve.  */
 int unocg_get_sensitivity(unocg_ctx* ctx, double* out);
 
-/* Solve several contexts together (e.g. one per grid size of an uneven batch): each
-   context's device-resident loop, with its per-(instance, load) convergence masks, is one
-   graph launch on the context's stream, and the launches run concurrently.  Blocks until
-   all are done.  infos may be NULL or hold n_ctx entries.                                  */
+/* Solve several contexts together (e.g. one per grid size of an uneven batch; Sec. 5.5,
+   batching).  With the graph driver (use_graph 1 or 3) the solves of all contexts are
+   captured as parallel branches of ONE CUDA graph and launched once: each branch is one
+   context's set-up, its device-resident WHILE loop over all its (instance, load) pairs with
+   their per-pair convergence flags (a converged pair's blocks return at once) and its
+   post-processing; each branch ends when its last pair converges.  The graph is kept for
+   later calls with the same contexts and options (it is rebuilt after any change that
+   invalidates a context's own graph, and dropped when a context is destroyed).  It runs after
+   the work already enqueued on every context's stream, and their later work runs after it.
+   The host-driven and persistent drivers run the contexts' solves concurrently on their own
+   streams.  A context may appear once.  Blocks until all are done; infos may be NULL or hold
+   n_ctx entries.                                                                           */
 int unocg_batch_solve(int n_ctx, unocg_ctx* const* ctxs, const unocg_solve_opts* opts,
                       unocg_solve_info* infos);
 

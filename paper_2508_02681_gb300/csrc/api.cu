@@ -10,6 +10,8 @@
 // IF node runs the FP64 residual replacement (fold u, r = f - K u) when the last residual check
 // requests it.
 #include <algorithm>
+#include <atomic>
+#include <map>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -147,7 +149,12 @@ struct unocg_ctx {
   // thermal FP32 K d: -1 automatic, 0 the register-march / element kernels, k >= 1 the TMA-staged
   // kernel with tile shape kKuTmaShapes[k - 1] (unocg_set_ku_tile / unocg_autotune_ku)
   int ku_tile = -1;
+  // changes whenever a captured graph of this context becomes invalid (and at creation): the
+  // batch graphs of unocg_batch_solve that include the context compare it
+  unsigned long long epoch = 0;
 };
+
+static std::atomic<unsigned long long> g_epoch{1};
 
 struct unocg_uno {
   int c = 1;
@@ -242,6 +249,7 @@ extern "C" int unocg_create(unocg_ctx** out, int physics, int batch, int n1, int
     if (!grid_supported(tg, 8) || !grid_supported(tg, 16)) return UNOCG_ERR_INVALID_ARG;
   }
   ctx = new unocg_ctx();
+  ctx->epoch = g_epoch.fetch_add(1);
   ctx->physics = physics;
   ctx->c = physics == UNOCG_THERMAL ? 1 : 3;
   ctx->dim = physics == UNOCG_THERMAL ? 3 : 6;
@@ -284,9 +292,13 @@ static void free_graph(unocg_ctx* ctx) {
   ctx->exec = nullptr;
   ctx->graph = nullptr;
   ctx->key = GraphKey();
+  ctx->epoch = g_epoch.fetch_add(1);
 }
 
+static void forget_batches(const unocg_ctx* ctx);
+
 extern "C" void unocg_destroy(unocg_ctx* ctx) {
+  if (ctx) forget_batches(ctx);
   if (!ctx) return;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   free_graph(ctx);
@@ -822,19 +834,14 @@ static cudaError_t enq_post(unocg_ctx* ctx, cudaStream_t s, const Plan& pl, bool
   return launch_average(aa, ctx->B, ctx->ceff, s);
 }
 
+// Captures one context's solve into the capture in progress on stream cs: set-up, the WHILE
+// conditional node whose body is one CG iteration (with an IF node for the residual replacement
+// of the mixed path), post-processing.  The conditional handles belong to the capture's graph.
 template <typename T>
-static int build_graph(unocg_ctx* ctx, const Plan& pl) {
-  cudaStream_t cs = nullptr, bs = nullptr, rs = nullptr;
-  CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-  CK(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
-  CK(cudaStreamCreateWithFlags(&rs, cudaStreamNonBlocking));
-  auto cleanup = [&]() {
-    cudaStreamDestroy(cs);
-    cudaStreamDestroy(bs);
-    cudaStreamDestroy(rs);
-  };
-  cudaGraph_t g = nullptr;
-  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+static cudaError_t capture_chain(unocg_ctx* ctx, const Plan& pl, cudaStream_t cs) {
+  cudaStream_t bs = nullptr, rs = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&rs, cudaStreamNonBlocking);
   cudaGraph_t cg = nullptr;
   cudaStreamCaptureStatus st;
   if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(cs, &st, nullptr, &cg, nullptr, nullptr, nullptr);
@@ -902,9 +909,21 @@ static int build_graph(unocg_ctx* ctx, const Plan& pl) {
     if (e == cudaSuccess) e = e2;
   }
   if (e == cudaSuccess) e = enq_post<T>(ctx, cs, pl);
+  if (bs) cudaStreamDestroy(bs);
+  if (rs) cudaStreamDestroy(rs);
+  return e;
+}
+
+template <typename T>
+static int build_graph(unocg_ctx* ctx, const Plan& pl) {
+  cudaStream_t cs = nullptr;
+  CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) e = capture_chain<T>(ctx, pl, cs);
   cudaError_t e3 = cudaStreamEndCapture(cs, &g);
   if (e == cudaSuccess) e = e3;
-  cleanup();
+  cudaStreamDestroy(cs);
   if (e != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
     return fail(ctx, UNOCG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
@@ -1281,17 +1300,165 @@ extern "C" int unocg_profile_iteration(unocg_ctx* ctx, const unocg_solve_opts* o
                   : profile_iters<double>(ctx, pl, reps, ms_out, n_out);
 }
 
+// ------------------------------------------------------------------ batch graph
+// unocg_batch_solve with the graph driver captures the solves of all its contexts (of any grid
+// sizes) as parallel branches of one CUDA graph -- each branch the context's set-up, its WHILE
+// loop of CG iterations over all its (instance, load) pairs with their convergence flags, and
+// its post-processing -- and launches it once.  Captured graphs are kept for reuse, keyed by
+// the contexts, their epochs and the solve options.
+namespace {
+struct BatchGraph {
+  std::vector<unocg_ctx*> ctxs;
+  std::vector<unsigned long long> epochs;
+  std::vector<GraphKey> keys;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t stream = nullptr;
+};
+std::mutex g_batch_mu;
+std::vector<BatchGraph*> g_batches;  // most recently built last
+constexpr size_t kMaxBatchGraphs = 4;
+
+void destroy_batch(BatchGraph* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+}  // namespace
+
+// drop the cached batch graphs that include `ctx` (called when it is destroyed)
+static void forget_batches(const unocg_ctx* ctx) {
+  std::lock_guard<std::mutex> lock(g_batch_mu);
+  for (size_t i = 0; i < g_batches.size();) {
+    BatchGraph* b = g_batches[i];
+    if (std::find(b->ctxs.begin(), b->ctxs.end(), ctx) != b->ctxs.end()) {
+      cudaStreamSynchronize(b->stream);
+      destroy_batch(b);
+      g_batches.erase(g_batches.begin() + i);
+    } else {
+      ++i;
+    }
+  }
+}
+
+static GraphKey graph_key(const unocg_ctx* ctx, const Plan& pl) {
+  GraphKey k;
+  k.precond = pl.o.precond; k.precision = pl.o.precision; k.flexible = pl.o.flexible;
+  k.replace_every = pl.o.replace_every; k.replace_drop = pl.o.replace_drop; k.max_iter = pl.o.max_iter;
+  k.L = ctx->L; k.tol = pl.o.tol;
+  return k;
+}
+
+template <typename T>
+static int build_batch(const std::vector<unocg_ctx*>& cx, const std::vector<Plan>& pls, BatchGraph* b) {
+  unocg_ctx* ctx = cx[0];
+  CK(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+  const size_t n = cx.size();
+  std::vector<cudaStream_t> ss(n, nullptr);
+  std::vector<cudaEvent_t> joins(n, nullptr);
+  cudaEvent_t fork = nullptr;
+  cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  for (size_t i = 0; i < n && e == cudaSuccess; ++i) {
+    e = cudaStreamCreateWithFlags(&ss[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&joins[i], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) e = cudaEventRecord(fork, b->stream);
+  for (size_t i = 0; i < n && e == cudaSuccess; ++i) {
+    e = cudaStreamWaitEvent(ss[i], fork, 0);  // the branch joins the capture
+    if (e == cudaSuccess) e = capture_chain<T>(cx[i], pls[i], ss[i]);
+    if (e == cudaSuccess) e = cudaEventRecord(joins[i], ss[i]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, joins[i], 0);
+  }
+  cudaGraph_t g = nullptr;
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(b->stream, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+    cudaError_t e3 = cudaStreamEndCapture(b->stream, &g);
+    if (e == cudaSuccess) e = e3;
+  }
+  for (size_t i = 0; i < n; ++i) {
+    if (ss[i]) cudaStreamDestroy(ss[i]);
+    if (joins[i]) cudaEventDestroy(joins[i]);
+  }
+  if (fork) cudaEventDestroy(fork);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
+  b->graph = g;
+  if (e != cudaSuccess) return fail(ctx, UNOCG_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+  return UNOCG_OK;
+}
+
 extern "C" int unocg_batch_solve(int n_ctx, unocg_ctx* const* ctxs, const unocg_solve_opts* opts,
                                  unocg_solve_info* infos) {
+  NvtxRange nvtx_("unocg_batch_solve");
   if (n_ctx < 1 || !ctxs || !opts) return UNOCG_ERR_INVALID_ARG;
-  // each context's loop is one graph launch on its own stream; they run concurrently
+  std::vector<unocg_ctx*> cx(ctxs, ctxs + n_ctx);
   for (int i = 0; i < n_ctx; ++i) {
-    int rc = unocg_solve_async(ctxs[i], opts);
-    if (rc) return rc;
+    if (!cx[i]) return UNOCG_ERR_INVALID_ARG;
+    for (int j = 0; j < i; ++j)
+      if (cx[j] == cx[i]) return fail(cx[i], UNOCG_ERR_INVALID_ARG, "a context appears twice in the batch");
+  }
+  const bool one_graph = n_ctx > 1 && (opts->use_graph == 1 || opts->use_graph == 3);
+  if (!one_graph) {
+    // host-driven or persistent drivers: each context's solve on its own stream, concurrently
+    for (int i = 0; i < n_ctx; ++i) {
+      int rc = unocg_solve_async(cx[i], opts);
+      if (rc) return rc;
+    }
+  } else {
+    std::vector<Plan> pls(n_ctx);
+    std::vector<GraphKey> keys(n_ctx);
+    std::vector<unsigned long long> epochs(n_ctx);
+    for (int i = 0; i < n_ctx; ++i) {
+      int rc = prepare_solve(cx[i], opts, &pls[i]);
+      if (rc) return rc;
+      keys[i] = graph_key(cx[i], pls[i]);
+      epochs[i] = cx[i]->epoch;
+    }
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    BatchGraph* b = nullptr;
+    for (size_t i = 0; i < g_batches.size() && !b; ++i) {
+      BatchGraph* c = g_batches[i];
+      if (c->ctxs == cx && c->epochs == epochs && c->keys.size() == keys.size() &&
+          std::equal(keys.begin(), keys.end(), c->keys.begin()))
+        b = c;
+    }
+    if (!b) {
+      b = new BatchGraph();
+      b->ctxs = cx;
+      b->epochs = epochs;
+      b->keys = keys;
+      int rc = pls[0].mixed ? build_batch<float>(cx, pls, b) : build_batch<double>(cx, pls, b);
+      if (rc) {
+        destroy_batch(b);
+        return rc;
+      }
+      if (g_batches.size() >= kMaxBatchGraphs) {
+        cudaStreamSynchronize(g_batches.front()->stream);
+        destroy_batch(g_batches.front());
+        g_batches.erase(g_batches.begin());
+      }
+      g_batches.push_back(b);
+    }
+    // stream order: each context's earlier work, then the batch graph, then its later work
+    for (unocg_ctx* c : cx) {
+      cudaError_t e = order_after(&c->join_ev, c->stream, b->stream);
+      if (e != cudaSuccess) return fail(c, UNOCG_ERR_CUDA, cudaGetErrorString(e));
+    }
+    cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
+    if (e != cudaSuccess) return fail(cx[0], UNOCG_ERR_CUDA, std::string("batch graph launch: ") + cudaGetErrorString(e));
+    for (unocg_ctx* c : cx) {
+      e = order_after(&c->join_ev, b->stream, c->stream);
+      if (e != cudaSuccess) return fail(c, UNOCG_ERR_CUDA, cudaGetErrorString(e));
+      c->last_opts = *opts;
+      c->last_precision = opts->precision;
+      c->last_path = 1;
+      c->solved = true;
+    }
   }
   int status = UNOCG_OK;
   for (int i = 0; i < n_ctx; ++i) {
-    int rc = unocg_solve_wait(ctxs[i], infos ? infos + i : nullptr);
+    int rc = unocg_solve_wait(cx[i], infos ? infos + i : nullptr);
     if (status == UNOCG_OK && rc != UNOCG_OK) status = rc;
   }
   return status;

@@ -47,3 +47,62 @@ def test_uneven_batch_256_instances():
         Cref = hz.effective_tensor(w["phase"], w["props"], 1, ref["u"], loads)
         assert rel(C[i], Cref) < 1e-6
     ub.close()
+
+
+def _ctx(shape, seed, contrast, batch=1):
+    from paper_2508_02681_gb300 import _lib
+    from paper_2508_02681_gb300.solver import Homogenization
+    from synth import rsa_spheres
+    h = Homogenization(_lib.THERMAL, shape, batch=batch)
+    ph = np.stack([rsa_spheres(shape, 2.0, 0.3, seed=seed + b)[0] for b in range(batch)])
+    h.set_microstructure(ph, 2)
+    h.set_phase_properties(np.stack([np.array([1.0, contrast * (b + 1)]) for b in range(batch)]))
+    h.set_macro_load(unit_loads(1))
+    h.set_uno_weights(_lib.W_REFERENCE_MEDIUM)
+    return h
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_one_graph_batch_equals_separate_solves(precision):
+    """The batch graph (all contexts as branches of one graph launch) gives the separate solves'
+    results: bit for bit in FP64 (same kernels, same launch shapes, deterministic reductions),
+    to the mixed-precision tolerance in mixed precision; it is reused on the next call, rebuilt
+    when a context's set-up changes its graph, and dropped with a destroyed context."""
+    from paper_2508_02681_gb300 import _lib, api
+    shapes = [(16, 16, 16), (24, 24, 24), (32, 16, 32)]
+    opts = dict(tol=1e-8 if precision == 0 else 1e-6, max_iter=3000, precision=precision)
+
+    def separate():
+        hs = [_ctx(s, 10 * i, 10.0 + i, batch=2) for i, s in enumerate(shapes)]
+        out = []
+        for h in hs:
+            info = h.solve(**opts)
+            out.append((info.iters.copy(), h.effective_tensor(), h.fluctuation(1, 2)))
+            h.close()
+        return out
+
+    ref = separate()
+    hs = [_ctx(s, 10 * i, 10.0 + i, batch=2) for i, s in enumerate(shapes)]
+    for call in range(2):  # built, then reused
+        infos = api.unocg_batch_solve([h.ctx for h in hs], api.make_opts(**opts), [2 * 3] * len(hs))
+        for h, info, (it, C, u) in zip(hs, infos, ref):
+            assert info.status == _lib.OK
+            assert np.array_equal(info.iters, it)
+            if precision == 0:
+                assert np.array_equal(h.effective_tensor(), C)
+                assert np.array_equal(h.fluctuation(1, 2), u)
+            else:
+                assert rel(h.effective_tensor(), C) < 1e-6
+    # a change of tile shape invalidates the second context's captured launches
+    api.unocg_set_ku_tile(hs[1].ctx, 0)
+    infos = api.unocg_batch_solve([h.ctx for h in hs], api.make_opts(**opts), [2 * 3] * len(hs))
+    assert all(i.status == _lib.OK for i in infos)
+    assert rel(hs[1].effective_tensor(), ref[1][1]) < (1e-12 if precision == 0 else 1e-6)
+    # a destroyed context leaves the batch; a new one at possibly the same address joins
+    hs[2].close()
+    hs[2] = _ctx(shapes[2], 20, 12.0, batch=2)
+    infos = api.unocg_batch_solve([h.ctx for h in hs], api.make_opts(**opts), [2 * 3] * len(hs))
+    assert all(i.status == _lib.OK for i in infos)
+    assert rel(hs[2].effective_tensor(), ref[2][1]) < (1e-12 if precision == 0 else 1e-6)
+    for h in hs:
+        h.close()
