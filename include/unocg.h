@@ -267,6 +267,34 @@ int unocg_uno_backward_dev(unocg_uno* op, int batch, const float* r_dev, const f
 int unocg_uno_features_dev(unocg_uno* op, int batch, const float* f_dev, const float* u_dev, float* ab_dev,
                            int accumulate, void* stream);
 
+/* ---------------------------------------------------------------- second-order training
+   Algorithm 4 (Sec. 5.4; c = 3: App. C) on the device for the paper's bypass-plus-modes weights
+   w = [w_0; w_1 .. w_n] (psi(w) = w^2 for c = 1; L L^T with L lower triangular holding the
+   parameters for c = 2 (Eq. (local-param-2)) and c = 3 (App. B.1); entries in the paper's
+   order).  Per learned mode k the loss is (1/2) v^T H_k v - b_k . v in the unique block
+   entries v = psi(w_0) + psi(w_k), H_k[e][f] = sum_m a_{k,m} (E_e E_f + E_f E_e)_m from the
+   features a_k (Eq. (features-c-1), Eq. (features-c-2), App. C); all other modes see psi(w_0)
+   and enter through the sums a_rest, b_rest of their features.  Each Newton-Raphson step
+   solves the arrow-shaped Hessian (bypass row / column plus one P x P block per mode, P =
+   c(c+1)/2) by its Schur complement in O(n), with Levenberg-Marquardt damping when a step
+   does not lower the loss.  The object owns its device buffers and its stream.             */
+typedef struct unocg_newton unocg_newton;
+/* c in {1, 2, 3}; n_modes >= 0 learned modes.                                              */
+int unocg_newton_create(unocg_newton** out, int c, int n_modes);
+void unocg_newton_destroy(unocg_newton* op);
+const char* unocg_newton_last_error(const unocg_newton* op);
+/* Host arrays: a_k, b_k [n_modes][C] (the features at the learned modes, multiplicities of
+   the conjugate modes included), a_rest, b_rest [C] (their sums over all other modes).
+   Non-finite values return UNOCG_ERR_INVALID_ARG.                                           */
+int unocg_newton_set_features(unocg_newton* op, const double* a_k, const double* b_k, const double* a_rest,
+                              const double* b_rest);
+/* Runs up to max_steps steps from w0 [1 + n_modes][C] (host), stopping when the loss changes by
+   at most tol * max(1, |loss|); writes the weights to w_out and the loss history (without the
+   constant delta; first entry the loss of w0) to hist, of capacity *n_hist on entry and
+   length on return (hist may be NULL).                                                     */
+int unocg_newton_run(unocg_newton* op, const double* w0, int max_steps, double tol, double* w_out, double* hist,
+                     int* n_hist);
+
 /* ---------------------------------------------------------------- operator-level entry points
    Device-pointer access to single steps of the hot path, on a context's microstructure and
    properties (instance 0 .. B-1 via `instance`).  Fields are double [c][N1][N2][N3].        */

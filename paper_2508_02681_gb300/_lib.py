@@ -90,6 +90,11 @@ SIGNATURES = {
     "unocg_uno_backward_dev": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp]),
     "unocg_apply_K_dev": (_i, [_vp, _i, _vp, _vp, _vp]),
     "unocg_apply_K32_dev": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "unocg_newton_create": (_i, [_vp, _i, _i]),
+    "unocg_newton_destroy": (None, [_vp]),
+    "unocg_newton_last_error": (C.c_char_p, [_vp]),
+    "unocg_newton_set_features": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "unocg_newton_run": (_i, [_vp, _vp, _i, C.c_double, _vp, _vp, _vp]),
     "unocg_set_ku_tile": (_i, [_vp, _i]),
     "unocg_get_ku_tile": (_i, [_vp, _vp]),
     "unocg_autotune_ku": (_i, [_vp, _i, _vp, _vp]),

@@ -460,3 +460,40 @@ def unocg_dir_autotune(ctx, opts: SolveOpts, reps: int = 3) -> np.ndarray:
     out = np.zeros(6)
     _dcheck(ctx, _lib.load().unocg_dir_autotune(ctx, C.byref(opts), reps, _ptr(out)))
     return out.reshape(3, 2)
+
+
+# ---------------------------------------------------------------- second-order training (device)
+def unocg_newton_run(c: int, a_k, b_k, a_rest, b_rest, w0, max_steps: int = 100, tol: float = 1e-12):
+    """Algorithm 4 on the device (``unocg_newton_*``): features at the learned modes ``a_k, b_k``
+    ``[n, C]``, sums over the other modes ``a_rest, b_rest`` ``[C]``, start weights ``w0``
+    ``[1 + n, C]``.  Returns (weights [1 + n, C], loss history without delta)."""
+    lib = _lib.load()
+    C_ = c * (c + 1) // 2
+    ak = np.ascontiguousarray(a_k, dtype=np.float64).reshape(-1, C_)
+    bk = np.ascontiguousarray(b_k, dtype=np.float64).reshape(-1, C_)
+    ar = np.ascontiguousarray(a_rest, dtype=np.float64).reshape(C_)
+    br = np.ascontiguousarray(b_rest, dtype=np.float64).reshape(C_)
+    w = np.ascontiguousarray(w0, dtype=np.float64).reshape(-1, C_)
+    n = ak.shape[0]
+    if bk.shape[0] != n or w.shape[0] != n + 1:
+        raise ValueError("features and weights do not match")
+    h = C.c_void_p()
+    rc = lib.unocg_newton_create(C.byref(h), c, n)
+    if rc != _lib.OK:
+        msg = lib.unocg_newton_last_error(h).decode() if h.value else "invalid arguments"
+        if h.value:
+            lib.unocg_newton_destroy(h)
+        raise UnocgError(rc, msg)
+    try:
+        rc = lib.unocg_newton_set_features(h, _ptr(ak), _ptr(bk), _ptr(ar), _ptr(br))
+        if rc != _lib.OK:
+            raise UnocgError(rc, lib.unocg_newton_last_error(h).decode())
+        out = np.empty_like(w)
+        hist = np.empty(max_steps + 1)
+        nh = C.c_int(hist.size)
+        rc = lib.unocg_newton_run(h, _ptr(w), max_steps, tol, _ptr(out), _ptr(hist), C.byref(nh))
+        if rc != _lib.OK:
+            raise UnocgError(rc, lib.unocg_newton_last_error(h).decode())
+        return out, [float(x) for x in hist[:nh.value]]
+    finally:
+        lib.unocg_newton_destroy(h)

@@ -3,18 +3,20 @@
 solved to a relative residual of 1e-6 by the GPU and by the FP64 oracle (assembled K, DFT by
 definition, Algorithm 2) on the same seeded inputs.
 
-Bars: FP64 GPU fields within 1e-9 (relative to the largest entry) of the oracle fields, both
-converged to a relative residual of 1e-10, where each lies within about 1e-10 of the discrete
-solution; at the workload tolerance of 1e-6 the FP64 iteration counts agree within one and the
-FP64 effective tensors lie within 1e-10 of the oracle's; mixed precision (FP32 fields and
-transforms, BF16 weights, FP64 reductions, residual replacement, flexible CG) gives effective
-tensors within 1e-6 of the oracle's, with a true FP64 residual of at most 1e-6.
+Bars: FP64 GPU fields within 1e-9 (relative to the largest entry) and FP64 effective tensors
+within 1e-10 of the oracle's, both solutions converged to a relative residual of 1e-10, where
+each lies within about 1e-10 of the discrete solution; at the workload tolerance of 1e-6 the
+FP64 iteration counts agree within one and the FP64 effective tensors within 1e-7; mixed
+precision (FP32 fields and transforms, BF16 weights, FP64 reductions, residual replacement,
+flexible CG) gives effective tensors within 1e-6 of the oracle's at the workload tolerance,
+with a true FP64 residual of at most 1e-6.
 
-Fields are not compared at a fixed CG iteration of the 1e-6 solve: the iterates of CG depend on
-rounding far more than the converged solution does.  On this workload a relative perturbation of
-1e-16 of the preconditioner output (the oracle run twice) moves the 71st iterate by 3e-10
-relative, and one more iteration moves it by 1.3e-7, so two correct FP64 implementations agree
-there only to about 1e-9 - 1e-8."""
+Fields and tensors of the 1e-6 solves are not held to the FP64 bars: the iterates of CG depend
+on rounding far more than the converged solution does.  On this workload a relative
+perturbation of 1e-16 of the preconditioner output (the oracle run twice) moves the 71st iterate
+by 3e-10 relative, and one more iteration moves it by 1.3e-7, so two correct FP64
+implementations agree there only to about 1e-9 - 1e-8 (the flux average is linear in the
+field: measured 1.8e-9 between the GPU and the oracle at 1e-6)."""
 import numpy as np
 import pytest
 
@@ -68,7 +70,7 @@ def _fp64_parity(w, ref, ref_tight, use_graph):
         assert abs(int(info.iters[l]) - ref["iters"][l]) <= 1, (l, int(info.iters[l]), ref["iters"][l])
     C = h.effective_tensor()[0]
     h.close()
-    assert rel(C, ref["C"]) < 1e-10
+    assert rel(C, ref["C"]) < 1e-7
     # converged fields
     h, info = _gpu(w, _lib.FP64, use_graph, TIGHT)
     assert info.status == _lib.OK

@@ -1,7 +1,8 @@
-"""Host parts of the 2D learned-UNO training (training.py) against the 2D oracle, without a GPU:
-Algorithm 4 on the 2D mode set recovers a generating bypass-plus-modes operator from features
-that the oracle computes on the full grid (folded onto the half grid with the multiplicity of
-the conjugate modes), and its loss history is the oracle's loss of the iterates."""
+"""The 2D learned-UNO training restated on the host (tests/newton_host.py, the reference for the
+device Newton of the library) against the 2D oracle, without a GPU: Algorithm 4 on the 2D mode
+set recovers a generating bypass-plus-modes operator from features that the oracle computes on
+the full grid (folded onto the half grid with the multiplicity of the conjugate modes), and its
+loss history is the oracle's loss of the iterates."""
 import numpy as np
 import pytest
 
@@ -21,7 +22,7 @@ def _half(x):
 
 @pytest.mark.parametrize("c", [1, 2])
 def test_newton_2d_recovers_a_generating_operator(c):
-    from paper_2508_02681_gb300 import training
+    from tests import newton_host as training
     M, Ns = 2, 8
     rng = np.random.default_rng(3 + c)
     C = uno2d.n_entries(c)

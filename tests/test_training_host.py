@@ -1,11 +1,14 @@
-"""Host side of the second-order training (Algorithm 4, c = 1): the Newton-Raphson iteration on
-the bypass-plus-modes weights reaches the oracle's global optimum from the features."""
+"""Second-order training (Algorithm 4) restated on the host (tests/newton_host.py, the reference
+for the device Newton of the library): the Newton-Raphson iteration on the bypass-plus-modes
+weights reaches the oracle's global optimum from the features (c = 1) and recovers a generating
+operator (c = 3); host parametrization and mode order against the oracle."""
 import numpy as np
 import pytest
 
 from oracle import training as ot
 from paper_2508_02681_gb300 import training as pt
 from synth import random_field
+from tests import newton_host as nh
 
 
 @pytest.mark.parametrize("shape,M,seed", [((8, 8, 8), 2, 0), ((6, 10, 8), 1, 1), ((12, 12, 16), 4, 2)])
@@ -18,7 +21,7 @@ def test_newton_reaches_the_global_optimum(shape, M, seed):
     a, b = ot.features_c1(R, U, shape)
     w_opt = ot.optimum_modes_c1(a, b, M, shape)
     w0 = 0.5 + rng.random(w_opt.shape)
-    w, hist = pt.second_order_modes(a, b, M, w0)
+    w, hist = nh.second_order_modes(a, b, M, w0)
     l_opt = ot.modes_loss_c1(w_opt, M, shape, a, b)
     assert ot.modes_loss_c1(w, M, shape, a, b) == pytest.approx(l_opt, rel=1e-9, abs=1e-12)
     assert all(h1 <= h0 + 1e-12 * abs(h0) for h0, h1 in zip(hist, hist[1:]))  # monotone
@@ -65,7 +68,7 @@ def test_newton_c3_recovers_a_generating_preconditioner():
     a, b = ot.features_general(R, U, shape)
     delta = float(np.sum(u ** 2)) / B
     w0 = ws + rng.standard_normal(ws.shape) * 0.05
-    w, hist = pt.second_order_modes_c3(a, b, M, w0)
+    w, hist = nh.second_order_modes_c3(a, b, M, w0)
     assert all(h1 <= h0 + 1e-12 * abs(h0) for h0, h1 in zip(hist, hist[1:]))
     assert hist[-1] + delta < 1e-9 * delta
     Q = uno.modes_Q(w, M, shape, 3)
