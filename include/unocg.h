@@ -134,16 +134,16 @@ int unocg_autotune(unocg_ctx* ctx, const unocg_solve_opts* opts, int reps, doubl
 
 /* Tile of the FP32 thermal K d (the operator apply of Algorithm 2 in mixed precision).
    tile = -1: automatic (default); 0: the register column march (below 10^6 nodes per field) or
-   the element kernel; k = 1..6: the TMA-staged kernel, whose block holds TY node rows over the
+   the element kernel; k = 1..8: the TMA-staged kernel, whose block holds TY node rows over the
    whole N3 extent (N3 / 4 threads per row) and marches over P node planes, with
-   (threads, P) = (256, 12), (512, 12), (256, 6), (512, 24), (128, 6), (256, 24) and
-   TY = threads / (N3 / 4).  The TMA kernel needs N3 in {32, 64, 128, 256} and TY dividing N2;
+   (TY, P) = (4, 12), (8, 12), (2, 12), (8, 24), (16, 6), (4, 24), (16, 12), (8, 6).  The TMA
+   kernel needs N3 a multiple of 32 up to 256, TY dividing N2 and 64 to 512 threads a block;
    unavailable shapes return UNOCG_ERR_INVALID_ARG.  Elastic problems ignore the setting.
-   unocg_get_ku_tile returns the tile the next solve uses (0 or 1..6).                       */
+   unocg_get_ku_tile returns the tile the next solve uses (0 or 1..8).                       */
 int unocg_set_ku_tile(unocg_ctx* ctx, int tile);
 int unocg_get_ku_tile(unocg_ctx* ctx, int* tile);
 /* Stencil autotuner: times `reps` FP32 K d launches over all B x L fields of the context for
-   the earlier kernels (times[0]) and each TMA tile shape (times[1..6], NaN where unavailable),
+   the earlier kernels (times[0]) and each TMA tile shape (times[1..8], NaN where unavailable),
    keeps the fastest (unocg_set_ku_tile) and returns its index in *best (may be NULL).  Needs
    the microstructure, properties and loads set.  UNOCG_ERR_DEVICE_TIMEOUT if a tile copy's
    bounded wait expired (the setting is then left unchanged).                               */

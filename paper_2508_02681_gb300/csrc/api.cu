@@ -15,6 +15,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
+#include <type_traits>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -551,6 +553,7 @@ static int ensure_workspace(unocg_ctx* ctx, int precision, int precond) {
   need = std::max(need, (size_t)BL * line_blocks_x(ctx->g, ctx->c, 8) * 2);
   need = std::max(need, (size_t)BL * line_blocks_x(ctx->g, ctx->c, 16) * 2);
   need = std::max(need, (size_t)BL * line_reg_blocks_x(ctx->g) * 2);
+  need = std::max(need, (size_t)BL * line_tma_blocks_x(ctx->g) * 2);
   need = std::max(need, (size_t)BL * node_blocks_x(ctx->g));
   need = std::max(need, (size_t)BL * ku_blocks_x(ctx->g, ctx->c));
   need = std::max(need, (size_t)BL * ku_tasks_x(ctx->g, ctx->c));
@@ -688,6 +691,17 @@ static cudaError_t enq_pre(unocg_ctx* ctx, cudaStream_t s, const Plan& pl, const
   return enq_residual_check<T>(ctx, s, ctl, 0, pl.o.precond);
 }
 
+// TMA-staged axis-1 pass of the mixed-precision loop (c = 1, power-of-two N1 up to 256);
+// UNOCG_LINE_TMA=0 at run time keeps the register-FFT pass (for comparisons)
+static bool line_tma_on(const unocg_ctx* ctx) {
+  static int env = -2;
+  if (env == -2) {
+    const char* e = std::getenv("UNOCG_LINE_TMA");
+    env = e ? std::atoi(e) : -1;
+  }
+  return env != 0 && line_tma_supported(ctx->g, ctx->c);
+}
+
 template <typename T>
 static cudaError_t enq_precond(unocg_ctx* ctx, cudaStream_t s, const Plan& pl, const LoopCtl& ctl, int part) {
   // part 0: transform axis 1 + block multiply (UNO) / direction update (Jacobi, none)
@@ -706,6 +720,8 @@ static cudaError_t enq_precond(unocg_ctx* ctx, cudaStream_t s, const Plan& pl, c
       la.sc = ctx->sc; la.red = Reduce{ctx->part, ctx->tickets + T_LINE};
       la.ft = tables(ctx, sizeof(T) == 8);
       la.flexible = pl.o.flexible; la.standalone = 0; la.gq = nullptr;
+      if constexpr (std::is_same<T, float>::value)
+        if (line_tma_on(ctx)) return launch_line_tma(la, ctx->flags + 6, ctx->spin_limit, s);
       return launch_line<T, QT>(la, 0, s);
     }
     PlaneInvArgs<T> pa{};
@@ -740,7 +756,7 @@ static int ku_tma_choice(const unocg_ctx* ctx) {
     const KuTmaShape sh = kKuTmaShapes[k];
     if (!ku_tma_supported(ctx->g, 1, sh)) continue;
     const long long blocks = BL * ku_tma_blocks_x(ctx->g, sh);
-    const long long work = (long long)sh.threads * sh.planes;
+    const long long work = (long long)ku_tma_threads(ctx->g, sh) * sh.planes;
     if (blocks >= 2LL * std::max(ctx->sm_count, 1) && work > best_work) { best = k + 1; best_work = work; }
     if (blocks > most_blocks) { most = k + 1; most_blocks = blocks; }
   }

@@ -10,31 +10,34 @@ namespace unocg {
 
 namespace {
 constexpr unsigned kFull = 0xffffffffu;
+static_assert(KT_UNROLL % KT_PS == 0 && KT_UNROLL % 2 == 0 && (KT_DS & (KT_DS - 1)) == 0,
+              "phase-ring slots repeat within the unrolled loop body; the node ring is a power of two");
 
 // Per-thread constants of the tile layout.
 struct KtGeom {
   int x0;            // first of the thread's KT_NV nodes along i3
-  int src_l, src_r;  // lanes holding the axis-3 neighbours (periodic within a row segment)
-  bool fix_l, fix_r; // warp-edge lanes of rows wider than a warp read the neighbour from smem
+  int src_l, src_r;  // lanes holding the axis-3 neighbours (periodic within the row)
+  bool fix_l, fix_r; // neighbour in another warp: read from shared memory instead
   int xl, xr;        // axis-3 neighbour columns (periodic)
-  int rm, rc, rp;    // buffer rows of the tile rows ty - 1, ty, ty + 1
-  int em, ec;        // conductivity rows of element rows ty - 1 (o2 = 1) and ty (o2 = 0)
+  int rm, rc, rp;    // offsets (row start + x0) of the tile rows ty - 1, ty, ty + 1 in a plane buffer
+  int em, ec;        // the same for element rows ty - 1 (o2 = 1) and ty (o2 = 0)
 };
 
-// Row of node values: v[0] = column x0 - 1, v[1..4] = x0 .. x0 + 3, v[5] = x0 + 4.
-__device__ __forceinline__ void kt_row(const float* row, const KtGeom& G, float (&v)[KT_NV + 2]) {
-  const float4 q = *reinterpret_cast<const float4*>(row + G.x0);
+// Row of node values at `p` = row start + x0: v[0] = column x0 - 1, v[1..4] = x0 .. x0 + 3,
+// v[5] = x0 + 4 (periodic).
+__device__ __forceinline__ void kt_row(const float* p, const KtGeom& G, float (&v)[KT_NV + 2]) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
   float l = __shfl_sync(kFull, q.w, G.src_l);
   float r = __shfl_sync(kFull, q.x, G.src_r);
-  if (G.fix_l) l = row[G.xl];
-  if (G.fix_r) r = row[G.xr];
+  if (G.fix_l) l = p[G.xl - G.x0];
+  if (G.fix_r) r = p[G.xr - G.x0];
   v[0] = l; v[1] = q.x; v[2] = q.y; v[3] = q.z; v[4] = q.w; v[5] = r;
 }
-// Row of element conductivities: v[0] = column x0 - 1, v[1..4] = x0 .. x0 + 3.
-__device__ __forceinline__ void kt_krow(const float* row, const KtGeom& G, float (&v)[KT_NV + 1]) {
-  const float4 q = *reinterpret_cast<const float4*>(row + G.x0);
+// Row of element conductivities at `p` = row start + x0: v[0] = column x0 - 1, v[1..4] = x0 .. x0 + 3.
+__device__ __forceinline__ void kt_krow(const float* p, const KtGeom& G, float (&v)[KT_NV + 1]) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
   float l = __shfl_sync(kFull, q.w, G.src_l);
-  if (G.fix_l) l = row[G.xl];
+  if (G.fix_l) l = p[G.xl - G.x0];
   v[0] = l; v[1] = q.x; v[2] = q.y; v[3] = q.z; v[4] = q.w;
 }
 
@@ -85,21 +88,23 @@ __global__ void __launch_bounds__(512) k_ku_tma(const __grid_constant__ KuTmaMap
   }
   KtGeom G;
   {
+    // a row of the tile is TPR = N3 / 4 consecutive threads; the axis-3 neighbours of a thread's
+    // four nodes are the last value of the previous thread of the row and the first of the next
+    // (periodic within the row), taken by shuffle where that thread is in the same warp
     const int TPR = n3 / KT_NV;
-    const int ty = tid / TPR;
-    G.x0 = (tid % TPR) * KT_NV;
-    const int lane = tid & 31;
-    const int seg = TPR < 32 ? TPR : 32;
-    const int ls = lane % seg, sb = lane - ls;
-    G.src_l = sb + (ls + seg - 1) % seg;
-    G.src_r = sb + (ls + 1) % seg;
-    G.fix_l = TPR > 32 && lane == 0;
-    G.fix_r = TPR > 32 && lane == 31;
+    const int ty = tid / TPR, xr_ = tid % TPR;
+    G.x0 = xr_ * KT_NV;
+    const int tl = xr_ == 0 ? tid + TPR - 1 : tid - 1;
+    const int tr = xr_ == TPR - 1 ? tid - TPR + 1 : tid + 1;
+    G.src_l = tl & 31;
+    G.src_r = tr & 31;
+    G.fix_l = (tl >> 5) != (tid >> 5);
+    G.fix_r = (tr >> 5) != (tid >> 5);
     G.xl = (G.x0 == 0 ? n3 : G.x0) - 1;
     G.xr = (G.x0 + KT_NV == n3) ? 0 : G.x0 + KT_NV;
-    G.rm = (ty == 0 ? TY : ty - 1) * n3;
-    G.rc = ty * n3;
-    G.rp = (ty + 1 == TY ? TY + 1 : ty + 1) * n3;
+    G.rm = (ty == 0 ? TY : ty - 1) * n3 + G.x0;
+    G.rc = ty * n3 + G.x0;
+    G.rp = (ty + 1 == TY ? TY + 1 : ty + 1) * n3 + G.x0;
     G.em = G.rm;
     G.ec = G.rc;
   }
@@ -128,27 +133,19 @@ __global__ void __launch_bounds__(512) k_ku_tma(const __grid_constant__ KuTmaMap
     tma_load_4d(dst, &maps.ph_rows, 0, i2_0, e, b, bar);
     tma_load_4d(dst + TY * n3, &maps.ph_row, 0, wrap_n(i2_0 - 1, n2), e, b, bar);
   };
-  // loads below got_d / got_p have completed (all threads wait for the loads in order)
-  int got_d = 0, got_p = 0;
-  auto wait_d = [&](int k) -> bool {
-    const bool ok = mbar_wait(&bar_d[k % KT_DS], (uint32_t)((k / KT_DS) & 1), lim);
-    if (ok) got_d = k + 1;
-    return ok;
-  };
-  auto wait_p = [&](int k) -> bool {
-    const bool ok = mbar_wait(&bar_p[k % KT_PS], (uint32_t)((k / KT_PS) & 1), lim);
-    if (ok) got_p = k + 1;
-    return ok;
-  };
-  // phase plane k -> conductivity plane k % 2
-  auto convert = [&](int k) {
-    const uint32_t* src = reinterpret_cast<const uint32_t*>(pbuf + (k % KT_PS) * psz);
-    float4* dst = reinterpret_cast<float4*>(kbuf + (k & 1) * kvals);
+  auto wait_d = [&](int k) -> bool { return mbar_wait(&bar_d[k % KT_DS], (uint32_t)((k / KT_DS) & 1), lim); };
+  auto wait_p = [&](int k) -> bool { return mbar_wait(&bar_p[k % KT_PS], (uint32_t)((k / KT_PS) & 1), lim); };
+  // phase slot ps -> conductivity slot ks
+  auto convert_slot = [&](int ps, int ks) {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(pbuf + ps * psz);
+    float4* dst = reinterpret_cast<float4*>(kbuf + ks * kvals);
     for (int w = tid; w < kvals / 4; w += blockDim.x) {
       const uint32_t v = src[w];
       dst[w] = make_float4(mt[v & 255u], mt[(v >> 8) & 255u], mt[(v >> 16) & 255u], mt[v >> 24]);
     }
   };
+  // phase plane k -> conductivity plane k % 2
+  auto convert = [&](int k) { convert_slot(k % KT_PS, k & 1); };
   auto timeout = [&]() {
     s_abort = 1;
     if (ka.err) atomicExch(ka.err, 1);
@@ -185,58 +182,61 @@ __global__ void __launch_bounds__(512) k_ku_tma(const __grid_constant__ KuTmaMap
       for (; issued_d < KT_DS + 2 && issued_d < ndl; ++issued_d) issue_d(issued_d);
       for (; issued_p < KT_PS + 2 && issued_p < npl; ++issued_p) issue_p(issued_p);
     }
-    float* pout = a.p + (long long)bl * g.n;
     const long long plane = (long long)n2 * n3;
     const int i2 = i2_0 + G.rc / n3;
+    const long long obase = (long long)bl * g.n + (long long)z0 * plane + (long long)i2 * n3 + G.x0;
 
     // One step at node plane z = z0 + j; S = j mod 6 selects the rotating register roles.
     auto step = [&](auto S_, int j) -> bool {
       constexpr int S = decltype(S_)::value;
       constexpr int PM = S % 3, PC = (S + 1) % 3, PN = (S + 2) % 3;
       constexpr int KM = S % 2, KC = (S + 1) % 2;
-      // node plane z + 1 (load j + 2)
-      if (!wait_d(j + 2)) timeout();
-      const float* dn = dbuf + ((j + 2) % KT_DS) * dvals;
+      // node plane z + 1 (load j + 2); the phase-ring slot and parity are fixed by S (6 is a
+      // multiple of its depth)
+      constexpr int PSL = (S + 2) % KT_PS, PPAR = ((S + 2) / KT_PS) & 1;
+      const int dsl = (j + 2) & (KT_DS - 1);
+      if (!mbar_wait(&bar_d[dsl], (uint32_t)(((j + 2) / KT_DS) & 1), lim)) timeout();
+      const float* dn = dbuf + dsl * dvals;
       kt_row(dn + G.rm, G, D[PN][0]); kt_row(dn + G.rc, G, D[PN][1]); kt_row(dn + G.rp, G, D[PN][2]);
       // element plane z (converted one step earlier)
-      const float* kc = kbuf + ((j + 1) & 1) * kvals;
+      const float* kc = kbuf + ((S + 1) & 1) * kvals;
       kt_krow(kc + G.ec, G, Kc[KC][0]);
       kt_krow(kc + G.em, G, Kc[KC][1]);
       // element plane z + 1 for the next step
       if (j + 2 < npl) {
-        if (!wait_p(j + 2)) timeout();
-        else convert(j + 2);
+        if (!mbar_wait(&bar_p[PSL], (uint32_t)PPAR, lim)) {
+          timeout();
+        } else {
+          convert_slot(PSL, S & 1);
+        }
       }
       const float(&dm)[3][KT_NV + 2] = D[PM];
       const float(&dc)[3][KT_NV + 2] = D[PC];
       const float(&dnr)[3][KT_NV + 2] = D[PN];
       const float(&km)[2][KT_NV + 1] = Kc[KM];
       const float(&kcr)[2][KT_NV + 1] = Kc[KC];
-      // pair sums: over the two element rows (Q), over the two element planes (E)
-      float Q0[KT_NV + 1], Q1[KT_NV + 1], E0[KT_NV + 1], E1[KT_NV + 1];
-#pragma unroll
-      for (int c = 0; c <= KT_NV; ++c) {
-        Q0[c] = kcr[0][c] + kcr[1][c];
-        Q1[c] = km[0][c] + km[1][c];
-        E0[c] = kcr[0][c] + km[0][c];
-        E1[c] = kcr[1][c] + km[1][c];
-      }
+      // pair sums over the two element rows (q) and over the two element planes (e), formed per
+      // element column as the nodes of the thread are visited (column i shared by nodes i - 1, i)
       float out[KT_NV];
       float sp = 0.f;
+      float q0l = kcr[0][0] + kcr[1][0], q1l = km[0][0] + km[1][0];
+      float e0l = kcr[0][0] + km[0][0], e1l = kcr[1][0] + km[1][0];
 #pragma unroll
       for (int i = 0; i < KT_NV; ++i) {
-        const float sk = (Q0[i] + Q0[i + 1]) + (Q1[i] + Q1[i + 1]);
+        const float q0r = kcr[0][i + 1] + kcr[1][i + 1], q1r = km[0][i + 1] + km[1][i + 1];
+        const float e0r = kcr[0][i + 1] + km[0][i + 1], e1r = kcr[1][i + 1] + km[1][i + 1];
+        const float sk = (q0l + q0r) + (q1l + q1r);
         float acc = 4.f * sk * dc[1][i + 1];
         // in-plane diagonal neighbours (0, s2, s3)
-        acc = fmaf(-E1[i], dc[0][i], acc);
-        acc = fmaf(-E1[i + 1], dc[0][i + 2], acc);
-        acc = fmaf(-E0[i], dc[2][i], acc);
-        acc = fmaf(-E0[i + 1], dc[2][i + 2], acc);
+        acc = fmaf(-e1l, dc[0][i], acc);
+        acc = fmaf(-e1r, dc[0][i + 2], acc);
+        acc = fmaf(-e0l, dc[2][i], acc);
+        acc = fmaf(-e0r, dc[2][i + 2], acc);
         // (s1, 0, s3)
-        acc = fmaf(-Q0[i], dnr[1][i], acc);
-        acc = fmaf(-Q0[i + 1], dnr[1][i + 2], acc);
-        acc = fmaf(-Q1[i], dm[1][i], acc);
-        acc = fmaf(-Q1[i + 1], dm[1][i + 2], acc);
+        acc = fmaf(-q0l, dnr[1][i], acc);
+        acc = fmaf(-q0r, dnr[1][i + 2], acc);
+        acc = fmaf(-q1l, dm[1][i], acc);
+        acc = fmaf(-q1r, dm[1][i + 2], acc);
         // (s1, s2, 0): the two elements along axis 3
         acc = fmaf(-(kcr[1][i] + kcr[1][i + 1]), dnr[0][i + 1], acc);
         acc = fmaf(-(kcr[0][i] + kcr[0][i + 1]), dnr[2][i + 1], acc);
@@ -253,13 +253,12 @@ __global__ void __launch_bounds__(512) k_ku_tma(const __grid_constant__ KuTmaMap
         acc = fmaf(-km[0][i + 1], dm[2][i + 2], acc);
         out[i] = acc;
         sp = fmaf(acc, dc[1][i + 1], sp);
+        q0l = q0r; q1l = q1r; e0l = e0r; e1l = e1r;
       }
       // the products d p of one step are summed in FP32 (four terms, whose rounding stays below
       // that of the FP32 p itself) and accumulated across steps in the float-float pair
       dot.add(sp);
-      const int z = z0 + j;
-      *reinterpret_cast<float4*>(pout + z * plane + (long long)i2 * n3 + G.x0) =
-          make_float4(out[0], out[1], out[2], out[3]);
+      *reinterpret_cast<float4*>(a.p + obase + (long long)j * plane) = make_float4(out[0], out[1], out[2], out[3]);
       __syncthreads();  // every thread is done with node plane j + 2 and phase plane j + 2
       if (s_abort) return false;
       if (tid == 0) {
@@ -288,9 +287,12 @@ __global__ void __launch_bounds__(512) k_ku_tma(const __grid_constant__ KuTmaMap
       if (!step(I5{}, j + 5)) { alive = false; break; }
     }
     if (!alive && tid == 0) {
-      // after a timeout: wait (bounded) for the copies still in flight before the block exits
-      for (int k = got_d; k < issued_d; ++k) (void)mbar_wait(&bar_d[k % KT_DS], (uint32_t)((k / KT_DS) & 1), lim);
-      for (int k = got_p; k < issued_p; ++k) (void)mbar_wait(&bar_p[k % KT_PS], (uint32_t)((k / KT_PS) & 1), lim);
+      // after a timeout: wait (bounded) for the copies still in flight before the block exits --
+      // the last one issued into each ring slot (earlier ones of that slot have completed)
+      for (int k = max(0, issued_d - KT_DS); k < issued_d; ++k)
+        (void)mbar_wait(&bar_d[k % KT_DS], (uint32_t)((k / KT_DS) & 1), lim);
+      for (int k = max(0, issued_p - KT_PS); k < issued_p; ++k)
+        (void)mbar_wait(&bar_p[k % KT_PS], (uint32_t)((k / KT_PS) & 1), lim);
     }
   }
   const double bs = block_sum_acc(dot, red_sh);
@@ -309,24 +311,27 @@ __global__ void __launch_bounds__(512) k_ku_tma(const __grid_constant__ KuTmaMap
 }
 
 // ---------------------------------------------------------------- host side
-// Tile shapes: threads per block (each row of the tile takes N3 / 4 threads) and node planes
-// per block.  kKuTmaShapes[0] is the default; the autotuner times the others.
-const KuTmaShape kKuTmaShapes[kKuTmaNumShapes] = {{256, 12}, {512, 12}, {256, 6}, {512, 24}, {128, 6}, {256, 24}};
+// Tile shapes: node rows TY per tile (each row takes N3 / 4 threads, so a block has
+// TY * N3 / 4 threads) and node planes per block.  The automatic choice and the autotuner pick
+// among them.
+const KuTmaShape kKuTmaShapes[kKuTmaNumShapes] = {{4, 12}, {8, 12}, {2, 12}, {8, 24}, {16, 6}, {4, 24}, {16, 12}, {8, 6}};
+
+int ku_tma_threads(const Grid& g, KuTmaShape s) { return s.rows * (g.n3 / KT_NV); }
 
 bool ku_tma_supported(const Grid& g, int c, KuTmaShape s) {
   if (c != 1) return false;
-  if (!(g.n3 == 32 || g.n3 == 64 || g.n3 == 128 || g.n3 == 256)) return false;
-  const int tpr = g.n3 / KT_NV;
-  if (s.threads % tpr != 0 || s.threads > 512 || s.threads < 32) return false;
-  const int ty = s.threads / tpr;
-  if (ty < 1 || g.n2 % ty != 0) return false;
-  if (kt_smem_bytes(ty, g.n3) > 200 * 1024) return false;
+  // whole rows in one TMA box (at most 256 values); rows of a multiple of 128 bytes keep every
+  // copy destination 128-byte aligned
+  if (g.n3 % 32 != 0 || g.n3 > 256) return false;
+  const int th = ku_tma_threads(g, s);
+  if (th % 32 != 0 || th < 64 || th > 512) return false;
+  if (s.rows < 1 || g.n2 % s.rows != 0 || (s.rows * g.n3) % 128 != 0) return false;
+  if (kt_smem_bytes(s.rows, g.n3) > 200 * 1024) return false;
   return tensor_map_encoder() != nullptr;
 }
 
 int ku_tma_blocks_x(const Grid& g, KuTmaShape s) {
-  const int ty = s.threads / (g.n3 / KT_NV);
-  return (g.n2 / ty) * ((g.n1 + s.planes - 1) / s.planes);
+  return (g.n2 / s.rows) * ((g.n1 + s.planes - 1) / s.planes);
 }
 
 static CUresult encode_4d(CUtensorMap* m, CUtensorMapDataType dt, size_t esz, const void* ptr, const Grid& g,
@@ -342,7 +347,7 @@ static CUresult encode_4d(CUtensorMap* m, CUtensorMapDataType dt, size_t esz, co
 
 cudaError_t launch_ku_tma(const StencilArgs<float>& a, KuTmaShape s, int* err, long long spin_limit, cudaStream_t st) {
   const Grid& g = a.g;
-  const int ty = s.threads / (g.n3 / KT_NV);
+  const int ty = s.rows;
   KuTmaMaps maps;
   const int B = a.BL / a.L;
   if (encode_4d(&maps.d_rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, a.d, g, a.BL, ty) != CUDA_SUCCESS ||
@@ -364,7 +369,7 @@ cudaError_t launch_ku_tma(const StencilArgs<float>& a, KuTmaShape s, int* err, l
     if (e != cudaSuccess) return e;
     smem_set = smem;
   }
-  return launch_pdl(k_ku_tma, dim3(ka.tiles * a.BL), dim3(s.threads), smem, st, maps, ka);
+  return launch_pdl(k_ku_tma, dim3(ka.tiles * a.BL), dim3(ku_tma_threads(g, s)), smem, st, maps, ka);
 }
 
 }  // namespace unocg

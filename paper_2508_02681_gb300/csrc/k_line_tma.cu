@@ -1,0 +1,221 @@
+// Axis-1 pass of the UNO preconditioner in the mixed-precision CG loop (Algorithm 2: FFT along
+// axis 1, block multiply s_hat = Q r_hat / n with the Parseval partials of r . s and, for the
+// flexible variant, r . s_old, inverse FFT along axis 1) for c = 1 on tiles staged by the TMA.
+//
+// A block owns KL_P = 16 consecutive (k2, k3) positions of one (instance, load) over all N1
+// values of axis 1.  One thread issues three tile copies: the axis-2/3 spectrum r_hat and the
+// previous s_hat (16 complex FP32 = 128 bytes per row, N1 rows, 128-byte swizzle so that the
+// column reads of the line transforms spread over the shared-memory banks) and the BF16 weights
+// Q (16 positions x N1 rows); an mbarrier with a transaction count signals their arrival.  A
+// line (one position) is transformed by G threads of one warp in registers (fft_reg.cuh: V
+// values each, one exchange through shared memory; the s_old tile, once its products with
+// r_hat are summed, is the exchange scratch).  The result overwrites the r_hat tile in place
+// (every thread writes the elements it read) and one bulk tensor store writes it to s_hat.
+// Loads of whole 128-byte rows replace the 16-byte-per-row accesses of a warp holding two
+// positions of 256-point lines.
+#include <type_traits>
+#include "kargs.h"
+#include "fft_reg.cuh"
+#include "tma.cuh"
+#include "driver_api.h"
+
+namespace unocg {
+
+constexpr int KL_P = 16;  // positions per block (one 128-byte row of complex FP32)
+
+struct alignas(64) LineTmaMaps {
+  CUtensorMap hat;   // r_hat  [BL][N1][2M] floats, box {32, N1, 1}, 128-byte swizzle
+  CUtensorMap shat;  // s_hat  same layout
+  CUtensorMap q;     // Q      [Bq][N1][M] bf16, box {16, N1, 1}
+};
+
+struct LineTmaArgs {
+  LineArgs<float, __nv_bfloat16> a;
+  int tiles;            // blocks per (instance, load)
+  int* err;
+  long long spin_limit;
+};
+
+template <int N1>
+__global__ void __launch_bounds__(KL_P * RegSplit<N1>::G) k_line_tma(const __grid_constant__ LineTmaMaps maps,
+                                                                     const LineTmaArgs la) {
+  using C = float2;
+  constexpr int G = RegSplit<N1>::G, V = RegSplit<N1>::V, VG = V / G, W = 32 / G;
+  constexpr int NTH = KL_P * G;
+  extern __shared__ unsigned char kl_raw[];
+  __shared__ double red_sh[32];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int s_abort;
+  const LineArgs<float, __nv_bfloat16>& a = la.a;
+  // tiles: r_hat (becomes s_hat) and s_old (becomes the exchange scratch), each N1 * 128
+  // bytes and 1024-byte aligned for the swizzle; Q (N1 * 32 bytes); twiddles (N1 complex)
+  unsigned char* base = kl_raw + ((1024u - (sm_addr(kl_raw) & 1023u)) & 1023u);
+  unsigned char* t_hat = base;
+  unsigned char* t_old = base + N1 * 128;
+  const __nv_bfloat16* t_q = reinterpret_cast<const __nv_bfloat16*>(base + 2 * N1 * 128);
+  C* tw1 = reinterpret_cast<C*>(base + 2 * N1 * 128 + N1 * 32);
+  const int tid = threadIdx.x;
+  const int bl = blockIdx.y;
+  const int tile = blockIdx.x;
+  const int pos0 = tile * KL_P;
+  const int M = a.g.n2 * a.g.n3h;
+  const int b = bl / a.L;
+  for (int i = tid; i < N1; i += NTH) tw1[i] = reinterpret_cast<const C*>(a.ft.tw1)[i];
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    s_abort = 0;
+    mbar_fence_init();
+  }
+  __syncthreads();
+  pdl_wait();  // r_hat, s_hat and the loop state come from the kernels before this one
+  const bool active = !a.sc[bl].done;
+  if (active && tid == 0) {
+    const uint32_t bytes = (uint32_t)(N1 * 128 * (a.flexible ? 2 : 1) + N1 * 32);
+    mbar_expect_tx(&bar, bytes);
+    tma_load_3d(t_hat, &maps.hat, 2 * pos0, 0, bl, &bar);
+    if (a.flexible) tma_load_3d(t_old, &maps.shat, 2 * pos0, 0, bl, &bar);
+    tma_load_3d(const_cast<__nv_bfloat16*>(t_q), &maps.q, pos0, 0, a.q_inst_stride ? b : 0, &bar);
+  }
+  DotAcc<float> gam, rso;
+  if (active) {
+    if (!mbar_wait(&bar, 0u, la.spin_limit)) {
+      s_abort = 1;
+      if (la.err) atomicExch(la.err, 1);
+    }
+    __syncthreads();
+    // after a timeout the copies may still be in flight: wait for them (bounded) before leaving
+    if (s_abort && tid == 0) (void)mbar_wait(&bar, 0u, la.spin_limit);
+    if (!s_abort) {
+      const int p = tid / G, g = tid % G;          // position within the tile, thread of the line
+      const int pos = pos0 + p;
+      const bool on = pos < M;
+      const int k3 = on ? pos % a.g.n3h : 0;
+      const float wt = (k3 == 0 || 2 * k3 == a.g.n3) ? 1.f : 2.f;
+      const float sc = (float)a.scale;
+      C v[V];
+#pragma unroll
+      for (int n1 = 0; n1 < V; ++n1) v[n1] = *reinterpret_cast<const C*>(t_hat + swz128_off8(g + G * n1, p));
+      if (a.flexible && on) {
+#pragma unroll
+        for (int n1 = 0; n1 < V; ++n1) {
+          const C so = *reinterpret_cast<const C*>(t_old + swz128_off8(g + G * n1, p));
+          rso.add_prod(wt * v[n1].x, so.x);
+          rso.add_prod(wt * v[n1].y, so.y);
+        }
+      }
+      __syncthreads();  // the s_old tile is free: exchange scratch of the line transforms
+      const int warp = tid >> 5, lane = tid & 31, w = lane / G;
+      C* scr = reinterpret_cast<C*>(t_old) + (size_t)warp * W * N1 + w;
+      fft_dist_a<N1, -1>(v, g, scr, W, tw1);
+      if (on) {
+#pragma unroll
+        for (int j = 0; j < VG; ++j)
+#pragma unroll
+          for (int k2 = 0; k2 < G; ++k2) {
+            const int k1 = scat_index<N1>(g, j, k2), e = j * G + k2;
+            const float q = __bfloat162float(t_q[k1 * KL_P + p]) * sc;
+            const C R = v[e];
+            const C S = make_float2(q * R.x, q * R.y);
+            gam.add_prod(wt * R.x, S.x);
+            gam.add_prod(wt * R.y, S.y);
+            v[e] = S;
+          }
+      }
+      fft_dist_b<N1, +1>(v, g, scr, W, tw1);
+#pragma unroll
+      for (int n1 = 0; n1 < V; ++n1) *reinterpret_cast<C*>(t_hat + swz128_off8(g + G * n1, p)) = v[n1];
+      fence_async_shared();
+    }
+    __syncthreads();
+    if (!s_abort && tid == 0) {
+      tma_store_3d(&maps.shat, 2 * pos0, 0, bl, t_hat);
+      tma_store_commit();
+    }
+  }
+  pdl_trigger();
+  double2 pr;
+  pr.x = block_sum_acc(gam, red_sh);
+  pr.y = block_sum_acc(rso, red_sh);
+  if (tid == 0) {
+    double* pp = a.red.part + ((long long)bl * gridDim.x + blockIdx.x) * 2;
+    pp[0] = pr.x;
+    pp[1] = pr.y;
+  }
+  if (last_block(a.red.ticket)) {
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int q = warp; q < a.BL; q += NTH / 32) {
+      const double* pp = a.red.part + (long long)q * gridDim.x * 2;
+      const double sg = warp_sum_partials(pp, gridDim.x, 2);
+      const double sr = warp_sum_partials(pp + 1, gridDim.x, 2);
+      if (lane == 0 && !a.sc[q].done) direction_update(a.sc[q], sg, sr, a.flexible);
+    }
+    __syncthreads();
+    if (tid == 0) *a.red.ticket = 0u;
+  }
+  // the tile must stay in shared memory until the bulk store has read it, and the store is
+  // complete before the block exits
+  if (active && tid == 0) tma_store_wait_all();
+}
+
+// ---------------------------------------------------------------- host side
+bool line_tma_supported(const Grid& g, int c) {
+  if (c != 1) return false;
+  if (!(g.n1 == 16 || g.n1 == 32 || g.n1 == 64 || g.n1 == 128 || g.n1 == 256)) return false;
+  const long long M = (long long)g.n2 * g.n3h;
+  if (M % 8 != 0) return false;  // 16-byte row strides of the Q and spectrum tensors
+  return tensor_map_encoder() != nullptr;
+}
+
+int line_tma_blocks_x(const Grid& g) { return (int)(((long long)g.n2 * g.n3h + KL_P - 1) / KL_P); }
+
+static CUresult encode_3d(CUtensorMap* m, CUtensorMapDataType dt, size_t esz, const void* ptr, cuuint64_t d0,
+                          cuuint64_t d1, cuuint64_t d2, cuuint32_t b0, cuuint32_t b1, CUtensorMapSwizzle sw) {
+  const cuuint64_t dims[3] = {d0, d1, d2};
+  const cuuint64_t strides[2] = {d0 * esz, d0 * d1 * esz};
+  const cuuint32_t box[3] = {b0, b1, 1u};
+  const cuuint32_t estr[3] = {1u, 1u, 1u};
+  return tensor_map_encoder()(m, dt, 3, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+}
+
+template <int N1>
+static cudaError_t line_tma_n(const LineTmaMaps& maps, const LineTmaArgs& la, cudaStream_t st) {
+  constexpr int NTH = KL_P * RegSplit<N1>::G;
+  const size_t smem = 1024 + 2 * (size_t)N1 * 128 + (size_t)N1 * 32 + (size_t)N1 * sizeof(float2);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_line_tma<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  return launch_pdl(k_line_tma<N1>, dim3(la.tiles, la.a.BL), dim3(NTH), smem, st, maps, la);
+}
+
+cudaError_t launch_line_tma(const LineArgs<float, __nv_bfloat16>& a, int* err, long long spin_limit, cudaStream_t st) {
+  const Grid& g = a.g;
+  const cuuint64_t M = (cuuint64_t)g.n2 * g.n3h;
+  const int Bq = a.q_inst_stride ? a.BL / a.L : 1;
+  LineTmaMaps maps;
+  if (encode_3d(&maps.hat, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, a.hat, 2 * M, g.n1, a.BL, 2 * KL_P, g.n1,
+                CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS ||
+      encode_3d(&maps.shat, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, a.shat, 2 * M, g.n1, a.BL, 2 * KL_P, g.n1,
+                CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS ||
+      encode_3d(&maps.q, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, a.Q, M, g.n1, Bq, KL_P, g.n1,
+                CU_TENSOR_MAP_SWIZZLE_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  LineTmaArgs la{};
+  la.a = a;
+  la.tiles = line_tma_blocks_x(g);
+  la.err = err;
+  la.spin_limit = spin_limit;
+  switch (g.n1) {
+    case 16: return line_tma_n<16>(maps, la, st);
+    case 32: return line_tma_n<32>(maps, la, st);
+    case 64: return line_tma_n<64>(maps, la, st);
+    case 128: return line_tma_n<128>(maps, la, st);
+    case 256: return line_tma_n<256>(maps, la, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace unocg

@@ -108,16 +108,23 @@ template <typename T> struct StencilArgs {
   long long spin_limit; // SM clock cycles a wait may take
 };
 
-// Tile shape of the TMA-staged thermal K d (k_ku_tma.cu): threads per block (N3 / 4 per node
-// row of the tile) and node planes per block.
+// Tile shape of the TMA-staged thermal K d (k_ku_tma.cu): node rows per tile (N3 / 4 threads
+// per row) and node planes per block.
 struct KuTmaShape {
-  int threads, planes;
+  int rows, planes;
 };
-constexpr int kKuTmaNumShapes = 6;
+constexpr int kKuTmaNumShapes = 8;
 extern const KuTmaShape kKuTmaShapes[kKuTmaNumShapes];
+int ku_tma_threads(const Grid& g, KuTmaShape s);
 bool ku_tma_supported(const Grid& g, int c, KuTmaShape s);
 int ku_tma_blocks_x(const Grid& g, KuTmaShape s);
 cudaError_t launch_ku_tma(const StencilArgs<float>& a, KuTmaShape s, int* err, long long spin_limit, cudaStream_t st);
+
+// TMA-staged axis-1 pass of the mixed-precision loop, c = 1 (k_line_tma.cu)
+bool line_tma_supported(const Grid& g, int c);
+int line_tma_blocks_x(const Grid& g);
+template <typename T, typename QT> struct LineArgs;
+cudaError_t launch_line_tma(const LineArgs<float, __nv_bfloat16>& a, int* err, long long spin_limit, cudaStream_t st);
 
 template <typename T> struct InitArgs {
   Grid g;

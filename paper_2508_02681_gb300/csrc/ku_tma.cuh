@@ -30,52 +30,9 @@
 #pragma once
 #include <cuda.h>
 #include "stencil.cuh"
+#include "tma.cuh"
 
 namespace unocg {
-
-// ---------------------------------------------------------------- mbarrier and TMA (inline PTX)
-__device__ __forceinline__ uint32_t sm_addr(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sm_addr(b)), "r"(count) : "memory");
-}
-// make barrier initialisation visible to the async (TMA) proxy
-__device__ __forceinline__ void mbar_fence_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sm_addr(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(sm_addr(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Waits until phase `parity` of barrier b has completed, at most `limit` SM clock cycles.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, long long limit) {
-  if (mbar_try(b, parity)) return true;
-  const long long t0 = clock64();
-  while (!mbar_try(b, parity))
-    if (clock64() - t0 > limit) return false;
-  return true;
-}
-// 4D tile copy global -> shared of the box at (c0, c1, c2, c3); completes on barrier b
-__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
-                                            uint64_t* b) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(sm_addr(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(sm_addr(b))
-      : "memory");
-}
 
 // ---------------------------------------------------------------- arguments
 // Tensor maps of one launch: d as [BL][N1][N2][N3] FP32, the phase labels as [B][N1][N2][N3] u8,
@@ -94,7 +51,7 @@ struct KuTmaArgs {
 };
 
 constexpr int KT_NV = 4;         // nodes per thread along i3
-constexpr int KT_DS = 4;         // node-plane ring depth
+constexpr int KT_DS = 4;         // node-plane ring depth (a power of two: cheap slot and phase)
 constexpr int KT_PS = 3;         // phase-plane ring depth
 constexpr int KT_UNROLL = 6;     // steps per loop body (the register window rotates with period 6)
 

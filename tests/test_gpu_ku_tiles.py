@@ -1,7 +1,7 @@
 """The FP32 thermal K d of the mixed-precision loop on TMA-staged tiles, against the assembled K
 of the oracle (Sec. 4.1): every tile shape the grid allows, grids of one and several tiles along
 i2 and i1, ragged plane chunks, two- and three-node periodic axes (the halo planes and rows wrap
-onto the tile itself), 32 to 256 nodes along i3 (a row in one warp, or across two), batches."""
+onto the tile itself), 32 to 256 nodes along i3 (a row in one warp, or across warps), batches."""
 import numpy as np
 import pytest
 
@@ -12,7 +12,8 @@ from tests.gpu_util import rel
 pytestmark = pytest.mark.gpu
 
 # (16, 2, 32): no tile shape divides N2 = 2, only the earlier kernel runs
-SHAPES = [(2, 16, 32), (3, 16, 64), (15, 16, 64), (25, 32, 128), (9, 8, 256), (16, 2, 32), (30, 64, 64)]
+SHAPES = [(2, 16, 32), (3, 16, 64), (15, 16, 64), (25, 32, 128), (9, 8, 256), (16, 2, 32), (30, 64, 64),
+          (5, 8, 192), (4, 12, 96), (6, 16, 160)]
 TOL32 = 4e-6   # FP32 stencil of 21 terms, relative to the largest |p|
 
 
@@ -36,7 +37,7 @@ def test_K32_every_tile_matches_assembled_K(shape):
     p_ref = fem.to_soa(K @ fem.from_soa(d.astype(np.float64)), 1, shape)
     dd = torch.tensor(d, device="cuda")
     ran = []
-    for tile in range(7):
+    for tile in range(9):
         try:
             api.unocg_set_ku_tile(ctx, tile)
         except _lib.UnocgError as err:

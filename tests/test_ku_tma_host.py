@@ -15,17 +15,17 @@ from synth import random_field, random_phase
 NV, DS, PS = 4, 4, 3
 
 
-def supported(shape, threads):
+def supported(shape, rows):
+    """Rows of the tile if the kernel takes this (grid, rows), else None (ku_tma_supported)."""
     n1, n2, n3 = shape
-    if n3 not in (32, 64, 128, 256):
+    if n3 % 32 or n3 > 256:
         return None
-    tpr = n3 // NV
-    if threads % tpr:
+    threads = rows * (n3 // NV)
+    if threads % 32 or not 64 <= threads <= 512:
         return None
-    ty = threads // tpr
-    if n2 % ty:
+    if n2 % rows or (rows * n3) % 128:
         return None
-    return ty
+    return rows
 
 
 def smem_layout(ty, n3):
@@ -35,11 +35,12 @@ def smem_layout(ty, n3):
     return dslot, kslot, pslot
 
 
-def emulate(shape, threads, planes, d, phase, kappa):
+def emulate(shape, rows, planes, d, phase, kappa):
     """p = K d as the kernel computes it (FP64 here; h = 1 / N1, scaled conductivities h/12 k)."""
     n1, n2, n3 = shape
-    ty_rows = supported(shape, threads)
+    ty_rows = supported(shape, rows)
     tpr = n3 // NV
+    threads = ty_rows * tpr
     h12 = (1.0 / n1) / 12.0
     mt = kappa * h12
     dslot, kslot, pslot = smem_layout(ty_rows, n3)
@@ -60,20 +61,21 @@ def emulate(shape, threads, planes, d, phase, kappa):
     tid = np.arange(threads)
     t_row = tid // tpr
     x0 = (tid % tpr) * NV
-    lane = tid % 32
-    seg = min(tpr, 32)
-    ls = lane % seg
-    sb = tid - ls                      # absolute thread index of the segment start
-    src_l = sb + (ls + seg - 1) % seg
-    src_r = sb + (ls + 1) % seg
-    fix_l = (tpr > 32) & (lane == 0)
-    fix_r = (tpr > 32) & (lane == 31)
+    xr_ = tid % tpr
+    # the neighbouring threads of the row (periodic); the shuffle reads that lane of the own
+    # warp, the kernel replaces it by a shared-memory read where the neighbour is in another warp
+    tl = np.where(xr_ == 0, tid + tpr - 1, tid - 1)
+    tr = np.where(xr_ == tpr - 1, tid - tpr + 1, tid + 1)
+    src_l = (tid & ~31) | (tl & 31)
+    src_r = (tid & ~31) | (tr & 31)
+    fix_l = (tl >> 5) != (tid >> 5)
+    fix_r = (tr >> 5) != (tid >> 5)
     xl = np.where(x0 == 0, n3, x0) - 1
     xr = np.where(x0 + NV == n3, 0, x0 + NV)
     rm = np.where(t_row == 0, ty_rows, t_row - 1)
     rc = t_row
     rp = np.where(t_row + 1 == ty_rows, ty_rows + 1, t_row + 1)
-    assert np.all(src_l // 32 == tid // 32) and np.all(src_r // 32 == tid // 32)
+    assert np.all(src_l < threads) and np.all(src_r < threads)
 
     def node_plane(q, i2_0):
         # the ring buffer of node plane q: rows 0..TY-1 tile, TY = i2_0 - 1, TY + 1 = i2_0 + TY
@@ -141,17 +143,20 @@ def emulate(shape, threads, planes, d, phase, kappa):
     return p, writes
 
 
-CASES = [((2, 16, 32), 128, 6), ((5, 16, 64), 256, 6), ((13, 16, 64), 128, 6), ((7, 8, 256), 256, 12),
-         ((9, 8, 256), 512, 12), ((6, 32, 128), 256, 24), ((3, 4, 256), 128, 6)]
+# (grid, rows TY, planes per block): one and several row tiles, ragged plane chunks, two-node
+# axes, rows in one warp (N3 <= 128), across warps (N3 = 160, 192, 256)
+CASES = [((2, 16, 32), 16, 6), ((5, 16, 64), 16, 6), ((13, 16, 64), 8, 6), ((7, 8, 256), 4, 12),
+         ((9, 8, 256), 8, 12), ((6, 32, 128), 8, 24), ((3, 4, 256), 2, 6), ((5, 8, 192), 4, 12),
+         ((4, 12, 96), 4, 6), ((3, 8, 160), 4, 6)]
 
 
-@pytest.mark.parametrize("shape,threads,planes", CASES)
-def test_tma_tiling_writes_each_node_once_and_equals_assembled_K(shape, threads, planes):
-    assert supported(shape, threads) is not None
+@pytest.mark.parametrize("shape,rows,planes", CASES)
+def test_tma_tiling_writes_each_node_once_and_equals_assembled_K(shape, rows, planes):
+    assert supported(shape, rows) is not None
     phase = random_phase(shape, 3, seed=sum(shape))
     kappa = np.array([1.0, 6.0, 0.4])
     d = random_field(shape, seed=3)
-    p, writes = emulate(shape, threads, planes, d, phase, kappa)
+    p, writes = emulate(shape, rows, planes, d, phase, kappa)
     assert np.all(writes == 1)
     K = fem.assemble_K(phase, kappa, 1)
     p_ref = (K @ d.ravel()).reshape(shape)
