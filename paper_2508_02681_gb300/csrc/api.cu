@@ -743,10 +743,13 @@ static cudaError_t enq_precond(unocg_ctx* ctx, cudaStream_t s, const Plan& pl, c
 }
 
 // Tile shape of the thermal FP32 K d (1-based index into kKuTmaShapes, 0: the earlier kernels).
-// Automatic choice: the supported shape with the most work per block (threads x planes) that
-// still gives two blocks per SM over all (instance, load) fields, else the one with most blocks.
+// Automatic choice: below 10^6 nodes per field the fields sit in L2 and the register column
+// march is faster (64^3, 3 loads: 16.4 against 22.8 us per launch); from there the TMA-staged
+// tile, with the supported shape of the most work per block (threads x planes) that still gives
+// two blocks per SM over all (instance, load) fields, else the one with most blocks.
 static int ku_tma_choice(const unocg_ctx* ctx) {
   if (ctx->c != 1 || ctx->ku_tile == 0) return 0;
+  if (ctx->ku_tile < 0 && ctx->g.n < 1000000) return 0;
   if (ctx->ku_tile > 0)
     return ku_tma_supported(ctx->g, 1, kKuTmaShapes[ctx->ku_tile - 1]) ? ctx->ku_tile : 0;
   const long long BL = (long long)ctx->B * std::max(ctx->L, 1);

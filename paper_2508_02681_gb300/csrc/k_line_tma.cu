@@ -95,19 +95,23 @@ __global__ void __launch_bounds__(KL_P * RegSplit<N1>::G) k_line_tma(const __gri
       C v[V];
 #pragma unroll
       for (int n1 = 0; n1 < V; ++n1) v[n1] = *reinterpret_cast<const C*>(t_hat + swz128_off8(g + G * n1, p));
+      // Parseval partials: the thread's V products are summed in FP32 (their rounding stays below
+      // that of the FP32 spectra themselves) and accumulated in the float-float pair
       if (a.flexible && on) {
+        float part = 0.f;
 #pragma unroll
         for (int n1 = 0; n1 < V; ++n1) {
           const C so = *reinterpret_cast<const C*>(t_old + swz128_off8(g + G * n1, p));
-          rso.add_prod(wt * v[n1].x, so.x);
-          rso.add_prod(wt * v[n1].y, so.y);
+          part = fmaf(v[n1].x, so.x, fmaf(v[n1].y, so.y, part));
         }
+        rso.add(wt * part);
       }
       __syncthreads();  // the s_old tile is free: exchange scratch of the line transforms
       const int warp = tid >> 5, lane = tid & 31, w = lane / G;
       C* scr = reinterpret_cast<C*>(t_old) + (size_t)warp * W * N1 + w;
       fft_dist_a<N1, -1>(v, g, scr, W, tw1);
       if (on) {
+        float part = 0.f;  // r . s = sum q |r_hat|^2 over the thread's modes
 #pragma unroll
         for (int j = 0; j < VG; ++j)
 #pragma unroll
@@ -115,11 +119,10 @@ __global__ void __launch_bounds__(KL_P * RegSplit<N1>::G) k_line_tma(const __gri
             const int k1 = scat_index<N1>(g, j, k2), e = j * G + k2;
             const float q = __bfloat162float(t_q[k1 * KL_P + p]) * sc;
             const C R = v[e];
-            const C S = make_float2(q * R.x, q * R.y);
-            gam.add_prod(wt * R.x, S.x);
-            gam.add_prod(wt * R.y, S.y);
-            v[e] = S;
+            part = fmaf(q, fmaf(R.x, R.x, R.y * R.y), part);
+            v[e] = make_float2(q * R.x, q * R.y);
           }
+        gam.add(wt * part);
       }
       fft_dist_b<N1, +1>(v, g, scr, W, tw1);
 #pragma unroll

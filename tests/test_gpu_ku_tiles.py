@@ -55,14 +55,17 @@ def test_K32_every_tile_matches_assembled_K(shape):
 
 
 def test_K32_batch_instances_and_default_tile():
-    """Instances of a batch take their own phase labels and conductivities."""
+    """Instances of a batch take their own phase labels and conductivities (TMA tile (4, 12))."""
     import torch
     from paper_2508_02681_gb300 import api
     shape, B = (12, 16, 128), 3
     phases = np.stack([random_phase(shape, 4, seed=40 + b) for b in range(B)])
     props = np.stack([np.array([1.0, 3.0, 10.0, 0.5]) * (b + 1) for b in range(B)])
     ctx = _ctx(shape, phases, props, batch=B)
-    assert api.unocg_get_ku_tile(ctx) > 0   # the automatic choice takes a TMA tile on this grid
+    # below 10^6 nodes the automatic choice keeps the column march; take a TMA tile explicitly
+    assert api.unocg_get_ku_tile(ctx) == 0
+    api.unocg_set_ku_tile(ctx, 1)
+    assert api.unocg_get_ku_tile(ctx) == 1
     for b in range(B):
         d = random_field((1,) + shape, seed=60 + b).astype(np.float32)
         K = fem.assemble_K(phases[b], props[b], 1)
