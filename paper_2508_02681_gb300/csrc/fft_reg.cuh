@@ -138,4 +138,63 @@ template <int N> __device__ __forceinline__ int scat_index(int g, int j, int k2)
   return g * VG + j + V * k2;
 }
 
+// ---------------------------------------------------------------- real-to-complex rows
+// shared by the plane passes (k_fft_reg.cu, k_plane_cl.cu)
+template <typename T>
+__device__ __forceinline__ void load_tw_reg(cplx<T>* dst, const void* src, int N) {
+  const cplx<T>* s = (const cplx<T>*)src;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) dst[i] = s[i];
+}
+
+// X(k), X(Nh-k) from the half-length spectrum Z in one row (in place), pair k <= Nh/2
+template <typename T>
+__device__ __forceinline__ void r2c_pair(cplx<T>* b, int k, int Nh, const cplx<T>* __restrict__ twN) {
+  using C = cplx<T>;
+  const T half = (T)0.5;
+  if (k == 0) {
+    C z = b[0];
+    b[0] = mk<T>(z.x + z.y, (T)0);
+    b[Nh] = mk<T>(z.x - z.y, (T)0);
+    return;
+  }
+  const int k2 = Nh - k;
+  C zk = b[k], zm = b[k2];
+  C e = mk<T>(half * (zk.x + zm.x), half * (zk.y - zm.y));
+  C o = mk<T>(half * (zk.y + zm.y), -half * (zk.x - zm.x));
+  C xk = cadd(e, cmul(twN[k], o));
+  if (k2 != k) {
+    C e2 = mk<T>(half * (zm.x + zk.x), half * (zm.y - zk.y));
+    C o2 = mk<T>(half * (zm.y + zk.y), -half * (zm.x - zk.x));
+    b[k2] = cadd(e2, cmul(twN[k2], o2));
+  }
+  b[k] = xk;
+}
+
+// inverse of r2c_pair up to the factor of the unnormalized inverse (see c2r_pre)
+template <typename T>
+__device__ __forceinline__ void c2r_pair(cplx<T>* b, int k, int Nh, const cplx<T>* __restrict__ twN) {
+  using C = cplx<T>;
+  if (k == 0) {
+    T x0 = b[0].x, xn = b[Nh].x;
+    b[0] = mk<T>(x0 + xn, x0 - xn);
+    return;
+  }
+  const int k2 = Nh - k;
+  C xk = b[k], xm = b[k2];
+  C wk = twN[k];
+  wk.y = -wk.y;
+  C e = mk<T>(xk.x + xm.x, xk.y - xm.y);
+  C o = cmul(mk<T>(xk.x - xm.x, xk.y + xm.y), wk);
+  C zk = mk<T>(e.x - o.y, e.y + o.x);
+  if (k2 != k) {
+    C w2 = twN[k2];
+    w2.y = -w2.y;
+    C e2 = mk<T>(xm.x + xk.x, xm.y - xk.y);
+    C o2 = cmul(mk<T>(xm.x - xk.x, xm.y + xk.y), w2);
+    b[k2] = mk<T>(e2.x - o2.y, e2.y + o2.x);
+  }
+  b[k] = zk;
+}
+
+
 }  // namespace unocg

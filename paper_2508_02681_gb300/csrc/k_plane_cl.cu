@@ -1,0 +1,281 @@
+// Transform passes of 256 x 256 planes (axes 2 and 3) of the mixed-precision loop on thread-block
+// clusters of two CTAs (Algorithm 2: forward and inverse unitary transform around the block
+// multiply; FP32).
+//
+// A half-spectrum plane of 256 rows x 129 complex FP32 values (264 KB) exceeds one block's
+// shared memory; one pass over it needs two.  The two CTAs of a cluster split the plane by rows
+// for the axis-3 transforms and by columns for the axis-2 transforms, and move the values between
+// the two splits through distributed shared memory: a CTA writes each row result into the shared
+// memory of the CTA that owns its column (rank 0: columns 0..64, rank 1: 65..128).  One cluster
+// barrier separates the phases.  Each phase uses the register-resident line FFTs of
+// fft_reg.cuh (rows: 128-point half-length lines, 8 threads each; columns: 256-point lines, 16
+// threads each).  This replaces the row pass plus the separate in-place axis-2 pass (one global
+// round trip of the spectrum less per transform).
+//
+//   k_plane_fwd_cl: r <- r - alpha p, ||r||_inf, rows (axis 3, r2c), exchange, columns (axis 2),
+//                   r_hat written; the last block performs the residual check.
+//   k_plane_inv_cl: columns (inverse axis 2) from s_hat, exchange, rows (c2r),
+//                   u <- u + alpha d_old, d <- s + beta d_old.
+#include <cooperative_groups.h>
+#include "kargs.h"
+#include "fft_reg.cuh"
+
+namespace cgr = cooperative_groups;
+
+namespace unocg {
+
+namespace {
+constexpr int PN = 256, PNh = 128, Pn3h = 129;
+constexpr int PG3 = RegSplit<PNh>::G, PV3 = RegSplit<PNh>::V, PRPW = 32 / PG3;  // rows: 8 threads, 16 values
+constexpr int PG2 = RegSplit<PN>::G, PV2 = RegSplit<PN>::V, PCW = 32 / PG2;     // columns: 16 threads, 16 values
+constexpr int PNW = 16;                          // warps per CTA
+// columns of rank r: [pcol0(r), pcol0(r) + pncol(r)) -- rank 0: 0..64, rank 1: 65..128
+__host__ __device__ constexpr int pcol0(int r) { return r ? 65 : 0; }
+__host__ __device__ constexpr int pncol(int r) { return r ? 64 : 65; }
+constexpr int PCP = 66;                          // pitch of the column buffer (column 65: scratch of the idle lane)
+constexpr int PRS = 130;                         // pitch of a row scratch (129 values)
+constexpr int PRP = 132;                         // pitch of the inverse row buffer
+constexpr size_t kTwBytes = (size_t)(PNh + PN + PN) * sizeof(float2);
+constexpr size_t kFwdSmem = (size_t)PN * PCP * sizeof(float2) + (size_t)PNW * PRPW * PRS * sizeof(float2) + kTwBytes;
+constexpr size_t kInvSmem = (size_t)PNh * PRP * sizeof(float2) + (size_t)PNW * PCW * PN * sizeof(float2) + kTwBytes;
+}  // namespace
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PNW * 32) k_plane_fwd_cl(PlaneFwdArgs<float> a) {
+  using C = float2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red_sh[32];
+  cgr::cluster_group cluster = cgr::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  C* colbuf = reinterpret_cast<C*>(smem_raw);                 // [256 rows][PCP] this rank's columns
+  C* rowscr = colbuf + PN * PCP;                               // [warp][PRPW rows][PRS]
+  C* tw3h = rowscr + PNW * PRPW * PRS;
+  C* tw2 = tw3h + PNh;
+  C* tw3 = tw2 + PN;
+  C* colbuf_peer = cluster.map_shared_rank(colbuf, 1 - rank);
+  load_tw_reg<float>(tw3h, a.ft.tw3h, PNh);
+  load_tw_reg<float>(tw2, a.ft.tw2, PN);
+  load_tw_reg<float>(tw3, a.ft.tw3, PN);
+  pdl_wait();
+  const int bl = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int plane_id = blockIdx.x >> 1;
+  const int comp = plane_id / a.g.n1, i1 = plane_id - comp * a.g.n1;
+  const long long field = (long long)bl * a.c + comp;
+  const long long base = (field * a.g.n1 + i1) * (long long)(PN * PN);
+  bool active = true;
+  double alpha = 0.0;
+  if (!a.standalone) {
+    const CgScal& st = a.sc[bl];
+    active = !st.done && (!a.after_replace || st.need_replace);
+    alpha = a.after_replace ? 0.0 : st.alpha;
+  }
+  __syncthreads();
+  float lmax = 0.f;
+  if (active) {  // the same for both CTAs of the cluster (one plane, one (instance, load))
+    const float al = (float)alpha;
+    const bool upd = alpha != 0.0;
+    // ---- rows of this rank: axis 3 (half-length complex lines of 128 points), r2c
+    for (int rg = warp; rg < PNh / PRPW; rg += PNW) {
+      const int rl = rg * PRPW + lane / PG3, g = lane % PG3;
+      const int row = rank * PNh + rl;
+      C v[PV3];
+      if (a.standalone) {
+        const C* src = reinterpret_cast<const C*>(a.src + base) + row * PNh;
+#pragma unroll
+        for (int n1 = 0; n1 < PV3; ++n1) v[n1] = src[g + PG3 * n1];
+      } else {
+        C* r = reinterpret_cast<C*>(a.r + base) + row * PNh;
+        const C* p = reinterpret_cast<const C*>(a.p + base) + row * PNh;
+        C q[PV3];
+#pragma unroll
+        for (int n1 = 0; n1 < PV3; ++n1) {
+          v[n1] = r[g + PG3 * n1];
+          q[n1] = p[g + PG3 * n1];
+        }
+        if (upd) {
+#pragma unroll
+          for (int n1 = 0; n1 < PV3; ++n1) {
+            v[n1].x -= al * q[n1].x;
+            v[n1].y -= al * q[n1].y;
+            r[g + PG3 * n1] = v[n1];
+          }
+        }
+#pragma unroll
+        for (int n1 = 0; n1 < PV3; ++n1) lmax = fmaxf(lmax, fmaxf(fabsf(v[n1].x), fabsf(v[n1].y)));
+      }
+      C* rs = rowscr + (warp * PRPW + lane / PG3) * PRS;
+      fft_dist_a<PNh, -1>(v, g, rs, 1, tw3h);
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < PV3 / PG3; ++j)
+#pragma unroll
+        for (int k2 = 0; k2 < PG3; ++k2) rs[scat_index<PNh>(g, j, k2)] = v[j * PG3 + k2];
+      __syncwarp();
+      for (int k = g; k <= PNh / 2; k += PG3) r2c_pair<float>(rs, k, PNh, tw3);
+      __syncwarp();
+      // each value to the column owner: rank 0 columns 0..64, rank 1 columns 65..128
+      for (int k3 = g; k3 < Pn3h; k3 += PG3) {
+        const int own = k3 < pcol0(1) ? 0 : 1;
+        C* dst = own == rank ? colbuf : colbuf_peer;
+        dst[row * PCP + (k3 - pcol0(own))] = rs[k3];
+      }
+      __syncwarp();
+    }
+  }
+  cluster.sync();  // both ranks' row values are in place (also orders the shared-memory writes)
+  if (active) {
+    // ---- columns of this rank: axis 2 (256-point lines)
+    const int ncol = pncol(rank), ncg = (ncol + PCW - 1) / PCW;
+    C* out = a.hat + (field * a.g.n1 + i1) * (long long)(PN * Pn3h) + pcol0(rank);
+    for (int cg = warp; cg < ncg; cg += PNW) {
+      const int col = cg * PCW + lane % PCW, g = lane / PCW;
+      const bool on = col < ncol;  // the idle lane works on the padding column 65
+      C v[PV2];
+#pragma unroll
+      for (int n1 = 0; n1 < PV2; ++n1) v[n1] = colbuf[(g + PG2 * n1) * PCP + col];
+      fft_dist_a<PN, -1>(v, g, colbuf + col, PCP, tw2);
+      if (on) {
+#pragma unroll
+        for (int j = 0; j < PV2 / PG2; ++j)
+#pragma unroll
+          for (int k2 = 0; k2 < PG2; ++k2) out[scat_index<PN>(g, j, k2) * Pn3h + col] = v[j * PG2 + k2];
+      }
+      __syncwarp();
+    }
+  }
+  pdl_trigger();
+  if (a.standalone) return;
+  const double bmax = block_max_t(lmax, red_sh);
+  if (threadIdx.x == 0 && active) atomic_max_nonneg(&a.sc[bl].rmax_bits, bmax);
+  if (last_block(a.ticket)) {
+    residual_decision(a.sc, a.BL, a.ctl, a.after_replace);
+    if (threadIdx.x == 0) *a.ticket = 0u;
+  }
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PNW * 32) k_plane_inv_cl(PlaneInvArgs<float> a) {
+  using C = float2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cgr::cluster_group cluster = cgr::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  C* rowbuf = reinterpret_cast<C*>(smem_raw);                 // [128 rows of this rank][PRP]
+  C* colscr = rowbuf + PNh * PRP;                              // [warp][256 slots][PCW columns]
+  C* tw3h = colscr + PNW * PCW * PN;
+  C* tw2 = tw3h + PNh;
+  C* tw3 = tw2 + PN;
+  C* rowbuf_peer = cluster.map_shared_rank(rowbuf, 1 - rank);
+  load_tw_reg<float>(tw3h, a.ft.tw3h, PNh);
+  load_tw_reg<float>(tw2, a.ft.tw2, PN);
+  load_tw_reg<float>(tw3, a.ft.tw3, PN);
+  pdl_wait();
+  const int bl = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int plane_id = blockIdx.x >> 1;
+  const int comp = plane_id / a.g.n1, i1 = plane_id - comp * a.g.n1;
+  const long long field = (long long)bl * a.c + comp;
+  const long long base = (field * a.g.n1 + i1) * (long long)(PN * PN);
+  // a finished (instance, load): both CTAs of the cluster return (no cluster barrier is pending)
+  if (!a.standalone && a.sc[bl].done) return;
+  const float alpha = a.standalone ? 0.f : (float)a.sc[bl].alpha;
+  const float beta = a.standalone ? 0.f : (float)a.sc[bl].beta;
+  __syncthreads();
+  // ---- columns of this rank: inverse axis 2 from s_hat, each value to the row owner
+  {
+    const int ncol = pncol(rank), ncg = (ncol + PCW - 1) / PCW;
+    const C* in = a.shat + (field * a.g.n1 + i1) * (long long)(PN * Pn3h) + pcol0(rank);
+    C* scr = colscr + warp * PCW * PN + (lane % PCW);
+    for (int cg = warp; cg < ncg; cg += PNW) {
+      const int col = cg * PCW + lane % PCW, g = lane / PCW;
+      const bool on = col < ncol;
+      C v[PV2];
+#pragma unroll
+      for (int j = 0; j < PV2 / PG2; ++j)
+#pragma unroll
+        for (int k2 = 0; k2 < PG2; ++k2)
+          v[j * PG2 + k2] = on ? in[scat_index<PN>(g, j, k2) * Pn3h + col] : make_float2(0.f, 0.f);
+      fft_dist_b<PN, +1>(v, g, scr, PCW, tw2);
+      if (on) {
+        const int k3 = pcol0(rank) + col;
+#pragma unroll
+        for (int n1 = 0; n1 < PV2; ++n1) {
+          const int row = g + PG2 * n1;       // rows 0..127 belong to rank 0, 128..255 to rank 1
+          C* dst = (row >> 7) == rank ? rowbuf : rowbuf_peer;
+          dst[(row & (PNh - 1)) * PRP + k3] = v[n1];
+        }
+      }
+      __syncwarp();
+    }
+  }
+  cluster.sync();  // every row of this rank is complete
+  // ---- rows of this rank: inverse axis 3 (half spectrum -> real row), CG updates
+  for (int rg = warp; rg < PNh / PRPW; rg += PNW) {
+    const int rl = rg * PRPW + lane / PG3, g = lane % PG3;
+    const int row = rank * PNh + rl;
+    C* rs = rowbuf + rl * PRP;
+    for (int k = g; k <= PNh / 2; k += PG3) c2r_pair<float>(rs, k, PNh, tw3);
+    __syncwarp();
+    C v[PV3];
+#pragma unroll
+    for (int j = 0; j < PV3 / PG3; ++j)
+#pragma unroll
+      for (int k2 = 0; k2 < PG3; ++k2) v[j * PG3 + k2] = rs[scat_index<PNh>(g, j, k2)];
+    fft_dist_b<PNh, +1>(v, g, rs, 1, tw3h);
+    if (a.standalone) {
+      C* dst = reinterpret_cast<C*>(a.dst + base) + row * PNh;
+#pragma unroll
+      for (int n1 = 0; n1 < PV3; ++n1) dst[g + PG3 * n1] = v[n1];
+    } else {
+      C* d = reinterpret_cast<C*>(a.d + base) + row * PNh;
+      C* u = reinterpret_cast<C*>(a.u + base) + row * PNh;
+#pragma unroll
+      for (int n1 = 0; n1 < PV3; ++n1) {
+        const C dv = d[g + PG3 * n1];
+        C uu = u[g + PG3 * n1];
+        uu.x += alpha * dv.x;
+        uu.y += alpha * dv.y;
+        u[g + PG3 * n1] = uu;
+        d[g + PG3 * n1] = make_float2(v[n1].x + beta * dv.x, v[n1].y + beta * dv.y);
+      }
+    }
+    __syncwarp();
+  }
+  pdl_trigger();
+}
+
+// ---------------------------------------------------------------- host side
+bool plane_cl_ok(const Grid& g) {
+#ifdef UNOCG_NO_CLUSTER_PLANES
+  return false;
+#endif
+  return g.n2 == PN && g.n3 == PN;
+}
+
+template <typename K, typename A>
+static cudaError_t launch_cl(K kern, size_t smem, const A& a, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2 * a.c * a.g.n1, a.BL);
+  cfg.blockDim = dim3(PNW * 32);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = UNOCG_PDL ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+cudaError_t launch_plane_fwd_cl(const PlaneFwdArgs<float>& a, cudaStream_t s) {
+  return launch_cl(k_plane_fwd_cl, kFwdSmem, a, s);
+}
+cudaError_t launch_plane_inv_cl(const PlaneInvArgs<float>& a, cudaStream_t s) {
+  return launch_cl(k_plane_inv_cl, kInvSmem, a, s);
+}
+
+}  // namespace unocg

@@ -120,6 +120,11 @@ bool ku_tma_supported(const Grid& g, int c, KuTmaShape s);
 int ku_tma_blocks_x(const Grid& g, KuTmaShape s);
 cudaError_t launch_ku_tma(const StencilArgs<float>& a, KuTmaShape s, int* err, long long spin_limit, cudaStream_t st);
 
+// 256 x 256 plane passes on two-CTA clusters, FP32 (k_plane_cl.cu)
+bool plane_cl_ok(const Grid& g);
+cudaError_t launch_plane_fwd_cl(const PlaneFwdArgs<float>& a, cudaStream_t s);
+cudaError_t launch_plane_inv_cl(const PlaneInvArgs<float>& a, cudaStream_t s);
+
 // TMA-staged axis-1 pass of the mixed-precision loop, c = 1 (k_line_tma.cu)
 bool line_tma_supported(const Grid& g, int c);
 int line_tma_blocks_x(const Grid& g);

@@ -1,5 +1,6 @@
 """Flexible (Polak-Ribiere) UNO-CG on grids whose (axis-2, axis-3) planes are too large for one
-block: the forward and inverse transforms then run as a row pass plus a separate axis-2 pass.
+block: the forward and inverse transforms then run as a row pass plus a separate axis-2 pass, or,
+for 256 x 256 FP32 planes, as one pass on a cluster of two blocks.
 The r . s_old term of the flexible coefficient reads the previous s_hat, so the inverse axis-2
 pass must leave it intact.  FP64 against the oracle's flexible PCG on the same inputs (fields
 1e-9, effective tensor 1e-10); mixed precision to the effective tensor (1e-6) with the true
@@ -69,4 +70,45 @@ def test_flexible_mixed_row_passes_converge(f32_case):
     assert np.all(info.true_rel_res <= 1e-6)
     assert np.all(info.iters <= np.array(ref["iters"]) + 8)
     assert rel(h.effective_tensor()[0], ref["C"]) < 1e-6
+    h.close()
+
+
+@pytest.fixture(scope="module")
+def cluster_case():
+    return _case((4, 256, 256))   # FP32 256 x 256 planes: one pass on two-CTA clusters
+
+
+@pytest.mark.parametrize("use_graph", [1, 0])
+def test_cluster_plane_passes_mixed_match_oracle(cluster_case, use_graph):
+    """256 x 256 planes in the mixed loop (forward and inverse plane passes on two-CTA clusters,
+    values exchanged through distributed shared memory) against the oracle's flexible PCG."""
+    from paper_2508_02681_gb300 import _lib
+    phase, loads, ref = cluster_case
+    h = _solver(phase, loads)
+    info = h.solve(tol=1e-6, max_iter=500, precond=_lib.PRECOND_UNO, precision=_lib.MIXED, flexible=1,
+                   replace_every=50, use_graph=use_graph)
+    assert info.status == _lib.OK
+    assert np.all(info.true_rel_res <= 1e-6)
+    assert np.all(info.iters <= np.array(ref["iters"]) + 8)
+    assert rel(h.effective_tensor()[0], ref["C"]) < 1e-6
+    h.close()
+
+
+def test_cluster_plane_passes_elastic_mixed_match_oracle():
+    """The same for three components per node (each component's plane is its own cluster)."""
+    from paper_2508_02681_gb300 import _lib
+    from paper_2508_02681_gb300.solver import Homogenization
+    phase, _ = rsa_spheres((2, 256, 256), 3.0, 0.25, seed=6)
+    props = np.array([[1.0, 0.3], [10.0, 0.2]])
+    loads = unit_loads(3)[[0, 3]]
+    ref = hz.solve(phase, props, 3, loads, precond="uno", tol=1e-9, flexible=True)
+    Cref = hz.effective_tensor(phase, props, 3, ref["u"], loads)
+    h = Homogenization(_lib.ELASTIC, phase.shape)
+    h.set_microstructure(phase, 2)
+    h.set_phase_properties(props)
+    h.set_macro_load(loads)
+    h.set_uno_weights(_lib.W_REFERENCE_MEDIUM)
+    info = h.solve(tol=1e-6, max_iter=500, precond=_lib.PRECOND_UNO, precision=_lib.MIXED, flexible=1)
+    assert info.status == _lib.OK and np.all(info.true_rel_res <= 1e-6)
+    assert rel(h.effective_tensor()[0], Cref) < 1e-6
     h.close()
