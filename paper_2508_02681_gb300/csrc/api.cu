@@ -614,21 +614,20 @@ struct Plan {
 
 // Forward transform over axes 3 and 2: whole planes in one pass where a plane fits one block's
 // shared memory, else the row pass (axis 3) followed by the in-place axis-2 column pass.
-// 256 x 256 FP32 planes: one pass on two-CTA clusters (UNOCG_PLANE_CL=0 keeps the row pass
-// plus axis-2 pass, for comparisons)
-static bool plane_cl_on(const Grid& g) {
-  static int env = -2;
-  if (env == -2) {
-    const char* e = std::getenv("UNOCG_PLANE_CL");
-    env = e ? std::atoi(e) : -1;
-  }
-  return env != 0 && plane_cl_ok(g);
+// 256 x 256 FP32 planes: one pass on two-CTA clusters.  UNOCG_PLANE_CL selects the passes that
+// take it, as a mask read at each enqueue: 1 forward, 2 inverse (default 1: the forward cluster
+// pass measured 487 -> 354 us per launch on a 256^3 field of three loads, the inverse one
+// 439 -> 477 us, so the inverse keeps the column pass plus row pass).
+static bool plane_cl_on(const Grid& g, int which) {
+  const char* e = std::getenv("UNOCG_PLANE_CL");
+  const int mask = e ? std::atoi(e) : 1;
+  return (mask & which) != 0 && plane_cl_ok(g);
 }
 
 template <typename T>
 static cudaError_t fwd_transform(PlaneFwdArgs<T>& a, cudaStream_t s, int only_pending) {
   if constexpr (std::is_same<T, float>::value)
-    if (plane_cl_on(a.g)) return launch_plane_fwd_cl(a, s);
+    if (plane_cl_on(a.g, 1)) return launch_plane_fwd_cl(a, s);
   a.rows = plane_rows(a.g, sizeof(T) * 2);
   cudaError_t e = launch_plane_fwd<T>(a, s);
   if (e != cudaSuccess || a.rows == 0) return e;
@@ -640,7 +639,7 @@ static cudaError_t fwd_transform(PlaneFwdArgs<T>& a, cudaStream_t s, int only_pe
 template <typename T>
 static cudaError_t inv_transform(PlaneInvArgs<T>& a, cudaStream_t s) {
   if constexpr (std::is_same<T, float>::value)
-    if (plane_cl_on(a.g)) return launch_plane_inv_cl(a, s);
+    if (plane_cl_on(a.g, 2)) return launch_plane_inv_cl(a, s);
   a.rows = plane_rows(a.g, sizeof(T) * 2);
   if (a.rows) {
     ColArgs<T> ca{a.g, a.c, a.BL, const_cast<cplx<T>*>(a.shat), a.sc, a.ft, 0, a.cols_out};

@@ -78,11 +78,13 @@ def cluster_case():
     return _case((4, 256, 256))   # FP32 256 x 256 planes: one pass on two-CTA clusters
 
 
-@pytest.mark.parametrize("use_graph", [1, 0])
-def test_cluster_plane_passes_mixed_match_oracle(cluster_case, use_graph):
-    """256 x 256 planes in the mixed loop (forward and inverse plane passes on two-CTA clusters,
-    values exchanged through distributed shared memory) against the oracle's flexible PCG."""
+@pytest.mark.parametrize("use_graph,passes", [(1, 1), (0, 1), (1, 3), (0, 3), (1, 0)])
+def test_cluster_plane_passes_mixed_match_oracle(cluster_case, use_graph, passes, monkeypatch):
+    """256 x 256 planes in the mixed loop (plane passes on two-CTA clusters, values exchanged
+    through distributed shared memory; `passes` masks which: 1 forward, 2 inverse) against the
+    oracle's flexible PCG."""
     from paper_2508_02681_gb300 import _lib
+    monkeypatch.setenv("UNOCG_PLANE_CL", str(passes))
     phase, loads, ref = cluster_case
     h = _solver(phase, loads)
     info = h.solve(tol=1e-6, max_iter=500, precond=_lib.PRECOND_UNO, precision=_lib.MIXED, flexible=1,
@@ -94,9 +96,11 @@ def test_cluster_plane_passes_mixed_match_oracle(cluster_case, use_graph):
     h.close()
 
 
-def test_cluster_plane_passes_elastic_mixed_match_oracle():
+@pytest.mark.parametrize("passes", [1, 3])
+def test_cluster_plane_passes_elastic_mixed_match_oracle(passes, monkeypatch):
     """The same for three components per node (each component's plane is its own cluster)."""
     from paper_2508_02681_gb300 import _lib
+    monkeypatch.setenv("UNOCG_PLANE_CL", str(passes))
     from paper_2508_02681_gb300.solver import Homogenization
     phase, _ = rsa_spheres((2, 256, 256), 3.0, 0.25, seed=6)
     props = np.array([[1.0, 0.3], [10.0, 0.2]])
