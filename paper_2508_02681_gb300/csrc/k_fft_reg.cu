@@ -315,15 +315,19 @@ __global__ void __launch_bounds__(kLineRegWarps * 32) k_line_reg(LineArgs<T, QT>
         qpre[j * G + k2] = on ? QRead<T, QT>::get(a.Q, qb + (long long)scat_index<N1>(g, j, k2) * M + pos) : (T)0;
   }
   pdl_wait();
-  // the spectra are requested together with the loop state (one memory latency)
-  C v[CC][V], so[CC][V];
+  // the spectra are requested together with the loop state (one memory latency); with one
+  // component the previous s_hat comes in the same batch, with three it is read one component
+  // at a time below (all six lines at once would not fit the register file)
+  constexpr bool CS = CC == 1;
+  C v[CC][V], so[CS ? V : 1];
 #pragma unroll
   for (int cc = 0; cc < CC; ++cc)
 #pragma unroll
     for (int n1 = 0; n1 < V; ++n1) {
       const long long gi = fbase + ((long long)(cc * N1 + g + G * n1)) * M + pos;
       v[cc][n1] = on ? a.hat[gi] : mk<T>((T)0, (T)0);
-      if (MODE == 0) so[cc][n1] = (on && a.flexible) ? a.shat[gi] : mk<T>((T)0, (T)0);
+      if constexpr (CS)
+        if (MODE == 0) so[n1] = (on && a.flexible) ? a.shat[gi] : mk<T>((T)0, (T)0);
     }
   const bool active = (MODE != 0) || !a.sc[bl].done;
   __syncthreads();
@@ -334,12 +338,22 @@ __global__ void __launch_bounds__(kLineRegWarps * 32) k_line_reg(LineArgs<T, QT>
     C* scr = scr_all + (size_t)warp * W * N1 + w;
     if (MODE == 0 && a.flexible && on) {
 #pragma unroll
-      for (int cc = 0; cc < CC; ++cc)
+      for (int cc = 0; cc < CC; ++cc) {
+        C sl[V];
 #pragma unroll
         for (int n1 = 0; n1 < V; ++n1) {
-          rso.add_prod(wt * v[cc][n1].x, so[cc][n1].x);
-          rso.add_prod(wt * v[cc][n1].y, so[cc][n1].y);
+          if constexpr (CS) {
+            sl[n1] = so[n1];
+          } else {
+            sl[n1] = a.shat[fbase + ((long long)(cc * N1 + g + G * n1)) * M + pos];
+          }
         }
+#pragma unroll
+        for (int n1 = 0; n1 < V; ++n1) {
+          rso.add_prod(wt * v[cc][n1].x, sl[n1].x);
+          rso.add_prod(wt * v[cc][n1].y, sl[n1].y);
+        }
+      }
     }
 #pragma unroll
     for (int cc = 0; cc < CC; ++cc) fft_dist_a<N1, -1>(v[cc], g, scr, W, tw1);
