@@ -25,6 +25,9 @@ namespace cgr = cooperative_groups;
 namespace unocg {
 
 namespace {
+// L2 prefetch of the 128-byte line holding p
+__device__ __forceinline__ void pf_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 constexpr int PN = 256, PNh = 128, Pn3h = 129;
 constexpr int PG3 = RegSplit<PNh>::G, PV3 = RegSplit<PNh>::V, PRPW = 32 / PG3;  // rows: 8 threads, 16 values
 constexpr int PG2 = RegSplit<PN>::G, PV2 = RegSplit<PN>::V, PCW = 32 / PG2;     // columns: 16 threads, 16 values
@@ -74,6 +77,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PNW * 32) k_plane_fw
   if (active) {  // the same for both CTAs of the cluster (one plane, one (instance, load))
     const float al = (float)alpha;
     const bool upd = alpha != 0.0;
+    // the rows of this warp's second row group are requested into L2 now (their loads follow
+    // the first group's transform)
+    if (!a.standalone && warp + PNW < PNh / PRPW) {
+      const int row = rank * PNh + (warp + PNW) * PRPW + lane / PG3;
+      const long long o = base + (long long)row * PN + (lane % PG3) * 32;
+      pf_l2(a.r + o);
+      pf_l2(a.p + o);
+    }
     // ---- rows of this rank: axis 3 (half-length complex lines of 128 points), r2c
     for (int rg = warp; rg < PNh / PRPW; rg += PNW) {
       const int rl = rg * PRPW + lane / PG3, g = lane % PG3;
@@ -129,18 +140,25 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PNW * 32) k_plane_fw
     C* out = a.hat + (field * a.g.n1 + i1) * (long long)(PN * Pn3h) + pcol0(rank);
     for (int cg = warp; cg < ncg; cg += PNW) {
       const int col = cg * PCW + lane % PCW, g = lane / PCW;
-      const bool on = col < ncol;  // the idle lane works on the padding column 65
       C v[PV2];
 #pragma unroll
       for (int n1 = 0; n1 < PV2; ++n1) v[n1] = colbuf[(g + PG2 * n1) * PCP + col];
       fft_dist_a<PN, -1>(v, g, colbuf + col, PCP, tw2);
-      if (on) {
-#pragma unroll
-        for (int j = 0; j < PV2 / PG2; ++j)
-#pragma unroll
-          for (int k2 = 0; k2 < PG2; ++k2) out[scat_index<PN>(g, j, k2) * Pn3h + col] = v[j * PG2 + k2];
-      }
+      // the column's spectrum back into its own slots of the column buffer (row k2 of column
+      // col); the idle lane's padding column 65 is not written out
       __syncwarp();
+#pragma unroll
+      for (int j = 0; j < PV2 / PG2; ++j)
+#pragma unroll
+        for (int k2 = 0; k2 < PG2; ++k2) colbuf[scat_index<PN>(g, j, k2) * PCP + col] = v[j * PG2 + k2];
+      __syncwarp();
+    }
+    __syncthreads();
+    // whole rows of this rank's columns: contiguous runs of ncol values in r_hat
+    for (int k2 = warp; k2 < PN; k2 += PNW) {
+      const C* src = colbuf + k2 * PCP;
+      C* dst = out + (long long)k2 * Pn3h;
+      for (int c = lane; c < ncol; c += 32) dst[c] = src[c];
     }
   }
   pdl_trigger();
@@ -178,23 +196,37 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PNW * 32) k_plane_in
   if (!a.standalone && a.sc[bl].done) return;
   const float alpha = a.standalone ? 0.f : (float)a.sc[bl].alpha;
   const float beta = a.standalone ? 0.f : (float)a.sc[bl].beta;
+  // the d and u rows of this thread's row phase are requested into L2 while the columns are
+  // transformed
+  if (!a.standalone) {
+    for (int rg = warp; rg < PNh / PRPW; rg += PNW) {
+      const int row = rank * PNh + rg * PRPW + lane / PG3;
+      const long long o = base + (long long)row * PN + (lane % PG3) * 32;
+      pf_l2(a.d + o);
+      pf_l2(a.u + o);
+    }
+  }
   __syncthreads();
-  // ---- columns of this rank: inverse axis 2 from s_hat, each value to the row owner
+  // ---- columns of this rank: inverse axis 2 from s_hat, each value to the row owner.  A warp's
+  // first two column groups are read before either is transformed (one memory latency).
   {
     const int ncol = pncol(rank), ncg = (ncol + PCW - 1) / PCW;
     const C* in = a.shat + (field * a.g.n1 + i1) * (long long)(PN * Pn3h) + pcol0(rank);
     C* scr = colscr + warp * PCW * PN + (lane % PCW);
-    for (int cg = warp; cg < ncg; cg += PNW) {
-      const int col = cg * PCW + lane % PCW, g = lane / PCW;
-      const bool on = col < ncol;
-      C v[PV2];
+    const int g = lane / PCW;
+    auto load_col = [&](int cg, C (&v)[PV2]) {
+      const int col = cg * PCW + lane % PCW;
+      const bool on = cg < ncg && col < ncol;
 #pragma unroll
       for (int j = 0; j < PV2 / PG2; ++j)
 #pragma unroll
         for (int k2 = 0; k2 < PG2; ++k2)
           v[j * PG2 + k2] = on ? in[scat_index<PN>(g, j, k2) * Pn3h + col] : make_float2(0.f, 0.f);
+    };
+    auto transform_col = [&](int cg, C (&v)[PV2]) {
+      const int col = cg * PCW + lane % PCW;
       fft_dist_b<PN, +1>(v, g, scr, PCW, tw2);
-      if (on) {
+      if (col < ncol) {
         const int k3 = pcol0(rank) + col;
 #pragma unroll
         for (int n1 = 0; n1 < PV2; ++n1) {
@@ -204,6 +236,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PNW * 32) k_plane_in
         }
       }
       __syncwarp();
+    };
+    for (int cg = warp; cg < ncg; cg += 2 * PNW) {
+      C v0[PV2], v1[PV2];
+      load_col(cg, v0);
+      load_col(cg + PNW, v1);
+      transform_col(cg, v0);
+      if (cg + PNW < ncg) transform_col(cg + PNW, v1);
     }
   }
   cluster.sync();  // every row of this rank is complete

@@ -70,12 +70,19 @@ __global__ void __launch_bounds__(KE_THREADS) k_ku_el(StencilArgs<T> a) {
 }
 
 // ============================================================================ init: r = f, u = d = 0
+// f = -sum_e A_e^T int_e B^T C_e eps_bar (Sec. 6) node by node: with the element-mean gradient of
+// the shape function of corner o, sg(o) / (4h) (sg = 2 o - 1 per axis), the integral over the
+// element is (h^2 / 4) sg(o), so f(node) = -(h^2 / 4) sum_o sigma_e(o) sg(o) over the 8 elements
+// e(o) = node - o.  The phase constants enter only through w_m(node) = sum_o c_m(e(o)) sg(o)
+// (c_0 = kappa or lambda, c_1 = mu), formed once for all loads of the instance:
+//   thermal  f = -(h^2/4) w_0 . eps_bar
+//   elastic  f_i = -(h^2/4) (tr(eps) w_0,i + 2 sum_k eps_ik w_1,k)   (eps from the Mandel load)
 template <typename T, int CC>
 __global__ void __launch_bounds__(256) k_init(InitArgs<T> a) {
+  constexpr int NM = CC == 1 ? 1 : 2;
   __shared__ double mt[2 * 256];
   const Grid& g = a.g;
-  const int bl = blockIdx.y;
-  const int b = bl / a.L, l = bl % a.L;
+  const int b = blockIdx.y;  // instance; the thread covers every load
   load_material<double>(mt, a.mat, b);
   __syncthreads();
   int i1, i2, i3;
@@ -83,17 +90,48 @@ __global__ void __launch_bounds__(256) k_init(InitArgs<T> a) {
   const long long n = g.n;
   const uint8_t* ph = a.phase + (long long)b * n;
   const long long node = ((long long)i1 * g.n2 + i2) * g.n3 + i3;
-  double f[CC];
-  node_rhs<CC>(ph, mt, g, i1, i2, i3, a.loads + l * (CC == 1 ? 3 : 6), f);
-  const long long o = (long long)bl * CC * n + node;
+  Nbr nb;
+  neighbours(g, i1, i2, i3, nb);
+  double w[NM][3];
 #pragma unroll
-  for (int i = 0; i < CC; ++i) {
-    if (a.r) a.r[o + i * n] = (T)f[i];
-    if (a.u) a.u[o + i * n] = (T)0;
-    if (a.d) a.d[o + i * n] = (T)0;
-    if (a.p) a.p[o + i * n] = (T)0;
-    if (a.u64) a.u64[o + i * n] = 0.0;
-    if (a.f64) a.f64[o + i * n] = f[i];
+  for (int m = 0; m < NM; ++m) w[m][0] = w[m][1] = w[m][2] = 0.0;
+#pragma unroll
+  for (int o = 0; o < 8; ++o) {
+    const int o1 = (o >> 2) & 1, o2 = (o >> 1) & 1, o3 = o & 1;
+    const int p = ph[eidx(nb, o1, o2, o3)];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+      const double v = mt[2 * p + m];
+      w[m][0] += o1 ? v : -v;
+      w[m][1] += o2 ? v : -v;
+      w[m][2] += o3 ? v : -v;
+    }
+  }
+  const double q = 0.25 * g.h * g.h;
+  for (int l = 0; l < a.L; ++l) {
+    const double* load = a.loads + l * (CC == 1 ? 3 : 6);
+    double f[CC];
+    if constexpr (CC == 1) {
+      f[0] = -q * (w[0][0] * load[0] + w[0][1] * load[1] + w[0][2] * load[2]);
+    } else {
+      const double is2 = 0.70710678118654752440;
+      const double e12 = load[3] * is2, e13 = load[4] * is2, e23 = load[5] * is2;
+      const double tr = load[0] + load[1] + load[2];
+      const double e[3][3] = {{load[0], e12, e13}, {e12, load[1], e23}, {e13, e23, load[2]}};
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        f[i] = -q * (tr * w[0][i] + 2.0 * (e[i][0] * w[1][0] + e[i][1] * w[1][1] + e[i][2] * w[1][2]));
+    }
+    const long long o = ((long long)b * a.L + l) * CC * n + node;
+#pragma unroll
+    for (int i = 0; i < CC; ++i) {
+      if (a.r) a.r[o + i * n] = (T)f[i];
+      if (a.u) a.u[o + i * n] = (T)0;
+      if (a.d) a.d[o + i * n] = (T)0;
+      if (a.p) a.p[o + i * n] = (T)0;
+      if (a.u64) a.u64[o + i * n] = 0.0;
+      if (a.f64) a.f64[o + i * n] = f[i];
+    }
   }
 }
 
@@ -141,11 +179,16 @@ __global__ void __launch_bounds__(256) k_true_res(TrueResArgs<T> a) {
 // rref <- rref - K w with w = u32 + alpha d, all products and sums in float pairs (df64.cuh):
 // the FP32 inputs are exact, the stencil coefficients are integers (thermal: 12 x the unit-cube
 // Laplacian, elastic: 72 x Klam / Kmu) times the phase constants as pairs, and the result is
-// rounded to FP64 once per node.  Element e = node - o holds the node as its corner o; its
-// corner b is the neighbour at offset b - o.
-template <int CC>
-__global__ void __launch_bounds__(256) k_replace(ReplaceArgs a) {
-  __shared__ float2 mp[2 * 256];  // phase constants (kappa, 0) or (lambda, mu) as pairs
+// rounded to FP64 once per node.
+// Thermal replacement as a march along axis 1 (each w formed once per node): a thread walks
+// KR_CZ nodes of one (i2, i3) column with the 3 x 3 neighbourhoods of w = u32 + alpha d on the planes z - 1, z, z + 1 and the
+// conductivities of the element planes z - 1, z in registers, all as float pairs.  For the
+// element at corner offset o of the node, 12 t_o = 4 w(node) - (the 3 face-diagonal and the
+// body-diagonal corners of the element, seen from the node).
+constexpr int KR_CZ = 8;
+__global__ void __launch_bounds__(256) k_replace_col(ReplaceArgs a) {
+  __shared__ float2 mp[2 * 256];
+  __shared__ double red_sh[32];
   const Grid& g = a.g;
   const int bl = blockIdx.y;
   const int b = bl / a.L;
@@ -159,82 +202,80 @@ __global__ void __launch_bounds__(256) k_replace(ReplaceArgs a) {
   const df32 al = df_from_double(a.sc[bl].alpha);
   int i1, i2, i3;
   double lmax = 0.0;
-  if (tile_node(g, i1, i2, i3)) {
-    const long long n = g.n;
+  if (tile_column_at(g, blockIdx.x, KR_CZ, i1, i2, i3)) {
+    const long long n = g.n, S = (long long)g.n2 * g.n3;
     const uint8_t* ph = a.phase + (long long)b * n;
-    const float* u32 = a.u32 + (long long)bl * CC * n;
-    const float* dd = a.d + (long long)bl * CC * n;
-    Nbr nb;
-    neighbours(g, i1, i2, i3, nb);
-    auto W = [&](int k, long long q) { return df_axpy(al, __ldg(dd + k * n + q), __ldg(u32 + k * n + q)); };
-    double kw[CC];
-    if (CC == 1) {
-      df32 w[3][3][3];
+    const float* u32 = a.u32 + (long long)bl * n;
+    const float* dd = a.d + (long long)bl * n;
+    const int c2[3] = {i2 ? i2 - 1 : g.n2 - 1, i2, (i2 + 1 == g.n2) ? 0 : i2 + 1};
+    const int c3[3] = {i3 ? i3 - 1 : g.n3 - 1, i3, (i3 + 1 == g.n3) ? 0 : i3 + 1};
+    long long off[3][3];
 #pragma unroll
-      for (int s1 = 0; s1 < 3; ++s1)
+    for (int x = 0; x < 3; ++x)
 #pragma unroll
-        for (int s2 = 0; s2 < 3; ++s2)
+      for (int y = 0; y < 3; ++y) off[x][y] = (long long)c2[x] * g.n3 + c3[y];
+    auto W = [&](long long q) { return df_axpy(al, __ldg(dd + q), __ldg(u32 + q)); };
+    auto K = [&](long long q) {
+      const float2 v = mp[2 * ph[q]];
+      return df32{v.x, v.y};
+    };
+    // w[plane: 0 = z - 1, 1 = z, 2 = z + 1][row][column], kap[element plane: 0 = z - 1, 1 = z][o2][o3]
+    df32 w[3][3][3], kap[2][2][2];
+    const long long zm = (long long)(i1 ? i1 - 1 : g.n1 - 1) * S;
 #pragma unroll
-          for (int s3 = 0; s3 < 3; ++s3) w[s1][s2][s3] = W(0, nidx(nb, s1, s2, s3));
+    for (int x = 0; x < 3; ++x)
+#pragma unroll
+      for (int y = 0; y < 3; ++y) {
+        w[0][x][y] = W(zm + off[x][y]);
+        w[1][x][y] = W((long long)i1 * S + off[x][y]);
+      }
+#pragma unroll
+    for (int o2 = 0; o2 < 2; ++o2)
+#pragma unroll
+      for (int o3 = 0; o3 < 2; ++o3) kap[0][o2][o3] = K(zm + off[1 - o2][1 - o3]);
+    const int zend = min(i1 + KR_CZ, g.n1);
+    const double h12 = g.h / 12.0;
+    for (int z = i1; z < zend; ++z) {
+      const long long zc = (long long)z * S, zn = (long long)((z + 1 == g.n1) ? 0 : z + 1) * S;
+#pragma unroll
+      for (int x = 0; x < 3; ++x)
+#pragma unroll
+        for (int y = 0; y < 3; ++y) w[2][x][y] = W(zn + off[x][y]);
+#pragma unroll
+      for (int o2 = 0; o2 < 2; ++o2)
+#pragma unroll
+        for (int o3 = 0; o3 < 2; ++o3) kap[1][o2][o3] = K(zc + off[1 - o2][1 - o3]);
+      df32 w4 = w[1][1][1];
+      w4.hi *= 4.0f;
+      w4.lo *= 4.0f;
       df32 acc = df_make(0.0f);
 #pragma unroll
       for (int o = 0; o < 8; ++o) {
         const int o1 = (o >> 2) & 1, o2 = (o >> 1) & 1, o3 = o & 1;
-        // 12 x (unit-cube Laplacian row): 4 on the node, -1 on the corners that differ from it in
-        // two or three coordinates, 0 on those that differ in one
-        df32 t = df_make(0.0f);
-        df_add_mul(t, 4.0f, w[1][1][1]);
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const int c1 = (c >> 2) & 1, c2 = (c >> 1) & 1, c3 = c & 1;
-          const int diff = (c1 != o1) + (c2 != o2) + (c3 != o3);
-          if (diff >= 2) df_add_mul(t, -1.0f, w[c1 - o1 + 1][c2 - o2 + 1][c3 - o3 + 1]);
-        }
-        const float2 kp = mp[2 * ph[eidx(nb, o1, o2, o3)]];
-        acc = df_add(acc, df_mul({kp.x, kp.y}, t));
+        // the coordinate of the corners away from the node: 2 for o = 0, 0 for o = 1
+        const int d1 = 2 - 2 * o1, d2 = 2 - 2 * o2, d3 = 2 - 2 * o3;
+        const df32 sd = df_add(df_add(w[d1][d2][1], w[d1][1][d3]), df_add(w[1][d2][d3], w[d1][d2][d3]));
+        const df32 t = df_add(w4, df_neg(sd));
+        acc = df_add(acc, df_mul(kap[1 - o1][o2][o3], t));
       }
-      kw[0] = df_to_double(acc) * (g.h / 12.0);
-    } else {
-      df32 out[3] = {df_make(0.0f), df_make(0.0f), df_make(0.0f)};
-      // one element at a time (not unrolled: the registers hold one element's 24 values)
-#pragma unroll 1
-      for (int o = 0; o < 8; ++o) {
-        const int o1 = (o >> 2) & 1, o2 = (o >> 1) & 1, o3 = o & 1;
-        df32 aL[3] = {df_make(0.0f), df_make(0.0f), df_make(0.0f)};
-        df32 aM[3] = {df_make(0.0f), df_make(0.0f), df_make(0.0f)};
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const int c1 = (c >> 2) & 1, c2 = (c >> 1) & 1, c3 = c & 1;
-          const long long q = nidx(nb, c1 - o1 + 1, c2 - o2 + 1, c3 - o3 + 1);
-          const df32 wk[3] = {W(0, q), W(1, q), W(2, q)};
-#pragma unroll
-          for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-              df_add_mul(aL[i], kElastic72.lam[o][i][c][k], wk[k]);
-              df_add_mul(aM[i], kElastic72.mu[o][i][c][k], wk[k]);
-            }
-        }
-        const int p = ph[eidx(nb, o1, o2, o3)];
-        const float2 lp = mp[2 * p], mu = mp[2 * p + 1];
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-          out[i] = df_add(out[i], df_add(df_mul({lp.x, lp.y}, aL[i]), df_mul({mu.x, mu.y}, aM[i])));
-      }
-#pragma unroll
-      for (int i = 0; i < 3; ++i) kw[i] = df_to_double(out[i]) * (g.h / 72.0);
-    }
-    const long long node = ((long long)i1 * g.n2 + i2) * g.n3 + i3;
-#pragma unroll
-    for (int i = 0; i < CC; ++i) {
-      const long long x = (long long)bl * CC * n + i * n + node;
-      const double rr = a.rref[x] - kw[i];
+      const long long x = (long long)bl * n + zc + off[1][1];
+      const double rr = a.rref[x] - df_to_double(acc) * h12;
       a.rref[x] = rr;
       if (a.r) a.r[x] = (float)rr;
       lmax = fmax(lmax, fabs(rr));
+#pragma unroll
+      for (int x2 = 0; x2 < 3; ++x2)
+#pragma unroll
+        for (int y = 0; y < 3; ++y) {
+          w[0][x2][y] = w[1][x2][y];
+          w[1][x2][y] = w[2][x2][y];
+        }
+#pragma unroll
+      for (int o2 = 0; o2 < 2; ++o2)
+#pragma unroll
+        for (int o3 = 0; o3 < 2; ++o3) kap[0][o2][o3] = kap[1][o2][o3];
     }
   }
-  __shared__ double red_sh[32];
   const double bm = block_max(lmax, red_sh);
   if (threadIdx.x == 0) atomic_max_nonneg(a.into_rmax ? &a.sc[bl].rmax_bits : &a.sc[bl].tmax_bits, bm);
 }
@@ -257,7 +298,48 @@ __global__ void __launch_bounds__(KE_THREADS) k_replace_el(ReplaceArgs a) {
 }
 
 // ============================================================================ pointwise kernels
+// Four consecutive elements as vector accesses (16-byte aligned addresses)
+__device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
+  const double2 q0 = reinterpret_cast<const double2*>(p)[0], q1 = reinterpret_cast<const double2*>(p)[1];
+  v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+}
+__device__ __forceinline__ void st4(float* p, const float (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double (&v)[4]) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+
+// u64[i] <- u64[i] + u32[i] + alpha d[i] (u32[i] <- 0) for the elements [4 q, 4 q + 4); returns
+// their sum (left to right)
+template <typename T>
+__device__ __forceinline__ double fold4(double* u64, T* u32, const T* d, long long q, double al) {
+  const long long i = 4 * q;
+  double v[4];
+  T dd[4];
+  ld4(u64 + i, v);
+  ld4(d + i, dd);
+  if (u32) {
+    T uu[4];
+    ld4(u32 + i, uu);
+    const T z[4] = {(T)0, (T)0, (T)0, (T)0};
+    st4(u32 + i, z);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] += (double)uu[k];
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) v[k] += al * (double)dd[k];
+  st4(u64 + i, v);
+  return ((v[0] + v[1]) + v[2]) + v[3];
+}
+
 // Mixed-precision fold before a residual replacement: u64 += u32 + alpha d; u32 = 0; alpha = 0.
+// Four elements per thread and step where the slab length is a multiple of four.
 template <typename T>
 __global__ void k_fold(FoldArgs<T> a) {
   const int bl = blockIdx.y;
@@ -266,7 +348,13 @@ __global__ void k_fold(FoldArgs<T> a) {
   const double al = s.alpha;
   const long long m = (long long)a.c * a.n;
   const long long base = (long long)bl * m;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x) {
+  const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
+  if ((m & 3) == 0) {
+    for (long long q = t0; q < (m >> 2); q += st)
+      (void)fold4<T>(a.u64 + base, a.u32 ? a.u32 + base : nullptr, a.d + base, q, al);
+    return;
+  }
+  for (long long i = t0; i < m; i += st) {
     double v = a.u64[base + i];
     if (a.u32) {
       v += (double)a.u32[base + i];
@@ -380,16 +468,22 @@ __global__ void __launch_bounds__(256) k_final(FoldArgs<T> a) {
   const int comp = blockIdx.z;
   const double al = a.sc[bl].alpha;
   const long long base = ((long long)bl * a.c + comp) * a.n;
+  const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
   double sum = 0.0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.n; i += (long long)gridDim.x * blockDim.x) {
-    double v = a.u64[base + i];
-    if (a.u32) {
-      v += (double)a.u32[base + i];
-      a.u32[base + i] = (T)0;
+  if ((a.n & 3) == 0) {
+    for (long long q = t0; q < (a.n >> 2); q += st)
+      sum += fold4<T>(a.u64 + base, a.u32 ? a.u32 + base : nullptr, a.d + base, q, al);
+  } else {
+    for (long long i = t0; i < a.n; i += st) {
+      double v = a.u64[base + i];
+      if (a.u32) {
+        v += (double)a.u32[base + i];
+        a.u32[base + i] = (T)0;
+      }
+      v += al * (double)a.d[base + i];
+      a.u64[base + i] = v;
+      sum += v;
     }
-    v += al * (double)a.d[base + i];
-    a.u64[base + i] = v;
-    sum += v;
   }
   double bs = block_sum(sum, red_sh);
   if (threadIdx.x == 0)
@@ -406,44 +500,169 @@ __global__ void k_zero_mean(double* u, const double* part, int nparts, int c, lo
   }
   __syncthreads();
   double* uf = u + f * n;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    uf[i] -= mean;
+  const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
+  if ((n & 1) == 0) {
+    double2* u2 = reinterpret_cast<double2*>(uf);
+    for (long long i = t0; i < (n >> 1); i += st) {
+      double2 v = u2[i];
+      v.x -= mean;
+      v.y -= mean;
+      u2[i] = v;
+    }
+    return;
+  }
+  for (long long i = t0; i < n; i += st) uf[i] -= mean;
 }
 
-// Averaged flux / stress per (instance, load) with the element-mean gradient.  One thread per
-// element, all loads of an instance; fixed-order warp and block reductions (deterministic).
-template <int CC>
-__global__ void __launch_bounds__(256) k_average(AvgArgs a) {
+// Averaged flux / stress per (instance, load): sum over elements of C_e (eps_bar + the element-mean
+// strain of u), per block, finished by k_average_finish.
+// The sums are regrouped by node (the element-mean gradient is linear in the corner values).
+// With s = 1 / (4h) and sg(o) = 2 o - 1 per axis, the element-mean gradient of element e is
+// s sum_o sg(o) u(e + o), so sum_e kappa_e grad_e = s sum_nodes u(node) w(node) with
+// w(node) = sum_o kappa(node - o) sg(o) over the 8 elements around the node (o: the node's corner
+// in element node - o).  Elastic: w_lambda and w_mu likewise, and for the Mandel components
+//   sum_e sigma_kk(u)  = s sum_nodes (u . w_lambda + 2 u_k w_mu,k)            (k < 3)
+//   sum_e sigma_kl(u)  = s sqrt(2) sum_nodes (u_k w_mu,l + u_l w_mu,k)       (kl = 12, 13, 23).
+// The loads add (sum_e C_e) eps_bar, with sum_e kappa_e = sum_nodes (sum_o kappa(node - o)) / 8.
+// A thread walks KA_CZ nodes along axis 1 (the element planes z - 1 and z in registers), all
+// loads of the instance in chunks of LC; fixed-order warp and block reductions (deterministic).
+constexpr int KA_CZ = 8;
+template <int CC, int LC>
+__global__ void __launch_bounds__(256) k_average_nodes(AvgArgs a) {
+  constexpr int DIM = CC == 1 ? 3 : 6, NM = CC == 1 ? 1 : 2;
   __shared__ double mt[2 * 256];
-  __shared__ double wsum[8][48];  // [warp][load * dim + i]
+  __shared__ double wsum[8][48 + NM];  // [warp][load * DIM + i], then the material sums
   const Grid& g = a.g;
   const int b = blockIdx.y;
-  const int DIM = CC == 1 ? 3 : 6;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   load_material<double>(mt, a.mat, b);
   __syncthreads();
   int i1, i2, i3;
-  const bool valid = tile_node(g, i1, i2, i3);
-  const long long n = g.n;
-  for (int l = 0; l < a.L; ++l) {
-    double sig[6] = {0, 0, 0, 0, 0, 0};
+  const bool valid = tile_column_at(g, blockIdx.x, KA_CZ, i1, i2, i3);
+  const long long n = g.n, S = (long long)g.n2 * g.n3;
+  const uint8_t* ph = a.phase + (long long)b * n;
+  // element (z - o1, i2 - o2, i3 - o3) sits at plane offset eo[o2][o3] of element plane z - o1
+  long long eo[2][2] = {{0, 0}, {0, 0}};
+  if (valid) {
+    const int m2 = i2 ? i2 - 1 : g.n2 - 1, m3 = i3 ? i3 - 1 : g.n3 - 1;
+    eo[0][0] = (long long)i2 * g.n3 + i3;
+    eo[0][1] = (long long)i2 * g.n3 + m3;
+    eo[1][0] = (long long)m2 * g.n3 + i3;
+    eo[1][1] = (long long)m2 * g.n3 + m3;
+  }
+  const int zend = valid ? min(i1 + KA_CZ, g.n1) : 0;
+  double msum[NM];
+#pragma unroll
+  for (int m = 0; m < NM; ++m) msum[m] = 0.0;
+  for (int l0 = 0; l0 < a.L; l0 += LC) {
+    double acc[LC][DIM];
+#pragma unroll
+    for (int lc = 0; lc < LC; ++lc)
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) acc[lc][i] = 0.0;
     if (valid) {
-      const long long e = ((long long)i1 * g.n2 + i2) * g.n3 + i3;
-      const int p = a.phase[(long long)b * n + e];
-      const double* u = a.u64 + ((long long)b * a.L + l) * CC * n;
-      element_mean_flux<CC>(u, mt, p, g, i1, i2, i3, a.loads + l * DIM, sig);
+      double pm[NM][2][2], pc[NM][2][2];
+      const long long zm = (long long)(i1 ? i1 - 1 : g.n1 - 1) * S;
+#pragma unroll
+      for (int o2 = 0; o2 < 2; ++o2)
+#pragma unroll
+        for (int o3 = 0; o3 < 2; ++o3) {
+          const int p = ph[zm + eo[o2][o3]];
+#pragma unroll
+          for (int m = 0; m < NM; ++m) pm[m][o2][o3] = mt[2 * p + m];
+        }
+      for (int z = i1; z < zend; ++z) {
+        const long long zc = (long long)z * S;
+#pragma unroll
+        for (int o2 = 0; o2 < 2; ++o2)
+#pragma unroll
+          for (int o3 = 0; o3 < 2; ++o3) {
+            const int p = ph[zc + eo[o2][o3]];
+#pragma unroll
+            for (int m = 0; m < NM; ++m) pc[m][o2][o3] = mt[2 * p + m];
+          }
+        double w[NM][3];
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+          const double sm = (pm[m][0][0] + pm[m][0][1]) + (pm[m][1][0] + pm[m][1][1]);  // o1 = 1
+          const double sc = (pc[m][0][0] + pc[m][0][1]) + (pc[m][1][0] + pc[m][1][1]);  // o1 = 0
+          const double tot = sm + sc;
+          const double s2 = (pm[m][1][0] + pm[m][1][1]) + (pc[m][1][0] + pc[m][1][1]);  // o2 = 1
+          const double s3 = (pm[m][0][1] + pm[m][1][1]) + (pc[m][0][1] + pc[m][1][1]);  // o3 = 1
+          w[m][0] = sm - sc;
+          w[m][1] = 2.0 * s2 - tot;
+          w[m][2] = 2.0 * s3 - tot;
+          if (l0 == 0) msum[m] += tot;
+        }
+        const long long node = zc + eo[0][0];
+#pragma unroll
+        for (int lc = 0; lc < LC; ++lc) {
+          if (l0 + lc >= a.L) break;
+          const double* u = a.u64 + ((long long)b * a.L + l0 + lc) * CC * n + node;
+          if constexpr (CC == 1) {
+            const double v = u[0];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) acc[lc][k] = fma(v, w[0][k], acc[lc][k]);
+          } else {
+            const double v0 = u[0], v1 = u[n], v2 = u[2 * n];
+            const double tr = fma(v0, w[0][0], fma(v1, w[0][1], v2 * w[0][2]));
+            acc[lc][0] += fma(2.0 * v0, w[1][0], tr);
+            acc[lc][1] += fma(2.0 * v1, w[1][1], tr);
+            acc[lc][2] += fma(2.0 * v2, w[1][2], tr);
+            acc[lc][3] += fma(v0, w[1][1], v1 * w[1][0]);
+            acc[lc][4] += fma(v0, w[1][2], v2 * w[1][0]);
+            acc[lc][5] += fma(v1, w[1][2], v2 * w[1][1]);
+          }
+        }
+#pragma unroll
+        for (int m = 0; m < NM; ++m)
+#pragma unroll
+          for (int o2 = 0; o2 < 2; ++o2)
+#pragma unroll
+            for (int o3 = 0; o3 < 2; ++o3) pm[m][o2][o3] = pc[m][o2][o3];
+      }
     }
-    for (int i = 0; i < DIM; ++i) {
-      double v = sig[i];
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) wsum[warp][l * DIM + i] = v;
+#pragma unroll
+    for (int lc = 0; lc < LC; ++lc) {
+      if (l0 + lc >= a.L) break;
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) {
+        double v = acc[lc][i];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) wsum[warp][(l0 + lc) * DIM + i] = v;
+      }
     }
   }
+#pragma unroll
+  for (int m = 0; m < NM; ++m) {
+    double v = msum[m];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) wsum[warp][48 + m] = v;
+  }
   __syncthreads();
+  const int nw = blockDim.x >> 5;
+  double mb[NM];  // block sums of kappa (lambda, mu) over elements
+#pragma unroll
+  for (int m = 0; m < NM; ++m) {
+    double t = 0.0;
+    for (int w2 = 0; w2 < nw; ++w2) t += wsum[w2][48 + m];
+    mb[m] = 0.125 * t;
+  }
+  const double sc = 0.25 / g.h;
+  const double sq2 = 1.41421356237309504880;
   for (int q = threadIdx.x; q < a.L * DIM; q += blockDim.x) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += wsum[w][q];
-    a.part[((long long)b * gridDim.x + blockIdx.x) * (8 * 6) + q] = s;
+    double t = 0.0;
+    for (int w2 = 0; w2 < nw; ++w2) t += wsum[w2][q];
+    const int l = q / DIM, i = q % DIM;
+    const double* ld = a.loads + l * DIM;
+    double v;
+    if constexpr (CC == 1) {
+      v = sc * t + mb[0] * ld[i];
+    } else {
+      const double tr = ld[0] + ld[1] + ld[2];
+      v = i < 3 ? sc * t + mb[0] * tr + 2.0 * mb[1] * ld[i] : sq2 * sc * t + 2.0 * mb[1] * ld[i];
+    }
+    a.part[((long long)b * gridDim.x + blockIdx.x) * (8 * 6) + q] = v;
   }
 }
 
@@ -567,7 +786,7 @@ template <typename T> cudaError_t launch_ku(const StencilArgs<T>& a, cudaStream_
   return launch_pdl(k_ku<T, 1>, ku_task_grid(a.g, 1, a.BL), dim3(256), 0, s, a);
 }
 template <typename T> cudaError_t launch_init(const InitArgs<T>& a, int BL, cudaStream_t s) {
-  dim3 grid = node_grid(a.g, BL);
+  dim3 grid = node_grid(a.g, BL / a.L);
   if (a.c == 1) k_init<T, 1><<<grid, 256, 0, s>>>(a);
   else k_init<T, 3><<<grid, 256, 0, s>>>(a);
   return cudaGetLastError();
@@ -585,7 +804,8 @@ static int pw_blocks(long long m) {
 }
 cudaError_t launch_replace(const ReplaceArgs& a, int BL, cudaStream_t s) {
   if (a.c == 1) {
-    k_replace<1><<<node_grid(a.g, BL), 256, 0, s>>>(a);
+    const dim3 grid(((a.g.n3 + 31) / 32) * ((a.g.n2 + 7) / 8) * ((a.g.n1 + KR_CZ - 1) / KR_CZ), BL);
+    k_replace_col<<<grid, 256, 0, s>>>(a);
     return cudaGetLastError();
   }
   static bool attr_set = false;
@@ -626,9 +846,9 @@ template <typename T> cudaError_t launch_invdiag(const DiagArgs<T>& a, int B, cu
   return cudaGetLastError();
 }
 cudaError_t launch_average(const AvgArgs& a, int B, double* out, cudaStream_t s) {
-  dim3 grid = node_grid(a.g, B);
-  if (a.c == 1) k_average<1><<<grid, 256, 0, s>>>(a);
-  else k_average<3><<<grid, 256, 0, s>>>(a);
+  const dim3 grid(((a.g.n3 + 31) / 32) * ((a.g.n2 + 7) / 8) * ((a.g.n1 + KA_CZ - 1) / KA_CZ), B);
+  if (a.c == 1) k_average_nodes<1, 3><<<grid, 256, 0, s>>>(a);
+  else k_average_nodes<3, 6><<<grid, 256, 0, s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_average_finish<<<B, 256, 0, s>>>(out, a.part, grid.x, B, a.L, a.c == 1 ? 3 : 6, 1.0 / (double)a.g.n);
