@@ -13,7 +13,6 @@
 // (every thread writes the elements it read) and one bulk tensor store writes it to s_hat.
 // Loads of whole 128-byte rows replace the 16-byte-per-row accesses of a warp holding two
 // positions of 256-point lines.
-#include <cstdlib>
 #include <type_traits>
 #include "kargs.h"
 #include "fft_reg.cuh"
@@ -35,12 +34,11 @@ struct LineTmaArgs {
   int tiles;            // blocks per (instance, load)
   int* err;
   long long spin_limit;
-  int pf;               // L2 prefetch distance in blocks (0: none)
 };
 
 template <int N1>
-__global__ void __launch_bounds__(KL_P * RegSplit<N1>::G) k_line_tma(const __grid_constant__ LineTmaMaps maps,
-                                                                     const LineTmaArgs la) {
+__global__ void __launch_bounds__(KL_P * RegSplit<N1>::G, 768 / (KL_P * RegSplit<N1>::G))
+    k_line_tma(const __grid_constant__ LineTmaMaps maps, const LineTmaArgs la) {
   using C = float2;
   constexpr int G = RegSplit<N1>::G, V = RegSplit<N1>::V, VG = V / G, W = 32 / G;
   constexpr int NTH = KL_P * G;
@@ -50,19 +48,20 @@ __global__ void __launch_bounds__(KL_P * RegSplit<N1>::G) k_line_tma(const __gri
   __shared__ int s_abort;
   const LineArgs<float, __nv_bfloat16>& a = la.a;
   // tiles: r_hat (becomes s_hat) and s_old (becomes the exchange scratch), each N1 * 128
-  // bytes and 1024-byte aligned for the swizzle; Q (N1 * 32 bytes); twiddles (N1 complex)
+  // bytes and 1024-byte aligned for the swizzle; Q (N1 * 32 bytes)
   unsigned char* base = kl_raw + ((1024u - (sm_addr(kl_raw) & 1023u)) & 1023u);
   unsigned char* t_hat = base;
   unsigned char* t_old = base + N1 * 128;
   const __nv_bfloat16* t_q = reinterpret_cast<const __nv_bfloat16*>(base + 2 * N1 * 128);
-  C* tw1 = reinterpret_cast<C*>(base + 2 * N1 * 128 + N1 * 32);
+  // twiddles from the global table (L1-resident): without their shared copy three 256-thread
+  // blocks fit an SM
+  const C* __restrict__ tw1 = reinterpret_cast<const C*>(a.ft.tw1);
   const int tid = threadIdx.x;
   const int bl = blockIdx.y;
   const int tile = blockIdx.x;
   const int pos0 = tile * KL_P;
   const int M = a.g.n2 * a.g.n3h;
   const int b = bl / a.L;
-  for (int i = tid; i < N1; i += NTH) tw1[i] = reinterpret_cast<const C*>(a.ft.tw1)[i];
   if (tid == 0) {
     mbar_init(&bar, 1);
     s_abort = 0;
@@ -77,18 +76,6 @@ __global__ void __launch_bounds__(KL_P * RegSplit<N1>::G) k_line_tma(const __gri
     tma_load_3d(t_hat, &maps.hat, 2 * pos0, 0, bl, &bar);
     if (a.flexible) tma_load_3d(t_old, &maps.shat, 2 * pos0, 0, bl, &bar);
     tma_load_3d(const_cast<__nv_bfloat16*>(t_q), &maps.q, pos0, 0, a.q_inst_stride ? b : 0, &bar);
-  }
-  // L2 prefetch of the tiles of the block one wave later (la.pf blocks on in launch order)
-  if (la.pf > 0 && tid == 32) {
-    const long long tgt = (long long)bl * gridDim.x + tile + la.pf;
-    if (tgt < (long long)a.BL * gridDim.x) {
-      const int bl2 = (int)(tgt / gridDim.x), pos2 = (int)(tgt - (long long)bl2 * gridDim.x) * KL_P;
-      if (!a.sc[bl2].done) {
-        tma_prefetch_3d(&maps.hat, 2 * pos2, 0, bl2);
-        if (a.flexible) tma_prefetch_3d(&maps.shat, 2 * pos2, 0, bl2);
-        tma_prefetch_3d(&maps.q, pos2, 0, a.q_inst_stride ? bl2 / a.L : 0);
-      }
-    }
   }
   DotAcc<float> gam, rso;
   if (active) {
@@ -198,26 +185,14 @@ static CUresult encode_3d(CUtensorMap* m, CUtensorMapDataType dt, size_t esz, co
 template <int N1>
 static cudaError_t line_tma_n(const LineTmaMaps& maps, const LineTmaArgs& la, cudaStream_t st) {
   constexpr int NTH = KL_P * RegSplit<N1>::G;
-  const size_t smem = 1024 + 2 * (size_t)N1 * 128 + (size_t)N1 * 32 + (size_t)N1 * sizeof(float2);
+  const size_t smem = 1024 + 2 * (size_t)N1 * 128 + (size_t)N1 * 32;
   static bool attr = false;
-  static int resident = 0;  // blocks resident at once on the device
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_line_tma<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    int per_sm = 0, dev = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_line_tma<N1>, NTH, smem) != cudaSuccess ||
-        cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-      (void)cudaGetLastError();
-      per_sm = sms = 0;
-    }
-    resident = per_sm * sms;
     attr = true;
   }
-  LineTmaArgs lb = la;
-  const char* e = std::getenv("UNOCG_PF");  // 0: no L2 prefetch (for comparisons)
-  lb.pf = (e && std::atoi(e) == 0) ? 0 : resident;
-  return launch_pdl(k_line_tma<N1>, dim3(la.tiles, la.a.BL), dim3(NTH), smem, st, maps, lb);
+  return launch_pdl(k_line_tma<N1>, dim3(la.tiles, la.a.BL), dim3(NTH), smem, st, maps, la);
 }
 
 cudaError_t launch_line_tma(const LineArgs<float, __nv_bfloat16>& a, int* err, long long spin_limit, cudaStream_t st) {

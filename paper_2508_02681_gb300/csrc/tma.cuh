@@ -75,13 +75,6 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
-// L2 prefetch of the box at (c0, c1, c2) of a 3D tensor map (no shared memory, no completion)
-__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap* map, int c0, int c1, int c2) {
-  asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(
-                   reinterpret_cast<uint64_t>(map)),
-               "r"(c0), "r"(c1), "r"(c2)
-               : "memory");
-}
 // Byte offset of the 8-byte element (row r, column p) of a shared tile with 128-byte rows written
 // by a TMA copy with 128-byte swizzle (tile base 1024-byte aligned): the 16-byte chunk index of
 // the column is XORed with the row index modulo 8.
