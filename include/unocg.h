@@ -123,7 +123,7 @@ const char* unocg_last_error(const unocg_ctx* ctx);
 
 /* Tuning of the periodic solver: radix_order of the shared-memory Stockham plans (0: radix 8,
    4, 2, then 3, 5; 1: radix 4, 2, 3, 5; 2: radix 5, 3, then 4, 2; the register FFT passes of
-   power-of-two axes have no radix choice) and the loop driver that use_graph = 3 takes (1 graph,
+   axes of 2^k and 3 x 2^k points have no radix choice) and the loop driver that use_graph = 3 takes (1 graph,
    2 persistent kernel when it fits).  Invalidates the captured graph.                       */
 int unocg_set_tuning(unocg_ctx* ctx, int radix_order, int path);
 /* Autotuner (batched solves, config sweeps): times `reps` solves of `opts` (after one warm-up

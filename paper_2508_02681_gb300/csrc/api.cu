@@ -705,7 +705,7 @@ static cudaError_t enq_pre(unocg_ctx* ctx, cudaStream_t s, const Plan& pl, const
   return enq_residual_check<T>(ctx, s, ctl, 0, pl.o.precond);
 }
 
-// TMA-staged axis-1 pass of the mixed-precision loop (c = 1, power-of-two N1 up to 256);
+// TMA-staged axis-1 pass of the mixed-precision loop (c = 1, N1 of 2^k or 3 x 2^k points up to 256);
 // UNOCG_LINE_TMA=0 at run time keeps the register-FFT pass (for comparisons)
 static bool line_tma_on(const unocg_ctx* ctx) {
   static int env = -2;

@@ -1,4 +1,4 @@
-// Register-resident line FFTs of compile-time power-of-two length, for the transform passes of
+// Register-resident line FFTs of compile-time length 2^k or 3 x 2^k, for the transform passes of
 // the UNO preconditioner (Algorithm 2) on grids whose axes are 16..256 points long.
 //
 // A line of N = V * G complex values is held by G cooperating threads of one warp, V values
@@ -65,20 +65,76 @@ template <int DIR, typename C> __device__ __forceinline__ void dft16(C* v) {
   }
 }
 
+// cos(2 pi k / 24), k any integer (multiples of 15 degrees)
+__host__ __device__ constexpr double cos24_q(int k) {  // 0 <= k <= 6
+  return k == 0 ? 1.0 : k == 1 ? 0.96592582628906828675 : k == 2 ? 0.86602540378443864676
+       : k == 3 ? 0.70710678118654752440 : k == 4 ? 0.5 : k == 5 ? 0.25881904510252076235 : 0.0;
+}
+__host__ __device__ constexpr double cos24(int k) {
+  const int m = ((k % 24) + 24) % 24, r = m > 12 ? 24 - m : m;  // 0 <= r <= 12
+  return r <= 6 ? cos24_q(r) : -cos24_q(12 - r);
+}
+
+// radix 3 M (M = 4, 8), natural order in and out: M-point DFTs of the samples a, a + 3, ...
+// (a < 3), twiddles W_3M^(a b), 3-point DFTs across a.  With n = a + 3 m and k = b + M c:
+//   X[b + M c] = sum_a W_3^(a c) W_3M^(a b) sum_m x[a + 3 m] W_M^(m b)
+template <int DIR, int M, typename C> __device__ __forceinline__ void dft3m(C* v) {
+  using T = decltype(v[0].x);
+  constexpr int N = 3 * M, S = 24 / N;  // W_N^m = W_24^(S m)
+  C y[3][M];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int m = 0; m < M; ++m) y[a][m] = v[a + 3 * m];
+    if constexpr (M == 4) dft4<DIR>(y[a]);
+    else dft8<DIR>(y[a]);
+  }
+#pragma unroll
+  for (int a = 1; a < 3; ++a)
+#pragma unroll
+    for (int b = 1; b < M; ++b) {
+      // W_N^(a b) = cos(2 pi a b / N) -/+ i sin(2 pi a b / N) (forward / inverse)
+      const T cr = (T)cos24(S * a * b), si = (T)cos24(S * a * b - 6);
+      const T sg = DIR < 0 ? -si : si;
+      const C x = y[a][b];
+      y[a][b] = mk<T>(x.x * cr - x.y * sg, x.x * sg + x.y * cr);
+    }
+#pragma unroll
+  for (int b = 0; b < M; ++b) {
+    C t[3] = {y[0][b], y[1][b], y[2][b]};
+    dft3<DIR>(t);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v[b + M * c] = t[c];
+  }
+}
+
 template <int R, int DIR, typename C> __device__ __forceinline__ void dft_pow2(C* v) {
   if constexpr (R == 2) dft2<DIR>(v);
   else if constexpr (R == 4) dft4<DIR>(v);
   else if constexpr (R == 8) dft8<DIR>(v);
   else if constexpr (R == 16) dft16<DIR>(v);
+  else if constexpr (R == 12) dft3m<DIR, 4>(v);
+  else if constexpr (R == 24) dft3m<DIR, 8>(v);
 }
 
-// split N = V * G with G | V, G <= 16, V <= 16
+// split N = V * G with G a power of two, G | V, G <= 16, V <= 24 (V = 12, 24 for the axes of
+// 3 x 2^k points)
 template <int N> struct RegSplit;
 template <> struct RegSplit<16> { static constexpr int V = 4, G = 4; };
+template <> struct RegSplit<24> { static constexpr int V = 12, G = 2; };
 template <> struct RegSplit<32> { static constexpr int V = 8, G = 4; };
+template <> struct RegSplit<48> { static constexpr int V = 12, G = 4; };
 template <> struct RegSplit<64> { static constexpr int V = 8, G = 8; };
+template <> struct RegSplit<96> { static constexpr int V = 24, G = 4; };
 template <> struct RegSplit<128> { static constexpr int V = 16, G = 8; };
+template <> struct RegSplit<192> { static constexpr int V = 24, G = 8; };
 template <> struct RegSplit<256> { static constexpr int V = 16, G = 16; };
+
+// threads per line of the split of n (0: no register split for n), for host-side grid sizes
+__host__ __device__ constexpr int reg_split_g(int n) {
+  return n == 16 ? 4 : n == 24 ? 2 : n == 32 ? 4 : n == 48 ? 4 : n == 64 ? 8 : n == 96 ? 4 : n == 128 ? 8
+       : n == 192 ? 8 : n == 256 ? 16 : 0;
+}
 
 template <int N> __device__ __forceinline__ int reg_slot(int k1, int t) {
   constexpr int V = RegSplit<N>::V, G = RegSplit<N>::G, VG = V / G;

@@ -1,5 +1,6 @@
 // Register-FFT versions of the three transform passes of UNO-CG (Algorithm 2), for grids whose
-// axes are powers of two (planes N2 = N3 in {32, 64, 128}, axis 1 in {16, ..., 256}).  Same
+// axes are 2^k or 3 x 2^k points (planes N2 = N3 in {32, 48, 64, 96, 128, 192}, axis 1 in
+// {16, ..., 256}).  Same
 // arguments, data layouts and CG bookkeeping as the shared-memory Stockham passes in
 // fft_kernels.cuh, which remain the path for every other grid.
 //
@@ -35,10 +36,16 @@ template <typename T, int N2, int N3> struct PlaneReg {
   static constexpr int NCG = (n3h + CW - 1) / CW;      // column groups
   static constexpr int NRG = N2 / RPW;                 // row groups
   static constexpr int P = pitch_reg(n3h, NCG * CW);   // plane pitch (complex), = 4 mod 16
-  static constexpr int NW = NCG > (NRG < 16 ? NRG : 16) ? NCG : (NRG < 16 ? NRG : 16);
+  // 24 values per thread (axes of 3 x 2^k points): at most 16 warps, the row and column groups
+  // spread evenly over them (192^2: 25 column groups on 13 warps)
+  static constexpr bool wide = V2 > 16 || V3 > 16;
+  static constexpr int WORK = NCG > NRG ? NCG : NRG, ROUNDS = (WORK + 15) / 16;
+  static constexpr int NW = wide ? (WORK + ROUNDS - 1) / ROUNDS
+                                 : (NCG > (NRG < 16 ? NRG : 16) ? NCG : (NRG < 16 ? NRG : 16));
   static constexpr size_t smem = ((size_t)N2 * P + Nh + N2 + N3) * sizeof(cplx<T>);
+  static constexpr bool fits = smem <= 220 * 1024;
   // first-group data requested with the loop state; off where it would exceed the registers
-  static constexpr bool prefetch = !(sizeof(T) == 8 && N2 >= 128);
+  static constexpr bool prefetch = !(sizeof(T) == 8 && N2 >= 128) && !wide;
 };
 
 }  // namespace
@@ -447,8 +454,11 @@ constexpr bool pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n 
 template <typename T> size_t plane_reg_smem(int n) {
   switch (n) {
     case 32: return PlaneReg<T, 32, 32>::smem;
+    case 48: return PlaneReg<T, 48, 48>::smem;
     case 64: return PlaneReg<T, 64, 64>::smem;
+    case 96: return PlaneReg<T, 96, 96>::smem;
     case 128: return PlaneReg<T, 128, 128>::smem;
+    case 192: return PlaneReg<T, 192, 192>::smem;
     default: return 0;
   }
 }
@@ -456,9 +466,25 @@ template <typename T> size_t plane_reg_smem(int n) {
 template <typename T, int N, typename Args, bool FWD>
 cudaError_t plane_reg_launch(const Args& a, cudaStream_t s) {
   using PR = PlaneReg<T, N, N>;
-  dim3 grid(a.c * a.g.n1, a.BL);
-  if constexpr (FWD) return launch_reg(k_plane_fwd_reg<T, N, N>, grid, PR::NW * 32, PR::smem, a, s);
-  else return launch_reg(k_plane_inv_reg<T, N, N>, grid, PR::NW * 32, PR::smem, a, s);
+  if constexpr (!PR::fits) {
+    return cudaErrorInvalidValue;  // plane_reg_ok refuses it
+  } else {
+    dim3 grid(a.c * a.g.n1, a.BL);
+    if constexpr (FWD) return launch_reg(k_plane_fwd_reg<T, N, N>, grid, PR::NW * 32, PR::smem, a, s);
+    else return launch_reg(k_plane_inv_reg<T, N, N>, grid, PR::NW * 32, PR::smem, a, s);
+  }
+}
+
+template <typename T, typename Args, bool FWD> cudaError_t plane_reg_dispatch(const Args& a, cudaStream_t s) {
+  switch (a.g.n2) {
+    case 32: return plane_reg_launch<T, 32, Args, FWD>(a, s);
+    case 48: return plane_reg_launch<T, 48, Args, FWD>(a, s);
+    case 64: return plane_reg_launch<T, 64, Args, FWD>(a, s);
+    case 96: return plane_reg_launch<T, 96, Args, FWD>(a, s);
+    case 128: return plane_reg_launch<T, 128, Args, FWD>(a, s);
+    case 192: return plane_reg_launch<T, 192, Args, FWD>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
@@ -467,46 +493,39 @@ bool plane_reg_ok(const Grid& g, int elem_bytes) {
 #ifdef UNOCG_NO_REG_FFT
   return false;
 #endif
-  if (g.n2 != g.n3 || !pow2_in(g.n2, 32, 128)) return false;
+  if (g.n2 != g.n3) return false;
+  if (!(pow2_in(g.n2, 32, 128) || g.n2 == 48 || g.n2 == 96 || g.n2 == 192)) return false;
   const size_t smem = elem_bytes == 16 ? plane_reg_smem<double>(g.n2) : plane_reg_smem<float>(g.n2);
   return smem > 0 && smem <= 220 * 1024;
 }
 
 template <typename T> cudaError_t launch_plane_fwd_reg(const PlaneFwdArgs<T>& a, cudaStream_t s) {
-  switch (a.g.n2) {
-    case 32: return plane_reg_launch<T, 32, PlaneFwdArgs<T>, true>(a, s);
-    case 64: return plane_reg_launch<T, 64, PlaneFwdArgs<T>, true>(a, s);
-    case 128: return plane_reg_launch<T, 128, PlaneFwdArgs<T>, true>(a, s);
-    default: return cudaErrorInvalidValue;
-  }
+  return plane_reg_dispatch<T, PlaneFwdArgs<T>, true>(a, s);
 }
 template <typename T> cudaError_t launch_plane_inv_reg(const PlaneInvArgs<T>& a, cudaStream_t s) {
-  switch (a.g.n2) {
-    case 32: return plane_reg_launch<T, 32, PlaneInvArgs<T>, false>(a, s);
-    case 64: return plane_reg_launch<T, 64, PlaneInvArgs<T>, false>(a, s);
-    case 128: return plane_reg_launch<T, 128, PlaneInvArgs<T>, false>(a, s);
-    default: return cudaErrorInvalidValue;
-  }
+  return plane_reg_dispatch<T, PlaneInvArgs<T>, false>(a, s);
 }
 template cudaError_t launch_plane_fwd_reg<float>(const PlaneFwdArgs<float>&, cudaStream_t);
 template cudaError_t launch_plane_fwd_reg<double>(const PlaneFwdArgs<double>&, cudaStream_t);
 template cudaError_t launch_plane_inv_reg<float>(const PlaneInvArgs<float>&, cudaStream_t);
 template cudaError_t launch_plane_inv_reg<double>(const PlaneInvArgs<double>&, cudaStream_t);
 
-// axis 1: N1 in 16..256 for c = 1; up to 64 for c = 3 (three components of V values each
-// stay in registers, beyond that they would spill)
+// axis 1: N1 in 16..256 (2^k, and 48, 96, 192) for c = 1; 2^k up to 64 for c = 3 (three
+// components of V values each stay in registers, beyond that they would spill); the 24-value
+// splits (96, 192) in FP32 only
 bool line_reg_ok(const Grid& g, int c, int elem_bytes) {
 #ifdef UNOCG_NO_REG_FFT
   return false;
 #endif
-  (void)elem_bytes;
-  if (!pow2_in(g.n1, 16, 256)) return false;
-  return c == 1 || g.n1 <= 64;
+  const int n = g.n1;
+  if (!(pow2_in(n, 16, 256) || n == 48 || n == 96 || n == 192)) return false;
+  if ((n == 96 || n == 192) && elem_bytes == 16) return false;
+  return c == 1 || (n <= 64 && n != 48);
 }
 
 int line_reg_blocks_x(const Grid& g) {
-  if (!pow2_in(g.n1, 16, 256)) return 0;
-  int G = g.n1 <= 32 ? 4 : (g.n1 <= 128 ? 8 : 16);
+  const int G = reg_split_g(g.n1);
+  if (G == 0) return 0;
   const int per_block = kLineRegWarps * (32 / G);
   const int M = g.n2 * g.n3h;
   return (M + per_block - 1) / per_block;
@@ -525,7 +544,16 @@ cudaError_t line_reg_cc(const LineArgs<T, QT>& a, cudaStream_t s) {
   switch (a.g.n1) {
     case 16: return line_reg_n<T, QT, CC, 16, MODE>(a, s);
     case 32: return line_reg_n<T, QT, CC, 32, MODE>(a, s);
+    case 48:
+      if constexpr (CC == 3) return cudaErrorInvalidValue;
+      else return line_reg_n<T, QT, CC, 48, MODE>(a, s);
     case 64: return line_reg_n<T, QT, CC, 64, MODE>(a, s);
+    case 96:
+      if constexpr (CC == 3 || sizeof(T) == 8) return cudaErrorInvalidValue;
+      else return line_reg_n<T, QT, CC, 96, MODE>(a, s);
+    case 192:
+      if constexpr (CC == 3 || sizeof(T) == 8) return cudaErrorInvalidValue;
+      else return line_reg_n<T, QT, CC, 192, MODE>(a, s);
     case 128:
       if constexpr (CC == 3) return cudaErrorInvalidValue;
       else return line_reg_n<T, QT, CC, 128, MODE>(a, s);

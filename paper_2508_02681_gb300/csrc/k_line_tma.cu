@@ -36,8 +36,18 @@ struct LineTmaArgs {
   long long spin_limit;
 };
 
+// shared memory of one block (1024-byte alignment slack, r_hat and s_old tiles, Q tile) and the
+// blocks per SM the launch bounds ask for: at most 24 warps, and what the 228 KB of shared memory
+// per SM hold (1 KB reserved per block)
+template <int N1> constexpr size_t kl_smem_bytes() { return 1024 + 2 * (size_t)N1 * 128 + (size_t)N1 * 32; }
+template <int N1> constexpr int kl_min_blocks() {
+  constexpr int by_threads = 768 / (KL_P * RegSplit<N1>::G);
+  constexpr int by_smem = (int)(233472 / (kl_smem_bytes<N1>() + 1024));
+  return by_threads < by_smem ? by_threads : by_smem;
+}
+
 template <int N1>
-__global__ void __launch_bounds__(KL_P * RegSplit<N1>::G, 768 / (KL_P * RegSplit<N1>::G))
+__global__ void __launch_bounds__(KL_P * RegSplit<N1>::G, kl_min_blocks<N1>())
     k_line_tma(const __grid_constant__ LineTmaMaps maps, const LineTmaArgs la) {
   using C = float2;
   constexpr int G = RegSplit<N1>::G, V = RegSplit<N1>::V, VG = V / G, W = 32 / G;
@@ -164,7 +174,9 @@ __global__ void __launch_bounds__(KL_P * RegSplit<N1>::G, 768 / (KL_P * RegSplit
 // ---------------------------------------------------------------- host side
 bool line_tma_supported(const Grid& g, int c) {
   if (c != 1) return false;
-  if (!(g.n1 == 16 || g.n1 == 32 || g.n1 == 64 || g.n1 == 128 || g.n1 == 256)) return false;
+  if (!(g.n1 == 16 || g.n1 == 32 || g.n1 == 48 || g.n1 == 64 || g.n1 == 96 || g.n1 == 128 || g.n1 == 192 ||
+        g.n1 == 256))
+    return false;
   const long long M = (long long)g.n2 * g.n3h;
   if (M % 8 != 0) return false;  // 16-byte row strides of the Q and spectrum tensors
   return tensor_map_encoder() != nullptr;
@@ -185,7 +197,7 @@ static CUresult encode_3d(CUtensorMap* m, CUtensorMapDataType dt, size_t esz, co
 template <int N1>
 static cudaError_t line_tma_n(const LineTmaMaps& maps, const LineTmaArgs& la, cudaStream_t st) {
   constexpr int NTH = KL_P * RegSplit<N1>::G;
-  const size_t smem = 1024 + 2 * (size_t)N1 * 128 + (size_t)N1 * 32;
+  const size_t smem = kl_smem_bytes<N1>();
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_line_tma<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -215,8 +227,11 @@ cudaError_t launch_line_tma(const LineArgs<float, __nv_bfloat16>& a, int* err, l
   switch (g.n1) {
     case 16: return line_tma_n<16>(maps, la, st);
     case 32: return line_tma_n<32>(maps, la, st);
+    case 48: return line_tma_n<48>(maps, la, st);
     case 64: return line_tma_n<64>(maps, la, st);
+    case 96: return line_tma_n<96>(maps, la, st);
     case 128: return line_tma_n<128>(maps, la, st);
+    case 192: return line_tma_n<192>(maps, la, st);
     case 256: return line_tma_n<256>(maps, la, st);
     default: return cudaErrorInvalidValue;
   }
