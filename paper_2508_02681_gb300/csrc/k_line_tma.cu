@@ -173,6 +173,7 @@ __global__ void __launch_bounds__(KL_P * RegSplit<N1>::G, kl_min_blocks<N1>())
 
 // ---------------------------------------------------------------- host side
 bool line_tma_supported(const Grid& g, int c) {
+  if (c == 3) return line_tma3_supported(g);
   if (c != 1) return false;
   if (!(g.n1 == 16 || g.n1 == 32 || g.n1 == 48 || g.n1 == 64 || g.n1 == 96 || g.n1 == 128 || g.n1 == 192 ||
         g.n1 == 256))
@@ -208,6 +209,7 @@ static cudaError_t line_tma_n(const LineTmaMaps& maps, const LineTmaArgs& la, cu
 }
 
 cudaError_t launch_line_tma(const LineArgs<float, __nv_bfloat16>& a, int* err, long long spin_limit, cudaStream_t st) {
+  if (a.c == 3) return launch_line_tma3(a, err, spin_limit, st);
   const Grid& g = a.g;
   const cuuint64_t M = (cuuint64_t)g.n2 * g.n3h;
   const int Bq = a.q_inst_stride ? a.BL / a.L : 1;

@@ -125,11 +125,14 @@ bool plane_cl_ok(const Grid& g);
 cudaError_t launch_plane_fwd_cl(const PlaneFwdArgs<float>& a, cudaStream_t s);
 cudaError_t launch_plane_inv_cl(const PlaneInvArgs<float>& a, cudaStream_t s);
 
-// TMA-staged axis-1 pass of the mixed-precision loop, c = 1 (k_line_tma.cu)
+// TMA-staged axis-1 pass of the mixed-precision loop, c = 1 and 3 (k_line_tma.cu)
 bool line_tma_supported(const Grid& g, int c);
 int line_tma_blocks_x(const Grid& g);
 template <typename T, typename QT> struct LineArgs;
 cudaError_t launch_line_tma(const LineArgs<float, __nv_bfloat16>& a, int* err, long long spin_limit, cudaStream_t st);
+// the same for c = 3, N1 in {16, 32, 64} (k_line_tma3.cu); launch_line_tma forwards c = 3 here
+bool line_tma3_supported(const Grid& g);
+cudaError_t launch_line_tma3(const LineArgs<float, __nv_bfloat16>& a, int* err, long long spin_limit, cudaStream_t st);
 
 template <typename T> struct InitArgs {
   Grid g;
