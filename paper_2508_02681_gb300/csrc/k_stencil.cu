@@ -180,6 +180,21 @@ __global__ void __launch_bounds__(256) k_true_res(TrueResArgs<T> a) {
 // the FP32 inputs are exact, the stencil coefficients are integers (thermal: 12 x the unit-cube
 // Laplacian, elastic: 72 x Klam / Kmu) times the phase constants as pairs, and the result is
 // rounded to FP64 once per node.
+// After the loop, a pair whose last residual check followed a replacement has had no step since
+// (the replacement folded u32 + alpha d into u64 and cleared both): K w = 0, and the final report
+// needs only max |rref|, taken here over the pair's field by all blocks of its row of the grid.
+__device__ __forceinline__ bool replace_w_zero(const ReplaceArgs& a, int bl) {
+  return !a.only_pending && a.sc[bl].just_replaced && a.sc[bl].done;
+}
+__device__ __forceinline__ double rref_max_share(const ReplaceArgs& a, int bl, double* red_sh) {
+  const long long m = (long long)a.c * a.g.n;
+  const double* x = a.rref + (long long)bl * m;
+  double v = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x)
+    v = fmax(v, fabs(x[i]));
+  return block_max(v, red_sh);
+}
+
 // Thermal replacement as a march along axis 1 (each w formed once per node): a thread walks
 // KR_CZ nodes of one (i2, i3) column with the 3 x 3 neighbourhoods of w = u32 + alpha d on the planes z - 1, z, z + 1 and the
 // conductivities of the element planes z - 1, z in registers, all as float pairs.  For the
@@ -199,6 +214,11 @@ __global__ void __launch_bounds__(256) k_replace_col(ReplaceArgs a) {
   }
   __syncthreads();
   if (a.only_pending && !a.sc[bl].need_replace) return;
+  if (replace_w_zero(a, bl)) {
+    const double bm = rref_max_share(a, bl, red_sh);
+    if (threadIdx.x == 0) atomic_max_nonneg(a.into_rmax ? &a.sc[bl].rmax_bits : &a.sc[bl].tmax_bits, bm);
+    return;
+  }
   const df32 al = df_from_double(a.sc[bl].alpha);
   int i1, i2, i3;
   double lmax = 0.0;
@@ -289,6 +309,11 @@ __global__ void __launch_bounds__(KE_THREADS) k_replace_el(ReplaceArgs a) {
   replace_elastic_consts(a.mat, bl / a.L, a.g.h, kc);
   __syncthreads();
   if (a.only_pending && !a.sc[bl].need_replace) return;
+  if (replace_w_zero(a, bl)) {
+    const double bm = rref_max_share(a, bl, red_sh);
+    if (threadIdx.x == 0) atomic_max_nonneg(a.into_rmax ? &a.sc[bl].rmax_bits : &a.sc[bl].tmax_bits, bm);
+    return;
+  }
   const long long off = (long long)bl * 3 * a.g.n;
   const double bm = replace_elastic_tile(a.g, a.phase + (long long)(bl / a.L) * a.g.n, a.u32 + off, a.d + off,
                                          df_from_double(a.sc[bl].alpha), a.rref + off, a.r ? a.r + off : nullptr, kc,
