@@ -281,6 +281,88 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PNW * 32) k_plane_in
   pdl_trigger();
 }
 
+// ---------------------------------------------------------------- row pass of 256^2 planes
+// Inverse axis 3 of 256 x 256 FP32 planes row by row, after the axis-2 column pass, fused with
+// the CG updates (the second half of the two-pass inverse transform).  A warp takes 4 rows (8
+// threads a row, the register line FFT of fft_reg.cuh), a block 32 rows of one plane: each warp
+// copies its rows of the half spectrum into shared memory in whole-row runs, untangles the real
+// spectrum pairwise (c2r_pair), transforms the 128-point half-length lines and updates u and d.
+// The rows of d and u are requested into L2 at the start.
+namespace {
+constexpr int RI_W = 8;                      // warps per block
+constexpr int RI_R = RI_W * PRPW;            // rows per block
+constexpr size_t kRowsInvSmem = (size_t)RI_R * PRP * sizeof(float2) + (size_t)(PNh + PN) * sizeof(float2);
+}  // namespace
+
+__global__ void __launch_bounds__(RI_W * 32) k_rows_inv256(PlaneInvArgs<float> a) {
+  using C = float2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* rowbuf = reinterpret_cast<C*>(smem_raw);  // [RI_R rows][PRP]
+  C* tw3h = rowbuf + RI_R * PRP;
+  C* tw3 = tw3h + PNh;
+  load_tw_reg<float>(tw3h, a.ft.tw3h, PNh);
+  load_tw_reg<float>(tw3, a.ft.tw3, PN);
+  constexpr int chunks = PN / RI_R;
+  const int bl = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int plane_id = blockIdx.x / chunks, ch = blockIdx.x - plane_id * chunks;
+  const int comp = plane_id / a.g.n1, i1 = plane_id - comp * a.g.n1;
+  const long long field = (long long)bl * a.c + comp;
+  const long long base = (field * a.g.n1 + i1) * (long long)(PN * PN);
+  const int rl = warp * PRPW + lane / PG3, g = lane % PG3;
+  const int row = ch * RI_R + rl;
+  if (!a.standalone) {  // each thread one 128-byte line of its row of d and of u
+    const long long o = base + (long long)row * PN + g * 32;
+    pf_l2(a.d + o);
+    pf_l2(a.u + o);
+  }
+  pdl_wait();
+  if (!a.standalone && a.sc[bl].done) return;
+  const float alpha = a.standalone ? 0.f : (float)a.sc[bl].alpha;
+  const float beta = a.standalone ? 0.f : (float)a.sc[bl].beta;
+  __syncthreads();  // twiddles
+  const C* in = a.shat + (field * a.g.n1 + i1) * (long long)(PN * Pn3h);
+#pragma unroll
+  for (int r = 0; r < PRPW; ++r) {
+    const int lr = warp * PRPW + r;
+    const C* src = in + (long long)(ch * RI_R + lr) * Pn3h;
+    C* dst = rowbuf + lr * PRP;
+#pragma unroll
+    for (int i = 0; i < (Pn3h + 31) / 32; ++i) {
+      const int k = lane + 32 * i;
+      if (k < Pn3h) dst[k] = src[k];
+    }
+  }
+  __syncwarp();
+  C* rs = rowbuf + rl * PRP;
+  for (int k = g; k <= PNh / 2; k += PG3) c2r_pair<float>(rs, k, PNh, tw3);
+  __syncwarp();
+  C v[PV3];
+#pragma unroll
+  for (int j = 0; j < PV3 / PG3; ++j)
+#pragma unroll
+    for (int k2 = 0; k2 < PG3; ++k2) v[j * PG3 + k2] = rs[scat_index<PNh>(g, j, k2)];
+  fft_dist_b<PNh, +1>(v, g, rs, 1, tw3h);
+  if (a.standalone) {
+    C* dst = reinterpret_cast<C*>(a.dst + base) + row * PNh;
+#pragma unroll
+    for (int n1 = 0; n1 < PV3; ++n1) dst[g + PG3 * n1] = v[n1];
+  } else {
+    C* d = reinterpret_cast<C*>(a.d + base) + row * PNh;
+    C* u = reinterpret_cast<C*>(a.u + base) + row * PNh;
+#pragma unroll
+    for (int n1 = 0; n1 < PV3; ++n1) {
+      const C dv = d[g + PG3 * n1];
+      C uu = u[g + PG3 * n1];
+      uu.x += alpha * dv.x;
+      uu.y += alpha * dv.y;
+      u[g + PG3 * n1] = uu;
+      d[g + PG3 * n1] = make_float2(v[n1].x + beta * dv.x, v[n1].y + beta * dv.y);
+    }
+  }
+  pdl_trigger();
+}
+
 // ---------------------------------------------------------------- host side
 bool plane_cl_ok(const Grid& g) {
 #ifdef UNOCG_NO_CLUSTER_PLANES
@@ -315,6 +397,23 @@ cudaError_t launch_plane_fwd_cl(const PlaneFwdArgs<float>& a, cudaStream_t s) {
 }
 cudaError_t launch_plane_inv_cl(const PlaneInvArgs<float>& a, cudaStream_t s) {
   return launch_cl(k_plane_inv_cl, kInvSmem, a, s);
+}
+
+bool rows_inv256_ok(const Grid& g) {
+#ifdef UNOCG_NO_CLUSTER_PLANES
+  return false;
+#endif
+  return g.n2 == PN && g.n3 == PN;
+}
+
+cudaError_t launch_rows_inv256(const PlaneInvArgs<float>& a, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_rows_inv256, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowsInvSmem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  return launch_pdl(k_rows_inv256, dim3(a.c * a.g.n1 * (PN / RI_R), a.BL), dim3(RI_W * 32), kRowsInvSmem, s, a);
 }
 
 }  // namespace unocg
