@@ -562,6 +562,8 @@ template <typename T> cudaError_t launch_plane_fwd(const PlaneFwdArgs<T>& a, cud
   const int eb = sizeof(cplx<T>);
   if (!a.rows && plane_reg_ok(a.g, eb)) return launch_plane_fwd_reg<T>(a, s);
   if (a.rows) {
+    if constexpr (sizeof(T) == 4)
+      if (rows_inv256_ok(a.g)) return launch_rows_fwd256(a, s);
     size_t smem = rows_smem(a.g, a.rows, eb);
     dim3 grid(a.c * a.g.n1 * (a.g.n2 / a.rows), a.BL);
     return launch_k(k_plane_fwd<T, 512>, grid, 512, smem, a, s);

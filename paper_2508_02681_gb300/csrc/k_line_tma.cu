@@ -13,6 +13,7 @@
 // (every thread writes the elements it read) and one bulk tensor store writes it to s_hat.
 // Loads of whole 128-byte rows replace the 16-byte-per-row accesses of a warp holding two
 // positions of 256-point lines.
+#include <cstdlib>
 #include <type_traits>
 #include "kargs.h"
 #include "fft_reg.cuh"
@@ -21,7 +22,15 @@
 
 namespace unocg {
 
-constexpr int KL_P = 16;  // positions per block (one 128-byte row of complex FP32)
+constexpr int KL_P = 16;  // positions per block (one 128-byte row of complex FP32), or 8 (64 bytes)
+
+// Byte offset of element (row r, column p) of a TMA tile of P complex FP32 per row, written with
+// the 128-byte swizzle (P = 16: chunk XOR r mod 8) or the 64-byte one (P = 8: the 16-byte chunk
+// index XOR bits 7..8 of the row's byte address, (r / 2) mod 4)
+template <int P> __device__ __forceinline__ uint32_t swz_off8(int r, int p) {
+  if constexpr (P == 16) return swz128_off8(r, p);
+  else return (uint32_t)(r * 64 + ((((p >> 1) ^ (r >> 1)) & 3) << 4) + ((p & 1) << 3));
+}
 
 struct alignas(64) LineTmaMaps {
   CUtensorMap hat;   // r_hat  [BL][N1][2M] floats, box {32, N1, 1}, 128-byte swizzle
@@ -39,37 +48,42 @@ struct LineTmaArgs {
 // shared memory of one block (1024-byte alignment slack, r_hat and s_old tiles, Q tile) and the
 // blocks per SM the launch bounds ask for: at most 24 warps, and what the 228 KB of shared memory
 // per SM hold (1 KB reserved per block)
-template <int N1> constexpr size_t kl_smem_bytes() { return 1024 + 2 * (size_t)N1 * 128 + (size_t)N1 * 32; }
-template <int N1> constexpr int kl_min_blocks() {
-  constexpr int by_threads = 768 / (KL_P * RegSplit<N1>::G);
-  constexpr int by_smem = (int)(233472 / (kl_smem_bytes<N1>() + 1024));
-  return by_threads < by_smem ? by_threads : by_smem;
+template <int N1, int P> constexpr size_t kl_smem_bytes() { return 1024 + 2 * (size_t)N1 * 8 * P + (size_t)N1 * 2 * P; }
+// blocks per SM the launch bounds ask for: at most 24 warps and what the 228 KB of shared memory
+// hold (1 KB reserved per block); 256-point lines in 8-position tiles keep at least 96 registers
+// (five blocks: no spills)
+template <int N1, int P> constexpr int kl_min_blocks() {
+  constexpr int by_threads = 768 / (P * RegSplit<N1>::G);
+  constexpr int by_smem = (int)(233472 / (kl_smem_bytes<N1, P>() + 1024));
+  constexpr int m = by_threads < by_smem ? by_threads : by_smem;
+  return (N1 == 256 && P == 8 && m > 5) ? 5 : m;
 }
 
-template <int N1>
-__global__ void __launch_bounds__(KL_P * RegSplit<N1>::G, kl_min_blocks<N1>())
+template <int N1, int P>
+__global__ void __launch_bounds__(P * RegSplit<N1>::G, kl_min_blocks<N1, P>())
     k_line_tma(const __grid_constant__ LineTmaMaps maps, const LineTmaArgs la) {
   using C = float2;
   constexpr int G = RegSplit<N1>::G, V = RegSplit<N1>::V, VG = V / G, W = 32 / G;
-  constexpr int NTH = KL_P * G;
+  constexpr int NTH = P * G;
+  constexpr int TB = N1 * 8 * P;  // bytes of one spectrum tile
   extern __shared__ unsigned char kl_raw[];
   __shared__ double red_sh[32];
   __shared__ __align__(8) uint64_t bar;
   __shared__ int s_abort;
   const LineArgs<float, __nv_bfloat16>& a = la.a;
-  // tiles: r_hat (becomes s_hat) and s_old (becomes the exchange scratch), each N1 * 128
-  // bytes and 1024-byte aligned for the swizzle; Q (N1 * 32 bytes)
+  // tiles: r_hat (becomes s_hat) and s_old (becomes the exchange scratch), each N1 rows of P
+  // complex, 1024-byte aligned for the swizzle; Q (N1 x P bf16)
   unsigned char* base = kl_raw + ((1024u - (sm_addr(kl_raw) & 1023u)) & 1023u);
   unsigned char* t_hat = base;
-  unsigned char* t_old = base + N1 * 128;
-  const __nv_bfloat16* t_q = reinterpret_cast<const __nv_bfloat16*>(base + 2 * N1 * 128);
+  unsigned char* t_old = base + TB;
+  const __nv_bfloat16* t_q = reinterpret_cast<const __nv_bfloat16*>(base + 2 * TB);
   // twiddles from the global table (L1-resident): without their shared copy three 256-thread
   // blocks fit an SM
   const C* __restrict__ tw1 = reinterpret_cast<const C*>(a.ft.tw1);
   const int tid = threadIdx.x;
   const int bl = blockIdx.y;
   const int tile = blockIdx.x;
-  const int pos0 = tile * KL_P;
+  const int pos0 = tile * P;
   const int M = a.g.n2 * a.g.n3h;
   const int b = bl / a.L;
   if (tid == 0) {
@@ -81,7 +95,7 @@ __global__ void __launch_bounds__(KL_P * RegSplit<N1>::G, kl_min_blocks<N1>())
   pdl_wait();  // r_hat, s_hat and the loop state come from the kernels before this one
   const bool active = !a.sc[bl].done;
   if (active && tid == 0) {
-    const uint32_t bytes = (uint32_t)(N1 * 128 * (a.flexible ? 2 : 1) + N1 * 32);
+    const uint32_t bytes = (uint32_t)(TB * (a.flexible ? 2 : 1) + N1 * 2 * P);
     mbar_expect_tx(&bar, bytes);
     tma_load_3d(t_hat, &maps.hat, 2 * pos0, 0, bl, &bar);
     if (a.flexible) tma_load_3d(t_old, &maps.shat, 2 * pos0, 0, bl, &bar);
@@ -105,14 +119,14 @@ __global__ void __launch_bounds__(KL_P * RegSplit<N1>::G, kl_min_blocks<N1>())
       const float sc = (float)a.scale;
       C v[V];
 #pragma unroll
-      for (int n1 = 0; n1 < V; ++n1) v[n1] = *reinterpret_cast<const C*>(t_hat + swz128_off8(g + G * n1, p));
+      for (int n1 = 0; n1 < V; ++n1) v[n1] = *reinterpret_cast<const C*>(t_hat + swz_off8<P>(g + G * n1, p));
       // Parseval partials: the thread's V products are summed in FP32 (their rounding stays below
       // that of the FP32 spectra themselves) and accumulated in the float-float pair
       if (a.flexible && on) {
         float part = 0.f;
 #pragma unroll
         for (int n1 = 0; n1 < V; ++n1) {
-          const C so = *reinterpret_cast<const C*>(t_old + swz128_off8(g + G * n1, p));
+          const C so = *reinterpret_cast<const C*>(t_old + swz_off8<P>(g + G * n1, p));
           part = fmaf(v[n1].x, so.x, fmaf(v[n1].y, so.y, part));
         }
         rso.add(wt * part);
@@ -128,7 +142,7 @@ __global__ void __launch_bounds__(KL_P * RegSplit<N1>::G, kl_min_blocks<N1>())
 #pragma unroll
           for (int k2 = 0; k2 < G; ++k2) {
             const int k1 = scat_index<N1>(g, j, k2), e = j * G + k2;
-            const float q = __bfloat162float(t_q[k1 * KL_P + p]) * sc;
+            const float q = __bfloat162float(t_q[k1 * P + p]) * sc;
             const C R = v[e];
             part = fmaf(q, fmaf(R.x, R.x, R.y * R.y), part);
             v[e] = make_float2(q * R.x, q * R.y);
@@ -137,7 +151,7 @@ __global__ void __launch_bounds__(KL_P * RegSplit<N1>::G, kl_min_blocks<N1>())
       }
       fft_dist_b<N1, +1>(v, g, scr, W, tw1);
 #pragma unroll
-      for (int n1 = 0; n1 < V; ++n1) *reinterpret_cast<C*>(t_hat + swz128_off8(g + G * n1, p)) = v[n1];
+      for (int n1 = 0; n1 < V; ++n1) *reinterpret_cast<C*>(t_hat + swz_off8<P>(g + G * n1, p)) = v[n1];
       fence_async_shared();
     }
     __syncthreads();
@@ -183,8 +197,17 @@ bool line_tma_supported(const Grid& g, int c) {
   return tensor_map_encoder() != nullptr;
 }
 
-int line_tma_blocks_x(const Grid& g) { return (int)(((long long)g.n2 * g.n3h + KL_P - 1) / KL_P); }
+// partial sums per (instance, load): one per block of the narrower tile (8 positions)
+int line_tma_blocks_x(const Grid& g) { return (int)(((long long)g.n2 * g.n3h + 7) / 8); }
 
+// positions per block: 16 (128-byte rows, 128-byte swizzle; the default) or 8 (64-byte rows,
+// 64-byte swizzle: half the shared memory per block, about twice the blocks per SM), selected by
+// UNOCG_LINE_P at every launch.  Measured per launch with three loads: 256^3 203.6 (16) against
+// 203.4 us (8), 192^3 83.4 against 97.6 us.
+static int line_tma_p(const Grid&) {
+  const char* e = std::getenv("UNOCG_LINE_P");
+  return (e && std::atoi(e) == 8) ? 8 : 16;
+}
 static CUresult encode_3d(CUtensorMap* m, CUtensorMapDataType dt, size_t esz, const void* ptr, cuuint64_t d0,
                           cuuint64_t d1, cuuint64_t d2, cuuint32_t b0, cuuint32_t b1, CUtensorMapSwizzle sw) {
   const cuuint64_t dims[3] = {d0, d1, d2};
@@ -195,17 +218,32 @@ static CUresult encode_3d(CUtensorMap* m, CUtensorMapDataType dt, size_t esz, co
                               sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
 }
 
-template <int N1>
+template <int N1, int P>
 static cudaError_t line_tma_n(const LineTmaMaps& maps, const LineTmaArgs& la, cudaStream_t st) {
-  constexpr int NTH = KL_P * RegSplit<N1>::G;
-  const size_t smem = kl_smem_bytes<N1>();
+  constexpr int NTH = P * RegSplit<N1>::G;
+  const size_t smem = kl_smem_bytes<N1, P>();
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_line_tma<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_line_tma<N1, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  return launch_pdl(k_line_tma<N1>, dim3(la.tiles, la.a.BL), dim3(NTH), smem, st, maps, la);
+  return launch_pdl(k_line_tma<N1, P>, dim3(la.tiles, la.a.BL), dim3(NTH), smem, st, maps, la);
+}
+
+template <int P>
+static cudaError_t line_tma_p_launch(const LineTmaMaps& maps, const LineTmaArgs& la, cudaStream_t st) {
+  switch (la.a.g.n1) {
+    case 16: return line_tma_n<16, P>(maps, la, st);
+    case 32: return line_tma_n<32, P>(maps, la, st);
+    case 48: return line_tma_n<48, P>(maps, la, st);
+    case 64: return line_tma_n<64, P>(maps, la, st);
+    case 96: return line_tma_n<96, P>(maps, la, st);
+    case 128: return line_tma_n<128, P>(maps, la, st);
+    case 192: return line_tma_n<192, P>(maps, la, st);
+    case 256: return line_tma_n<256, P>(maps, la, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_line_tma(const LineArgs<float, __nv_bfloat16>& a, int* err, long long spin_limit, cudaStream_t st) {
@@ -213,30 +251,22 @@ cudaError_t launch_line_tma(const LineArgs<float, __nv_bfloat16>& a, int* err, l
   const Grid& g = a.g;
   const cuuint64_t M = (cuuint64_t)g.n2 * g.n3h;
   const int Bq = a.q_inst_stride ? a.BL / a.L : 1;
+  const int P = line_tma_p(g);
+  const CUtensorMapSwizzle sw = P == 16 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
   LineTmaMaps maps;
-  if (encode_3d(&maps.hat, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, a.hat, 2 * M, g.n1, a.BL, 2 * KL_P, g.n1,
-                CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS ||
-      encode_3d(&maps.shat, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, a.shat, 2 * M, g.n1, a.BL, 2 * KL_P, g.n1,
-                CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS ||
-      encode_3d(&maps.q, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, a.Q, M, g.n1, Bq, KL_P, g.n1,
-                CU_TENSOR_MAP_SWIZZLE_NONE) != CUDA_SUCCESS)
+  if (encode_3d(&maps.hat, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, a.hat, 2 * M, g.n1, a.BL, 2 * P, g.n1, sw) !=
+          CUDA_SUCCESS ||
+      encode_3d(&maps.shat, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, a.shat, 2 * M, g.n1, a.BL, 2 * P, g.n1, sw) !=
+          CUDA_SUCCESS ||
+      encode_3d(&maps.q, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, a.Q, M, g.n1, Bq, P, g.n1, CU_TENSOR_MAP_SWIZZLE_NONE) !=
+          CUDA_SUCCESS)
     return cudaErrorInvalidValue;
   LineTmaArgs la{};
   la.a = a;
-  la.tiles = line_tma_blocks_x(g);
+  la.tiles = (int)((M + P - 1) / P);
   la.err = err;
   la.spin_limit = spin_limit;
-  switch (g.n1) {
-    case 16: return line_tma_n<16>(maps, la, st);
-    case 32: return line_tma_n<32>(maps, la, st);
-    case 48: return line_tma_n<48>(maps, la, st);
-    case 64: return line_tma_n<64>(maps, la, st);
-    case 96: return line_tma_n<96>(maps, la, st);
-    case 128: return line_tma_n<128>(maps, la, st);
-    case 192: return line_tma_n<192>(maps, la, st);
-    case 256: return line_tma_n<256>(maps, la, st);
-    default: return cudaErrorInvalidValue;
-  }
+  return P == 16 ? line_tma_p_launch<16>(maps, la, st) : line_tma_p_launch<8>(maps, la, st);
 }
 
 }  // namespace unocg

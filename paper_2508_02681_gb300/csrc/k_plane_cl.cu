@@ -363,6 +363,98 @@ __global__ void __launch_bounds__(RI_W * 32) k_rows_inv256(PlaneInvArgs<float> a
   pdl_trigger();
 }
 
+// Forward axis 3 of 256 x 256 FP32 planes row by row, before the axis-2 column pass, fused with
+// r <- r - alpha p and ||r||_inf (the first half of the two-pass forward transform; the last
+// block performs the residual check).  Same layout as k_rows_inv256: 4 rows per warp, 32 per
+// block; each row's half spectrum (129 values) is written in one run.
+__global__ void __launch_bounds__(RI_W * 32) k_rows_fwd256(PlaneFwdArgs<float> a) {
+  using C = float2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red_sh[32];
+  C* rowbuf = reinterpret_cast<C*>(smem_raw);  // [RI_R rows][PRP]
+  C* tw3h = rowbuf + RI_R * PRP;
+  C* tw3 = tw3h + PNh;
+  load_tw_reg<float>(tw3h, a.ft.tw3h, PNh);
+  load_tw_reg<float>(tw3, a.ft.tw3, PN);
+  constexpr int chunks = PN / RI_R;
+  const int bl = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int plane_id = blockIdx.x / chunks, ch = blockIdx.x - plane_id * chunks;
+  const int comp = plane_id / a.g.n1, i1 = plane_id - comp * a.g.n1;
+  const long long field = (long long)bl * a.c + comp;
+  const long long base = (field * a.g.n1 + i1) * (long long)(PN * PN);
+  const int rl = warp * PRPW + lane / PG3, g = lane % PG3;
+  const int row = ch * RI_R + rl;
+  pdl_wait();
+  bool active = true;
+  double alpha = 0.0;
+  if (!a.standalone) {
+    const CgScal& st = a.sc[bl];
+    active = !st.done && (!a.after_replace || st.need_replace);
+    alpha = a.after_replace ? 0.0 : st.alpha;
+  }
+  __syncthreads();  // twiddles
+  float lmax = 0.f;
+  if (active) {
+    C v[PV3];
+    if (a.standalone) {
+      const C* src = reinterpret_cast<const C*>(a.src + base) + row * PNh;
+#pragma unroll
+      for (int n1 = 0; n1 < PV3; ++n1) v[n1] = src[g + PG3 * n1];
+    } else {
+      C* r = reinterpret_cast<C*>(a.r + base) + row * PNh;
+      const C* p = reinterpret_cast<const C*>(a.p + base) + row * PNh;
+      const float al = (float)alpha;
+      C q[PV3];
+#pragma unroll
+      for (int n1 = 0; n1 < PV3; ++n1) {
+        v[n1] = r[g + PG3 * n1];
+        q[n1] = p[g + PG3 * n1];
+      }
+      if (alpha != 0.0) {
+#pragma unroll
+        for (int n1 = 0; n1 < PV3; ++n1) {
+          v[n1].x -= al * q[n1].x;
+          v[n1].y -= al * q[n1].y;
+          r[g + PG3 * n1] = v[n1];
+        }
+      }
+#pragma unroll
+      for (int n1 = 0; n1 < PV3; ++n1) lmax = fmaxf(lmax, fmaxf(fabsf(v[n1].x), fabsf(v[n1].y)));
+    }
+    C* rs = rowbuf + rl * PRP;
+    fft_dist_a<PNh, -1>(v, g, rs, 1, tw3h);
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < PV3 / PG3; ++j)
+#pragma unroll
+      for (int k2 = 0; k2 < PG3; ++k2) rs[scat_index<PNh>(g, j, k2)] = v[j * PG3 + k2];
+    __syncwarp();
+    for (int k = g; k <= PNh / 2; k += PG3) r2c_pair<float>(rs, k, PNh, tw3);
+    __syncwarp();
+    C* out = a.hat + (field * a.g.n1 + i1) * (long long)(PN * Pn3h);
+#pragma unroll
+    for (int r = 0; r < PRPW; ++r) {
+      const int lr = warp * PRPW + r;
+      const C* src = rowbuf + lr * PRP;
+      C* dst = out + (long long)(ch * RI_R + lr) * Pn3h;
+#pragma unroll
+      for (int i = 0; i < (Pn3h + 31) / 32; ++i) {
+        const int k = lane + 32 * i;
+        if (k < Pn3h) dst[k] = src[k];
+      }
+    }
+  }
+  pdl_trigger();
+  if (a.standalone) return;
+  const double bmax = block_max_t(lmax, red_sh);
+  if (threadIdx.x == 0 && active) atomic_max_nonneg(&a.sc[bl].rmax_bits, bmax);
+  if (last_block(a.ticket)) {
+    residual_decision(a.sc, a.BL, a.ctl, a.after_replace);
+    if (threadIdx.x == 0) *a.ticket = 0u;
+  }
+}
+
 // ---------------------------------------------------------------- host side
 bool plane_cl_ok(const Grid& g) {
 #ifdef UNOCG_NO_CLUSTER_PLANES
@@ -414,6 +506,16 @@ cudaError_t launch_rows_inv256(const PlaneInvArgs<float>& a, cudaStream_t s) {
     attr = true;
   }
   return launch_pdl(k_rows_inv256, dim3(a.c * a.g.n1 * (PN / RI_R), a.BL), dim3(RI_W * 32), kRowsInvSmem, s, a);
+}
+
+cudaError_t launch_rows_fwd256(const PlaneFwdArgs<float>& a, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_rows_fwd256, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowsInvSmem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  return launch_pdl(k_rows_fwd256, dim3(a.c * a.g.n1 * (PN / RI_R), a.BL), dim3(RI_W * 32), kRowsInvSmem, s, a);
 }
 
 }  // namespace unocg

@@ -127,6 +127,8 @@ cudaError_t launch_plane_inv_cl(const PlaneInvArgs<float>& a, cudaStream_t s);
 // inverse axis-3 row pass of 256 x 256 FP32 planes with the CG updates (after the column pass)
 bool rows_inv256_ok(const Grid& g);
 cudaError_t launch_rows_inv256(const PlaneInvArgs<float>& a, cudaStream_t s);
+// forward axis-3 row pass of the same planes, fused with r <- r - alpha p (before the column pass)
+cudaError_t launch_rows_fwd256(const PlaneFwdArgs<float>& a, cudaStream_t s);
 
 // TMA-staged axis-1 pass of the mixed-precision loop, c = 1 and 3 (k_line_tma.cu)
 bool line_tma_supported(const Grid& g, int c);
