@@ -705,15 +705,11 @@ static cudaError_t enq_pre(unocg_ctx* ctx, cudaStream_t s, const Plan& pl, const
   return enq_residual_check<T>(ctx, s, ctl, 0, pl.o.precond);
 }
 
-// TMA-staged axis-1 pass of the mixed-precision loop (c = 1, N1 of 2^k or 3 x 2^k points up to 256);
+// TMA-staged axis-1 pass of the mixed-precision loop (c = 1: N1 of 2^k or 3 x 2^k points up to 256; c = 3: up to 64);
 // UNOCG_LINE_TMA=0 at run time keeps the register-FFT pass (for comparisons)
 static bool line_tma_on(const unocg_ctx* ctx) {
-  static int env = -2;
-  if (env == -2) {
-    const char* e = std::getenv("UNOCG_LINE_TMA");
-    env = e ? std::atoi(e) : -1;
-  }
-  return env != 0 && line_tma_supported(ctx->g, ctx->c);
+  const char* e = std::getenv("UNOCG_LINE_TMA");  // read at every enqueue
+  return !(e && std::atoi(e) == 0) && line_tma_supported(ctx->g, ctx->c);
 }
 
 template <typename T>
