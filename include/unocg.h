@@ -136,15 +136,18 @@ int unocg_autotune(unocg_ctx* ctx, const unocg_solve_opts* opts, int reps, doubl
    tile = -1: automatic (default); 0: the register column march (below 10^6 nodes per field) or
    the element kernel; k = 1..8: the TMA-staged kernel, whose block holds TY node rows over the
    whole N3 extent (N3 / 4 threads per row) and marches over P node planes, with
-   (TY, P) = (4, 12), (8, 12), (2, 12), (8, 24), (16, 6), (4, 24), (16, 12), (8, 6).  The TMA
-   kernel needs N3 a multiple of 32 up to 256, TY dividing N2 and 64 to 512 threads a block;
-   unavailable shapes return UNOCG_ERR_INVALID_ARG.  Elastic problems ignore the setting.
-   unocg_get_ku_tile returns the tile the next solve uses (0 or 1..8).                       */
+   (TY, P) = (4, 12), (8, 12), (2, 12), (8, 24), (16, 6), (4, 24), (16, 12), (8, 6); k = 9..16:
+   the vector march with the shape of k - 8 (the same block layout, node planes read straight
+   from global memory instead of staged by the TMA).  The TMA kernel needs N3 a multiple of 32
+   up to 256, the vector march up to 512; both TY dividing N2 and 64 to 512 threads a block
+   (a multiple of 32).  Unavailable shapes return UNOCG_ERR_INVALID_ARG.  Elastic problems
+   ignore the setting.  unocg_get_ku_tile returns the tile the next solve uses (0..16).      */
 int unocg_set_ku_tile(unocg_ctx* ctx, int tile);
 int unocg_get_ku_tile(unocg_ctx* ctx, int* tile);
 /* Stencil autotuner: times `reps` FP32 K d launches over all B x L fields of the context for
-   the earlier kernels (times[0]) and each TMA tile shape (times[1..8], NaN where unavailable),
-   keeps the fastest (unocg_set_ku_tile) and returns its index in *best (may be NULL).  Needs
+   the earlier kernels (times[0]), each TMA tile shape (times[1..8]) and each vector-march shape
+   (times[9..16]), NaN where unavailable (times: double[17]), keeps the fastest
+   (unocg_set_ku_tile) and returns its index in *best (may be NULL).  Needs
    the microstructure, properties and loads set.  UNOCG_ERR_DEVICE_TIMEOUT if a tile copy's
    bounded wait expired (the setting is then left unchanged).                               */
 int unocg_autotune_ku(unocg_ctx* ctx, int reps, double* times, int* best);
@@ -301,7 +304,7 @@ int unocg_newton_run(unocg_newton* op, const double* w0, int max_steps, double t
 /* p = K d (Sec. 4.1, matrix-free), in FP64.                                                 */
 int unocg_apply_K_dev(unocg_ctx* ctx, int instance, const double* d_dev, double* p_dev, void* stream);
 /* p = K d (Sec. 4.1, matrix-free) in FP32 with the kernel of the mixed-precision loop: for
-   thermal problems the TMA-staged tile kernel of unocg_set_ku_tile where the grid allows it.
+   thermal problems the kernel of unocg_set_ku_tile where the grid allows it.
    Fields are float [c][N1][N2][N3], caller-owned device memory, enqueued on `stream`.         */
 int unocg_apply_K32_dev(unocg_ctx* ctx, int instance, const float* d_dev, float* p_dev, void* stream);
 /* s = P r with the context's current UNO weights (Algorithm 2, transform / block multiply /

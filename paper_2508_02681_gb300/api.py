@@ -252,9 +252,9 @@ def unocg_get_ku_tile(ctx) -> int:
 
 
 def unocg_autotune_ku(ctx, reps: int = 20):
-    """Times of the K d candidates (index 0: the earlier kernels, 1..8: TMA tile shapes; NaN where
-    unavailable) and the index kept."""
-    times = np.zeros(9)
+    """Times of the K d candidates (index 0: the earlier kernels, 1..8: TMA tile shapes, 9..16:
+    vector-march shapes; NaN where unavailable) and the index kept."""
+    times = np.zeros(17)
     best = C.c_int(0)
     _check(ctx, _lib.load().unocg_autotune_ku(ctx, reps, _ptr(times), C.byref(best)))
     return times, best.value

@@ -148,8 +148,9 @@ struct unocg_ctx {
   // tuning (unocg_set_tuning / unocg_autotune): radix order of the Stockham plans and the loop
   // driver taken by use_graph = 3
   int radix_order = 0, tuned_path = 1;
-  // thermal FP32 K d: -1 automatic, 0 the register-march / element kernels, k >= 1 the TMA-staged
-  // kernel with tile shape kKuTmaShapes[k - 1] (unocg_set_ku_tile / unocg_autotune_ku)
+  // thermal FP32 K d: -1 automatic, 0 the register-march / element kernels, k = 1..8 the
+  // TMA-staged kernel with tile shape kKuTmaShapes[k - 1], k = 9..16 the vector march with tile
+  // shape kKuTmaShapes[k - 9] (unocg_set_ku_tile / unocg_autotune_ku)
   int ku_tile = -1;
   // changes whenever a captured graph of this context becomes invalid (and at creation): the
   // batch graphs of unocg_batch_solve that include the context compare it
@@ -557,9 +558,12 @@ static int ensure_workspace(unocg_ctx* ctx, int precision, int precond) {
   need = std::max(need, (size_t)BL * node_blocks_x(ctx->g));
   need = std::max(need, (size_t)BL * ku_blocks_x(ctx->g, ctx->c));
   need = std::max(need, (size_t)BL * ku_tasks_x(ctx->g, ctx->c));
-  for (int k = 0; k < kKuTmaNumShapes; ++k)
+  for (int k = 0; k < kKuTmaNumShapes; ++k) {
     if (ku_tma_supported(ctx->g, ctx->c, kKuTmaShapes[k]))
       need = std::max(need, (size_t)BL * ku_tma_blocks_x(ctx->g, kKuTmaShapes[k]));
+    if (ku_vec_supported(ctx->g, ctx->c, kKuTmaShapes[k]))
+      need = std::max(need, (size_t)BL * ku_vec_blocks_x(ctx->g, kKuTmaShapes[k]));
+  }
   need = std::max(need, (size_t)BL * jac_blocks_x((long long)ctx->c * n, BL));
   need = std::max(need, (size_t)BL * ctx->c * 1184);
   need = std::max(need, (size_t)ctx->B * node_blocks_x(ctx->g) * 48);
@@ -752,28 +756,43 @@ static cudaError_t enq_precond(unocg_ctx* ctx, cudaStream_t s, const Plan& pl, c
   return launch_jac<T>(a, 1, s);
 }
 
-// Tile shape of the thermal FP32 K d (1-based index into kKuTmaShapes, 0: the earlier kernels).
+// K d tiles: 0 the earlier kernels, 1..8 the TMA-staged kernel with shape kKuTmaShapes[k - 1],
+// 9..16 the vector march (register window over node planes read from global memory) with shape
+// kKuTmaShapes[k - 9].
+constexpr int kKuTiles = 2 * kKuTmaNumShapes;
+static bool ku_tile_ok(const Grid& g, int c, int tile) {
+  if (tile == 0) return true;
+  if (tile < 0 || tile > kKuTiles) return false;
+  return tile <= kKuTmaNumShapes ? ku_tma_supported(g, c, kKuTmaShapes[tile - 1])
+                                 : ku_vec_supported(g, c, kKuTmaShapes[tile - 1 - kKuTmaNumShapes]);
+}
+
 // Automatic choice: below 10^6 nodes per field the fields sit in L2 and the register column
-// march is faster (64^3, 3 loads: 16.4 against 22.8 us per launch); from there the TMA-staged
-// tile, with the supported shape of the most work per block (threads x planes) that still gives
-// two blocks per SM over all (instance, load) fields, else the one with most blocks.
+// march is faster (64^3, 3 loads: 16.4 us per launch against 22.8 for the TMA tile and 24 for the
+// vector march with 24 planes); from there the vector march, with the first shape of
+// (4, 24), (8, 24), (4, 12), (8, 12) that the grid allows with at least two blocks per SM over
+// all (instance, load) fields (256^3 x 3 loads: 197 / 202 us against 237 for the best TMA tile;
+// 192^3: 110 / 114 against 125), else the TMA tile of most blocks.
 static int ku_tma_choice(const unocg_ctx* ctx) {
   if (ctx->c != 1 || ctx->ku_tile == 0) return 0;
   if (ctx->ku_tile < 0 && ctx->g.n < 1000000) return 0;
-  if (ctx->ku_tile > 0)
-    return ku_tma_supported(ctx->g, 1, kKuTmaShapes[ctx->ku_tile - 1]) ? ctx->ku_tile : 0;
+  if (ctx->ku_tile > 0) return ku_tile_ok(ctx->g, 1, ctx->ku_tile) ? ctx->ku_tile : 0;
   const long long BL = (long long)ctx->B * std::max(ctx->L, 1);
-  int best = 0, most = 0;
-  long long best_work = -1, most_blocks = -1;
+  const long long want = 2LL * std::max(ctx->sm_count, 1);
+  static const int pref[] = {6, 4, 1, 2};  // 1-based shape indices: (4,24), (8,24), (4,12), (8,12)
+  for (int k : pref) {
+    const KuTmaShape sh = kKuTmaShapes[k - 1];
+    if (ku_vec_supported(ctx->g, 1, sh) && BL * ku_vec_blocks_x(ctx->g, sh) >= want) return kKuTmaNumShapes + k;
+  }
+  int most = 0;
+  long long most_blocks = -1;
   for (int k = 0; k < kKuTmaNumShapes; ++k) {
     const KuTmaShape sh = kKuTmaShapes[k];
     if (!ku_tma_supported(ctx->g, 1, sh)) continue;
     const long long blocks = BL * ku_tma_blocks_x(ctx->g, sh);
-    const long long work = (long long)ku_tma_threads(ctx->g, sh) * sh.planes;
-    if (blocks >= 2LL * std::max(ctx->sm_count, 1) && work > best_work) { best = k + 1; best_work = work; }
     if (blocks > most_blocks) { most = k + 1; most_blocks = blocks; }
   }
-  return best ? best : most;
+  return most;
 }
 
 template <typename T>
@@ -1534,8 +1553,8 @@ extern "C" int unocg_apply_K32_dev(unocg_ctx* ctx, int instance, const float* d_
 }
 
 extern "C" int unocg_set_ku_tile(unocg_ctx* ctx, int tile) {
-  if (!ctx || tile < -1 || tile > kKuTmaNumShapes) return fail(ctx, UNOCG_ERR_INVALID_ARG, "invalid K d tile");
-  if (tile > 0 && !ku_tma_supported(ctx->g, ctx->c, kKuTmaShapes[tile - 1]))
+  if (!ctx || tile < -1 || tile > kKuTiles) return fail(ctx, UNOCG_ERR_INVALID_ARG, "invalid K d tile");
+  if (tile > 0 && !ku_tile_ok(ctx->g, ctx->c, tile))
     return fail(ctx, UNOCG_ERR_INVALID_ARG, "K d tile shape not available for this grid / physics");
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->ku_tile = tile;
@@ -1551,8 +1570,8 @@ extern "C" int unocg_get_ku_tile(unocg_ctx* ctx, int* tile) {
 
 // Times `reps` launches of the FP32 K d over all B x L fields of the context (standalone mode,
 // CUDA events on the context stream, after one warm-up launch) for the earlier kernels
-// (times[0]) and every TMA tile shape (times[k], NaN where the grid does not allow it), keeps
-// the fastest and returns its index in *best.
+// (times[0]), every TMA tile shape (times[1..8]) and every vector-march shape (times[9..16]),
+// NaN where the grid does not allow it; keeps the fastest and returns its index in *best.
 extern "C" int unocg_autotune_ku(unocg_ctx* ctx, int reps, double* times, int* best) {
   if (!ctx || reps < 1 || !times) return fail(ctx, UNOCG_ERR_INVALID_ARG, "invalid autotune arguments");
   if (!ctx->have_phase || !ctx->have_props || ctx->L < 1)
@@ -1568,9 +1587,9 @@ extern "C" int unocg_autotune_ku(unocg_ctx* ctx, int reps, double* times, int* b
   double bt = 1e300;
   int bk = 0;
   const int saved = ctx->ku_tile;
-  for (int k = 0; k <= kKuTmaNumShapes && rc == UNOCG_OK; ++k) {
+  for (int k = 0; k <= kKuTiles && rc == UNOCG_OK; ++k) {
     times[k] = std::nan("");
-    if (k > 0 && !ku_tma_supported(ctx->g, ctx->c, kKuTmaShapes[k - 1])) continue;
+    if (!ku_tile_ok(ctx->g, ctx->c, k)) continue;
     ctx->ku_tile = k;
     StencilArgs<float> a = ku_args<float>(ctx);
     a.standalone = 1;

@@ -802,6 +802,10 @@ template <typename T, int CC> static cudaError_t launch_ku_el(const StencilArgs<
 
 template <typename T> cudaError_t launch_ku(const StencilArgs<T>& a, cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
+    // tiles 9..16: the vector march with shape kKuTmaShapes[tile - 9]
+    if (a.c == 1 && a.ku_tma > kKuTmaNumShapes && a.ku_tma <= 2 * kKuTmaNumShapes &&
+        ku_vec_supported(a.g, 1, kKuTmaShapes[a.ku_tma - 1 - kKuTmaNumShapes]))
+      return launch_ku_vec(a, kKuTmaShapes[a.ku_tma - 1 - kKuTmaNumShapes], s);
     if (a.c == 1 && a.ku_tma > 0 && a.ku_tma <= kKuTmaNumShapes &&
         ku_tma_supported(a.g, 1, kKuTmaShapes[a.ku_tma - 1]))
       return launch_ku_tma(a, kKuTmaShapes[a.ku_tma - 1], a.err, a.spin_limit, s);

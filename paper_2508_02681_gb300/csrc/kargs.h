@@ -103,7 +103,8 @@ template <typename T> struct StencilArgs {
   CgScal* sc;
   Reduce red;
   int standalone;       // no CG bookkeeping (operator apply)
-  int ku_tma;           // FP32 thermal: 1 + index into kKuTmaShapes of the TMA-staged kernel, 0 none
+  int ku_tma;           // FP32 thermal: 1 + index into kKuTmaShapes of the TMA-staged kernel,
+                        // 9 + index of the vector march, 0 none
   int* err;             // bounded waits: flag raised on expiry (null: none)
   long long spin_limit; // SM clock cycles a wait may take
 };
@@ -119,6 +120,11 @@ int ku_tma_threads(const Grid& g, KuTmaShape s);
 bool ku_tma_supported(const Grid& g, int c, KuTmaShape s);
 int ku_tma_blocks_x(const Grid& g, KuTmaShape s);
 cudaError_t launch_ku_tma(const StencilArgs<float>& a, KuTmaShape s, int* err, long long spin_limit, cudaStream_t st);
+// the same stencil as a register march over node planes read straight from global memory
+// (k_ku_vec.cu), same tile shapes
+bool ku_vec_supported(const Grid& g, int c, KuTmaShape s);
+int ku_vec_blocks_x(const Grid& g, KuTmaShape s);
+cudaError_t launch_ku_vec(const StencilArgs<float>& a, KuTmaShape s, cudaStream_t st);
 
 // 256 x 256 plane passes on two-CTA clusters, FP32 (k_plane_cl.cu)
 bool plane_cl_ok(const Grid& g);

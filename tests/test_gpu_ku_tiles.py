@@ -37,7 +37,7 @@ def test_K32_every_tile_matches_assembled_K(shape):
     p_ref = fem.to_soa(K @ fem.from_soa(d.astype(np.float64)), 1, shape)
     dd = torch.tensor(d, device="cuda")
     ran = []
-    for tile in range(9):
+    for tile in range(17):
         try:
             api.unocg_set_ku_tile(ctx, tile)
         except _lib.UnocgError as err:
@@ -103,3 +103,75 @@ def test_ku_autotune_keeps_the_fastest_and_solves_match():
         Cs.append(h.effective_tensor()[0])
     assert rel(Cs[1], Cs[0]) < 1e-6
     h.close()
+
+
+# tile shapes (node rows, node planes), in the order of the library's table (indices 1..8; the
+# vector march takes 9..16 for the same shapes)
+TILE_SHAPES = [(4, 12), (8, 12), (2, 12), (8, 24), (16, 6), (4, 24), (16, 12), (8, 6)]
+
+
+def _vec_supported(shape, rows):
+    n1, n2, n3 = shape
+    th = rows * (n3 // 4)
+    return n3 % 32 == 0 and n3 <= 512 and th % 32 == 0 and 64 <= th <= 512 and n2 % rows == 0
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_K32_vector_march_tiles_available(shape):
+    """The vector-march tiles (9..16) the library accepts are those of the stated rule."""
+    from paper_2508_02681_gb300 import _lib, api
+    phase = random_phase(shape, 4, seed=3)
+    ctx = _ctx(shape, phase, np.array([1.0, 2.0, 3.0, 4.0]))
+    for k, (rows, planes) in enumerate(TILE_SHAPES, start=1):
+        ok = True
+        try:
+            api.unocg_set_ku_tile(ctx, 8 + k)
+        except _lib.UnocgError as err:
+            assert err.code == _lib.ERR_INVALID_ARG
+            ok = False
+        assert ok == _vec_supported(shape, rows), (k, rows)
+        if ok:
+            assert api.unocg_get_ku_tile(ctx) == 8 + k
+    api.unocg_destroy(ctx)
+
+
+def test_vector_march_solve_matches_oracle():
+    """The vector march (tile 14: shape (4, 24)) inside the mixed loop, 16 x 256 x 256, against
+    the oracle's flexible PCG."""
+    from oracle import homogenize as hz
+    from paper_2508_02681_gb300 import _lib, api
+    from paper_2508_02681_gb300.solver import Homogenization
+    from synth import rsa_spheres, unit_loads
+    shape = (16, 256, 256)
+    phase, _ = rsa_spheres(shape, 5.0, 0.3, seed=21)
+    props = np.array([1.0, 20.0])
+    loads = unit_loads(1)[:1]
+    ref = hz.solve(phase, props, 1, loads, precond="uno", tol=1e-8, flexible=True)
+    C_ref = hz.effective_tensor(phase, props, 1, ref["u"], loads)
+    h = Homogenization(_lib.THERMAL, shape)
+    h.set_microstructure(phase, 2)
+    h.set_phase_properties(props)
+    h.set_macro_load(loads)
+    h.set_uno_weights(_lib.W_REFERENCE_MEDIUM)
+    api.unocg_set_ku_tile(h.ctx, 14)
+    info = h.solve(tol=1e-6, max_iter=500, precond=_lib.PRECOND_UNO, precision=_lib.MIXED, flexible=1)
+    assert api.unocg_get_ku_tile(h.ctx) == 14
+    assert info.status == _lib.OK and np.all(info.true_rel_res <= 1e-6)
+    assert np.all(info.iters <= np.array(ref["iters"]) + 8)
+    assert rel(h.effective_tensor()[0], C_ref) < 1e-6
+    h.close()
+
+
+def test_auto_choice_takes_the_vector_march_on_large_grids():
+    """256^3 with three loads: the automatic K d tile is the vector march with shape (4, 24);
+    below 10^6 nodes per field the column march (tile 0)."""
+    from paper_2508_02681_gb300 import _lib, api
+    from paper_2508_02681_gb300.solver import Homogenization
+    from synth import unit_loads
+    for shape, want in (((256, 256, 256), 14), ((64, 64, 64), 0)):
+        h = Homogenization(_lib.THERMAL, shape)
+        h.set_microstructure(np.zeros(shape, dtype=np.uint8), 2)
+        h.set_phase_properties(np.array([1.0, 2.0]))
+        h.set_macro_load(unit_loads(1))
+        assert api.unocg_get_ku_tile(h.ctx) == want, shape
+        h.close()
