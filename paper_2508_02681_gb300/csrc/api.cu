@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <cstring>
 #include <cstdlib>
+#include <initializer_list>
 #include <type_traits>
 #include <mutex>
 #include <string>
@@ -767,23 +768,29 @@ static bool ku_tile_ok(const Grid& g, int c, int tile) {
                                  : ku_vec_supported(g, c, kKuTmaShapes[tile - 1 - kKuTmaNumShapes]);
 }
 
-// Automatic choice: below 10^6 nodes per field the fields sit in L2 and the register column
-// march is faster (64^3, 3 loads: 16.4 us per launch against 22.8 for the TMA tile and 24 for the
-// vector march with 24 planes); from there the vector march, with the first shape of
-// (4, 24), (8, 24), (4, 12), (8, 12) that the grid allows with at least two blocks per SM over
-// all (instance, load) fields (256^3 x 3 loads: 197 / 202 us against 237 for the best TMA tile;
-// 192^3: 110 / 114 against 125), else the TMA tile of most blocks.
+// Automatic choice, the vector march in both regimes:
+//  * below 10^6 nodes per field (fields in L2, latency bound): the first of the 6-plane tiles
+//    (8, 6), (16, 6) with at least one block per SM over all (instance, load) fields, else the
+//    register column march (64^3, 3 loads, back-to-back launches: 5.6 us for (8, 6) against 8.0
+//    for the column march and 9.0 for the best TMA tile);
+//  * from 10^6 nodes: the first of (4, 24), (8, 24), (4, 12), (8, 12) with at least two blocks
+//    per SM (256^3 x 3 loads: 197 / 202 us against 237 for the best TMA tile; 192^3: 110 / 114
+//    against 125), else the TMA tile of most blocks.
 static int ku_tma_choice(const unocg_ctx* ctx) {
   if (ctx->c != 1 || ctx->ku_tile == 0) return 0;
-  if (ctx->ku_tile < 0 && ctx->g.n < 1000000) return 0;
   if (ctx->ku_tile > 0) return ku_tile_ok(ctx->g, 1, ctx->ku_tile) ? ctx->ku_tile : 0;
   const long long BL = (long long)ctx->B * std::max(ctx->L, 1);
-  const long long want = 2LL * std::max(ctx->sm_count, 1);
-  static const int pref[] = {6, 4, 1, 2};  // 1-based shape indices: (4,24), (8,24), (4,12), (8,12)
-  for (int k : pref) {
-    const KuTmaShape sh = kKuTmaShapes[k - 1];
-    if (ku_vec_supported(ctx->g, 1, sh) && BL * ku_vec_blocks_x(ctx->g, sh) >= want) return kKuTmaNumShapes + k;
-  }
+  const long long sms = std::max(ctx->sm_count, 1);
+  auto first_vec = [&](std::initializer_list<int> pref, long long want) {
+    for (int k : pref) {  // 1-based shape indices
+      const KuTmaShape sh = kKuTmaShapes[k - 1];
+      if (ku_vec_supported(ctx->g, 1, sh) && BL * ku_vec_blocks_x(ctx->g, sh) >= want) return kKuTmaNumShapes + k;
+    }
+    return 0;
+  };
+  if (ctx->g.n < 1000000) return first_vec({8, 5}, sms);  // (8, 6), (16, 6); else the column march
+  const int v = first_vec({6, 4, 1, 2}, 2 * sms);         // (4, 24), (8, 24), (4, 12), (8, 12)
+  if (v) return v;
   int most = 0;
   long long most_blocks = -1;
   for (int k = 0; k < kKuTmaNumShapes; ++k) {

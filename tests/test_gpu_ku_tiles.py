@@ -62,7 +62,8 @@ def test_K32_batch_instances_and_default_tile():
     phases = np.stack([random_phase(shape, 4, seed=40 + b) for b in range(B)])
     props = np.stack([np.array([1.0, 3.0, 10.0, 0.5]) * (b + 1) for b in range(B)])
     ctx = _ctx(shape, phases, props, batch=B)
-    # below 10^6 nodes the automatic choice keeps the column march; take a TMA tile explicitly
+    # too few blocks for the vector march: the automatic choice keeps the column march; take a
+    # TMA tile explicitly
     assert api.unocg_get_ku_tile(ctx) == 0
     api.unocg_set_ku_tile(ctx, 1)
     assert api.unocg_get_ku_tile(ctx) == 1
@@ -163,12 +164,13 @@ def test_vector_march_solve_matches_oracle():
 
 
 def test_auto_choice_takes_the_vector_march_on_large_grids():
-    """256^3 with three loads: the automatic K d tile is the vector march with shape (4, 24);
-    below 10^6 nodes per field the column march (tile 0)."""
+    """Three loads: 256^3 takes the vector march with shape (4, 24) (tile 14); 64^3, below 10^6
+    nodes per field, the one with shape (8, 6) (tile 16, at least one block per SM); a grid too
+    small for one block per SM the column march (tile 0)."""
     from paper_2508_02681_gb300 import _lib, api
     from paper_2508_02681_gb300.solver import Homogenization
     from synth import unit_loads
-    for shape, want in (((256, 256, 256), 14), ((64, 64, 64), 0)):
+    for shape, want in (((256, 256, 256), 14), ((64, 64, 64), 16), ((24, 16, 32), 0)):
         h = Homogenization(_lib.THERMAL, shape)
         h.set_microstructure(np.zeros(shape, dtype=np.uint8), 2)
         h.set_phase_properties(np.array([1.0, 2.0]))
