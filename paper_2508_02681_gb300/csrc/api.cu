@@ -619,13 +619,13 @@ struct Plan {
 
 // Forward transform over axes 3 and 2: whole planes in one pass where a plane fits one block's
 // shared memory, else the row pass (axis 3) followed by the in-place axis-2 column pass.
-// 256 x 256 FP32 planes: one pass on two-CTA clusters.  UNOCG_PLANE_CL selects the passes that
-// take it, as a mask read at each enqueue: 1 forward, 2 inverse (default 1: the forward cluster
-// pass measured 487 -> 354 us per launch on a 256^3 field of three loads, the inverse one
-// 439 -> 477 us, so the inverse keeps the column pass plus row pass).
+// 256 x 256 FP32 planes may take one pass on two-CTA clusters instead.  UNOCG_PLANE_CL selects
+// the passes that take it, as a mask read at each enqueue: 1 forward, 2 inverse (default 0: on a
+// 256^3 field of three loads, with the register row and column passes, the forward measured
+// 281 us per launch as two passes against 310 us on clusters, the inverse 302 against 444 us).
 static bool plane_cl_on(const Grid& g, int which) {
   const char* e = std::getenv("UNOCG_PLANE_CL");
-  const int mask = e ? std::atoi(e) : 1;
+  const int mask = e ? std::atoi(e) : 0;
   return (mask & which) != 0 && plane_cl_ok(g);
 }
 

@@ -12,6 +12,7 @@
 #pragma once
 #include "kargs.h"
 #include "fft.cuh"
+#include <cstdlib>
 #include <type_traits>
 
 namespace unocg {
@@ -548,6 +549,12 @@ bool grid_supported(const Grid& g, int elem_bytes) {
   return cols <= 220 * 1024 && line_smem_bytes(g, 3, elem_bytes, 0) <= 220 * 1024;
 }
 template <typename T> cudaError_t launch_cols(const ColArgs<T>& a, int dir, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    // 256^2 planes: the register column pass (UNOCG_COLS_REG=0, read at every launch, selects
+    // the shared-memory pass below; 256^3 x 3 loads: inverse transform 302 against 333 us)
+    const char* e = std::getenv("UNOCG_COLS_REG");
+    if (!(e && std::atoi(e) == 0) && rows_inv256_ok(a.g)) return launch_cols_reg256(a, dir, s);
+  }
   const int eb = sizeof(cplx<T>);
   size_t smem = (2 * (size_t)a.g.n2 * 16 + a.g.n2) * eb;
   dim3 grid((a.g.n3h + 15) / 16, (unsigned)((long long)a.BL * a.c * a.g.n1));

@@ -455,6 +455,56 @@ __global__ void __launch_bounds__(RI_W * 32) k_rows_fwd256(PlaneFwdArgs<float> a
   }
 }
 
+// ---------------------------------------------------------------- column pass of 256^2 planes
+// FFT along axis 2 of 256 x 256 FP32 half-spectrum planes (129 columns of 256 points), in place
+// or into a.out.  A warp takes two adjacent columns (16 threads a column, the register line FFT
+// of fft_reg.cuh) and reads them straight from global memory into the line FFT's distribution:
+// thread g holds rows g + 16 j, and the scattered order of the 256-point split is the same row
+// set, so results go back to global memory from the same registers.  The only shared memory is
+// the warp's exchange scratch and the twiddles: no block barrier after the start, the warps of
+// a block run independently and one warp's loads overlap another's arithmetic.  The (plane,
+// column pair) units are numbered across the grid, 65 a plane (the last one holds the Nyquist
+// column and an idle half).
+namespace {
+constexpr int CR_W = 8;                      // warps per block
+constexpr int CR_PAIRS = (Pn3h + 1) / 2;     // 65 column pairs a plane
+constexpr size_t kColsRegSmem = (size_t)CR_W * 2 * PN * sizeof(float2) + (size_t)PN * sizeof(float2);
+}  // namespace
+
+template <int DIR>
+__global__ void __launch_bounds__(CR_W * 32) k_cols_reg256(ColArgs<float> a, long long units) {
+  using C = float2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* scr_all = reinterpret_cast<C*>(smem_raw);  // [warp][2 lines][256]
+  C* tw2 = scr_all + CR_W * 2 * PN;
+  load_tw_reg<float>(tw2, a.ft.tw2, PN);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long unit = (long long)blockIdx.x * CR_W + warp;
+  if (unit >= units) return;
+  const long long plane = unit / CR_PAIRS;  // (bl * c + comp) * n1 + i1
+  const int pair = (int)(unit - plane * CR_PAIRS);
+  const int bl = (int)(plane / ((long long)a.c * a.g.n1));
+  if (a.sc && (a.sc[bl].done || (a.only_pending && !a.sc[bl].just_replaced))) return;
+  const int line = lane / PG2, g = lane % PG2;
+  const int col = 2 * pair + line;
+  const bool on = col < Pn3h;
+  const C* src = a.data + plane * (long long)(PN * Pn3h) + col;
+  C* dst = (a.out ? a.out : a.data) + plane * (long long)(PN * Pn3h) + col;
+  C* scr = scr_all + (warp * 2 + line) * PN;
+  C v[PV2];
+  // natural rows g + 16 j in; the scattered index of value j * G + k2 is g + 16 k2 (V = G)
+  static_assert(PV2 == PG2, "256-point split with V = G");
+#pragma unroll
+  for (int j = 0; j < PV2; ++j) v[j] = on ? __ldg(src + (long long)(g + PG2 * j) * Pn3h) : make_float2(0.f, 0.f);
+  if (DIR < 0) fft_dist_a<PN, -1>(v, g, scr, 1, tw2);
+  else fft_dist_b<PN, +1>(v, g, scr, 1, tw2);
+  if (on) {
+#pragma unroll
+    for (int j = 0; j < PV2; ++j) dst[(long long)(g + PG2 * j) * Pn3h] = v[j];
+  }
+}
+
 // ---------------------------------------------------------------- host side
 bool plane_cl_ok(const Grid& g) {
 #ifdef UNOCG_NO_CLUSTER_PLANES
@@ -516,6 +566,25 @@ cudaError_t launch_rows_fwd256(const PlaneFwdArgs<float>& a, cudaStream_t s) {
     attr = true;
   }
   return launch_pdl(k_rows_fwd256, dim3(a.c * a.g.n1 * (PN / RI_R), a.BL), dim3(RI_W * 32), kRowsInvSmem, s, a);
+}
+
+// register column pass of 256 x 256 FP32 planes (see k_cols_reg256)
+cudaError_t launch_cols_reg256(const ColArgs<float>& a, int dir, cudaStream_t s) {
+  if (!rows_inv256_ok(a.g)) return cudaErrorInvalidValue;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_cols_reg256<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kColsRegSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_cols_reg256<+1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kColsRegSmem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const long long units = (long long)a.BL * a.c * a.g.n1 * CR_PAIRS;
+  const dim3 grid((unsigned)((units + CR_W - 1) / CR_W));
+  if (dir < 0) k_cols_reg256<-1><<<grid, CR_W * 32, kColsRegSmem, s>>>(a, units);
+  else k_cols_reg256<+1><<<grid, CR_W * 32, kColsRegSmem, s>>>(a, units);
+  return cudaGetLastError();
 }
 
 }  // namespace unocg

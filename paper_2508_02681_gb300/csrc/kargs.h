@@ -267,5 +267,7 @@ bool plane_fits(const Grid& g, int elem_bytes);
 int plane_rows(const Grid& g, int elem_bytes);  // 0 if whole planes fit, else rows per block
 bool grid_supported(const Grid& g, int elem_bytes);
 template <typename T> cudaError_t launch_cols(const ColArgs<T>& a, int dir, cudaStream_t s);
+// axis-2 pass of 256 x 256 FP32 planes, two columns a warp in registers (k_plane_cl.cu)
+cudaError_t launch_cols_reg256(const ColArgs<float>& a, int dir, cudaStream_t s);
 
 }  // namespace unocg

@@ -1,6 +1,7 @@
 """Flexible (Polak-Ribiere) UNO-CG on grids whose (axis-2, axis-3) planes are too large for one
-block: the forward and inverse transforms then run as a row pass plus a separate axis-2 pass, or,
-for 256 x 256 FP32 planes, as one pass on a cluster of two blocks.
+block: the forward and inverse transforms then run as a row pass plus a separate axis-2 pass (for
+256 x 256 FP32 planes both in registers), or, for 256 x 256 FP32 planes, as one pass on a cluster
+of two blocks.
 The r . s_old term of the flexible coefficient reads the previous s_hat, so the inverse axis-2
 pass must leave it intact.  FP64 against the oracle's flexible PCG on the same inputs (fields
 1e-9, effective tensor 1e-10); mixed precision to the effective tensor (1e-6) with the true
@@ -78,13 +79,16 @@ def cluster_case():
     return _case((4, 256, 256))   # FP32 256 x 256 planes: one pass on two-CTA clusters
 
 
-@pytest.mark.parametrize("use_graph,passes", [(1, 1), (0, 1), (1, 3), (0, 3), (1, 0)])
-def test_cluster_plane_passes_mixed_match_oracle(cluster_case, use_graph, passes, monkeypatch):
-    """256 x 256 planes in the mixed loop (plane passes on two-CTA clusters, values exchanged
-    through distributed shared memory; `passes` masks which: 1 forward, 2 inverse) against the
-    oracle's flexible PCG."""
+@pytest.mark.parametrize("use_graph,passes,cols_reg", [(1, 1, 1), (0, 1, 1), (1, 3, 1), (0, 3, 1), (1, 0, 1),
+                                                      (0, 0, 1), (1, 0, 0), (1, 2, 0)])
+def test_cluster_plane_passes_mixed_match_oracle(cluster_case, use_graph, passes, cols_reg, monkeypatch):
+    """256 x 256 planes in the mixed loop against the oracle's flexible PCG: plane passes on
+    two-CTA clusters (values exchanged through distributed shared memory; `passes` masks which:
+    1 forward, 2 inverse) or as row pass plus column pass (the register column pass, two columns
+    a warp, or with `cols_reg` 0 the shared-memory one)."""
     from paper_2508_02681_gb300 import _lib
     monkeypatch.setenv("UNOCG_PLANE_CL", str(passes))
+    monkeypatch.setenv("UNOCG_COLS_REG", str(cols_reg))
     phase, loads, ref = cluster_case
     h = _solver(phase, loads)
     info = h.solve(tol=1e-6, max_iter=500, precond=_lib.PRECOND_UNO, precision=_lib.MIXED, flexible=1,
@@ -96,7 +100,7 @@ def test_cluster_plane_passes_mixed_match_oracle(cluster_case, use_graph, passes
     h.close()
 
 
-@pytest.mark.parametrize("passes", [1, 3])
+@pytest.mark.parametrize("passes", [0, 1, 3])
 def test_cluster_plane_passes_elastic_mixed_match_oracle(passes, monkeypatch):
     """The same for three components per node (each component's plane is its own cluster)."""
     from paper_2508_02681_gb300 import _lib
