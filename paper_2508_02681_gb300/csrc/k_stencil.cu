@@ -810,6 +810,12 @@ template <typename T> cudaError_t launch_ku(const StencilArgs<T>& a, cudaStream_
         ku_tma_supported(a.g, 1, kKuTmaShapes[a.ku_tma - 1]))
       return launch_ku_tma(a, kKuTmaShapes[a.ku_tma - 1], a.err, a.spin_limit, s);
   }
+  if constexpr (sizeof(T) == 4) {
+    // elastic K d with packed element pairs (k_ku_el2.cu; UNOCG_KU_EL2=0, read at every launch,
+    // selects the scalar element kernel): 256^3 x 6 loads 1720 against 2336 us per launch
+    const char* e = std::getenv("UNOCG_KU_EL2");
+    if (a.c == 3 && !(e && std::atoi(e) == 0) && ku_el2_supported(a.g)) return launch_ku_el2(a, s);
+  }
   if (a.c != 1) return launch_ku_el<T, 3>(a, s);
   if (thermal_element(a.g)) return launch_ku_el<T, 1>(a, s);
   return launch_pdl(k_ku<T, 1>, ku_task_grid(a.g, 1, a.BL), dim3(256), 0, s, a);

@@ -125,6 +125,10 @@ cudaError_t launch_ku_tma(const StencilArgs<float>& a, KuTmaShape s, int* err, l
 bool ku_vec_supported(const Grid& g, int c, KuTmaShape s);
 int ku_vec_blocks_x(const Grid& g, KuTmaShape s);
 cudaError_t launch_ku_vec(const StencilArgs<float>& a, KuTmaShape s, cudaStream_t st);
+// elastic K d element by element with element pairs in packed FP32x2 arithmetic (k_ku_el2.cu);
+// N3 even, same tiles (and blocks per launch) as the scalar element kernel
+bool ku_el2_supported(const Grid& g);
+cudaError_t launch_ku_el2(const StencilArgs<float>& a, cudaStream_t st);
 
 // 256 x 256 plane passes on two-CTA clusters, FP32 (k_plane_cl.cu)
 bool plane_cl_ok(const Grid& g);
