@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.environ.get("UNOCG_BUILD_DIR", os.path.join(ROOT, "_build"))
 LIB = os.environ.get("UNOCG_LIB_OUT", os.path.join(HERE, "libunocg.so"))
 SOURCES = ["api.cu", "k_stencil.cu", "k_setup.cu", "k_fft_plane.cu", "k_line64.cu", "k_line32.cu", "k_persist.cu",
-           "k_fft_reg.cu", "k_ku_tma.cu", "k_ku_vec.cu", "k_ku_el2.cu", "k_newton.cu", "k_line_tma.cu", "k_line_tma3.cu", "k_plane_cl.cu", "dirichlet/k_dirichlet.cu", "dirichlet/k_dirichlet_reg.cu", "dirichlet/api_dirichlet.cu"]
+           "k_fft_reg.cu", "k_ku_tma.cu", "k_ku_vec.cu", "k_ku_el2.cu", "k_newton.cu", "k_line_tma.cu", "k_line_tma3.cu", "k_line_tp.cu", "k_plane_cl.cu", "dirichlet/k_dirichlet.cu", "dirichlet/k_dirichlet_reg.cu", "dirichlet/api_dirichlet.cu"]
 # loads of data written by other blocks of the same launch must bypass L1
 PER_FILE = {"k_persist.cu": ["-Xptxas", "-dlcm=cg"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

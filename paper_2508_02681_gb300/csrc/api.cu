@@ -717,6 +717,15 @@ static bool line_tma_on(const unocg_ctx* ctx) {
   return !(e && std::atoi(e) == 0) && line_tma_supported(ctx->g, ctx->c);
 }
 
+// c = 1: the persistent TMA pipeline for the axis-1 pass with UNOCG_LINE_TP=1 (read at each
+// enqueue).  Off by default: with the conflict-free lane layout both passes move the same bytes
+// at about the same rate (256^3 x 3 loads: 174 us per launch pipelined, 170 us one tile per
+// block).
+static bool line_tp_on(const unocg_ctx* ctx) {
+  const char* e = std::getenv("UNOCG_LINE_TP");
+  return ctx->c == 1 && e && std::atoi(e) == 1 && line_tp_supported(ctx->g);
+}
+
 template <typename T>
 static cudaError_t enq_precond(unocg_ctx* ctx, cudaStream_t s, const Plan& pl, const LoopCtl& ctl, int part) {
   // part 0: transform axis 1 + block multiply (UNO) / direction update (Jacobi, none)
@@ -736,7 +745,10 @@ static cudaError_t enq_precond(unocg_ctx* ctx, cudaStream_t s, const Plan& pl, c
       la.ft = tables(ctx, sizeof(T) == 8);
       la.flexible = pl.o.flexible; la.standalone = 0; la.gq = nullptr;
       if constexpr (std::is_same<T, float>::value)
-        if (line_tma_on(ctx)) return launch_line_tma(la, ctx->flags + 6, ctx->spin_limit, s);
+        if (line_tma_on(ctx)) {
+          if (line_tp_on(ctx)) return launch_line_tp(la, ctx->flags + 6, ctx->spin_limit, ctx->sm_count, s);
+          return launch_line_tma(la, ctx->flags + 6, ctx->spin_limit, s);
+        }
       return launch_line<T, QT>(la, 0, s);
     }
     PlaneInvArgs<T> pa{};

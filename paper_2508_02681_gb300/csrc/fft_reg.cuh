@@ -147,29 +147,30 @@ template <int DIR, typename C> __device__ __forceinline__ C twiddle(C x, C w) {
   return cmul(x, w);
 }
 
-// natural -> scattered (see the header).  scr: this line's N slots at stride ss; tw: W_N^m.
-// All lanes of the warp must call it; scr may be reused after the caller's next __syncwarp().
-template <int N, int DIR, typename C>
-__device__ __forceinline__ void fft_dist_a(C* v, int g, C* scr, int ss, const C* __restrict__ tw) {
+// natural -> scattered (see the header).  slot(s) is this line's exchange slot s < N (a reference
+// into shared memory); tw: W_N^m.  All lanes of the warp must call it; the slots may be reused
+// after the caller's next __syncwarp().
+template <int N, int DIR, typename C, typename Slot>
+__device__ __forceinline__ void fft_dist_a_at(C* v, int g, Slot slot, const C* __restrict__ tw) {
   constexpr int V = RegSplit<N>::V, G = RegSplit<N>::G, VG = V / G;
   dft_pow2<V, DIR>(v);
 #pragma unroll
   for (int k1 = 1; k1 < V; ++k1) v[k1] = twiddle<DIR>(v[k1], tw[g * k1]);
   __syncwarp();
 #pragma unroll
-  for (int k1 = 0; k1 < V; ++k1) scr[reg_slot<N>(k1, g) * ss] = v[k1];
+  for (int k1 = 0; k1 < V; ++k1) slot(reg_slot<N>(k1, g)) = v[k1];
   __syncwarp();
 #pragma unroll
   for (int j = 0; j < VG; ++j)
 #pragma unroll
-    for (int t = 0; t < G; ++t) v[j * G + t] = scr[reg_slot<N>(g * VG + j, t) * ss];
+    for (int t = 0; t < G; ++t) v[j * G + t] = slot(reg_slot<N>(g * VG + j, t));
 #pragma unroll
   for (int j = 0; j < VG; ++j) dft_pow2<G, DIR>(v + j * G);
 }
 
 // scattered -> natural
-template <int N, int DIR, typename C>
-__device__ __forceinline__ void fft_dist_b(C* v, int g, C* scr, int ss, const C* __restrict__ tw) {
+template <int N, int DIR, typename C, typename Slot>
+__device__ __forceinline__ void fft_dist_b_at(C* v, int g, Slot slot, const C* __restrict__ tw) {
   constexpr int V = RegSplit<N>::V, G = RegSplit<N>::G, VG = V / G;
 #pragma unroll
   for (int j = 0; j < VG; ++j) dft_pow2<G, DIR>(v + j * G);
@@ -181,11 +182,33 @@ __device__ __forceinline__ void fft_dist_b(C* v, int g, C* scr, int ss, const C*
 #pragma unroll
   for (int j = 0; j < VG; ++j)
 #pragma unroll
-    for (int t = 0; t < G; ++t) scr[reg_slot<N>(g * VG + j, t) * ss] = v[j * G + t];
+    for (int t = 0; t < G; ++t) slot(reg_slot<N>(g * VG + j, t)) = v[j * G + t];
   __syncwarp();
 #pragma unroll
-  for (int k1 = 0; k1 < V; ++k1) v[k1] = scr[reg_slot<N>(k1, g) * ss];
+  for (int k1 = 0; k1 < V; ++k1) v[k1] = slot(reg_slot<N>(k1, g));
   dft_pow2<V, DIR>(v);
+}
+
+// the slots at base[s ^ x]: a line's own N slots with the slot index bits of x flipped (two lines
+// whose accesses would fall on the same banks use complementary banks with x = 0 and x = 8)
+template <typename C> struct XorSlot {
+  C* base;
+  int x;
+  __device__ __forceinline__ C& operator()(int s) const { return base[s ^ x]; }
+};
+// the slots at scr[s * ss]
+template <typename C> struct StrideSlot {
+  C* scr;
+  int ss;
+  __device__ __forceinline__ C& operator()(int s) const { return scr[s * ss]; }
+};
+template <int N, int DIR, typename C>
+__device__ __forceinline__ void fft_dist_a(C* v, int g, C* scr, int ss, const C* __restrict__ tw) {
+  fft_dist_a_at<N, DIR>(v, g, StrideSlot<C>{scr, ss}, tw);
+}
+template <int N, int DIR, typename C>
+__device__ __forceinline__ void fft_dist_b(C* v, int g, C* scr, int ss, const C* __restrict__ tw) {
+  fft_dist_b_at<N, DIR>(v, g, StrideSlot<C>{scr, ss}, tw);
 }
 
 // index k of value v[j G + k2] in the scattered distribution of thread g

@@ -111,7 +111,13 @@ __global__ void __launch_bounds__(P * RegSplit<N1>::G, kl_min_blocks<N1, P>())
     // after a timeout the copies may still be in flight: wait for them (bounded) before leaving
     if (s_abort && tid == 0) (void)mbar_wait(&bar, 0u, la.spin_limit);
     if (!s_abort) {
-      const int p = tid / G, g = tid % G;          // position within the tile, thread of the line
+      // position within the tile and thread of the line; 16-thread lines in 16-position tiles
+      // interleave their lanes (0-7 and 16-23 one line, 8-15 and 24-31 the other) so that each
+      // half-warp reads eight consecutive rows of two positions: distinct chunks of the swizzle
+      constexpr bool ilv = G == 16 && P == 16;
+      const int lane_ = tid & 31;
+      const int p = ilv ? (tid >> 5) * W + ((lane_ >> 3) & 1) : tid / G;
+      const int g = ilv ? (lane_ & 7) + ((lane_ >> 4) << 3) : tid % G;
       const int pos = pos0 + p;
       const bool on = pos < M;
       const int k3 = on ? pos % a.g.n3h : 0;
@@ -132,9 +138,10 @@ __global__ void __launch_bounds__(P * RegSplit<N1>::G, kl_min_blocks<N1, P>())
         rso.add(wt * part);
       }
       __syncthreads();  // the s_old tile is free: exchange scratch of the line transforms
-      const int warp = tid >> 5, lane = tid & 31, w = lane / G;
-      C* scr = reinterpret_cast<C*>(t_old) + (size_t)warp * W * N1 + w;
-      fft_dist_a<N1, -1>(v, g, scr, W, tw1);
+      // exchange slots: the line's own N1 slots, odd lines with slot index bit 3 flipped
+      const int w = p % W, warp = tid >> 5;
+      const XorSlot<C> scr{reinterpret_cast<C*>(t_old) + (size_t)(warp * W + w) * N1, (w & 1) << 3};
+      fft_dist_a_at<N1, -1>(v, g, scr, tw1);
       if (on) {
         float part = 0.f;  // r . s = sum q |r_hat|^2 over the thread's modes
 #pragma unroll
@@ -149,7 +156,7 @@ __global__ void __launch_bounds__(P * RegSplit<N1>::G, kl_min_blocks<N1, P>())
           }
         gam.add(wt * part);
       }
-      fft_dist_b<N1, +1>(v, g, scr, W, tw1);
+      fft_dist_b_at<N1, +1>(v, g, scr, tw1);
 #pragma unroll
       for (int n1 = 0; n1 < V; ++n1) *reinterpret_cast<C*>(t_hat + swz_off8<P>(g + G * n1, p)) = v[n1];
       fence_async_shared();

@@ -123,8 +123,9 @@ __global__ void __launch_bounds__(K3_P * RegSplit<N1>::G, k3_min_blocks<N1>())
         rso.add(wt * part);
       }
       __syncthreads();  // the s_old tiles have been read: the first one is the exchange scratch
+      // exchange slots: the line's own N1 slots, odd lines with slot index bit 3 flipped
       const int warp = tid >> 5, lane = tid & 31, w = lane / G;
-      C* scr = reinterpret_cast<C*>(t_old) + (size_t)warp * W * N1 + w;
+      const XorSlot<C> scr{reinterpret_cast<C*>(t_old) + (size_t)(warp * W + w) * N1, (w & 1) << 3};
       C v[V];
       // forward transforms; the spectrum of each component goes back into its tile, row k1 of
       // the thread's column (the line's inputs have all been read at the first warp
@@ -134,7 +135,7 @@ __global__ void __launch_bounds__(K3_P * RegSplit<N1>::G, k3_min_blocks<N1>())
         unsigned char* t = t_hat + cc * TB;
 #pragma unroll
         for (int n1 = 0; n1 < V; ++n1) v[n1] = *tile_at(t, g + G * n1, p);
-        fft_dist_a<N1, -1>(v, g, scr, W, tw1);
+        fft_dist_a_at<N1, -1>(v, g, scr, tw1);
 #pragma unroll
         for (int j = 0; j < VG; ++j)
 #pragma unroll
@@ -180,7 +181,7 @@ __global__ void __launch_bounds__(K3_P * RegSplit<N1>::G, k3_min_blocks<N1>())
         for (int j = 0; j < VG; ++j)
 #pragma unroll
           for (int k2 = 0; k2 < G; ++k2) v[j * G + k2] = *tile_at(t, scat_index<N1>(g, j, k2), p);
-        fft_dist_b<N1, +1>(v, g, scr, W, tw1);
+        fft_dist_b_at<N1, +1>(v, g, scr, tw1);
 #pragma unroll
         for (int n1 = 0; n1 < V; ++n1) *tile_at(t, g + G * n1, p) = v[n1];
         __syncwarp();

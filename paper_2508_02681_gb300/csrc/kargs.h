@@ -148,6 +148,10 @@ cudaError_t launch_line_tma(const LineArgs<float, __nv_bfloat16>& a, int* err, l
 // the same for c = 3, N1 in {16, 32, 64} (k_line_tma3.cu); launch_line_tma forwards c = 3 here
 bool line_tma3_supported(const Grid& g);
 cudaError_t launch_line_tma3(const LineArgs<float, __nv_bfloat16>& a, int* err, long long spin_limit, cudaStream_t st);
+// the same pass for c = 1 as a persistent pipeline of TMA tiles (k_line_tp.cu): N1 = 64, 128, 256
+bool line_tp_supported(const Grid& g);
+cudaError_t launch_line_tp(const LineArgs<float, __nv_bfloat16>& a, int* err, long long spin_limit, int sm_count,
+                           cudaStream_t st);
 
 template <typename T> struct InitArgs {
   Grid g;
