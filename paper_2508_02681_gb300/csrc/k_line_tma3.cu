@@ -220,9 +220,191 @@ __global__ void __launch_bounds__(K3_P * RegSplit<N1>::G, k3_min_blocks<N1>())
   if (active && tid == 0) tma_store_wait_all();
 }
 
+// ---------------------------------------------------------------- axes of 96..256 points
+// For longer axis-1 lines the s_old tiles and the weights do not fit next to the three r_hat
+// tiles, so only the r_hat tiles are staged (TMA, 128-byte swizzle): the previous s_hat is read
+// by every thread for its own elements straight from global memory (component by component,
+// before that component's transform), the block entries likewise at the multiply, and each line
+// uses its own column of its tile as the exchange slots (its values are in registers before the
+// first exchange and go back to the same column after the last).  Lanes of the 16-thread lines
+// of 256 points interleave as in k_line_tma, so that a half-warp touches eight rows of two
+// positions (distinct chunks of the swizzle); the 8-thread lines of 128 and 192 points and the
+// 4-thread lines of 96 points hold that by construction.
+namespace {
+template <int N1> constexpr size_t k3w_smem_bytes() { return 1024 + 3 * (size_t)N1 * 128; }
+template <int N1> constexpr int k3w_min_blocks() {
+  constexpr int by_threads = 1024 / (K3_P * RegSplit<N1>::G);
+  constexpr int by_smem = (int)(233472 / (k3w_smem_bytes<N1>() + 1024 + 512));
+  return by_threads < by_smem ? by_threads : by_smem;
+}
+struct SwzSlot {
+  unsigned char* t;
+  int p;
+  __device__ __forceinline__ float2& operator()(int s) const { return *tile_at(t, s, p); }
+};
+}  // namespace
+
+template <int N1>
+__global__ void __launch_bounds__(K3_P * RegSplit<N1>::G, k3w_min_blocks<N1>())
+    k_line_tma3w(const __grid_constant__ Line3Maps maps, const Line3Args la) {
+  using C = float2;
+  constexpr int G = RegSplit<N1>::G, V = RegSplit<N1>::V, VG = V / G, W = 32 / G;
+  constexpr int NTH = K3_P * G;
+  constexpr int TB = N1 * 128;  // bytes of one tile
+  extern __shared__ unsigned char k3_raw[];
+  __shared__ double red_sh[32];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int s_abort;
+  const LineArgs<float, __nv_bfloat16>& a = la.a;
+  unsigned char* t_hat = k3_raw + ((1024u - (sm_addr(k3_raw) & 1023u)) & 1023u);  // three tiles
+  const C* __restrict__ tw1 = reinterpret_cast<const C*>(a.ft.tw1);
+  const int tid = threadIdx.x;
+  const int bl = blockIdx.y;
+  const int pos0 = blockIdx.x * K3_P;
+  const int M = a.g.n2 * a.g.n3h;
+  const int b = bl / a.L;
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    s_abort = 0;
+    mbar_fence_init();
+  }
+  __syncthreads();
+  pdl_wait();  // r_hat, s_hat and the loop state come from the kernels before this one
+  const bool active = !a.sc[bl].done;
+  if (active && tid == 0) {
+    mbar_expect_tx(&bar, (uint32_t)(3 * TB));
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) tma_load_3d(t_hat + cc * TB, &maps.hat, 2 * pos0, 0, bl * 3 + cc, &bar);
+  }
+  DotAcc<float> gam, rso;
+  if (active) {
+    if (!mbar_wait(&bar, 0u, la.spin_limit)) {
+      s_abort = 1;
+      if (la.err) atomicExch(la.err, 1);
+    }
+    __syncthreads();
+    if (s_abort && tid == 0) (void)mbar_wait(&bar, 0u, la.spin_limit);
+    if (!s_abort) {
+      const int warp = tid >> 5, lane = tid & 31;
+      const int w = G == 16 ? (lane >> 3) & 1 : lane / G;
+      const int g = G == 16 ? (lane & 7) + ((lane >> 4) << 3) : lane % G;
+      const int p = warp * W + w;  // position within the tile
+      const int pos = pos0 + p;
+      const bool on = pos < M;
+      const int k3 = on ? pos % a.g.n3h : 0;
+      const float wt = (k3 == 0 || 2 * k3 == a.g.n3) ? 1.f : 2.f;
+      const float sc = (float)a.scale;
+      // previous s_hat of this position, component cc, row r: [(bl * 3 + cc) * N1 + r] * M + pos
+      const C* so_base = reinterpret_cast<const C*>(a.shat) + (long long)bl * 3 * N1 * M + (on ? pos : 0);
+      C v[V];
+      // forward transforms, component by component; r . s_old on the way
+#pragma unroll 1
+      for (int cc = 0; cc < 3; ++cc) {
+        unsigned char* t = t_hat + cc * TB;
+        if (a.flexible && on) {
+          C so[V];
+#pragma unroll
+          for (int n1 = 0; n1 < V; ++n1) so[n1] = __ldg(so_base + ((long long)cc * N1 + g + G * n1) * M);
+          float part = 0.f;
+#pragma unroll
+          for (int n1 = 0; n1 < V; ++n1) {
+            const C rv = *tile_at(t, g + G * n1, p);
+            part = fmaf(rv.x, so[n1].x, fmaf(rv.y, so[n1].y, part));
+          }
+          rso.add(wt * part);
+        }
+#pragma unroll
+        for (int n1 = 0; n1 < V; ++n1) v[n1] = *tile_at(t, g + G * n1, p);
+        fft_dist_a_at<N1, -1>(v, g, SwzSlot{t, p}, tw1);
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < VG; ++j)
+#pragma unroll
+          for (int k2 = 0; k2 < G; ++k2) *tile_at(t, scat_index<N1>(g, j, k2), p) = v[j * G + k2];
+        __syncwarp();
+      }
+      // s_hat = Q r_hat / n at the thread's frequencies, all components; r . s
+      if (on) {
+        const __nv_bfloat16* qrow = a.Q + (a.q_inst_stride ? (long long)b * a.q_inst_stride : 0) + 6LL * pos;
+        float part = 0.f;
+#pragma unroll
+        for (int j = 0; j < VG; ++j)
+#pragma unroll
+          for (int k2 = 0; k2 < G; ++k2) {
+            const int k1 = scat_index<N1>(g, j, k2);
+            // entries (Q00, Q11, Q01, Q22, Q12, Q02) of the block, three bf16 pairs
+            const __nv_bfloat162* qp = reinterpret_cast<const __nv_bfloat162*>(qrow + (long long)k1 * 6 * M);
+            const float2 qa = __bfloat1622float2(qp[0]), qb = __bfloat1622float2(qp[1]),
+                         qc = __bfloat1622float2(qp[2]);
+            const float q00 = qa.x * sc, q11 = qa.y * sc, q01 = qb.x * sc, q22 = qb.y * sc, q12 = qc.x * sc,
+                        q02 = qc.y * sc;
+            C* r0 = tile_at(t_hat, k1, p);
+            C* r1 = tile_at(t_hat + TB, k1, p);
+            C* r2 = tile_at(t_hat + 2 * TB, k1, p);
+            const C R0 = *r0, R1 = *r1, R2 = *r2;
+            const C S0 = make_float2(q00 * R0.x + q01 * R1.x + q02 * R2.x, q00 * R0.y + q01 * R1.y + q02 * R2.y);
+            const C S1 = make_float2(q01 * R0.x + q11 * R1.x + q12 * R2.x, q01 * R0.y + q11 * R1.y + q12 * R2.y);
+            const C S2 = make_float2(q02 * R0.x + q12 * R1.x + q22 * R2.x, q02 * R0.y + q12 * R1.y + q22 * R2.y);
+            part = fmaf(R0.x, S0.x, fmaf(R0.y, S0.y, part));
+            part = fmaf(R1.x, S1.x, fmaf(R1.y, S1.y, part));
+            part = fmaf(R2.x, S2.x, fmaf(R2.y, S2.y, part));
+            *r0 = S0;
+            *r1 = S1;
+            *r2 = S2;
+          }
+        gam.add(wt * part);
+      }
+      __syncwarp();
+      // inverse transforms back to the natural order, component by component
+#pragma unroll 1
+      for (int cc = 0; cc < 3; ++cc) {
+        unsigned char* t = t_hat + cc * TB;
+#pragma unroll
+        for (int j = 0; j < VG; ++j)
+#pragma unroll
+          for (int k2 = 0; k2 < G; ++k2) v[j * G + k2] = *tile_at(t, scat_index<N1>(g, j, k2), p);
+        fft_dist_b_at<N1, +1>(v, g, SwzSlot{t, p}, tw1);
+        __syncwarp();
+#pragma unroll
+        for (int n1 = 0; n1 < V; ++n1) *tile_at(t, g + G * n1, p) = v[n1];
+        __syncwarp();
+      }
+      fence_async_shared();
+    }
+    __syncthreads();
+    if (!s_abort && tid == 0) {
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) tma_store_3d(&maps.shat, 2 * pos0, 0, bl * 3 + cc, t_hat + cc * TB);
+      tma_store_commit();
+    }
+  }
+  pdl_trigger();
+  double2 pr;
+  pr.x = block_sum_acc(gam, red_sh);
+  pr.y = block_sum_acc(rso, red_sh);
+  if (tid == 0) {
+    double* pp = a.red.part + ((long long)bl * gridDim.x + blockIdx.x) * 2;
+    pp[0] = pr.x;
+    pp[1] = pr.y;
+  }
+  if (last_block(a.red.ticket)) {
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int q = warp; q < a.BL; q += NTH / 32) {
+      const double* pp = a.red.part + (long long)q * gridDim.x * 2;
+      const double sg = warp_sum_partials(pp, gridDim.x, 2);
+      const double sr = warp_sum_partials(pp + 1, gridDim.x, 2);
+      if (lane == 0 && !a.sc[q].done) direction_update(a.sc[q], sg, sr, a.flexible);
+    }
+    __syncthreads();
+    if (tid == 0) *a.red.ticket = 0u;
+  }
+  if (active && tid == 0) tma_store_wait_all();
+}
+
 // ---------------------------------------------------------------- host side
 bool line_tma3_supported(const Grid& g) {
-  if (!(g.n1 == 16 || g.n1 == 32 || g.n1 == 64)) return false;
+  if (!(g.n1 == 16 || g.n1 == 32 || g.n1 == 64 || g.n1 == 96 || g.n1 == 128 || g.n1 == 192 || g.n1 == 256))
+    return false;
   const long long M = (long long)g.n2 * g.n3h;
   if (M % 8 != 0) return false;  // 16-byte row strides of the Q and spectrum tensors
   return tensor_map_encoder() != nullptr;
@@ -237,6 +419,19 @@ CUresult encode3(CUtensorMap* m, CUtensorMapDataType dt, size_t esz, const void*
   const cuuint32_t estr[3] = {1u, 1u, 1u};
   return tensor_map_encoder()(m, dt, 3, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                               sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+}
+
+template <int N1>
+cudaError_t line_tma3w_n(const Line3Maps& maps, const Line3Args& la, cudaStream_t st) {
+  constexpr int NTH = K3_P * RegSplit<N1>::G;
+  const size_t smem = k3w_smem_bytes<N1>();
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_line_tma3w<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  return launch_pdl(k_line_tma3w<N1>, dim3(la.tiles, la.a.BL), dim3(NTH), smem, st, maps, la);
 }
 
 template <int N1>
@@ -275,6 +470,10 @@ cudaError_t launch_line_tma3(const LineArgs<float, __nv_bfloat16>& a, int* err, 
     case 16: return line_tma3_n<16>(maps, la, st);
     case 32: return line_tma3_n<32>(maps, la, st);
     case 64: return line_tma3_n<64>(maps, la, st);
+    case 96: return line_tma3w_n<96>(maps, la, st);
+    case 128: return line_tma3w_n<128>(maps, la, st);
+    case 192: return line_tma3w_n<192>(maps, la, st);
+    case 256: return line_tma3w_n<256>(maps, la, st);
     default: return cudaErrorInvalidValue;
   }
 }
