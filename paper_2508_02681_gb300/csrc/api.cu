@@ -785,9 +785,11 @@ static bool ku_tile_ok(const Grid& g, int c, int tile) {
 //    (8, 6), (16, 6) with at least one block per SM over all (instance, load) fields, else the
 //    register column march (64^3, 3 loads, back-to-back launches: 5.6 us for (8, 6) against 8.0
 //    for the column march and 9.0 for the best TMA tile);
-//  * from 10^6 nodes: the first of (4, 24), (8, 24), (4, 12), (8, 12) with at least two blocks
-//    per SM (256^3 x 3 loads: 197 / 202 us against 237 for the best TMA tile; 192^3: 110 / 114
-//    against 125), else the TMA tile of most blocks.
+//  * from 10^6 nodes: of the vector shapes (4, 24), (8, 24), (4, 12), (8, 12), (2, 12) with at
+//    least two blocks per SM the one that keeps the most warps resident, the earlier on a tie
+//    (256^3 x 3 loads: (4, 24) 178 us against 182 for (2, 12) and 218 for the best TMA tile;
+//    192^3: (2, 12) 88 us, 15 warps per SM, against 97 us for (4, 24), 12 warps), else the TMA
+//    tile of most blocks.
 static int ku_tma_choice(const unocg_ctx* ctx) {
   if (ctx->c != 1 || ctx->ku_tile == 0) return 0;
   if (ctx->ku_tile > 0) return ku_tile_ok(ctx->g, 1, ctx->ku_tile) ? ctx->ku_tile : 0;
@@ -801,7 +803,16 @@ static int ku_tma_choice(const unocg_ctx* ctx) {
     return 0;
   };
   if (ctx->g.n < 1000000) return first_vec({8, 5}, sms);  // (8, 6), (16, 6); else the column march
-  const int v = first_vec({6, 4, 1, 2}, 2 * sms);         // (4, 24), (8, 24), (4, 12), (8, 12)
+  // from 10^6 nodes: of (4, 24), (8, 24), (4, 12), (8, 12), (2, 12) with at least two blocks per
+  // SM, the one with the most resident warps (128 registers a thread), the earlier on a tie
+  int v = 0, v_warps = 0;
+  for (int k : {6, 4, 1, 2, 3}) {
+    const KuTmaShape sh = kKuTmaShapes[k - 1];
+    if (!ku_vec_supported(ctx->g, 1, sh) || BL * ku_vec_blocks_x(ctx->g, sh) < 2 * sms) continue;
+    const int threads = ku_tma_threads(ctx->g, sh);
+    const int warps = std::min(65536 / (threads * 128), 2048 / threads) * (threads / 32);
+    if (warps > v_warps) { v = kKuTmaNumShapes + k; v_warps = warps; }
+  }
   if (v) return v;
   int most = 0;
   long long most_blocks = -1;

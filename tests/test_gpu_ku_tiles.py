@@ -164,13 +164,14 @@ def test_vector_march_solve_matches_oracle():
 
 
 def test_auto_choice_takes_the_vector_march_on_large_grids():
-    """Three loads: 256^3 takes the vector march with shape (4, 24) (tile 14); 64^3, below 10^6
-    nodes per field, the one with shape (8, 6) (tile 16, at least one block per SM); a grid too
-    small for one block per SM the column march (tile 0)."""
+    """Three loads: 256^3 takes the vector march with shape (4, 24) (tile 14); 192^3 the one with
+    shape (2, 12) (tile 11: 15 warps per SM against 12 for (4, 24)); 64^3, below 10^6 nodes per
+    field, the one with shape (8, 6) (tile 16, at least one block per SM); a grid too small for
+    one block per SM the column march (tile 0)."""
     from paper_2508_02681_gb300 import _lib, api
     from paper_2508_02681_gb300.solver import Homogenization
     from synth import unit_loads
-    for shape, want in (((256, 256, 256), 14), ((64, 64, 64), 16), ((24, 16, 32), 0)):
+    for shape, want in (((256, 256, 256), 14), ((192, 192, 192), 11), ((64, 64, 64), 16), ((24, 16, 32), 0)):
         h = Homogenization(_lib.THERMAL, shape)
         h.set_microstructure(np.zeros(shape, dtype=np.uint8), 2)
         h.set_phase_properties(np.array([1.0, 2.0]))
