@@ -277,6 +277,25 @@ __global__ void __launch_bounds__(K3_P * RegSplit<N1>::G, k3w_min_blocks<N1>())
     for (int cc = 0; cc < 3; ++cc) tma_load_3d(t_hat + cc * TB, &maps.hat, 2 * pos0, 0, bl * 3 + cc, &bar);
   }
   DotAcc<float> gam, rso;
+  // lanes: see the header of this section
+  const int warp = tid >> 5, lane = tid & 31;
+  const int w = G == 16 ? (lane >> 3) & 1 : lane / G;
+  const int g = G == 16 ? (lane & 7) + ((lane >> 4) << 3) : lane % G;
+  const int p = warp * W + w;  // position within the tile
+  const int pos = pos0 + p;
+  const bool on = pos < M;
+  // previous s_hat of this position, component cc, row r: [(bl * 3 + cc) * N1 + r] * M + pos; the
+  // values of one component are requested one step ahead (component 0 while the tiles arrive)
+  const C* so_base = reinterpret_cast<const C*>(a.shat) + (long long)bl * 3 * N1 * M + (on ? pos : 0);
+  const bool use_so = active && a.flexible && on;
+  C so[V];
+  auto load_so = [&](int cc) {
+    if (use_so) {
+#pragma unroll
+      for (int n1 = 0; n1 < V; ++n1) so[n1] = __ldg(so_base + ((long long)cc * N1 + g + G * n1) * M);
+    }
+  };
+  load_so(0);
   if (active) {
     if (!mbar_wait(&bar, 0u, la.spin_limit)) {
       s_abort = 1;
@@ -285,26 +304,15 @@ __global__ void __launch_bounds__(K3_P * RegSplit<N1>::G, k3w_min_blocks<N1>())
     __syncthreads();
     if (s_abort && tid == 0) (void)mbar_wait(&bar, 0u, la.spin_limit);
     if (!s_abort) {
-      const int warp = tid >> 5, lane = tid & 31;
-      const int w = G == 16 ? (lane >> 3) & 1 : lane / G;
-      const int g = G == 16 ? (lane & 7) + ((lane >> 4) << 3) : lane % G;
-      const int p = warp * W + w;  // position within the tile
-      const int pos = pos0 + p;
-      const bool on = pos < M;
       const int k3 = on ? pos % a.g.n3h : 0;
       const float wt = (k3 == 0 || 2 * k3 == a.g.n3) ? 1.f : 2.f;
       const float sc = (float)a.scale;
-      // previous s_hat of this position, component cc, row r: [(bl * 3 + cc) * N1 + r] * M + pos
-      const C* so_base = reinterpret_cast<const C*>(a.shat) + (long long)bl * 3 * N1 * M + (on ? pos : 0);
       C v[V];
       // forward transforms, component by component; r . s_old on the way
 #pragma unroll 1
       for (int cc = 0; cc < 3; ++cc) {
         unsigned char* t = t_hat + cc * TB;
-        if (a.flexible && on) {
-          C so[V];
-#pragma unroll
-          for (int n1 = 0; n1 < V; ++n1) so[n1] = __ldg(so_base + ((long long)cc * N1 + g + G * n1) * M);
+        if (use_so) {
           float part = 0.f;
 #pragma unroll
           for (int n1 = 0; n1 < V; ++n1) {
@@ -313,6 +321,7 @@ __global__ void __launch_bounds__(K3_P * RegSplit<N1>::G, k3w_min_blocks<N1>())
           }
           rso.add(wt * part);
         }
+        if (cc < 2) load_so(cc + 1);
 #pragma unroll
         for (int n1 = 0; n1 < V; ++n1) v[n1] = *tile_at(t, g + G * n1, p);
         fft_dist_a_at<N1, -1>(v, g, SwzSlot{t, p}, tw1);
