@@ -28,7 +28,8 @@ constexpr int K2_THREADS = 160;
 // one layer: [a2][component][slot] float2 (forces on nodes e, e + 1) and float (node e + 2); then
 // the carried upper-plane corners [4 corners][component][slot] float2
 constexpr int K2_LAYER_F2 = 2 * 3 * K2_SLOTS;
-constexpr size_t kKuEl2Smem = 2 * (size_t)K2_LAYER_F2 * (sizeof(float2) + sizeof(float)) + 12 * K2_SLOTS * sizeof(float2);
+constexpr size_t kKuEl2Smem = 2 * (size_t)K2_LAYER_F2 * (sizeof(float2) + sizeof(float)) + 12 * K2_SLOTS * sizeof(float2) +
+                               3 * 3 * K2_SLOTS * sizeof(float2);
 
 __device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 p_sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
@@ -146,6 +147,12 @@ __global__ void __launch_bounds__(K2_THREADS, 4) k_ku_el2(StencilArgs<float> a) 
   // the upper-plane corner forces of the pair wait for the next layer here, [corner][comp][slot]
   // (in shared memory rather than registers: four blocks per SM instead of three)
   float2* carry = reinterpret_cast<float2*>(r_buf + 2 * K2_LAYER_F2);
+  // d at the pair's nodes (e, e + 1) of its lower node row, [plane mod 3][component][slot]: the
+  // node-pair threads of the next layer take d for the dot product d . p from here.  Plane q is
+  // written in the element phase of layer q - 1 and read in the node phase of layer q; three
+  // buffers, because the element phase of layer q + 1 (writing plane q + 2) may already run
+  // while other threads are in the node phase of layer q.
+  float2* dsave = carry + 12 * K2_SLOTS;
   // element pair of this thread: elements e, e + 1 (e even) of element row e2
   const bool is_el = tid < K2_SLOTS;
   const int s2 = tid / K2_PAIRS, kp = tid - s2 * K2_PAIRS;
@@ -164,12 +171,13 @@ __global__ void __launch_bounds__(K2_THREADS, 4) k_ku_el2(StencilArgs<float> a) 
   const float h = g.hf;
   DotAcc<float> dp;
   W2p L[3], H[3];
-  auto load_plane = [&](int z, W2p(&W)[3]) {
+  auto load_plane = [&](int z, W2p(&W)[3], float2* save) {
     const float* dz = d + (long long)z * S;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       const float* di = dz + (long long)i * n;
       const float2 lo = __ldg(reinterpret_cast<const float2*>(di + rlo + ce));
+      if (save) save[i * K2_SLOTS + tid] = lo;
       const float2 hi = __ldg(reinterpret_cast<const float2*>(di + rhi + ce));
       W[i] = walsh_pair(lo, __ldg(di + rlo + ce2), hi, __ldg(di + rhi + ce2));
     }
@@ -183,8 +191,8 @@ __global__ void __launch_bounds__(K2_THREADS, 4) k_ku_el2(StencilArgs<float> a) 
     if (is_el) {
       // the element layer below the first node plane only contributes its upper corners
       const int zm = z0 ? z0 - 1 : n1 - 1;
-      load_plane(zm, L);
-      load_plane(z0, H);
+      load_plane(zm, L, nullptr);
+      load_plane(z0, H, dsave);
       float2 k[7], flo[4][3], fhi[4][3];
       consts_at(zm, k);
       element_pair(L, H, k, flo, fhi);
@@ -199,7 +207,7 @@ __global__ void __launch_bounds__(K2_THREADS, 4) k_ku_el2(StencilArgs<float> a) 
       if (is_el) {
 #pragma unroll
         for (int i = 0; i < 3; ++i) L[i] = H[i];
-        load_plane(z + 1 == n1 ? 0 : z + 1, H);
+        load_plane(z + 1 == n1 ? 0 : z + 1, H, dsave + ((z + 1 - z0) % 3) * 3 * K2_SLOTS);
         float2 k[7], flo[4][3], fhi[4][3];
         consts_at(z, k);
         element_pair(L, H, k, flo, fhi);
@@ -232,7 +240,7 @@ __global__ void __launch_bounds__(K2_THREADS, 4) k_ku_el2(StencilArgs<float> a) 
           const float w0 = rr[i * K2_SLOTS + sA - 1], w1 = rr[(3 + i) * K2_SLOTS + sB - 1];
           const float2 v = make_float2((u0.x + w0) + (u1.x + w1), u0.y + u1.y);
           *reinterpret_cast<float2*>(p + (long long)i * n + q) = v;
-          const float2 dv = __ldg(reinterpret_cast<const float2*>(d + (long long)i * n + q));
+          const float2 dv = dsave[((z - z0) % 3) * 3 * K2_SLOTS + i * K2_SLOTS + sA];  // nodes (n, n + 1)
           sp = fmaf(v.x, dv.x, sp);
           sp = fmaf(v.y, dv.y, sp);
         }
