@@ -2,8 +2,8 @@
 // in the Walsh basis of ku_elastic.cuh, with two neighbouring elements of a row computed together
 // in packed FP32x2 arithmetic (one instruction for both elements of every add, multiply and fma).
 //
-// Work layout: a block computes the same 32 (i3) x 8 (i2) node tile over KE_CZ node planes as
-// k_ku_el.  Its first 17 x 9 threads each own one element pair (e, e + 1), e even, of one element
+// Work layout: a block computes the same 32 (i3) x 8 (i2) node tile as k_ku_el, over 16 or 32
+// node planes.  Its first 17 x 9 threads each own one element pair (e, e + 1), e even, of one element
 // row (the tile's elements plus the lower halo row and the pair holding the lower halo column)
 // and march along i1: per element layer a thread loads its two node rows of the new node plane
 // (one 8-byte load of nodes e, e + 1 and one 4-byte load of node e + 2 per row and component),
@@ -12,8 +12,10 @@
 // at once; the thread publishes, per component and lower/upper node row, (force on node e, force
 // on node e + 1) and the force on node e + 2 in a double-buffered shared array (one barrier per
 // layer), keeping the upper-plane corners for the next layer.  The first 16 x 8 threads then own
-// two nodes each and add the four contributions of the neighbouring pairs and rows.  Measured at
-// 256^3 x 6 loads: 1644 us per launch against 2336 us for the scalar element kernel.
+// two nodes each and add the four contributions of the neighbouring pairs and rows, taking d for
+// the dot product d . p from the element threads' loads.  Measured at 256^3 x 6 loads: 1433 us
+// per launch against 2336 us for the scalar element kernel.
+#include <cstdlib>
 #include "kargs.h"
 #include "stencil.cuh"
 #include "ku_elastic.cuh"
@@ -118,7 +120,7 @@ __device__ __forceinline__ void element_pair(const W2p (&L)[3], const W2p (&H)[3
 }
 }  // namespace
 
-__global__ void __launch_bounds__(K2_THREADS, 4) k_ku_el2(StencilArgs<float> a) {
+__global__ void __launch_bounds__(K2_THREADS, 4) k_ku_el2(StencilArgs<float> a, int cz) {
   extern __shared__ __align__(16) unsigned char k2_raw[];
   __shared__ __align__(16) float mt[2 * 256];
   __shared__ double red_sh[32];
@@ -138,8 +140,8 @@ __global__ void __launch_bounds__(K2_THREADS, 4) k_ku_el2(StencilArgs<float> a) 
   bx /= nt3;
   const int b2 = bx % nt2;
   const int b1 = bx / nt2;
-  const int t3 = b3 * KE_T3, t2 = b2 * KE_T2, z0 = b1 * KE_CZ;
-  const int zend = min(z0 + KE_CZ, n1);
+  const int t3 = b3 * KE_T3, t2 = b2 * KE_T2, z0 = b1 * cz;
+  const int zend = min(z0 + cz, n1);
   const long long S = (long long)n2 * n3;
   const int tid = threadIdx.x;
   float2* lf_buf = reinterpret_cast<float2*>(k2_raw);                 // [2 layers][K2_LAYER_F2]
@@ -274,7 +276,15 @@ cudaError_t launch_ku_el2(const StencilArgs<float>& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  return launch_pdl(k_ku_el2, dim3(ke_tiles(a.g), a.BL), dim3(K2_THREADS), kKuEl2Smem, s, a);
+  // node planes per block: 16 below 10^6 nodes per field, 32 from there (one pre-loop element
+  // layer per block; 256^3 x 6 loads: 1616 / 1505 / 1433 us per launch for 8 / 16 / 32 planes,
+  // 64^3 elastic solve 4.20 ms with 16 against 4.53 ms with 32); UNOCG_KE2_CZ overrides
+  const Grid& g = a.g;
+  const char* e = std::getenv("UNOCG_KE2_CZ");
+  const int cz = (e && std::atoi(e) > 0) ? std::atoi(e) : (g.n >= 1000000 ? 32 : 16);
+  const int tiles = ((g.n3 + KE_T3 - 1) / KE_T3) * ((g.n2 + KE_T2 - 1) / KE_T2) * ((g.n1 + cz - 1) / cz);
+  if (tiles > ke_tiles(g)) return cudaErrorInvalidValue;  // partial sums are sized for KE_CZ planes
+  return launch_pdl(k_ku_el2, dim3(tiles, a.BL), dim3(K2_THREADS), kKuEl2Smem, s, a, cz);
 }
 
 }  // namespace unocg
