@@ -9,8 +9,11 @@
 // Q (16 positions x N1 rows); an mbarrier with a transaction count signals their arrival.  A
 // line (one position) is transformed by G threads of one warp in registers (fft_reg.cuh: V
 // values each, one exchange through shared memory; the s_old tile, once its products with
-// r_hat are summed, is the exchange scratch).  The result overwrites the r_hat tile in place
-// (every thread writes the elements it read) and one bulk tensor store writes it to s_hat.
+// r_hat are summed, holds the exchange slots, each line its own N1 with the slot index bit 3
+// flipped for every other line).  The 16 threads of the two 256-point lines of a warp interleave
+// their lanes so that a half-warp reads eight consecutive rows of two positions (eight distinct
+// 16-byte chunks of the swizzle, no bank conflicts).  The result overwrites the r_hat tile in
+// place (every thread writes the elements it read) and one bulk tensor store writes it to s_hat.
 // Loads of whole 128-byte rows replace the 16-byte-per-row accesses of a warp holding two
 // positions of 256-point lines.
 #include <cstdlib>
@@ -209,8 +212,8 @@ int line_tma_blocks_x(const Grid& g) { return (int)(((long long)g.n2 * g.n3h + 7
 
 // positions per block: 16 (128-byte rows, 128-byte swizzle; the default) or 8 (64-byte rows,
 // 64-byte swizzle: half the shared memory per block, about twice the blocks per SM), selected by
-// UNOCG_LINE_P at every launch.  Measured per launch with three loads: 256^3 203.6 (16) against
-// 203.4 us (8), 192^3 83.4 against 97.6 us.
+// UNOCG_LINE_P at every launch.  Measured per launch with three loads, before the conflict-free
+// lane layout: 256^3 203.6 (16) against 203.4 us (8), 192^3 83.4 against 97.6 us.
 static int line_tma_p(const Grid&) {
   const char* e = std::getenv("UNOCG_LINE_P");
   return (e && std::atoi(e) == 8) ? 8 : 16;

@@ -2,7 +2,8 @@
 // Algorithm 2: FFT of each displacement component along axis 1, the block multiply
 // s_hat(k) = Q(k) r_hat(k) / n with the symmetric 3 x 3 block Q(k) of every frequency, the
 // Parseval partials of r . s and, for the flexible variant, r . s_old, inverse FFT along axis 1)
-// on tiles staged by the TMA, for axes of N1 <= 64 points.
+// on tiles staged by the TMA: k_line_tma3 for axes of N1 <= 64 points (all operands staged),
+// k_line_tma3w for 96..256 points (only the r_hat tiles staged; see its section below).
 //
 // A block owns K3_P = 16 consecutive (k2, k3) positions of one (instance, load) over all N1
 // values of axis 1 and all three components.  One thread issues the tile copies: r_hat and
@@ -14,7 +15,8 @@
 // three components of its own frequencies, and the inverse transforms follow component by
 // component.  So a thread holds one component's V values at a time, where the register pass
 // (k_line_reg) holds all three.  The first s_old tile, once its products with r_hat are summed,
-// is the exchange scratch; bulk tensor stores write the three results to s_hat.
+// holds the exchange slots (each line its own N1, bit 3 of the slot index flipped for every
+// other line); bulk tensor stores write the three results to s_hat.
 #include "kargs.h"
 #include "fft_reg.cuh"
 #include "tma.cuh"

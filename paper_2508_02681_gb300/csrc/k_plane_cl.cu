@@ -1,21 +1,25 @@
-// Transform passes of 256 x 256 planes (axes 2 and 3) of the mixed-precision loop on thread-block
-// clusters of two CTAs (Algorithm 2: forward and inverse unitary transform around the block
-// multiply; FP32).
+// Transform passes of 256 x 256 planes (axes 2 and 3) of the mixed-precision loop (Algorithm 2:
+// forward and inverse unitary transform around the block multiply; FP32).  A half-spectrum plane
+// of 256 rows x 129 complex FP32 values (264 KB) exceeds one block's shared memory, so a
+// transform is either two passes through global memory or one pass over two blocks.
 //
-// A half-spectrum plane of 256 rows x 129 complex FP32 values (264 KB) exceeds one block's
-// shared memory; one pass over it needs two.  The two CTAs of a cluster split the plane by rows
-// for the axis-3 transforms and by columns for the axis-2 transforms, and move the values between
-// the two splits through distributed shared memory: a CTA writes each row result into the shared
-// memory of the CTA that owns its column (rank 0: columns 0..64, rank 1: 65..128).  One cluster
-// barrier separates the phases.  Each phase uses the register-resident line FFTs of
-// fft_reg.cuh (rows: 128-point half-length lines, 8 threads each; columns: 256-point lines, 16
-// threads each).  This replaces the row pass plus the separate in-place axis-2 pass (one global
-// round trip of the spectrum less per transform).
+// Two passes (the default): register row passes (k_rows_fwd256 / k_rows_inv256: 4 rows a warp,
+// the CG updates fused) and a register column pass (k_cols_reg256: two columns a warp, read
+// straight into the line FFT's distribution, no block barrier).
+//
+// One pass on thread-block clusters of two CTAs (selected per transform): the two CTAs split the
+// plane by rows for the axis-3 transforms and by columns for the axis-2 transforms, and move the
+// values between the two splits through distributed shared memory: a CTA writes each row result
+// into the shared memory of the CTA that owns its column (rank 0: columns 0..64, rank 1:
+// 65..128), with one cluster barrier between the phases.
 //
 //   k_plane_fwd_cl: r <- r - alpha p, ||r||_inf, rows (axis 3, r2c), exchange, columns (axis 2),
 //                   r_hat written; the last block performs the residual check.
 //   k_plane_inv_cl: columns (inverse axis 2) from s_hat, exchange, rows (c2r),
 //                   u <- u + alpha d_old, d <- s + beta d_old.
+//
+// Every phase uses the register-resident line FFTs of fft_reg.cuh (rows: 128-point half-length
+// lines, 8 threads each; columns: 256-point lines, 16 threads each).
 #include <cooperative_groups.h>
 #include "kargs.h"
 #include "fft_reg.cuh"
