@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--bc", default="periodic", choices=["periodic", "dirichlet", "mixed"],
                     help="with --profile-only: boundary conditions of the profiled solves (mixed: Dirichlet faces on axis 2)")
     ap.add_argument("--elastic", action="store_true",
-                    help="with --profile-only: the 64^3 elastic workload (six loads) instead of the thermal one")
+                    help="with --profile-only: the 64^3 elastic workload (six loads) instead of the thermal one; "
+                         "with --grid, an elastic N^3 workload (six loads, contrast 10)")
     ap.add_argument("--no-elastic", action="store_true", help="skip the elastic measurement")
     ap.add_argument("--no-dirichlet", action="store_true", help="skip the Dirichlet-BC measurement")
     ap.add_argument("--no-hbm", action="store_true", help="skip the HBM-resident (192^3, 256^3) measurement")
@@ -509,7 +510,13 @@ def main():
         if args.no_graph:
             opts.use_graph = 0
         hp = h
-        if args.elastic:
+        if args.elastic and args.grid:
+            h.close()
+            from synth import config_seed
+            we = hbm_workload(3, args.grid, 6.0 * args.grid / 64.0, 10.0, config_seed(6, 1))
+            L = we["loads"].shape[0]
+            hp = periodic_solver(we, stream)
+        elif args.elastic:
             h.close()
             we = workload(3)
             L = we["loads"].shape[0]
