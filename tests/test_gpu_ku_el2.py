@@ -1,9 +1,9 @@
 """The FP32 elastic K d with element pairs in packed FP32x2 arithmetic (Sec. 4.1, element forces in
 the Walsh basis, two elements of a row per thread) against the assembled K of the oracle: grids of
 one and several node tiles along every axis, ragged tiles (N3 not a multiple of 32, N2 not a
-multiple of 8, N1 not a multiple of the plane chunk), two- and four-node periodic axes (the halo
-element pairs wrap onto the tile itself), several phases; and a mixed-precision elastic solve with
-it against the oracle's flexible PCG."""
+multiple of 8, N1 not a multiple of the plane chunk of 8, 16 or 32 planes), two- and four-node
+periodic axes (the halo element pairs wrap onto the tile itself), several phases; and a
+mixed-precision elastic solve with it against the oracle's flexible PCG."""
 import numpy as np
 import pytest
 
@@ -22,8 +22,11 @@ def _props():
     return np.array([[1.0, 0.3], [10.0, 0.2], [3.0, 0.45]])
 
 
+@pytest.mark.parametrize("cz", ["", "8", "32"])
 @pytest.mark.parametrize("shape", SHAPES)
-def test_K32_elastic_pairs_match_assembled_K(shape, monkeypatch):
+def test_K32_elastic_pairs_match_assembled_K(shape, cz, monkeypatch):
+    """`cz`: node planes per block (default: 16 below 10^6 nodes per field; 8 and 32 as set by
+    UNOCG_KE2_CZ, 32 being the default of large grids)."""
     import torch
     from paper_2508_02681_gb300 import api
     phase = random_phase(shape, 3, seed=sum(shape) + 1)
@@ -35,6 +38,8 @@ def test_K32_elastic_pairs_match_assembled_K(shape, monkeypatch):
     K = fem.assemble_K(phase, props, 3)
     p_ref = fem.to_soa(K @ fem.from_soa(d.astype(np.float64)), 3, shape)
     dd = torch.tensor(d, device="cuda")
+    if cz:
+        monkeypatch.setenv("UNOCG_KE2_CZ", cz)
     out = {}
     for flag in ("1", "0"):
         monkeypatch.setenv("UNOCG_KU_EL2", flag)
